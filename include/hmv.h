@@ -1,0 +1,149 @@
+/*
+ * hmv.h -- exact multiprecision Hankel / Toeplitz / circulant matrix-vector
+ * product on one NVIDIA GB300 GPU (sm_103a).
+ *
+ * Operation (Beliakov, arXiv:1402.5287, Sec. 1, matrices A_H, A_T, A_C and
+ * the schoolbook product): for n x n structured A and vector x,
+ *     Hankel     y_i = sum_{j<n} h_{i+j} x_j            h has 2n-1 entries
+ *     Toeplitz   y_i = sum_{j<n} h_{n-1-i+j} x_j        h has 2n-1 entries
+ *     Circulant  y_i = sum_{j<n} c_{(i-j) mod n} x_j     c has n entries
+ * (0-based indices).  Toeplitz is computed as the row-reversed Hankel
+ * product and circulant as a Toeplitz product with the wrapped sequence
+ * h_k = c_{(n-1-k) mod n}, as Sec. 1 describes.
+ *
+ * Methods: the recursive half-size Hankel products of Sec. 3 (Algorithm 1)
+ * down to a leaf size, with every leaf product done as an exact digit-plane
+ * contraction on the tensor cores; or a plain schoolbook kernel on 32-bit
+ * limbs (comparison).  Every intermediate is an exact integer, so all
+ * methods return bit-identical results.
+ *
+ * Number format (block fixed point, one exponent per vector):
+ *     value_k = (neg_k ? -1 : +1) * M_k * 2^(exponent - b),   0 <= M_k < 2^b
+ * M_k is stored as ceil(b/32) little-endian uint32 limbs, entries one after
+ * another (entry-major); neg_k is one uint8 per entry.  For nrhs > 1 the
+ * right-hand sides are stored one after another (vector r holds entries
+ * r*len .. r*len+len-1).
+ *
+ * Result rounding (the paper assumes MPFR-style numbers and states no rule):
+ * the exact rows Z_i = sum_j (+-M_a)(+-M_x) are rounded to b bits, half to
+ * even, with the least exponent E_y for which every rounded mantissa is
+ * below 2^b.  E_y is chosen from the exact rows (no double rounding).  An
+ * all-zero result has E_y = E_h + E_x; a zero entry has neg = 0.
+ *
+ * Errors: every call returns an hmv_status; nothing is thrown across this
+ * interface.  A call that returns an error writes no output.
+ * Concurrency: a plan is not re-entrant; distinct plans may be used from
+ * different threads on different streams.
+ */
+#ifndef HMV_H_
+#define HMV_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HMV_OK = 0,
+    HMV_EINVAL = 1,        /* bad argument: sizes, b, kind, bits set at or above b, ... */
+    HMV_ENOMEM = 2,        /* device or host allocation failed */
+    HMV_ECUDA = 3,         /* a CUDA runtime/driver call failed */
+    HMV_ETIMEOUT = 4,      /* a bounded device-side wait gave up (kernel returned early) */
+    HMV_ENOTLOADED = 5,    /* hmv_matvec before hmv_load_matrix */
+    HMV_EFFTBOUND = 6,     /* FFT path: error bound not below 1/2 (no result written) */
+    HMV_EUNSUPPORTED = 7   /* method or configuration not available in this build */
+} hmv_status;
+
+typedef enum { HMV_HANKEL = 0, HMV_TOEPLITZ = 1, HMV_CIRCULANT = 2 } hmv_kind;
+
+typedef enum {
+    HMV_AUTO = 0,          /* Karatsuba recursion with the cost-model depth */
+    HMV_SCHOOLBOOK = 1,    /* plain schoolbook on 32-bit limbs, CUDA cores */
+    HMV_KARATSUBA = 2,     /* Algorithm 1 to the given depth, tensor-core leaves */
+    HMV_FFT64 = 3          /* split-FP64 FFT with a proven rounding bound */
+} hmv_method;
+
+/* flags for hmv_desc.flags */
+#define HMV_FLAG_TIMING 1u     /* record CUDA-event times of each stage (hmv_get_stats) */
+#define HMV_FLAG_SIMT_LEAF 2u  /* leaf products on CUDA cores instead of tensor cores */
+
+typedef struct {
+    int32_t n;        /* matrix order, n >= 1 */
+    int32_t b;        /* mantissa bits, 1 <= b <= 1<<20 */
+    int32_t nrhs;     /* right-hand sides per hmv_matvec, >= 1 */
+    int32_t kind;     /* hmv_kind */
+    int32_t method;   /* hmv_method */
+    int32_t levels;   /* Karatsuba depth L (levels of Algorithm 1); -1 = cost model */
+    uint32_t flags;   /* HMV_FLAG_* */
+    int32_t reserved; /* must be 0 */
+} hmv_desc;
+
+typedef struct {
+    int32_t len;       /* entries per vector */
+    int32_t nrhs;      /* vectors */
+    int32_t b;         /* mantissa bits (must equal the plan's b) */
+    int32_t exponent;  /* block exponent E (written by hmv_matvec for y) */
+    uint32_t *limbs;   /* len*nrhs*ceil(b/32) limbs, caller-owned */
+    uint8_t *neg;      /* len*nrhs sign flags, caller-owned */
+    int32_t on_device; /* 1: limbs/neg are device pointers (stream-ordered on the
+                          plan's stream), 0: host pointers (call is synchronous) */
+    int32_t reserved;  /* must be 0 */
+} hmv_vec;
+
+typedef struct hmv_plan_s hmv_plan_t;
+
+typedef struct {
+    int32_t levels;          /* Karatsuba depth actually used */
+    int32_t leaves;          /* 3^levels */
+    int32_t leaf_rows_max;   /* largest leaf order */
+    int32_t digits;          /* balanced radix-2^8 digits per operand in the tree */
+    int64_t leaf_tiles;      /* 128 x 256 output tiles per matvec */
+    double leaf_macs;        /* useful digit multiply-adds per matvec in the leaves */
+    double leaf_macs_issued; /* digit multiply-adds issued to the tensor cores */
+    int64_t device_bytes;    /* device memory held by the plan */
+    /* with HMV_FLAG_TIMING: accumulated milliseconds and launch counts */
+    double ms_prepass, ms_leaf, ms_post, ms_round, ms_total;
+    int64_t launches_leaf, launches_total, matvecs;
+} hmv_stats;
+
+/* Create a plan: checks the descriptor, chooses the recursion depth and
+ * allocates device memory.  stream: a cudaStream_t (NULL = legacy default
+ * stream).  *out is set only on HMV_OK; release it with hmv_free. */
+hmv_status hmv_plan(const hmv_desc *desc, void *stream, hmv_plan_t **out);
+
+/* Load the matrix sequence h (len 2n-1, or n for circulant; nrhs 1).  The
+ * plan encodes it into resident device digit planes and runs the matrix
+ * side of Algorithm 1, steps 4 and 6, for every level once; h may be freed
+ * after the call returns (host) or after the stream reaches it (device). */
+hmv_status hmv_load_matrix(hmv_plan_t *plan, const hmv_vec *h);
+
+/* Y = A X for the loaded matrix and a block of nrhs right-hand sides (one
+ * shared exponent, as every hmv_vec has).  x: len n, nrhs = plan nrhs.
+ * y: len n, nrhs = plan nrhs, same b, limbs and neg allocated by the
+ * caller; y->exponent is written: the least exponent over the whole block.
+ * x and y must both be host or both be device pointers.  Device pointers:
+ * the work is ordered on the plan's stream; the call returns once the
+ * exponent has been read back (one stream synchronisation). */
+hmv_status hmv_matvec(hmv_plan_t *plan, const hmv_vec *x, hmv_vec *y);
+
+/* Release everything the plan holds.  NULL is ignored. */
+void hmv_free(hmv_plan_t *plan);
+
+/* Plan facts and (with HMV_FLAG_TIMING) stage times. */
+hmv_status hmv_get_stats(const hmv_plan_t *plan, hmv_stats *out);
+
+/* Zero the timing counters of hmv_get_stats. */
+hmv_status hmv_reset_stats(hmv_plan_t *plan);
+
+/* Static description of a status code. */
+const char *hmv_status_string(hmv_status s);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int32_t hmv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HMV_H_ */

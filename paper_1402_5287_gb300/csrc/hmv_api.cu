@@ -1,0 +1,436 @@
+// C ABI of libhmv: plans, matrix loading and the matrix-vector product.
+//
+// Karatsuba path (Beliakov, arXiv:1402.5287, Sec. 3, Algorithm 1), level
+// synchronous: every node of a level is handled by one launch.
+//   load:    encode h -> matrix-side steps 4 and 6 for levels 0..L-1 ->
+//            bf16 leaf slabs (resident)
+//   matvec:  encode x -> vector-side steps 3 and 5 for levels 0..L-1 ->
+//            leaf products (tensor cores) -> leaf digit normalisation ->
+//            step 8 for levels L-1..0 -> exact rows -> b-bit rounding
+// Schoolbook path: one CUDA-core kernel on 32-bit limbs -> the same rounding.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "hmv_internal.h"
+
+namespace hmv {
+cudaError_t launch_colsum_normalize(hmv_plan_s *p, int rhs);
+size_t leaf_tc_smem_bytes();
+
+namespace {
+
+constexpr int kMaxLevels = 16;
+constexpr int kMaxBits = 1 << 20;
+
+struct Guard {  // records the first CUDA error of a sequence of calls
+    cudaError_t err = cudaSuccess;
+    bool operator()(cudaError_t e) {
+        if (err == cudaSuccess && e != cudaSuccess) err = e;
+        return err == cudaSuccess;
+    }
+};
+
+hmv_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return HMV_OK;
+    if (e == cudaErrorMemoryAllocation) return HMV_ENOMEM;
+    return HMV_ECUDA;
+}
+
+int ceil_div(long long a, long long b) { return static_cast<int>((a + b - 1) / b); }
+long long round_up(long long a, long long b) { return (a + b - 1) / b * b; }
+
+// node orders of every level: children of a node of order s have orders
+// m = floor((s+1)/2), m, m1 = ceil((s+1)/2)  (Algorithm 1, step 2)
+std::vector<LevelGeom> build_levels(int n, int L) {
+    std::vector<LevelGeom> lv(L + 1);
+    lv[0].nodes = 1;
+    lv[0].size = {n};
+    for (int l = 0; l < L; ++l) {
+        std::vector<int> &ch = lv[l + 1].size;
+        ch.reserve(lv[l].size.size() * 3);
+        for (int s : lv[l].size) {
+            const int m = (s + 1) / 2, m1 = (s + 2) / 2;
+            ch.push_back(m);
+            ch.push_back(m);
+            ch.push_back(m1);
+        }
+        lv[l + 1].nodes = static_cast<int>(ch.size());
+    }
+    for (auto &g : lv) {
+        g.smax = *std::max_element(g.size.begin(), g.size.end());
+        g.rowsA = 2 * g.smax - 1;
+        g.rowsX = g.smax;
+    }
+    return lv;
+}
+
+// Estimated seconds of one matvec at depth L on this GPU (tensor work from
+// the tile count, memory work from the bytes the level kernels move).
+double cost_model(int n, int b, int L, int num_sms) {
+    std::vector<LevelGeom> lv = build_levels(n, L);
+    const int Dl = ceil_div(b + L + 2, 8);
+    const long long Dp = round_up(Dl, 16);
+    const int Uo = static_cast<int>(round_up(2LL * Dl - 1, TN));
+    const int NUB = Uo / TN;
+    double ksteps = 0;  // 128x256x16 MMAs
+    for (int ub = 0; ub < NUB; ++ub) {
+        const int u0 = ub * TN;
+        const int s_min = std::max(0, u0 - (Dl - 1)), s_max = std::min(Dl - 1, u0 + TN - 1);
+        const int nsb = (s_max >= s_min) ? s_max / KS - s_min / KS + 1 : 0;
+        for (int s : lv[L].size) ksteps += static_cast<double>(ceil_div(s, TM)) * nsb * s * (KS / 16);
+    }
+    const double mma_s = ksteps * 128.0 / (static_cast<double>(num_sms) * 1.9e9);
+    double bytes = 0;
+    for (int l = 0; l <= L; ++l)
+        bytes += static_cast<double>(lv[l].nodes) * lv[l].rowsX * (Dp * 2.0 + (Uo + 8) * 4.0 * 4.0);
+    bytes += static_cast<double>(lv[L].nodes) * lv[L].rowsX * Dp * 16.0 * 2.0;
+    return mma_s + bytes / 5.0e12;
+}
+
+template <typename T>
+cudaError_t dalloc(hmv_plan_s *p, T **ptr, size_t count) {
+    *ptr = nullptr;
+    if (count == 0) count = 1;
+    void *v = nullptr;
+    cudaError_t e = cudaMalloc(&v, count * sizeof(T));
+    if (e != cudaSuccess) return e;
+    p->allocations.push_back(v);
+    p->device_bytes += static_cast<int64_t>(count * sizeof(T));
+    *ptr = static_cast<T *>(v);
+    return cudaSuccess;
+}
+
+bool valid_vec(const hmv_vec *v, int len, int nrhs, int b) {
+    return v && v->len == len && v->nrhs == nrhs && v->b == b && v->limbs && v->neg &&
+           (v->on_device == 0 || v->on_device == 1) && v->reserved == 0;
+}
+
+__global__ void k_validate(const uint32_t *limbs, int rows, int L32, int b, int32_t *dstat) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= rows) return;
+    const int topbits = b - 32 * (L32 - 1);
+    if (topbits < 32 && (limbs[static_cast<size_t>(k) * L32 + L32 - 1] >> topbits) != 0)
+        atomicExch(dstat, DEV_BADINPUT);
+}
+
+void timing_mark(hmv_plan_s *p, int k) {
+    if (p->timing) cudaEventRecord(p->ev[k], p->stream);
+}
+
+float elapsed(hmv_plan_s *p, int a, int b) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, p->ev[a], p->ev[b]);
+    return ms;
+}
+
+}  // namespace
+}  // namespace hmv
+
+using namespace hmv;
+
+extern "C" {
+
+const char *hmv_status_string(hmv_status s) {
+    switch (s) {
+        case HMV_OK: return "ok";
+        case HMV_EINVAL: return "invalid argument";
+        case HMV_ENOMEM: return "out of memory";
+        case HMV_ECUDA: return "CUDA error";
+        case HMV_ETIMEOUT: return "device wait timed out";
+        case HMV_ENOTLOADED: return "matrix not loaded";
+        case HMV_EFFTBOUND: return "FFT error bound not below 1/2";
+        case HMV_EUNSUPPORTED: return "unsupported configuration";
+    }
+    return "unknown status";
+}
+
+int32_t hmv_version(void) { return 100; }
+
+void hmv_free(hmv_plan_t *p) {
+    if (!p) return;
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    for (void *a : p->allocations) cudaFree(a);
+    for (auto &g : p->lv)
+        if (g.d_size) cudaFree(g.d_size);
+    if (p->timing)
+        for (auto &e : p->ev) cudaEventDestroy(e);
+    delete p;
+}
+
+hmv_status hmv_plan(const hmv_desc *desc, void *stream, hmv_plan_t **out) {
+    if (!desc || !out) return HMV_EINVAL;
+    const hmv_desc &d = *desc;
+    if (d.n < 1 || d.b < 1 || d.b > kMaxBits || d.nrhs < 1 || d.reserved != 0) return HMV_EINVAL;
+    if (d.kind < HMV_HANKEL || d.kind > HMV_CIRCULANT) return HMV_EINVAL;
+    if (d.method < HMV_AUTO || d.method > HMV_FFT64) return HMV_EINVAL;
+    if (d.levels < -1 || d.levels > kMaxLevels) return HMV_EINVAL;
+    if (d.flags & ~(HMV_FLAG_TIMING | HMV_FLAG_SIMT_LEAF)) return HMV_EINVAL;
+    if (d.method == HMV_FFT64) return HMV_EUNSUPPORTED;
+    if (static_cast<long long>(d.n) * d.nrhs > (1LL << 30)) return HMV_EINVAL;
+
+    hmv_plan_s *p = new (std::nothrow) hmv_plan_s();
+    if (!p) return HMV_ENOMEM;
+    p->desc = d;
+    p->stream = static_cast<cudaStream_t>(stream);
+    p->n = d.n;
+    p->b = d.b;
+    p->nrhs = d.nrhs;
+    p->kind = d.kind;
+    p->method = (d.method == HMV_AUTO) ? HMV_KARATSUBA : d.method;
+    p->L32 = (d.b + 31) / 32;
+    p->timing = (d.flags & HMV_FLAG_TIMING) != 0;
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (ce != cudaSuccess) { delete p; return from_cuda(ce); }
+    if (p->timing)
+        for (auto &e : p->ev) cudaEventCreate(&e);
+
+    Guard g;
+    const int n = d.n;
+    if (p->method == HMV_SCHOOLBOOK) {
+        p->L = 0;
+        p->ZW = 2 * p->L32 + 2;
+        g(dalloc(p, &p->colsum, static_cast<size_t>(n) * 2 * p->L32));
+    } else {
+        // depth: explicit, or the cheapest by the cost model (node order >= 2)
+        int L = d.levels;
+        if (L < 0) {
+            double best = 1e300;
+            for (int t = 0; t <= kMaxLevels; ++t) {
+                if (t > 0 && build_levels(n, t - 1).back().smax <= 2) break;
+                double c = cost_model(n, d.b, t, p->num_sms);
+                if (c < best) { best = c; L = t; }
+            }
+        }
+        p->L = L;
+        p->lv = build_levels(n, L);
+        p->Dl = ceil_div(static_cast<long long>(d.b) + L + 2, 8);
+        p->Dp = static_cast<int>(round_up(p->Dl, 16));
+        p->Uo = static_cast<int>(round_up(2LL * p->Dl - 1, TN));
+        p->NUB = p->Uo / TN;
+        p->Wo = p->Uo + EXTRA_DIGITS;
+        p->ZW = p->Wo / 4;
+        const LevelGeom &leaf = p->lv[L];
+        p->MT = ceil_div(leaf.smax, TM);
+        p->RA = static_cast<int>(round_up(leaf.rowsA, 8));
+        p->RX = leaf.rowsX;
+        size_t maxA = 0, maxX = 0, maxPost = 0;
+        for (auto &lg : p->lv) {
+            maxA = std::max(maxA, static_cast<size_t>(lg.nodes) * lg.rowsA * p->Dp);
+            maxX = std::max(maxX, static_cast<size_t>(lg.nodes) * lg.rowsX * p->Dp);
+            maxPost = std::max(maxPost, static_cast<size_t>(lg.nodes) * lg.rowsX * p->Wo);
+        }
+        for (auto &lg : p->lv) {
+            if (g(cudaMalloc(&lg.d_size, lg.size.size() * sizeof(int))))
+                g(cudaMemcpy(lg.d_size, lg.size.data(), lg.size.size() * sizeof(int), cudaMemcpyHostToDevice));
+        }
+        g(dalloc(p, &p->a_lvl[0], maxA));
+        if (L > 0) g(dalloc(p, &p->a_lvl[1], maxA));
+        g(dalloc(p, &p->x_lvl[0], maxX));
+        if (L > 0) g(dalloc(p, &p->x_lvl[1], maxX));
+        const bool simt = (d.flags & HMV_FLAG_SIMT_LEAF) != 0;
+        if (!simt) {
+            g(dalloc(p, &p->hrev, static_cast<size_t>(leaf.nodes) * p->RA * p->Dp));
+            g(dalloc(p, &p->xg, static_cast<size_t>(leaf.nodes) * p->RX * 8 * (p->Dp + 8)));
+        }
+        g(dalloc(p, &p->leaf_dig, static_cast<size_t>(leaf.nodes) * p->MT * TM * p->Uo));
+        g(dalloc(p, &p->leaf_carry, static_cast<size_t>(leaf.nodes) * p->MT * TM * p->NUB));
+        g(dalloc(p, &p->post[0], maxPost));
+        if (L > 0) g(dalloc(p, &p->post[1], maxPost));
+        // tiles: leaf-major (neighbouring CTAs share a leaf's operands in L2),
+        // within a leaf the longest K loops first
+        std::vector<Tile> tiles;
+        double macs = 0, issued = 0;
+        for (int lf = 0; lf < leaf.nodes; ++lf) {
+            const int m = leaf.size[lf];
+            std::vector<Tile> lt;
+            for (int mt = 0; mt < ceil_div(m, TM); ++mt)
+                for (int ub = 0; ub < p->NUB; ++ub) {
+                    const int u0 = ub * TN;
+                    const int s_min = std::max(0, u0 - (p->Dl - 1)), s_max = std::min(p->Dl - 1, u0 + TN - 1);
+                    const int nsb = (s_max >= s_min) ? s_max / KS - s_min / KS + 1 : 0;
+                    lt.push_back(Tile{lf, mt * TM, ub, nsb * m});
+                    issued += static_cast<double>(TM) * TN * KS * nsb * m;
+                }
+            std::stable_sort(lt.begin(), lt.end(), [](const Tile &a, const Tile &b2) { return a.cost > b2.cost; });
+            tiles.insert(tiles.end(), lt.begin(), lt.end());
+            macs += static_cast<double>(m) * m * static_cast<double>(p->Dl) * p->Dl;
+        }
+        p->leaf_macs = macs;
+        p->leaf_macs_issued = issued;
+        p->ntiles = static_cast<int>(tiles.size());
+        if (g(dalloc(p, &p->d_tiles, tiles.size())))
+            g(cudaMemcpy(p->d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice));
+        if (!simt && g.err == cudaSuccess) g(make_tensor_maps(p));
+    }
+    const int hlen = (d.kind == HMV_CIRCULANT) ? n : 2 * n - 1;
+    const size_t rows = static_cast<size_t>(n) * d.nrhs;
+    g(dalloc(p, &p->zmag, rows * p->ZW));
+    g(dalloc(p, &p->zneg, rows));
+    g(dalloc(p, &p->zbits, rows));
+    g(dalloc(p, &p->dstat, 8));
+    g(dalloc(p, &p->x_limbs_d, rows * p->L32));
+    g(dalloc(p, &p->x_neg_d, rows));
+    g(dalloc(p, &p->y_limbs_d, rows * p->L32));
+    g(dalloc(p, &p->y_neg_d, rows));
+    g(dalloc(p, &p->h_limbs_d, static_cast<size_t>(hlen) * p->L32));
+    g(dalloc(p, &p->h_neg_d, hlen));
+    if (g.err != cudaSuccess) {
+        hmv_status st = from_cuda(g.err);
+        hmv_free(p);
+        cudaGetLastError();
+        return st;
+    }
+    *out = p;
+    return HMV_OK;
+}
+
+hmv_status hmv_load_matrix(hmv_plan_t *p, const hmv_vec *h) {
+    if (!p) return HMV_EINVAL;
+    const int hlen = (p->kind == HMV_CIRCULANT) ? p->n : 2 * p->n - 1;
+    if (!valid_vec(h, hlen, 1, p->b)) return HMV_EINVAL;
+    p->loaded = false;
+    Guard g;
+    const size_t nl = static_cast<size_t>(hlen) * p->L32;
+    const cudaMemcpyKind kind = h->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    g(cudaMemcpyAsync(p->h_limbs_d, h->limbs, nl * sizeof(uint32_t), kind, p->stream));
+    g(cudaMemcpyAsync(p->h_neg_d, h->neg, hlen, kind, p->stream));
+    g(cudaMemsetAsync(p->dstat, 0, 8 * sizeof(int32_t), p->stream));
+    k_validate<<<ceil_div(hlen, 128), 128, 0, p->stream>>>(p->h_limbs_d, hlen, p->L32, p->b, p->dstat);
+    g(cudaGetLastError());
+    if (p->method != HMV_SCHOOLBOOK) {
+        // level 0 holds the Hankel sequence (circulant: the wrapped Toeplitz sequence)
+        g(launch_encode(p, p->h_limbs_d, p->h_neg_d, 2 * p->n - 1, p->kind == HMV_CIRCULANT ? p->n : 0, p->a_lvl[0]));
+        for (int l = 0; l < p->L; ++l) g(launch_prepass(p, l, true, p->a_lvl[l % 2], p->a_lvl[(l + 1) % 2]));
+        p->a_leaf = p->a_lvl[p->L % 2];
+        if (p->hrev) g(launch_pack_matrix(p, p->a_leaf));
+    }
+    int32_t st[8] = {0};
+    g(cudaMemcpyAsync(st, p->dstat, sizeof st, cudaMemcpyDeviceToHost, p->stream));
+    g(cudaStreamSynchronize(p->stream));
+    if (g.err != cudaSuccess) return from_cuda(g.err);
+    if (st[0] == DEV_BADINPUT) return HMV_EINVAL;
+    if (st[0] != DEV_OK) return HMV_ECUDA;
+    p->e_h = h->exponent;
+    p->loaded = true;
+    return HMV_OK;
+}
+
+hmv_status hmv_matvec(hmv_plan_t *p, const hmv_vec *x, hmv_vec *y) {
+    if (!p) return HMV_EINVAL;
+    if (!valid_vec(x, p->n, p->nrhs, p->b) || !valid_vec(y, p->n, p->nrhs, p->b)) return HMV_EINVAL;
+    if (x->on_device != y->on_device) return HMV_EINVAL;
+    if (!p->loaded) return HMV_ENOTLOADED;
+    Guard g;
+    const size_t rows = static_cast<size_t>(p->n) * p->nrhs;
+    const uint32_t *xl = x->limbs;
+    const uint8_t *xn = x->neg;
+    timing_mark(p, 0);
+    if (!x->on_device) {
+        g(cudaMemcpyAsync(p->x_limbs_d, x->limbs, rows * p->L32 * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                          p->stream));
+        g(cudaMemcpyAsync(p->x_neg_d, x->neg, rows, cudaMemcpyHostToDevice, p->stream));
+        xl = p->x_limbs_d;
+        xn = p->x_neg_d;
+    }
+    g(cudaMemsetAsync(p->dstat, 0, 8 * sizeof(int32_t), p->stream));
+    k_validate<<<ceil_div(static_cast<long long>(rows), 128), 128, 0, p->stream>>>(xl, static_cast<int>(rows), p->L32,
+                                                                                  p->b, p->dstat);
+    g(cudaGetLastError());
+    timing_mark(p, 1);
+    float ms_pre = 0, ms_leaf = 0, ms_post = 0;
+    for (int r = 0; r < p->nrhs && g.err == cudaSuccess; ++r) {
+        const uint32_t *xr = xl + static_cast<size_t>(r) * p->n * p->L32;
+        const uint8_t *xnr = xn + static_cast<size_t>(r) * p->n;
+        if (p->method == HMV_SCHOOLBOOK) {
+            timing_mark(p, 2);
+            g(launch_schoolbook(p, xr, xnr, r));
+            timing_mark(p, 3);
+            g(launch_colsum_normalize(p, r));
+            timing_mark(p, 4);
+        } else {
+            g(launch_encode(p, xr, xnr, p->n, 0, p->x_lvl[0]));
+            for (int l = 0; l < p->L; ++l) g(launch_prepass(p, l, false, p->x_lvl[l % 2], p->x_lvl[(l + 1) % 2]));
+            const int8_t *x_leaf = p->x_lvl[p->L % 2];
+            if (p->xg) g(launch_pack_vector(p, x_leaf));
+            timing_mark(p, 2);
+            if (p->xg) g(launch_leaf_tc(p));
+            else g(launch_leaf_simt(p, p->a_leaf, x_leaf));
+            timing_mark(p, 3);
+            g(launch_leaf_normalize(p, p->post[p->L % 2]));
+            for (int l = p->L - 1; l >= 0; --l) g(launch_postpass(p, l, p->post[(l + 1) % 2], p->post[l % 2]));
+            g(launch_final_normalize(p, p->post[0], r));
+            timing_mark(p, 4);
+        }
+        if (p->timing && g.err == cudaSuccess) {
+            g(cudaEventSynchronize(p->ev[4]));
+            ms_pre += elapsed(p, 1, 2);
+            ms_leaf += elapsed(p, 2, 3);
+            ms_post += elapsed(p, 3, 4);
+        }
+        timing_mark(p, 1);
+    }
+    uint32_t *yl = y->on_device ? y->limbs : p->y_limbs_d;
+    uint8_t *yn = y->on_device ? y->neg : p->y_neg_d;
+    timing_mark(p, 5);
+    g(launch_round(p, static_cast<int>(rows), p->e_h + x->exponent, yl, yn));
+    timing_mark(p, 6);
+    int32_t st[8] = {0};
+    g(cudaMemcpyAsync(st, p->dstat, sizeof st, cudaMemcpyDeviceToHost, p->stream));
+    g(cudaStreamSynchronize(p->stream));
+    if (g.err != cudaSuccess) return from_cuda(g.err);
+    if (st[0] == DEV_BADINPUT) return HMV_EINVAL;
+    if (st[0] == DEV_TIMEOUT) return HMV_ETIMEOUT;
+    if (st[0] != DEV_OK) return HMV_ECUDA;
+    if (!y->on_device) {
+        g(cudaMemcpyAsync(y->limbs, yl, rows * p->L32 * sizeof(uint32_t), cudaMemcpyDeviceToHost, p->stream));
+        g(cudaMemcpyAsync(y->neg, yn, rows, cudaMemcpyDeviceToHost, p->stream));
+        g(cudaStreamSynchronize(p->stream));
+        if (g.err != cudaSuccess) return from_cuda(g.err);
+    }
+    y->exponent = st[3];
+    if (p->timing) {
+        p->ms_prepass += ms_pre;
+        p->ms_leaf += ms_leaf;
+        p->ms_post += ms_post;
+        p->ms_round += elapsed(p, 5, 6);
+        p->ms_total += elapsed(p, 0, 6);
+    }
+    p->matvecs++;
+    return HMV_OK;
+}
+
+hmv_status hmv_get_stats(const hmv_plan_t *p, hmv_stats *o) {
+    if (!p || !o) return HMV_EINVAL;
+    memset(o, 0, sizeof *o);
+    o->levels = p->L;
+    o->leaves = p->lv.empty() ? 1 : p->lv[p->L].nodes;
+    o->leaf_rows_max = p->lv.empty() ? p->n : p->lv[p->L].smax;
+    o->digits = p->Dl;
+    o->leaf_tiles = p->ntiles;
+    o->leaf_macs = p->leaf_macs;
+    o->leaf_macs_issued = p->leaf_macs_issued;
+    o->device_bytes = p->device_bytes;
+    o->ms_prepass = p->ms_prepass;
+    o->ms_leaf = p->ms_leaf;
+    o->ms_post = p->ms_post;
+    o->ms_round = p->ms_round;
+    o->ms_total = p->ms_total;
+    o->launches_leaf = p->launches_leaf;
+    o->launches_total = p->launches_total;
+    o->matvecs = p->matvecs;
+    return HMV_OK;
+}
+
+hmv_status hmv_reset_stats(hmv_plan_t *p) {
+    if (!p) return HMV_EINVAL;
+    p->ms_prepass = p->ms_leaf = p->ms_post = p->ms_round = p->ms_total = 0;
+    p->launches_leaf = p->launches_total = p->matvecs = 0;
+    return HMV_OK;
+}
+
+}  // extern "C"

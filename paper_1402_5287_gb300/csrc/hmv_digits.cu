@@ -1,0 +1,540 @@
+// Digit-plane kernels of the Karatsuba-style Hankel product (Beliakov,
+// arXiv:1402.5287, Sec. 3, Algorithm 1) and the final rounding.
+//
+// Representation: every operand in the recursion tree is a signed integer
+// held as Dl balanced radix-2^8 digits d_u in [-128, 127] (value
+// sum_u d_u 256^u), one int8 per digit, Dp (>= Dl, multiple of 16) digits per
+// row.  Sums and differences of Algorithm 1 are formed digit-wise and
+// renormalised with an exact carry chain, so every intermediate is exact.
+#include <cuda_bf16.h>
+
+#include "hmv_internal.h"
+
+namespace hmv {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int blocks_for(long long work, int threads = kThreads) {
+    return static_cast<int>((work + threads - 1) / threads);
+}
+
+// balanced digit of t (|t| <= 257) with its carry: t = d + 256*carry
+__device__ __forceinline__ int balance(int t, int &carry) {
+    int c = (t + 128) >> 8;  // floor((t + 128) / 256)
+    carry = c;
+    return t - (c << 8);
+}
+
+__device__ __forceinline__ uint16_t bf16_bits_of_small_int(int v) {
+    // integers with |v| <= 256 are exact in bf16: the float has zero low bits
+    return static_cast<uint16_t>(__float_as_uint(static_cast<float>(v)) >> 16);
+}
+
+// ------------------------------------------------------------------ encode
+// Sign-magnitude limbs -> balanced digits (the number representation of
+// Sec. 2, a = sum_k B^k a_k, with base B = 2^8 and signed digits).
+// circ_n > 0: row k takes entry (circ_n - 1 - k) mod circ_n (circulant ->
+// Toeplitz sequence); otherwise row k takes entry k.
+__global__ void k_encode(const uint32_t *__restrict__ limbs, const uint8_t *__restrict__ neg, int rows, int L32,
+                         int b, int circ_n, int8_t *__restrict__ out, int Dp, int32_t *dstat) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= rows) return;
+    int src = k;
+    if (circ_n > 0) src = ((circ_n - 1 - k) % circ_n + circ_n) % circ_n;
+    const uint32_t *m = limbs + static_cast<size_t>(src) * L32;
+    const int topbits = b - 32 * (L32 - 1);
+    if (topbits < 32 && (m[L32 - 1] >> topbits) != 0) atomicExch(dstat, DEV_BADINPUT);
+    const int sgn = neg[src] ? -1 : 1;
+    int8_t *o = out + static_cast<size_t>(k) * Dp;
+    int carry = 0;
+    for (int u0 = 0; u0 < Dp; u0 += 16) {
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int li = u0 / 4 + q;
+            w[q] = (li < L32) ? m[li] : 0u;
+        }
+        uint32_t packed[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint32_t pk = 0;
+#pragma unroll
+            for (int by = 0; by < 4; ++by) {
+                int byte = static_cast<int>((w[q] >> (8 * by)) & 0xFFu);
+                int c2;
+                int d = balance(sgn * byte + carry, c2);
+                carry = c2;
+                pk |= (static_cast<uint32_t>(d) & 0xFFu) << (8 * by);
+            }
+            packed[q] = pk;
+        }
+        *reinterpret_cast<uint4 *>(o + u0) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+    }
+    if (carry != 0) atomicExch(dstat, DEV_OVERFLOW);
+}
+
+// ------------------------------------------------------------------ pre-pass
+// One level of Algorithm 1, steps 3-6, for every node of a level.
+// Node nu (order s) has children 3nu (c, h -> p), 3nu+1 (d, f -> q),
+// 3nu+2 (e, g -> r).  0-based:
+//   matrix side  c_k = a_{2k} + a_{2k+1},  d_k = a_{2k+1},  e_k = a_{2k}
+//   vector side  h_k = x_{2k},  f_k = x_{2k} - x_{2k+1},  g_k = x_{2k-1} - x_{2k}
+// with a_q = 0 for q >= 2s-1 and x_q = 0 for q < 0 or q >= s.
+__global__ void k_prepass(const int8_t *__restrict__ in, int in_rows, const int *__restrict__ in_size,
+                          int8_t *__restrict__ out, int out_rows, const int *__restrict__ out_size, int nchildren,
+                          int Dp, int matrix_side, int32_t *dstat) {
+    long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    int child = static_cast<int>(idx / out_rows);
+    int k = static_cast<int>(idx % out_rows);
+    if (child >= nchildren) return;
+    const int parent = child / 3, t = child % 3;
+    const int s = in_size[parent];
+    const int cs = out_size[child];
+    const int cnt = matrix_side ? 2 * cs - 1 : cs;
+    if (k >= cnt) return;
+    const int len = matrix_side ? 2 * s - 1 : s;
+    int q1, q2, s1, s2;
+    if (matrix_side) {
+        if (t == 0) { q1 = 2 * k; s1 = 1; q2 = 2 * k + 1; s2 = 1; }
+        else if (t == 1) { q1 = 2 * k + 1; s1 = 1; q2 = 0; s2 = 0; }
+        else { q1 = 2 * k; s1 = 1; q2 = 0; s2 = 0; }
+    } else {
+        if (t == 0) { q1 = 2 * k; s1 = 1; q2 = 0; s2 = 0; }
+        else if (t == 1) { q1 = 2 * k; s1 = 1; q2 = 2 * k + 1; s2 = -1; }
+        else { q1 = 2 * k - 1; s1 = 1; q2 = 2 * k; s2 = -1; }
+    }
+    if (q1 < 0 || q1 >= len) s1 = 0;
+    if (q2 < 0 || q2 >= len) s2 = 0;
+    const int8_t *r1 = in + (static_cast<size_t>(parent) * in_rows + (s1 ? q1 : 0)) * Dp;
+    const int8_t *r2 = in + (static_cast<size_t>(parent) * in_rows + (s2 ? q2 : 0)) * Dp;
+    int8_t *o = out + (static_cast<size_t>(child) * out_rows + k) * Dp;
+    int carry = 0;
+    for (int u0 = 0; u0 < Dp; u0 += 16) {
+        uint4 v1 = s1 ? *reinterpret_cast<const uint4 *>(r1 + u0) : make_uint4(0, 0, 0, 0);
+        uint4 v2 = s2 ? *reinterpret_cast<const uint4 *>(r2 + u0) : make_uint4(0, 0, 0, 0);
+        const uint32_t a1[4] = {v1.x, v1.y, v1.z, v1.w};
+        const uint32_t a2[4] = {v2.x, v2.y, v2.z, v2.w};
+        uint32_t packed[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint32_t pk = 0;
+#pragma unroll
+            for (int by = 0; by < 4; ++by) {
+                int d1 = static_cast<int8_t>((a1[q] >> (8 * by)) & 0xFFu);
+                int d2 = static_cast<int8_t>((a2[q] >> (8 * by)) & 0xFFu);
+                int c2;
+                int d = balance(s1 * d1 + s2 * d2 + carry, c2);
+                carry = c2;
+                pk |= (static_cast<uint32_t>(d) & 0xFFu) << (8 * by);
+            }
+            packed[q] = pk;
+        }
+        *reinterpret_cast<uint4 *>(o + u0) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+    }
+    if (carry != 0) atomicExch(dstat, DEV_OVERFLOW);
+}
+
+// ------------------------------------------------------------------ packing
+// Matrix-side leaves -> bf16 slabs, digits reversed (most significant first)
+// and pre-tiled for the tensor cores: hrev[leaf][c][k][kk] holds digit
+// (Dp-1-8c-kk) of a_k; rows k >= 2*size-1 are zero.  One 16-byte run per
+// (chunk, row), rows adjacent, so any run of rows of one chunk is a block of
+// 8-row x 16-byte core matrices.
+__global__ void k_pack_matrix(const int8_t *__restrict__ leafd, int rowsA, const int *__restrict__ size,
+                              uint16_t *__restrict__ hrev, int RA, int Dp, int nleaves) {
+    long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int chunks = Dp / 8;
+    long long per_leaf = static_cast<long long>(RA) * chunks;
+    int leaf = static_cast<int>(idx / per_leaf);
+    if (leaf >= nleaves) return;
+    int rem = static_cast<int>(idx % per_leaf);
+    int c = rem / RA, k = rem % RA;
+    uint16_t v[8];
+    if (k < 2 * size[leaf] - 1) {
+        const int8_t *src = leafd + (static_cast<size_t>(leaf) * rowsA + k) * Dp + (Dp - 8 * c - 8);
+        uint2 raw = *reinterpret_cast<const uint2 *>(src);
+        const uint32_t w[2] = {raw.x, raw.y};
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            int sidx = 7 - i;  // reversed
+            int d = static_cast<int8_t>((w[sidx / 4] >> (8 * (sidx % 4))) & 0xFFu);
+            v[i] = bf16_bits_of_small_int(d);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = 0;
+    }
+    uint4 pk = make_uint4(v[0] | (uint32_t(v[1]) << 16), v[2] | (uint32_t(v[3]) << 16), v[4] | (uint32_t(v[5]) << 16),
+                          v[6] | (uint32_t(v[7]) << 16));
+    *reinterpret_cast<uint4 *>(hrev + ((static_cast<size_t>(leaf) * chunks + c) * RA + k) * 8) = pk;
+}
+
+// Vector-side leaves -> bf16 shifted copies, pre-tiled as 8x8 blocks:
+// xg[leaf][j][e][r][kk] = digit (8e + r + kk - 7) of x_j, e in [0, Dp/8 + 1)
+// (zero outside [0, Dp) and for j >= size).  Block e is the core matrix of
+// every (n-group g, k-group c) with g + c = e - e0 of the digit-Toeplitz
+// operand whose window starts at chunk e0.
+__global__ void k_pack_vector(const int8_t *__restrict__ leafd, int rowsX, const int *__restrict__ size,
+                              uint16_t *__restrict__ xg, int RX, int Dp, int nleaves) {
+    long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int chunks = Dp / 8 + 1;
+    long long per_leaf = static_cast<long long>(RX) * chunks * 8;
+    int leaf = static_cast<int>(idx / per_leaf);
+    if (leaf >= nleaves) return;
+    long long rem = idx % per_leaf;
+    int j = static_cast<int>(rem / (8 * chunks));
+    int e = static_cast<int>((rem / 8) % chunks);
+    int r = static_cast<int>(rem % 8);
+    uint16_t v[8];
+    const bool live = j < size[leaf];
+    const int8_t *row = leafd + (static_cast<size_t>(leaf) * rowsX + j) * Dp;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        int u = 8 * e + r + i - 7;
+        int d = (live && u >= 0 && u < Dp) ? static_cast<int>(row[u]) : 0;
+        v[i] = bf16_bits_of_small_int(d);
+    }
+    uint4 pk = make_uint4(v[0] | (uint32_t(v[1]) << 16), v[2] | (uint32_t(v[3]) << 16), v[4] | (uint32_t(v[5]) << 16),
+                          v[6] | (uint32_t(v[7]) << 16));
+    *reinterpret_cast<uint4 *>(xg + (((static_cast<size_t>(leaf) * RX + j) * chunks + e) * 8 + r) * 8) = pk;
+}
+
+// ------------------------------------------------------------------ CUDA-core leaf
+// Same output as the tensor-core leaf: for tile (leaf, i0, ub) and row
+// i = i0 + blockIdx.y, the column sums Y[i][u] = sum_j sum_s a_{i+j}[s] x_j[u-s]
+// for u in [ub*TN, ub*TN+TN), normalised to digits in [0, 256) plus the
+// carry out of the block (floor of the block value / 256^TN).
+__global__ void k_leaf_simt(const int8_t *__restrict__ A, int rowsA, const int8_t *__restrict__ X, int rowsX,
+                            const int *__restrict__ size, int Dp, int Dl, const Tile *__restrict__ tiles,
+                            uint8_t *__restrict__ dig, int32_t *__restrict__ carry, int MT, int Uo, int NUB,
+                            int32_t *dstat) {
+    const Tile tl = tiles[blockIdx.x];
+    const int m = size[tl.leaf];
+    const int i = tl.i0 + blockIdx.y;
+    if (i >= m) return;
+    __shared__ long long col[TN];
+    const int u = tl.ub * TN + threadIdx.x;
+    long long acc = 0;
+    const int s_lo = max(0, u - (Dl - 1)), s_hi = min(Dl - 1, u);
+    for (int j = 0; j < m; ++j) {
+        const int8_t *a = A + (static_cast<size_t>(tl.leaf) * rowsA + i + j) * Dp;
+        const int8_t *x = X + (static_cast<size_t>(tl.leaf) * rowsX + j) * Dp;
+        int part = 0;  // |part| <= Dl * 2^14 < 2^31 for Dl < 2^17
+        for (int s = s_lo; s <= s_hi; ++s) part += static_cast<int>(a[s]) * static_cast<int>(x[u - s]);
+        acc += part;
+    }
+    col[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long c = 0;
+        uint8_t *o = dig + (static_cast<size_t>(tl.leaf) * MT * TM + i) * Uo + tl.ub * TN;
+        for (int q = 0; q < TN; ++q) {
+            long long t = col[q] + c;
+            o[q] = static_cast<uint8_t>(t & 255);
+            c = t >> 8;
+        }
+        if (c > INT32_MAX || c < INT32_MIN) atomicExch(dstat, DEV_OVERFLOW);
+        carry[(static_cast<size_t>(tl.leaf) * MT * TM + i) * NUB + tl.ub] = static_cast<int32_t>(c);
+    }
+}
+
+// ------------------------------------------------------------------ leaf normalise
+// Joins the per-block digits and block carries of one leaf row into one
+// digit vector: out[u] in [0, 256) for u < Wo-1, out[Wo-1] holds the signed rest.
+__global__ void k_leaf_normalize(const uint8_t *__restrict__ dig, const int32_t *__restrict__ carry,
+                                 const int *__restrict__ size, int nleaves, int MT, int Uo, int NUB,
+                                 int32_t *__restrict__ out, int rowsX, int Wo) {
+    long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    int leaf = static_cast<int>(idx / rowsX), row = static_cast<int>(idx % rowsX);
+    if (leaf >= nleaves || row >= size[leaf]) return;
+    const size_t r = static_cast<size_t>(leaf) * MT * TM + row;
+    const uint8_t *d = dig + r * Uo;
+    const int32_t *cy = carry + r * NUB;
+    int32_t *o = out + (static_cast<size_t>(leaf) * rowsX + row) * Wo;
+    long long c = 0;
+    for (int u0 = 0; u0 < Uo; u0 += 16) {
+        if (u0 > 0 && (u0 % TN) == 0) c += cy[u0 / TN - 1];
+        uint4 v = *reinterpret_cast<const uint4 *>(d + u0);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+        int res[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            long long t = static_cast<long long>((w[q / 4] >> (8 * (q % 4))) & 0xFFu) + c;
+            res[q] = static_cast<int>(t & 255);
+            c = t >> 8;
+        }
+#pragma unroll
+        for (int q = 0; q < 16; q += 4)
+            *reinterpret_cast<int4 *>(o + u0 + q) = make_int4(res[q], res[q + 1], res[q + 2], res[q + 3]);
+    }
+    c += cy[NUB - 1];
+    for (int u = Uo; u < Wo - 1; ++u) {
+        o[u] = static_cast<int>(c & 255);
+        c >>= 8;
+    }
+    o[Wo - 1] = static_cast<int>(c);
+}
+
+// ------------------------------------------------------------------ post-pass
+// Algorithm 1, step 8 (0-based): y_{2k} = p_k - q_k, y_{2k+1} = p_k + r_k,
+// digit-wise without carries (digits grow by at most one bit per level).
+__global__ void k_postpass(const int32_t *__restrict__ in, int rows_in, int32_t *__restrict__ out, int rows_out,
+                           const int *__restrict__ parent_size, int nparents, int Wo) {
+    const int g4 = Wo / 4;
+    long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    long long per = static_cast<long long>(rows_out) * g4;
+    int nu = static_cast<int>(idx / per);
+    if (nu >= nparents) return;
+    int rem = static_cast<int>(idx % per);
+    int i = rem / g4, g = rem % g4;
+    if (i >= parent_size[nu]) return;
+    const int k = i >> 1;
+    const int other = (i & 1) ? 2 : 1;
+    const int4 p = reinterpret_cast<const int4 *>(in + (static_cast<size_t>(3 * nu) * rows_in + k) * Wo)[g];
+    const int4 o = reinterpret_cast<const int4 *>(in + (static_cast<size_t>(3 * nu + other) * rows_in + k) * Wo)[g];
+    int4 y;
+    if (i & 1) y = make_int4(p.x + o.x, p.y + o.y, p.z + o.z, p.w + o.w);
+    else y = make_int4(p.x - o.x, p.y - o.y, p.z - o.z, p.w - o.w);
+    reinterpret_cast<int4 *>(out + (static_cast<size_t>(nu) * rows_out + i) * Wo)[g] = y;
+}
+
+// ------------------------------------------------------------------ final normalise
+// Row digit vector (int32 digits, radix 256) -> |Z| as 32-bit limbs, sign, bit length.
+__global__ void k_final_normalize(const int32_t *__restrict__ in, int n, int Wo, uint32_t *__restrict__ zmag,
+                                  uint8_t *__restrict__ zneg, int32_t *__restrict__ zbits, int ZW, int32_t *dstat,
+                                  int row_offset) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t *d = in + static_cast<size_t>(i) * Wo;
+    long long c = 0;
+    for (int u = 0; u < Wo; ++u) c = (static_cast<long long>(d[u]) + c) >> 8;
+    const int sgn = (c < 0) ? -1 : 1;
+    if (c > 0 || c < -1) atomicExch(dstat, DEV_OVERFLOW);
+    c = 0;
+    uint32_t *z = zmag + static_cast<size_t>(row_offset + i) * ZW;
+    int top = -1;
+    uint32_t topv = 0;
+    for (int w = 0; w < ZW; ++w) {
+        uint32_t limb = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int u = 4 * w + q;
+            long long t = (u < Wo ? static_cast<long long>(sgn) * d[u] : 0) + c;
+            limb |= static_cast<uint32_t>(t & 255) << (8 * q);
+            c = t >> 8;
+        }
+        z[w] = limb;
+        if (limb) { top = w; topv = limb; }
+    }
+    if (c != 0) atomicExch(dstat, DEV_OVERFLOW);
+    int bits = (top < 0) ? 0 : 32 * top + (32 - __clz(topv));
+    zbits[row_offset + i] = bits;
+    zneg[row_offset + i] = (bits > 0 && sgn < 0) ? 1 : 0;
+    atomicMax(dstat + 1, bits);
+}
+
+// Signed 128-bit column sums of 32-bit limb weights -> |Z| limbs, sign, bits.
+__global__ void k_colsum_normalize(const __int128 *__restrict__ cs, int n, int ncols, uint32_t *__restrict__ zmag,
+                                   uint8_t *__restrict__ zneg, int32_t *__restrict__ zbits, int ZW, int32_t *dstat,
+                                   int row_offset) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const __int128 *d = cs + static_cast<size_t>(i) * ncols;
+    __int128 c = 0;
+    for (int w = 0; w < ncols; ++w) c = (d[w] + c) >> 32;
+    const int sgn = (c < 0) ? -1 : 1;
+    c = 0;
+    uint32_t *z = zmag + static_cast<size_t>(row_offset + i) * ZW;
+    int top = -1;
+    uint32_t topv = 0;
+    for (int w = 0; w < ZW; ++w) {
+        __int128 t = (w < ncols ? (sgn < 0 ? -d[w] : d[w]) : static_cast<__int128>(0)) + c;
+        uint32_t limb = static_cast<uint32_t>(static_cast<unsigned __int128>(t) & 0xFFFFFFFFu);
+        c = t >> 32;
+        z[w] = limb;
+        if (limb) { top = w; topv = limb; }
+    }
+    if (c != 0) atomicExch(dstat, DEV_OVERFLOW);
+    int bits = (top < 0) ? 0 : 32 * top + (32 - __clz(topv));
+    zbits[row_offset + i] = bits;
+    zneg[row_offset + i] = (bits > 0 && sgn < 0) ? 1 : 0;
+    atomicMax(dstat + 1, bits);
+}
+
+// ------------------------------------------------------------------ rounding
+// bit pos of |Z| (0 outside)
+__device__ __forceinline__ uint32_t zbit(const uint32_t *z, int ZW, long long pos) {
+    if (pos < 0 || pos >= 32LL * ZW) return 0;
+    return (z[pos >> 5] >> (pos & 31)) & 1u;
+}
+// 32 bits of |Z| starting at bit pos (pos may be negative: zeros shifted in)
+__device__ __forceinline__ uint32_t zword(const uint32_t *z, int ZW, long long pos) {
+    long long w = (pos >= 0) ? (pos >> 5) : -((-pos + 31) >> 5);
+    int sh = static_cast<int>(pos - 32 * w);
+    uint32_t lo = (w >= 0 && w < ZW) ? z[w] : 0u;
+    uint32_t hi = (w + 1 >= 0 && w + 1 < ZW) ? z[w + 1] : 0u;
+    return sh ? ((lo >> sh) | (hi << (32 - sh))) : lo;
+}
+// round bit and sticky of |Z| / 2^t (t > 0)
+__device__ void round_bits(const uint32_t *z, int ZW, long long t, uint32_t &half, uint32_t &sticky) {
+    half = zbit(z, ZW, t - 1);
+    sticky = 0;
+    long long below = t - 1;  // bits [0, below)
+    long long full = below >> 5;
+    for (long long w = 0; w < full && w < ZW; ++w) sticky |= z[w];
+    int rem = static_cast<int>(below & 31);
+    if (rem && full < ZW) sticky |= z[full] & ((1u << rem) - 1u);
+    sticky = sticky ? 1u : 0u;
+}
+
+// dstat: [0] error, [1] max bit length, [2] round-up-to-2^b flag, [3] E_y
+// A row can reach 2^b only if it has the maximum bit length.
+__global__ void k_round_check(const uint32_t *__restrict__ zmag, const int32_t *__restrict__ zbits, int rows, int ZW,
+                              int b, int32_t *dstat) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows) return;
+    const int B = dstat[1];
+    const long long t = static_cast<long long>(B) - b;
+    if (B == 0 || t <= 0 || zbits[i] != B) return;
+    const uint32_t *z = zmag + static_cast<size_t>(i) * ZW;
+    // all b bits of |Z| >> t set?
+    for (long long p = t; p < t + b; ++p)
+        if (!zbit(z, ZW, p)) return;
+    uint32_t half, sticky;
+    round_bits(z, ZW, t, half, sticky);
+    if (half) atomicExch(dstat + 2, 1);  // an all-ones mantissa is odd: a half rounds up
+}
+
+__global__ void k_round(const uint32_t *__restrict__ zmag, const uint8_t *__restrict__ zneg, int n, int nrhs, int ZW,
+                        int b, int L32, int e_in, int reverse, int32_t *dstat, uint32_t *__restrict__ y,
+                        uint8_t *__restrict__ yneg) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * nrhs) return;
+    if (dstat[0] != DEV_OK) return;  // an earlier stage failed: write nothing
+    const int rhs = idx / n, i = idx % n;
+    const int orow = rhs * n + (reverse ? (n - 1 - i) : i);
+    uint32_t *o = y + static_cast<size_t>(orow) * L32;
+    const int B = dstat[1];
+    if (B == 0) {
+        for (int w = 0; w < L32; ++w) o[w] = 0;
+        yneg[orow] = 0;
+        if (idx == 0) dstat[3] = e_in;
+        return;
+    }
+    const long long t = static_cast<long long>(B) - b + dstat[2];
+    const uint32_t *z = zmag + static_cast<size_t>(idx) * ZW;
+    const int topbits = b - 32 * (L32 - 1);
+    uint32_t any = 0;
+    for (int w = 0; w < L32; ++w) {
+        uint32_t v = zword(z, ZW, t + 32LL * w);
+        if (w == L32 - 1 && topbits < 32) v &= (1u << topbits) - 1u;
+        o[w] = v;
+    }
+    if (t > 0) {
+        uint32_t half, sticky;
+        round_bits(z, ZW, t, half, sticky);
+        if (half && (sticky || (o[0] & 1u))) {
+            for (int w = 0; w < L32; ++w) {
+                o[w] += 1u;
+                if (o[w] != 0) break;
+            }
+            if (topbits < 32 && (o[L32 - 1] >> topbits)) atomicExch(dstat, DEV_OVERFLOW);
+        }
+    }
+    for (int w = 0; w < L32; ++w) any |= o[w];
+    yneg[orow] = (any && zneg[idx]) ? 1 : 0;
+    if (idx == 0) dstat[3] = static_cast<int32_t>(e_in + t - b);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+cudaError_t launch_encode(hmv_plan_s *p, const uint32_t *limbs, const uint8_t *neg, int rows, int circulant_n,
+                          int8_t *out) {
+    k_encode<<<blocks_for(rows, 128), 128, 0, p->stream>>>(limbs, neg, rows, p->L32, p->b, circulant_n, out, p->Dp,
+                                                           p->dstat);
+    p->launches_total++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prepass(hmv_plan_s *p, int level, bool matrix_side, const int8_t *in, int8_t *out) {
+    const LevelGeom &pl = p->lv[level], &cl = p->lv[level + 1];
+    const int in_rows = matrix_side ? pl.rowsA : pl.rowsX;
+    const int out_rows = matrix_side ? cl.rowsA : cl.rowsX;
+    long long work = static_cast<long long>(cl.nodes) * out_rows;
+    k_prepass<<<blocks_for(work, 128), 128, 0, p->stream>>>(in, in_rows, pl.d_size, out, out_rows, cl.d_size,
+                                                            cl.nodes, p->Dp, matrix_side ? 1 : 0, p->dstat);
+    p->launches_total++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_matrix(hmv_plan_s *p, const int8_t *leaf_digits) {
+    const LevelGeom &ll = p->lv[p->L];
+    long long work = static_cast<long long>(ll.nodes) * p->RA * (p->Dp / 8);
+    k_pack_matrix<<<blocks_for(work), kThreads, 0, p->stream>>>(leaf_digits, ll.rowsA, ll.d_size, p->hrev, p->RA,
+                                                                p->Dp, ll.nodes);
+    p->launches_total++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_vector(hmv_plan_s *p, const int8_t *leaf_digits) {
+    const LevelGeom &ll = p->lv[p->L];
+    long long work = static_cast<long long>(ll.nodes) * p->RX * 8 * (p->Dp / 8 + 1);
+    k_pack_vector<<<blocks_for(work), kThreads, 0, p->stream>>>(leaf_digits, ll.rowsX, ll.d_size, p->xg, p->RX,
+                                                                p->Dp, ll.nodes);
+    p->launches_total++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_simt(hmv_plan_s *p, const int8_t *a_leaf, const int8_t *x_leaf) {
+    const LevelGeom &ll = p->lv[p->L];
+    dim3 grid(p->ntiles, TM);
+    k_leaf_simt<<<grid, TN, 0, p->stream>>>(a_leaf, ll.rowsA, x_leaf, ll.rowsX, ll.d_size, p->Dp, p->Dl, p->d_tiles,
+                                            p->leaf_dig, p->leaf_carry, p->MT, p->Uo, p->NUB, p->dstat);
+    p->launches_leaf++;
+    p->launches_total++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_normalize(hmv_plan_s *p, int32_t *out) {
+    const LevelGeom &ll = p->lv[p->L];
+    long long work = static_cast<long long>(ll.nodes) * ll.rowsX;
+    k_leaf_normalize<<<blocks_for(work, 128), 128, 0, p->stream>>>(p->leaf_dig, p->leaf_carry, ll.d_size, ll.nodes,
+                                                                   p->MT, p->Uo, p->NUB, out, ll.rowsX, p->Wo);
+    p->launches_total++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_postpass(hmv_plan_s *p, int level, const int32_t *in, int32_t *out) {
+    const LevelGeom &pl = p->lv[level], &cl = p->lv[level + 1];
+    long long work = static_cast<long long>(pl.nodes) * pl.rowsX * (p->Wo / 4);
+    k_postpass<<<blocks_for(work), kThreads, 0, p->stream>>>(in, cl.rowsX, out, pl.rowsX, pl.d_size, pl.nodes, p->Wo);
+    p->launches_total++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_final_normalize(hmv_plan_s *p, const int32_t *in, int rhs) {
+    k_final_normalize<<<blocks_for(p->n, 128), 128, 0, p->stream>>>(in, p->n, p->Wo, p->zmag, p->zneg, p->zbits,
+                                                                    p->ZW, p->dstat, rhs * p->n);
+    p->launches_total++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_colsum_normalize(hmv_plan_s *p, int rhs) {
+    k_colsum_normalize<<<blocks_for(p->n, 128), 128, 0, p->stream>>>(p->colsum, p->n, 2 * p->L32, p->zmag, p->zneg,
+                                                                     p->zbits, p->ZW, p->dstat, rhs * p->n);
+    p->launches_total++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_round(hmv_plan_s *p, int rows, int e_in, uint32_t *y_limbs, uint8_t *y_neg) {
+    k_round_check<<<blocks_for(rows, 128), 128, 0, p->stream>>>(p->zmag, p->zbits, rows, p->ZW, p->b, p->dstat);
+    k_round<<<blocks_for(rows, 128), 128, 0, p->stream>>>(p->zmag, p->zneg, p->n, p->nrhs, p->ZW, p->b, p->L32, e_in,
+                                                          p->kind != HMV_HANKEL ? 1 : 0, p->dstat, y_limbs, y_neg);
+    p->launches_total += 2;
+    return cudaGetLastError();
+}
+
+}  // namespace hmv

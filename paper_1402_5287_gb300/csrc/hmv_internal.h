@@ -1,0 +1,118 @@
+// Internal declarations shared by the CUDA translation units of libhmv.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/hmv.h"
+
+namespace hmv {
+
+// ---------------------------------------------------------------- geometry
+// Leaf contraction tile: TM leaf rows x TN output digits; each s-block holds
+// KS digits of the matrix operand; JC shifts j share one staged slab.
+constexpr int TM = 128;
+constexpr int TN = 256;
+constexpr int KS = 128;
+constexpr int JC = 64;
+constexpr int AR = TM + JC;                   // rows of one staged Hankel slab
+constexpr int A_BYTES = AR * KS * 2;          // bf16 slab bytes
+constexpr int NE = TN / 8 + KS / 8 - 1;       // core matrices of one shifted-x operand
+constexpr int B_BYTES = NE * 128;             // bf16 bytes of one shifted-x operand
+constexpr int A_STAGES = 2;
+constexpr int B_STAGES = 8;
+// j-steps per exact fp32 accumulation window: FLUSH_J * KS products of
+// magnitude <= 2^14 keep every partial sum within 2^24.
+constexpr int FLUSH_J = 1024 / KS;
+constexpr int EXTRA_DIGITS = 8;               // room above the leaf product for carries
+
+// Device error codes written to the plan's status word.
+enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BADINPUT = 2, DEV_OVERFLOW = 3 };
+
+struct LevelGeom {
+    int nodes = 0;                 // 3^l
+    int smax = 0;                  // largest node order at this level
+    int rowsA = 0;                 // per-node row stride of the matrix side (>= 2*smax-1)
+    int rowsX = 0;                 // per-node row stride of the vector side (>= smax)
+    std::vector<int> size;         // node orders
+    int *d_size = nullptr;         // device copy of size
+};
+
+struct Tile {
+    int leaf, i0, ub, cost;
+};
+
+}  // namespace hmv
+
+struct hmv_plan_s {
+    hmv_desc desc;
+    cudaStream_t stream = nullptr;
+    int n = 0, b = 0, nrhs = 1, kind = 0, method = 0;
+    int L = 0;                     // Karatsuba depth
+    int L32 = 0;                   // limbs per entry
+    int Dl = 0;                    // balanced digits per operand in the tree
+    int Dp = 0;                    // padded digit stride (multiple of 16)
+    int Uo = 0;                    // leaf output digits covered by tiles (multiple of TN)
+    int NUB = 0;                   // leaf output digit blocks
+    int Wo = 0;                    // post-pass digit stride (multiple of 4)
+    int ZW = 0;                    // limbs of the exact rows (Wo / 4)
+    int MT = 0;                    // 128-row tiles per leaf
+    std::vector<hmv::LevelGeom> lv;
+    bool loaded = false;
+    int e_h = 0;                   // exponent of the loaded matrix
+
+    // device buffers
+    int8_t *a_lvl[2] = {nullptr, nullptr};   // matrix-side digit planes, ping-pong
+    int8_t *a_leaf = nullptr;                // matrix-side leaf digits (int8), resident
+    int8_t *x_lvl[2] = {nullptr, nullptr};   // vector-side digit planes, ping-pong
+    int8_t *x_leaf = nullptr;                // vector-side leaf digits (int8)
+    uint16_t *hrev = nullptr;                // bf16 [leaf][RA][Dp], digits reversed
+    uint16_t *xg = nullptr;                  // bf16 [leaf][RX][8][Dp], 8 shifted copies
+    int RA = 0, RX = 0;
+    uint8_t *leaf_dig = nullptr;             // [leaf][MT*TM][Uo]
+    int32_t *leaf_carry = nullptr;           // [leaf][MT*TM][NUB]
+    int32_t *post[2] = {nullptr, nullptr};   // [node][rowsX][Wo] per level, ping-pong
+    uint32_t *zmag = nullptr;                // [nrhs*n][ZW] exact |Z|
+    uint8_t *zneg = nullptr;                 // [nrhs*n]
+    int32_t *zbits = nullptr;                // [nrhs*n] bit lengths
+    int32_t *dstat = nullptr;                // device status block (see k_round_*)
+    hmv::Tile *d_tiles = nullptr;
+    int ntiles = 0;
+    // schoolbook
+    __int128 *colsum = nullptr;              // [n][2*L32]
+    // staging for host vectors
+    uint32_t *x_limbs_d = nullptr, *y_limbs_d = nullptr;
+    uint8_t *x_neg_d = nullptr, *y_neg_d = nullptr, *h_neg_d = nullptr;
+    uint32_t *h_limbs_d = nullptr;
+
+    CUtensorMap mapA, mapB;
+    bool maps_ok = false;
+    int num_sms = 0;
+    int64_t device_bytes = 0;
+    std::vector<void *> allocations;
+
+    // stats
+    bool timing = false;
+    cudaEvent_t ev[8];
+    double ms_prepass = 0, ms_leaf = 0, ms_post = 0, ms_round = 0, ms_total = 0;
+    int64_t launches_leaf = 0, launches_total = 0, matvecs = 0;
+    double leaf_macs = 0, leaf_macs_issued = 0;
+};
+
+namespace hmv {
+// launchers (all asynchronous on plan->stream); return a cudaError_t
+cudaError_t launch_encode(hmv_plan_s *p, const uint32_t *limbs, const uint8_t *neg, int rows, int circulant_n,
+                          int8_t *out);
+cudaError_t launch_prepass(hmv_plan_s *p, int level, bool matrix_side, const int8_t *in, int8_t *out);
+cudaError_t launch_pack_matrix(hmv_plan_s *p, const int8_t *leaf_digits);
+cudaError_t launch_pack_vector(hmv_plan_s *p, const int8_t *leaf_digits);
+cudaError_t launch_leaf_tc(hmv_plan_s *p);
+cudaError_t launch_leaf_simt(hmv_plan_s *p, const int8_t *a_leaf, const int8_t *x_leaf);
+cudaError_t launch_leaf_normalize(hmv_plan_s *p, int32_t *out);
+cudaError_t launch_postpass(hmv_plan_s *p, int level, const int32_t *in, int32_t *out);
+cudaError_t launch_final_normalize(hmv_plan_s *p, const int32_t *in, int rhs);
+cudaError_t launch_schoolbook(hmv_plan_s *p, const uint32_t *x_limbs, const uint8_t *x_neg, int rhs);
+cudaError_t launch_round(hmv_plan_s *p, int rows, int e_in, uint32_t *y_limbs, uint8_t *y_neg);
+cudaError_t make_tensor_maps(hmv_plan_s *p);
+}  // namespace hmv

@@ -1,0 +1,322 @@
+// Leaf products of Algorithm 1 (Beliakov, arXiv:1402.5287, Sec. 3) on the
+// sm_103a tensor cores.
+//
+// A leaf is a small exact Hankel product p_i = sum_{j<m} a_{i+j} x_j whose
+// entries are big integers held as balanced radix-2^8 digits.  In digits,
+//     Y[i][u] = sum_{j<m} sum_s a_{i+j}[s] * x_j[u-s],
+// a GEMM with M = i (leaf rows), N = u (product digits), K = (j, s):
+//   * A[i][(j,s)] = a_{i+j}[s] is Hankel in the index: one staged slab of
+//     rows of the leaf sequence serves every shift j by moving the
+//     descriptor start by j rows (16 bytes), never materialising the matrix;
+//   * B[u][(j,s)] = x_j[u-s] is Toeplitz in the digits: with K ordered by
+//     descending s, core matrix (n-group g, k-group c) depends only on g + c,
+//     so one row of 8x8 blocks (8 shifted copies of x_j, loaded by TMA) with
+//     both descriptor strides equal to 128 bytes is the whole operand.
+// Digits (|d| <= 128) are exact in bf16; products are <= 2^14; an fp32
+// accumulation window of 1024 products keeps every partial sum within 2^24,
+// so each window is an exact integer.  The epilogue reads each window from
+// TMEM, converts it to int32 and adds it into the tile's exact value kept as
+// 256 base-256 digits per row plus a carry word (carry propagation in
+// registers), so nothing but the final digits ever leaves the SM.
+//
+// Warp roles (192 threads): warp 0 issues TMA loads, warp 1 allocates TMEM
+// and one lane issues tcgen05.mma, warps 2-5 run the epilogue on the four
+// TMEM lane quarters.  Two 128x256 fp32 accumulators (all 512 TMEM columns)
+// let the MMAs of one window overlap the epilogue of the previous one.
+// Every wait is bounded; on a timeout the kernel records DEV_TIMEOUT, drains
+// and frees its TMEM, and returns.
+#include "hmv_internal.h"
+#include "tc_ptx.cuh"
+
+namespace hmv {
+namespace {
+
+constexpr int kProducerWarp = 0;
+constexpr int kMmaWarp = 1;
+constexpr int kEpiWarp0 = 2;
+constexpr int kNumEpiWarps = 4;
+constexpr int kThreads = (2 + kNumEpiWarps) * 32;
+constexpr uint64_t kTimeoutNs = 2000000000ull;  // 2 s for any single wait
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kIdesc = idesc_bf16_f32(TM, TN);
+constexpr uint32_t kLboA = AR * 16;  // K-direction core-matrix step of the slab
+
+struct __align__(1024) Smem {
+    uint8_t a[A_STAGES][A_BYTES];
+    uint8_t b[B_STAGES][B_BYTES];
+    uint64_t a_full[A_STAGES], a_empty[A_STAGES];
+    uint64_t b_full[B_STAGES], b_empty[B_STAGES];
+    uint64_t acc_full[2], acc_empty[2];
+    uint64_t drain;
+    uint32_t tmem_base;
+    volatile int abort;
+};
+
+struct TileInfo {
+    int leaf, i0, ub, u0, m, sb_lo, sb_hi, njc, Q;
+};
+
+__device__ __forceinline__ TileInfo decode(const Tile &t, const int *size, int Dl) {
+    TileInfo ti;
+    ti.leaf = t.leaf;
+    ti.i0 = t.i0;
+    ti.ub = t.ub;
+    ti.u0 = t.ub * TN;
+    ti.m = size[t.leaf];
+    const int s_min = max(0, ti.u0 - (Dl - 1));
+    const int s_max = min(Dl - 1, ti.u0 + TN - 1);
+    ti.sb_lo = s_min / KS;
+    ti.sb_hi = (s_max >= s_min) ? s_max / KS : ti.sb_lo - 1;
+    ti.njc = (ti.m + JC - 1) / JC;
+    ti.Q = (ti.sb_hi - ti.sb_lo + 1) * ti.m;
+    return ti;
+}
+
+__device__ __forceinline__ void fail(Smem &sm, int32_t *dstat) {
+    sm.abort = 1;
+    atomicExch(dstat, DEV_TIMEOUT);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_leaf_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+              const Tile *__restrict__ tiles, int ntiles, const int *__restrict__ size, int Dl, int Dp,
+              uint8_t *__restrict__ dig, int32_t *__restrict__ carry, int MT, int Uo, int NUB, int32_t *dstat) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < A_STAGES; ++s) { mbar_init(&sm.a_full[s], 1); mbar_init(&sm.a_empty[s], 1); }
+        for (int s = 0; s < B_STAGES; ++s) { mbar_init(&sm.b_full[s], 1); mbar_init(&sm.b_empty[s], 1); }
+        for (int s = 0; s < 2; ++s) { mbar_init(&sm.acc_full[s], 1); mbar_init(&sm.acc_empty[s], kNumEpiWarps); }
+        mbar_init(&sm.drain, 1);
+        sm.abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == kMmaWarp) {
+        tmem_alloc(&sm.tmem_base, kTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sm.tmem_base;
+
+    if (warp == kProducerWarp) {
+        if (lane == 0) {
+            tma_prefetch_desc(&mapA);
+            tma_prefetch_desc(&mapB);
+            int as = 0, aph = 0, bs = 0, bph = 0;
+            for (int t = blockIdx.x; t < ntiles && !sm.abort; t += gridDim.x) {
+                const TileInfo ti = decode(tiles[t], size, Dl);
+                for (int sb = ti.sb_lo; sb <= ti.sb_hi && !sm.abort; ++sb) {
+                    const int s_lo = sb * KS;
+                    for (int jc = 0; jc < ti.njc && !sm.abort; ++jc) {
+                        const int j0 = jc * JC;
+                        const int jn = min(JC, ti.m - j0);
+                        if (!mbar_wait(&sm.a_empty[as], aph ^ 1, kTimeoutNs)) { fail(sm, dstat); break; }
+                        mbar_arrive_expect_tx(&sm.a_full[as], A_BYTES);
+                        tma_load_4d(sm.a[as], &mapA, &sm.a_full[as], 0, ti.i0 + j0, (Dp - s_lo - KS) / 8, ti.leaf);
+                        if (++as == A_STAGES) { as = 0; aph ^= 1; }
+                        for (int jj = 0; jj < jn; ++jj) {
+                            if (!mbar_wait(&sm.b_empty[bs], bph ^ 1, kTimeoutNs)) { fail(sm, dstat); break; }
+                            mbar_arrive_expect_tx(&sm.b_full[bs], B_BYTES);
+                            tma_load_5d(sm.b[bs], &mapB, &sm.b_full[bs], 0, 0, (ti.u0 - s_lo - KS) / 8 + 1,
+                                        j0 + jj, ti.leaf);
+                            if (++bs == B_STAGES) { bs = 0; bph ^= 1; }
+                        }
+                    }
+                }
+            }
+        }
+    } else if (warp == kMmaWarp) {
+        if (lane == 0) {
+            int as = 0, aph = 0, bs = 0, bph = 0, ab = 0;
+            int accph[2] = {0, 0};
+            const uint32_t a_base0 = smem_u32(sm.a[0]);
+            const uint32_t b_base0 = smem_u32(sm.b[0]);
+            for (int t = blockIdx.x; t < ntiles && !sm.abort; t += gridDim.x) {
+                const TileInfo ti = decode(tiles[t], size, Dl);
+                int q = 0;
+                uint32_t acc_flag = 0;
+                for (int sb = ti.sb_lo; sb <= ti.sb_hi && !sm.abort; ++sb) {
+                    for (int jc = 0; jc < ti.njc && !sm.abort; ++jc) {
+                        const int jn = min(JC, ti.m - jc * JC);
+                        if (!mbar_wait(&sm.a_full[as], aph, kTimeoutNs)) { fail(sm, dstat); break; }
+                        const uint32_t a_base = a_base0 + as * A_BYTES;
+                        for (int jj = 0; jj < jn; ++jj) {
+                            if (q % FLUSH_J == 0) {
+                                if (!mbar_wait(&sm.acc_empty[ab], accph[ab] ^ 1, kTimeoutNs)) { fail(sm, dstat); break; }
+                                acc_flag = 0;
+                            }
+                            if (!mbar_wait(&sm.b_full[bs], bph, kTimeoutNs)) { fail(sm, dstat); break; }
+                            tc_fence_after();
+                            const uint32_t b_base = b_base0 + bs * B_BYTES;
+                            const uint32_t d_tmem = tmem + ab * TN;
+#pragma unroll
+                            for (int ks = 0; ks < KS / 16; ++ks) {
+                                const uint64_t ad = smem_desc(a_base + jj * 16 + ks * 2 * kLboA, kLboA, 128);
+                                const uint64_t bd = smem_desc(b_base + ks * 256, 128, 128);
+                                mma_bf16_ss(d_tmem, ad, bd, kIdesc, (acc_flag | ks) ? 1u : 0u);
+                            }
+                            acc_flag = 1;
+                            mma_commit(&sm.b_empty[bs]);
+                            if (++bs == B_STAGES) { bs = 0; bph ^= 1; }
+                            ++q;
+                            if (q % FLUSH_J == 0 || q == ti.Q) {
+                                mma_commit(&sm.acc_full[ab]);
+                                accph[ab] ^= 1;
+                                ab ^= 1;
+                            }
+                        }
+                        mma_commit(&sm.a_empty[as]);
+                        if (++as == A_STAGES) { as = 0; aph ^= 1; }
+                    }
+                }
+            }
+            // all MMAs issued by this thread complete before TMEM is released
+            mma_commit(&sm.drain);
+            if (!mbar_wait(&sm.drain, 0, kTimeoutNs)) fail(sm, dstat);
+        }
+    } else {
+        // epilogue: warp w serves TMEM lanes 32*(w%4) .. +31
+        const int lq = warp % 4;
+        const uint32_t lane_addr = tmem + (static_cast<uint32_t>(lq * 32) << 16);
+        int ab = 0;
+        int eph[2] = {0, 0};
+        for (int t = blockIdx.x; t < ntiles && !sm.abort; t += gridDim.x) {
+            const TileInfo ti = decode(tiles[t], size, Dl);
+            const int G = (ti.Q + FLUSH_J - 1) / FLUSH_J;
+            uint32_t st[TN / 4];
+#pragma unroll
+            for (int w = 0; w < TN / 4; ++w) st[w] = 0;
+            int co = 0;
+            bool ok = true;
+            for (int g = 0; g < G; ++g) {
+                if (!mbar_wait(&sm.acc_full[ab], eph[ab], kTimeoutNs)) { fail(sm, dstat); ok = false; break; }
+                eph[ab] ^= 1;
+                tc_fence_after();
+                int c = 0;
+#pragma unroll
+                for (int ch = 0; ch < TN / 32; ++ch) {
+                    uint32_t v[32];
+                    tmem_ld_32x32b_x32(lane_addr + ab * TN + ch * 32, v);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int q4 = 0; q4 < 8; ++q4) {
+                        const uint32_t word = st[ch * 8 + q4];
+                        uint32_t nw = 0;
+#pragma unroll
+                        for (int by = 0; by < 4; ++by) {
+                            const int x = __float2int_rn(__uint_as_float(v[q4 * 4 + by]));
+                            const int tt = static_cast<int>((word >> (8 * by)) & 0xFFu) + x + c;
+                            nw |= static_cast<uint32_t>(tt & 0xFF) << (8 * by);
+                            c = tt >> 8;
+                        }
+                        st[ch * 8 + q4] = nw;
+                    }
+                }
+                co += c;
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm.acc_empty[ab]);
+                ab ^= 1;
+            }
+            if (!ok) break;
+            const int row = ti.i0 + lq * 32 + lane;
+            if (row < ti.m) {
+                const size_t r = static_cast<size_t>(ti.leaf) * MT * TM + row;
+                uint4 *o = reinterpret_cast<uint4 *>(dig + r * Uo + ti.u0);
+#pragma unroll
+                for (int w = 0; w < TN / 16; ++w)
+                    o[w] = make_uint4(st[4 * w], st[4 * w + 1], st[4 * w + 2], st[4 * w + 3]);
+                carry[r * NUB + ti.ub] = co;
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (sm.abort && threadIdx.x == 0) {
+        // let copies still in flight land before the shared memory goes away
+        const uint64_t t0 = global_ns();
+        while (global_ns() - t0 < 20000000ull) { }
+    }
+    __syncthreads();
+    tc_fence_after();
+    if (warp == kMmaWarp) tmem_dealloc(tmem, kTmemCols);
+}
+
+}  // namespace
+
+size_t leaf_tc_smem_bytes() { return sizeof(Smem) + 1024; }
+
+cudaError_t launch_leaf_tc(hmv_plan_s *p) {
+    static bool attr_set = false;
+    const size_t smem = sizeof(Smem);
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_leaf_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int grid = std::min(p->ntiles, p->num_sms);
+    if (grid <= 0) return cudaSuccess;
+    k_leaf_tc<<<grid, kThreads, smem, p->stream>>>(p->mapA, p->mapB, p->d_tiles, p->ntiles, p->lv[p->L].d_size, p->Dl,
+                                                   p->Dp, p->leaf_dig, p->leaf_carry, p->MT, p->Uo, p->NUB, p->dstat);
+    p->launches_leaf++;
+    p->launches_total++;
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ tensor maps
+namespace {
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn get_encode() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &ptr, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(ptr);
+    }
+    return fn;
+}
+}  // namespace
+
+cudaError_t make_tensor_maps(hmv_plan_s *p) {
+    EncodeTiledFn enc = get_encode();
+    if (!enc) return cudaErrorNotSupported;
+    const int nleaves = p->lv[p->L].nodes;
+    const cuuint64_t chunks = static_cast<cuuint64_t>(p->Dp / 8);
+    // A: hrev[leaf][chunk][RA][8] bf16 (packed): (8 digits, rows, chunks, leaf)
+    {
+        cuuint64_t dims[4] = {8, static_cast<cuuint64_t>(p->RA), chunks, static_cast<cuuint64_t>(nleaves)};
+        cuuint64_t strides[3] = {16, static_cast<cuuint64_t>(p->RA) * 16, chunks * p->RA * 16};
+        cuuint32_t box[4] = {8, static_cast<cuuint32_t>(AR), static_cast<cuuint32_t>(KS / 8), 1};
+        cuuint32_t es[4] = {1, 1, 1, 1};
+        CUresult r = enc(&p->mapA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, p->hrev, dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+    // B: xg[leaf][RX][chunk][8][8] bf16 (packed): (8 digits, 8 copies, chunks, j, leaf)
+    {
+        const cuuint64_t xc = chunks + 1;
+        cuuint64_t dims[5] = {8, 8, xc, static_cast<cuuint64_t>(p->RX), static_cast<cuuint64_t>(nleaves)};
+        cuuint64_t strides[4] = {16, 128, xc * 128, static_cast<cuuint64_t>(p->RX) * xc * 128};
+        cuuint32_t box[5] = {8, 8, static_cast<cuuint32_t>(NE), 1, 1};
+        cuuint32_t es[5] = {1, 1, 1, 1, 1};
+        CUresult r = enc(&p->mapB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, p->xg, dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+    p->maps_ok = true;
+    return cudaSuccess;
+}
+
+}  // namespace hmv

@@ -1,0 +1,163 @@
+"""ctypes binding of libhmv (include/hmv.h): argument marshalling only.
+
+Every step of the product runs in the CUDA library; there is no CPU path.
+Loading fails loudly if libhmv.so has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .inputs import FixedVec
+
+HANKEL, TOEPLITZ, CIRCULANT = 0, 1, 2
+AUTO, SCHOOLBOOK, KARATSUBA, FFT64 = 0, 1, 2, 3
+FLAG_TIMING, FLAG_SIMT_LEAF = 1, 2
+STATUS = {0: "HMV_OK", 1: "HMV_EINVAL", 2: "HMV_ENOMEM", 3: "HMV_ECUDA", 4: "HMV_ETIMEOUT",
+          5: "HMV_ENOTLOADED", 6: "HMV_EFFTBOUND", 7: "HMV_EUNSUPPORTED"}
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libhmv.so")
+EXPORTS = ["hmv_plan", "hmv_load_matrix", "hmv_matvec", "hmv_free", "hmv_get_stats", "hmv_reset_stats",
+           "hmv_status_string", "hmv_version"]
+
+
+class HmvError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}")
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("b", ctypes.c_int32), ("nrhs", ctypes.c_int32), ("kind", ctypes.c_int32),
+                ("method", ctypes.c_int32), ("levels", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("reserved", ctypes.c_int32)]
+
+
+class Vec(ctypes.Structure):
+    _fields_ = [("len", ctypes.c_int32), ("nrhs", ctypes.c_int32), ("b", ctypes.c_int32),
+                ("exponent", ctypes.c_int32), ("limbs", ctypes.c_void_p), ("neg", ctypes.c_void_p),
+                ("on_device", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int32), ("leaves", ctypes.c_int32), ("leaf_rows_max", ctypes.c_int32),
+                ("digits", ctypes.c_int32), ("leaf_tiles", ctypes.c_int64), ("leaf_macs", ctypes.c_double),
+                ("leaf_macs_issued", ctypes.c_double), ("device_bytes", ctypes.c_int64),
+                ("ms_prepass", ctypes.c_double), ("ms_leaf", ctypes.c_double), ("ms_post", ctypes.c_double),
+                ("ms_round", ctypes.c_double), ("ms_total", ctypes.c_double), ("launches_leaf", ctypes.c_int64),
+                ("launches_total", ctypes.c_int64), ("matvecs", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """The CUDA library; raises if it is missing (no fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"libhmv.so not built ({path}); run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        vp = ctypes.c_void_p
+        lib.hmv_plan.argtypes = [ctypes.POINTER(Desc), vp, ctypes.POINTER(vp)]
+        lib.hmv_plan.restype = ctypes.c_int
+        lib.hmv_load_matrix.argtypes = [vp, ctypes.POINTER(Vec)]
+        lib.hmv_load_matrix.restype = ctypes.c_int
+        lib.hmv_matvec.argtypes = [vp, ctypes.POINTER(Vec), ctypes.POINTER(Vec)]
+        lib.hmv_matvec.restype = ctypes.c_int
+        lib.hmv_free.argtypes = [vp]
+        lib.hmv_free.restype = None
+        lib.hmv_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+        lib.hmv_get_stats.restype = ctypes.c_int
+        lib.hmv_reset_stats.argtypes = [vp]
+        lib.hmv_reset_stats.restype = ctypes.c_int
+        lib.hmv_status_string.argtypes = [ctypes.c_int]
+        lib.hmv_status_string.restype = ctypes.c_char_p
+        lib.hmv_version.argtypes = []
+        lib.hmv_version.restype = ctypes.c_int32
+        _lib = lib
+    return _lib
+
+
+def _check(st: int, where: str):
+    if st != 0:
+        raise HmvError(st, where)
+
+
+def _host_vec(v: FixedVec, nrhs: int = 1) -> tuple[Vec, tuple]:
+    limbs = np.ascontiguousarray(v.limbs, dtype=np.uint32)
+    neg = np.ascontiguousarray(v.neg, dtype=np.uint8)
+    vec = Vec(v.count // nrhs, nrhs, v.b, v.exponent, limbs.ctypes.data, neg.ctypes.data, 0, 0)
+    return vec, (limbs, neg)
+
+
+class Plan:
+    """One plan = one matrix order, precision, kind, method and stream."""
+
+    def __init__(self, n: int, b: int, kind: int = HANKEL, method: int = AUTO, levels: int = -1, nrhs: int = 1,
+                 flags: int = 0, stream=None):
+        self.lib = load_library()
+        self.n, self.b, self.kind, self.nrhs = n, b, kind, nrhs
+        self.L32 = (b + 31) // 32
+        d = Desc(n, b, nrhs, kind, method, levels, flags, 0)
+        handle = ctypes.c_void_p()
+        s = ctypes.c_void_p(0 if stream is None else int(stream))
+        _check(self.lib.hmv_plan(ctypes.byref(d), s, ctypes.byref(handle)), "hmv_plan")
+        self.handle = handle
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self.lib.hmv_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---------------------------------------------------------------- host
+    def load_matrix(self, h: FixedVec):
+        vec, keep = _host_vec(h)
+        _check(self.lib.hmv_load_matrix(self.handle, ctypes.byref(vec)), "hmv_load_matrix")
+        del keep
+
+    def matvec(self, x: FixedVec) -> FixedVec:
+        """Host in, host out (copies to and from the device inside the call)."""
+        xv, keep = _host_vec(x, self.nrhs)
+        rows = self.n * self.nrhs
+        y_limbs = np.zeros((rows, self.L32), dtype=np.uint32)
+        y_neg = np.zeros(rows, dtype=np.uint8)
+        yv = Vec(self.n, self.nrhs, self.b, 0, y_limbs.ctypes.data, y_neg.ctypes.data, 0, 0)
+        _check(self.lib.hmv_matvec(self.handle, ctypes.byref(xv), ctypes.byref(yv)), "hmv_matvec")
+        del keep
+        return FixedVec(y_limbs, y_neg, self.b, int(yv.exponent))
+
+    # ---------------------------------------------------------------- device
+    def load_matrix_device(self, limbs_ptr: int, neg_ptr: int, length: int, exponent: int):
+        vec = Vec(length, 1, self.b, exponent, limbs_ptr, neg_ptr, 1, 0)
+        _check(self.lib.hmv_load_matrix(self.handle, ctypes.byref(vec)), "hmv_load_matrix")
+
+    def matvec_device(self, x_limbs_ptr: int, x_neg_ptr: int, x_exponent: int, y_limbs_ptr: int,
+                      y_neg_ptr: int) -> int:
+        """Device pointers in and out (ordered on the plan's stream); returns E_y."""
+        xv = Vec(self.n, self.nrhs, self.b, x_exponent, x_limbs_ptr, x_neg_ptr, 1, 0)
+        yv = Vec(self.n, self.nrhs, self.b, 0, y_limbs_ptr, y_neg_ptr, 1, 0)
+        _check(self.lib.hmv_matvec(self.handle, ctypes.byref(xv), ctypes.byref(yv)), "hmv_matvec")
+        return int(yv.exponent)
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(self.lib.hmv_get_stats(self.handle, ctypes.byref(s)), "hmv_get_stats")
+        return {name: getattr(s, name) for name, _ in Stats._fields_}
+
+    def reset_stats(self):
+        _check(self.lib.hmv_reset_stats(self.handle), "hmv_reset_stats")

@@ -1,0 +1,69 @@
+"""The C-ABI library builds for sm_103a, loads and exports every entry point
+declared in include/hmv.h; descriptor checks answer without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1402_5287_gb300 as pkg
+from paper_1402_5287_gb300 import hmv
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(hmv_\w+)\s*\(", text))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pkg.build()
+    return hmv.load_library()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert {"hmv_plan", "hmv_load_matrix", "hmv_matvec", "hmv_free"} <= names
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(hmv.EXPORTS) <= names
+
+
+def test_status_strings_and_version(lib):
+    assert lib.hmv_status_string(0) == b"ok"
+    assert lib.hmv_status_string(1) == b"invalid argument"
+    assert lib.hmv_status_string(99) == b"unknown status"
+    assert lib.hmv_version() >= 100
+
+
+@pytest.mark.parametrize("field,value", [("n", 0), ("b", 0), ("b", (1 << 20) + 1), ("nrhs", 0), ("kind", 3),
+                                         ("method", 9), ("levels", -2), ("levels", 17), ("flags", 1 << 7),
+                                         ("reserved", 1)])
+def test_plan_rejects_bad_descriptors_without_gpu(lib, field, value):
+    d = hmv.Desc(16, 64, 1, 0, 0, -1, 0, 0)
+    setattr(d, field, value)
+    out = ctypes.c_void_p()
+    assert lib.hmv_plan(ctypes.byref(d), None, ctypes.byref(out)) == 1
+    assert out.value is None
+
+
+def test_null_arguments(lib):
+    out = ctypes.c_void_p()
+    assert lib.hmv_plan(None, None, ctypes.byref(out)) == 1
+    assert lib.hmv_load_matrix(None, None) == 1
+    assert lib.hmv_matvec(None, None, None) == 1
+    lib.hmv_free(None)  # NULL is ignored
+
+
+def test_struct_layouts_match_header():
+    assert ctypes.sizeof(hmv.Desc) == 32
+    assert ctypes.sizeof(hmv.Vec) == 40
+    assert hmv.Vec.limbs.offset == 16 and hmv.Vec.neg.offset == 24 and hmv.Vec.on_device.offset == 32
+    assert ctypes.sizeof(hmv.Stats) == 4 * 4 + 8 + 8 * 2 + 8 + 8 * 5 + 8 * 3
