@@ -1,0 +1,382 @@
+"""Benchmark: exact Hankel matvecs/s at n = 8000, b = 33220 bits (10^4 digits).
+
+One step = one whole y = A x through the C ABI (encode x, Algorithm 1 steps
+3/5 for every level, tensor-core leaf products, step 8 for every level,
+exact rows, b-bit rounding), inputs resident in device memory.  Prints ONE
+JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the plain schoolbook definition,
+threaded over rows) on a bounded sample of rows of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Hankel matvecs/s at n=8000, 10^4 digits"
+UNIT = "matvecs/s"
+WORKLOAD = "large"
+WORKLOAD_DESC = "Hankel y=Ax, n=8000, b=33220 bits (10^4 decimal digits), h and x uniform signed fixed-point in (-1,1)"
+
+
+# ---------------------------------------------------------------- distributed helpers
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def init_dist(world: int, backend: str):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    if not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def reduce_max(dist, value: float) -> float:
+    """Largest value over all ranks (the job's time is its slowest rank's)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64)
+    if dist.get_backend() == "nccl":
+        t = t.cuda()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank: int, world: int, seconds_max: float) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return units_per_rank * world / seconds_max if seconds_max > 0 else 0.0
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="hmv_clocks_", suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=self.out,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.out.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return None
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "", 1).isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "", 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- CPU oracle timing
+
+def oracle_sample(n, h, x, seconds_target=(10.0, 30.0), rows_per_batch=None):
+    """Times the oracle on whole rows of the workload until ~10-30 s of work;
+    returns (matvecs/s extrapolated from rows/s, cores, rows timed)."""
+    import random
+
+    import numpy as np
+
+    import oracle
+    cores = oracle.default_threads()
+    batch = rows_per_batch or cores
+    rng = random.Random(7)
+    done, t_used = 0, 0.0
+    while t_used < seconds_target[0]:
+        rows = np.array(sorted(rng.sample(range(n), batch)), dtype=np.int32)
+        t0 = time.perf_counter()
+        oracle.exact_rows(oracle.HANKEL, n, h.b, h, x, rows, cores)
+        t_used += time.perf_counter() - t0
+        done += batch
+        if t_used > seconds_target[1] * 0.5:
+            break
+    per_matvec = t_used / done * n
+    return 1.0 / per_matvec, cores, done, t_used
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    n, b, h, x = load_workload(args)
+    cores = oracle.default_threads()
+    import numpy as np
+    import random
+    rng = random.Random(11)
+    per_step = []
+    for step in range(args.warmup + args.steps):
+        rows = np.array(sorted(rng.sample(range(n), cores)), dtype=np.int32)
+        t0 = time.perf_counter()
+        oracle.exact_rows(oracle.HANKEL, n, b, h, x, rows, cores)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            per_step.append(dt)
+    mean = sum(per_step) / len(per_step)
+    value = 1.0 / (mean * n / cores)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32 limbs (exact)", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "n": n, "b": b, "method": "CPU oracle: schoolbook definition"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"each step: {cores} random rows of the n={n} product, one per thread; "
+                                       f"matvecs/s extrapolated as cores/(step time * n)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1402_5287_gb300 import hmv
+    from paper_1402_5287_gb300.inputs import workload
+    import paper_1402_5287_gb300 as pkg
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
+    pkg.build()
+    n, b, h, x = load_workload(args)
+    L32 = (b + 31) // 32
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+
+    plan = hmv.Plan(n, b, method=hmv.AUTO, levels=args.levels, flags=hmv.FLAG_TIMING, stream=stream.cuda_stream)
+    plan.load_matrix(h)
+    with torch.cuda.stream(stream):
+        xl = torch.from_numpy(x.limbs.view(np.int32)).to(dev)
+        xn = torch.from_numpy(x.neg).to(dev)
+        yl = torch.empty_like(xl)
+        yn = torch.empty_like(xn)
+    stream.synchronize()
+
+    def step():
+        return plan.matvec_device(xl.data_ptr(), xn.data_ptr(), x.exponent, yl.data_ptr(), yn.data_ptr())
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    plan.reset_stats()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    secs = ev0.elapsed_time(ev1) / 1e3
+    secs_max = reduce_max(dist, secs)
+    st = plan.stats()
+    value = aggregate_rate(args.steps, world, secs_max)
+
+    # roofline of the dominant kernel (leaf products): useful digit MACs x 2 per
+    # launch over its mean CUDA-event duration on the plan's stream
+    leaf_ms = st["ms_leaf"] / max(st["launches_leaf"], 1)
+    flops_per_launch = 2.0 * st["leaf_macs"]
+    achieved_tflops = flops_per_launch / (leaf_ms / 1e3) / 1e12 if leaf_ms > 0 else 0.0
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    peak = peaks.get("bf16_tflops_sustained")
+    peak_src = "measured sustained bf16 (MEASURED_PEAKS.json)"
+    if peak is None:
+        peak, peak_src = 1700.0, "fallback sustained bf16"
+
+    # end to end through the public API: host x in, host y out, copies inside the timed region
+    e2e = None
+    if True:
+        pin_x_l = torch.from_numpy(x.limbs.view(np.int32)).pin_memory()
+        pin_x_n = torch.from_numpy(x.neg).pin_memory()
+        pin_y_l = torch.empty_like(pin_x_l).pin_memory()
+        pin_y_n = torch.empty_like(pin_x_n).pin_memory()
+        xv = hmv.Vec(n, 1, b, x.exponent, pin_x_l.data_ptr(), pin_x_n.data_ptr(), 0, 0)
+        yv = hmv.Vec(n, 1, b, 0, pin_y_l.data_ptr(), pin_y_n.data_ptr(), 0, 0)
+        import ctypes
+        for _ in range(1):
+            plan.lib.hmv_matvec(plan.handle, ctypes.byref(xv), ctypes.byref(yv))
+        k2 = max(1, min(args.steps, 5))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(k2):
+            rc = plan.lib.hmv_matvec(plan.handle, ctypes.byref(xv), ctypes.byref(yv))
+            if rc != 0:
+                raise RuntimeError(f"hmv_matvec failed: {rc}")
+        t_e2e = time.perf_counter() - t0
+        t_e2e = reduce_max(dist, t_e2e)
+        e2e = {"value": aggregate_rate(k2, world, t_e2e), "unit": UNIT,
+               "h2d_bytes_per_step": n * L32 * 4 + n, "d2h_bytes_per_step": n * L32 * 4 + n}
+    plan.close()
+
+    comparisons = {}
+    if args.compare and rank == 0:
+        comparisons = compare_kernels(hmv, h, x, n, b, stream)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, rows, t_used = oracle_sample(n, h, x)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{rows} random rows of the n={n}, b={b} product ({t_used:.1f} s on {cores} threads); "
+                         f"matvecs/s extrapolated from rows/s"}
+
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": secs_max / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "n": n, "b": b, "kind": "hankel", "method": "karatsuba+tcgen05",
+                   "levels": st["levels"], "leaves": st["leaves"], "leaf_rows_max": st["leaf_rows_max"],
+                   "digits_per_operand": st["digits"], "leaf_tiles": st["leaf_tiles"],
+                   "digit_format": "balanced radix-2^8 digits held exactly in bf16, fp32 windows < 2^24",
+                   "l2": "working set of several GB per step (inputs larger than L2)",
+                   "parallelism": f"{world} independent replica(s), one per GPU"},
+        "roofline": {"bound": "tensor", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved_tflops / peak if peak else None, "traffic": None,
+                     "kernel": "k_leaf_tc", "peak_source": peak_src,
+                     "flops_per_launch": flops_per_launch, "launch_ms": leaf_ms,
+                     "issued_over_useful": st["leaf_macs_issued"] / st["leaf_macs"] if st["leaf_macs"] else None},
+        "stage_ms": {"prepass": st["ms_prepass"] / max(st["matvecs"], 1), "leaf": leaf_ms,
+                     "post": st["ms_post"] / max(st["matvecs"], 1), "round": st["ms_round"] / max(st["matvecs"], 1)},
+        "gpu_launches": int(st["launches_total"]),
+        "clocks": clocks.summary(),
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    if comparisons:
+        line["comparisons"] = comparisons
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def compare_kernels(hmv, h, x, n, b, stream):
+    """Same workload through the comparison paths (one timed matvec each)."""
+    import numpy as np
+    import torch
+    out = {}
+    for name, method, levels in (("tensor_core_schoolbook_L0", hmv.KARATSUBA, 0),
+                                 ("plain_schoolbook_cuda_cores", hmv.SCHOOLBOOK, -1)):
+        plan = hmv.Plan(n, b, method=method, levels=levels, stream=stream.cuda_stream)
+        plan.load_matrix(h)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        xl = torch.from_numpy(x.limbs.view(np.int32)).to(dev)
+        xn = torch.from_numpy(x.neg).to(dev)
+        yl = torch.empty_like(xl)
+        yn = torch.empty_like(xn)
+        torch.cuda.synchronize()
+        reps = 2 if method == hmv.KARATSUBA else 1
+        plan.matvec_device(xl.data_ptr(), xn.data_ptr(), x.exponent, yl.data_ptr(), yn.data_ptr())
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            plan.matvec_device(xl.data_ptr(), xn.data_ptr(), x.exponent, yl.data_ptr(), yn.data_ptr())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s = e0.elapsed_time(e1) / 1e3 / reps
+        out[name] = {"value": 1.0 / s, "unit": UNIT, "ms_per_matvec": s * 1e3}
+        plan.close()
+    return out
+
+
+def load_workload(args):
+    """The benchmark workload, or a smaller one of the same recipe (--n/--b,
+    for profiling captures)."""
+    from paper_1402_5287_gb300.inputs import BASE_SEED, uniform_vec, workload
+    global WORKLOAD_DESC
+    if args.n is None and args.b is None:
+        return workload(WORKLOAD)
+    n = args.n or 8000
+    b = args.b or 33220
+    WORKLOAD_DESC = f"Hankel y=Ax, n={n}, b={b} bits, h and x uniform signed fixed-point in (-1,1)"
+    return n, b, uniform_vec(BASE_SEED + 2, 0, 2 * n - 1, b, 0), uniform_vec(BASE_SEED + 2, 1, n, b, 0)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--levels", type=int, default=-1, help="Karatsuba depth (-1: cost model)")
+    ap.add_argument("--compare", action="store_true", help="also time the schoolbook comparison kernels")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=None, help="matrix order (profiling runs; default 8000)")
+    ap.add_argument("--b", type=int, default=None, help="mantissa bits (profiling runs; default 33220)")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
