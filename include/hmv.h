@@ -136,6 +136,46 @@ hmv_status hmv_get_stats(const hmv_plan_t *plan, hmv_stats *out);
 /* Zero the timing counters of hmv_get_stats. */
 hmv_status hmv_reset_stats(hmv_plan_t *plan);
 
+/*
+ * Scratch-free schoolbook product (no counterpart in the paper: it is an
+ * interface for callers, not part of the method).
+ *
+ * For callers that cannot allocate device memory while they run: code that
+ * must stay inside another runtime's memory budget, code on a path where a
+ * cudaMalloc would synchronise the device or fail under a memory cap, and
+ * callers with no allocator of their own.  hmv_schoolbook_noalloc computes
+ * the same y = A x as hmv_matvec with HMV_SCHOOLBOOK (same rounding, bit for
+ * bit) without a plan and without calling cudaMalloc, cudaFree or any
+ * allocating routine.  Its only working memory is one scratch array of
+ * HMV_NOALLOC_SCRATCH_BYTES compiled into the library as a device variable:
+ * every GPU that loads the library holds it until the process exits.
+ *
+ * Arguments: n, b, kind as in hmv_desc; h_limbs/h_neg (2n-1 entries, or n
+ * for circulant), x_limbs/x_neg (n entries) and y_limbs/y_neg (n entries)
+ * are DEVICE pointers in the layout of hmv_vec, allocated by the caller;
+ * the exponents of h and x are passed by value and E_y is written to the
+ * host int *y_exponent.  stream: a cudaStream_t (NULL = legacy default).
+ * The call orders its work on the stream and returns after one stream
+ * synchronisation (to read E_y back).
+ * Limit: with L = ceil(b/32), it needs at most
+ *     n * (32 L + 8 L + 13) + 1536  bytes  <=  HMV_NOALLOC_SCRATCH_BYTES
+ * (for example n <= 3200 at b = 1024, n <= 100 at b = 33220); larger
+ * problems return HMV_EINVAL and do nothing.  Bits at or above b in h or x
+ * also return HMV_EINVAL and leave y unwritten.
+ * Set-up: the first call on each device looks the scratch array's device
+ * address up (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.
+ * Sharing: all calls on a device use the same scratch array, which keeps
+ * the last call's contents (the call clears what must start at zero).
+ * Calls whose work overlaps on the GPU (other streams, other threads) race
+ * on it: order them on one stream or otherwise serialise them.
+ */
+#define HMV_NOALLOC_SCRATCH_BYTES (4u << 20)
+hmv_status hmv_schoolbook_noalloc(int32_t n, int32_t b, int32_t kind,
+                                  const uint32_t *h_limbs, const uint8_t *h_neg, int32_t h_exponent,
+                                  const uint32_t *x_limbs, const uint8_t *x_neg, int32_t x_exponent,
+                                  uint32_t *y_limbs, uint8_t *y_neg, int32_t *y_exponent, void *stream);
+
 /* Static description of a status code. */
 const char *hmv_status_string(hmv_status s);
 

@@ -537,4 +537,15 @@ cudaError_t launch_round(hmv_plan_s *p, int rows, int e_in, uint32_t *y_limbs, u
     return cudaGetLastError();
 }
 
+// Normalisation and rounding on caller-given buffers (used by the
+// scratch-free entry point); dstat must start zeroed.
+cudaError_t launch_colsum_round_raw(const __int128 *colsum, int n, int L32, uint32_t *zmag, uint8_t *zneg,
+                                    int32_t *zbits, int ZW, int32_t *dstat, int b, int e_in, int reverse,
+                                    uint32_t *y, uint8_t *yneg, cudaStream_t stream) {
+    k_colsum_normalize<<<blocks_for(n, 128), 128, 0, stream>>>(colsum, n, 2 * L32, zmag, zneg, zbits, ZW, dstat, 0);
+    k_round_check<<<blocks_for(n, 128), 128, 0, stream>>>(zmag, zbits, n, ZW, b, dstat);
+    k_round<<<blocks_for(n, 128), 128, 0, stream>>>(zmag, zneg, n, 1, ZW, b, L32, e_in, reverse, dstat, y, yneg);
+    return cudaGetLastError();
+}
+
 }  // namespace hmv

@@ -61,4 +61,19 @@ cudaError_t launch_schoolbook(hmv_plan_s *p, const uint32_t *x_limbs, const uint
     return cudaGetLastError();
 }
 
+// Same kernel on caller-given buffers (used by the scratch-free entry point).
+cudaError_t launch_schoolbook_raw(const uint32_t *hl, const uint8_t *hn, const uint32_t *xl, const uint8_t *xn, int n,
+                                  int L32, int circ, __int128 *colsum, cudaStream_t stream) {
+    const int ncols = 2 * L32;
+    dim3 grid((ncols + kT - 1) / kT, n);
+    const size_t smem = static_cast<size_t>(2) * L32 * sizeof(uint32_t);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_schoolbook, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+    }
+    k_schoolbook<<<grid, kT, smem, stream>>>(hl, hn, xl, xn, n, L32, circ, colsum);
+    return cudaGetLastError();
+}
+
 }  // namespace hmv

@@ -20,7 +20,8 @@ STATUS = {0: "HMV_OK", 1: "HMV_EINVAL", 2: "HMV_ENOMEM", 3: "HMV_ECUDA", 4: "HMV
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libhmv.so")
 EXPORTS = ["hmv_plan", "hmv_load_matrix", "hmv_matvec", "hmv_free", "hmv_get_stats", "hmv_reset_stats",
-           "hmv_status_string", "hmv_version"]
+           "hmv_status_string", "hmv_version", "hmv_schoolbook_noalloc"]
+NOALLOC_SCRATCH_BYTES = 4 << 20
 
 
 class HmvError(RuntimeError):
@@ -77,6 +78,10 @@ def load_library(path: str = LIB_PATH):
         lib.hmv_status_string.restype = ctypes.c_char_p
         lib.hmv_version.argtypes = []
         lib.hmv_version.restype = ctypes.c_int32
+        i32 = ctypes.c_int32
+        lib.hmv_schoolbook_noalloc.argtypes = [i32, i32, i32, vp, vp, i32, vp, vp, i32, vp, vp,
+                                               ctypes.POINTER(i32), vp]
+        lib.hmv_schoolbook_noalloc.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -91,6 +96,22 @@ def _host_vec(v: FixedVec, nrhs: int = 1) -> tuple[Vec, tuple]:
     neg = np.ascontiguousarray(v.neg, dtype=np.uint8)
     vec = Vec(v.count // nrhs, nrhs, v.b, v.exponent, limbs.ctypes.data, neg.ctypes.data, 0, 0)
     return vec, (limbs, neg)
+
+
+def schoolbook_noalloc(n: int, b: int, kind: int, h_ptrs: tuple[int, int], h_exponent: int,
+                      x_ptrs: tuple[int, int], x_exponent: int, y_ptrs: tuple[int, int], stream=None) -> int:
+    """hmv_schoolbook_noalloc on device pointers (limbs, neg); returns E_y.
+
+    For callers that cannot allocate device memory: the call uses only the
+    given buffers and the library's fixed scratch array.
+    """
+    lib = load_library()
+    e = ctypes.c_int32(0)
+    s = ctypes.c_void_p(0 if stream is None else int(stream))
+    _check(lib.hmv_schoolbook_noalloc(n, b, kind, h_ptrs[0], h_ptrs[1], h_exponent, x_ptrs[0], x_ptrs[1],
+                                      x_exponent, y_ptrs[0], y_ptrs[1], ctypes.byref(e), s),
+           "hmv_schoolbook_noalloc")
+    return int(e.value)
 
 
 class Plan:
