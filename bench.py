@@ -321,9 +321,12 @@ def compare_kernels(hmv, h, x, n, b, stream):
     import numpy as np
     import torch
     out = {}
-    for name, method, levels in (("tensor_core_schoolbook_L0", hmv.KARATSUBA, 0),
-                                 ("plain_schoolbook_cuda_cores", hmv.SCHOOLBOOK, -1)):
-        plan = hmv.Plan(n, b, method=method, levels=levels, stream=stream.cuda_stream)
+    for name, method, levels, w in (("split_fp64_fft_auto_width", hmv.FFT64, -1, 0),
+                                    ("split_fp64_fft_16bit_pieces", hmv.FFT64, -1, 16),
+                                    ("tensor_core_schoolbook_L0", hmv.KARATSUBA, 0, 0),
+                                    ("plain_schoolbook_cuda_cores", hmv.SCHOOLBOOK, -1, 0)):
+        plan = hmv.Plan(n, b, method=method, levels=levels, stream=stream.cuda_stream, piece_bits=w,
+                        flags=hmv.FLAG_TIMING)
         plan.load_matrix(h)
         dev = torch.device("cuda", torch.cuda.current_device())
         xl = torch.from_numpy(x.limbs.view(np.int32)).to(dev)
@@ -331,7 +334,7 @@ def compare_kernels(hmv, h, x, n, b, stream):
         yl = torch.empty_like(xl)
         yn = torch.empty_like(xn)
         torch.cuda.synchronize()
-        reps = 2 if method == hmv.KARATSUBA else 1
+        reps = 1 if method == hmv.SCHOOLBOOK else 2
         plan.matvec_device(xl.data_ptr(), xn.data_ptr(), x.exponent, yl.data_ptr(), yn.data_ptr())
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -342,6 +345,12 @@ def compare_kernels(hmv, h, x, n, b, stream):
         torch.cuda.synchronize()
         s = e0.elapsed_time(e1) / 1e3 / reps
         out[name] = {"value": 1.0 / s, "unit": UNIT, "ms_per_matvec": s * 1e3}
+        if method == hmv.FFT64:
+            st = plan.stats()
+            out[name].update({"piece_bits": st["fft_piece_bits"], "log2_len": st["fft_log2_len"],
+                              "error_bound": st["fft_bound"], "max_rounding_distance": st["fft_max_dist"],
+                              "fft_matvecs": st["fft_matvecs"], "fallbacks_to_integer_path": st["fft_fallbacks"],
+                              "ms_fft_per_matvec": st["ms_fft"] / max(st["fft_matvecs"], 1)})
         plan.close()
     return out
 

@@ -61,7 +61,10 @@ typedef enum {
     HMV_AUTO = 0,          /* Karatsuba recursion with the cost-model depth */
     HMV_SCHOOLBOOK = 1,    /* plain schoolbook on 32-bit limbs, CUDA cores */
     HMV_KARATSUBA = 2,     /* Algorithm 1 to the given depth, tensor-core leaves */
-    HMV_FFT64 = 3          /* split-FP64 FFT with a proven rounding bound */
+    HMV_FFT64 = 3          /* split-FP64 FFT with a proven rounding bound; when the bound
+                              for the actual data is not below 1/2 the call computes the
+                              product with the Karatsuba path instead (counted in
+                              hmv_stats.fft_fallbacks) */
 } hmv_method;
 
 /* flags for hmv_desc.flags */
@@ -76,7 +79,9 @@ typedef struct {
     int32_t method;   /* hmv_method */
     int32_t levels;   /* Karatsuba depth L (levels of Algorithm 1); -1 = cost model */
     uint32_t flags;   /* HMV_FLAG_* */
-    int32_t reserved; /* must be 0 */
+    int32_t piece_bits; /* HMV_FFT64 only: piece width w in bits (4..20), or 0 to take
+                           the largest w whose worst-case error bound is below 1/2;
+                           other methods: must be 0 */
 } hmv_desc;
 
 typedef struct {
@@ -105,6 +110,14 @@ typedef struct {
     /* with HMV_FLAG_TIMING: accumulated milliseconds and launch counts */
     double ms_prepass, ms_leaf, ms_post, ms_round, ms_total;
     int64_t launches_leaf, launches_total, matvecs;
+    /* HMV_FFT64 plans */
+    int32_t fft_piece_bits;  /* w */
+    int32_t fft_log2_len;    /* K: cyclic convolution length 2^K */
+    double fft_bound;        /* error bound of the last matvec (the result is exact when < 1/2) */
+    double fft_max_dist;     /* largest |c - round(c)| seen in the last FFT matvec */
+    int64_t fft_matvecs;     /* matvecs done by the FFT path */
+    int64_t fft_fallbacks;   /* matvecs whose bound failed and that took the integer path */
+    double ms_fft;           /* with HMV_FLAG_TIMING: time in the FFT path */
 } hmv_stats;
 
 /* Create a plan: checks the descriptor, chooses the recursion depth and

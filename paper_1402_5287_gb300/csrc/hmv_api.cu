@@ -163,12 +163,13 @@ void hmv_free(hmv_plan_t *p) {
 hmv_status hmv_plan(const hmv_desc *desc, void *stream, hmv_plan_t **out) {
     if (!desc || !out) return HMV_EINVAL;
     const hmv_desc &d = *desc;
-    if (d.n < 1 || d.b < 1 || d.b > kMaxBits || d.nrhs < 1 || d.reserved != 0) return HMV_EINVAL;
+    if (d.n < 1 || d.b < 1 || d.b > kMaxBits || d.nrhs < 1) return HMV_EINVAL;
     if (d.kind < HMV_HANKEL || d.kind > HMV_CIRCULANT) return HMV_EINVAL;
     if (d.method < HMV_AUTO || d.method > HMV_FFT64) return HMV_EINVAL;
     if (d.levels < -1 || d.levels > kMaxLevels) return HMV_EINVAL;
     if (d.flags & ~(HMV_FLAG_TIMING | HMV_FLAG_SIMT_LEAF)) return HMV_EINVAL;
-    if (d.method == HMV_FFT64) return HMV_EUNSUPPORTED;
+    if (d.method == HMV_FFT64 ? (d.piece_bits != 0 && (d.piece_bits < 4 || d.piece_bits > 16)) : d.piece_bits != 0)
+        return HMV_EINVAL;
     if (static_cast<long long>(d.n) * d.nrhs > (1LL << 30)) return HMV_EINVAL;
 
     hmv_plan_s *p = new (std::nothrow) hmv_plan_s();
@@ -267,6 +268,25 @@ hmv_status hmv_plan(const hmv_desc *desc, void *stream, hmv_plan_t **out) {
             g(cudaMemcpy(p->d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice));
         if (!simt && g.err == cudaSuccess) g(make_tensor_maps(p));
     }
+    const int hlen0 = (d.kind == HMV_CIRCULANT) ? n : 2 * n - 1;
+    if (p->method == HMV_FFT64) {
+        int w = d.piece_bits;
+        if (w == 0) {  // the largest width whose worst-case bound is below 1/2
+            w = 4;
+            for (int t = 16; t >= 4; --t)
+                if (fft_worst_bound(n, d.b, t, hlen0) < 0.5) { w = t; break; }
+        }
+        p->fft_w = w;
+        fft_geometry(n, d.b, w, p->fft_P, p->fft_S, p->fft_K);
+        p->fft_N = 1LL << p->fft_K;
+        p->ZW = std::max(p->ZW, ceil_div(static_cast<long long>(w) * (2 * p->fft_P + 3), 32) + 1);
+        g(dalloc(p, &p->fft_a, static_cast<size_t>(p->fft_N)));
+        g(dalloc(p, &p->fft_x, static_cast<size_t>(p->fft_N)));
+        g(dalloc(p, &p->fft_tw, static_cast<size_t>(p->fft_N / 2)));
+        g(dalloc(p, &p->fft_sumsq, 2));
+        g(dalloc(p, &p->fft_maxdist, 1));
+        if (g.err == cudaSuccess) g(fft_init(p));
+    }
     const int hlen = (d.kind == HMV_CIRCULANT) ? n : 2 * n - 1;
     const size_t rows = static_cast<size_t>(n) * d.nrhs;
     g(dalloc(p, &p->zmag, rows * p->ZW));
@@ -309,12 +329,18 @@ hmv_status hmv_load_matrix(hmv_plan_t *p, const hmv_vec *h) {
         p->a_leaf = p->a_lvl[p->L % 2];
         if (p->hrev) g(launch_pack_matrix(p, p->a_leaf));
     }
+    if (p->method == HMV_FFT64) g(fft_load_matrix(p));
     int32_t st[8] = {0};
     g(cudaMemcpyAsync(st, p->dstat, sizeof st, cudaMemcpyDeviceToHost, p->stream));
     g(cudaStreamSynchronize(p->stream));
     if (g.err != cudaSuccess) return from_cuda(g.err);
     if (st[0] == DEV_BADINPUT) return HMV_EINVAL;
     if (st[0] != DEV_OK) return HMV_ECUDA;
+    if (p->method == HMV_FFT64) {
+        unsigned long long sq = 0;
+        if (!g(cudaMemcpy(&sq, p->fft_sumsq, sizeof sq, cudaMemcpyDeviceToHost))) return from_cuda(g.err);
+        p->fft_sumsq_a = static_cast<double>(sq);
+    }
     p->e_h = h->exponent;
     p->loaded = true;
     return HMV_OK;
@@ -346,7 +372,25 @@ hmv_status hmv_matvec(hmv_plan_t *p, const hmv_vec *x, hmv_vec *y) {
     for (int r = 0; r < p->nrhs && g.err == cudaSuccess; ++r) {
         const uint32_t *xr = xl + static_cast<size_t>(r) * p->n * p->L32;
         const uint8_t *xnr = xn + static_cast<size_t>(r) * p->n;
-        if (p->method == HMV_SCHOOLBOOK) {
+        bool use_fft = false;
+        if (p->method == HMV_FFT64) {
+            // the bound needs the exact norm of this vector's pieces
+            g(fft_vector_pieces(p, xr, xnr));
+            unsigned long long sq = 0;
+            g(cudaMemcpyAsync(&sq, p->fft_sumsq + 1, sizeof sq, cudaMemcpyDeviceToHost, p->stream));
+            g(cudaStreamSynchronize(p->stream));
+            p->fft_bound = fft_error_bound(p->fft_sumsq_a, static_cast<double>(sq), p->fft_K);
+            use_fft = p->fft_bound < 0.5;
+            if (use_fft) p->fft_matvecs++;
+            else p->fft_fallbacks++;
+        }
+        if (use_fft) {
+            timing_mark(p, 2);
+            g(cudaMemsetAsync(p->fft_maxdist, 0, sizeof(unsigned long long), p->stream));
+            g(fft_vector_product(p, r));
+            timing_mark(p, 3);
+            timing_mark(p, 4);
+        } else if (p->method == HMV_SCHOOLBOOK) {
             timing_mark(p, 2);
             g(launch_schoolbook(p, xr, xnr, r));
             timing_mark(p, 3);
@@ -369,7 +413,8 @@ hmv_status hmv_matvec(hmv_plan_t *p, const hmv_vec *x, hmv_vec *y) {
         if (p->timing && g.err == cudaSuccess) {
             g(cudaEventSynchronize(p->ev[4]));
             ms_pre += elapsed(p, 1, 2);
-            ms_leaf += elapsed(p, 2, 3);
+            if (use_fft) p->ms_fft += elapsed(p, 2, 3);
+            else ms_leaf += elapsed(p, 2, 3);
             ms_post += elapsed(p, 3, 4);
         }
         timing_mark(p, 1);
@@ -393,6 +438,13 @@ hmv_status hmv_matvec(hmv_plan_t *p, const hmv_vec *x, hmv_vec *y) {
         if (g.err != cudaSuccess) return from_cuda(g.err);
     }
     y->exponent = st[3];
+    if (p->method == HMV_FFT64) {
+        unsigned long long md = 0;
+        if (!g(cudaMemcpy(&md, p->fft_maxdist, sizeof md, cudaMemcpyDeviceToHost))) return from_cuda(g.err);
+        double dd;
+        memcpy(&dd, &md, sizeof dd);
+        p->fft_maxdist_h = dd;
+    }
     if (p->timing) {
         p->ms_prepass += ms_pre;
         p->ms_leaf += ms_leaf;
@@ -423,13 +475,21 @@ hmv_status hmv_get_stats(const hmv_plan_t *p, hmv_stats *o) {
     o->launches_leaf = p->launches_leaf;
     o->launches_total = p->launches_total;
     o->matvecs = p->matvecs;
+    o->fft_piece_bits = p->fft_w;
+    o->fft_log2_len = p->fft_K;
+    o->fft_bound = p->fft_bound;
+    o->fft_max_dist = p->fft_maxdist_h;
+    o->fft_matvecs = p->fft_matvecs;
+    o->fft_fallbacks = p->fft_fallbacks;
+    o->ms_fft = p->ms_fft;
     return HMV_OK;
 }
 
 hmv_status hmv_reset_stats(hmv_plan_t *p) {
     if (!p) return HMV_EINVAL;
-    p->ms_prepass = p->ms_leaf = p->ms_post = p->ms_round = p->ms_total = 0;
+    p->ms_prepass = p->ms_leaf = p->ms_post = p->ms_round = p->ms_total = p->ms_fft = 0;
     p->launches_leaf = p->launches_total = p->matvecs = 0;
+    p->fft_matvecs = p->fft_fallbacks = 0;
     return HMV_OK;
 }
 

@@ -92,6 +92,18 @@ struct hmv_plan_s {
     int64_t device_bytes = 0;
     std::vector<void *> allocations;
 
+    // split-FP64 FFT path
+    int fft_w = 0, fft_P = 0, fft_S = 0, fft_K = 0;
+    long long fft_N = 0;
+    double2 *fft_a = nullptr;                // spectrum of the matrix sequence
+    double2 *fft_x = nullptr;                // work array of the vector side
+    double2 *fft_tw = nullptr;               // omega_N^m, m < N/2
+    unsigned long long *fft_sumsq = nullptr; // exact sums of squares of the pieces [a, x]
+    unsigned long long *fft_maxdist = nullptr;
+    double fft_sumsq_a = 0, fft_bound = 0, fft_maxdist_h = 0;
+    int64_t fft_matvecs = 0, fft_fallbacks = 0;
+    double ms_fft = 0;
+
     // stats
     bool timing = false;
     cudaEvent_t ev[8];
@@ -115,4 +127,12 @@ cudaError_t launch_final_normalize(hmv_plan_s *p, const int32_t *in, int rhs);
 cudaError_t launch_schoolbook(hmv_plan_s *p, const uint32_t *x_limbs, const uint8_t *x_neg, int rhs);
 cudaError_t launch_round(hmv_plan_s *p, int rows, int e_in, uint32_t *y_limbs, uint8_t *y_neg);
 cudaError_t make_tensor_maps(hmv_plan_s *p);
+// FFT path (hmv_fft.cu)
+double fft_error_bound(double sumsq_a, double sumsq_x, int K);
+void fft_geometry(int n, int b, int w, int &P, int &S, int &K);
+double fft_worst_bound(int n, int b, int w, int hlen);
+cudaError_t fft_init(hmv_plan_s *p);
+cudaError_t fft_load_matrix(hmv_plan_s *p);
+cudaError_t fft_vector_pieces(hmv_plan_s *p, const uint32_t *xl, const uint8_t *xn);
+cudaError_t fft_vector_product(hmv_plan_s *p, int rhs);
 }  // namespace hmv

@@ -33,7 +33,7 @@ class HmvError(RuntimeError):
 class Desc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("b", ctypes.c_int32), ("nrhs", ctypes.c_int32), ("kind", ctypes.c_int32),
                 ("method", ctypes.c_int32), ("levels", ctypes.c_int32), ("flags", ctypes.c_uint32),
-                ("reserved", ctypes.c_int32)]
+                ("piece_bits", ctypes.c_int32)]
 
 
 class Vec(ctypes.Structure):
@@ -48,7 +48,10 @@ class Stats(ctypes.Structure):
                 ("leaf_macs_issued", ctypes.c_double), ("device_bytes", ctypes.c_int64),
                 ("ms_prepass", ctypes.c_double), ("ms_leaf", ctypes.c_double), ("ms_post", ctypes.c_double),
                 ("ms_round", ctypes.c_double), ("ms_total", ctypes.c_double), ("launches_leaf", ctypes.c_int64),
-                ("launches_total", ctypes.c_int64), ("matvecs", ctypes.c_int64)]
+                ("launches_total", ctypes.c_int64), ("matvecs", ctypes.c_int64),
+                ("fft_piece_bits", ctypes.c_int32), ("fft_log2_len", ctypes.c_int32), ("fft_bound", ctypes.c_double),
+                ("fft_max_dist", ctypes.c_double), ("fft_matvecs", ctypes.c_int64),
+                ("fft_fallbacks", ctypes.c_int64), ("ms_fft", ctypes.c_double)]
 
 
 _lib = None
@@ -118,11 +121,11 @@ class Plan:
     """One plan = one matrix order, precision, kind, method and stream."""
 
     def __init__(self, n: int, b: int, kind: int = HANKEL, method: int = AUTO, levels: int = -1, nrhs: int = 1,
-                 flags: int = 0, stream=None):
+                 flags: int = 0, stream=None, piece_bits: int = 0):
         self.lib = load_library()
         self.n, self.b, self.kind, self.nrhs = n, b, kind, nrhs
         self.L32 = (b + 31) // 32
-        d = Desc(n, b, nrhs, kind, method, levels, flags, 0)
+        d = Desc(n, b, nrhs, kind, method, levels, flags, piece_bits)
         handle = ctypes.c_void_p()
         s = ctypes.c_void_p(0 if stream is None else int(stream))
         _check(self.lib.hmv_plan(ctypes.byref(d), s, ctypes.byref(handle)), "hmv_plan")

@@ -45,13 +45,20 @@ def test_status_strings_and_version(lib):
 
 @pytest.mark.parametrize("field,value", [("n", 0), ("b", 0), ("b", (1 << 20) + 1), ("nrhs", 0), ("kind", 3),
                                          ("method", 9), ("levels", -2), ("levels", 17), ("flags", 1 << 7),
-                                         ("reserved", 1)])
+                                         ("piece_bits", 5), ("piece_bits", -1)])
 def test_plan_rejects_bad_descriptors_without_gpu(lib, field, value):
     d = hmv.Desc(16, 64, 1, 0, 0, -1, 0, 0)
     setattr(d, field, value)
     out = ctypes.c_void_p()
     assert lib.hmv_plan(ctypes.byref(d), None, ctypes.byref(out)) == 1
     assert out.value is None
+
+
+def test_fft_piece_bits_range_without_gpu(lib):
+    out = ctypes.c_void_p()
+    for w in (3, 21, -1):
+        d = hmv.Desc(16, 64, 1, 0, 3, -1, 0, w)
+        assert lib.hmv_plan(ctypes.byref(d), None, ctypes.byref(out)) == 1
 
 
 def test_null_arguments(lib):
@@ -66,4 +73,4 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(hmv.Desc) == 32
     assert ctypes.sizeof(hmv.Vec) == 40
     assert hmv.Vec.limbs.offset == 16 and hmv.Vec.neg.offset == 24 and hmv.Vec.on_device.offset == 32
-    assert ctypes.sizeof(hmv.Stats) == 4 * 4 + 8 + 8 * 2 + 8 + 8 * 5 + 8 * 3
+    assert ctypes.sizeof(hmv.Stats) == 4 * 4 + 8 + 8 * 2 + 8 + 8 * 5 + 8 * 3 + 4 * 2 + 8 * 5
