@@ -150,6 +150,45 @@ hmv_status hmv_get_stats(const hmv_plan_t *plan, hmv_stats *out);
 hmv_status hmv_reset_stats(hmv_plan_t *plan);
 
 /*
+ * Batched products (block-Lanczos style workloads): `count` independent
+ * Hankel/Toeplitz/circulant matrices, each with its own n, b, kind and
+ * block of nrhs right-hand sides (descs[i]; method HMV_AUTO or
+ * HMV_KARATSUBA, depth -1 for the cost model), advanced together.  Every
+ * (matrix, right-hand side) pair is a leaf problem of Algorithm 1 (Sec. 3);
+ * the leaf products of all pairs of a wave run in one persistent
+ * tensor-core launch, and one hmv_batch_matvec call replays one captured
+ * CUDA graph holding every wave and every level kernel.  wave_bytes bounds
+ * the device memory of one wave's leaf operands and outputs (pairs are
+ * grouped in order; a pair larger than the budget gets a wave of its own).
+ * stream: as for hmv_plan; NULL makes the batch create its own stream
+ * (the legacy default stream cannot be captured).  Results are bit-identical
+ * to hmv_matvec on each matrix alone.
+ */
+typedef struct hmv_batch_s hmv_batch_t;
+typedef struct {
+    int32_t matrices;          /* count */
+    int32_t pairs;             /* sum of nrhs */
+    int32_t waves;             /* persistent leaf launches per call */
+    int32_t reserved;
+    int64_t leaf_tiles;        /* 128 x 256 leaf tiles per call */
+    double leaf_macs;          /* useful digit multiply-adds per call */
+    int64_t device_bytes;      /* device memory held by the batch */
+    int64_t graph_launches;    /* graph launches so far (one per hmv_batch_matvec) */
+    int64_t kernels_per_graph; /* kernel launches captured in the graph */
+} hmv_batch_info;
+
+hmv_status hmv_batch_create(int32_t count, const hmv_desc *descs, void *stream, uint64_t wave_bytes,
+                            hmv_batch_t **out);
+/* Load matrix `index` (as hmv_load_matrix). */
+hmv_status hmv_batch_load_matrix(hmv_batch_t *batch, int32_t index, const hmv_vec *h);
+/* xs[i], ys[i]: the blocks of matrix i (all host or all device pointers);
+ * every ys[i].exponent is written.  Synchronous: returns after the results
+ * (and, for host buffers, their copies) are complete. */
+hmv_status hmv_batch_matvec(hmv_batch_t *batch, const hmv_vec *xs, hmv_vec *ys);
+hmv_status hmv_batch_get_info(const hmv_batch_t *batch, hmv_batch_info *out);
+void hmv_batch_free(hmv_batch_t *batch);
+
+/*
  * Scratch-free schoolbook product (no counterpart in the paper: it is an
  * interface for callers, not part of the method).
  *

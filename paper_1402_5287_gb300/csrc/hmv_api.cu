@@ -116,6 +116,16 @@ __global__ void k_validate(const uint32_t *limbs, int rows, int L32, int b, int3
         atomicExch(dstat, DEV_BADINPUT);
 }
 
+}  // namespace
+
+cudaError_t launch_validate(hmv_plan_s *p, const uint32_t *limbs, int rows) {
+    k_validate<<<ceil_div(rows, 128), 128, 0, p->stream>>>(limbs, rows, p->L32, p->b, p->dstat);
+    p->launches_total++;
+    return cudaGetLastError();
+}
+
+namespace {
+
 void timing_mark(hmv_plan_s *p, int k) {
     if (p->timing) cudaEventRecord(p->ev[k], p->stream);
 }
@@ -161,6 +171,14 @@ void hmv_free(hmv_plan_t *p) {
 }
 
 hmv_status hmv_plan(const hmv_desc *desc, void *stream, hmv_plan_t **out) {
+    return hmv::plan_create(desc, stream, false, out);
+}
+
+}  // extern "C"
+
+namespace hmv {
+
+hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch, hmv_plan_s **out) {
     if (!desc || !out) return HMV_EINVAL;
     const hmv_desc &d = *desc;
     if (d.n < 1 || d.b < 1 || d.b > kMaxBits || d.nrhs < 1) return HMV_EINVAL;
@@ -183,6 +201,11 @@ hmv_status hmv_plan(const hmv_desc *desc, void *stream, hmv_plan_t **out) {
     p->method = (d.method == HMV_AUTO) ? HMV_KARATSUBA : d.method;
     p->L32 = (d.b + 31) / 32;
     p->timing = (d.flags & HMV_FLAG_TIMING) != 0;
+    p->external_scratch = external_scratch;
+    if (external_scratch && (p->method != HMV_KARATSUBA || (d.flags & HMV_FLAG_SIMT_LEAF))) {
+        delete p;
+        return HMV_EUNSUPPORTED;
+    }
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -229,19 +252,25 @@ hmv_status hmv_plan(const hmv_desc *desc, void *stream, hmv_plan_t **out) {
             if (g(cudaMalloc(&lg.d_size, lg.size.size() * sizeof(int))))
                 g(cudaMemcpy(lg.d_size, lg.size.data(), lg.size.size() * sizeof(int), cudaMemcpyHostToDevice));
         }
-        g(dalloc(p, &p->a_lvl[0], maxA));
-        if (L > 0) g(dalloc(p, &p->a_lvl[1], maxA));
-        g(dalloc(p, &p->x_lvl[0], maxX));
-        if (L > 0) g(dalloc(p, &p->x_lvl[1], maxX));
         const bool simt = (d.flags & HMV_FLAG_SIMT_LEAF) != 0;
-        if (!simt) {
-            g(dalloc(p, &p->hrev, static_cast<size_t>(leaf.nodes) * p->RA * p->Dp));
-            g(dalloc(p, &p->xg, static_cast<size_t>(leaf.nodes) * p->RX * 8 * (p->Dp + 8)));
+        p->bytes_a_lvl = maxA;
+        p->bytes_x_lvl = maxX;
+        p->bytes_post = maxPost * sizeof(int32_t);
+        p->elems_xg = static_cast<size_t>(leaf.nodes) * p->RX * 8 * (p->Dp + 8);
+        p->bytes_dig = static_cast<size_t>(leaf.nodes) * p->MT * TM * p->Uo;
+        p->elems_carry = static_cast<size_t>(leaf.nodes) * p->MT * TM * p->NUB;
+        if (!simt) g(dalloc(p, &p->hrev, static_cast<size_t>(leaf.nodes) * p->RA * p->Dp));
+        if (!external_scratch) {
+            g(dalloc(p, &p->a_lvl[0], maxA));
+            if (L > 0) g(dalloc(p, &p->a_lvl[1], maxA));
+            g(dalloc(p, &p->x_lvl[0], maxX));
+            if (L > 0) g(dalloc(p, &p->x_lvl[1], maxX));
+            if (!simt) g(dalloc(p, &p->xg, p->elems_xg));
+            g(dalloc(p, &p->leaf_dig, p->bytes_dig));
+            g(dalloc(p, &p->leaf_carry, p->elems_carry));
+            g(dalloc(p, &p->post[0], maxPost));
+            if (L > 0) g(dalloc(p, &p->post[1], maxPost));
         }
-        g(dalloc(p, &p->leaf_dig, static_cast<size_t>(leaf.nodes) * p->MT * TM * p->Uo));
-        g(dalloc(p, &p->leaf_carry, static_cast<size_t>(leaf.nodes) * p->MT * TM * p->NUB));
-        g(dalloc(p, &p->post[0], maxPost));
-        if (L > 0) g(dalloc(p, &p->post[1], maxPost));
         // tiles: leaf-major (neighbouring CTAs share a leaf's operands in L2),
         // within a leaf the longest K loops first
         std::vector<Tile> tiles;
@@ -254,7 +283,7 @@ hmv_status hmv_plan(const hmv_desc *desc, void *stream, hmv_plan_t **out) {
                     const int u0 = ub * TN;
                     const int s_min = std::max(0, u0 - (p->Dl - 1)), s_max = std::min(p->Dl - 1, u0 + TN - 1);
                     const int nsb = (s_max >= s_min) ? s_max / KS - s_min / KS + 1 : 0;
-                    lt.push_back(Tile{lf, mt * TM, ub, nsb * m});
+                    lt.push_back(Tile{lf, mt * TM, ub, nsb * m, 0});
                     issued += static_cast<double>(TM) * TN * KS * nsb * m;
                 }
             std::stable_sort(lt.begin(), lt.end(), [](const Tile &a, const Tile &b2) { return a.cost > b2.cost; });
@@ -264,9 +293,11 @@ hmv_status hmv_plan(const hmv_desc *desc, void *stream, hmv_plan_t **out) {
         p->leaf_macs = macs;
         p->leaf_macs_issued = issued;
         p->ntiles = static_cast<int>(tiles.size());
+        p->tiles = tiles;
         if (g(dalloc(p, &p->d_tiles, tiles.size())))
             g(cudaMemcpy(p->d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice));
-        if (!simt && g.err == cudaSuccess) g(make_tensor_maps(p));
+        if (!simt) g(dalloc(p, &p->d_prob, 1));
+        if (!simt && !external_scratch && g.err == cudaSuccess) g(make_tensor_maps(p));
     }
     const int hlen0 = (d.kind == HMV_CIRCULANT) ? n : 2 * n - 1;
     if (p->method == HMV_FFT64) {
@@ -308,6 +339,10 @@ hmv_status hmv_plan(const hmv_desc *desc, void *stream, hmv_plan_t **out) {
     *out = p;
     return HMV_OK;
 }
+
+}  // namespace hmv
+
+extern "C" {
 
 hmv_status hmv_load_matrix(hmv_plan_t *p, const hmv_vec *h) {
     if (!p) return HMV_EINVAL;

@@ -1,0 +1,357 @@
+// Batched exact Hankel products: many matrices of different order and
+// precision, each with a block of right-hand sides (as in block Lanczos),
+// advanced together by one CUDA graph launch per call.
+//
+// Every (matrix, right-hand side) pair is one leaf problem of Algorithm 1
+// (Beliakov, arXiv:1402.5287, Sec. 3).  The leaf products of all pairs of a
+// wave run in ONE persistent tensor-core launch over a combined tile list
+// (each tile names its problem; each problem carries its own TMA
+// descriptors); the level kernels of all pairs run around it.  Pairs are
+// grouped into waves so that the per-pair leaf operands and outputs of one
+// wave fit a memory budget; level and post-pass buffers are shared by all
+// pairs, since they are used one pair after another.  The whole sequence
+// (every wave, every pair, the rounding of every matrix) is captured once in
+// a CUDA graph and replayed by each hmv_batch_matvec.
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "hmv_internal.h"
+
+namespace hmv {
+namespace {
+
+struct Pair {
+    int plan, rhs, wave;
+    uint16_t *xg;
+    uint8_t *dig;
+    int32_t *carry;
+};
+
+}  // namespace
+}  // namespace hmv
+
+struct hmv_batch_s {
+    cudaStream_t stream = nullptr;
+    std::vector<hmv_plan_s *> plans;
+    std::vector<hmv::Pair> pairs;
+    int nwaves = 0;
+    std::vector<hmv::LeafProblem *> d_probs;  // per wave
+    std::vector<hmv::Tile *> d_tiles;         // per wave
+    std::vector<int> ntiles;                  // per wave
+    std::vector<void *> allocations;
+    int8_t *a_lvl[2] = {nullptr, nullptr}, *x_lvl[2] = {nullptr, nullptr};
+    int32_t *post[2] = {nullptr, nullptr};
+    int64_t device_bytes = 0;
+    cudaGraphExec_t exec = nullptr;
+    bool own_stream = false;
+    double leaf_macs = 0;
+    int64_t tiles_total = 0;
+    int64_t graph_launches = 0, kernels_per_launch = 0;
+    int num_sms = 0;
+};
+
+namespace hmv {
+namespace {
+
+cudaError_t balloc(hmv_batch_s *B, void **ptr, size_t bytes) {
+    *ptr = nullptr;
+    cudaError_t e = cudaMalloc(ptr, bytes ? bytes : 1);
+    if (e == cudaSuccess) {
+        B->allocations.push_back(*ptr);
+        B->device_bytes += static_cast<int64_t>(bytes);
+    }
+    return e;
+}
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+size_t pair_bytes(const hmv_plan_s *p) {
+    return align256(p->elems_xg * 2) + align256(p->bytes_dig) + align256(p->elems_carry * 4);
+}
+
+// Point a plan's working buffers at a pair's and the batch's shared ones.
+void bind(hmv_batch_s *B, hmv_plan_s *p, const Pair &pr) {
+    p->x_lvl[0] = B->x_lvl[0];
+    p->x_lvl[1] = B->x_lvl[1];
+    p->post[0] = B->post[0];
+    p->post[1] = B->post[1];
+    p->xg = pr.xg;
+    p->leaf_dig = pr.dig;
+    p->leaf_carry = pr.carry;
+}
+
+// The whole batched product, issued on B->stream (captured into a graph).
+cudaError_t issue(hmv_batch_s *B) {
+    cudaError_t e = cudaSuccess;
+    int64_t kernels = 0;
+    for (hmv_plan_s *p : B->plans) {
+        if (e == cudaSuccess) e = cudaMemsetAsync(p->dstat, 0, 8 * sizeof(int32_t), B->stream);
+        if (e == cudaSuccess) e = launch_validate(p, p->x_limbs_d, p->n * p->nrhs);
+        ++kernels;
+    }
+    for (int w = 0; w < B->nwaves && e == cudaSuccess; ++w) {
+        for (const Pair &pr : B->pairs) {
+            if (pr.wave != w || e != cudaSuccess) continue;
+            hmv_plan_s *p = B->plans[pr.plan];
+            bind(B, p, pr);
+            const uint32_t *xr = p->x_limbs_d + static_cast<size_t>(pr.rhs) * p->n * p->L32;
+            const uint8_t *xnr = p->x_neg_d + static_cast<size_t>(pr.rhs) * p->n;
+            e = launch_encode(p, xr, xnr, p->n, 0, p->x_lvl[0]);
+            for (int l = 0; l < p->L && e == cudaSuccess; ++l)
+                e = launch_prepass(p, l, false, p->x_lvl[l % 2], p->x_lvl[(l + 1) % 2]);
+            if (e == cudaSuccess) e = launch_pack_vector(p, p->x_lvl[p->L % 2]);
+            kernels += 2 + p->L;
+        }
+        if (e == cudaSuccess)
+            e = launch_leaf_tc_multi(B->d_probs[w], B->d_tiles[w], B->ntiles[w], B->plans[0]->dstat, B->stream,
+                                     B->num_sms);
+        ++kernels;
+        for (const Pair &pr : B->pairs) {
+            if (pr.wave != w || e != cudaSuccess) continue;
+            hmv_plan_s *p = B->plans[pr.plan];
+            bind(B, p, pr);
+            e = launch_leaf_normalize(p, p->post[p->L % 2]);
+            for (int l = p->L - 1; l >= 0 && e == cudaSuccess; --l)
+                e = launch_postpass(p, l, p->post[(l + 1) % 2], p->post[l % 2]);
+            if (e == cudaSuccess) e = launch_final_normalize(p, p->post[0], pr.rhs);
+            kernels += 2 + p->L;
+        }
+    }
+    for (hmv_plan_s *p : B->plans) {
+        if (e == cudaSuccess)
+            e = launch_round(p, p->n * p->nrhs, p->e_h + p->batch_x_exponent, p->y_limbs_d, p->y_neg_d);
+        kernels += 2;
+    }
+    B->kernels_per_launch = kernels;
+    return e;
+}
+
+}  // namespace
+}  // namespace hmv
+
+using namespace hmv;
+
+extern "C" {
+
+void hmv_batch_free(hmv_batch_t *B) {
+    if (!B) return;
+    if (B->stream) cudaStreamSynchronize(B->stream);
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    for (hmv_plan_s *p : B->plans) {
+        // the batch owns the shared buffers these point to
+        p->x_lvl[0] = p->x_lvl[1] = nullptr;
+        p->a_lvl[0] = p->a_lvl[1] = nullptr;
+        p->post[0] = p->post[1] = nullptr;
+        p->xg = nullptr;
+        p->leaf_dig = nullptr;
+        p->leaf_carry = nullptr;
+        hmv_free(p);
+    }
+    for (void *a : B->allocations) cudaFree(a);
+    if (B->own_stream) cudaStreamDestroy(B->stream);
+    delete B;
+}
+
+hmv_status hmv_batch_create(int32_t count, const hmv_desc *descs, void *stream, uint64_t wave_bytes,
+                            hmv_batch_t **out) {
+    if (count < 1 || !descs || !out) return HMV_EINVAL;
+    for (int i = 0; i < count; ++i) {
+        const hmv_desc &d = descs[i];
+        if (d.method != HMV_AUTO && d.method != HMV_KARATSUBA) return HMV_EUNSUPPORTED;
+        if (d.flags & HMV_FLAG_SIMT_LEAF) return HMV_EUNSUPPORTED;
+    }
+    hmv_batch_s *B = new (std::nothrow) hmv_batch_s();
+    if (!B) return HMV_ENOMEM;
+    B->stream = static_cast<cudaStream_t>(stream);
+    if (!B->stream) {  // the legacy default stream cannot be captured into a graph
+        if (cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete B;
+            return HMV_ECUDA;
+        }
+        B->own_stream = true;
+    }
+    for (int i = 0; i < count; ++i) {
+        hmv_desc d = descs[i];
+        d.flags &= ~HMV_FLAG_TIMING;  // no host-side event syncs inside a graph
+        hmv_plan_s *p = nullptr;
+        hmv_status st = plan_create(&d, B->stream, true, &p);
+        if (st != HMV_OK) { hmv_batch_free(B); return st; }
+        B->plans.push_back(p);
+    }
+    B->num_sms = B->plans[0]->num_sms;
+    cudaError_t e = cudaSuccess;
+    size_t mA = 0, mX = 0, mP = 0;
+    for (hmv_plan_s *p : B->plans) {
+        mA = std::max(mA, p->bytes_a_lvl);
+        mX = std::max(mX, p->bytes_x_lvl);
+        mP = std::max(mP, p->bytes_post);
+    }
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = balloc(B, reinterpret_cast<void **>(&B->a_lvl[k]), mA);
+        if (e == cudaSuccess) e = balloc(B, reinterpret_cast<void **>(&B->x_lvl[k]), mX);
+        if (e == cudaSuccess) e = balloc(B, reinterpret_cast<void **>(&B->post[k]), mP);
+    }
+    // waves: pairs in order, a new wave when the budget would be exceeded
+    std::vector<size_t> wave_size;
+    for (int i = 0; i < count; ++i) {
+        hmv_plan_s *p = B->plans[i];
+        p->a_lvl[0] = B->a_lvl[0];
+        p->a_lvl[1] = B->a_lvl[1];
+        for (int r = 0; r < p->nrhs; ++r) {
+            const size_t sz = pair_bytes(p);
+            if (wave_size.empty() || (wave_size.back() + sz > wave_bytes && wave_size.back() > 0))
+                wave_size.push_back(0);
+            B->pairs.push_back(Pair{i, r, static_cast<int>(wave_size.size()) - 1, nullptr, nullptr, nullptr});
+            wave_size.back() += sz;
+        }
+    }
+    B->nwaves = static_cast<int>(wave_size.size());
+    const size_t arena_bytes = *std::max_element(wave_size.begin(), wave_size.end());
+    uint8_t *arena = nullptr;
+    if (e == cudaSuccess) e = balloc(B, reinterpret_cast<void **>(&arena), arena_bytes);
+    // carve each wave's pairs out of the arena (waves reuse it in turn)
+    std::vector<size_t> off(B->nwaves, 0);
+    for (Pair &pr : B->pairs) {
+        hmv_plan_s *p = B->plans[pr.plan];
+        uint8_t *base = arena + off[pr.wave];
+        pr.xg = reinterpret_cast<uint16_t *>(base);
+        base += align256(p->elems_xg * 2);
+        pr.dig = base;
+        base += align256(p->bytes_dig);
+        pr.carry = reinterpret_cast<int32_t *>(base);
+        off[pr.wave] += pair_bytes(p);
+    }
+    // per wave: leaf problems (own TMA descriptors) and the combined tile list
+    for (int w = 0; w < B->nwaves && e == cudaSuccess; ++w) {
+        std::vector<LeafProblem> probs;
+        std::vector<Tile> tiles;
+        for (const Pair &pr : B->pairs) {
+            if (pr.wave != w) continue;
+            hmv_plan_s *p = B->plans[pr.plan];
+            LeafProblem lp;
+            memset(&lp, 0, sizeof lp);
+            e = encode_tensor_map_A(p, &lp.mapA);
+            if (e == cudaSuccess) e = encode_tensor_map_B(p, pr.xg, &lp.mapB);
+            if (e != cudaSuccess) break;
+            bind(B, p, pr);
+            fill_leaf_problem(p, lp);
+            const int idx = static_cast<int>(probs.size());
+            probs.push_back(lp);
+            for (Tile t : p->tiles) {
+                t.prob = idx;
+                tiles.push_back(t);
+            }
+            B->leaf_macs += p->leaf_macs;
+        }
+        if (e != cudaSuccess) break;
+        LeafProblem *dp = nullptr;
+        Tile *dt = nullptr;
+        e = balloc(B, reinterpret_cast<void **>(&dp), probs.size() * sizeof(LeafProblem));
+        if (e == cudaSuccess) e = cudaMemcpy(dp, probs.data(), probs.size() * sizeof(LeafProblem), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = balloc(B, reinterpret_cast<void **>(&dt), tiles.size() * sizeof(Tile));
+        if (e == cudaSuccess) e = cudaMemcpy(dt, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice);
+        B->d_probs.push_back(dp);
+        B->d_tiles.push_back(dt);
+        B->ntiles.push_back(static_cast<int>(tiles.size()));
+        B->tiles_total += static_cast<int64_t>(tiles.size());
+    }
+    if (e != cudaSuccess) {
+        hmv_status st = (e == cudaErrorMemoryAllocation) ? HMV_ENOMEM : HMV_ECUDA;
+        hmv_batch_free(B);
+        cudaGetLastError();
+        return st;
+    }
+    *out = B;
+    return HMV_OK;
+}
+
+hmv_status hmv_batch_load_matrix(hmv_batch_t *B, int32_t index, const hmv_vec *h) {
+    if (!B || index < 0 || index >= static_cast<int32_t>(B->plans.size())) return HMV_EINVAL;
+    if (B->exec) {  // the captured rounding holds the old matrix exponent
+        cudaStreamSynchronize(B->stream);
+        cudaGraphExecDestroy(B->exec);
+        B->exec = nullptr;
+    }
+    return hmv_load_matrix(B->plans[index], h);
+}
+
+hmv_status hmv_batch_matvec(hmv_batch_t *B, const hmv_vec *xs, hmv_vec *ys) {
+    if (!B || !xs || !ys) return HMV_EINVAL;
+    const int count = static_cast<int>(B->plans.size());
+    for (int i = 0; i < count; ++i) {
+        hmv_plan_s *p = B->plans[i];
+        const hmv_vec &x = xs[i], &y = ys[i];
+        if (!p->loaded) return HMV_ENOTLOADED;
+        if (x.len != p->n || x.nrhs != p->nrhs || x.b != p->b || !x.limbs || !x.neg || x.reserved ||
+            y.len != p->n || y.nrhs != p->nrhs || y.b != p->b || !y.limbs || !y.neg || y.reserved ||
+            x.on_device != y.on_device || (x.on_device != 0 && x.on_device != 1))
+            return HMV_EINVAL;
+    }
+    cudaError_t e = leaf_tc_prepare();
+    // inputs into the buffers the graph reads
+    for (int i = 0; i < count && e == cudaSuccess; ++i) {
+        hmv_plan_s *p = B->plans[i];
+        const size_t rows = static_cast<size_t>(p->n) * p->nrhs;
+        const cudaMemcpyKind k = xs[i].on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        e = cudaMemcpyAsync(p->x_limbs_d, xs[i].limbs, rows * p->L32 * sizeof(uint32_t), k, B->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(p->x_neg_d, xs[i].neg, rows, k, B->stream);
+        if (p->batch_x_exponent != xs[i].exponent && B->exec) {
+            // the exponent is a kernel argument of the captured rounding: capture again
+            cudaGraphExecDestroy(B->exec);
+            B->exec = nullptr;
+        }
+        p->batch_x_exponent = xs[i].exponent;
+    }
+    if (e == cudaSuccess && !B->exec) {
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t ie = issue(B);
+            e = cudaStreamEndCapture(B->stream, &graph);
+            if (e == cudaSuccess) e = ie;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&B->exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+    }
+    if (e == cudaSuccess) e = cudaGraphLaunch(B->exec, B->stream);
+    if (e == cudaSuccess) B->graph_launches++;
+    std::vector<int32_t> st(8 * count, 0);
+    for (int i = 0; i < count && e == cudaSuccess; ++i)
+        e = cudaMemcpyAsync(&st[8 * i], B->plans[i]->dstat, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, B->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(B->stream);
+    if (e != cudaSuccess) { cudaGetLastError(); return e == cudaErrorMemoryAllocation ? HMV_ENOMEM : HMV_ECUDA; }
+    for (int i = 0; i < count; ++i) {
+        if (st[8 * i] == DEV_BADINPUT) return HMV_EINVAL;
+        if (st[8 * i] == DEV_TIMEOUT) return HMV_ETIMEOUT;
+        if (st[8 * i] != DEV_OK) return HMV_ECUDA;
+    }
+    for (int i = 0; i < count && e == cudaSuccess; ++i) {
+        hmv_plan_s *p = B->plans[i];
+        const size_t rows = static_cast<size_t>(p->n) * p->nrhs;
+        const cudaMemcpyKind k = ys[i].on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        e = cudaMemcpyAsync(ys[i].limbs, p->y_limbs_d, rows * p->L32 * sizeof(uint32_t), k, B->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ys[i].neg, p->y_neg_d, rows, k, B->stream);
+        ys[i].exponent = st[8 * i + 3];
+        p->matvecs++;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(B->stream);
+    return e == cudaSuccess ? HMV_OK : HMV_ECUDA;
+}
+
+hmv_status hmv_batch_get_info(const hmv_batch_t *B, hmv_batch_info *o) {
+    if (!B || !o) return HMV_EINVAL;
+    memset(o, 0, sizeof *o);
+    o->matrices = static_cast<int32_t>(B->plans.size());
+    o->pairs = static_cast<int32_t>(B->pairs.size());
+    o->waves = B->nwaves;
+    o->leaf_tiles = B->tiles_total;
+    o->leaf_macs = B->leaf_macs;
+    o->device_bytes = B->device_bytes;
+    for (const hmv_plan_s *p : B->plans) o->device_bytes += p->device_bytes;
+    o->graph_launches = B->graph_launches;
+    o->kernels_per_graph = B->kernels_per_launch;
+    return HMV_OK;
+}
+
+}  // extern "C"

@@ -40,7 +40,19 @@ struct LevelGeom {
 };
 
 struct Tile {
-    int leaf, i0, ub, cost;
+    int leaf, i0, ub, cost, prob;  // prob: index into the launch's LeafProblem array
+};
+
+// Everything the leaf kernel needs to know about one leaf problem (one
+// matrix tree with one right-hand side).  Lives in device memory; the TMA
+// descriptors are read from here by the kernel.
+struct __align__(64) LeafProblem {
+    CUtensorMap mapA;   // bf16 Hankel slabs of the matrix leaves
+    CUtensorMap mapB;   // bf16 shifted copies of the vector leaves
+    const int *size;    // leaf orders
+    uint8_t *dig;       // [leaf][MT*TM][Uo] output digits
+    int32_t *carry;     // [leaf][MT*TM][NUB] output block carries
+    int Dl, Dp, Uo, NUB, MT, pad_[3];
 };
 
 }  // namespace hmv
@@ -88,6 +100,11 @@ struct hmv_plan_s {
 
     CUtensorMap mapA, mapB;
     bool maps_ok = false;
+    hmv::LeafProblem *d_prob = nullptr;      // this plan's leaf problem (one entry)
+    bool external_scratch = false;           // level, post and leaf buffers owned by a batch
+    std::vector<hmv::Tile> tiles;            // host copy of the tile list
+    int batch_x_exponent = 0;                // exponent of the x block last given to a batch
+    size_t bytes_a_lvl = 0, bytes_x_lvl = 0, bytes_post = 0, elems_xg = 0, bytes_dig = 0, elems_carry = 0;
     int num_sms = 0;
     int64_t device_bytes = 0;
     std::vector<void *> allocations;
@@ -119,7 +136,16 @@ cudaError_t launch_encode(hmv_plan_s *p, const uint32_t *limbs, const uint8_t *n
 cudaError_t launch_prepass(hmv_plan_s *p, int level, bool matrix_side, const int8_t *in, int8_t *out);
 cudaError_t launch_pack_matrix(hmv_plan_s *p, const int8_t *leaf_digits);
 cudaError_t launch_pack_vector(hmv_plan_s *p, const int8_t *leaf_digits);
+hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch, hmv_plan_s **out);
+cudaError_t launch_validate(hmv_plan_s *p, const uint32_t *limbs, int rows);
+cudaError_t launch_colsum_normalize(hmv_plan_s *p, int rhs);
+cudaError_t leaf_tc_prepare();
 cudaError_t launch_leaf_tc(hmv_plan_s *p);
+cudaError_t launch_leaf_tc_multi(const LeafProblem *probs, const Tile *tiles, int ntiles, int32_t *dstat,
+                                 cudaStream_t stream, int num_sms);
+cudaError_t encode_tensor_map_A(hmv_plan_s *p, CUtensorMap *map);
+cudaError_t encode_tensor_map_B(hmv_plan_s *p, uint16_t *xg, CUtensorMap *map);
+void fill_leaf_problem(hmv_plan_s *p, LeafProblem &lp);
 cudaError_t launch_leaf_simt(hmv_plan_s *p, const int8_t *a_leaf, const int8_t *x_leaf);
 cudaError_t launch_leaf_normalize(hmv_plan_s *p, int32_t *out);
 cudaError_t launch_postpass(hmv_plan_s *p, int level, const int32_t *in, int32_t *out);

@@ -25,6 +25,8 @@
 // let the MMAs of one window overlap the epilogue of the previous one.
 // Every wait is bounded; on a timeout the kernel records DEV_TIMEOUT, drains
 // and frees its TMEM, and returns.
+#include <cstring>
+
 #include "hmv_internal.h"
 #include "tc_ptx.cuh"
 
@@ -53,11 +55,17 @@ struct __align__(1024) Smem {
 };
 
 struct TileInfo {
-    int leaf, i0, ub, u0, m, sb_lo, sb_hi, njc, Q;
+    const LeafProblem *pr;
+    int leaf, i0, ub, u0, m, sb_lo, sb_hi, njc, Q, Dl, Dp;
 };
 
-__device__ __forceinline__ TileInfo decode(const Tile &t, const int *size, int Dl) {
+__device__ __forceinline__ TileInfo decode(const Tile &t, const LeafProblem *probs) {
     TileInfo ti;
+    ti.pr = probs + t.prob;
+    const int Dl = ti.pr->Dl;
+    ti.Dl = Dl;
+    ti.Dp = ti.pr->Dp;
+    const int *size = ti.pr->size;
     ti.leaf = t.leaf;
     ti.i0 = t.i0;
     ti.ub = t.ub;
@@ -78,9 +86,7 @@ __device__ __forceinline__ void fail(Smem &sm, int32_t *dstat) {
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
-    k_leaf_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-              const Tile *__restrict__ tiles, int ntiles, const int *__restrict__ size, int Dl, int Dp,
-              uint8_t *__restrict__ dig, int32_t *__restrict__ carry, int MT, int Uo, int NUB, int32_t *dstat) {
+    k_leaf_tc(const LeafProblem *__restrict__ probs, const Tile *__restrict__ tiles, int ntiles, int32_t *dstat) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -104,11 +110,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (warp == kProducerWarp) {
         if (lane == 0) {
-            tma_prefetch_desc(&mapA);
-            tma_prefetch_desc(&mapB);
             int as = 0, aph = 0, bs = 0, bph = 0;
             for (int t = blockIdx.x; t < ntiles && !sm.abort; t += gridDim.x) {
-                const TileInfo ti = decode(tiles[t], size, Dl);
+                const TileInfo ti = decode(tiles[t], probs);
+                const CUtensorMap *mapA = &ti.pr->mapA;
+                const CUtensorMap *mapB = &ti.pr->mapB;
+                const int Dp = ti.Dp;
                 for (int sb = ti.sb_lo; sb <= ti.sb_hi && !sm.abort; ++sb) {
                     const int s_lo = sb * KS;
                     for (int jc = 0; jc < ti.njc && !sm.abort; ++jc) {
@@ -116,12 +123,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const int jn = min(JC, ti.m - j0);
                         if (!mbar_wait(&sm.a_empty[as], aph ^ 1, kTimeoutNs)) { fail(sm, dstat); break; }
                         mbar_arrive_expect_tx(&sm.a_full[as], A_BYTES);
-                        tma_load_4d(sm.a[as], &mapA, &sm.a_full[as], 0, ti.i0 + j0, (Dp - s_lo - KS) / 8, ti.leaf);
+                        tma_load_4d(sm.a[as], mapA, &sm.a_full[as], 0, ti.i0 + j0, (Dp - s_lo - KS) / 8, ti.leaf);
                         if (++as == A_STAGES) { as = 0; aph ^= 1; }
                         for (int jj = 0; jj < jn; ++jj) {
                             if (!mbar_wait(&sm.b_empty[bs], bph ^ 1, kTimeoutNs)) { fail(sm, dstat); break; }
                             mbar_arrive_expect_tx(&sm.b_full[bs], B_BYTES);
-                            tma_load_5d(sm.b[bs], &mapB, &sm.b_full[bs], 0, 0, (ti.u0 - s_lo - KS) / 8 + 1,
+                            tma_load_5d(sm.b[bs], mapB, &sm.b_full[bs], 0, 0, (ti.u0 - s_lo - KS) / 8 + 1,
                                         j0 + jj, ti.leaf);
                             if (++bs == B_STAGES) { bs = 0; bph ^= 1; }
                         }
@@ -136,7 +143,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t a_base0 = smem_u32(sm.a[0]);
             const uint32_t b_base0 = smem_u32(sm.b[0]);
             for (int t = blockIdx.x; t < ntiles && !sm.abort; t += gridDim.x) {
-                const TileInfo ti = decode(tiles[t], size, Dl);
+                const TileInfo ti = decode(tiles[t], probs);
                 int q = 0;
                 uint32_t acc_flag = 0;
                 for (int sb = ti.sb_lo; sb <= ti.sb_hi && !sm.abort; ++sb) {
@@ -185,7 +192,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         int ab = 0;
         int eph[2] = {0, 0};
         for (int t = blockIdx.x; t < ntiles && !sm.abort; t += gridDim.x) {
-            const TileInfo ti = decode(tiles[t], size, Dl);
+            const TileInfo ti = decode(tiles[t], probs);
             const int G = (ti.Q + FLUSH_J - 1) / FLUSH_J;
             uint32_t st[TN / 4];
 #pragma unroll
@@ -225,12 +232,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!ok) break;
             const int row = ti.i0 + lq * 32 + lane;
             if (row < ti.m) {
-                const size_t r = static_cast<size_t>(ti.leaf) * MT * TM + row;
-                uint4 *o = reinterpret_cast<uint4 *>(dig + r * Uo + ti.u0);
+                const LeafProblem &pr = *ti.pr;
+                const size_t r = static_cast<size_t>(ti.leaf) * pr.MT * TM + row;
+                uint4 *o = reinterpret_cast<uint4 *>(pr.dig + r * pr.Uo + ti.u0);
 #pragma unroll
                 for (int w = 0; w < TN / 16; ++w)
                     o[w] = make_uint4(st[4 * w], st[4 * w + 1], st[4 * w + 2], st[4 * w + 3]);
-                carry[r * NUB + ti.ub] = co;
+                pr.carry[r * pr.NUB + ti.ub] = co;
             }
         }
     }
@@ -251,22 +259,32 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 size_t leaf_tc_smem_bytes() { return sizeof(Smem) + 1024; }
 
-cudaError_t launch_leaf_tc(hmv_plan_s *p) {
+cudaError_t leaf_tc_prepare() {
     static bool attr_set = false;
-    const size_t smem = sizeof(Smem);
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_leaf_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(smem));
+                                             static_cast<int>(sizeof(Smem)));
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    const int grid = std::min(p->ntiles, p->num_sms);
+    return cudaSuccess;
+}
+
+cudaError_t launch_leaf_tc_multi(const LeafProblem *probs, const Tile *tiles, int ntiles, int32_t *dstat,
+                                 cudaStream_t stream, int num_sms) {
+    const size_t smem = sizeof(Smem);
+    cudaError_t pe = leaf_tc_prepare();
+    if (pe != cudaSuccess) return pe;
+    const int grid = std::min(ntiles, num_sms);
     if (grid <= 0) return cudaSuccess;
-    k_leaf_tc<<<grid, kThreads, smem, p->stream>>>(p->mapA, p->mapB, p->d_tiles, p->ntiles, p->lv[p->L].d_size, p->Dl,
-                                                   p->Dp, p->leaf_dig, p->leaf_carry, p->MT, p->Uo, p->NUB, p->dstat);
+    k_leaf_tc<<<grid, kThreads, smem, stream>>>(probs, tiles, ntiles, dstat);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_tc(hmv_plan_s *p) {
     p->launches_leaf++;
     p->launches_total++;
-    return cudaGetLastError();
+    return launch_leaf_tc_multi(p->d_prob, p->d_tiles, p->ntiles, p->dstat, p->stream, p->num_sms);
 }
 
 // ------------------------------------------------------------------ tensor maps
@@ -287,36 +305,61 @@ EncodeTiledFn get_encode() {
 }
 }  // namespace
 
-cudaError_t make_tensor_maps(hmv_plan_s *p) {
+cudaError_t encode_tensor_map_A(hmv_plan_s *p, CUtensorMap *map) {
     EncodeTiledFn enc = get_encode();
     if (!enc) return cudaErrorNotSupported;
     const int nleaves = p->lv[p->L].nodes;
     const cuuint64_t chunks = static_cast<cuuint64_t>(p->Dp / 8);
-    // A: hrev[leaf][chunk][RA][8] bf16 (packed): (8 digits, rows, chunks, leaf)
-    {
-        cuuint64_t dims[4] = {8, static_cast<cuuint64_t>(p->RA), chunks, static_cast<cuuint64_t>(nleaves)};
-        cuuint64_t strides[3] = {16, static_cast<cuuint64_t>(p->RA) * 16, chunks * p->RA * 16};
-        cuuint32_t box[4] = {8, static_cast<cuuint32_t>(AR), static_cast<cuuint32_t>(KS / 8), 1};
-        cuuint32_t es[4] = {1, 1, 1, 1};
-        CUresult r = enc(&p->mapA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, p->hrev, dims, strides, box, es,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    }
-    // B: xg[leaf][RX][chunk][8][8] bf16 (packed): (8 digits, 8 copies, chunks, j, leaf)
-    {
-        const cuuint64_t xc = chunks + 1;
-        cuuint64_t dims[5] = {8, 8, xc, static_cast<cuuint64_t>(p->RX), static_cast<cuuint64_t>(nleaves)};
-        cuuint64_t strides[4] = {16, 128, xc * 128, static_cast<cuuint64_t>(p->RX) * xc * 128};
-        cuuint32_t box[5] = {8, 8, static_cast<cuuint32_t>(NE), 1, 1};
-        cuuint32_t es[5] = {1, 1, 1, 1, 1};
-        CUresult r = enc(&p->mapB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, p->xg, dims, strides, box, es,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    }
-    p->maps_ok = true;
-    return cudaSuccess;
+    // hrev[leaf][chunk][RA][8] bf16 (packed): (8 digits, rows, chunks, leaf)
+    cuuint64_t dims[4] = {8, static_cast<cuuint64_t>(p->RA), chunks, static_cast<cuuint64_t>(nleaves)};
+    cuuint64_t strides[3] = {16, static_cast<cuuint64_t>(p->RA) * 16, chunks * p->RA * 16};
+    cuuint32_t box[4] = {8, static_cast<cuuint32_t>(AR), static_cast<cuuint32_t>(KS / 8), 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, p->hrev, dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t encode_tensor_map_B(hmv_plan_s *p, uint16_t *xg, CUtensorMap *map) {
+    EncodeTiledFn enc = get_encode();
+    if (!enc) return cudaErrorNotSupported;
+    const int nleaves = p->lv[p->L].nodes;
+    // xg[leaf][RX][chunk][8][8] bf16 (packed): (8 digits, 8 copies, chunks, j, leaf)
+    const cuuint64_t xc = static_cast<cuuint64_t>(p->Dp / 8 + 1);
+    cuuint64_t dims[5] = {8, 8, xc, static_cast<cuuint64_t>(p->RX), static_cast<cuuint64_t>(nleaves)};
+    cuuint64_t strides[4] = {16, 128, xc * 128, static_cast<cuuint64_t>(p->RX) * xc * 128};
+    cuuint32_t box[5] = {8, 8, static_cast<cuuint32_t>(NE), 1, 1};
+    cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, xg, dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+void fill_leaf_problem(hmv_plan_s *p, LeafProblem &lp) {
+    lp.size = p->lv[p->L].d_size;
+    lp.dig = p->leaf_dig;
+    lp.carry = p->leaf_carry;
+    lp.Dl = p->Dl;
+    lp.Dp = p->Dp;
+    lp.Uo = p->Uo;
+    lp.NUB = p->NUB;
+    lp.MT = p->MT;
+}
+
+cudaError_t make_tensor_maps(hmv_plan_s *p) {
+    LeafProblem lp;
+    memset(&lp, 0, sizeof lp);
+    cudaError_t e = encode_tensor_map_A(p, &lp.mapA);
+    if (e == cudaSuccess) e = encode_tensor_map_B(p, p->xg, &lp.mapB);
+    if (e != cudaSuccess) return e;
+    p->mapA = lp.mapA;
+    p->mapB = lp.mapB;
+    fill_leaf_problem(p, lp);
+    e = cudaMemcpy(p->d_prob, &lp, sizeof lp, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) p->maps_ok = true;
+    return e;
 }
 
 }  // namespace hmv

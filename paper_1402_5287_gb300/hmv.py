@@ -20,7 +20,8 @@ STATUS = {0: "HMV_OK", 1: "HMV_EINVAL", 2: "HMV_ENOMEM", 3: "HMV_ECUDA", 4: "HMV
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libhmv.so")
 EXPORTS = ["hmv_plan", "hmv_load_matrix", "hmv_matvec", "hmv_free", "hmv_get_stats", "hmv_reset_stats",
-           "hmv_status_string", "hmv_version", "hmv_schoolbook_noalloc"]
+           "hmv_status_string", "hmv_version", "hmv_schoolbook_noalloc", "hmv_batch_create",
+           "hmv_batch_load_matrix", "hmv_batch_matvec", "hmv_batch_get_info", "hmv_batch_free"]
 NOALLOC_SCRATCH_BYTES = 4 << 20
 
 
@@ -54,6 +55,13 @@ class Stats(ctypes.Structure):
                 ("fft_fallbacks", ctypes.c_int64), ("ms_fft", ctypes.c_double)]
 
 
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("matrices", ctypes.c_int32), ("pairs", ctypes.c_int32), ("waves", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("leaf_tiles", ctypes.c_int64), ("leaf_macs", ctypes.c_double),
+                ("device_bytes", ctypes.c_int64), ("graph_launches", ctypes.c_int64),
+                ("kernels_per_graph", ctypes.c_int64)]
+
+
 _lib = None
 
 
@@ -85,6 +93,16 @@ def load_library(path: str = LIB_PATH):
         lib.hmv_schoolbook_noalloc.argtypes = [i32, i32, i32, vp, vp, i32, vp, vp, i32, vp, vp,
                                                ctypes.POINTER(i32), vp]
         lib.hmv_schoolbook_noalloc.restype = ctypes.c_int
+        lib.hmv_batch_create.argtypes = [i32, ctypes.POINTER(Desc), vp, ctypes.c_uint64, ctypes.POINTER(vp)]
+        lib.hmv_batch_create.restype = ctypes.c_int
+        lib.hmv_batch_load_matrix.argtypes = [vp, i32, ctypes.POINTER(Vec)]
+        lib.hmv_batch_load_matrix.restype = ctypes.c_int
+        lib.hmv_batch_matvec.argtypes = [vp, ctypes.POINTER(Vec), ctypes.POINTER(Vec)]
+        lib.hmv_batch_matvec.restype = ctypes.c_int
+        lib.hmv_batch_get_info.argtypes = [vp, ctypes.POINTER(BatchInfo)]
+        lib.hmv_batch_get_info.restype = ctypes.c_int
+        lib.hmv_batch_free.argtypes = [vp]
+        lib.hmv_batch_free.restype = None
         _lib = lib
     return _lib
 
@@ -185,3 +203,77 @@ class Plan:
 
     def reset_stats(self):
         _check(self.lib.hmv_reset_stats(self.handle), "hmv_reset_stats")
+
+
+class Batch:
+    """Many matrices (each with a block of right-hand sides) advanced by one
+    CUDA graph launch per call (hmv_batch_*)."""
+
+    def __init__(self, problems, stream=None, wave_bytes: int = 32 << 30):
+        """problems: list of dicts with n, b and optionally kind, nrhs, levels."""
+        self.lib = load_library()
+        self.problems = [{"kind": HANKEL, "nrhs": 1, "levels": -1, **pr} for pr in problems]
+        arr = (Desc * len(problems))()
+        for i, pr in enumerate(self.problems):
+            arr[i] = Desc(pr["n"], pr["b"], pr["nrhs"], pr["kind"], AUTO, pr["levels"], 0, 0)
+        handle = ctypes.c_void_p()
+        s = ctypes.c_void_p(0 if stream is None else int(stream))
+        _check(self.lib.hmv_batch_create(len(problems), arr, s, wave_bytes, ctypes.byref(handle)), "hmv_batch_create")
+        self.handle = handle
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self.lib.hmv_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def load_matrix(self, index: int, h: FixedVec):
+        vec, keep = _host_vec(h)
+        _check(self.lib.hmv_batch_load_matrix(self.handle, index, ctypes.byref(vec)), "hmv_batch_load_matrix")
+        del keep
+
+    def matvec(self, xs):
+        """Host blocks in, host blocks out."""
+        n = len(self.problems)
+        xa = (Vec * n)()
+        ya = (Vec * n)()
+        keep, outs = [], []
+        for i, (pr, x) in enumerate(zip(self.problems, xs)):
+            v, k = _host_vec(x, pr["nrhs"])
+            xa[i] = v
+            keep.append(k)
+            rows = pr["n"] * pr["nrhs"]
+            yl = np.zeros((rows, (pr["b"] + 31) // 32), dtype=np.uint32)
+            yn = np.zeros(rows, dtype=np.uint8)
+            outs.append((yl, yn))
+            ya[i] = Vec(pr["n"], pr["nrhs"], pr["b"], 0, yl.ctypes.data, yn.ctypes.data, 0, 0)
+        _check(self.lib.hmv_batch_matvec(self.handle, xa, ya), "hmv_batch_matvec")
+        return [FixedVec(yl, yn, pr["b"], int(ya[i].exponent)) for i, ((yl, yn), pr) in
+                enumerate(zip(outs, self.problems))]
+
+    def matvec_device(self, xs_ptrs, ys_ptrs, x_exponents):
+        """Device blocks: xs_ptrs/ys_ptrs are lists of (limbs, neg) pointers; returns exponents."""
+        n = len(self.problems)
+        xa = (Vec * n)()
+        ya = (Vec * n)()
+        for i, pr in enumerate(self.problems):
+            xa[i] = Vec(pr["n"], pr["nrhs"], pr["b"], x_exponents[i], xs_ptrs[i][0], xs_ptrs[i][1], 1, 0)
+            ya[i] = Vec(pr["n"], pr["nrhs"], pr["b"], 0, ys_ptrs[i][0], ys_ptrs[i][1], 1, 0)
+        _check(self.lib.hmv_batch_matvec(self.handle, xa, ya), "hmv_batch_matvec")
+        return [int(ya[i].exponent) for i in range(n)]
+
+    def info(self) -> dict:
+        s = BatchInfo()
+        _check(self.lib.hmv_batch_get_info(self.handle, ctypes.byref(s)), "hmv_batch_get_info")
+        return {name: getattr(s, name) for name, _ in BatchInfo._fields_}
