@@ -94,6 +94,10 @@ template <typename T>
 cudaError_t dalloc(hmv_plan_s *p, T **ptr, size_t count) {
     *ptr = nullptr;
     if (count == 0) count = 1;
+    if (p->dry_run) {  // footprint query: count the bytes, allocate nothing
+        p->device_bytes += static_cast<int64_t>(count * sizeof(T));
+        return cudaSuccess;
+    }
     void *v = nullptr;
     cudaError_t e = cudaMalloc(&v, count * sizeof(T));
     if (e != cudaSuccess) return e;
@@ -171,14 +175,25 @@ void hmv_free(hmv_plan_t *p) {
 }
 
 hmv_status hmv_plan(const hmv_desc *desc, void *stream, hmv_plan_t **out) {
-    return hmv::plan_create(desc, stream, false, out);
+    return hmv::plan_create(desc, stream, false, out, false);
+}
+
+hmv_status hmv_plan_bytes(const hmv_desc *desc, uint64_t *bytes) {
+    if (!bytes) return HMV_EINVAL;
+    hmv_plan_s *p = nullptr;
+    hmv_status st = hmv::plan_create(desc, nullptr, false, &p, true);
+    if (st != HMV_OK) return st;
+    *bytes = static_cast<uint64_t>(p->device_bytes);
+    delete p;
+    return HMV_OK;
 }
 
 }  // extern "C"
 
 namespace hmv {
 
-hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch, hmv_plan_s **out) {
+hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch, hmv_plan_s **out,
+                       bool dry_run) {
     if (!desc || !out) return HMV_EINVAL;
     const hmv_desc &d = *desc;
     if (d.n < 1 || d.b < 1 || d.b > kMaxBits || d.nrhs < 1) return HMV_EINVAL;
@@ -206,12 +221,19 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
         delete p;
         return HMV_EUNSUPPORTED;
     }
+    p->dry_run = dry_run;
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (ce != cudaSuccess) { delete p; return from_cuda(ce); }
-    if (p->timing)
+    if (ce != cudaSuccess) {
+        if (!dry_run) { delete p; return from_cuda(ce); }
+        cudaGetLastError();
+        p->num_sms = 152;  // footprint query without a device: GB300's SM count
+    }
+    if (p->timing && !dry_run)
         for (auto &e : p->ev) cudaEventCreate(&e);
+    else
+        p->timing = false;
 
     Guard g;
     const int n = d.n;
@@ -249,6 +271,7 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
             maxPost = std::max(maxPost, static_cast<size_t>(lg.nodes) * lg.rowsX * p->Wo);
         }
         for (auto &lg : p->lv) {
+            if (dry_run) { p->device_bytes += static_cast<int64_t>(lg.size.size() * sizeof(int)); continue; }
             if (g(cudaMalloc(&lg.d_size, lg.size.size() * sizeof(int))))
                 g(cudaMemcpy(lg.d_size, lg.size.data(), lg.size.size() * sizeof(int), cudaMemcpyHostToDevice));
         }
@@ -294,10 +317,10 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
         p->leaf_macs_issued = issued;
         p->ntiles = static_cast<int>(tiles.size());
         p->tiles = tiles;
-        if (g(dalloc(p, &p->d_tiles, tiles.size())))
+        if (g(dalloc(p, &p->d_tiles, tiles.size())) && !dry_run)
             g(cudaMemcpy(p->d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice));
         if (!simt) g(dalloc(p, &p->d_prob, 1));
-        if (!simt && !external_scratch && g.err == cudaSuccess) g(make_tensor_maps(p));
+        if (!simt && !external_scratch && !dry_run && g.err == cudaSuccess) g(make_tensor_maps(p));
     }
     const int hlen0 = (d.kind == HMV_CIRCULANT) ? n : 2 * n - 1;
     if (p->method == HMV_FFT64) {
@@ -316,7 +339,7 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
         g(dalloc(p, &p->fft_tw, static_cast<size_t>(p->fft_N / 2)));
         g(dalloc(p, &p->fft_sumsq, 2));
         g(dalloc(p, &p->fft_maxdist, 1));
-        if (g.err == cudaSuccess) g(fft_init(p));
+        if (g.err == cudaSuccess && !dry_run) g(fft_init(p));
     }
     const int hlen = (d.kind == HMV_CIRCULANT) ? n : 2 * n - 1;
     const size_t rows = static_cast<size_t>(n) * d.nrhs;

@@ -355,3 +355,105 @@ hmv_status hmv_batch_get_info(const hmv_batch_t *B, hmv_batch_info *o) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// One matvec for each of several independent plans, with every leaf product
+// in one persistent tensor-core launch: the step of a continuous-batching
+// server, whose set of plans changes from one call to the next.
+extern "C" hmv_status hmv_matvec_many(int32_t count, hmv_plan_t *const *plans, const hmv_vec *xs, hmv_vec *ys) {
+    if (count < 1 || !plans || !xs || !ys) return HMV_EINVAL;
+    for (int i = 0; i < count; ++i) {
+        hmv_plan_s *p = plans[i];
+        if (!p) return HMV_EINVAL;
+        for (int k = 0; k < i; ++k)
+            if (plans[k] == p) return HMV_EINVAL;  // a plan holds one product at a time
+        if (p->method != HMV_KARATSUBA || !p->hrev || p->external_scratch || p->nrhs != 1) return HMV_EUNSUPPORTED;
+        if (!p->loaded) return HMV_ENOTLOADED;
+        const hmv_vec &x = xs[i], &y = ys[i];
+        if (x.len != p->n || x.nrhs != 1 || x.b != p->b || !x.limbs || !x.neg || x.reserved ||
+            y.len != p->n || y.nrhs != 1 || y.b != p->b || !y.limbs || !y.neg || y.reserved ||
+            x.on_device != y.on_device || (x.on_device != 0 && x.on_device != 1))
+            return HMV_EINVAL;
+    }
+    cudaStream_t s = plans[0]->stream;
+    std::vector<cudaStream_t> saved(count);
+    for (int i = 0; i < count; ++i) {
+        saved[i] = plans[i]->stream;
+        plans[i]->stream = s;
+    }
+    cudaError_t e = leaf_tc_prepare();
+    std::vector<LeafProblem> probs;
+    std::vector<Tile> tiles;
+    for (int i = 0; i < count && e == cudaSuccess; ++i) {
+        hmv_plan_s *p = plans[i];
+        const uint32_t *xl = xs[i].limbs;
+        const uint8_t *xn = xs[i].neg;
+        if (!xs[i].on_device) {
+            e = cudaMemcpyAsync(p->x_limbs_d, xl, static_cast<size_t>(p->n) * p->L32 * sizeof(uint32_t),
+                                cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(p->x_neg_d, xn, p->n, cudaMemcpyHostToDevice, s);
+            xl = p->x_limbs_d;
+            xn = p->x_neg_d;
+        }
+        if (e == cudaSuccess) e = cudaMemsetAsync(p->dstat, 0, 8 * sizeof(int32_t), s);
+        if (e == cudaSuccess) e = launch_validate(p, xl, p->n);
+        if (e == cudaSuccess) e = launch_encode(p, xl, xn, p->n, 0, p->x_lvl[0]);
+        for (int l = 0; l < p->L && e == cudaSuccess; ++l)
+            e = launch_prepass(p, l, false, p->x_lvl[l % 2], p->x_lvl[(l + 1) % 2]);
+        if (e == cudaSuccess) e = launch_pack_vector(p, p->x_lvl[p->L % 2]);
+        const int idx = static_cast<int>(probs.size());
+        probs.push_back(p->hprob);
+        for (Tile t : p->tiles) {
+            t.prob = idx;
+            tiles.push_back(t);
+        }
+    }
+    LeafProblem *dp = nullptr;
+    Tile *dt = nullptr;
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&dp), probs.size() * sizeof(LeafProblem), s);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&dt), tiles.size() * sizeof(Tile), s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dp, probs.data(), probs.size() * sizeof(LeafProblem), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dt, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        e = launch_leaf_tc_multi(dp, dt, static_cast<int>(tiles.size()), plans[0]->dstat, s, plans[0]->num_sms);
+        plans[0]->launches_leaf++;
+    }
+    if (dp) cudaFreeAsync(dp, s);
+    if (dt) cudaFreeAsync(dt, s);
+    for (int i = 0; i < count && e == cudaSuccess; ++i) {
+        hmv_plan_s *p = plans[i];
+        e = launch_leaf_normalize(p, p->post[p->L % 2]);
+        for (int l = p->L - 1; l >= 0 && e == cudaSuccess; --l)
+            e = launch_postpass(p, l, p->post[(l + 1) % 2], p->post[l % 2]);
+        if (e == cudaSuccess) e = launch_final_normalize(p, p->post[0], 0);
+        uint32_t *yl = ys[i].on_device ? ys[i].limbs : p->y_limbs_d;
+        uint8_t *yn = ys[i].on_device ? ys[i].neg : p->y_neg_d;
+        if (e == cudaSuccess) e = launch_round(p, p->n, p->e_h + xs[i].exponent, yl, yn);
+    }
+    std::vector<int32_t> st(8 * count, 0);
+    for (int i = 0; i < count && e == cudaSuccess; ++i)
+        e = cudaMemcpyAsync(&st[8 * i], plans[i]->dstat, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    cudaError_t se = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = se;
+    for (int i = 0; i < count; ++i) plans[i]->stream = saved[i];
+    if (e != cudaSuccess) { cudaGetLastError(); return e == cudaErrorMemoryAllocation ? HMV_ENOMEM : HMV_ECUDA; }
+    // a leaf-kernel timeout is recorded in the first plan's status word
+    for (int i = 0; i < count; ++i) {
+        if (st[8 * i] == DEV_BADINPUT) return HMV_EINVAL;
+        if (st[8 * i] == DEV_TIMEOUT) return HMV_ETIMEOUT;
+        if (st[8 * i] != DEV_OK) return HMV_ECUDA;
+    }
+    for (int i = 0; i < count && e == cudaSuccess; ++i) {
+        hmv_plan_s *p = plans[i];
+        if (!ys[i].on_device) {
+            e = cudaMemcpyAsync(ys[i].limbs, p->y_limbs_d, static_cast<size_t>(p->n) * p->L32 * sizeof(uint32_t),
+                                cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(ys[i].neg, p->y_neg_d, p->n, cudaMemcpyDeviceToHost, s);
+        }
+        ys[i].exponent = st[8 * i + 3];
+        p->matvecs++;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? HMV_OK : HMV_ECUDA;
+}

@@ -104,6 +104,8 @@ struct hmv_plan_s {
     bool external_scratch = false;           // level, post and leaf buffers owned by a batch
     std::vector<hmv::Tile> tiles;            // host copy of the tile list
     int batch_x_exponent = 0;                // exponent of the x block last given to a batch
+    bool dry_run = false;                    // footprint query: nothing is allocated
+    hmv::LeafProblem hprob;                  // host copy of *d_prob
     size_t bytes_a_lvl = 0, bytes_x_lvl = 0, bytes_post = 0, elems_xg = 0, bytes_dig = 0, elems_carry = 0;
     int num_sms = 0;
     int64_t device_bytes = 0;
@@ -136,7 +138,8 @@ cudaError_t launch_encode(hmv_plan_s *p, const uint32_t *limbs, const uint8_t *n
 cudaError_t launch_prepass(hmv_plan_s *p, int level, bool matrix_side, const int8_t *in, int8_t *out);
 cudaError_t launch_pack_matrix(hmv_plan_s *p, const int8_t *leaf_digits);
 cudaError_t launch_pack_vector(hmv_plan_s *p, const int8_t *leaf_digits);
-hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch, hmv_plan_s **out);
+hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch, hmv_plan_s **out,
+                       bool dry_run = false);
 cudaError_t launch_validate(hmv_plan_s *p, const uint32_t *limbs, int rows);
 cudaError_t launch_colsum_normalize(hmv_plan_s *p, int rhs);
 cudaError_t leaf_tc_prepare();

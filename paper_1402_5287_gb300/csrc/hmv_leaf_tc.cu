@@ -357,6 +357,7 @@ cudaError_t make_tensor_maps(hmv_plan_s *p) {
     p->mapA = lp.mapA;
     p->mapB = lp.mapB;
     fill_leaf_problem(p, lp);
+    p->hprob = lp;
     e = cudaMemcpy(p->d_prob, &lp, sizeof lp, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) p->maps_ok = true;
     return e;

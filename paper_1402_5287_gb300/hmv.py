@@ -21,7 +21,8 @@ STATUS = {0: "HMV_OK", 1: "HMV_EINVAL", 2: "HMV_ENOMEM", 3: "HMV_ECUDA", 4: "HMV
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libhmv.so")
 EXPORTS = ["hmv_plan", "hmv_load_matrix", "hmv_matvec", "hmv_free", "hmv_get_stats", "hmv_reset_stats",
            "hmv_status_string", "hmv_version", "hmv_schoolbook_noalloc", "hmv_batch_create",
-           "hmv_batch_load_matrix", "hmv_batch_matvec", "hmv_batch_get_info", "hmv_batch_free"]
+           "hmv_batch_load_matrix", "hmv_batch_matvec", "hmv_batch_get_info", "hmv_batch_free",
+           "hmv_plan_bytes", "hmv_matvec_many"]
 NOALLOC_SCRATCH_BYTES = 4 << 20
 
 
@@ -103,6 +104,10 @@ def load_library(path: str = LIB_PATH):
         lib.hmv_batch_get_info.restype = ctypes.c_int
         lib.hmv_batch_free.argtypes = [vp]
         lib.hmv_batch_free.restype = None
+        lib.hmv_plan_bytes.argtypes = [ctypes.POINTER(Desc), ctypes.POINTER(ctypes.c_uint64)]
+        lib.hmv_plan_bytes.restype = ctypes.c_int
+        lib.hmv_matvec_many.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(Vec), ctypes.POINTER(Vec)]
+        lib.hmv_matvec_many.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -133,6 +138,30 @@ def schoolbook_noalloc(n: int, b: int, kind: int, h_ptrs: tuple[int, int], h_exp
                                       x_exponent, y_ptrs[0], y_ptrs[1], ctypes.byref(e), s),
            "hmv_schoolbook_noalloc")
     return int(e.value)
+
+
+def plan_bytes(n: int, b: int, kind: int = HANKEL, method: int = AUTO, levels: int = -1, nrhs: int = 1,
+               flags: int = 0, piece_bits: int = 0) -> int:
+    """Device bytes hmv_plan would allocate (no allocation, no GPU needed)."""
+    lib = load_library()
+    d = Desc(n, b, nrhs, kind, method, levels, flags, piece_bits)
+    out = ctypes.c_uint64(0)
+    _check(lib.hmv_plan_bytes(ctypes.byref(d), ctypes.byref(out)), "hmv_plan_bytes")
+    return int(out.value)
+
+
+def matvec_many_device(plans, xs_ptrs, ys_ptrs, x_exponents) -> list[int]:
+    """hmv_matvec_many on device pointers: one product per plan in one step."""
+    lib = load_library()
+    n = len(plans)
+    pa = (ctypes.c_void_p * n)(*[p.handle.value for p in plans])
+    xa = (Vec * n)()
+    ya = (Vec * n)()
+    for i, p in enumerate(plans):
+        xa[i] = Vec(p.n, 1, p.b, x_exponents[i], xs_ptrs[i][0], xs_ptrs[i][1], 1, 0)
+        ya[i] = Vec(p.n, 1, p.b, 0, ys_ptrs[i][0], ys_ptrs[i][1], 1, 0)
+    _check(lib.hmv_matvec_many(n, pa, xa, ya), "hmv_matvec_many")
+    return [int(ya[i].exponent) for i in range(n)]
 
 
 class Plan:

@@ -1,0 +1,144 @@
+"""Continuous-batching server for Lanczos-style clients of the exact Hankel
+product.
+
+Each request brings a matrix (its h) and a start vector and asks for a chain
+of products v_{k+1} = A v_k against its device-resident A, the access
+pattern of a Krylov/Lanczos driver (the eigenvalue and orthogonalisation
+stages are the client's, not this engine's).  The server
+
+  * admits arrived requests in order while the device memory its plans need
+    (hmv_plan_bytes, computed without allocating) fits the budget,
+  * keeps every admitted matrix resident (one plan per request),
+  * runs steps: each step advances EVERY active request by one product with
+    one hmv_matvec_many call, whose leaf products share one persistent
+    tensor-core launch; requests that arrive during a step join at the next
+    one, finished requests leave and free their memory (continuous batching),
+  * records, per product, the time from when it became ready (arrival for
+    the first, the previous product's completion otherwise) to completion.
+
+Every step is exact, so each request's results are identical whether it runs
+alone or in any mix.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import hmv
+from .inputs import FixedVec
+
+
+@dataclass
+class Request:
+    rid: int
+    n: int
+    b: int
+    h: FixedVec
+    x0: FixedVec
+    matvecs: int
+    arrival: float = 0.0
+    kind: int = hmv.HANKEL
+    # filled by the server
+    admitted: float | None = None
+    finished: float | None = None
+    latencies: list = field(default_factory=list)
+    result: FixedVec | None = None
+    footprint: int = 0
+
+
+def percentile(values, q):
+    if not values:
+        return None
+    return float(np.percentile(np.asarray(values, dtype=np.float64), q))
+
+
+class Server:
+    def __init__(self, memory_budget: int, max_active: int = 128, device: int = 0, clock=time.perf_counter):
+        import torch
+        self.torch = torch
+        self.dev = torch.device("cuda", device)
+        self.stream = torch.cuda.Stream(device=self.dev)
+        self.budget = memory_budget
+        self.max_active = max_active
+        self.clock = clock
+
+    def _admit(self, r: Request, now: float):
+        torch = self.torch
+        r.plan = hmv.Plan(r.n, r.b, kind=r.kind, stream=self.stream.cuda_stream)
+        r.plan.load_matrix(r.h)
+        with torch.cuda.stream(self.stream):
+            r.xl = torch.from_numpy(r.x0.limbs.view(np.int32)).to(self.dev)
+            r.xn = torch.from_numpy(r.x0.neg).to(self.dev)
+            r.yl = torch.empty_like(r.xl)
+            r.yn = torch.empty_like(r.xn)
+        r.x_exp = r.x0.exponent
+        r.done = 0
+        r.admitted = now
+
+    def _finish(self, r: Request, now: float):
+        self.stream.synchronize()
+        r.result = FixedVec(r.xl.cpu().numpy().view(np.uint32), r.xn.cpu().numpy(), r.b, r.x_exp)
+        r.plan.close()
+        r.plan = None
+        del r.xl, r.xn, r.yl, r.yn
+        r.finished = now
+
+    def run(self, requests: list[Request]) -> dict:
+        pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
+        for r in pending:
+            r.footprint = hmv.plan_bytes(r.n, r.b, kind=r.kind)
+            if r.footprint > self.budget:
+                raise ValueError(f"request {r.rid} needs {r.footprint} bytes, more than the whole budget")
+        active: list[Request] = []
+        used = 0
+        steps, step_sizes, peak_active, peak_used = 0, [], 0, 0
+        t0 = self.clock()
+        while pending or active:
+            now = self.clock() - t0
+            while pending and pending[0].arrival <= now and len(active) < self.max_active:
+                r = pending[0]
+                if used + r.footprint > self.budget:
+                    break  # in order: wait for memory to free up
+                pending.pop(0)
+                self._admit(r, now)
+                r.ready = r.arrival
+                used += r.footprint
+                active.append(r)
+            peak_active = max(peak_active, len(active))
+            peak_used = max(peak_used, used)
+            if not active:
+                if pending:
+                    time.sleep(max(0.0, min(pending[0].arrival - (self.clock() - t0), 0.05)))
+                continue
+            exps = hmv.matvec_many_device([r.plan for r in active],
+                                          [(r.xl.data_ptr(), r.xn.data_ptr()) for r in active],
+                                          [(r.yl.data_ptr(), r.yn.data_ptr()) for r in active],
+                                          [r.x_exp for r in active])
+            t_end = self.clock() - t0
+            steps += 1
+            step_sizes.append(len(active))
+            still = []
+            for r, e in zip(active, exps):
+                r.latencies.append(t_end - r.ready)
+                r.ready = t_end
+                r.xl, r.yl = r.yl, r.xl
+                r.xn, r.yn = r.yn, r.xn
+                r.x_exp = e
+                r.done += 1
+                if r.done == r.matvecs:
+                    self._finish(r, t_end)
+                    used -= r.footprint
+                else:
+                    still.append(r)
+            active = still
+        total = self.clock() - t0
+        lat = [v for r in requests for v in r.latencies]
+        req_lat = [r.finished - r.arrival for r in requests]
+        nmv = sum(r.matvecs for r in requests)
+        return {"matvecs": nmv, "seconds": total, "matvecs_per_s": nmv / total if total > 0 else None,
+                "p50_ms": percentile(lat, 50) * 1e3, "p99_ms": percentile(lat, 99) * 1e3,
+                "request_p50_s": percentile(req_lat, 50), "request_p99_s": percentile(req_lat, 99),
+                "steps": steps, "mean_step_batch": float(np.mean(step_sizes)) if step_sizes else 0.0,
+                "peak_active": peak_active, "peak_bytes": peak_used}

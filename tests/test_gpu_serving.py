@@ -1,0 +1,81 @@
+"""Continuous batching: hmv_matvec_many equals separate products, and every
+served request's result is the same alone and in any mix (exact)."""
+import numpy as np
+import pytest
+
+import paper_1402_5287_gb300 as pkg
+from paper_1402_5287_gb300 import hmv
+from paper_1402_5287_gb300.inputs import FixedVec, uniform_vec
+
+from test_gpu_parity import assert_same
+
+pytestmark = pytest.mark.gpu
+
+SPECS = [(40, 256, hmv.HANKEL), (150, 1024, hmv.TOEPLITZ), (64, 2048, hmv.HANKEL), (9, 100, hmv.CIRCULANT),
+         (200, 700, hmv.HANKEL)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    pkg.build()
+    hmv.load_library()
+
+
+def make(seed):
+    out = []
+    for i, (n, b, kind) in enumerate(SPECS):
+        hlen = n if kind == hmv.CIRCULANT else 2 * n - 1
+        out.append((n, b, kind, uniform_vec(seed + i, 0, hlen, b, 1), uniform_vec(seed + i, 1, n, b, 0)))
+    return out
+
+
+def test_matvec_many_equals_separate_products():
+    torch = pytest.importorskip("torch")
+    probs = make(300)
+    stream = torch.cuda.Stream()
+    plans, xs, ys, want = [], [], [], []
+    for n, b, kind, h, x in probs:
+        with hmv.Plan(n, b, kind=kind) as p1:
+            p1.load_matrix(h)
+            want.append(p1.matvec(x))
+        p = hmv.Plan(n, b, kind=kind, stream=stream.cuda_stream)
+        p.load_matrix(h)
+        plans.append(p)
+        xs.append((torch.from_numpy(x.limbs.view(np.int32)).cuda(), torch.from_numpy(x.neg).cuda()))
+        ys.append((torch.zeros_like(xs[-1][0]), torch.zeros_like(xs[-1][1])))
+    torch.cuda.synchronize()
+    exps = hmv.matvec_many_device(plans, [(a.data_ptr(), b2.data_ptr()) for a, b2 in xs],
+                                  [(a.data_ptr(), b2.data_ptr()) for a, b2 in ys], [x.exponent for *_, x in probs])
+    for (n, b, kind, h, x), (yl, yn), e, w in zip(probs, ys, exps, want):
+        assert_same(FixedVec(yl.cpu().numpy().view(np.uint32), yn.cpu().numpy(), b, e), w)
+    for p in plans:
+        p.close()
+
+
+def chain_alone(n, b, kind, h, x, k):
+    with hmv.Plan(n, b, kind=kind) as p:
+        p.load_matrix(h)
+        for _ in range(k):
+            x = p.matvec(x)
+    return x
+
+
+@pytest.mark.parametrize("budget_plans", [100, 2])
+def test_served_results_same_alone_and_in_the_mix(budget_plans):
+    from paper_1402_5287_gb300.serving import Request, Server
+    probs = make(400)
+    k = 3
+    # together: all at once, so that every step carries several requests
+    reqs = [Request(i, n, b, h, x, k, arrival=0.0, kind=kind) for i, (n, b, kind, h, x) in enumerate(probs)]
+    biggest = max(hmv.plan_bytes(n, b, kind=kind) for n, b, kind, _, _ in probs)
+    srv = Server(memory_budget=budget_plans * biggest)
+    stats = srv.run(reqs)
+    assert stats["matvecs"] == k * len(probs)
+    assert stats["peak_bytes"] <= budget_plans * biggest
+    if budget_plans == 2:
+        assert stats["peak_active"] < len(probs)  # admission waited for memory
+    else:
+        assert stats["mean_step_batch"] > 1.0  # products of different requests shared steps
+    for r, (n, b, kind, h, x) in zip(reqs, probs):
+        assert len(r.latencies) == k
+        assert_same(r.result, chain_alone(n, b, kind, h, x, k))
