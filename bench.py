@@ -21,6 +21,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -368,6 +370,102 @@ def load_workload(args):
     return n, b, uniform_vec(BASE_SEED + 2, 0, 2 * n - 1, b, 0), uniform_vec(BASE_SEED + 2, 1, n, b, 0)
 
 
+def batched_workload(count=64, nrhs=8):
+    """64 Hankel matrices, n ~ U[32, 2048], b from {4096, 16384, 33220}, 8
+    right-hand sides each, entries uniform in (-1, 1)."""
+    import random
+
+    from paper_1402_5287_gb300.inputs import BASE_SEED, uniform_vec
+    rng = random.Random(BASE_SEED + 3)
+    probs = []
+    for i in range(count):
+        n = rng.randint(32, 2048)
+        b = rng.choice([4096, 16384, 33220])
+        h = uniform_vec(BASE_SEED + 3, 2 * i, 2 * n - 1, b, 0)
+        x = uniform_vec(BASE_SEED + 3, 2 * i + 1, n * nrhs, b, 0)
+        probs.append((n, b, h, x))
+    return probs
+
+
+def run_batched(args):
+    import torch
+
+    import paper_1402_5287_gb300 as pkg
+    from paper_1402_5287_gb300 import hmv
+    pkg.build()
+    nrhs = 8
+    probs = batched_workload(64, nrhs)
+    specs = [dict(n=n, b=b, nrhs=nrhs) for n, b, _, _ in probs]
+    stream = torch.cuda.Stream()
+    bt = hmv.Batch(specs, stream=stream.cuda_stream, wave_bytes=args.wave_gb << 30)
+    for i, (_, _, h, _) in enumerate(probs):
+        bt.load_matrix(i, h)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    xs, ys = [], []
+    for n, b, _, x in probs:
+        xs.append((torch.from_numpy(x.limbs.view(np.int32)).to(dev), torch.from_numpy(x.neg).to(dev)))
+        ys.append((torch.empty_like(xs[-1][0]), torch.empty_like(xs[-1][1])))
+    xp = [(a.data_ptr(), c.data_ptr()) for a, c in xs]
+    yp = [(a.data_ptr(), c.data_ptr()) for a, c in ys]
+    ex = [x.exponent for *_, x in probs]
+    torch.cuda.synchronize()
+    for _ in range(max(args.warmup, 1)):
+        bt.matvec_device(xp, yp, ex)
+    t0 = time.perf_counter()
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        for _ in range(args.steps):
+            bt.matvec_device(xp, yp, ex)
+    secs = time.perf_counter() - t0
+    info = bt.info()
+    bt.close()
+    mv = 64 * nrhs * args.steps
+    line = {"metric": "batched Hankel matvecs/s (64 matrices x 8 right-hand sides)", "value": mv / secs,
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 1),
+            "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "64 Hankel matrices, n ~ U[32,2048], b in {4096,16384,33220}, 8 RHS each, "
+                                   "uniform fixed-point in (-1,1); one CUDA graph launch per step",
+                       "waves": info["waves"], "pairs": info["pairs"], "leaf_tiles": info["leaf_tiles"],
+                       "kernels_per_graph": info["kernels_per_graph"], "wave_budget_gb": args.wave_gb,
+                       "device_gb": info["device_bytes"] / 1e9},
+            "useful_leaf_tflops": 2 * info["leaf_macs"] * args.steps / secs / 1e12,
+            "graph_launches_per_step": 1, "clocks": clocks.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serving(args):
+    import random
+
+    import torch
+
+    import paper_1402_5287_gb300 as pkg
+    from paper_1402_5287_gb300.inputs import BASE_SEED, uniform_vec
+    from paper_1402_5287_gb300.serving import Request, Server
+    pkg.build()
+    rng = random.Random(BASE_SEED + 4)
+    reqs, t = [], 0.0
+    for i in range(args.requests):
+        t += rng.expovariate(args.rate)
+        n = rng.randint(64, 4096)
+        b = rng.choice([2048, 8192, 33220])
+        reqs.append(Request(i, n, b, uniform_vec(BASE_SEED + 4, 2 * i, 2 * n - 1, b, 0),
+                            uniform_vec(BASE_SEED + 4, 2 * i + 1, n, b, 0), args.matvecs_per_request, arrival=t))
+    srv = Server(memory_budget=args.serve_gb << 30)
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        st = srv.run(reqs)
+    line = {"metric": "served Hankel matvecs/s with p50/p99 matvec latency", "value": st["matvecs_per_s"],
+            "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic", "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+            "config": {"workload": f"{args.requests} requests, Poisson arrivals at {args.rate}/s, n ~ U[64,4096], "
+                                   f"b in {{2048,8192,33220}}, {args.matvecs_per_request} chained matvecs per "
+                                   f"request against a resident A (cap on the 2n of a full Lanczos run)",
+                       "memory_budget_gb": args.serve_gb},
+            "serving": st, "clocks": clocks.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -379,11 +477,23 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="matrix order (profiling runs; default 8000)")
     ap.add_argument("--b", type=int, default=None, help="mantissa bits (profiling runs; default 33220)")
+    ap.add_argument("--workload", choices=["matvec", "batched", "serving"], default="matvec",
+                    help="matvec: the n=8000 metric; batched: 64 matrices x 8 RHS per graph launch; "
+                         "serving: Poisson requests with continuous batching")
+    ap.add_argument("--wave-gb", type=int, default=48, help="batched: device memory per wave")
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--rate", type=float, default=4.0, help="serving: Poisson arrival rate (requests/s)")
+    ap.add_argument("--matvecs-per-request", type=int, default=16)
+    ap.add_argument("--serve-gb", type=int, default=200, help="serving: device memory budget")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_ours(args)
 
 
