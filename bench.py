@@ -201,7 +201,8 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
 
-    plan = hmv.Plan(n, b, method=hmv.AUTO, levels=args.levels, flags=hmv.FLAG_TIMING, stream=stream.cuda_stream)
+    method = {"auto": hmv.AUTO, "karatsuba": hmv.KARATSUBA, "fft64": hmv.FFT64, "schoolbook": hmv.SCHOOLBOOK}[args.method]
+    plan = hmv.Plan(n, b, method=method, levels=args.levels, flags=hmv.FLAG_TIMING, stream=stream.cuda_stream)
     plan.load_matrix(h)
     with torch.cuda.stream(stream):
         xl = torch.from_numpy(x.limbs.view(np.int32)).to(dev)
@@ -249,6 +250,8 @@ def run_ours(args):
     peak_src = "measured sustained bf16 (MEASURED_PEAKS.json)"
     if peak is None:
         peak, peak_src = 1700.0, "fallback sustained bf16"
+
+    traffic = leaf_traffic(st["leaf_tiles"], n, b)
 
     # end to end through the public API: host x in, host y out, copies inside the timed region
     e2e = None
@@ -299,7 +302,7 @@ def run_ours(args):
                    "l2": "working set of several GB per step (inputs larger than L2)",
                    "parallelism": f"{world} independent replica(s), one per GPU"},
         "roofline": {"bound": "tensor", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / peak if peak else None, "traffic": None,
+                     "frac": achieved_tflops / peak if peak else None, "traffic": traffic,
                      "kernel": "k_leaf_tc", "peak_source": peak_src,
                      "flops_per_launch": flops_per_launch, "launch_ms": leaf_ms,
                      "issued_over_useful": st["leaf_macs_issued"] / st["leaf_macs"] if st["leaf_macs"] else None},
@@ -355,6 +358,33 @@ def compare_kernels(hmv, h, x, n, b, stream):
                               "ms_fft_per_matvec": st["ms_fft"] / max(st["fft_matvecs"], 1)})
         plan.close()
     return out
+
+
+LEAF_SOURCES = ["paper_1402_5287_gb300/csrc/hmv_leaf_tc.cu", "paper_1402_5287_gb300/csrc/tc_ptx.cuh",
+                "paper_1402_5287_gb300/csrc/hmv_internal.h"]
+
+
+def leaf_sources_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in LEAF_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def leaf_traffic(tiles, n, b):
+    """DRAM bytes per launch of the leaf kernel from the committed ncu capture
+    (profiles/k_leaf_tc_traffic.json), or None when the capture is for another
+    workload or the kernel has changed since."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "k_leaf_tc_traffic.json")) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("sources_sha256_16") != leaf_sources_hash() or rec.get("n") != n or rec.get("b") != b:
+        return None
+    return rec.get("dram_bytes_per_launch")
 
 
 def load_workload(args):
@@ -473,6 +503,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--levels", type=int, default=-1, help="Karatsuba depth (-1: cost model)")
+    ap.add_argument("--method", choices=["auto", "karatsuba", "fft64", "schoolbook"], default="auto",
+                    help="product method (profiling runs; the metric uses auto = Karatsuba + tcgen05)")
     ap.add_argument("--compare", action="store_true", help="also time the schoolbook comparison kernels")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="matrix order (profiling runs; default 8000)")

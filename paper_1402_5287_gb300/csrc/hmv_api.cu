@@ -320,6 +320,7 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
         if (g(dalloc(p, &p->d_tiles, tiles.size())) && !dry_run)
             g(cudaMemcpy(p->d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice));
         if (!simt) g(dalloc(p, &p->d_prob, 1));
+        if (!simt) g(dalloc(p, &p->d_counter, 1));
         if (!simt && !external_scratch && !dry_run && g.err == cudaSuccess) g(make_tensor_maps(p));
     }
     const int hlen0 = (d.kind == HMV_CIRCULANT) ? n : 2 * n - 1;

@@ -104,8 +104,8 @@ cudaError_t issue(hmv_batch_s *B) {
             kernels += 2 + p->L;
         }
         if (e == cudaSuccess)
-            e = launch_leaf_tc_multi(B->d_probs[w], B->d_tiles[w], B->ntiles[w], B->plans[0]->dstat, B->stream,
-                                     B->num_sms);
+            e = launch_leaf_tc_multi(B->d_probs[w], B->d_tiles[w], B->ntiles[w], B->plans[0]->dstat,
+                                     B->plans[0]->d_counter, B->stream, B->num_sms);
         ++kernels;
         for (const Pair &pr : B->pairs) {
             if (pr.wave != w || e != cudaSuccess) continue;
@@ -416,7 +416,8 @@ extern "C" hmv_status hmv_matvec_many(int32_t count, hmv_plan_t *const *plans, c
         e = cudaMemcpyAsync(dp, probs.data(), probs.size() * sizeof(LeafProblem), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dt, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
-        e = launch_leaf_tc_multi(dp, dt, static_cast<int>(tiles.size()), plans[0]->dstat, s, plans[0]->num_sms);
+        e = launch_leaf_tc_multi(dp, dt, static_cast<int>(tiles.size()), plans[0]->dstat, plans[0]->d_counter, s,
+                                 plans[0]->num_sms);
         plans[0]->launches_leaf++;
     }
     if (dp) cudaFreeAsync(dp, s);

@@ -101,6 +101,7 @@ struct hmv_plan_s {
     CUtensorMap mapA, mapB;
     bool maps_ok = false;
     hmv::LeafProblem *d_prob = nullptr;      // this plan's leaf problem (one entry)
+    int *d_counter = nullptr;                // tile counter of the leaf kernel's dynamic schedule
     bool external_scratch = false;           // level, post and leaf buffers owned by a batch
     std::vector<hmv::Tile> tiles;            // host copy of the tile list
     int batch_x_exponent = 0;                // exponent of the x block last given to a batch
@@ -145,7 +146,7 @@ cudaError_t launch_colsum_normalize(hmv_plan_s *p, int rhs);
 cudaError_t leaf_tc_prepare();
 cudaError_t launch_leaf_tc(hmv_plan_s *p);
 cudaError_t launch_leaf_tc_multi(const LeafProblem *probs, const Tile *tiles, int ntiles, int32_t *dstat,
-                                 cudaStream_t stream, int num_sms);
+                                 int *tile_counter, cudaStream_t stream, int num_sms);
 cudaError_t encode_tensor_map_A(hmv_plan_s *p, CUtensorMap *map);
 cudaError_t encode_tensor_map_B(hmv_plan_s *p, uint16_t *xg, CUtensorMap *map);
 void fill_leaf_problem(hmv_plan_s *p, LeafProblem &lp);

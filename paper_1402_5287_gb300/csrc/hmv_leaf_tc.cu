@@ -21,7 +21,10 @@
 //
 // Warp roles (192 threads): warp 0 issues TMA loads, warp 1 allocates TMEM
 // and one lane issues tcgen05.mma, warps 2-5 run the epilogue on the four
-// TMEM lane quarters.  Two 128x256 fp32 accumulators (all 512 TMEM columns)
+// TMEM lane quarters.  Tiles are handed out in list order from a global
+// counter (the producer takes the next index and passes it to the CTA's
+// consumers through a small shared-memory queue), so the grid works on
+// neighbouring tiles of the same leaves and their operands stay in L2.  Two 128x256 fp32 accumulators (all 512 TMEM columns)
 // let the MMAs of one window overlap the epilogue of the previous one.
 // Every wait is bounded; on a timeout the kernel records DEV_TIMEOUT, drains
 // and frees its TMEM, and returns.
@@ -42,6 +45,8 @@ constexpr uint64_t kTimeoutNs = 2000000000ull;  // 2 s for any single wait
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kIdesc = idesc_bf16_f32(TM, TN);
 constexpr uint32_t kLboA = AR * 16;  // K-direction core-matrix step of the slab
+constexpr int kTileQ = 4;            // tile indices handed from the producer to the consumers
+constexpr int kTileConsumers = 1 + kNumEpiWarps;
 
 struct __align__(1024) Smem {
     uint8_t a[A_STAGES][A_BYTES];
@@ -49,6 +54,8 @@ struct __align__(1024) Smem {
     uint64_t a_full[A_STAGES], a_empty[A_STAGES];
     uint64_t b_full[B_STAGES], b_empty[B_STAGES];
     uint64_t acc_full[2], acc_empty[2];
+    uint64_t tq_full[kTileQ], tq_empty[kTileQ];
+    int tile_q[kTileQ];
     uint64_t drain;
     uint32_t tmem_base;
     volatile int abort;
@@ -86,7 +93,8 @@ __device__ __forceinline__ void fail(Smem &sm, int32_t *dstat) {
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
-    k_leaf_tc(const LeafProblem *__restrict__ probs, const Tile *__restrict__ tiles, int ntiles, int32_t *dstat) {
+    k_leaf_tc(const LeafProblem *__restrict__ probs, const Tile *__restrict__ tiles, int ntiles, int *tile_counter,
+              int32_t *dstat) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -95,6 +103,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int s = 0; s < A_STAGES; ++s) { mbar_init(&sm.a_full[s], 1); mbar_init(&sm.a_empty[s], 1); }
         for (int s = 0; s < B_STAGES; ++s) { mbar_init(&sm.b_full[s], 1); mbar_init(&sm.b_empty[s], 1); }
         for (int s = 0; s < 2; ++s) { mbar_init(&sm.acc_full[s], 1); mbar_init(&sm.acc_empty[s], kNumEpiWarps); }
+        for (int s = 0; s < kTileQ; ++s) { mbar_init(&sm.tq_full[s], 1); mbar_init(&sm.tq_empty[s], kTileConsumers); }
         mbar_init(&sm.drain, 1);
         sm.abort = 0;
         fence_mbar_init();
@@ -111,7 +120,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == kProducerWarp) {
         if (lane == 0) {
             int as = 0, aph = 0, bs = 0, bph = 0;
-            for (int t = blockIdx.x; t < ntiles && !sm.abort; t += gridDim.x) {
+            for (int k = 0; !sm.abort; ++k) {
+                // next tile in list order for the whole grid, handed to this CTA's consumers
+                const int qs = k % kTileQ, qph = (k / kTileQ) & 1;
+                if (!mbar_wait(&sm.tq_empty[qs], qph ^ 1, kTimeoutNs)) { fail(sm, dstat); break; }
+                int t = atomicAdd(tile_counter, 1);
+                if (t >= ntiles) t = -1;
+                sm.tile_q[qs] = t;
+                mbar_arrive(&sm.tq_full[qs]);
+                if (t < 0) break;
                 const TileInfo ti = decode(tiles[t], probs);
                 const CUtensorMap *mapA = &ti.pr->mapA;
                 const CUtensorMap *mapB = &ti.pr->mapB;
@@ -142,7 +159,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             int accph[2] = {0, 0};
             const uint32_t a_base0 = smem_u32(sm.a[0]);
             const uint32_t b_base0 = smem_u32(sm.b[0]);
-            for (int t = blockIdx.x; t < ntiles && !sm.abort; t += gridDim.x) {
+            for (int k = 0; !sm.abort; ++k) {
+                const int qs = k % kTileQ, qph = (k / kTileQ) & 1;
+                if (!mbar_wait(&sm.tq_full[qs], qph, kTimeoutNs)) { fail(sm, dstat); break; }
+                const int t = sm.tile_q[qs];
+                mbar_arrive(&sm.tq_empty[qs]);
+                if (t < 0) break;
                 const TileInfo ti = decode(tiles[t], probs);
                 int q = 0;
                 uint32_t acc_flag = 0;
@@ -191,7 +213,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t lane_addr = tmem + (static_cast<uint32_t>(lq * 32) << 16);
         int ab = 0;
         int eph[2] = {0, 0};
-        for (int t = blockIdx.x; t < ntiles && !sm.abort; t += gridDim.x) {
+        for (int k = 0; !sm.abort; ++k) {
+            const int qs = k % kTileQ, qph = (k / kTileQ) & 1;
+            if (!mbar_wait(&sm.tq_full[qs], qph, kTimeoutNs)) { fail(sm, dstat); break; }
+            const int t = sm.tile_q[qs];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.tq_empty[qs]);
+            if (t < 0) break;
             const TileInfo ti = decode(tiles[t], probs);
             const int G = (ti.Q + FLUSH_J - 1) / FLUSH_J;
             uint32_t st[TN / 4];
@@ -271,20 +299,22 @@ cudaError_t leaf_tc_prepare() {
 }
 
 cudaError_t launch_leaf_tc_multi(const LeafProblem *probs, const Tile *tiles, int ntiles, int32_t *dstat,
-                                 cudaStream_t stream, int num_sms) {
+                                 int *tile_counter, cudaStream_t stream, int num_sms) {
     const size_t smem = sizeof(Smem);
     cudaError_t pe = leaf_tc_prepare();
     if (pe != cudaSuccess) return pe;
     const int grid = std::min(ntiles, num_sms);
     if (grid <= 0) return cudaSuccess;
-    k_leaf_tc<<<grid, kThreads, smem, stream>>>(probs, tiles, ntiles, dstat);
+    cudaError_t me = cudaMemsetAsync(tile_counter, 0, sizeof(int), stream);
+    if (me != cudaSuccess) return me;
+    k_leaf_tc<<<grid, kThreads, smem, stream>>>(probs, tiles, ntiles, tile_counter, dstat);
     return cudaGetLastError();
 }
 
 cudaError_t launch_leaf_tc(hmv_plan_s *p) {
     p->launches_leaf++;
     p->launches_total++;
-    return launch_leaf_tc_multi(p->d_prob, p->d_tiles, p->ntiles, p->dstat, p->stream, p->num_sms);
+    return launch_leaf_tc_multi(p->d_prob, p->d_tiles, p->ntiles, p->dstat, p->d_counter, p->stream, p->num_sms);
 }
 
 // ------------------------------------------------------------------ tensor maps
