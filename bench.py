@@ -202,7 +202,11 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
 
     method = {"auto": hmv.AUTO, "karatsuba": hmv.KARATSUBA, "fft64": hmv.FFT64, "schoolbook": hmv.SCHOOLBOOK}[args.method]
-    plan = hmv.Plan(n, b, method=method, levels=args.levels, flags=hmv.FLAG_TIMING, stream=stream.cuda_stream)
+    split_flag = {-1: 0, 0: 0, 1: hmv.FLAG_DIGIT_SPLIT1, 2: hmv.FLAG_DIGIT_SPLIT2}[args.digit_split]
+    if args.digit_split == 0 and method == hmv.AUTO:
+        method = hmv.KARATSUBA  # no digit split
+    plan = hmv.Plan(n, b, method=method, levels=args.levels, flags=hmv.FLAG_TIMING | split_flag,
+                    stream=stream.cuda_stream)
     plan.load_matrix(h)
     with torch.cuda.stream(stream):
         xl = torch.from_numpy(x.limbs.view(np.int32)).to(dev)
@@ -296,6 +300,7 @@ def run_ours(args):
         "ms_per_step": secs_max / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "n": n, "b": b, "kind": "hankel", "method": "karatsuba+tcgen05",
+                   "digit_split_levels": args.digit_split,
                    "levels": st["levels"], "leaves": st["leaves"], "leaf_rows_max": st["leaf_rows_max"],
                    "digits_per_operand": st["digits"], "leaf_tiles": st["leaf_tiles"],
                    "digit_format": "balanced radix-2^8 digits held exactly in bf16, fp32 windows < 2^24",
@@ -382,7 +387,8 @@ def leaf_traffic(tiles, n, b):
             rec = json.load(f)
     except (OSError, ValueError):
         return None
-    if rec.get("sources_sha256_16") != leaf_sources_hash() or rec.get("n") != n or rec.get("b") != b:
+    if (rec.get("sources_sha256_16") != leaf_sources_hash() or rec.get("n") != n or rec.get("b") != b
+            or rec.get("leaf_tiles") != tiles):
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -503,6 +509,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--levels", type=int, default=-1, help="Karatsuba depth (-1: cost model)")
+    ap.add_argument("--digit-split", type=int, choices=[-1, 0, 1, 2], default=-1,
+                    help="levels of Karatsuba on the mantissas on top of the index recursion (-1: cost model)")
     ap.add_argument("--method", choices=["auto", "karatsuba", "fft64", "schoolbook"], default="auto",
                     help="product method (profiling runs; the metric uses auto = Karatsuba + tcgen05)")
     ap.add_argument("--compare", action="store_true", help="also time the schoolbook comparison kernels")

@@ -58,7 +58,8 @@ typedef enum {
 typedef enum { HMV_HANKEL = 0, HMV_TOEPLITZ = 1, HMV_CIRCULANT = 2 } hmv_kind;
 
 typedef enum {
-    HMV_AUTO = 0,          /* Karatsuba recursion with the cost-model depth */
+    HMV_AUTO = 0,          /* Karatsuba recursion; with levels = -1 and no split flag the
+                              cost model also picks the digit-split depth (0-2) */
     HMV_SCHOOLBOOK = 1,    /* plain schoolbook on 32-bit limbs, CUDA cores */
     HMV_KARATSUBA = 2,     /* Algorithm 1 to the given depth, tensor-core leaves */
     HMV_FFT64 = 3          /* split-FP64 FFT with a proven rounding bound; when the bound
@@ -70,6 +71,10 @@ typedef enum {
 /* flags for hmv_desc.flags */
 #define HMV_FLAG_TIMING 1u     /* record CUDA-event times of each stage (hmv_get_stats) */
 #define HMV_FLAG_SIMT_LEAF 2u  /* leaf products on CUDA cores instead of tensor cores */
+/* Karatsuba splitting of the mantissas themselves (three products of half
+ * the width per level), on top of the index recursion; HMV_AUTO/HMV_KARATSUBA */
+#define HMV_FLAG_DIGIT_SPLIT1 4u  /* one level */
+#define HMV_FLAG_DIGIT_SPLIT2 8u  /* two levels */
 
 typedef struct {
     int32_t n;        /* matrix order, n >= 1 */

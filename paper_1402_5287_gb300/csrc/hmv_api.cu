@@ -79,7 +79,7 @@ double cost_model(int n, int b, int L, int num_sms) {
     for (int ub = 0; ub < NUB; ++ub) {
         const int u0 = ub * TN;
         const int s_min = std::max(0, u0 - (Dl - 1)), s_max = std::min(Dl - 1, u0 + TN - 1);
-        const int nsb = (s_max >= s_min) ? s_max / KS - s_min / KS + 1 : 0;
+        const int nsb = (s_max >= s_min) ? (s_max - s_min / 8 * 8 + KS) / KS : 0;
         for (int s : lv[L].size) ksteps += static_cast<double>(ceil_div(s, TM)) * nsb * s * (KS / 16);
     }
     const double mma_s = ksteps * 128.0 / (static_cast<double>(num_sms) * 1.9e9);
@@ -88,6 +88,42 @@ double cost_model(int n, int b, int L, int num_sms) {
         bytes += static_cast<double>(lv[l].nodes) * lv[l].rowsX * (Dp * 2.0 + (Uo + 8) * 4.0 * 4.0);
     bytes += static_cast<double>(lv[L].nodes) * lv[L].rowsX * Dp * 16.0 * 2.0;
     return mma_s + bytes / 5.0e12;
+}
+
+// Cheapest index depth for (n, b) and its estimated seconds.
+int best_depth(int n, int b, int num_sms, double *cost) {
+    int L = 0;
+    double best = 1e300;
+    for (int t = 0; t <= kMaxLevels; ++t) {
+        if (t > 0 && build_levels(n, t - 1).back().smax <= 2) break;
+        const double c = cost_model(n, b, t, num_sms);
+        if (c < best) { best = c; L = t; }
+    }
+    if (cost) *cost = best;
+    return L;
+}
+
+// Digit-split levels for HMV_AUTO: 3^d products of about b/2^d bits, each
+// at its own best depth, plus the level kernels, which grow by about 3/2
+// per split level (measured: 10.4, 15.2, 22.4 ms at n = 8000, b = 33220
+// for d = 0, 1, 2, i.e. about 3.9e-11 s per n*b at d = 0).  The leaf
+// estimate of the narrower products is scaled by (1 - 0.055 d): measured
+// leaf times (203.6, 167.1, 149.0 ms) beat the tile count by that much,
+// the narrower operands running at higher clocks under the power cap.
+int auto_digit_levels(int n, int b, int num_sms) {
+    int best_d = 0;
+    double best = 1e300;
+    int bd = b;
+    double mult = 1.0;
+    for (int d = 0; d <= 2; ++d) {
+        double leaf = 0;
+        best_depth(n, bd, num_sms, &leaf);
+        const double t = mult * leaf * (1.0 - 0.055 * d) + 3.9e-11 * n * static_cast<double>(b) * std::pow(1.5, d);
+        if (t < best) { best = t; best_d = d; }
+        bd = 32 * (((bd + 31) / 32 + 1) / 2) + 1;  // the children's width
+        mult *= 3.0;
+    }
+    return best_d;
 }
 
 template <typename T>
@@ -118,6 +154,14 @@ __global__ void k_validate(const uint32_t *limbs, int rows, int L32, int b, int3
     const int topbits = b - 32 * (L32 - 1);
     if (topbits < 32 && (limbs[static_cast<size_t>(k) * L32 + L32 - 1] >> topbits) != 0)
         atomicExch(dstat, DEV_BADINPUT);
+}
+
+// Descendants of a split plan report into the top plan's status word.
+void share_status(hmv_plan_s *p, int32_t *dstat) {
+    for (hmv_plan_s *c : p->children) {
+        c->dstat = dstat;
+        share_status(c, dstat);
+    }
 }
 
 }  // namespace
@@ -166,6 +210,7 @@ int32_t hmv_version(void) { return 100; }
 void hmv_free(hmv_plan_t *p) {
     if (!p) return;
     if (p->stream) cudaStreamSynchronize(p->stream);
+    for (hmv_plan_s *c : p->children) hmv_free(c);
     for (void *a : p->allocations) cudaFree(a);
     for (auto &g : p->lv)
         if (g.d_size) cudaFree(g.d_size);
@@ -200,7 +245,11 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
     if (d.kind < HMV_HANKEL || d.kind > HMV_CIRCULANT) return HMV_EINVAL;
     if (d.method < HMV_AUTO || d.method > HMV_FFT64) return HMV_EINVAL;
     if (d.levels < -1 || d.levels > kMaxLevels) return HMV_EINVAL;
-    if (d.flags & ~(HMV_FLAG_TIMING | HMV_FLAG_SIMT_LEAF)) return HMV_EINVAL;
+    if (d.flags & ~(HMV_FLAG_TIMING | HMV_FLAG_SIMT_LEAF | HMV_FLAG_DIGIT_SPLIT1 | HMV_FLAG_DIGIT_SPLIT2))
+        return HMV_EINVAL;
+    int digit_levels = (d.flags & HMV_FLAG_DIGIT_SPLIT2) ? 2 : ((d.flags & HMV_FLAG_DIGIT_SPLIT1) ? 1 : 0);
+    if (digit_levels && ((d.method != HMV_AUTO && d.method != HMV_KARATSUBA) || (d.flags & HMV_FLAG_SIMT_LEAF)))
+        return HMV_EINVAL;
     if (d.method == HMV_FFT64 ? (d.piece_bits != 0 && (d.piece_bits < 4 || d.piece_bits > 16)) : d.piece_bits != 0)
         return HMV_EINVAL;
     if (static_cast<long long>(d.n) * d.nrhs > (1LL << 30)) return HMV_EINVAL;
@@ -237,21 +286,28 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
 
     Guard g;
     const int n = d.n;
-    if (p->method == HMV_SCHOOLBOOK) {
+    int dl = digit_levels;
+    if (dl == 0 && d.method == HMV_AUTO && d.levels < 0 && !(d.flags & HMV_FLAG_SIMT_LEAF) && !external_scratch)
+        dl = auto_digit_levels(n, d.b, p->num_sms);
+    digit_levels = dl;
+    p->digit_levels = digit_levels;
+    if (digit_levels && !external_scratch) {
+        hmv_status st = split_plan_create(p, d, digit_levels);
+        if (st != HMV_OK) { hmv_free(p); return st; }
+        g(dalloc(p, &p->combined, static_cast<size_t>(n) * p->Wo));
+        g(dalloc(p, &p->d_counter, 1));
+        if (d.kind == HMV_CIRCULANT) {
+            g(dalloc(p, &p->h_wrap, static_cast<size_t>(2 * n - 1) * p->L32));
+            g(dalloc(p, &p->h_wrap_neg, static_cast<size_t>(2 * n - 1)));
+        }
+    } else if (p->method == HMV_SCHOOLBOOK) {
         p->L = 0;
         p->ZW = 2 * p->L32 + 2;
         g(dalloc(p, &p->colsum, static_cast<size_t>(n) * 2 * p->L32));
     } else {
         // depth: explicit, or the cheapest by the cost model (node order >= 2)
         int L = d.levels;
-        if (L < 0) {
-            double best = 1e300;
-            for (int t = 0; t <= kMaxLevels; ++t) {
-                if (t > 0 && build_levels(n, t - 1).back().smax <= 2) break;
-                double c = cost_model(n, d.b, t, p->num_sms);
-                if (c < best) { best = c; L = t; }
-            }
-        }
+        if (L < 0) L = best_depth(n, d.b, p->num_sms, nullptr);
         p->L = L;
         p->lv = build_levels(n, L);
         p->Dl = ceil_div(static_cast<long long>(d.b) + L + 2, 8);
@@ -305,7 +361,7 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
                 for (int ub = 0; ub < p->NUB; ++ub) {
                     const int u0 = ub * TN;
                     const int s_min = std::max(0, u0 - (p->Dl - 1)), s_max = std::min(p->Dl - 1, u0 + TN - 1);
-                    const int nsb = (s_max >= s_min) ? s_max / KS - s_min / KS + 1 : 0;
+                    const int nsb = (s_max >= s_min) ? (s_max - s_min / 8 * 8 + KS) / KS : 0;  // as the kernel
                     lt.push_back(Tile{lf, mt * TM, ub, nsb * m, 0});
                     issued += static_cast<double>(TM) * TN * KS * nsb * m;
                 }
@@ -360,6 +416,7 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
         cudaGetLastError();
         return st;
     }
+    if (!p->children.empty()) share_status(p, p->dstat);
     *out = p;
     return HMV_OK;
 }
@@ -376,11 +433,32 @@ hmv_status hmv_load_matrix(hmv_plan_t *p, const hmv_vec *h) {
     Guard g;
     const size_t nl = static_cast<size_t>(hlen) * p->L32;
     const cudaMemcpyKind kind = h->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    g(cudaMemcpyAsync(p->h_limbs_d, h->limbs, nl * sizeof(uint32_t), kind, p->stream));
-    g(cudaMemcpyAsync(p->h_neg_d, h->neg, hlen, kind, p->stream));
+    if (h->limbs != p->h_limbs_d)  // a split parent may hand a child its own staging buffer
+        g(cudaMemcpyAsync(p->h_limbs_d, h->limbs, nl * sizeof(uint32_t), kind, p->stream));
+    if (h->neg != p->h_neg_d) g(cudaMemcpyAsync(p->h_neg_d, h->neg, hlen, kind, p->stream));
     g(cudaMemsetAsync(p->dstat, 0, 8 * sizeof(int32_t), p->stream));
     k_validate<<<ceil_div(hlen, 128), 128, 0, p->stream>>>(p->h_limbs_d, hlen, p->L32, p->b, p->dstat);
     g(cudaGetLastError());
+    if (!p->children.empty()) {
+        int32_t vs[8] = {0};
+        g(cudaMemcpyAsync(vs, p->dstat, sizeof vs, cudaMemcpyDeviceToHost, p->stream));
+        g(cudaStreamSynchronize(p->stream));
+        if (g.err != cudaSuccess) return from_cuda(g.err);
+        if (vs[0] == DEV_BADINPUT) return HMV_EINVAL;
+        const uint32_t *hl = p->h_limbs_d;
+        const uint8_t *hn = p->h_neg_d;
+        if (p->kind == HMV_CIRCULANT) {
+            g(launch_wrap_circulant(p, p->h_limbs_d, p->h_neg_d));
+            hl = p->h_wrap;
+            hn = p->h_wrap_neg;
+        }
+        if (g.err != cudaSuccess) return from_cuda(g.err);
+        hmv_status st = split_load_matrix(p, hl, hn);
+        if (st != HMV_OK) return st;
+        p->e_h = h->exponent;
+        p->loaded = true;
+        return HMV_OK;
+    }
     if (p->method != HMV_SCHOOLBOOK) {
         // level 0 holds the Hankel sequence (circulant: the wrapped Toeplitz sequence)
         g(launch_encode(p, p->h_limbs_d, p->h_neg_d, 2 * p->n - 1, p->kind == HMV_CIRCULANT ? p->n : 0, p->a_lvl[0]));
@@ -443,7 +521,14 @@ hmv_status hmv_matvec(hmv_plan_t *p, const hmv_vec *x, hmv_vec *y) {
             if (use_fft) p->fft_matvecs++;
             else p->fft_fallbacks++;
         }
-        if (use_fft) {
+        if (!p->children.empty()) {
+            g(split_vector_side(p, xr, xnr));
+            timing_mark(p, 2);
+            g(split_leaf_launch(p));
+            timing_mark(p, 3);
+            g(split_post(p, r));
+            timing_mark(p, 4);
+        } else if (use_fft) {
             timing_mark(p, 2);
             g(cudaMemsetAsync(p->fft_maxdist, 0, sizeof(unsigned long long), p->stream));
             g(fft_vector_product(p, r));
@@ -518,10 +603,16 @@ hmv_status hmv_matvec(hmv_plan_t *p, const hmv_vec *x, hmv_vec *y) {
 hmv_status hmv_get_stats(const hmv_plan_t *p, hmv_stats *o) {
     if (!p || !o) return HMV_EINVAL;
     memset(o, 0, sizeof *o);
-    o->levels = p->L;
-    o->leaves = p->lv.empty() ? 1 : p->lv[p->L].nodes;
-    o->leaf_rows_max = p->lv.empty() ? p->n : p->lv[p->L].smax;
-    o->digits = p->Dl;
+    const hmv_plan_s *q = p;
+    int unsplit = 1;
+    while (!q->children.empty()) {
+        q = q->children[0];
+        unsplit *= 3;
+    }
+    o->levels = q->L;
+    o->leaves = unsplit * (q->lv.empty() ? 1 : q->lv[q->L].nodes);
+    o->leaf_rows_max = q->lv.empty() ? q->n : q->lv[q->L].smax;
+    o->digits = q->Dl;
     o->leaf_tiles = p->ntiles;
     o->leaf_macs = p->leaf_macs;
     o->leaf_macs_issued = p->leaf_macs_issued;

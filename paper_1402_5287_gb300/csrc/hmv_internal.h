@@ -106,6 +106,15 @@ struct hmv_plan_s {
     std::vector<hmv::Tile> tiles;            // host copy of the tile list
     int batch_x_exponent = 0;                // exponent of the x block last given to a batch
     bool dry_run = false;                    // footprint query: nothing is allocated
+    // digit-dimension split (Karatsuba on the mantissas): three child plans
+    std::vector<hmv_plan_s *> children;
+    int digit_levels = 0;
+    int split_bits = 0;                      // s: V = V1 2^s + V0
+    int32_t *combined = nullptr;             // [n][Wo] exact digit vector of this plan's rows
+    uint32_t *h_wrap = nullptr;              // circulant: the wrapped Hankel sequence (2n-1 rows)
+    uint8_t *h_wrap_neg = nullptr;
+    hmv::LeafProblem *split_probs = nullptr; // leaf problems of all unsplit descendants
+    hmv::Tile *split_tiles = nullptr;
     hmv::LeafProblem hprob;                  // host copy of *d_prob
     size_t bytes_a_lvl = 0, bytes_x_lvl = 0, bytes_post = 0, elems_xg = 0, bytes_dig = 0, elems_carry = 0;
     int num_sms = 0;
@@ -144,6 +153,12 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
 cudaError_t launch_validate(hmv_plan_s *p, const uint32_t *limbs, int rows);
 cudaError_t launch_colsum_normalize(hmv_plan_s *p, int rhs);
 cudaError_t leaf_tc_prepare();
+hmv_status split_plan_create(hmv_plan_s *p, const hmv_desc &d, int digit_levels);
+hmv_status split_load_matrix(hmv_plan_s *p, const uint32_t *h_limbs, const uint8_t *h_neg);
+cudaError_t split_vector_side(hmv_plan_s *p, const uint32_t *xl, const uint8_t *xn);
+cudaError_t split_leaf_launch(hmv_plan_s *p);
+cudaError_t split_post(hmv_plan_s *p, int rhs);
+cudaError_t launch_wrap_circulant(hmv_plan_s *p, const uint32_t *c_limbs, const uint8_t *c_neg);
 cudaError_t launch_leaf_tc(hmv_plan_s *p);
 cudaError_t launch_leaf_tc_multi(const LeafProblem *probs, const Tile *tiles, int ntiles, int32_t *dstat,
                                  int *tile_counter, cudaStream_t stream, int num_sms);

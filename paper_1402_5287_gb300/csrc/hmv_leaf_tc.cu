@@ -63,7 +63,7 @@ struct __align__(1024) Smem {
 
 struct TileInfo {
     const LeafProblem *pr;
-    int leaf, i0, ub, u0, m, sb_lo, sb_hi, njc, Q, Dl, Dp;
+    int leaf, i0, ub, u0, m, s_base, nsb, njc, Q, Dl, Dp;
 };
 
 __device__ __forceinline__ TileInfo decode(const Tile &t, const LeafProblem *probs) {
@@ -78,12 +78,14 @@ __device__ __forceinline__ TileInfo decode(const Tile &t, const LeafProblem *pro
     ti.ub = t.ub;
     ti.u0 = t.ub * TN;
     ti.m = size[t.leaf];
+    // s-blocks of KS digits start at the tile's first useful digit (rounded
+    // down to 8 for the TMA coordinates), not at multiples of KS
     const int s_min = max(0, ti.u0 - (Dl - 1));
     const int s_max = min(Dl - 1, ti.u0 + TN - 1);
-    ti.sb_lo = s_min / KS;
-    ti.sb_hi = (s_max >= s_min) ? s_max / KS : ti.sb_lo - 1;
+    ti.s_base = s_min / 8 * 8;
+    ti.nsb = (s_max >= s_min) ? (s_max - ti.s_base + KS) / KS : 0;
     ti.njc = (ti.m + JC - 1) / JC;
-    ti.Q = (ti.sb_hi - ti.sb_lo + 1) * ti.m;
+    ti.Q = ti.nsb * ti.m;
     return ti;
 }
 
@@ -133,8 +135,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const CUtensorMap *mapA = &ti.pr->mapA;
                 const CUtensorMap *mapB = &ti.pr->mapB;
                 const int Dp = ti.Dp;
-                for (int sb = ti.sb_lo; sb <= ti.sb_hi && !sm.abort; ++sb) {
-                    const int s_lo = sb * KS;
+                for (int sb = 0; sb < ti.nsb && !sm.abort; ++sb) {
+                    const int s_lo = ti.s_base + sb * KS;
                     for (int jc = 0; jc < ti.njc && !sm.abort; ++jc) {
                         const int j0 = jc * JC;
                         const int jn = min(JC, ti.m - j0);
@@ -168,7 +170,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const TileInfo ti = decode(tiles[t], probs);
                 int q = 0;
                 uint32_t acc_flag = 0;
-                for (int sb = ti.sb_lo; sb <= ti.sb_hi && !sm.abort; ++sb) {
+                for (int sb = 0; sb < ti.nsb && !sm.abort; ++sb) {
                     for (int jc = 0; jc < ti.njc && !sm.abort; ++jc) {
                         const int jn = min(JC, ti.m - jc * JC);
                         if (!mbar_wait(&sm.a_full[as], aph, kTimeoutNs)) { fail(sm, dstat); break; }

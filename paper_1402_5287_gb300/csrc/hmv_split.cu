@@ -1,0 +1,276 @@
+// Karatsuba in the digit dimension, on top of the index recursion.
+//
+// Algorithm 1 (Beliakov, arXiv:1402.5287, Sec. 3) saves products along the
+// matrix index; the same bilinear trick also applies to the numbers
+// themselves (Karatsuba's own splitting, which Sec. 3 names as its
+// inspiration).  With every mantissa split at s bits, V = V1 2^s + V0
+// (|V0| < 2^s, |V1| < 2^(b-s), both with the sign of V), the exact rows are
+//     Z = Z11 2^(2s) + (Zm - Z00 - Z11) 2^s + Z00,
+//     Z00 = A(h0) x0,  Z11 = A(h1) x1,  Zm = A(h0 + h1)(x0 + x1),
+// three Hankel products of about half the width: 3/4 of the digit
+// multiply-adds per level.  Each of the three is an ordinary plan (index
+// recursion plus tensor-core leaves); a split plan may itself split again.
+// All leaf products of all descendants run in ONE persistent tensor-core
+// launch; the exact digit vectors of the three children are combined with
+// digit shifts (s is a multiple of 32 bits), then normalised and rounded
+// once, exactly like an unsplit plan.
+#include <algorithm>
+#include <cstring>
+
+#include "hmv_internal.h"
+
+namespace hmv {
+namespace {
+
+// Sign-magnitude rows (b bits, L32 limbs) -> the three children's rows
+// (bc bits, Lc limbs): lo = M mod 2^s, hi = M >> s, mid = lo + hi, each with
+// the sign of the entry (zero magnitudes are +).
+__global__ void k_split(const uint32_t *__restrict__ limbs, const uint8_t *__restrict__ neg, int rows, int L32,
+                        int sl, int Lc, uint32_t *__restrict__ lo, uint32_t *__restrict__ hi,
+                        uint32_t *__restrict__ mid, uint8_t *__restrict__ nlo, uint8_t *__restrict__ nhi,
+                        uint8_t *__restrict__ nmid) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= rows) return;
+    const uint32_t *m = limbs + static_cast<size_t>(k) * L32;
+    uint32_t *ol = lo + static_cast<size_t>(k) * Lc;
+    uint32_t *oh = hi + static_cast<size_t>(k) * Lc;
+    uint32_t *om = mid + static_cast<size_t>(k) * Lc;
+    uint32_t anyl = 0, anyh = 0;
+    unsigned long long c = 0;
+    for (int q = 0; q < Lc; ++q) {
+        const uint32_t vl = (q < sl && q < L32) ? m[q] : 0u;
+        const uint32_t vh = (q + sl < L32) ? m[q + sl] : 0u;
+        ol[q] = vl;
+        oh[q] = vh;
+        c += static_cast<unsigned long long>(vl) + vh;
+        om[q] = static_cast<uint32_t>(c);
+        c >>= 32;
+        anyl |= vl;
+        anyh |= vh;
+    }
+    const uint8_t s = neg[k] ? 1 : 0;
+    nlo[k] = anyl ? s : 0;
+    nhi[k] = anyh ? s : 0;
+    nmid[k] = (anyl | anyh) ? s : 0;
+}
+
+// z[u] = Z00[u] + (Zm - Z00 - Z11)[u - ds] + Z11[u - 2 ds], int32 digits,
+// radix 2^8, no carries (the digits stay far below 2^31).
+__global__ void k_combine(const int32_t *__restrict__ z00, const int32_t *__restrict__ zm,
+                          const int32_t *__restrict__ z11, int Wc, int n, int ds, int32_t *__restrict__ out, int Wp) {
+    const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= static_cast<long long>(n) * Wp) return;
+    const int i = static_cast<int>(idx / Wp), u = static_cast<int>(idx % Wp);
+    const size_t r = static_cast<size_t>(i) * Wc;
+    auto at = [&](const int32_t *z, int v) -> int32_t { return (v >= 0 && v < Wc) ? z[r + v] : 0; };
+    out[static_cast<size_t>(i) * Wp + u] =
+        at(z00, u) + at(zm, u - ds) - at(z00, u - ds) - at(z11, u - ds) + at(z11, u - 2 * ds);
+}
+
+void collect_leaf_plans(hmv_plan_s *p, std::vector<hmv_plan_s *> &out) {
+    if (p->children.empty()) {
+        out.push_back(p);
+        return;
+    }
+    for (hmv_plan_s *c : p->children) collect_leaf_plans(c, out);
+}
+
+// Split rows of a vector into the three children's staging buffers,
+// recursively down to the unsplit plans.
+cudaError_t split_down(hmv_plan_s *p, const uint32_t *limbs, const uint8_t *neg, int rows, bool matrix) {
+    if (p->children.empty()) return cudaSuccess;
+    hmv_plan_s *c0 = p->children[0], *c1 = p->children[1], *cm = p->children[2];
+    uint32_t *dst[3];
+    uint8_t *dneg[3];
+    for (int t = 0; t < 3; ++t) {
+        dst[t] = matrix ? p->children[t]->h_limbs_d : p->children[t]->x_limbs_d;
+        dneg[t] = matrix ? p->children[t]->h_neg_d : p->children[t]->x_neg_d;
+    }
+    k_split<<<(rows + 127) / 128, 128, 0, p->stream>>>(limbs, neg, rows, p->L32, p->split_bits / 32, c0->L32,
+                                                       dst[0], dst[1], dst[2], dneg[0], dneg[1], dneg[2]);
+    p->launches_total++;
+    cudaError_t e = cudaGetLastError();
+    (void)c1;
+    (void)cm;
+    for (int t = 0; t < 3 && e == cudaSuccess; ++t)
+        e = split_down(p->children[t], dst[t], dneg[t], rows, matrix);
+    return e;
+}
+
+// The exact digit vector of a plan's rows after its post-pass (unsplit) or
+// after combining its children (split).
+cudaError_t combine_up(hmv_plan_s *p, const int32_t **out, int *width) {
+    if (p->children.empty()) {
+        *out = p->post[0];
+        *width = p->Wo;
+        return cudaSuccess;
+    }
+    const int32_t *z[3];
+    int w[3];
+    for (int t = 0; t < 3; ++t) {
+        cudaError_t e = combine_up(p->children[t], &z[t], &w[t]);
+        if (e != cudaSuccess) return e;
+    }
+    const long long work = static_cast<long long>(p->n) * p->Wo;
+    k_combine<<<static_cast<unsigned>((work + 255) / 256), 256, 0, p->stream>>>(z[0], z[2], z[1], w[0], p->n,
+                                                                               p->split_bits / 8, p->combined,
+                                                                               p->Wo);
+    p->launches_total++;
+    *out = p->combined;
+    *width = p->Wo;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// Children of a split plan (called from plan_create).
+hmv_status split_plan_create(hmv_plan_s *p, const hmv_desc &d, int digit_levels) {
+    p->split_bits = 32 * ((p->L32 + 1) / 2);
+    const int bc = p->split_bits + 1;  // lo, hi < 2^s; lo + hi < 2^(s+1)
+    for (int t = 0; t < 3; ++t) {
+        hmv_desc cd = d;
+        cd.b = bc;
+        cd.nrhs = 1;
+        cd.kind = HMV_HANKEL;       // the parent maps the kind onto the Hankel sequence
+        cd.method = HMV_KARATSUBA;
+        cd.flags &= ~(HMV_FLAG_TIMING | HMV_FLAG_DIGIT_SPLIT1 | HMV_FLAG_DIGIT_SPLIT2);
+        if (digit_levels > 1) cd.flags |= HMV_FLAG_DIGIT_SPLIT1;
+        cd.levels = -1;
+        hmv_plan_s *c = nullptr;
+        hmv_status st = plan_create(&cd, p->stream, false, &c, p->dry_run);
+        if (st != HMV_OK) return st;
+        p->children.push_back(c);
+        p->device_bytes += c->device_bytes;
+    }
+    int wc = p->children[0]->Wo;
+    for (hmv_plan_s *c : p->children) wc = std::max(wc, c->Wo);
+    p->Wo = 2 * (p->split_bits / 8) + wc;
+    p->ZW = p->Wo / 4;
+    double macs = 0, issued = 0;
+    for (hmv_plan_s *c : p->children) {
+        macs += c->leaf_macs;
+        issued += c->leaf_macs_issued;
+    }
+    p->leaf_macs = macs;
+    p->leaf_macs_issued = issued;
+    return HMV_OK;
+}
+
+// Matrix side: map the kind onto a Hankel sequence of 2n-1 entries, split it
+// for every descendant and load the unsplit plans.
+hmv_status split_load_matrix(hmv_plan_s *p, const uint32_t *h_limbs, const uint8_t *h_neg) {
+    cudaError_t e = split_down(p, h_limbs, h_neg, 2 * p->n - 1, true);
+    if (e != cudaSuccess) return HMV_ECUDA;
+    std::vector<hmv_plan_s *> leaves;
+    collect_leaf_plans(p, leaves);
+    for (hmv_plan_s *c : leaves) {
+        hmv_vec v;
+        memset(&v, 0, sizeof v);
+        v.len = 2 * c->n - 1;
+        v.nrhs = 1;
+        v.b = c->b;
+        v.exponent = 0;
+        v.limbs = c->h_limbs_d;
+        v.neg = c->h_neg_d;
+        v.on_device = 1;
+        hmv_status st = hmv_load_matrix(c, &v);
+        if (st != HMV_OK) return st;
+    }
+    return HMV_OK;
+}
+
+// One right-hand side, in three phases so that the caller can time the leaf
+// launch: (1) split x and run the vector side of every unsplit plan; (2) one
+// leaf launch for all of them; (3) their post-passes, the combines, and the
+// exact rows of right-hand side `rhs` in the top plan.
+cudaError_t split_vector_side(hmv_plan_s *p, const uint32_t *xl, const uint8_t *xn) {
+    cudaError_t e = split_down(p, xl, xn, p->n, false);
+    std::vector<hmv_plan_s *> leaves;
+    collect_leaf_plans(p, leaves);
+    for (hmv_plan_s *c : leaves) {
+        if (e != cudaSuccess) break;
+        c->stream = p->stream;
+        e = launch_encode(c, c->x_limbs_d, c->x_neg_d, c->n, 0, c->x_lvl[0]);
+        for (int l = 0; l < c->L && e == cudaSuccess; ++l)
+            e = launch_prepass(c, l, false, c->x_lvl[l % 2], c->x_lvl[(l + 1) % 2]);
+        if (e == cudaSuccess) e = launch_pack_vector(c, c->x_lvl[c->L % 2]);
+    }
+    return e;
+}
+
+cudaError_t split_leaf_launch(hmv_plan_s *p) {
+    cudaError_t e = cudaSuccess;
+    if (!p->split_probs) {
+        // the set of unsplit plans is fixed: build and upload the combined lists once
+        std::vector<hmv_plan_s *> leaves;
+        collect_leaf_plans(p, leaves);
+        std::vector<LeafProblem> probs;
+        std::vector<Tile> tiles;
+        for (hmv_plan_s *c : leaves) {
+            const int idx = static_cast<int>(probs.size());
+            probs.push_back(c->hprob);
+            for (Tile t : c->tiles) {
+                t.prob = idx;
+                tiles.push_back(t);
+            }
+        }
+        e = cudaMalloc(reinterpret_cast<void **>(&p->split_probs), probs.size() * sizeof(LeafProblem));
+        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&p->split_tiles), tiles.size() * sizeof(Tile));
+        if (e == cudaSuccess) {
+            p->allocations.push_back(p->split_probs);
+            p->allocations.push_back(p->split_tiles);
+            e = cudaMemcpy(p->split_probs, probs.data(), probs.size() * sizeof(LeafProblem), cudaMemcpyHostToDevice);
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpy(p->split_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice);
+        p->ntiles = static_cast<int>(tiles.size());
+    }
+    if (e == cudaSuccess) {
+        e = launch_leaf_tc_multi(p->split_probs, p->split_tiles, p->ntiles, p->dstat, p->d_counter, p->stream,
+                                 p->num_sms);
+        p->launches_leaf++;
+        p->launches_total++;
+    }
+    return e;
+}
+
+cudaError_t split_post(hmv_plan_s *p, int rhs) {
+    std::vector<hmv_plan_s *> leaves;
+    collect_leaf_plans(p, leaves);
+    cudaError_t e = cudaSuccess;
+    for (hmv_plan_s *c : leaves) {
+        if (e != cudaSuccess) break;
+        e = launch_leaf_normalize(c, c->post[c->L % 2]);
+        for (int l = c->L - 1; l >= 0 && e == cudaSuccess; --l)
+            e = launch_postpass(c, l, c->post[(l + 1) % 2], c->post[l % 2]);
+    }
+    const int32_t *z = nullptr;
+    int w = 0;
+    if (e == cudaSuccess) e = combine_up(p, &z, &w);
+    if (e == cudaSuccess) e = launch_final_normalize(p, z, rhs);
+    for (hmv_plan_s *c : leaves) {
+        p->launches_total += c->launches_total;
+        c->launches_total = 0;
+    }
+    return e;
+}
+
+namespace {
+__global__ void k_wrap(const uint32_t *__restrict__ c, const uint8_t *__restrict__ cn, int n, int L32,
+                       uint32_t *__restrict__ h, uint8_t *__restrict__ hn) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 2 * n - 1) return;
+    const int src = ((n - 1 - k) % n + n) % n;  // circulant -> Toeplitz sequence
+    for (int q = 0; q < L32; ++q) h[static_cast<size_t>(k) * L32 + q] = c[static_cast<size_t>(src) * L32 + q];
+    hn[k] = cn[src];
+}
+}  // namespace
+
+cudaError_t launch_wrap_circulant(hmv_plan_s *p, const uint32_t *c_limbs, const uint8_t *c_neg) {
+    k_wrap<<<(2 * p->n - 1 + 127) / 128, 128, 0, p->stream>>>(c_limbs, c_neg, p->n, p->L32, p->h_wrap,
+                                                                p->h_wrap_neg);
+    p->launches_total++;
+    return cudaGetLastError();
+}
+
+}  // namespace hmv
