@@ -205,7 +205,8 @@ def run_ours(args):
     split_flag = {-1: 0, 0: 0, 1: hmv.FLAG_DIGIT_SPLIT1, 2: hmv.FLAG_DIGIT_SPLIT2}[args.digit_split]
     if args.digit_split == 0 and method == hmv.AUTO:
         method = hmv.KARATSUBA  # no digit split
-    plan = hmv.Plan(n, b, method=method, levels=args.levels, flags=hmv.FLAG_TIMING | split_flag,
+    tile_flag = hmv.FLAG_TILE128 if args.tile == 128 else 0
+    plan = hmv.Plan(n, b, method=method, levels=args.levels, flags=hmv.FLAG_TIMING | split_flag | tile_flag,
                     stream=stream.cuda_stream)
     plan.load_matrix(h)
     with torch.cuda.stream(stream):
@@ -303,6 +304,7 @@ def run_ours(args):
                    "digit_split_levels": args.digit_split,
                    "levels": st["levels"], "leaves": st["leaves"], "leaf_rows_max": st["leaf_rows_max"],
                    "digits_per_operand": st["digits"], "leaf_tiles": st["leaf_tiles"],
+                   "leaf_tile_digits": st["leaf_tile_digits"],
                    "digit_format": "balanced radix-2^8 digits held exactly in bf16, fp32 windows < 2^24",
                    "l2": "working set of several GB per step (inputs larger than L2)",
                    "parallelism": f"{world} independent replica(s), one per GPU"},
@@ -513,6 +515,8 @@ def main(argv=None):
                     help="levels of Karatsuba on the mantissas on top of the index recursion (-1: cost model)")
     ap.add_argument("--method", choices=["auto", "karatsuba", "fft64", "schoolbook"], default="auto",
                     help="product method (profiling runs; the metric uses auto = Karatsuba + tcgen05)")
+    ap.add_argument("--tile", type=int, choices=[0, 128, 256], default=0,
+                    help="leaf tile width in product digits (profiling runs; 0: the plan's default)")
     ap.add_argument("--compare", action="store_true", help="also time the schoolbook comparison kernels")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="matrix order (profiling runs; default 8000)")

@@ -75,6 +75,7 @@ typedef enum {
  * the width per level), on top of the index recursion; HMV_AUTO/HMV_KARATSUBA */
 #define HMV_FLAG_DIGIT_SPLIT1 4u  /* one level */
 #define HMV_FLAG_DIGIT_SPLIT2 8u  /* two levels */
+#define HMV_FLAG_TILE128 16u      /* leaf tiles of 128 product digits (default 256) */
 
 typedef struct {
     int32_t n;        /* matrix order, n >= 1 */
@@ -108,7 +109,7 @@ typedef struct {
     int32_t leaves;          /* 3^levels */
     int32_t leaf_rows_max;   /* largest leaf order */
     int32_t digits;          /* balanced radix-2^8 digits per operand in the tree */
-    int64_t leaf_tiles;      /* 128 x 256 output tiles per matvec */
+    int64_t leaf_tiles;      /* 128 x leaf_tile_digits output tiles per matvec */
     double leaf_macs;        /* useful digit multiply-adds per matvec in the leaves */
     double leaf_macs_issued; /* digit multiply-adds issued to the tensor cores */
     int64_t device_bytes;    /* device memory held by the plan */
@@ -123,6 +124,9 @@ typedef struct {
     int64_t fft_matvecs;     /* matvecs done by the FFT path */
     int64_t fft_fallbacks;   /* matvecs whose bound failed and that took the integer path */
     double ms_fft;           /* with HMV_FLAG_TIMING: time in the FFT path */
+    int32_t leaf_tile_digits; /* product digits per leaf tile (256, or 128 with HMV_FLAG_TILE128
+                                 or when HMV_AUTO's cost model prefers it); 0 without tiles */
+    int32_t reserved0;
 } hmv_stats;
 
 /* Create a plan: checks the descriptor, chooses the recursion depth and

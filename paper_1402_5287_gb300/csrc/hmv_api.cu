@@ -67,22 +67,28 @@ std::vector<LevelGeom> build_levels(int n, int L) {
     return lv;
 }
 
+// SM cycles one 128 x tn x 16 MMA takes inside the leaf kernel (measured at
+// n = 8000: 256-wide tiles run at the tensor pipe's rate, 128-wide ones at
+// 0.57 of it per MAC, because the issuing thread cannot keep up with the
+// shorter MMAs).
+inline double mma_cycles(int tn) { return tn == 128 ? 115.0 : 128.0; }
+
 // Estimated seconds of one matvec at depth L on this GPU (tensor work from
 // the tile count, memory work from the bytes the level kernels move).
-double cost_model(int n, int b, int L, int num_sms) {
+double cost_model(int n, int b, int L, int num_sms, int tn = TN_DEFAULT) {
     std::vector<LevelGeom> lv = build_levels(n, L);
     const int Dl = ceil_div(b + L + 2, 8);
     const long long Dp = round_up(Dl, 16);
-    const int Uo = static_cast<int>(round_up(2LL * Dl - 1, TN));
-    const int NUB = Uo / TN;
-    double ksteps = 0;  // 128x256x16 MMAs
+    const int Uo = static_cast<int>(round_up(2LL * Dl - 1, tn));
+    const int NUB = Uo / tn;
+    double ksteps = 0;  // 128 x tn x 16 MMAs
     for (int ub = 0; ub < NUB; ++ub) {
-        const int u0 = ub * TN;
-        const int s_min = std::max(0, u0 - (Dl - 1)), s_max = std::min(Dl - 1, u0 + TN - 1);
+        const int u0 = ub * tn;
+        const int s_min = std::max(0, u0 - (Dl - 1)), s_max = std::min(Dl - 1, u0 + tn - 1);
         const int nsb = (s_max >= s_min) ? (s_max - s_min / 8 * 8 + KS) / KS : 0;
         for (int s : lv[L].size) ksteps += static_cast<double>(ceil_div(s, TM)) * nsb * s * (KS / 16);
     }
-    const double mma_s = ksteps * 128.0 / (static_cast<double>(num_sms) * 1.9e9);
+    const double mma_s = ksteps * mma_cycles(tn) / (static_cast<double>(num_sms) * 1.9e9);
     double bytes = 0;
     for (int l = 0; l <= L; ++l)
         bytes += static_cast<double>(lv[l].nodes) * lv[l].rowsX * (Dp * 2.0 + (Uo + 8) * 4.0 * 4.0);
@@ -91,12 +97,12 @@ double cost_model(int n, int b, int L, int num_sms) {
 }
 
 // Cheapest index depth for (n, b) and its estimated seconds.
-int best_depth(int n, int b, int num_sms, double *cost) {
+int best_depth(int n, int b, int num_sms, double *cost, int tn = TN_DEFAULT) {
     int L = 0;
     double best = 1e300;
     for (int t = 0; t <= kMaxLevels; ++t) {
         if (t > 0 && build_levels(n, t - 1).back().smax <= 2) break;
-        const double c = cost_model(n, b, t, num_sms);
+        const double c = cost_model(n, b, t, num_sms, tn);
         if (c < best) { best = c; L = t; }
     }
     if (cost) *cost = best;
@@ -245,7 +251,8 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
     if (d.kind < HMV_HANKEL || d.kind > HMV_CIRCULANT) return HMV_EINVAL;
     if (d.method < HMV_AUTO || d.method > HMV_FFT64) return HMV_EINVAL;
     if (d.levels < -1 || d.levels > kMaxLevels) return HMV_EINVAL;
-    if (d.flags & ~(HMV_FLAG_TIMING | HMV_FLAG_SIMT_LEAF | HMV_FLAG_DIGIT_SPLIT1 | HMV_FLAG_DIGIT_SPLIT2))
+    if (d.flags & ~(HMV_FLAG_TIMING | HMV_FLAG_SIMT_LEAF | HMV_FLAG_DIGIT_SPLIT1 | HMV_FLAG_DIGIT_SPLIT2 |
+                    HMV_FLAG_TILE128))
         return HMV_EINVAL;
     int digit_levels = (d.flags & HMV_FLAG_DIGIT_SPLIT2) ? 2 : ((d.flags & HMV_FLAG_DIGIT_SPLIT1) ? 1 : 0);
     if (digit_levels && ((d.method != HMV_AUTO && d.method != HMV_KARATSUBA) || (d.flags & HMV_FLAG_SIMT_LEAF)))
@@ -266,6 +273,7 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
     p->L32 = (d.b + 31) / 32;
     p->timing = (d.flags & HMV_FLAG_TIMING) != 0;
     p->external_scratch = external_scratch;
+    p->tn = (d.flags & HMV_FLAG_TILE128) ? 128 : TN_DEFAULT;
     if (external_scratch && (p->method != HMV_KARATSUBA || (d.flags & HMV_FLAG_SIMT_LEAF))) {
         delete p;
         return HMV_EUNSUPPORTED;
@@ -305,20 +313,35 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
         p->ZW = 2 * p->L32 + 2;
         g(dalloc(p, &p->colsum, static_cast<size_t>(n) * 2 * p->L32));
     } else {
-        // depth: explicit, or the cheapest by the cost model (node order >= 2)
+        // depth: explicit, or the cheapest by the cost model (node order >= 2);
+        // under HMV_AUTO the tile width too (128 only pays where it cuts the
+        // padded product digits enough, i.e. for short mantissas)
         int L = d.levels;
-        if (L < 0) L = best_depth(n, d.b, p->num_sms, nullptr);
+        const bool auto_tile = d.method == HMV_AUTO && !(d.flags & (HMV_FLAG_TILE128 | HMV_FLAG_SIMT_LEAF));
+        if (auto_tile) {
+            double c256 = 0, c128 = 0;
+            const int L256 = L < 0 ? best_depth(n, d.b, p->num_sms, &c256, 256) : L;
+            const int L128 = L < 0 ? best_depth(n, d.b, p->num_sms, &c128, 128) : L;
+            if (L >= 0) {
+                c256 = cost_model(n, d.b, L, p->num_sms, 256);
+                c128 = cost_model(n, d.b, L, p->num_sms, 128);
+            }
+            p->tn = c128 < c256 ? 128 : 256;
+            L = c128 < c256 ? L128 : L256;
+        } else if (L < 0) {
+            L = best_depth(n, d.b, p->num_sms, nullptr, p->tn);
+        }
         p->L = L;
         p->lv = build_levels(n, L);
         p->Dl = ceil_div(static_cast<long long>(d.b) + L + 2, 8);
         p->Dp = static_cast<int>(round_up(p->Dl, 16));
-        p->Uo = static_cast<int>(round_up(2LL * p->Dl - 1, TN));
-        p->NUB = p->Uo / TN;
+        p->Uo = static_cast<int>(round_up(2LL * p->Dl - 1, p->tn));
+        p->NUB = p->Uo / p->tn;
         p->Wo = p->Uo + EXTRA_DIGITS;
         p->ZW = p->Wo / 4;
         const LevelGeom &leaf = p->lv[L];
         p->MT = ceil_div(leaf.smax, TM);
-        p->RA = static_cast<int>(round_up(leaf.rowsA, 8));
+        p->RA = static_cast<int>(round_up(leaf.rowsA, 32));  // whole 32-row groups for the A tensor map
         p->RX = leaf.rowsX;
         size_t maxA = 0, maxX = 0, maxPost = 0;
         for (auto &lg : p->lv) {
@@ -359,11 +382,11 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
             std::vector<Tile> lt;
             for (int mt = 0; mt < ceil_div(m, TM); ++mt)
                 for (int ub = 0; ub < p->NUB; ++ub) {
-                    const int u0 = ub * TN;
-                    const int s_min = std::max(0, u0 - (p->Dl - 1)), s_max = std::min(p->Dl - 1, u0 + TN - 1);
+                    const int u0 = ub * p->tn;
+                    const int s_min = std::max(0, u0 - (p->Dl - 1)), s_max = std::min(p->Dl - 1, u0 + p->tn - 1);
                     const int nsb = (s_max >= s_min) ? (s_max - s_min / 8 * 8 + KS) / KS : 0;  // as the kernel
                     lt.push_back(Tile{lf, mt * TM, ub, nsb * m, 0});
-                    issued += static_cast<double>(TM) * TN * KS * nsb * m;
+                    issued += static_cast<double>(TM) * p->tn * KS * nsb * m;
                 }
             std::stable_sort(lt.begin(), lt.end(), [](const Tile &a, const Tile &b2) { return a.cost > b2.cost; });
             tiles.insert(tiles.end(), lt.begin(), lt.end());
@@ -632,6 +655,7 @@ hmv_status hmv_get_stats(const hmv_plan_t *p, hmv_stats *o) {
     o->fft_matvecs = p->fft_matvecs;
     o->fft_fallbacks = p->fft_fallbacks;
     o->ms_fft = p->ms_fft;
+    o->leaf_tile_digits = (q->method == HMV_KARATSUBA && !q->lv.empty() && q->hrev) ? q->tn : 0;
     return HMV_OK;
 }
 

@@ -39,6 +39,7 @@ struct hmv_batch_s {
     std::vector<hmv::LeafProblem *> d_probs;  // per wave
     std::vector<hmv::Tile *> d_tiles;         // per wave
     std::vector<int> ntiles;                  // per wave
+    std::vector<int> wave_tn;                 // tile width of each wave's leaf launch
     std::vector<void *> allocations;
     int8_t *a_lvl[2] = {nullptr, nullptr}, *x_lvl[2] = {nullptr, nullptr};
     int32_t *post[2] = {nullptr, nullptr};
@@ -105,7 +106,7 @@ cudaError_t issue(hmv_batch_s *B) {
         }
         if (e == cudaSuccess)
             e = launch_leaf_tc_multi(B->d_probs[w], B->d_tiles[w], B->ntiles[w], B->plans[0]->dstat,
-                                     B->plans[0]->d_counter, B->stream, B->num_sms);
+                                     B->plans[0]->d_counter, B->stream, B->num_sms, B->wave_tn[w]);
         ++kernels;
         for (const Pair &pr : B->pairs) {
             if (pr.wave != w || e != cudaSuccess) continue;
@@ -192,18 +193,28 @@ hmv_status hmv_batch_create(int32_t count, const hmv_desc *descs, void *stream, 
         if (e == cudaSuccess) e = balloc(B, reinterpret_cast<void **>(&B->x_lvl[k]), mX);
         if (e == cudaSuccess) e = balloc(B, reinterpret_cast<void **>(&B->post[k]), mP);
     }
-    // waves: pairs in order, a new wave when the budget would be exceeded
+    // waves: the pairs of each leaf tile width in order (one leaf launch per
+    // wave, so one width per wave), a new wave when the budget would be exceeded
     std::vector<size_t> wave_size;
     for (int i = 0; i < count; ++i) {
-        hmv_plan_s *p = B->plans[i];
-        p->a_lvl[0] = B->a_lvl[0];
-        p->a_lvl[1] = B->a_lvl[1];
-        for (int r = 0; r < p->nrhs; ++r) {
-            const size_t sz = pair_bytes(p);
-            if (wave_size.empty() || (wave_size.back() + sz > wave_bytes && wave_size.back() > 0))
-                wave_size.push_back(0);
-            B->pairs.push_back(Pair{i, r, static_cast<int>(wave_size.size()) - 1, nullptr, nullptr, nullptr});
-            wave_size.back() += sz;
+        B->plans[i]->a_lvl[0] = B->a_lvl[0];
+        B->plans[i]->a_lvl[1] = B->a_lvl[1];
+    }
+    for (int tn : {256, 128}) {
+        bool fresh = true;
+        for (int i = 0; i < count; ++i) {
+            hmv_plan_s *p = B->plans[i];
+            if (p->tn != tn) continue;
+            for (int r = 0; r < p->nrhs; ++r) {
+                const size_t sz = pair_bytes(p);
+                if (fresh || (wave_size.back() + sz > wave_bytes && wave_size.back() > 0)) {
+                    wave_size.push_back(0);
+                    B->wave_tn.push_back(tn);
+                    fresh = false;
+                }
+                B->pairs.push_back(Pair{i, r, static_cast<int>(wave_size.size()) - 1, nullptr, nullptr, nullptr});
+                wave_size.back() += sz;
+            }
         }
     }
     B->nwaves = static_cast<int>(wave_size.size());
@@ -382,8 +393,6 @@ extern "C" hmv_status hmv_matvec_many(int32_t count, hmv_plan_t *const *plans, c
         plans[i]->stream = s;
     }
     cudaError_t e = leaf_tc_prepare();
-    std::vector<LeafProblem> probs;
-    std::vector<Tile> tiles;
     for (int i = 0; i < count && e == cudaSuccess; ++i) {
         hmv_plan_s *p = plans[i];
         const uint32_t *xl = xs[i].limbs;
@@ -401,27 +410,38 @@ extern "C" hmv_status hmv_matvec_many(int32_t count, hmv_plan_t *const *plans, c
         for (int l = 0; l < p->L && e == cudaSuccess; ++l)
             e = launch_prepass(p, l, false, p->x_lvl[l % 2], p->x_lvl[(l + 1) % 2]);
         if (e == cudaSuccess) e = launch_pack_vector(p, p->x_lvl[p->L % 2]);
-        const int idx = static_cast<int>(probs.size());
-        probs.push_back(p->hprob);
-        for (Tile t : p->tiles) {
-            t.prob = idx;
-            tiles.push_back(t);
+    }
+    // one persistent launch per tile width present (normally one)
+    for (int tn : {256, 128}) {
+        std::vector<LeafProblem> gp;
+        std::vector<Tile> gt;
+        for (int i = 0; i < count; ++i) {
+            if (plans[i]->tn != tn) continue;
+            const int idx = static_cast<int>(gp.size());
+            gp.push_back(plans[i]->hprob);
+            for (Tile t : plans[i]->tiles) {
+                t.prob = idx;
+                gt.push_back(t);
+            }
         }
+        if (gp.empty() || e != cudaSuccess) continue;
+        LeafProblem *dp = nullptr;
+        Tile *dt = nullptr;
+        e = cudaMallocAsync(reinterpret_cast<void **>(&dp), gp.size() * sizeof(LeafProblem), s);
+        if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&dt), gt.size() * sizeof(Tile), s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dp, gp.data(), gp.size() * sizeof(LeafProblem), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dt, gt.data(), gt.size() * sizeof(Tile), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) {
+            e = launch_leaf_tc_multi(dp, dt, static_cast<int>(gt.size()), plans[0]->dstat, plans[0]->d_counter, s,
+                                     plans[0]->num_sms, tn);
+            plans[0]->launches_leaf++;
+        }
+        // pageable host vectors: the copies above must finish before they go away
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (dp) cudaFreeAsync(dp, s);
+        if (dt) cudaFreeAsync(dt, s);
     }
-    LeafProblem *dp = nullptr;
-    Tile *dt = nullptr;
-    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&dp), probs.size() * sizeof(LeafProblem), s);
-    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&dt), tiles.size() * sizeof(Tile), s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(dp, probs.data(), probs.size() * sizeof(LeafProblem), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dt, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) {
-        e = launch_leaf_tc_multi(dp, dt, static_cast<int>(tiles.size()), plans[0]->dstat, plans[0]->d_counter, s,
-                                 plans[0]->num_sms);
-        plans[0]->launches_leaf++;
-    }
-    if (dp) cudaFreeAsync(dp, s);
-    if (dt) cudaFreeAsync(dt, s);
     for (int i = 0; i < count && e == cudaSuccess; ++i) {
         hmv_plan_s *p = plans[i];
         e = launch_leaf_normalize(p, p->post[p->L % 2]);

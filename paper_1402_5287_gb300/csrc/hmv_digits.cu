@@ -204,18 +204,18 @@ __global__ void k_pack_vector(const int8_t *__restrict__ leafd, int rowsX, const
 // ------------------------------------------------------------------ CUDA-core leaf
 // Same output as the tensor-core leaf: for tile (leaf, i0, ub) and row
 // i = i0 + blockIdx.y, the column sums Y[i][u] = sum_j sum_s a_{i+j}[s] x_j[u-s]
-// for u in [ub*TN, ub*TN+TN), normalised to digits in [0, 256) plus the
-// carry out of the block (floor of the block value / 256^TN).
+// for u in [ub*tn, ub*tn+tn), normalised to digits in [0, 256) plus the
+// carry out of the block (floor of the block value / 256^tn), tn <= TN.
 __global__ void k_leaf_simt(const int8_t *__restrict__ A, int rowsA, const int8_t *__restrict__ X, int rowsX,
                             const int *__restrict__ size, int Dp, int Dl, const Tile *__restrict__ tiles,
                             uint8_t *__restrict__ dig, int32_t *__restrict__ carry, int MT, int Uo, int NUB,
-                            int32_t *dstat) {
+                            int32_t *dstat, int tn) {
     const Tile tl = tiles[blockIdx.x];
     const int m = size[tl.leaf];
     const int i = tl.i0 + blockIdx.y;
     if (i >= m) return;
     __shared__ long long col[TN];
-    const int u = tl.ub * TN + threadIdx.x;
+    const int u = tl.ub * tn + threadIdx.x;
     long long acc = 0;
     const int s_lo = max(0, u - (Dl - 1)), s_hi = min(Dl - 1, u);
     for (int j = 0; j < m; ++j) {
@@ -229,8 +229,8 @@ __global__ void k_leaf_simt(const int8_t *__restrict__ A, int rowsA, const int8_
     __syncthreads();
     if (threadIdx.x == 0) {
         long long c = 0;
-        uint8_t *o = dig + (static_cast<size_t>(tl.leaf) * MT * TM + i) * Uo + tl.ub * TN;
-        for (int q = 0; q < TN; ++q) {
+        uint8_t *o = dig + (static_cast<size_t>(tl.leaf) * MT * TM + i) * Uo + tl.ub * tn;
+        for (int q = 0; q < tn; ++q) {
             long long t = col[q] + c;
             o[q] = static_cast<uint8_t>(t & 255);
             c = t >> 8;
@@ -245,7 +245,7 @@ __global__ void k_leaf_simt(const int8_t *__restrict__ A, int rowsA, const int8_
 // digit vector: out[u] in [0, 256) for u < Wo-1, out[Wo-1] holds the signed rest.
 __global__ void k_leaf_normalize(const uint8_t *__restrict__ dig, const int32_t *__restrict__ carry,
                                  const int *__restrict__ size, int nleaves, int MT, int Uo, int NUB,
-                                 int32_t *__restrict__ out, int rowsX, int Wo) {
+                                 int32_t *__restrict__ out, int rowsX, int Wo, int tn) {
     long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
     int leaf = static_cast<int>(idx / rowsX), row = static_cast<int>(idx % rowsX);
     if (leaf >= nleaves || row >= size[leaf]) return;
@@ -255,7 +255,7 @@ __global__ void k_leaf_normalize(const uint8_t *__restrict__ dig, const int32_t 
     int32_t *o = out + (static_cast<size_t>(leaf) * rowsX + row) * Wo;
     long long c = 0;
     for (int u0 = 0; u0 < Uo; u0 += 16) {
-        if (u0 > 0 && (u0 % TN) == 0) c += cy[u0 / TN - 1];
+        if (u0 > 0 && (u0 % tn) == 0) c += cy[u0 / tn - 1];
         uint4 v = *reinterpret_cast<const uint4 *>(d + u0);
         const uint32_t w[4] = {v.x, v.y, v.z, v.w};
         int res[16];
@@ -491,8 +491,9 @@ cudaError_t launch_pack_vector(hmv_plan_s *p, const int8_t *leaf_digits) {
 cudaError_t launch_leaf_simt(hmv_plan_s *p, const int8_t *a_leaf, const int8_t *x_leaf) {
     const LevelGeom &ll = p->lv[p->L];
     dim3 grid(p->ntiles, TM);
-    k_leaf_simt<<<grid, TN, 0, p->stream>>>(a_leaf, ll.rowsA, x_leaf, ll.rowsX, ll.d_size, p->Dp, p->Dl, p->d_tiles,
-                                            p->leaf_dig, p->leaf_carry, p->MT, p->Uo, p->NUB, p->dstat);
+    k_leaf_simt<<<grid, p->tn, 0, p->stream>>>(a_leaf, ll.rowsA, x_leaf, ll.rowsX, ll.d_size, p->Dp, p->Dl,
+                                               p->d_tiles, p->leaf_dig, p->leaf_carry, p->MT, p->Uo, p->NUB, p->dstat,
+                                               p->tn);
     p->launches_leaf++;
     p->launches_total++;
     return cudaGetLastError();
@@ -502,7 +503,7 @@ cudaError_t launch_leaf_normalize(hmv_plan_s *p, int32_t *out) {
     const LevelGeom &ll = p->lv[p->L];
     long long work = static_cast<long long>(ll.nodes) * ll.rowsX;
     k_leaf_normalize<<<blocks_for(work, 128), 128, 0, p->stream>>>(p->leaf_dig, p->leaf_carry, ll.d_size, ll.nodes,
-                                                                   p->MT, p->Uo, p->NUB, out, ll.rowsX, p->Wo);
+                                                                   p->MT, p->Uo, p->NUB, out, ll.rowsX, p->Wo, p->tn);
     p->launches_total++;
     return cudaGetLastError();
 }

@@ -10,22 +10,22 @@
 namespace hmv {
 
 // ---------------------------------------------------------------- geometry
-// Leaf contraction tile: TM leaf rows x TN output digits; each s-block holds
-// KS digits of the matrix operand; JC shifts j share one staged slab.
+// Leaf contraction tile: TM leaf rows x TN output digits (TN = 256, or 128
+// per plan: hmv_plan_s::tn); each s-block holds KS digits of the matrix
+// operand; JC shifts j share one staged slab.
 constexpr int TM = 128;
 constexpr int TN = 256;
 constexpr int KS = 128;
 constexpr int JC = 64;
 constexpr int AR = TM + JC;                   // rows of one staged Hankel slab
+static_assert(TM % 32 == 0 && JC % 32 == 0 && AR / 32 <= 256, "A slabs are whole 32-row groups");
 constexpr int A_BYTES = AR * KS * 2;          // bf16 slab bytes
-constexpr int NE = TN / 8 + KS / 8 - 1;       // core matrices of one shifted-x operand
-constexpr int B_BYTES = NE * 128;             // bf16 bytes of one shifted-x operand
 constexpr int A_STAGES = 2;
-constexpr int B_STAGES = 8;
 // j-steps per exact fp32 accumulation window: FLUSH_J * KS products of
 // magnitude <= 2^14 keep every partial sum within 2^24.
 constexpr int FLUSH_J = 1024 / KS;
 constexpr int EXTRA_DIGITS = 8;               // room above the leaf product for carries
+constexpr int TN_DEFAULT = 256;
 
 // Device error codes written to the plan's status word.
 enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BADINPUT = 2, DEV_OVERFLOW = 3 };
@@ -70,6 +70,7 @@ struct hmv_plan_s {
     int Wo = 0;                    // post-pass digit stride (multiple of 4)
     int ZW = 0;                    // limbs of the exact rows (Wo / 4)
     int MT = 0;                    // 128-row tiles per leaf
+    int tn = hmv::TN_DEFAULT;           // leaf tile width in product digits (256 or 128)
     std::vector<hmv::LevelGeom> lv;
     bool loaded = false;
     int e_h = 0;                   // exponent of the loaded matrix
@@ -161,7 +162,7 @@ cudaError_t split_post(hmv_plan_s *p, int rhs);
 cudaError_t launch_wrap_circulant(hmv_plan_s *p, const uint32_t *c_limbs, const uint8_t *c_neg);
 cudaError_t launch_leaf_tc(hmv_plan_s *p);
 cudaError_t launch_leaf_tc_multi(const LeafProblem *probs, const Tile *tiles, int ntiles, int32_t *dstat,
-                                 int *tile_counter, cudaStream_t stream, int num_sms);
+                                 int *tile_counter, cudaStream_t stream, int num_sms, int tn);
 cudaError_t encode_tensor_map_A(hmv_plan_s *p, CUtensorMap *map);
 cudaError_t encode_tensor_map_B(hmv_plan_s *p, uint16_t *xg, CUtensorMap *map);
 void fill_leaf_problem(hmv_plan_s *p, LeafProblem &lp);

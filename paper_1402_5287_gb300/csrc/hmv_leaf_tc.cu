@@ -42,17 +42,26 @@ constexpr int kEpiWarp0 = 2;
 constexpr int kNumEpiWarps = 4;
 constexpr int kThreads = (2 + kNumEpiWarps) * 32;
 constexpr uint64_t kTimeoutNs = 2000000000ull;  // 2 s for any single wait
-constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kIdesc = idesc_bf16_f32(TM, TN);
+// Tile width in product digits: 256 (one 128x256 MMA per k-step) or 128
+// (narrow operands, where the wide tile's triangular edges waste more).
+template <int TNv>
+struct Geo {
+    static constexpr int NEv = TNv / 8 + KS / 8 - 1;        // core matrices of one shifted-x operand
+    static constexpr int BB = NEv * 128;                    // its bytes
+    static constexpr int BS = TNv == 256 ? 8 : 16;          // B ring slots
+    static constexpr uint32_t kTmemCols = 2 * TNv;          // two accumulators
+    static constexpr uint32_t kIdesc = idesc_bf16_f32(TM, TNv);
+};
 constexpr uint32_t kLboA = AR * 16;  // K-direction core-matrix step of the slab
 constexpr int kTileQ = 4;            // tile indices handed from the producer to the consumers
 constexpr int kTileConsumers = 1 + kNumEpiWarps;
 
+template <int TNv>
 struct __align__(1024) Smem {
     uint8_t a[A_STAGES][A_BYTES];
-    uint8_t b[B_STAGES][B_BYTES];
+    uint8_t b[Geo<TNv>::BS][Geo<TNv>::BB];
     uint64_t a_full[A_STAGES], a_empty[A_STAGES];
-    uint64_t b_full[B_STAGES], b_empty[B_STAGES];
+    uint64_t b_full[Geo<TNv>::BS], b_empty[Geo<TNv>::BS];
     uint64_t acc_full[2], acc_empty[2];
     uint64_t tq_full[kTileQ], tq_empty[kTileQ];
     int tile_q[kTileQ];
@@ -66,6 +75,7 @@ struct TileInfo {
     int leaf, i0, ub, u0, m, s_base, nsb, njc, Q, Dl, Dp;
 };
 
+template <int TNv>
 __device__ __forceinline__ TileInfo decode(const Tile &t, const LeafProblem *probs) {
     TileInfo ti;
     ti.pr = probs + t.prob;
@@ -76,12 +86,12 @@ __device__ __forceinline__ TileInfo decode(const Tile &t, const LeafProblem *pro
     ti.leaf = t.leaf;
     ti.i0 = t.i0;
     ti.ub = t.ub;
-    ti.u0 = t.ub * TN;
+    ti.u0 = t.ub * TNv;
     ti.m = size[t.leaf];
     // s-blocks of KS digits start at the tile's first useful digit (rounded
     // down to 8 for the TMA coordinates), not at multiples of KS
     const int s_min = max(0, ti.u0 - (Dl - 1));
-    const int s_max = min(Dl - 1, ti.u0 + TN - 1);
+    const int s_max = min(Dl - 1, ti.u0 + TNv - 1);
     ti.s_base = s_min / 8 * 8;
     ti.nsb = (s_max >= s_min) ? (s_max - ti.s_base + KS) / KS : 0;
     ti.njc = (ti.m + JC - 1) / JC;
@@ -89,16 +99,22 @@ __device__ __forceinline__ TileInfo decode(const Tile &t, const LeafProblem *pro
     return ti;
 }
 
-__device__ __forceinline__ void fail(Smem &sm, int32_t *dstat) {
+template <class S>
+__device__ __forceinline__ void fail(S &sm, int32_t *dstat) {
     sm.abort = 1;
     atomicExch(dstat, DEV_TIMEOUT);
 }
 
+template <int TNv>
 __global__ void __launch_bounds__(kThreads, 1)
     k_leaf_tc(const LeafProblem *__restrict__ probs, const Tile *__restrict__ tiles, int ntiles, int *tile_counter,
               int32_t *dstat) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
+    using G = Geo<TNv>;
+    constexpr int B_STAGES = G::BS;
+    constexpr int B_BYTES = G::BB;
+    constexpr int TN = TNv;
+    Smem<TNv> &sm = *reinterpret_cast<Smem<TNv> *>(smem_raw);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
 
     if (threadIdx.x == 0) {
@@ -111,7 +127,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         fence_mbar_init();
     }
     if (warp == kMmaWarp) {
-        tmem_alloc(&sm.tmem_base, kTmemCols);
+        tmem_alloc(&sm.tmem_base, G::kTmemCols);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -131,7 +147,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 sm.tile_q[qs] = t;
                 mbar_arrive(&sm.tq_full[qs]);
                 if (t < 0) break;
-                const TileInfo ti = decode(tiles[t], probs);
+                const TileInfo ti = decode<TNv>(tiles[t], probs);
                 const CUtensorMap *mapA = &ti.pr->mapA;
                 const CUtensorMap *mapB = &ti.pr->mapB;
                 const int Dp = ti.Dp;
@@ -142,13 +158,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const int jn = min(JC, ti.m - j0);
                         if (!mbar_wait(&sm.a_empty[as], aph ^ 1, kTimeoutNs)) { fail(sm, dstat); break; }
                         mbar_arrive_expect_tx(&sm.a_full[as], A_BYTES);
-                        tma_load_4d(sm.a[as], mapA, &sm.a_full[as], 0, ti.i0 + j0, (Dp - s_lo - KS) / 8, ti.leaf);
+                        tma_load_4d(sm.a[as], mapA, &sm.a_full[as], 0, (ti.i0 + j0) / 32, (Dp - s_lo - KS) / 8,
+                                    ti.leaf);
                         if (++as == A_STAGES) { as = 0; aph ^= 1; }
                         for (int jj = 0; jj < jn; ++jj) {
                             if (!mbar_wait(&sm.b_empty[bs], bph ^ 1, kTimeoutNs)) { fail(sm, dstat); break; }
                             mbar_arrive_expect_tx(&sm.b_full[bs], B_BYTES);
-                            tma_load_5d(sm.b[bs], mapB, &sm.b_full[bs], 0, 0, (ti.u0 - s_lo - KS) / 8 + 1,
-                                        j0 + jj, ti.leaf);
+                            tma_load_4d(sm.b[bs], mapB, &sm.b_full[bs], 0, (ti.u0 - s_lo - KS) / 8 + 1, j0 + jj,
+                                        ti.leaf);
                             if (++bs == B_STAGES) { bs = 0; bph ^= 1; }
                         }
                     }
@@ -167,7 +184,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int t = sm.tile_q[qs];
                 mbar_arrive(&sm.tq_empty[qs]);
                 if (t < 0) break;
-                const TileInfo ti = decode(tiles[t], probs);
+                const TileInfo ti = decode<TNv>(tiles[t], probs);
                 int q = 0;
                 uint32_t acc_flag = 0;
                 for (int sb = 0; sb < ti.nsb && !sm.abort; ++sb) {
@@ -184,12 +201,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                             tc_fence_after();
                             const uint32_t b_base = b_base0 + bs * B_BYTES;
                             const uint32_t d_tmem = tmem + ab * TN;
-#pragma unroll
-                            for (int ks = 0; ks < KS / 16; ++ks) {
-                                const uint64_t ad = smem_desc(a_base + jj * 16 + ks * 2 * kLboA, kLboA, 128);
-                                const uint64_t bd = smem_desc(b_base + ks * 256, 128, 128);
-                                mma_bf16_ss(d_tmem, ad, bd, kIdesc, (acc_flag | ks) ? 1u : 0u);
-                            }
+                            // K = 16 steps: A two slab chunks on, B two core matrices on
+                            static_assert(KS == 128, "eight K = 16 MMAs per j-step");
+                            mma_bf16_ss_k128<2 * kLboA, 256>(d_tmem, smem_desc(a_base + jj * 16, kLboA, 128),
+                                                             smem_desc(b_base, 128, 128), G::kIdesc, acc_flag);
                             acc_flag = 1;
                             mma_commit(&sm.b_empty[bs]);
                             if (++bs == B_STAGES) { bs = 0; bph ^= 1; }
@@ -222,7 +237,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(&sm.tq_empty[qs]);
             if (t < 0) break;
-            const TileInfo ti = decode(tiles[t], probs);
+            const TileInfo ti = decode<TNv>(tiles[t], probs);
             const int G = (ti.Q + FLUSH_J - 1) / FLUSH_J;
             uint32_t st[TN / 4];
 #pragma unroll
@@ -282,41 +297,49 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncthreads();
     tc_fence_after();
-    if (warp == kMmaWarp) tmem_dealloc(tmem, kTmemCols);
+    if (warp == kMmaWarp) tmem_dealloc(tmem, G::kTmemCols);
 }
 
 }  // namespace
 
-size_t leaf_tc_smem_bytes() { return sizeof(Smem) + 1024; }
-
-cudaError_t leaf_tc_prepare() {
+template <int TNv>
+cudaError_t prepare_one() {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_leaf_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(sizeof(Smem)));
+        cudaError_t e = cudaFuncSetAttribute(k_leaf_tc<TNv>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(sizeof(Smem<TNv>)));
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     return cudaSuccess;
 }
 
+cudaError_t leaf_tc_prepare() {
+    cudaError_t e = prepare_one<256>();
+    if (e == cudaSuccess) e = prepare_one<128>();
+    return e;
+}
+
 cudaError_t launch_leaf_tc_multi(const LeafProblem *probs, const Tile *tiles, int ntiles, int32_t *dstat,
-                                 int *tile_counter, cudaStream_t stream, int num_sms) {
-    const size_t smem = sizeof(Smem);
+                                 int *tile_counter, cudaStream_t stream, int num_sms, int tn) {
     cudaError_t pe = leaf_tc_prepare();
     if (pe != cudaSuccess) return pe;
     const int grid = std::min(ntiles, num_sms);
     if (grid <= 0) return cudaSuccess;
     cudaError_t me = cudaMemsetAsync(tile_counter, 0, sizeof(int), stream);
     if (me != cudaSuccess) return me;
-    k_leaf_tc<<<grid, kThreads, smem, stream>>>(probs, tiles, ntiles, tile_counter, dstat);
+    if (tn == 128)
+        k_leaf_tc<128><<<grid, kThreads, sizeof(Smem<128>), stream>>>(probs, tiles, ntiles, tile_counter, dstat);
+    else
+        k_leaf_tc<256><<<grid, kThreads, sizeof(Smem<256>), stream>>>(probs, tiles, ntiles, tile_counter, dstat);
     return cudaGetLastError();
 }
 
 cudaError_t launch_leaf_tc(hmv_plan_s *p) {
     p->launches_leaf++;
     p->launches_total++;
-    return launch_leaf_tc_multi(p->d_prob, p->d_tiles, p->ntiles, p->dstat, p->d_counter, p->stream, p->num_sms);
+    return launch_leaf_tc_multi(p->d_prob, p->d_tiles, p->ntiles, p->dstat, p->d_counter, p->stream, p->num_sms,
+                                p->tn);
 }
 
 // ------------------------------------------------------------------ tensor maps
@@ -342,10 +365,13 @@ cudaError_t encode_tensor_map_A(hmv_plan_s *p, CUtensorMap *map) {
     if (!enc) return cudaErrorNotSupported;
     const int nleaves = p->lv[p->L].nodes;
     const cuuint64_t chunks = static_cast<cuuint64_t>(p->Dp / 8);
-    // hrev[leaf][chunk][RA][8] bf16 (packed): (8 digits, rows, chunks, leaf)
-    cuuint64_t dims[4] = {8, static_cast<cuuint64_t>(p->RA), chunks, static_cast<cuuint64_t>(nleaves)};
-    cuuint64_t strides[3] = {16, static_cast<cuuint64_t>(p->RA) * 16, chunks * p->RA * 16};
-    cuuint32_t box[4] = {8, static_cast<cuuint32_t>(AR), static_cast<cuuint32_t>(KS / 8), 1};
+    // hrev[leaf][chunk][RA][8] bf16 (packed), read as rows of 32 matrix rows
+    // (512 B): (256 elements, RA/32 row groups, chunks, leaf).  A box starts
+    // at row i0 + j0, a multiple of 32, so it is whole row groups, and it
+    // lands in shared memory in the same order as 8-element rows would.
+    cuuint64_t dims[4] = {256, static_cast<cuuint64_t>(p->RA / 32), chunks, static_cast<cuuint64_t>(nleaves)};
+    cuuint64_t strides[3] = {512, static_cast<cuuint64_t>(p->RA) * 16, chunks * p->RA * 16};
+    cuuint32_t box[4] = {256, static_cast<cuuint32_t>(AR / 32), static_cast<cuuint32_t>(KS / 8), 1};
     cuuint32_t es[4] = {1, 1, 1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, p->hrev, dims, strides, box, es,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -357,13 +383,14 @@ cudaError_t encode_tensor_map_B(hmv_plan_s *p, uint16_t *xg, CUtensorMap *map) {
     EncodeTiledFn enc = get_encode();
     if (!enc) return cudaErrorNotSupported;
     const int nleaves = p->lv[p->L].nodes;
-    // xg[leaf][RX][chunk][8][8] bf16 (packed): (8 digits, 8 copies, chunks, j, leaf)
+    // xg[leaf][RX][chunk][8][8] bf16 (packed), one 128-byte core matrix per
+    // row: (64 elements, chunks, j, leaf)
     const cuuint64_t xc = static_cast<cuuint64_t>(p->Dp / 8 + 1);
-    cuuint64_t dims[5] = {8, 8, xc, static_cast<cuuint64_t>(p->RX), static_cast<cuuint64_t>(nleaves)};
-    cuuint64_t strides[4] = {16, 128, xc * 128, static_cast<cuuint64_t>(p->RX) * xc * 128};
-    cuuint32_t box[5] = {8, 8, static_cast<cuuint32_t>(NE), 1, 1};
-    cuuint32_t es[5] = {1, 1, 1, 1, 1};
-    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, xg, dims, strides, box, es,
+    cuuint64_t dims[4] = {64, xc, static_cast<cuuint64_t>(p->RX), static_cast<cuuint64_t>(nleaves)};
+    cuuint64_t strides[3] = {128, xc * 128, static_cast<cuuint64_t>(p->RX) * xc * 128};
+    cuuint32_t box[4] = {64, static_cast<cuuint32_t>(p->tn / 8 + KS / 8 - 1), 1, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, xg, dims, strides, box, es,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;

@@ -134,6 +134,7 @@ hmv_status split_plan_create(hmv_plan_s *p, const hmv_desc &d, int digit_levels)
         cd.kind = HMV_HANKEL;       // the parent maps the kind onto the Hankel sequence
         cd.method = HMV_KARATSUBA;
         cd.flags &= ~(HMV_FLAG_TIMING | HMV_FLAG_DIGIT_SPLIT1 | HMV_FLAG_DIGIT_SPLIT2);
+        if (p->tn == 128) cd.flags |= HMV_FLAG_TILE128;
         if (digit_levels > 1) cd.flags |= HMV_FLAG_DIGIT_SPLIT1;
         cd.levels = -1;
         hmv_plan_s *c = nullptr;
@@ -226,8 +227,10 @@ cudaError_t split_leaf_launch(hmv_plan_s *p) {
         p->ntiles = static_cast<int>(tiles.size());
     }
     if (e == cudaSuccess) {
+        const hmv_plan_s *q = p;
+        while (!q->children.empty()) q = q->children[0];  // every unsplit descendant has the same width
         e = launch_leaf_tc_multi(p->split_probs, p->split_tiles, p->ntiles, p->dstat, p->d_counter, p->stream,
-                                 p->num_sms);
+                                 p->num_sms, q->tn);
         p->launches_leaf++;
         p->launches_total++;
     }

@@ -14,7 +14,7 @@ from .inputs import FixedVec
 
 HANKEL, TOEPLITZ, CIRCULANT = 0, 1, 2
 AUTO, SCHOOLBOOK, KARATSUBA, FFT64 = 0, 1, 2, 3
-FLAG_TIMING, FLAG_SIMT_LEAF, FLAG_DIGIT_SPLIT1, FLAG_DIGIT_SPLIT2 = 1, 2, 4, 8
+FLAG_TIMING, FLAG_SIMT_LEAF, FLAG_DIGIT_SPLIT1, FLAG_DIGIT_SPLIT2, FLAG_TILE128 = 1, 2, 4, 8, 16
 STATUS = {0: "HMV_OK", 1: "HMV_EINVAL", 2: "HMV_ENOMEM", 3: "HMV_ECUDA", 4: "HMV_ETIMEOUT",
           5: "HMV_ENOTLOADED", 6: "HMV_EFFTBOUND", 7: "HMV_EUNSUPPORTED"}
 
@@ -53,7 +53,8 @@ class Stats(ctypes.Structure):
                 ("launches_total", ctypes.c_int64), ("matvecs", ctypes.c_int64),
                 ("fft_piece_bits", ctypes.c_int32), ("fft_log2_len", ctypes.c_int32), ("fft_bound", ctypes.c_double),
                 ("fft_max_dist", ctypes.c_double), ("fft_matvecs", ctypes.c_int64),
-                ("fft_fallbacks", ctypes.c_int64), ("ms_fft", ctypes.c_double)]
+                ("fft_fallbacks", ctypes.c_int64), ("ms_fft", ctypes.c_double),
+                ("leaf_tile_digits", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -239,12 +240,12 @@ class Batch:
     CUDA graph launch per call (hmv_batch_*)."""
 
     def __init__(self, problems, stream=None, wave_bytes: int = 32 << 30):
-        """problems: list of dicts with n, b and optionally kind, nrhs, levels."""
+        """problems: list of dicts with n, b and optionally kind, nrhs, levels, flags."""
         self.lib = load_library()
-        self.problems = [{"kind": HANKEL, "nrhs": 1, "levels": -1, **pr} for pr in problems]
+        self.problems = [{"kind": HANKEL, "nrhs": 1, "levels": -1, "flags": 0, **pr} for pr in problems]
         arr = (Desc * len(problems))()
         for i, pr in enumerate(self.problems):
-            arr[i] = Desc(pr["n"], pr["b"], pr["nrhs"], pr["kind"], AUTO, pr["levels"], 0, 0)
+            arr[i] = Desc(pr["n"], pr["b"], pr["nrhs"], pr["kind"], AUTO, pr["levels"], pr["flags"], 0)
         handle = ctypes.c_void_p()
         s = ctypes.c_void_p(0 if stream is None else int(stream))
         _check(self.lib.hmv_batch_create(len(problems), arr, s, wave_bytes, ctypes.byref(handle)), "hmv_batch_create")

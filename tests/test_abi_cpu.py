@@ -73,4 +73,4 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(hmv.Desc) == 32
     assert ctypes.sizeof(hmv.Vec) == 40
     assert hmv.Vec.limbs.offset == 16 and hmv.Vec.neg.offset == 24 and hmv.Vec.on_device.offset == 32
-    assert ctypes.sizeof(hmv.Stats) == 4 * 4 + 8 + 8 * 2 + 8 + 8 * 5 + 8 * 3 + 4 * 2 + 8 * 5
+    assert ctypes.sizeof(hmv.Stats) == 4 * 4 + 8 + 8 * 2 + 8 + 8 * 5 + 8 * 3 + 4 * 2 + 8 * 5 + 4 * 2

@@ -34,11 +34,12 @@ def inputs(seed):
     return hs, xs
 
 
-def single(pr, h, x):
+def single(pr, h, x, stats=False):
     with hmv.Plan(pr["n"], pr["b"], kind=pr.get("kind", hmv.HANKEL), nrhs=pr["nrhs"],
                   levels=pr.get("levels", -1)) as p:
         p.load_matrix(h)
-        return p.matvec(x)
+        y = p.matvec(x)
+        return (y, p.stats()) if stats else y
 
 
 @pytest.mark.parametrize("wave_bytes", [1 << 34, 1])
@@ -55,10 +56,14 @@ def test_batch_equals_single_plans(wave_bytes):
         info2 = bt.info()
     npairs = sum(pr["nrhs"] for pr in PROBLEMS)
     assert info["pairs"] == npairs and info2["graph_launches"] == 2
-    assert info["waves"] == (1 if wave_bytes > 1 else npairs)
+    widths = set()
     for pr, h, x, y, x2, y2 in zip(PROBLEMS, hs, xs, ys, xs2, ys2):
-        assert_same(y, single(pr, h, x))
+        y1, st = single(pr, h, x, stats=True)
+        widths.add(st["leaf_tile_digits"])
+        assert_same(y, y1)
         assert_same(y2, single(pr, h, x2))
+    # one leaf launch per wave, so one tile width per wave
+    assert info["waves"] == (len(widths) if wave_bytes > 1 else npairs)
 
 
 def test_batch_against_oracle():

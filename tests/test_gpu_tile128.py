@@ -1,0 +1,143 @@
+"""Leaf tiles 128 product digits wide (HMV_FLAG_TILE128): bit-exact parity
+with the oracle on every row, alone and under the digit split, and equality
+with the 256-wide tiles in every entry point (single plan, batch, many)."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1402_5287_gb300 as pkg
+from paper_1402_5287_gb300 import hmv
+from paper_1402_5287_gb300.inputs import FixedVec, uniform_vec, workload
+
+from test_gpu_parity import assert_same, oracle_matvec, sampled_parity
+
+pytestmark = pytest.mark.gpu
+
+T128 = hmv.FLAG_TILE128
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    pkg.build()
+    hmv.load_library()
+
+
+def run(n, b, h, x, flags=0, kind=hmv.HANKEL, method=hmv.KARATSUBA, levels=-1, nrhs=1):
+    with hmv.Plan(n, b, kind=kind, method=method, levels=levels, flags=flags, nrhs=nrhs) as p:
+        p.load_matrix(h)
+        return p.matvec(x), p.stats()
+
+
+# sizes: one tile, several tiles with a ragged tail in both dimensions, the
+# narrowest digit counts (b = 1, 33) and digit counts just past a tile edge
+@pytest.mark.parametrize("n,b,levels", [(64, 2048, 1), (129, 1000, 2), (7, 33, 0), (30, 1, 0), (200, 520, 3),
+                                        (1, 64, 0), (45, 4100, 2), (300, 264, -1)])
+def test_tile128_all_rows(n, b, levels):
+    h = uniform_vec(80 + n, 0, 2 * n - 1, b, 2)
+    x = uniform_vec(80 + n, 1, n, b, -3)
+    y, st = run(n, b, h, x, flags=T128, levels=levels)
+    assert_same(y, oracle_matvec(oracle.HANKEL, n, h, x))
+    y256, _ = run(n, b, h, x, levels=levels)
+    assert_same(y, y256)
+
+
+@pytest.mark.parametrize("kind", [hmv.TOEPLITZ, hmv.CIRCULANT])
+def test_tile128_toeplitz_circulant(kind):
+    n, b = 110, 900
+    hlen = n if kind == hmv.CIRCULANT else 2 * n - 1
+    h = uniform_vec(91, 0, hlen, b)
+    x = uniform_vec(91, 1, n, b)
+    ok = oracle.TOEPLITZ if kind == hmv.TOEPLITZ else oracle.CIRCULANT
+    y, _ = run(n, b, h, x, flags=T128, kind=kind, levels=2)
+    assert_same(y, oracle_matvec(ok, n, h, x))
+
+
+def test_tile128_block_rhs():
+    n, b, k = 50, 700, 3
+    h = uniform_vec(93, 0, 2 * n - 1, b)
+    x = uniform_vec(93, 1, n * k, b)
+    y, _ = run(n, b, h, x, flags=T128, nrhs=k, levels=1)
+    y256, _ = run(n, b, h, x, nrhs=k, levels=1)
+    assert_same(y, y256)
+
+
+def test_tile128_worst_case_digits():
+    """All-(-128) balanced digits: every product +2^14, full windows 2^24."""
+    n, b = 80, 2046
+    m = int("80" * ((b + 7) // 8), 16) & ((1 << b) - 1)
+    h = FixedVec.from_ints([-m] * (2 * n - 1), b, 0)
+    x = FixedVec.from_ints([-m] * n, b, 0)
+    want = oracle_matvec(oracle.HANKEL, n, h, x)
+    assert_same(run(n, b, h, x, flags=T128, levels=0)[0], want)
+    assert_same(run(n, b, h, x, flags=T128, levels=2)[0], want)
+
+
+@pytest.mark.parametrize("split", [hmv.FLAG_DIGIT_SPLIT1, hmv.FLAG_DIGIT_SPLIT2])
+def test_tile128_under_digit_split(split):
+    n, b = 100, 4100
+    h = uniform_vec(95, 0, 2 * n - 1, b, 1)
+    x = uniform_vec(95, 1, n, b, -1)
+    y, _ = run(n, b, h, x, flags=T128 | split, method=hmv.AUTO)
+    assert_same(y, oracle_matvec(oracle.HANKEL, n, h, x))
+
+
+def test_tile128_batch_and_many_mixed_widths():
+    problems = [dict(n=40, b=1500, nrhs=2), dict(n=90, b=600, nrhs=1, flags=T128),
+                dict(n=33, b=2100, nrhs=1, flags=T128, kind=hmv.TOEPLITZ), dict(n=20, b=300, nrhs=1)]
+    hs, xs = [], []
+    for i, pr in enumerate(problems):
+        hs.append(uniform_vec(97 + i, 0, 2 * pr["n"] - 1, pr["b"]))
+        xs.append(uniform_vec(97 + i, 1, pr["n"] * pr["nrhs"], pr["b"]))
+    with hmv.Batch(problems) as bt:
+        for i, h in enumerate(hs):
+            bt.load_matrix(i, h)
+        ys = bt.matvec(xs)
+    for pr, h, x, y in zip(problems, hs, xs, ys):
+        want, _ = run(pr["n"], pr["b"], h, x, kind=pr.get("kind", hmv.HANKEL), nrhs=pr["nrhs"])
+        assert_same(y, want)
+    # hmv_matvec_many: one product per plan, the two widths in one step
+    import torch
+    dev = torch.device("cuda", 0)
+    plans, xp, yp, keep, exps = [], [], [], [], []
+    singles = [pr for pr in problems if pr["nrhs"] == 1]
+    for i, pr in enumerate(problems):
+        if pr["nrhs"] != 1:
+            continue
+        p = hmv.Plan(pr["n"], pr["b"], kind=pr.get("kind", hmv.HANKEL), method=hmv.KARATSUBA,
+                     flags=pr.get("flags", 0))
+        p.load_matrix(hs[i])
+        xl = torch.from_numpy(xs[i].limbs.view(np.int32)).to(dev)
+        xn = torch.from_numpy(xs[i].neg).to(dev)
+        yl, yn = torch.empty_like(xl), torch.empty_like(xn)
+        keep.append((i, xl, xn, yl, yn))
+        plans.append(p)
+        xp.append((xl.data_ptr(), xn.data_ptr()))
+        yp.append((yl.data_ptr(), yn.data_ptr()))
+        exps.append(xs[i].exponent)
+    out = hmv.matvec_many_device(plans, xp, yp, exps)
+    torch.cuda.synchronize()
+    assert len(singles) == len(plans)
+    for (i, xl, xn, yl, yn), e in zip(keep, out):
+        y = FixedVec(yl.cpu().numpy().view(np.uint32), yn.cpu().numpy(), problems[i]["b"], e)
+        assert_same(y, ys[i])
+    for p in plans:
+        p.close()
+
+
+def test_tile128_large_workload_matches_default():
+    n, b, h, x = workload("large")
+    y0, _ = run(n, b, h, x, method=hmv.AUTO)
+    y, st = run(n, b, h, x, flags=T128, method=hmv.AUTO)
+    assert_same(y, y0)
+    sampled_parity(oracle.HANKEL, n, h, x, y, 3, 11)
+
+
+@pytest.mark.parametrize("n,b,want", [(300, 256, 128), (300, 64, 128), (200, 4096, 256), (120, 1024, 256)])
+def test_auto_chooses_tile_width_and_stays_exact(n, b, want):
+    """HMV_AUTO takes 128-wide tiles only where they cut the padded product
+    digits enough (short mantissas); either way the result is exact."""
+    h = uniform_vec(99 + b, 0, 2 * n - 1, b, 1)
+    x = uniform_vec(99 + b, 1, n, b, 2)
+    y, st = run(n, b, h, x, method=hmv.AUTO)
+    assert st["leaf_tile_digits"] == want
+    assert_same(y, oracle_matvec(oracle.HANKEL, n, h, x))
