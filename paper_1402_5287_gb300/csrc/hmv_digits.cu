@@ -176,29 +176,44 @@ __global__ void k_pack_matrix(const int8_t *__restrict__ leafd, int rowsA, const
 // (zero outside [0, Dp) and for j >= size).  Block e is the core matrix of
 // every (n-group g, k-group c) with g + c = e - e0 of the digit-Toeplitz
 // operand whose window starts at chunk e0.
-__global__ void k_pack_vector(const int8_t *__restrict__ leafd, int rowsX, const int *__restrict__ size,
-                              uint16_t *__restrict__ xg, int RX, int Dp, int nleaves) {
-    long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+// One block per (leaf, j, segment of at most kPackSeg chunks): the segment's
+// digits are staged once in shared memory, and each thread builds 16-byte
+// rows from two aligned 8-byte words (consecutive threads store consecutive
+// rows).
+constexpr int kPackSeg = 128;
+__global__ void __launch_bounds__(128) k_pack_vector(const int8_t *__restrict__ leafd, int rowsX,
+                                                     const int *__restrict__ size, uint16_t *__restrict__ xg, int RX,
+                                                     int Dp, int seg) {
+    __shared__ __align__(16) uint64_t s[kPackSeg + 2];
+    const int leaf = blockIdx.x / RX, j = blockIdx.x % RX;
     const int chunks = Dp / 8 + 1;
-    long long per_leaf = static_cast<long long>(RX) * chunks * 8;
-    int leaf = static_cast<int>(idx / per_leaf);
-    if (leaf >= nleaves) return;
-    long long rem = idx % per_leaf;
-    int j = static_cast<int>(rem / (8 * chunks));
-    int e = static_cast<int>((rem / 8) % chunks);
-    int r = static_cast<int>(rem % 8);
-    uint16_t v[8];
+    const int e0 = blockIdx.y * seg;
+    const int ne = min(seg, chunks - e0);
     const bool live = j < size[leaf];
     const int8_t *row = leafd + (static_cast<size_t>(leaf) * rowsX + j) * Dp;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        int u = 8 * e + r + i - 7;
-        int d = (live && u >= 0 && u < Dp) ? static_cast<int>(row[u]) : 0;
-        v[i] = bf16_bits_of_small_int(d);
+    // s word t holds digits base + 8t .. base + 8t + 7 (zero outside [0, Dp))
+    const int base = 8 * e0 - 8;
+    for (int t = threadIdx.x; t < ne + 2; t += blockDim.x) {
+        const int u = base + 8 * t;  // Dp and u are multiples of 8
+        s[t] = (live && u >= 0 && u < Dp) ? *reinterpret_cast<const uint64_t *>(row + u) : 0ull;
     }
-    uint4 pk = make_uint4(v[0] | (uint32_t(v[1]) << 16), v[2] | (uint32_t(v[3]) << 16), v[4] | (uint32_t(v[5]) << 16),
-                          v[6] | (uint32_t(v[7]) << 16));
-    *reinterpret_cast<uint4 *>(xg + (((static_cast<size_t>(leaf) * RX + j) * chunks + e) * 8 + r) * 8) = pk;
+    __syncthreads();
+    uint4 *out = reinterpret_cast<uint4 *>(xg + ((static_cast<size_t>(leaf) * RX + j) * chunks + e0) * 64);
+    for (int q = threadIdx.x; q < 8 * ne; q += blockDim.x) {
+        const int el = q >> 3, r = q & 7;
+        // digits 8(e0+el) + r - 7 + i (i = 0..7) are bytes r+1 .. r+8 of words el, el+1
+        const uint64_t lo = s[el], hi = s[el + 1];
+        const int sh = 8 * (r + 1);
+        const uint64_t w = (sh == 64) ? hi : ((lo >> sh) | (hi << (64 - sh)));
+        uint32_t pk[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int d0 = static_cast<int8_t>((w >> (16 * h)) & 0xFFu);
+            const int d1 = static_cast<int8_t>((w >> (16 * h + 8)) & 0xFFu);
+            pk[h] = bf16_bits_of_small_int(d0) | (static_cast<uint32_t>(bf16_bits_of_small_int(d1)) << 16);
+        }
+        out[q] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
 }
 
 // ------------------------------------------------------------------ CUDA-core leaf
@@ -242,39 +257,37 @@ __global__ void k_leaf_simt(const int8_t *__restrict__ A, int rowsA, const int8_
 
 // ------------------------------------------------------------------ leaf normalise
 // Joins the per-block digits and block carries of one leaf row into one
-// digit vector: out[u] in [0, 256) for u < Wo-1, out[Wo-1] holds the signed rest.
+// carry-save digit vector with small digits, elementwise: out[u] = dig[u] for
+// u < Uo, plus the carry out of block t (a signed 32-bit integer) spread over
+// digits (t+1)*tn .. (t+1)*tn + 3 as three base-256 digits and a signed top
+// part; out[Uo+4 .. Wo) = 0.  Every digit is then within [-128, 510], so L
+// levels of the post-pass keep them within 510 * 2^L; the final normalise
+// propagates all carries.  One block per leaf row.
 __global__ void k_leaf_normalize(const uint8_t *__restrict__ dig, const int32_t *__restrict__ carry,
-                                 const int *__restrict__ size, int nleaves, int MT, int Uo, int NUB,
-                                 int32_t *__restrict__ out, int rowsX, int Wo, int tn) {
-    long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-    int leaf = static_cast<int>(idx / rowsX), row = static_cast<int>(idx % rowsX);
-    if (leaf >= nleaves || row >= size[leaf]) return;
+                                 const int *__restrict__ size, int MT, int Uo, int NUB, int32_t *__restrict__ out,
+                                 int rowsX, int Wo, int tn) {
+    const int leaf = blockIdx.x / rowsX, row = blockIdx.x % rowsX;
+    if (row >= size[leaf]) return;
     const size_t r = static_cast<size_t>(leaf) * MT * TM + row;
-    const uint8_t *d = dig + r * Uo;
+    const uint32_t *d = reinterpret_cast<const uint32_t *>(dig + r * Uo);
     const int32_t *cy = carry + r * NUB;
-    int32_t *o = out + (static_cast<size_t>(leaf) * rowsX + row) * Wo;
-    long long c = 0;
-    for (int u0 = 0; u0 < Uo; u0 += 16) {
-        if (u0 > 0 && (u0 % tn) == 0) c += cy[u0 / tn - 1];
-        uint4 v = *reinterpret_cast<const uint4 *>(d + u0);
-        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-        int res[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            long long t = static_cast<long long>((w[q / 4] >> (8 * (q % 4))) & 0xFFu) + c;
-            res[q] = static_cast<int>(t & 255);
-            c = t >> 8;
+    int4 *o = reinterpret_cast<int4 *>(out + (static_cast<size_t>(leaf) * rowsX + row) * Wo);
+    for (int g = threadIdx.x; g < Wo / 4; g += blockDim.x) {
+        const int u0 = 4 * g;
+        int4 v = make_int4(0, 0, 0, 0);
+        if (u0 < Uo) {
+            const uint32_t w = d[g];
+            v = make_int4(w & 0xFF, (w >> 8) & 0xFF, (w >> 16) & 0xFF, w >> 24);
         }
-#pragma unroll
-        for (int q = 0; q < 16; q += 4)
-            *reinterpret_cast<int4 *>(o + u0 + q) = make_int4(res[q], res[q + 1], res[q + 2], res[q + 3]);
+        if (u0 > 0 && u0 <= Uo && u0 % tn == 0) {
+            const int32_t c = cy[u0 / tn - 1];
+            v.x += c & 0xFF;
+            v.y += (c >> 8) & 0xFF;
+            v.z += (c >> 16) & 0xFF;
+            v.w += c >> 24;  // arithmetic shift: the signed top part
+        }
+        o[g] = v;
     }
-    c += cy[NUB - 1];
-    for (int u = Uo; u < Wo - 1; ++u) {
-        o[u] = static_cast<int>(c & 255);
-        c >>= 8;
-    }
-    o[Wo - 1] = static_cast<int>(c);
 }
 
 // ------------------------------------------------------------------ post-pass
@@ -481,9 +494,11 @@ cudaError_t launch_pack_matrix(hmv_plan_s *p, const int8_t *leaf_digits) {
 
 cudaError_t launch_pack_vector(hmv_plan_s *p, const int8_t *leaf_digits) {
     const LevelGeom &ll = p->lv[p->L];
-    long long work = static_cast<long long>(ll.nodes) * p->RX * 8 * (p->Dp / 8 + 1);
-    k_pack_vector<<<blocks_for(work), kThreads, 0, p->stream>>>(leaf_digits, ll.rowsX, ll.d_size, p->xg, p->RX,
-                                                                p->Dp, ll.nodes);
+    const int chunks = p->Dp / 8 + 1;
+    const int nseg = (chunks + kPackSeg - 1) / kPackSeg;
+    const int seg = (chunks + nseg - 1) / nseg;  // balanced segments of at most kPackSeg chunks
+    const dim3 grid(static_cast<unsigned>(ll.nodes) * p->RX, nseg);
+    k_pack_vector<<<grid, 128, 0, p->stream>>>(leaf_digits, ll.rowsX, ll.d_size, p->xg, p->RX, p->Dp, seg);
     p->launches_total++;
     return cudaGetLastError();
 }
@@ -501,9 +516,8 @@ cudaError_t launch_leaf_simt(hmv_plan_s *p, const int8_t *a_leaf, const int8_t *
 
 cudaError_t launch_leaf_normalize(hmv_plan_s *p, int32_t *out) {
     const LevelGeom &ll = p->lv[p->L];
-    long long work = static_cast<long long>(ll.nodes) * ll.rowsX;
-    k_leaf_normalize<<<blocks_for(work, 128), 128, 0, p->stream>>>(p->leaf_dig, p->leaf_carry, ll.d_size, ll.nodes,
-                                                                   p->MT, p->Uo, p->NUB, out, ll.rowsX, p->Wo, p->tn);
+    k_leaf_normalize<<<static_cast<unsigned>(ll.nodes) * ll.rowsX, 128, 0, p->stream>>>(
+        p->leaf_dig, p->leaf_carry, ll.d_size, p->MT, p->Uo, p->NUB, out, ll.rowsX, p->Wo, p->tn);
     p->launches_total++;
     return cudaGetLastError();
 }
