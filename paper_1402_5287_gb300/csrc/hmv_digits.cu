@@ -32,47 +32,98 @@ __device__ __forceinline__ uint16_t bf16_bits_of_small_int(int v) {
     return static_cast<uint16_t>(__float_as_uint(static_cast<float>(v)) >> 16);
 }
 
+// Renormalisation of one window of 32 x kDigitsPerLane digits, held
+// kDigitsPerLane per lane (lane l: window digits kDigitsPerLane*l ..), to
+// balanced digits in [-128, 127] (kBalanced) or digits in [0, 256).  Each lane
+// runs a local carry chain, then the carries leaving the lanes are passed up
+// by one lane and absorbed until none is left: after round r only lanes
+// above r can hold a new carry, so at most 32 rounds.  wcarry: the carry into
+// lane 0 on entry, the carry out of lane 31 on return (all lanes).
+constexpr int kDigitsPerLane = 32;
+template <bool kBalanced>
+__device__ __forceinline__ int norm_digit(int t, int &carry) {
+    if (kBalanced) return balance(t, carry);
+    carry = t >> 8;  // floor division by 256
+    return t & 255;
+}
+template <bool kBalanced>
+__device__ __forceinline__ void warp_carry(int (&d)[kDigitsPerLane], int lane, int &wcarry) {
+    int c = (lane == 0) ? wcarry : 0;
+#pragma unroll
+    for (int q = 0; q < kDigitsPerLane; ++q) d[q] = norm_digit<kBalanced>(d[q] + c, c);
+    int pending = c, out = 0;
+    for (int round = 0; round <= 32; ++round) {
+        out += __shfl_sync(0xffffffffu, pending, 31);
+        int incoming = __shfl_up_sync(0xffffffffu, pending, 1);
+        if (lane == 0) incoming = 0;
+        if (!__any_sync(0xffffffffu, incoming != 0)) break;
+        c = incoming;
+#pragma unroll
+        for (int q = 0; q < kDigitsPerLane; ++q) d[q] = norm_digit<kBalanced>(d[q] + c, c);
+        pending = c;
+    }
+    wcarry = out;
+}
+__device__ __forceinline__ void warp_balance(int (&d)[kDigitsPerLane], int lane, int &wcarry) {
+    warp_carry<true>(d, lane, wcarry);
+}
+
+// Store a lane's digits [ub, ub + kDigitsPerLane) of a Dp-digit int8 row;
+// digits at or past Dp must be zero (else the row overflowed).
+__device__ __forceinline__ void store_lane_digits(const int (&d)[kDigitsPerLane], int ub, int Dp, int8_t *o,
+                                                  int32_t *dstat) {
+#pragma unroll
+    for (int q = 0; q < kDigitsPerLane; ++q)
+        if (ub + q >= Dp && d[q] != 0) atomicExch(dstat, DEV_OVERFLOW);
+#pragma unroll
+    for (int h = 0; h < kDigitsPerLane / 16; ++h) {
+        const int uh = ub + 16 * h;  // Dp is a multiple of 16
+        if (uh >= Dp) break;
+        uint32_t pk[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            pk[q] = (static_cast<uint32_t>(d[16 * h + 4 * q]) & 0xFFu) |
+                    ((static_cast<uint32_t>(d[16 * h + 4 * q + 1]) & 0xFFu) << 8) |
+                    ((static_cast<uint32_t>(d[16 * h + 4 * q + 2]) & 0xFFu) << 16) |
+                    ((static_cast<uint32_t>(d[16 * h + 4 * q + 3]) & 0xFFu) << 24);
+        *reinterpret_cast<uint4 *>(o + uh) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+}
+
 // ------------------------------------------------------------------ encode
 // Sign-magnitude limbs -> balanced digits (the number representation of
 // Sec. 2, a = sum_k B^k a_k, with base B = 2^8 and signed digits).
 // circ_n > 0: row k takes entry (circ_n - 1 - k) mod circ_n (circulant ->
 // Toeplitz sequence); otherwise row k takes entry k.
-__global__ void k_encode(const uint32_t *__restrict__ limbs, const uint8_t *__restrict__ neg, int rows, int L32,
-                         int b, int circ_n, int8_t *__restrict__ out, int Dp, int32_t *dstat) {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= rows) return;
+// One warp per row, windows of 32 x kDigitsPerLane digits (8 limbs per lane).
+__global__ void __launch_bounds__(256) k_encode(const uint32_t *__restrict__ limbs, const uint8_t *__restrict__ neg,
+                                                int rows, int L32, int b, int circ_n, int8_t *__restrict__ out, int Dp,
+                                                int32_t *dstat) {
+    const int lane = threadIdx.x & 31;
+    const int k = static_cast<int>((static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
+    if (k >= rows) return;  // warp-uniform
     int src = k;
     if (circ_n > 0) src = ((circ_n - 1 - k) % circ_n + circ_n) % circ_n;
     const uint32_t *m = limbs + static_cast<size_t>(src) * L32;
     const int topbits = b - 32 * (L32 - 1);
-    if (topbits < 32 && (m[L32 - 1] >> topbits) != 0) atomicExch(dstat, DEV_BADINPUT);
+    if (lane == 0 && topbits < 32 && (m[L32 - 1] >> topbits) != 0) atomicExch(dstat, DEV_BADINPUT);
     const int sgn = neg[src] ? -1 : 1;
     int8_t *o = out + static_cast<size_t>(k) * Dp;
-    int carry = 0;
-    for (int u0 = 0; u0 < Dp; u0 += 16) {
-        uint32_t w[4];
+    int wcarry = 0;
+    for (int u0 = 0; u0 < Dp; u0 += 32 * kDigitsPerLane) {
+        const int ub = u0 + kDigitsPerLane * lane;
+        int d[kDigitsPerLane];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            int li = u0 / 4 + q;
-            w[q] = (li < L32) ? m[li] : 0u;
+        for (int q = 0; q < kDigitsPerLane / 4; ++q) {
+            const int li = ub / 4 + q;
+            const uint32_t w = (li < L32) ? m[li] : 0u;
+#pragma unroll
+            for (int by = 0; by < 4; ++by) d[4 * q + by] = sgn * static_cast<int>((w >> (8 * by)) & 0xFFu);
         }
-        uint32_t packed[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            uint32_t pk = 0;
-#pragma unroll
-            for (int by = 0; by < 4; ++by) {
-                int byte = static_cast<int>((w[q] >> (8 * by)) & 0xFFu);
-                int c2;
-                int d = balance(sgn * byte + carry, c2);
-                carry = c2;
-                pk |= (static_cast<uint32_t>(d) & 0xFFu) << (8 * by);
-            }
-            packed[q] = pk;
-        }
-        *reinterpret_cast<uint4 *>(o + u0) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        warp_balance(d, lane, wcarry);
+        store_lane_digits(d, ub, Dp, o, dstat);
     }
-    if (carry != 0) atomicExch(dstat, DEV_OVERFLOW);
+    if (lane == 0 && wcarry != 0) atomicExch(dstat, DEV_OVERFLOW);
 }
 
 // ------------------------------------------------------------------ pre-pass
@@ -82,12 +133,20 @@ __global__ void k_encode(const uint32_t *__restrict__ limbs, const uint8_t *__re
 //   matrix side  c_k = a_{2k} + a_{2k+1},  d_k = a_{2k+1},  e_k = a_{2k}
 //   vector side  h_k = x_{2k},  f_k = x_{2k} - x_{2k+1},  g_k = x_{2k-1} - x_{2k}
 // with a_q = 0 for q >= 2s-1 and x_q = 0 for q < 0 or q >= s.
-__global__ void k_prepass(const int8_t *__restrict__ in, int in_rows, const int *__restrict__ in_size,
-                          int8_t *__restrict__ out, int out_rows, const int *__restrict__ out_size, int nchildren,
-                          int Dp, int matrix_side, int32_t *dstat) {
-    long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-    int child = static_cast<int>(idx / out_rows);
-    int k = static_cast<int>(idx % out_rows);
+// One thread per child row, 64 digits per step; the next step's 64-byte
+// slices of both parent rows are loaded before this step's carry chain runs,
+// so the chain (carries in {-1, 0, 1}) never waits on memory.
+__device__ __forceinline__ void load_slice64(const int8_t *r, bool on, int u, int Dp, uint4 (&v)[4]) {
+#pragma unroll
+    for (int h = 0; h < 4; ++h)
+        v[h] = (on && u + 16 * h < Dp) ? *reinterpret_cast<const uint4 *>(r + u + 16 * h) : make_uint4(0, 0, 0, 0);
+}
+__global__ void __launch_bounds__(128) k_prepass(const int8_t *__restrict__ in, int in_rows,
+                                                 const int *__restrict__ in_size, int8_t *__restrict__ out,
+                                                 int out_rows, const int *__restrict__ out_size, int nchildren, int Dp,
+                                                 int matrix_side, int32_t *dstat) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    const int child = w / out_rows, k = w % out_rows;
     if (child >= nchildren) return;
     const int parent = child / 3, t = child % 3;
     const int s = in_size[parent];
@@ -110,28 +169,36 @@ __global__ void k_prepass(const int8_t *__restrict__ in, int in_rows, const int 
     const int8_t *r1 = in + (static_cast<size_t>(parent) * in_rows + (s1 ? q1 : 0)) * Dp;
     const int8_t *r2 = in + (static_cast<size_t>(parent) * in_rows + (s2 ? q2 : 0)) * Dp;
     int8_t *o = out + (static_cast<size_t>(child) * out_rows + k) * Dp;
+    uint4 n1[4], n2[4];
+    load_slice64(r1, s1 != 0, 0, Dp, n1);
+    load_slice64(r2, s2 != 0, 0, Dp, n2);
     int carry = 0;
-    for (int u0 = 0; u0 < Dp; u0 += 16) {
-        uint4 v1 = s1 ? *reinterpret_cast<const uint4 *>(r1 + u0) : make_uint4(0, 0, 0, 0);
-        uint4 v2 = s2 ? *reinterpret_cast<const uint4 *>(r2 + u0) : make_uint4(0, 0, 0, 0);
-        const uint32_t a1[4] = {v1.x, v1.y, v1.z, v1.w};
-        const uint32_t a2[4] = {v2.x, v2.y, v2.z, v2.w};
-        uint32_t packed[4];
+    for (int u0 = 0; u0 < Dp; u0 += 64) {
+        uint4 v1[4], v2[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            uint32_t pk = 0;
+        for (int h = 0; h < 4; ++h) { v1[h] = n1[h]; v2[h] = n2[h]; }
+        load_slice64(r1, s1 != 0, u0 + 64, Dp, n1);
+        load_slice64(r2, s2 != 0, u0 + 64, Dp, n2);
 #pragma unroll
-            for (int by = 0; by < 4; ++by) {
-                int d1 = static_cast<int8_t>((a1[q] >> (8 * by)) & 0xFFu);
-                int d2 = static_cast<int8_t>((a2[q] >> (8 * by)) & 0xFFu);
-                int c2;
-                int d = balance(s1 * d1 + s2 * d2 + carry, c2);
-                carry = c2;
-                pk |= (static_cast<uint32_t>(d) & 0xFFu) << (8 * by);
+        for (int h = 0; h < 4; ++h) {
+            if (u0 + 16 * h >= Dp) break;  // Dp is a multiple of 16
+            const uint32_t a1[4] = {v1[h].x, v1[h].y, v1[h].z, v1[h].w};
+            const uint32_t a2[4] = {v2[h].x, v2[h].y, v2[h].z, v2[h].w};
+            uint32_t packed[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t pk = 0;
+#pragma unroll
+                for (int by = 0; by < 4; ++by) {
+                    const int d1 = static_cast<int8_t>((a1[q] >> (8 * by)) & 0xFFu);
+                    const int d2 = static_cast<int8_t>((a2[q] >> (8 * by)) & 0xFFu);
+                    const int d = balance(s1 * d1 + s2 * d2 + carry, carry);
+                    pk |= (static_cast<uint32_t>(d) & 0xFFu) << (8 * by);
+                }
+                packed[q] = pk;
             }
-            packed[q] = pk;
+            *reinterpret_cast<uint4 *>(o + u0 + 16 * h) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
         }
-        *reinterpret_cast<uint4 *>(o + u0) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
     }
     if (carry != 0) atomicExch(dstat, DEV_OVERFLOW);
 }
@@ -314,38 +381,68 @@ __global__ void k_postpass(const int32_t *__restrict__ in, int rows_in, int32_t 
 }
 
 // ------------------------------------------------------------------ final normalise
-// Row digit vector (int32 digits, radix 256) -> |Z| as 32-bit limbs, sign, bit length.
-__global__ void k_final_normalize(const int32_t *__restrict__ in, int n, int Wo, uint32_t *__restrict__ zmag,
-                                  uint8_t *__restrict__ zneg, int32_t *__restrict__ zbits, int ZW, int32_t *dstat,
-                                  int row_offset) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int32_t *d = in + static_cast<size_t>(i) * Wo;
-    long long c = 0;
-    for (int u = 0; u < Wo; ++u) c = (static_cast<long long>(d[u]) + c) >> 8;
-    const int sgn = (c < 0) ? -1 : 1;
-    if (c > 0 || c < -1) atomicExch(dstat, DEV_OVERFLOW);
-    c = 0;
-    uint32_t *z = zmag + static_cast<size_t>(row_offset + i) * ZW;
-    int top = -1;
-    uint32_t topv = 0;
-    for (int w = 0; w < ZW; ++w) {
-        uint32_t limb = 0;
+// Row digit vector (int32 digits, radix 256) -> |Z| as 32-bit limbs, sign, bit
+// length.  One warp per row: a first pass of carry propagation gives the sign
+// (the carry out of the top), a second one over sign * digits gives the
+// magnitude's digits in [0, 256), four to a limb.
+__device__ __forceinline__ void load_lane_digits(const int32_t *d, int ub, int Wo, int (&v)[kDigitsPerLane], int sgn) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            int u = 4 * w + q;
-            long long t = (u < Wo ? static_cast<long long>(sgn) * d[u] : 0) + c;
-            limb |= static_cast<uint32_t>(t & 255) << (8 * q);
-            c = t >> 8;
-        }
-        z[w] = limb;
-        if (limb) { top = w; topv = limb; }
+    for (int g = 0; g < kDigitsPerLane / 4; ++g) {
+        const int u = ub + 4 * g;  // Wo is a multiple of 4
+        const int4 w = (u < Wo) ? *reinterpret_cast<const int4 *>(d + u) : make_int4(0, 0, 0, 0);
+        v[4 * g] = sgn * w.x;
+        v[4 * g + 1] = sgn * w.y;
+        v[4 * g + 2] = sgn * w.z;
+        v[4 * g + 3] = sgn * w.w;
     }
-    if (c != 0) atomicExch(dstat, DEV_OVERFLOW);
-    int bits = (top < 0) ? 0 : 32 * top + (32 - __clz(topv));
-    zbits[row_offset + i] = bits;
-    zneg[row_offset + i] = (bits > 0 && sgn < 0) ? 1 : 0;
-    atomicMax(dstat + 1, bits);
+}
+__global__ void __launch_bounds__(256) k_final_normalize(const int32_t *__restrict__ in, int n, int Wo,
+                                                         uint32_t *__restrict__ zmag, uint8_t *__restrict__ zneg,
+                                                         int32_t *__restrict__ zbits, int ZW, int32_t *dstat,
+                                                         int row_offset) {
+    const int lane = threadIdx.x & 31;
+    const int i = static_cast<int>((static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
+    if (i >= n) return;  // warp-uniform
+    const int32_t *d = in + static_cast<size_t>(i) * Wo;
+    int v[kDigitsPerLane];
+    int wc = 0;
+    for (int u0 = 0; u0 < Wo; u0 += 32 * kDigitsPerLane) {
+        load_lane_digits(d, u0 + kDigitsPerLane * lane, Wo, v, 1);
+        warp_carry<false>(v, lane, wc);
+    }
+    const int sgn = (wc < 0) ? -1 : 1;  // digits in [0, 256) below the carry: the value is negative iff it is
+    uint32_t *z = zmag + static_cast<size_t>(row_offset + i) * ZW;
+    int bits = 0;
+    bool bad = false;
+    wc = 0;
+    for (int u0 = 0; u0 < Wo; u0 += 32 * kDigitsPerLane) {
+        const int ub = u0 + kDigitsPerLane * lane;
+        load_lane_digits(d, ub, Wo, v, sgn);
+        warp_carry<false>(v, lane, wc);
+#pragma unroll
+        for (int g = 0; g < kDigitsPerLane / 4; ++g) {
+            const int u = ub + 4 * g;
+            const uint32_t limb = static_cast<uint32_t>(v[4 * g]) | (static_cast<uint32_t>(v[4 * g + 1]) << 8) |
+                                  (static_cast<uint32_t>(v[4 * g + 2]) << 16) |
+                                  (static_cast<uint32_t>(v[4 * g + 3]) << 24);
+            if (u < Wo) {
+                z[u / 4] = limb;
+                if (limb) bits = 32 * (u / 4) + (32 - __clz(limb));
+            } else if (limb) {
+                bad = true;  // |Z| does not fit the row
+            }
+        }
+    }
+    if (wc != 0) bad = true;
+    for (int w = Wo / 4 + lane; w < ZW; w += 32) z[w] = 0u;  // limbs above the row's digits
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) bits = max(bits, __shfl_xor_sync(0xffffffffu, bits, off));
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicExch(dstat, DEV_OVERFLOW);
+    if (lane == 0) {
+        zbits[row_offset + i] = bits;
+        zneg[row_offset + i] = (bits > 0 && sgn < 0) ? 1 : 0;
+        atomicMax(dstat + 1, bits);
+    }
 }
 
 // Signed 128-bit column sums of 32-bit limb weights -> |Z| limbs, sign, bits.
@@ -466,8 +563,8 @@ __global__ void k_round(const uint32_t *__restrict__ zmag, const uint8_t *__rest
 // ------------------------------------------------------------------ launchers
 cudaError_t launch_encode(hmv_plan_s *p, const uint32_t *limbs, const uint8_t *neg, int rows, int circulant_n,
                           int8_t *out) {
-    k_encode<<<blocks_for(rows, 128), 128, 0, p->stream>>>(limbs, neg, rows, p->L32, p->b, circulant_n, out, p->Dp,
-                                                           p->dstat);
+    k_encode<<<static_cast<unsigned>((rows + 7) / 8), 256, 0, p->stream>>>(limbs, neg, rows, p->L32, p->b,
+                                                                           circulant_n, out, p->Dp, p->dstat);  // a warp per row
     p->launches_total++;
     return cudaGetLastError();
 }
@@ -476,8 +573,8 @@ cudaError_t launch_prepass(hmv_plan_s *p, int level, bool matrix_side, const int
     const LevelGeom &pl = p->lv[level], &cl = p->lv[level + 1];
     const int in_rows = matrix_side ? pl.rowsA : pl.rowsX;
     const int out_rows = matrix_side ? cl.rowsA : cl.rowsX;
-    long long work = static_cast<long long>(cl.nodes) * out_rows;
-    k_prepass<<<blocks_for(work, 128), 128, 0, p->stream>>>(in, in_rows, pl.d_size, out, out_rows, cl.d_size,
+    const long long rows = static_cast<long long>(cl.nodes) * out_rows;  // one thread per child row
+    k_prepass<<<blocks_for(rows, 128), 128, 0, p->stream>>>(in, in_rows, pl.d_size, out, out_rows, cl.d_size,
                                                             cl.nodes, p->Dp, matrix_side ? 1 : 0, p->dstat);
     p->launches_total++;
     return cudaGetLastError();
@@ -531,8 +628,8 @@ cudaError_t launch_postpass(hmv_plan_s *p, int level, const int32_t *in, int32_t
 }
 
 cudaError_t launch_final_normalize(hmv_plan_s *p, const int32_t *in, int rhs) {
-    k_final_normalize<<<blocks_for(p->n, 128), 128, 0, p->stream>>>(in, p->n, p->Wo, p->zmag, p->zneg, p->zbits,
-                                                                    p->ZW, p->dstat, rhs * p->n);
+    k_final_normalize<<<static_cast<unsigned>((p->n + 7) / 8), 256, 0, p->stream>>>(  // a warp per row
+        in, p->n, p->Wo, p->zmag, p->zneg, p->zbits, p->ZW, p->dstat, rhs * p->n);
     p->launches_total++;
     return cudaGetLastError();
 }
