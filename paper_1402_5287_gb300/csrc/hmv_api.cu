@@ -357,7 +357,10 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
         const bool simt = (d.flags & HMV_FLAG_SIMT_LEAF) != 0;
         p->bytes_a_lvl = maxA;
         p->bytes_x_lvl = maxX;
-        p->bytes_post = maxPost * sizeof(int32_t);
+        // post-pass digits: leaf digits lie in [-128, 510] and each level at most
+        // doubles them, so int16 holds them through 6 levels
+        p->post16 = L <= 6;
+        p->bytes_post = maxPost * (p->post16 ? sizeof(int16_t) : sizeof(int32_t));
         p->elems_xg = static_cast<size_t>(leaf.nodes) * p->RX * 8 * (p->Dp + 8);
         p->bytes_dig = static_cast<size_t>(leaf.nodes) * p->MT * TM * p->Uo;
         p->elems_carry = static_cast<size_t>(leaf.nodes) * p->MT * TM * p->NUB;
@@ -370,8 +373,9 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
             if (!simt) g(dalloc(p, &p->xg, p->elems_xg));
             g(dalloc(p, &p->leaf_dig, p->bytes_dig));
             g(dalloc(p, &p->leaf_carry, p->elems_carry));
-            g(dalloc(p, &p->post[0], maxPost));
-            if (L > 0) g(dalloc(p, &p->post[1], maxPost));
+            const size_t post_words = (p->bytes_post + sizeof(int32_t) - 1) / sizeof(int32_t);
+            g(dalloc(p, &p->post[0], post_words));
+            if (L > 0) g(dalloc(p, &p->post[1], post_words));
         }
         // tiles: leaf-major (neighbouring CTAs share a leaf's operands in L2),
         // within a leaf the longest K loops first
@@ -574,7 +578,7 @@ hmv_status hmv_matvec(hmv_plan_t *p, const hmv_vec *x, hmv_vec *y) {
             timing_mark(p, 3);
             g(launch_leaf_normalize(p, p->post[p->L % 2]));
             for (int l = p->L - 1; l >= 0; --l) g(launch_postpass(p, l, p->post[(l + 1) % 2], p->post[l % 2]));
-            g(launch_final_normalize(p, p->post[0], r));
+            g(launch_final_normalize(p, p->post[0], r, p->post16));
             timing_mark(p, 4);
         }
         if (p->timing && g.err == cudaSuccess) {

@@ -328,17 +328,30 @@ __global__ void k_leaf_simt(const int8_t *__restrict__ A, int rowsA, const int8_
 // u < Uo, plus the carry out of block t (a signed 32-bit integer) spread over
 // digits (t+1)*tn .. (t+1)*tn + 3 as three base-256 digits and a signed top
 // part; out[Uo+4 .. Wo) = 0.  Every digit is then within [-128, 510], so L
-// levels of the post-pass keep them within 510 * 2^L; the final normalise
-// propagates all carries.  One block per leaf row.
+// levels of the post-pass keep them within 510 * 2^L (int16 digits while
+// L <= 6, else int32); the final normalise propagates all carries.  One block
+// per leaf row.
+template <class T>
+__device__ __forceinline__ void store4(T *o, int g, int4 v);
+template <>
+__device__ __forceinline__ void store4<int32_t>(int32_t *o, int g, int4 v) {
+    reinterpret_cast<int4 *>(o)[g] = v;
+}
+template <>
+__device__ __forceinline__ void store4<int16_t>(int16_t *o, int g, int4 v) {
+    reinterpret_cast<uint2 *>(o)[g] = make_uint2((static_cast<uint32_t>(v.x) & 0xFFFFu) | (static_cast<uint32_t>(v.y) << 16),
+                                                 (static_cast<uint32_t>(v.z) & 0xFFFFu) | (static_cast<uint32_t>(v.w) << 16));
+}
+template <class T>
 __global__ void k_leaf_normalize(const uint8_t *__restrict__ dig, const int32_t *__restrict__ carry,
-                                 const int *__restrict__ size, int MT, int Uo, int NUB, int32_t *__restrict__ out,
-                                 int rowsX, int Wo, int tn) {
+                                 const int *__restrict__ size, int MT, int Uo, int NUB, T *__restrict__ out, int rowsX,
+                                 int Wo, int tn) {
     const int leaf = blockIdx.x / rowsX, row = blockIdx.x % rowsX;
     if (row >= size[leaf]) return;
     const size_t r = static_cast<size_t>(leaf) * MT * TM + row;
     const uint32_t *d = reinterpret_cast<const uint32_t *>(dig + r * Uo);
     const int32_t *cy = carry + r * NUB;
-    int4 *o = reinterpret_cast<int4 *>(out + (static_cast<size_t>(leaf) * rowsX + row) * Wo);
+    T *o = out + (static_cast<size_t>(leaf) * rowsX + row) * Wo;
     for (int g = threadIdx.x; g < Wo / 4; g += blockDim.x) {
         const int u0 = 4 * g;
         int4 v = make_int4(0, 0, 0, 0);
@@ -353,31 +366,46 @@ __global__ void k_leaf_normalize(const uint8_t *__restrict__ dig, const int32_t 
             v.z += (c >> 16) & 0xFF;
             v.w += c >> 24;  // arithmetic shift: the signed top part
         }
-        o[g] = v;
+        store4<T>(o, g, v);
     }
 }
 
 // ------------------------------------------------------------------ post-pass
 // Algorithm 1, step 8 (0-based): y_{2k} = p_k - q_k, y_{2k+1} = p_k + r_k,
 // digit-wise without carries (digits grow by at most one bit per level).
-__global__ void k_postpass(const int32_t *__restrict__ in, int rows_in, int32_t *__restrict__ out, int rows_out,
-                           const int *__restrict__ parent_size, int nparents, int Wo) {
-    const int g4 = Wo / 4;
-    long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-    long long per = static_cast<long long>(rows_out) * g4;
-    int nu = static_cast<int>(idx / per);
-    if (nu >= nparents) return;
-    int rem = static_cast<int>(idx % per);
-    int i = rem / g4, g = rem % g4;
+// One block per output row, 16 bytes of digits per thread and step.
+template <class T>
+__global__ void k_postpass(const T *__restrict__ in, int rows_in, T *__restrict__ out, int rows_out,
+                           const int *__restrict__ parent_size, int Wo) {
+    const int nu = blockIdx.x / rows_out, i = blockIdx.x % rows_out;
     if (i >= parent_size[nu]) return;
     const int k = i >> 1;
     const int other = (i & 1) ? 2 : 1;
-    const int4 p = reinterpret_cast<const int4 *>(in + (static_cast<size_t>(3 * nu) * rows_in + k) * Wo)[g];
-    const int4 o = reinterpret_cast<const int4 *>(in + (static_cast<size_t>(3 * nu + other) * rows_in + k) * Wo)[g];
-    int4 y;
-    if (i & 1) y = make_int4(p.x + o.x, p.y + o.y, p.z + o.z, p.w + o.w);
-    else y = make_int4(p.x - o.x, p.y - o.y, p.z - o.z, p.w - o.w);
-    reinterpret_cast<int4 *>(out + (static_cast<size_t>(nu) * rows_out + i) * Wo)[g] = y;
+    const int4 *p = reinterpret_cast<const int4 *>(in + (static_cast<size_t>(3 * nu) * rows_in + k) * Wo);
+    const int4 *o = reinterpret_cast<const int4 *>(in + (static_cast<size_t>(3 * nu + other) * rows_in + k) * Wo);
+    int4 *y = reinterpret_cast<int4 *>(out + (static_cast<size_t>(nu) * rows_out + i) * Wo);
+    const int groups = Wo * static_cast<int>(sizeof(T)) / 16;  // Wo is a multiple of 8
+    for (int g = threadIdx.x; g < groups; g += blockDim.x) {
+        const int4 a = p[g], b = o[g];
+        int4 r;
+        if (sizeof(T) == 4) {
+            r = (i & 1) ? make_int4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w)
+                        : make_int4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+        } else {  // two int16 digits per word, no carries between halves
+            const int av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+            int rv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int alo = static_cast<int16_t>(av[q] & 0xFFFF), ahi = av[q] >> 16;
+                const int blo = static_cast<int16_t>(bv[q] & 0xFFFF), bhi = bv[q] >> 16;
+                const int lo = (i & 1) ? alo + blo : alo - blo;
+                const int hi = (i & 1) ? ahi + bhi : ahi - bhi;
+                rv[q] = static_cast<int>((static_cast<uint32_t>(lo) & 0xFFFFu) | (static_cast<uint32_t>(hi) << 16));
+            }
+            r = make_int4(rv[0], rv[1], rv[2], rv[3]);
+        }
+        y[g] = r;
+    }
 }
 
 // ------------------------------------------------------------------ final normalise
@@ -385,25 +413,33 @@ __global__ void k_postpass(const int32_t *__restrict__ in, int rows_in, int32_t 
 // length.  One warp per row: a first pass of carry propagation gives the sign
 // (the carry out of the top), a second one over sign * digits gives the
 // magnitude's digits in [0, 256), four to a limb.
-__device__ __forceinline__ void load_lane_digits(const int32_t *d, int ub, int Wo, int (&v)[kDigitsPerLane], int sgn) {
+__device__ __forceinline__ int4 load4(const int32_t *d, int u) { return *reinterpret_cast<const int4 *>(d + u); }
+__device__ __forceinline__ int4 load4(const int16_t *d, int u) {
+    const uint2 w = *reinterpret_cast<const uint2 *>(d + u);
+    return make_int4(static_cast<int16_t>(w.x & 0xFFFFu), static_cast<int>(w.x) >> 16,
+                     static_cast<int16_t>(w.y & 0xFFFFu), static_cast<int>(w.y) >> 16);
+}
+template <class T>
+__device__ __forceinline__ void load_lane_digits(const T *d, int ub, int Wo, int (&v)[kDigitsPerLane], int sgn) {
 #pragma unroll
     for (int g = 0; g < kDigitsPerLane / 4; ++g) {
         const int u = ub + 4 * g;  // Wo is a multiple of 4
-        const int4 w = (u < Wo) ? *reinterpret_cast<const int4 *>(d + u) : make_int4(0, 0, 0, 0);
+        const int4 w = (u < Wo) ? load4(d, u) : make_int4(0, 0, 0, 0);
         v[4 * g] = sgn * w.x;
         v[4 * g + 1] = sgn * w.y;
         v[4 * g + 2] = sgn * w.z;
         v[4 * g + 3] = sgn * w.w;
     }
 }
-__global__ void __launch_bounds__(256) k_final_normalize(const int32_t *__restrict__ in, int n, int Wo,
+template <class T>
+__global__ void __launch_bounds__(256) k_final_normalize(const T *__restrict__ in, int n, int Wo,
                                                          uint32_t *__restrict__ zmag, uint8_t *__restrict__ zneg,
                                                          int32_t *__restrict__ zbits, int ZW, int32_t *dstat,
                                                          int row_offset) {
     const int lane = threadIdx.x & 31;
     const int i = static_cast<int>((static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
     if (i >= n) return;  // warp-uniform
-    const int32_t *d = in + static_cast<size_t>(i) * Wo;
+    const T *d = in + static_cast<size_t>(i) * Wo;
     int v[kDigitsPerLane];
     int wc = 0;
     for (int u0 = 0; u0 < Wo; u0 += 32 * kDigitsPerLane) {
@@ -613,23 +649,38 @@ cudaError_t launch_leaf_simt(hmv_plan_s *p, const int8_t *a_leaf, const int8_t *
 
 cudaError_t launch_leaf_normalize(hmv_plan_s *p, int32_t *out) {
     const LevelGeom &ll = p->lv[p->L];
-    k_leaf_normalize<<<static_cast<unsigned>(ll.nodes) * ll.rowsX, 128, 0, p->stream>>>(
-        p->leaf_dig, p->leaf_carry, ll.d_size, p->MT, p->Uo, p->NUB, out, ll.rowsX, p->Wo, p->tn);
+    const unsigned blocks = static_cast<unsigned>(ll.nodes) * ll.rowsX;
+    if (p->post16)
+        k_leaf_normalize<int16_t><<<blocks, 128, 0, p->stream>>>(p->leaf_dig, p->leaf_carry, ll.d_size, p->MT, p->Uo,
+                                                                 p->NUB, reinterpret_cast<int16_t *>(out), ll.rowsX,
+                                                                 p->Wo, p->tn);
+    else
+        k_leaf_normalize<int32_t><<<blocks, 128, 0, p->stream>>>(p->leaf_dig, p->leaf_carry, ll.d_size, p->MT, p->Uo,
+                                                                 p->NUB, out, ll.rowsX, p->Wo, p->tn);
     p->launches_total++;
     return cudaGetLastError();
 }
 
 cudaError_t launch_postpass(hmv_plan_s *p, int level, const int32_t *in, int32_t *out) {
     const LevelGeom &pl = p->lv[level], &cl = p->lv[level + 1];
-    long long work = static_cast<long long>(pl.nodes) * pl.rowsX * (p->Wo / 4);
-    k_postpass<<<blocks_for(work), kThreads, 0, p->stream>>>(in, cl.rowsX, out, pl.rowsX, pl.d_size, pl.nodes, p->Wo);
+    const unsigned blocks = static_cast<unsigned>(pl.nodes) * pl.rowsX;  // one block per output row
+    if (p->post16)
+        k_postpass<int16_t><<<blocks, 128, 0, p->stream>>>(reinterpret_cast<const int16_t *>(in), cl.rowsX,
+                                                           reinterpret_cast<int16_t *>(out), pl.rowsX, pl.d_size, p->Wo);
+    else
+        k_postpass<int32_t><<<blocks, 128, 0, p->stream>>>(in, cl.rowsX, out, pl.rowsX, pl.d_size, p->Wo);
     p->launches_total++;
     return cudaGetLastError();
 }
-
-cudaError_t launch_final_normalize(hmv_plan_s *p, const int32_t *in, int rhs) {
-    k_final_normalize<<<static_cast<unsigned>((p->n + 7) / 8), 256, 0, p->stream>>>(  // a warp per row
-        in, p->n, p->Wo, p->zmag, p->zneg, p->zbits, p->ZW, p->dstat, rhs * p->n);
+cudaError_t launch_final_normalize(hmv_plan_s *p, const int32_t *in, int rhs, bool in16) {
+    const unsigned blocks = static_cast<unsigned>((p->n + 7) / 8);  // a warp per row
+    if (in16)
+        k_final_normalize<int16_t><<<blocks, 256, 0, p->stream>>>(reinterpret_cast<const int16_t *>(in), p->n, p->Wo,
+                                                                  p->zmag, p->zneg, p->zbits, p->ZW, p->dstat,
+                                                                  rhs * p->n);
+    else
+        k_final_normalize<int32_t><<<blocks, 256, 0, p->stream>>>(in, p->n, p->Wo, p->zmag, p->zneg, p->zbits, p->ZW,
+                                                                  p->dstat, rhs * p->n);
     p->launches_total++;
     return cudaGetLastError();
 }

@@ -71,6 +71,7 @@ struct hmv_plan_s {
     int ZW = 0;                    // limbs of the exact rows (Wo / 4)
     int MT = 0;                    // 128-row tiles per leaf
     int tn = hmv::TN_DEFAULT;           // leaf tile width in product digits (256 or 128)
+    bool post16 = false;                // post-pass digits as int16 (depth <= 6), else int32
     std::vector<hmv::LevelGeom> lv;
     bool loaded = false;
     int e_h = 0;                   // exponent of the loaded matrix
@@ -169,7 +170,8 @@ void fill_leaf_problem(hmv_plan_s *p, LeafProblem &lp);
 cudaError_t launch_leaf_simt(hmv_plan_s *p, const int8_t *a_leaf, const int8_t *x_leaf);
 cudaError_t launch_leaf_normalize(hmv_plan_s *p, int32_t *out);
 cudaError_t launch_postpass(hmv_plan_s *p, int level, const int32_t *in, int32_t *out);
-cudaError_t launch_final_normalize(hmv_plan_s *p, const int32_t *in, int rhs);
+// in16: the digits are int16 (a plan's post buffers with post16), else int32
+cudaError_t launch_final_normalize(hmv_plan_s *p, const int32_t *in, int rhs, bool in16);
 cudaError_t launch_schoolbook(hmv_plan_s *p, const uint32_t *x_limbs, const uint8_t *x_neg, int rhs);
 cudaError_t launch_round(hmv_plan_s *p, int rows, int e_in, uint32_t *y_limbs, uint8_t *y_neg);
 cudaError_t make_tensor_maps(hmv_plan_s *p);

@@ -56,15 +56,20 @@ __global__ void k_split(const uint32_t *__restrict__ limbs, const uint8_t *__res
 
 // z[u] = Z00[u] + (Zm - Z00 - Z11)[u - ds] + Z11[u - 2 ds], int32 digits,
 // radix 2^8, no carries (the digits stay far below 2^31).
+// Digit u of z, an int16 (is16) or int32 digit row of width Wc, 0 outside it.
+__device__ __forceinline__ int32_t digit_at(const int32_t *z, bool is16, size_t row, int Wc, int v) {
+    if (v < 0 || v >= Wc) return 0;
+    return is16 ? static_cast<int32_t>(reinterpret_cast<const int16_t *>(z)[row * Wc + v]) : z[row * Wc + v];
+}
 __global__ void k_combine(const int32_t *__restrict__ z00, const int32_t *__restrict__ zm,
-                          const int32_t *__restrict__ z11, int Wc, int n, int ds, int32_t *__restrict__ out, int Wp) {
-    const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (idx >= static_cast<long long>(n) * Wp) return;
-    const int i = static_cast<int>(idx / Wp), u = static_cast<int>(idx % Wp);
-    const size_t r = static_cast<size_t>(i) * Wc;
-    auto at = [&](const int32_t *z, int v) -> int32_t { return (v >= 0 && v < Wc) ? z[r + v] : 0; };
-    out[static_cast<size_t>(i) * Wp + u] =
-        at(z00, u) + at(zm, u - ds) - at(z00, u - ds) - at(z11, u - ds) + at(z11, u - 2 * ds);
+                          const int32_t *__restrict__ z11, int in16_mask, int Wc, int n, int ds,
+                          int32_t *__restrict__ out, int Wp) {
+    const int i = blockIdx.x;  // grid: (rows, column blocks)
+    const bool a16 = in16_mask & 1, m16 = in16_mask & 2, b16 = in16_mask & 4;
+    for (int u = blockIdx.y * blockDim.x + threadIdx.x; u < Wp; u += gridDim.y * blockDim.x)
+        out[static_cast<size_t>(i) * Wp + u] = digit_at(z00, a16, i, Wc, u) + digit_at(zm, m16, i, Wc, u - ds) -
+                                               digit_at(z00, a16, i, Wc, u - ds) - digit_at(z11, b16, i, Wc, u - ds) +
+                                               digit_at(z11, b16, i, Wc, u - 2 * ds);
 }
 
 void collect_leaf_plans(hmv_plan_s *p, std::vector<hmv_plan_s *> &out) {
@@ -99,25 +104,27 @@ cudaError_t split_down(hmv_plan_s *p, const uint32_t *limbs, const uint8_t *neg,
 
 // The exact digit vector of a plan's rows after its post-pass (unsplit) or
 // after combining its children (split).
-cudaError_t combine_up(hmv_plan_s *p, const int32_t **out, int *width) {
+cudaError_t combine_up(hmv_plan_s *p, const int32_t **out, int *width, bool *is16) {
     if (p->children.empty()) {
         *out = p->post[0];
         *width = p->Wo;
+        *is16 = p->post16;
         return cudaSuccess;
     }
     const int32_t *z[3];
     int w[3];
+    bool s16[3];
     for (int t = 0; t < 3; ++t) {
-        cudaError_t e = combine_up(p->children[t], &z[t], &w[t]);
+        cudaError_t e = combine_up(p->children[t], &z[t], &w[t], &s16[t]);
         if (e != cudaSuccess) return e;
     }
-    const long long work = static_cast<long long>(p->n) * p->Wo;
-    k_combine<<<static_cast<unsigned>((work + 255) / 256), 256, 0, p->stream>>>(z[0], z[2], z[1], w[0], p->n,
-                                                                               p->split_bits / 8, p->combined,
-                                                                               p->Wo);
+    const int mask = (s16[0] ? 1 : 0) | (s16[2] ? 2 : 0) | (s16[1] ? 4 : 0);
+    const dim3 grid(static_cast<unsigned>(p->n), static_cast<unsigned>(std::min(65535, (p->Wo + 255) / 256)));
+    k_combine<<<grid, 256, 0, p->stream>>>(z[0], z[2], z[1], mask, w[0], p->n, p->split_bits / 8, p->combined, p->Wo);
     p->launches_total++;
     *out = p->combined;
     *width = p->Wo;
+    *is16 = false;
     return cudaGetLastError();
 }
 
@@ -249,8 +256,9 @@ cudaError_t split_post(hmv_plan_s *p, int rhs) {
     }
     const int32_t *z = nullptr;
     int w = 0;
-    if (e == cudaSuccess) e = combine_up(p, &z, &w);
-    if (e == cudaSuccess) e = launch_final_normalize(p, z, rhs);
+    bool z16 = false;
+    if (e == cudaSuccess) e = combine_up(p, &z, &w, &z16);
+    if (e == cudaSuccess) e = launch_final_normalize(p, z, rhs, z16);
     for (hmv_plan_s *c : leaves) {
         p->launches_total += c->launches_total;
         c->launches_total = 0;

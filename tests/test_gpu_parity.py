@@ -55,9 +55,11 @@ def test_small_workload_all_rows():
 
 @pytest.mark.parametrize("n,b,levels", [
     (64, 2048, 0), (64, 2048, 1), (200, 512, 2), (300, 2048, 3), (257, 700, 1),
-    (130, 64, 0), (129, 1000, 1), (33, 2040, 4), (1, 64, 0), (2, 31, 1), (3, 1, 2), (17, 33, 3)])
+    (130, 64, 0), (129, 1000, 1), (33, 2040, 4), (1, 64, 0), (2, 31, 1), (3, 1, 2), (17, 33, 3),
+    (300, 256, 6), (400, 128, 7), (700, 40, 8)])
 def test_karatsuba_levels_all_rows(n, b, levels):
-    """Several 128-row tiles, ragged row and digit tails, depths 0-4."""
+    """Several 128-row tiles, ragged row and digit tails, depths 0-8 (int16
+    post-pass digits through depth 6, int32 beyond)."""
     h = rand_vec(n + b, 0, 2 * n - 1, b, 1)
     x = rand_vec(n + b, 1, n, b, -2)
     assert_same(run(n, b, h, x, method=hmv.KARATSUBA, levels=levels), oracle_matvec(oracle.HANKEL, n, h, x))
@@ -107,7 +109,11 @@ def test_worst_case_digits_hit_the_accumulation_bound():
     mm = (1 << b) - 1
     h = FixedVec.from_ints([mm if k % 3 else -mm for k in range(2 * n - 1)], b, 0)
     x = FixedVec.from_ints([-mm if j % 2 else mm for j in range(n)], b, 0)
-    assert_same(run(n, b, h, x, method=hmv.KARATSUBA, levels=1), oracle_matvec(oracle.HANKEL, n, h, x))
+    want = oracle_matvec(oracle.HANKEL, n, h, x)
+    assert_same(run(n, b, h, x, method=hmv.KARATSUBA, levels=1), want)
+    # the deepest recursion whose post-pass digits are int16, and one past it
+    assert_same(run(n, b, h, x, method=hmv.KARATSUBA, levels=6), want)
+    assert_same(run(n, b, h, x, method=hmv.KARATSUBA, levels=7), want)
 
 
 def test_zero_and_unit_vectors():
