@@ -116,7 +116,16 @@ int best_depth(int n, int b, int num_sms, double *cost, int tn = TN_DEFAULT) {
 // estimate of the narrower products is scaled by (1 - 0.055 d): measured
 // leaf times (203.6, 167.1, 149.0 ms) beat the tile count by that much,
 // the narrower operands running at higher clocks under the power cap.
-int auto_digit_levels(int n, int b, int num_sms) {
+// Digit split for HMV_AUTO: kToom4 or the number of Karatsuba levels d (3^d
+// products of about b/2^d bits, d <= 2), each product at its own best depth,
+// plus the level kernels, which scale with the products' total width (n*b
+// times 1, 3/2, 9/4 for d = 0, 1, 2 and 7/4 for Toom-4; measured 10.4, 15.2,
+// 22.4 ms at n = 8000, b = 33220 for d = 0, 1, 2, about 3.9e-11 s per n*b at
+// d = 0).  The leaf estimate of the narrower products is scaled by
+// (1 - 0.055 d): measured leaf times fall below the tile-count model as the
+// products narrow (Toom-4's quarter-width products count as d = 2).
+constexpr int kToom4 = 4;
+int auto_digit_scheme(int n, int b, int num_sms) {
     int best_d = 0;
     double best = 1e300;
     int bd = b;
@@ -128,6 +137,13 @@ int auto_digit_levels(int n, int b, int num_sms) {
         if (t < best) { best = t; best_d = d; }
         bd = 32 * (((bd + 31) / 32 + 1) / 2) + 1;  // the children's width
         mult *= 3.0;
+    }
+    const int L32 = (b + 31) / 32;
+    if (L32 >= 4) {
+        double leaf = 0;
+        best_depth(n, 32 * ((L32 + 3) / 4) + 4, num_sms, &leaf);
+        const double t = 7.0 * leaf * (1.0 - 0.11) + 3.9e-11 * n * static_cast<double>(b) * 1.75;
+        if (t < best) best_d = kToom4;
     }
     return best_d;
 }
@@ -252,11 +268,15 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
     if (d.method < HMV_AUTO || d.method > HMV_FFT64) return HMV_EINVAL;
     if (d.levels < -1 || d.levels > kMaxLevels) return HMV_EINVAL;
     if (d.flags & ~(HMV_FLAG_TIMING | HMV_FLAG_SIMT_LEAF | HMV_FLAG_DIGIT_SPLIT1 | HMV_FLAG_DIGIT_SPLIT2 |
-                    HMV_FLAG_TILE128))
+                    HMV_FLAG_TILE128 | HMV_FLAG_DIGIT_TOOM4))
+        return HMV_EINVAL;
+    if ((d.flags & HMV_FLAG_DIGIT_TOOM4) && (d.flags & (HMV_FLAG_DIGIT_SPLIT1 | HMV_FLAG_DIGIT_SPLIT2)))
         return HMV_EINVAL;
     int digit_levels = (d.flags & HMV_FLAG_DIGIT_SPLIT2) ? 2 : ((d.flags & HMV_FLAG_DIGIT_SPLIT1) ? 1 : 0);
+    if (d.flags & HMV_FLAG_DIGIT_TOOM4) digit_levels = kToom4;
     if (digit_levels && ((d.method != HMV_AUTO && d.method != HMV_KARATSUBA) || (d.flags & HMV_FLAG_SIMT_LEAF)))
         return HMV_EINVAL;
+    if (digit_levels == kToom4 && (d.b + 31) / 32 < 4) return HMV_EINVAL;  // four parts of at least one limb
     if (d.method == HMV_FFT64 ? (d.piece_bits != 0 && (d.piece_bits < 4 || d.piece_bits > 16)) : d.piece_bits != 0)
         return HMV_EINVAL;
     if (static_cast<long long>(d.n) * d.nrhs > (1LL << 30)) return HMV_EINVAL;
@@ -296,14 +316,31 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
     const int n = d.n;
     int dl = digit_levels;
     if (dl == 0 && d.method == HMV_AUTO && d.levels < 0 && !(d.flags & HMV_FLAG_SIMT_LEAF) && !external_scratch)
-        dl = auto_digit_levels(n, d.b, p->num_sms);
+        dl = auto_digit_scheme(n, d.b, p->num_sms);
     digit_levels = dl;
-    p->digit_levels = digit_levels;
+    p->digit_levels = digit_levels == kToom4 ? 0 : digit_levels;
     if (digit_levels && !external_scratch) {
-        hmv_status st = split_plan_create(p, d, digit_levels);
+        hmv_status st = digit_levels == kToom4 ? toom4_plan_create(p, d) : split_plan_create(p, d, digit_levels);
         if (st != HMV_OK) { hmv_free(p); return st; }
         g(dalloc(p, &p->combined, static_cast<size_t>(n) * p->Wo));
         g(dalloc(p, &p->d_counter, 1));
+        if (p->toom4) {
+            // the children's staging rows never move: one table for the matrix side, one for x
+            g(dalloc(p, &p->toom_ptrs, 14));
+            g(dalloc(p, &p->toom_neg_ptrs, 14));
+            uint32_t *tl[14];
+            uint8_t *tn[14];
+            for (int t = 0; t < 7; ++t) {
+                tl[t] = p->children[t]->h_limbs_d;
+                tn[t] = p->children[t]->h_neg_d;
+                tl[7 + t] = p->children[t]->x_limbs_d;
+                tn[7 + t] = p->children[t]->x_neg_d;
+            }
+            if (!dry_run && g.err == cudaSuccess) {
+                g(cudaMemcpy(p->toom_ptrs, tl, sizeof tl, cudaMemcpyHostToDevice));
+                g(cudaMemcpy(p->toom_neg_ptrs, tn, sizeof tn, cudaMemcpyHostToDevice));
+            }
+        }
         if (d.kind == HMV_CIRCULANT) {
             g(dalloc(p, &p->h_wrap, static_cast<size_t>(2 * n - 1) * p->L32));
             g(dalloc(p, &p->h_wrap_neg, static_cast<size_t>(2 * n - 1)));
@@ -633,8 +670,8 @@ hmv_status hmv_get_stats(const hmv_plan_t *p, hmv_stats *o) {
     const hmv_plan_s *q = p;
     int unsplit = 1;
     while (!q->children.empty()) {
+        unsplit *= static_cast<int>(q->children.size());
         q = q->children[0];
-        unsplit *= 3;
     }
     o->levels = q->L;
     o->leaves = unsplit * (q->lv.empty() ? 1 : q->lv[q->L].nodes);
@@ -660,6 +697,7 @@ hmv_status hmv_get_stats(const hmv_plan_t *p, hmv_stats *o) {
     o->fft_fallbacks = p->fft_fallbacks;
     o->ms_fft = p->ms_fft;
     o->leaf_tile_digits = (q->method == HMV_KARATSUBA && !q->lv.empty() && q->hrev) ? q->tn : 0;
+    o->digit_products = unsplit;
     return HMV_OK;
 }
 

@@ -435,7 +435,7 @@ template <class T>
 __global__ void __launch_bounds__(256) k_final_normalize(const T *__restrict__ in, int n, int Wo,
                                                          uint32_t *__restrict__ zmag, uint8_t *__restrict__ zneg,
                                                          int32_t *__restrict__ zbits, int ZW, int32_t *dstat,
-                                                         int row_offset) {
+                                                         int row_offset, int track_max) {
     const int lane = threadIdx.x & 31;
     const int i = static_cast<int>((static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
     if (i >= n) return;  // warp-uniform
@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(256) k_final_normalize(const T *__restrict__ i
     if (lane == 0) {
         zbits[row_offset + i] = bits;
         zneg[row_offset + i] = (bits > 0 && sgn < 0) ? 1 : 0;
-        atomicMax(dstat + 1, bits);
+        if (track_max) atomicMax(dstat + 1, bits);
     }
 }
 
@@ -672,15 +672,16 @@ cudaError_t launch_postpass(hmv_plan_s *p, int level, const int32_t *in, int32_t
     p->launches_total++;
     return cudaGetLastError();
 }
-cudaError_t launch_final_normalize(hmv_plan_s *p, const int32_t *in, int rhs, bool in16) {
+cudaError_t launch_final_normalize(hmv_plan_s *p, const int32_t *in, int rhs, bool in16, bool track_max) {
     const unsigned blocks = static_cast<unsigned>((p->n + 7) / 8);  // a warp per row
+    const int tm = track_max ? 1 : 0;
     if (in16)
         k_final_normalize<int16_t><<<blocks, 256, 0, p->stream>>>(reinterpret_cast<const int16_t *>(in), p->n, p->Wo,
                                                                   p->zmag, p->zneg, p->zbits, p->ZW, p->dstat,
-                                                                  rhs * p->n);
+                                                                  rhs * p->n, tm);
     else
         k_final_normalize<int32_t><<<blocks, 256, 0, p->stream>>>(in, p->n, p->Wo, p->zmag, p->zneg, p->zbits, p->ZW,
-                                                                  p->dstat, rhs * p->n);
+                                                                  p->dstat, rhs * p->n, tm);
     p->launches_total++;
     return cudaGetLastError();
 }

@@ -72,6 +72,124 @@ __global__ void k_combine(const int32_t *__restrict__ z00, const int32_t *__rest
                                                digit_at(z11, b16, i, Wc, u - 2 * ds);
 }
 
+// ------------------------------------------------------------------ Toom-4
+// Each mantissa M = sum_k V_k 2^(ks), k = 0..3 (|V_k| < 2^s, all with the
+// sign of the entry), read as a polynomial in t = 2^s; so are the exact rows,
+// Z(t) = A(h(t)) x(t) = sum_m C_m t^m, m = 0..6.  Seven products at the
+// points 0, 1, -1, 2, -2, 1/2 (homogenised: 8 h(1/2)) and infinity fix the
+// C_m; 360 C_m = sum_t N[m][t] P_t with the integer matrix below (360 times
+// the inverse of the evaluation matrix), and Z = Z(2^s).
+__constant__ int8_t kToomEval[7][4] = {{1, 0, 0, 0}, {1, 1, 1, 1},   {1, -1, 1, -1}, {1, 2, 4, 8},
+                                       {1, -2, 4, -8}, {8, 4, 2, 1}, {0, 0, 0, 1}};
+__constant__ int16_t kToomInterp[7][7] = {{360, 0, 0, 0, 0, 0, 0},
+                                          {-720, -240, -80, 10, 6, 16, -720},
+                                          {-450, 240, 240, -15, -15, 0, 1440},
+                                          {900, 540, -140, -20, 0, -20, 900},
+                                          {90, -60, -60, 15, 15, 0, -1800},
+                                          {-180, -120, 40, 10, -6, 4, -180},
+                                          {0, 0, 0, 0, 0, 0, 360}};
+constexpr uint64_t kToomDen = 360;
+
+// Sign-magnitude rows (L32 limbs) -> the seven children's rows (Lc limbs):
+// child t gets E_t = sum_k kToomEval[t][k] V_k times the entry's sign, as a
+// sign and a magnitude (|E_t| < 15 * 2^s <= 2^(32 Lc)).  One thread per
+// (row, point).
+__global__ void k_toom4_split(const uint32_t *__restrict__ limbs, const uint8_t *__restrict__ neg, int rows,
+                              int L32, int sl, int Lc, uint32_t *const *__restrict__ dst,
+                              uint8_t *const *__restrict__ dneg) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * 7) return;
+    const int k = idx / 7, t = idx % 7;
+    const uint32_t *m = limbs + static_cast<size_t>(k) * L32;
+    uint32_t *o = dst[t] + static_cast<size_t>(k) * Lc;
+    long long carry = 0;
+    for (int q = 0; q < Lc; ++q) {
+        long long e = carry;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const int li = p * sl + q;  // limb q of V_p
+            const uint32_t v = (q < sl && li < L32) ? m[li] : 0u;
+            e += static_cast<long long>(kToomEval[t][p]) * v;
+        }
+        o[q] = static_cast<uint32_t>(e);
+        carry = e >> 32;  // arithmetic: floor
+    }
+    // carry is 0 or -1 here (the value fits Lc limbs): -1 means E < 0
+    bool any = false;
+    if (carry < 0) {
+        unsigned long long c = 1;  // |E| = ~E + 1
+        for (int q = 0; q < Lc; ++q) {
+            c += static_cast<unsigned long long>(~o[q]);
+            o[q] = static_cast<uint32_t>(c);
+            c >>= 32;
+            any |= o[q] != 0;
+        }
+    } else {
+        for (int q = 0; q < Lc; ++q) any |= o[q] != 0;
+    }
+    const bool eneg = (carry < 0) != (neg[k] != 0);
+    dneg[t][k] = (any && eneg) ? 1 : 0;
+}
+
+// 360 Z as int32 carry-save digits: z[u] = sum_m sum_t N[m][t] P_t[u - m ds],
+// four digits per thread (ds and the children's widths are multiples of 4).
+// The children's digits are int16 (bit t of in16_mask) or int32.
+__device__ __forceinline__ int4 child4(const int32_t *z, bool is16, size_t row, int Wc, int v) {
+    if (is16) {
+        const uint2 w = *reinterpret_cast<const uint2 *>(reinterpret_cast<const int16_t *>(z) + row * Wc + v);
+        return make_int4(static_cast<int16_t>(w.x & 0xFFFFu), static_cast<int>(w.x) >> 16,
+                         static_cast<int16_t>(w.y & 0xFFFFu), static_cast<int>(w.y) >> 16);
+    }
+    return *reinterpret_cast<const int4 *>(z + row * Wc + v);
+}
+struct ToomChildren {
+    const int32_t *z[7];
+};
+__global__ void k_toom4_combine(ToomChildren ch, int in16_mask, int Wc, int ds, int32_t *__restrict__ out, int Wp) {
+    const int i = blockIdx.x;
+    for (int g = blockIdx.y * blockDim.x + threadIdx.x; g < Wp / 4; g += gridDim.y * blockDim.x) {
+        const int u = 4 * g;
+        int4 acc = make_int4(0, 0, 0, 0);
+        for (int mm = 0; mm < 7; ++mm) {
+            const int v = u - mm * ds;
+            if (v < 0) break;
+            if (v >= Wc) continue;
+#pragma unroll
+            for (int t = 0; t < 7; ++t) {
+                const int c = kToomInterp[mm][t];
+                if (c == 0) continue;
+                const int4 d = child4(ch.z[t], (in16_mask >> t) & 1, i, Wc, v);
+                acc.x += c * d.x;
+                acc.y += c * d.y;
+                acc.z += c * d.z;
+                acc.w += c * d.w;
+            }
+        }
+        reinterpret_cast<int4 *>(out + static_cast<size_t>(i) * Wp)[g] = acc;
+    }
+}
+
+// |360 Z| limbs -> |Z| limbs (exact: a nonzero remainder is an internal
+// error), with the bit length and the maximum over rows.
+__global__ void k_div_exact(uint32_t *__restrict__ zmag, int32_t *__restrict__ zbits, int n, int ZW, int32_t *dstat,
+                            int row_offset) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t *z = zmag + static_cast<size_t>(row_offset + i) * ZW;
+    uint64_t r = 0;
+    int bits = 0;
+    for (int w = ZW - 1; w >= 0; --w) {
+        const uint64_t cur = (r << 32) | z[w];
+        const uint64_t q = cur / kToomDen;
+        r = cur - q * kToomDen;
+        z[w] = static_cast<uint32_t>(q);
+        if (bits == 0 && q != 0) bits = 32 * w + (32 - __clz(static_cast<uint32_t>(q)));
+    }
+    if (r != 0) atomicExch(dstat, DEV_OVERFLOW);
+    zbits[row_offset + i] = bits;
+    atomicMax(dstat + 1, bits);
+}
+
 void collect_leaf_plans(hmv_plan_s *p, std::vector<hmv_plan_s *> &out) {
     if (p->children.empty()) {
         out.push_back(p);
@@ -84,6 +202,14 @@ void collect_leaf_plans(hmv_plan_s *p, std::vector<hmv_plan_s *> &out) {
 // recursively down to the unsplit plans.
 cudaError_t split_down(hmv_plan_s *p, const uint32_t *limbs, const uint8_t *neg, int rows, bool matrix) {
     if (p->children.empty()) return cudaSuccess;
+    if (p->toom4) {
+        uint32_t *const *ddst = p->toom_ptrs + (matrix ? 0 : 7);  // the same rows, uploaded at plan creation
+        uint8_t *const *dn = p->toom_neg_ptrs + (matrix ? 0 : 7);
+        k_toom4_split<<<(rows * 7 + 127) / 128, 128, 0, p->stream>>>(limbs, neg, rows, p->L32, p->split_bits / 32,
+                                                                     p->children[0]->L32, ddst, dn);
+        p->launches_total++;
+        return cudaGetLastError();
+    }
     hmv_plan_s *c0 = p->children[0], *c1 = p->children[1], *cm = p->children[2];
     uint32_t *dst[3];
     uint8_t *dneg[3];
@@ -110,6 +236,23 @@ cudaError_t combine_up(hmv_plan_s *p, const int32_t **out, int *width, bool *is1
         *width = p->Wo;
         *is16 = p->post16;
         return cudaSuccess;
+    }
+    if (p->toom4) {
+        ToomChildren ch;
+        int mask = 0, wc = 0;
+        for (int t = 0; t < 7; ++t) {
+            hmv_plan_s *c = p->children[t];  // unsplit children
+            ch.z[t] = c->post[0];
+            mask |= c->post16 ? (1 << t) : 0;
+            wc = c->Wo;
+        }
+        const dim3 grid(static_cast<unsigned>(p->n), static_cast<unsigned>(std::min(65535, (p->Wo / 4 + 255) / 256)));
+        k_toom4_combine<<<grid, 256, 0, p->stream>>>(ch, mask, wc, p->split_bits / 8, p->combined, p->Wo);
+        p->launches_total++;
+        *out = p->combined;
+        *width = p->Wo;
+        *is16 = false;
+        return cudaGetLastError();
     }
     const int32_t *z[3];
     int w[3];
@@ -153,6 +296,42 @@ hmv_status split_plan_create(hmv_plan_s *p, const hmv_desc &d, int digit_levels)
     int wc = p->children[0]->Wo;
     for (hmv_plan_s *c : p->children) wc = std::max(wc, c->Wo);
     p->Wo = 2 * (p->split_bits / 8) + wc;
+    p->ZW = p->Wo / 4;
+    double macs = 0, issued = 0;
+    for (hmv_plan_s *c : p->children) {
+        macs += c->leaf_macs;
+        issued += c->leaf_macs_issued;
+    }
+    p->leaf_macs = macs;
+    p->leaf_macs_issued = issued;
+    return HMV_OK;
+}
+
+// Seven unsplit children of s + 4 bits (|E_t| < 15 * 2^s), s = the limb
+// boundary nearest above b/4.
+hmv_status toom4_plan_create(hmv_plan_s *p, const hmv_desc &d) {
+    p->toom4 = true;
+    p->split_bits = 32 * ((p->L32 + 3) / 4);
+    for (int t = 0; t < 7; ++t) {
+        hmv_desc cd = d;
+        cd.b = p->split_bits + 4;
+        cd.nrhs = 1;
+        cd.kind = HMV_HANKEL;  // the parent maps the kind onto the Hankel sequence
+        cd.method = HMV_KARATSUBA;
+        cd.flags &= ~(HMV_FLAG_TIMING | HMV_FLAG_DIGIT_SPLIT1 | HMV_FLAG_DIGIT_SPLIT2 | HMV_FLAG_DIGIT_TOOM4);
+        if (p->tn == 128) cd.flags |= HMV_FLAG_TILE128;
+        cd.levels = -1;
+        hmv_plan_s *c = nullptr;
+        hmv_status st = plan_create(&cd, p->stream, false, &c, p->dry_run);
+        if (st != HMV_OK) return st;
+        p->children.push_back(c);
+        p->device_bytes += c->device_bytes;
+        // the combine's int32 sums: at most 6960 (the three largest rows of
+        // the interpolation matrix) times 510 * 2^L per digit
+        if (c->L > 9) return HMV_EUNSUPPORTED;
+    }
+    // 360 Z spans the six shifted products plus one child row and the factor 360
+    p->Wo = 6 * (p->split_bits / 8) + p->children[0]->Wo + 4;
     p->ZW = p->Wo / 4;
     double macs = 0, issued = 0;
     for (hmv_plan_s *c : p->children) {
@@ -258,7 +437,12 @@ cudaError_t split_post(hmv_plan_s *p, int rhs) {
     int w = 0;
     bool z16 = false;
     if (e == cudaSuccess) e = combine_up(p, &z, &w, &z16);
-    if (e == cudaSuccess) e = launch_final_normalize(p, z, rhs, z16);
+    if (e == cudaSuccess) e = launch_final_normalize(p, z, rhs, z16, !p->toom4);
+    if (e == cudaSuccess && p->toom4) {  // the rows are 360 Z: divide, then take the bit lengths
+        k_div_exact<<<(p->n + 127) / 128, 128, 0, p->stream>>>(p->zmag, p->zbits, p->n, p->ZW, p->dstat, rhs * p->n);
+        p->launches_total++;
+        e = cudaGetLastError();
+    }
     for (hmv_plan_s *c : leaves) {
         p->launches_total += c->launches_total;
         c->launches_total = 0;

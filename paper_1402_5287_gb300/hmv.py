@@ -15,6 +15,7 @@ from .inputs import FixedVec
 HANKEL, TOEPLITZ, CIRCULANT = 0, 1, 2
 AUTO, SCHOOLBOOK, KARATSUBA, FFT64 = 0, 1, 2, 3
 FLAG_TIMING, FLAG_SIMT_LEAF, FLAG_DIGIT_SPLIT1, FLAG_DIGIT_SPLIT2, FLAG_TILE128 = 1, 2, 4, 8, 16
+FLAG_DIGIT_TOOM4 = 32
 STATUS = {0: "HMV_OK", 1: "HMV_EINVAL", 2: "HMV_ENOMEM", 3: "HMV_ECUDA", 4: "HMV_ETIMEOUT",
           5: "HMV_ENOTLOADED", 6: "HMV_EFFTBOUND", 7: "HMV_EUNSUPPORTED"}
 
@@ -54,7 +55,7 @@ class Stats(ctypes.Structure):
                 ("fft_piece_bits", ctypes.c_int32), ("fft_log2_len", ctypes.c_int32), ("fft_bound", ctypes.c_double),
                 ("fft_max_dist", ctypes.c_double), ("fft_matvecs", ctypes.c_int64),
                 ("fft_fallbacks", ctypes.c_int64), ("ms_fft", ctypes.c_double),
-                ("leaf_tile_digits", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
+                ("leaf_tile_digits", ctypes.c_int32), ("digit_products", ctypes.c_int32)]
 
 
 class BatchInfo(ctypes.Structure):
