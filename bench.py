@@ -202,7 +202,8 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
 
     method = {"auto": hmv.AUTO, "karatsuba": hmv.KARATSUBA, "fft64": hmv.FFT64, "schoolbook": hmv.SCHOOLBOOK}[args.method]
-    split_flag = {-1: 0, 0: 0, 1: hmv.FLAG_DIGIT_SPLIT1, 2: hmv.FLAG_DIGIT_SPLIT2}[args.digit_split]
+    split_flag = {-1: 0, 0: 0, 1: hmv.FLAG_DIGIT_SPLIT1, 2: hmv.FLAG_DIGIT_SPLIT2, 4: hmv.FLAG_DIGIT_TOOM4,
+                  6: hmv.FLAG_DIGIT_TOOM6}[args.digit_split]
     if args.digit_split == 0 and method == hmv.AUTO:
         method = hmv.KARATSUBA  # no digit split
     tile_flag = hmv.FLAG_TILE128 if args.tile == 128 else 0
@@ -301,7 +302,8 @@ def run_ours(args):
         "ms_per_step": secs_max / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "n": n, "b": b, "kind": "hankel", "method": "karatsuba+tcgen05",
-                   "digit_split_levels": args.digit_split,
+                   "digit_split": DIGIT_SPLIT_NAMES.get(st["digit_products"], str(st["digit_products"])),
+                   "digit_products": st["digit_products"],
                    "levels": st["levels"], "leaves": st["leaves"], "leaf_rows_max": st["leaf_rows_max"],
                    "digits_per_operand": st["digits"], "leaf_tiles": st["leaf_tiles"],
                    "leaf_tile_digits": st["leaf_tile_digits"],
@@ -369,6 +371,10 @@ def compare_kernels(hmv, h, x, n, b, stream):
 
 LEAF_SOURCES = ["paper_1402_5287_gb300/csrc/hmv_leaf_tc.cu", "paper_1402_5287_gb300/csrc/tc_ptx.cuh",
                 "paper_1402_5287_gb300/csrc/hmv_internal.h"]
+
+
+DIGIT_SPLIT_NAMES = {1: "none", 3: "karatsuba, one level", 9: "karatsuba, two levels", 7: "toom-4",
+                     11: "toom-6"}
 
 
 def leaf_sources_hash() -> str:
@@ -511,8 +517,9 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--levels", type=int, default=-1, help="Karatsuba depth (-1: cost model)")
-    ap.add_argument("--digit-split", type=int, choices=[-1, 0, 1, 2], default=-1,
-                    help="levels of Karatsuba on the mantissas on top of the index recursion (-1: cost model)")
+    ap.add_argument("--digit-split", type=int, choices=[-1, 0, 1, 2, 4, 6], default=-1,
+                    help="split of the mantissas on top of the index recursion: Karatsuba levels 1 or 2, "
+                         "Toom-4 or Toom-6 (4, 6), none (0) or the cost model's choice (-1)")
     ap.add_argument("--method", choices=["auto", "karatsuba", "fft64", "schoolbook"], default="auto",
                     help="product method (profiling runs; the metric uses auto = Karatsuba + tcgen05)")
     ap.add_argument("--tile", type=int, choices=[0, 128, 256], default=0,

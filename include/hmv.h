@@ -76,13 +76,15 @@ typedef enum {
 #define HMV_FLAG_DIGIT_SPLIT1 4u  /* one level */
 #define HMV_FLAG_DIGIT_SPLIT2 8u  /* two levels */
 #define HMV_FLAG_TILE128 16u      /* leaf tiles of 128 product digits (default 256) */
-/* Toom-Cook 4-way splitting of the mantissas instead: each mantissa cut into
- * four parts, seven products of about a quarter of the width (evaluated at
- * 0, 1, -1, 2, -2, 1/2 and infinity), the exact rows recovered by integer
- * interpolation and one exact division by 360; HMV_AUTO/HMV_KARATSUBA, not
- * with HMV_FLAG_DIGIT_SPLIT1/2.  HMV_AUTO picks the digit split (none,
- * Karatsuba one or two levels, Toom-4) by its cost model when no flag is set. */
-#define HMV_FLAG_DIGIT_TOOM4 32u
+/* Toom-Cook splitting of the mantissas instead: each mantissa cut into K
+ * parts, 2K-1 products of about 1/K of the width, the exact rows recovered by
+ * integer interpolation and one exact division (by 360 for K = 4, 1008000
+ * for K = 6).  K = 4 evaluates at 0, 1, -1, 2, -2, 1/2 and infinity; K = 6
+ * adds -1/2, 3, -3 and 1/3.  HMV_AUTO/HMV_KARATSUBA; at most one digit-split
+ * flag.  Without one, HMV_AUTO picks the digit split (none, Karatsuba one or
+ * two levels, Toom-4, Toom-6) by its cost model. */
+#define HMV_FLAG_DIGIT_TOOM4 32u  /* needs b > 96 */
+#define HMV_FLAG_DIGIT_TOOM6 64u  /* needs b > 160 */
 
 typedef struct {
     int32_t n;        /* matrix order, n >= 1 */
@@ -133,7 +135,7 @@ typedef struct {
     double ms_fft;           /* with HMV_FLAG_TIMING: time in the FFT path */
     int32_t leaf_tile_digits; /* product digits per leaf tile (256, or 128 with HMV_FLAG_TILE128
                                  or when HMV_AUTO's cost model prefers it); 0 without tiles */
-    int32_t digit_products;  /* products the digit split runs (1; 3 or 9 Karatsuba; 7 Toom-4) */
+    int32_t digit_products;  /* products the digit split runs (1; 3 or 9 Karatsuba; 7 or 11 Toom) */
 } hmv_stats;
 
 /* Create a plan: checks the descriptor, chooses the recursion depth and

@@ -116,15 +116,15 @@ int best_depth(int n, int b, int num_sms, double *cost, int tn = TN_DEFAULT) {
 // estimate of the narrower products is scaled by (1 - 0.055 d): measured
 // leaf times (203.6, 167.1, 149.0 ms) beat the tile count by that much,
 // the narrower operands running at higher clocks under the power cap.
-// Digit split for HMV_AUTO: kToom4 or the number of Karatsuba levels d (3^d
+// Digit split for HMV_AUTO: kToom4, kToom6 or the number of Karatsuba levels d (3^d
 // products of about b/2^d bits, d <= 2), each product at its own best depth,
 // plus the level kernels, which scale with the products' total width (n*b
 // times 1, 3/2, 9/4 for d = 0, 1, 2 and 7/4 for Toom-4; measured 10.4, 15.2,
 // 22.4 ms at n = 8000, b = 33220 for d = 0, 1, 2, about 3.9e-11 s per n*b at
-// d = 0).  The leaf estimate of the narrower products is scaled by
-// (1 - 0.055 d): measured leaf times fall below the tile-count model as the
-// products narrow (Toom-4's quarter-width products count as d = 2).
-constexpr int kToom4 = 4;
+// d = 0; (2K-1)/K for Toom-K).  The leaf estimate of the narrower products is
+// scaled by (1 - 0.055 d): measured leaf times fall below the tile-count model
+// as the products narrow (Toom-K's products count as d = log2 K).
+constexpr int kToom4 = 4, kToom6 = 6;
 int auto_digit_scheme(int n, int b, int num_sms) {
     int best_d = 0;
     double best = 1e300;
@@ -138,12 +138,15 @@ int auto_digit_scheme(int n, int b, int num_sms) {
         bd = 32 * (((bd + 31) / 32 + 1) / 2) + 1;  // the children's width
         mult *= 3.0;
     }
+    // Toom-K: 2K-1 products of s + g bits; narrowing counted as d = log2 K
     const int L32 = (b + 31) / 32;
-    if (L32 >= 4) {
+    for (int K : {4, 6}) {
+        if (L32 < K) continue;
         double leaf = 0;
-        best_depth(n, 32 * ((L32 + 3) / 4) + 4, num_sms, &leaf);
-        const double t = 7.0 * leaf * (1.0 - 0.11) + 3.9e-11 * n * static_cast<double>(b) * 1.75;
-        if (t < best) best_d = kToom4;
+        best_depth(n, 32 * ((L32 + K - 1) / K) + (K == 4 ? 4 : 9), num_sms, &leaf);
+        const double t = (2 * K - 1) * leaf * (1.0 - 0.055 * std::log2(static_cast<double>(K))) +
+                         3.9e-11 * n * static_cast<double>(b) * (2.0 * K - 1) / K;
+        if (t < best) { best = t; best_d = (K == 4) ? kToom4 : kToom6; }
     }
     return best_d;
 }
@@ -268,15 +271,18 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
     if (d.method < HMV_AUTO || d.method > HMV_FFT64) return HMV_EINVAL;
     if (d.levels < -1 || d.levels > kMaxLevels) return HMV_EINVAL;
     if (d.flags & ~(HMV_FLAG_TIMING | HMV_FLAG_SIMT_LEAF | HMV_FLAG_DIGIT_SPLIT1 | HMV_FLAG_DIGIT_SPLIT2 |
-                    HMV_FLAG_TILE128 | HMV_FLAG_DIGIT_TOOM4))
+                    HMV_FLAG_TILE128 | HMV_FLAG_DIGIT_TOOM4 | HMV_FLAG_DIGIT_TOOM6))
         return HMV_EINVAL;
-    if ((d.flags & HMV_FLAG_DIGIT_TOOM4) && (d.flags & (HMV_FLAG_DIGIT_SPLIT1 | HMV_FLAG_DIGIT_SPLIT2)))
-        return HMV_EINVAL;
+    const uint32_t split_flags =
+        d.flags & (HMV_FLAG_DIGIT_SPLIT1 | HMV_FLAG_DIGIT_SPLIT2 | HMV_FLAG_DIGIT_TOOM4 | HMV_FLAG_DIGIT_TOOM6);
+    if (split_flags & (split_flags - 1)) return HMV_EINVAL;  // at most one digit split
     int digit_levels = (d.flags & HMV_FLAG_DIGIT_SPLIT2) ? 2 : ((d.flags & HMV_FLAG_DIGIT_SPLIT1) ? 1 : 0);
     if (d.flags & HMV_FLAG_DIGIT_TOOM4) digit_levels = kToom4;
+    if (d.flags & HMV_FLAG_DIGIT_TOOM6) digit_levels = kToom6;
     if (digit_levels && ((d.method != HMV_AUTO && d.method != HMV_KARATSUBA) || (d.flags & HMV_FLAG_SIMT_LEAF)))
         return HMV_EINVAL;
-    if (digit_levels == kToom4 && (d.b + 31) / 32 < 4) return HMV_EINVAL;  // four parts of at least one limb
+    if ((digit_levels == kToom4 || digit_levels == kToom6) && (d.b + 31) / 32 < digit_levels)
+        return HMV_EINVAL;  // K parts of at least one limb
     if (d.method == HMV_FFT64 ? (d.piece_bits != 0 && (d.piece_bits < 4 || d.piece_bits > 16)) : d.piece_bits != 0)
         return HMV_EINVAL;
     if (static_cast<long long>(d.n) * d.nrhs > (1LL << 30)) return HMV_EINVAL;
@@ -318,27 +324,30 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
     if (dl == 0 && d.method == HMV_AUTO && d.levels < 0 && !(d.flags & HMV_FLAG_SIMT_LEAF) && !external_scratch)
         dl = auto_digit_scheme(n, d.b, p->num_sms);
     digit_levels = dl;
-    p->digit_levels = digit_levels == kToom4 ? 0 : digit_levels;
+    const bool toom = digit_levels == kToom4 || digit_levels == kToom6;
+    p->digit_levels = toom ? 0 : digit_levels;
     if (digit_levels && !external_scratch) {
-        hmv_status st = digit_levels == kToom4 ? toom4_plan_create(p, d) : split_plan_create(p, d, digit_levels);
+        hmv_status st = toom ? toom_plan_create(p, d, digit_levels) : split_plan_create(p, d, digit_levels);
         if (st != HMV_OK) { hmv_free(p); return st; }
-        g(dalloc(p, &p->combined, static_cast<size_t>(n) * p->Wo));
+        if (toom) g(dalloc(p, &p->combined64, static_cast<size_t>(n) * p->Wo));
+        else g(dalloc(p, &p->combined, static_cast<size_t>(n) * p->Wo));
         g(dalloc(p, &p->d_counter, 1));
-        if (p->toom4) {
+        if (toom) {
             // the children's staging rows never move: one table for the matrix side, one for x
-            g(dalloc(p, &p->toom_ptrs, 14));
-            g(dalloc(p, &p->toom_neg_ptrs, 14));
-            uint32_t *tl[14];
-            uint8_t *tn[14];
-            for (int t = 0; t < 7; ++t) {
+            const int P = static_cast<int>(p->children.size());
+            g(dalloc(p, &p->toom_ptrs, 2 * P));
+            g(dalloc(p, &p->toom_neg_ptrs, 2 * P));
+            uint32_t *tl[22];
+            uint8_t *tn[22];
+            for (int t = 0; t < P; ++t) {
                 tl[t] = p->children[t]->h_limbs_d;
                 tn[t] = p->children[t]->h_neg_d;
-                tl[7 + t] = p->children[t]->x_limbs_d;
-                tn[7 + t] = p->children[t]->x_neg_d;
+                tl[P + t] = p->children[t]->x_limbs_d;
+                tn[P + t] = p->children[t]->x_neg_d;
             }
             if (!dry_run && g.err == cudaSuccess) {
-                g(cudaMemcpy(p->toom_ptrs, tl, sizeof tl, cudaMemcpyHostToDevice));
-                g(cudaMemcpy(p->toom_neg_ptrs, tn, sizeof tn, cudaMemcpyHostToDevice));
+                g(cudaMemcpy(p->toom_ptrs, tl, 2 * P * sizeof(uint32_t *), cudaMemcpyHostToDevice));
+                g(cudaMemcpy(p->toom_neg_ptrs, tn, 2 * P * sizeof(uint8_t *), cudaMemcpyHostToDevice));
             }
         }
         if (d.kind == HMV_CIRCULANT) {
@@ -615,7 +624,7 @@ hmv_status hmv_matvec(hmv_plan_t *p, const hmv_vec *x, hmv_vec *y) {
             timing_mark(p, 3);
             g(launch_leaf_normalize(p, p->post[p->L % 2]));
             for (int l = p->L - 1; l >= 0; --l) g(launch_postpass(p, l, p->post[(l + 1) % 2], p->post[l % 2]));
-            g(launch_final_normalize(p, p->post[0], r, p->post16));
+            g(launch_final_normalize(p, p->post[0], r, p->post16 ? 2 : 4));
             timing_mark(p, 4);
         }
         if (p->timing && g.err == cudaSuccess) {

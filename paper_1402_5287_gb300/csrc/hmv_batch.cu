@@ -115,7 +115,7 @@ cudaError_t issue(hmv_batch_s *B) {
             e = launch_leaf_normalize(p, p->post[p->L % 2]);
             for (int l = p->L - 1; l >= 0 && e == cudaSuccess; --l)
                 e = launch_postpass(p, l, p->post[(l + 1) % 2], p->post[l % 2]);
-            if (e == cudaSuccess) e = launch_final_normalize(p, p->post[0], pr.rhs, p->post16);
+            if (e == cudaSuccess) e = launch_final_normalize(p, p->post[0], pr.rhs, p->post16 ? 2 : 4);
             kernels += 2 + p->L;
         }
     }
@@ -447,7 +447,7 @@ extern "C" hmv_status hmv_matvec_many(int32_t count, hmv_plan_t *const *plans, c
         e = launch_leaf_normalize(p, p->post[p->L % 2]);
         for (int l = p->L - 1; l >= 0 && e == cudaSuccess; --l)
             e = launch_postpass(p, l, p->post[(l + 1) % 2], p->post[l % 2]);
-        if (e == cudaSuccess) e = launch_final_normalize(p, p->post[0], 0, p->post16);
+        if (e == cudaSuccess) e = launch_final_normalize(p, p->post[0], 0, p->post16 ? 2 : 4);
         uint32_t *yl = ys[i].on_device ? ys[i].limbs : p->y_limbs_d;
         uint8_t *yn = ys[i].on_device ? ys[i].neg : p->y_neg_d;
         if (e == cudaSuccess) e = launch_round(p, p->n, p->e_h + xs[i].exponent, yl, yn);

@@ -8,6 +8,8 @@
 // renormalised with an exact carry chain, so every intermediate is exact.
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "hmv_internal.h"
 
 namespace hmv {
@@ -40,32 +42,35 @@ __device__ __forceinline__ uint16_t bf16_bits_of_small_int(int v) {
 // above r can hold a new carry, so at most 32 rounds.  wcarry: the carry into
 // lane 0 on entry, the carry out of lane 31 on return (all lanes).
 constexpr int kDigitsPerLane = 32;
-template <bool kBalanced>
-__device__ __forceinline__ int norm_digit(int t, int &carry) {
-    if (kBalanced) return balance(t, carry);
+template <bool kBalanced, class D>
+__device__ __forceinline__ D norm_digit(D t, D &carry) {
+    if (kBalanced) {
+        carry = (t + 128) >> 8;  // floor((t + 128) / 256)
+        return t - (carry << 8);
+    }
     carry = t >> 8;  // floor division by 256
     return t & 255;
 }
-template <bool kBalanced>
-__device__ __forceinline__ void warp_carry(int (&d)[kDigitsPerLane], int lane, int &wcarry) {
-    int c = (lane == 0) ? wcarry : 0;
+template <bool kBalanced, class D>
+__device__ __forceinline__ void warp_carry(D (&d)[kDigitsPerLane], int lane, D &wcarry) {
+    D c = (lane == 0) ? wcarry : D(0);
 #pragma unroll
-    for (int q = 0; q < kDigitsPerLane; ++q) d[q] = norm_digit<kBalanced>(d[q] + c, c);
-    int pending = c, out = 0;
+    for (int q = 0; q < kDigitsPerLane; ++q) d[q] = norm_digit<kBalanced, D>(d[q] + c, c);
+    D pending = c, out = 0;
     for (int round = 0; round <= 32; ++round) {
         out += __shfl_sync(0xffffffffu, pending, 31);
-        int incoming = __shfl_up_sync(0xffffffffu, pending, 1);
+        D incoming = __shfl_up_sync(0xffffffffu, pending, 1);
         if (lane == 0) incoming = 0;
         if (!__any_sync(0xffffffffu, incoming != 0)) break;
         c = incoming;
 #pragma unroll
-        for (int q = 0; q < kDigitsPerLane; ++q) d[q] = norm_digit<kBalanced>(d[q] + c, c);
+        for (int q = 0; q < kDigitsPerLane; ++q) d[q] = norm_digit<kBalanced, D>(d[q] + c, c);
         pending = c;
     }
     wcarry = out;
 }
 __device__ __forceinline__ void warp_balance(int (&d)[kDigitsPerLane], int lane, int &wcarry) {
-    warp_carry<true>(d, lane, wcarry);
+    warp_carry<true, int>(d, lane, wcarry);
 }
 
 // Store a lane's digits [ub, ub + kDigitsPerLane) of a Dp-digit int8 row;
@@ -413,22 +418,33 @@ __global__ void k_postpass(const T *__restrict__ in, int rows_in, T *__restrict_
 // length.  One warp per row: a first pass of carry propagation gives the sign
 // (the carry out of the top), a second one over sign * digits gives the
 // magnitude's digits in [0, 256), four to a limb.
-__device__ __forceinline__ int4 load4(const int32_t *d, int u) { return *reinterpret_cast<const int4 *>(d + u); }
-__device__ __forceinline__ int4 load4(const int16_t *d, int u) {
-    const uint2 w = *reinterpret_cast<const uint2 *>(d + u);
-    return make_int4(static_cast<int16_t>(w.x & 0xFFFFu), static_cast<int>(w.x) >> 16,
-                     static_cast<int16_t>(w.y & 0xFFFFu), static_cast<int>(w.y) >> 16);
+struct Digits4 {
+    long long x, y, z, w;
+};
+__device__ __forceinline__ Digits4 load4(const int32_t *d, int u) {
+    const int4 w = *reinterpret_cast<const int4 *>(d + u);
+    return {w.x, w.y, w.z, w.w};
 }
-template <class T>
-__device__ __forceinline__ void load_lane_digits(const T *d, int ub, int Wo, int (&v)[kDigitsPerLane], int sgn) {
+__device__ __forceinline__ Digits4 load4(const int16_t *d, int u) {
+    const uint2 w = *reinterpret_cast<const uint2 *>(d + u);
+    return {static_cast<int16_t>(w.x & 0xFFFFu), static_cast<int>(w.x) >> 16, static_cast<int16_t>(w.y & 0xFFFFu),
+            static_cast<int>(w.y) >> 16};
+}
+__device__ __forceinline__ Digits4 load4(const int64_t *d, int u) {
+    const longlong2 a = reinterpret_cast<const longlong2 *>(d + u)[0];
+    const longlong2 b = reinterpret_cast<const longlong2 *>(d + u)[1];
+    return {a.x, a.y, b.x, b.y};
+}
+template <class T, class D>
+__device__ __forceinline__ void load_lane_digits(const T *d, int ub, int Wo, D (&v)[kDigitsPerLane], int sgn) {
 #pragma unroll
     for (int g = 0; g < kDigitsPerLane / 4; ++g) {
         const int u = ub + 4 * g;  // Wo is a multiple of 4
-        const int4 w = (u < Wo) ? load4(d, u) : make_int4(0, 0, 0, 0);
-        v[4 * g] = sgn * w.x;
-        v[4 * g + 1] = sgn * w.y;
-        v[4 * g + 2] = sgn * w.z;
-        v[4 * g + 3] = sgn * w.w;
+        const Digits4 w = (u < Wo) ? load4(d, u) : Digits4{0, 0, 0, 0};
+        v[4 * g] = static_cast<D>(sgn * w.x);
+        v[4 * g + 1] = static_cast<D>(sgn * w.y);
+        v[4 * g + 2] = static_cast<D>(sgn * w.z);
+        v[4 * g + 3] = static_cast<D>(sgn * w.w);
     }
 }
 template <class T>
@@ -439,12 +455,13 @@ __global__ void __launch_bounds__(256) k_final_normalize(const T *__restrict__ i
     const int lane = threadIdx.x & 31;
     const int i = static_cast<int>((static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
     if (i >= n) return;  // warp-uniform
+    using D = typename std::conditional<sizeof(T) == 8, long long, int>::type;  // int32 digits with carries fit int
     const T *d = in + static_cast<size_t>(i) * Wo;
-    int v[kDigitsPerLane];
-    int wc = 0;
+    D v[kDigitsPerLane];
+    D wc = 0;
     for (int u0 = 0; u0 < Wo; u0 += 32 * kDigitsPerLane) {
         load_lane_digits(d, u0 + kDigitsPerLane * lane, Wo, v, 1);
-        warp_carry<false>(v, lane, wc);
+        warp_carry<false, D>(v, lane, wc);
     }
     const int sgn = (wc < 0) ? -1 : 1;  // digits in [0, 256) below the carry: the value is negative iff it is
     uint32_t *z = zmag + static_cast<size_t>(row_offset + i) * ZW;
@@ -454,7 +471,7 @@ __global__ void __launch_bounds__(256) k_final_normalize(const T *__restrict__ i
     for (int u0 = 0; u0 < Wo; u0 += 32 * kDigitsPerLane) {
         const int ub = u0 + kDigitsPerLane * lane;
         load_lane_digits(d, ub, Wo, v, sgn);
-        warp_carry<false>(v, lane, wc);
+        warp_carry<false, D>(v, lane, wc);
 #pragma unroll
         for (int g = 0; g < kDigitsPerLane / 4; ++g) {
             const int u = ub + 4 * g;
@@ -672,11 +689,15 @@ cudaError_t launch_postpass(hmv_plan_s *p, int level, const int32_t *in, int32_t
     p->launches_total++;
     return cudaGetLastError();
 }
-cudaError_t launch_final_normalize(hmv_plan_s *p, const int32_t *in, int rhs, bool in16, bool track_max) {
+cudaError_t launch_final_normalize(hmv_plan_s *p, const int32_t *in, int rhs, int digit_bytes, bool track_max) {
     const unsigned blocks = static_cast<unsigned>((p->n + 7) / 8);  // a warp per row
     const int tm = track_max ? 1 : 0;
-    if (in16)
+    if (digit_bytes == 2)
         k_final_normalize<int16_t><<<blocks, 256, 0, p->stream>>>(reinterpret_cast<const int16_t *>(in), p->n, p->Wo,
+                                                                  p->zmag, p->zneg, p->zbits, p->ZW, p->dstat,
+                                                                  rhs * p->n, tm);
+    else if (digit_bytes == 8)
+        k_final_normalize<int64_t><<<blocks, 256, 0, p->stream>>>(reinterpret_cast<const int64_t *>(in), p->n, p->Wo,
                                                                   p->zmag, p->zneg, p->zbits, p->ZW, p->dstat,
                                                                   rhs * p->n, tm);
     else

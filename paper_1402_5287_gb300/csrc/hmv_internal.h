@@ -112,9 +112,10 @@ struct hmv_plan_s {
     // V = V1 2^s + V0) or Toom-4 (seven child plans, V = sum_k V_k 2^(ks))
     std::vector<hmv_plan_s *> children;
     int digit_levels = 0;
-    bool toom4 = false;
-    uint32_t **toom_ptrs = nullptr;          // device tables of the children's limb rows (h: 0..6, x: 7..13)
+    int toom = 0;                            // 4 or 6: Toom-Cook split with 2*toom-1 children
+    uint32_t **toom_ptrs = nullptr;          // device tables of the children's limb rows (h, then x)
     uint8_t **toom_neg_ptrs = nullptr;
+    int64_t *combined64 = nullptr;           // Toom: [n][Wo] int64 digits of Den * Z
     int split_bits = 0;                      // s
     int32_t *combined = nullptr;             // [n][Wo] exact digit vector of this plan's rows
     uint32_t *h_wrap = nullptr;              // circulant: the wrapped Hankel sequence (2n-1 rows)
@@ -160,7 +161,7 @@ cudaError_t launch_validate(hmv_plan_s *p, const uint32_t *limbs, int rows);
 cudaError_t launch_colsum_normalize(hmv_plan_s *p, int rhs);
 cudaError_t leaf_tc_prepare();
 hmv_status split_plan_create(hmv_plan_s *p, const hmv_desc &d, int digit_levels);
-hmv_status toom4_plan_create(hmv_plan_s *p, const hmv_desc &d);
+hmv_status toom_plan_create(hmv_plan_s *p, const hmv_desc &d, int K);
 hmv_status split_load_matrix(hmv_plan_s *p, const uint32_t *h_limbs, const uint8_t *h_neg);
 cudaError_t split_vector_side(hmv_plan_s *p, const uint32_t *xl, const uint8_t *xn);
 cudaError_t split_leaf_launch(hmv_plan_s *p);
@@ -175,9 +176,9 @@ void fill_leaf_problem(hmv_plan_s *p, LeafProblem &lp);
 cudaError_t launch_leaf_simt(hmv_plan_s *p, const int8_t *a_leaf, const int8_t *x_leaf);
 cudaError_t launch_leaf_normalize(hmv_plan_s *p, int32_t *out);
 cudaError_t launch_postpass(hmv_plan_s *p, int level, const int32_t *in, int32_t *out);
-// in16: the digits are int16 (a plan's post buffers with post16), else int32;
+// digit_bytes: 2 (a plan's post buffers with post16), 4 or 8 (int64 Toom sums);
 // track_max: also fold the rows' bit lengths into the plan's maximum
-cudaError_t launch_final_normalize(hmv_plan_s *p, const int32_t *in, int rhs, bool in16, bool track_max = true);
+cudaError_t launch_final_normalize(hmv_plan_s *p, const int32_t *in, int rhs, int digit_bytes, bool track_max = true);
 cudaError_t launch_schoolbook(hmv_plan_s *p, const uint32_t *x_limbs, const uint8_t *x_neg, int rhs);
 cudaError_t launch_round(hmv_plan_s *p, int rows, int e_in, uint32_t *y_limbs, uint8_t *y_neg);
 cudaError_t make_tensor_maps(hmv_plan_s *p);

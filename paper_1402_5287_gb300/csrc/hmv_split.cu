@@ -72,44 +72,83 @@ __global__ void k_combine(const int32_t *__restrict__ z00, const int32_t *__rest
                                                digit_at(z11, b16, i, Wc, u - 2 * ds);
 }
 
-// ------------------------------------------------------------------ Toom-4
-// Each mantissa M = sum_k V_k 2^(ks), k = 0..3 (|V_k| < 2^s, all with the
+// ------------------------------------------------------------------ Toom-Cook
+// Each mantissa M = sum_k V_k 2^(ks), k = 0..K-1 (|V_k| < 2^s, all with the
 // sign of the entry), read as a polynomial in t = 2^s; so are the exact rows,
-// Z(t) = A(h(t)) x(t) = sum_m C_m t^m, m = 0..6.  Seven products at the
-// points 0, 1, -1, 2, -2, 1/2 (homogenised: 8 h(1/2)) and infinity fix the
-// C_m; 360 C_m = sum_t N[m][t] P_t with the integer matrix below (360 times
-// the inverse of the evaluation matrix), and Z = Z(2^s).
-__constant__ int8_t kToomEval[7][4] = {{1, 0, 0, 0}, {1, 1, 1, 1},   {1, -1, 1, -1}, {1, 2, 4, 8},
-                                       {1, -2, 4, -8}, {8, 4, 2, 1}, {0, 0, 0, 1}};
-__constant__ int16_t kToomInterp[7][7] = {{360, 0, 0, 0, 0, 0, 0},
-                                          {-720, -240, -80, 10, 6, 16, -720},
-                                          {-450, 240, 240, -15, -15, 0, 1440},
-                                          {900, 540, -140, -20, 0, -20, 900},
-                                          {90, -60, -60, 15, 15, 0, -1800},
-                                          {-180, -120, 40, 10, -6, 4, -180},
-                                          {0, 0, 0, 0, 0, 0, 360}};
-constexpr uint64_t kToomDen = 360;
+// Z(t) = A(h(t)) x(t) = sum_m C_m t^m, m = 0..2K-2.  2K-1 products at chosen
+// points fix the C_m; Den C_m = sum_t N[m][t] P_t with the integer matrix N =
+// Den times the inverse of the evaluation matrix, and Z = Z(2^s).  A point
+// p/q is evaluated homogenised, q^(K-1) V(p/q) = sum_k V_k p^k q^(K-1-k), and
+// infinity gives the leading part.  The tables are that evaluation matrix's
+// rows and its inverse scaled by Den (exact rational elimination).
+//   K = 4: points 0, 1, -1, 2, -2, 1/2, inf; Den = 360; |E| < 15 * 2^s.
+//   K = 6: points 0, 1, -1, 2, -2, 1/2, -1/2, 3, -3, 1/3, inf; Den = 1008000;
+//          |E| < 364 * 2^s.
+__constant__ int16_t kToom4Eval[7][4] = {{1, 0, 0, 0}, {1, 1, 1, 1},   {1, -1, 1, -1}, {1, 2, 4, 8},
+                                         {1, -2, 4, -8}, {8, 4, 2, 1}, {0, 0, 0, 1}};
+__constant__ int32_t kToom4Interp[7][7] = {{360, 0, 0, 0, 0, 0, 0},
+                                           {-720, -240, -80, 10, 6, 16, -720},
+                                           {-450, 240, 240, -15, -15, 0, 1440},
+                                           {900, 540, -140, -20, 0, -20, 900},
+                                           {90, -60, -60, 15, 15, 0, -1800},
+                                           {-180, -120, 40, 10, -6, 4, -180},
+                                           {0, 0, 0, 0, 0, 0, 360}};
+__constant__ int16_t kToom6Eval[11][6] = {{1, 0, 0, 0, 0, 0},     {1, 1, 1, 1, 1, 1},         {1, -1, 1, -1, 1, -1},
+                                          {1, 2, 4, 8, 16, 32},   {1, -2, 4, -8, 16, -32},    {32, 16, 8, 4, 2, 1},
+                                          {32, -16, 8, -4, 2, -1}, {1, 3, 9, 27, 81, 243},    {1, -3, 9, -27, 81, -243},
+                                          {243, 81, 27, 9, 3, 1}, {0, 0, 0, 0, 0, 1}};
+__constant__ int32_t kToom6Interp[11][11] = {
+    {1008000, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0},
+    {-3024000, 126000, 63000, -2016, -1440, -2880, -576, 60, 48, 108, -3024000},
+    {-5404000, -252000, -252000, 5040, 5040, 2880, 2880, -160, -160, 0, 9072000},
+    {16212000, -927500, -85750, 13328, 5200, 21200, -2672, -375, -204, -579, 16212000},
+    {5880000, 1099000, 1099000, -25760, -25760, -3920, -3920, 840, 840, 0, -48636000},
+    {-17640000, 1834000, -731500, -24640, 4480, -24640, 4480, 630, 0, 630, -17640000},
+    {-1596000, -371000, -371000, 22960, 22960, 1120, 1120, -840, -840, 0, 52920000},
+    {4788000, -570500, 271250, 14672, -9200, 6800, -1328, -375, 204, -171, 4788000},
+    {112000, 28000, 28000, -2240, -2240, -80, -80, 160, 160, 0, -14364000},
+    {-336000, 42000, -21000, -1344, 960, -480, 96, 60, -48, 12, -336000},
+    {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1008000}};
+template <int K>
+struct Toom;
+template <>
+struct Toom<4> {
+    static constexpr int P = 7;
+    static constexpr uint64_t Den = 360;
+    __device__ static int eval(int t, int k) { return kToom4Eval[t][k]; }
+    __device__ static int interp(int m, int t) { return kToom4Interp[m][t]; }
+};
+template <>
+struct Toom<6> {
+    static constexpr int P = 11;
+    static constexpr uint64_t Den = 1008000;
+    __device__ static int eval(int t, int k) { return kToom6Eval[t][k]; }
+    __device__ static int interp(int m, int t) { return kToom6Interp[m][t]; }
+};
 
-// Sign-magnitude rows (L32 limbs) -> the seven children's rows (Lc limbs):
-// child t gets E_t = sum_k kToomEval[t][k] V_k times the entry's sign, as a
-// sign and a magnitude (|E_t| < 15 * 2^s <= 2^(32 Lc)).  One thread per
-// (row, point).
-__global__ void k_toom4_split(const uint32_t *__restrict__ limbs, const uint8_t *__restrict__ neg, int rows,
-                              int L32, int sl, int Lc, uint32_t *const *__restrict__ dst,
-                              uint8_t *const *__restrict__ dneg) {
+// Sign-magnitude rows (L32 limbs) -> the children's rows (Lc limbs): child t
+// gets E_t = sum_k eval(t, k) V_k times the entry's sign, as a sign and a
+// magnitude (|E_t| < 2^(32 Lc)).  One thread per (row, point).
+template <int K>
+__global__ void k_toom_split(const uint32_t *__restrict__ limbs, const uint8_t *__restrict__ neg, int rows, int L32,
+                             int sl, int Lc, uint32_t *const *__restrict__ dst, uint8_t *const *__restrict__ dneg) {
+    constexpr int P = Toom<K>::P;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= rows * 7) return;
-    const int k = idx / 7, t = idx % 7;
+    if (idx >= rows * P) return;
+    const int k = idx / P, t = idx % P;
     const uint32_t *m = limbs + static_cast<size_t>(k) * L32;
     uint32_t *o = dst[t] + static_cast<size_t>(k) * Lc;
+    int c[K];
+#pragma unroll
+    for (int p = 0; p < K; ++p) c[p] = Toom<K>::eval(t, p);
     long long carry = 0;
     for (int q = 0; q < Lc; ++q) {
         long long e = carry;
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
+        for (int p = 0; p < K; ++p) {
             const int li = p * sl + q;  // limb q of V_p
             const uint32_t v = (q < sl && li < L32) ? m[li] : 0u;
-            e += static_cast<long long>(kToomEval[t][p]) * v;
+            e += static_cast<long long>(c[p]) * v;
         }
         o[q] = static_cast<uint32_t>(e);
         carry = e >> 32;  // arithmetic: floor
@@ -117,11 +156,11 @@ __global__ void k_toom4_split(const uint32_t *__restrict__ limbs, const uint8_t 
     // carry is 0 or -1 here (the value fits Lc limbs): -1 means E < 0
     bool any = false;
     if (carry < 0) {
-        unsigned long long c = 1;  // |E| = ~E + 1
+        unsigned long long cc = 1;  // |E| = ~E + 1
         for (int q = 0; q < Lc; ++q) {
-            c += static_cast<unsigned long long>(~o[q]);
-            o[q] = static_cast<uint32_t>(c);
-            c >>= 32;
+            cc += static_cast<unsigned long long>(~o[q]);
+            o[q] = static_cast<uint32_t>(cc);
+            cc >>= 32;
             any |= o[q] != 0;
         }
     } else {
@@ -131,7 +170,7 @@ __global__ void k_toom4_split(const uint32_t *__restrict__ limbs, const uint8_t 
     dneg[t][k] = (any && eneg) ? 1 : 0;
 }
 
-// 360 Z as int32 carry-save digits: z[u] = sum_m sum_t N[m][t] P_t[u - m ds],
+// Den Z as int64 carry-save digits: z[u] = sum_m sum_t N[m][t] P_t[u - m ds],
 // four digits per thread (ds and the children's widths are multiples of 4).
 // The children's digits are int16 (bit t of in16_mask) or int32.
 __device__ __forceinline__ int4 child4(const int32_t *z, bool is16, size_t row, int Wc, int v) {
@@ -143,45 +182,51 @@ __device__ __forceinline__ int4 child4(const int32_t *z, bool is16, size_t row, 
     return *reinterpret_cast<const int4 *>(z + row * Wc + v);
 }
 struct ToomChildren {
-    const int32_t *z[7];
+    const int32_t *z[11];
 };
-__global__ void k_toom4_combine(ToomChildren ch, int in16_mask, int Wc, int ds, int32_t *__restrict__ out, int Wp) {
+template <int K>
+__global__ void k_toom_combine(ToomChildren ch, int in16_mask, int Wc, int ds, int64_t *__restrict__ out, int Wp) {
+    constexpr int P = Toom<K>::P;
     const int i = blockIdx.x;
     for (int g = blockIdx.y * blockDim.x + threadIdx.x; g < Wp / 4; g += gridDim.y * blockDim.x) {
         const int u = 4 * g;
-        int4 acc = make_int4(0, 0, 0, 0);
-        for (int mm = 0; mm < 7; ++mm) {
+        long long a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        for (int mm = 0; mm < P; ++mm) {
             const int v = u - mm * ds;
             if (v < 0) break;
             if (v >= Wc) continue;
 #pragma unroll
-            for (int t = 0; t < 7; ++t) {
-                const int c = kToomInterp[mm][t];
+            for (int t = 0; t < P; ++t) {
+                const long long c = Toom<K>::interp(mm, t);
                 if (c == 0) continue;
                 const int4 d = child4(ch.z[t], (in16_mask >> t) & 1, i, Wc, v);
-                acc.x += c * d.x;
-                acc.y += c * d.y;
-                acc.z += c * d.z;
-                acc.w += c * d.w;
+                a0 += c * d.x;
+                a1 += c * d.y;
+                a2 += c * d.z;
+                a3 += c * d.w;
             }
         }
-        reinterpret_cast<int4 *>(out + static_cast<size_t>(i) * Wp)[g] = acc;
+        int64_t *o = out + static_cast<size_t>(i) * Wp + u;
+        reinterpret_cast<longlong2 *>(o)[0] = make_longlong2(a0, a1);
+        reinterpret_cast<longlong2 *>(o)[1] = make_longlong2(a2, a3);
     }
 }
 
-// |360 Z| limbs -> |Z| limbs (exact: a nonzero remainder is an internal
+// |Den Z| limbs -> |Z| limbs (exact: a nonzero remainder is an internal
 // error), with the bit length and the maximum over rows.
+template <int K>
 __global__ void k_div_exact(uint32_t *__restrict__ zmag, int32_t *__restrict__ zbits, int n, int ZW, int32_t *dstat,
                             int row_offset) {
+    constexpr uint64_t Den = Toom<K>::Den;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint32_t *z = zmag + static_cast<size_t>(row_offset + i) * ZW;
     uint64_t r = 0;
     int bits = 0;
     for (int w = ZW - 1; w >= 0; --w) {
-        const uint64_t cur = (r << 32) | z[w];
-        const uint64_t q = cur / kToomDen;
-        r = cur - q * kToomDen;
+        const uint64_t cur = (r << 32) | z[w];  // r < Den < 2^20: no overflow
+        const uint64_t q = cur / Den;
+        r = cur - q * Den;
         z[w] = static_cast<uint32_t>(q);
         if (bits == 0 && q != 0) bits = 32 * w + (32 - __clz(static_cast<uint32_t>(q)));
     }
@@ -202,11 +247,17 @@ void collect_leaf_plans(hmv_plan_s *p, std::vector<hmv_plan_s *> &out) {
 // recursively down to the unsplit plans.
 cudaError_t split_down(hmv_plan_s *p, const uint32_t *limbs, const uint8_t *neg, int rows, bool matrix) {
     if (p->children.empty()) return cudaSuccess;
-    if (p->toom4) {
-        uint32_t *const *ddst = p->toom_ptrs + (matrix ? 0 : 7);  // the same rows, uploaded at plan creation
-        uint8_t *const *dn = p->toom_neg_ptrs + (matrix ? 0 : 7);
-        k_toom4_split<<<(rows * 7 + 127) / 128, 128, 0, p->stream>>>(limbs, neg, rows, p->L32, p->split_bits / 32,
-                                                                     p->children[0]->L32, ddst, dn);
+    if (p->toom) {
+        const int P = static_cast<int>(p->children.size());
+        uint32_t *const *ddst = p->toom_ptrs + (matrix ? 0 : P);  // the same rows, uploaded at plan creation
+        uint8_t *const *dn = p->toom_neg_ptrs + (matrix ? 0 : P);
+        const unsigned blocks = static_cast<unsigned>((static_cast<long long>(rows) * P + 127) / 128);
+        if (p->toom == 4)
+            k_toom_split<4><<<blocks, 128, 0, p->stream>>>(limbs, neg, rows, p->L32, p->split_bits / 32,
+                                                           p->children[0]->L32, ddst, dn);
+        else
+            k_toom_split<6><<<blocks, 128, 0, p->stream>>>(limbs, neg, rows, p->L32, p->split_bits / 32,
+                                                           p->children[0]->L32, ddst, dn);
         p->launches_total++;
         return cudaGetLastError();
     }
@@ -230,36 +281,42 @@ cudaError_t split_down(hmv_plan_s *p, const uint32_t *limbs, const uint8_t *neg,
 
 // The exact digit vector of a plan's rows after its post-pass (unsplit) or
 // after combining its children (split).
-cudaError_t combine_up(hmv_plan_s *p, const int32_t **out, int *width, bool *is16) {
+cudaError_t combine_up(hmv_plan_s *p, const int32_t **out, int *width, int *digit_bytes) {
     if (p->children.empty()) {
         *out = p->post[0];
         *width = p->Wo;
-        *is16 = p->post16;
+        *digit_bytes = p->post16 ? 2 : 4;
         return cudaSuccess;
     }
-    if (p->toom4) {
+    if (p->toom) {
         ToomChildren ch;
         int mask = 0, wc = 0;
-        for (int t = 0; t < 7; ++t) {
+        for (size_t t = 0; t < p->children.size(); ++t) {
             hmv_plan_s *c = p->children[t];  // unsplit children
             ch.z[t] = c->post[0];
             mask |= c->post16 ? (1 << t) : 0;
             wc = c->Wo;
         }
         const dim3 grid(static_cast<unsigned>(p->n), static_cast<unsigned>(std::min(65535, (p->Wo / 4 + 255) / 256)));
-        k_toom4_combine<<<grid, 256, 0, p->stream>>>(ch, mask, wc, p->split_bits / 8, p->combined, p->Wo);
+        if (p->toom == 4)
+            k_toom_combine<4><<<grid, 256, 0, p->stream>>>(ch, mask, wc, p->split_bits / 8, p->combined64, p->Wo);
+        else
+            k_toom_combine<6><<<grid, 256, 0, p->stream>>>(ch, mask, wc, p->split_bits / 8, p->combined64, p->Wo);
         p->launches_total++;
-        *out = p->combined;
+        *out = reinterpret_cast<const int32_t *>(p->combined64);
         *width = p->Wo;
-        *is16 = false;
+        *digit_bytes = 8;
         return cudaGetLastError();
     }
     const int32_t *z[3];
     int w[3];
     bool s16[3];
     for (int t = 0; t < 3; ++t) {
-        cudaError_t e = combine_up(p->children[t], &z[t], &w[t], &s16[t]);
+        int bytes = 4;
+        cudaError_t e = combine_up(p->children[t], &z[t], &w[t], &bytes);
         if (e != cudaSuccess) return e;
+        if (bytes == 8) return cudaErrorNotSupported;  // Toom plans are never children
+        s16[t] = bytes == 2;
     }
     const int mask = (s16[0] ? 1 : 0) | (s16[2] ? 2 : 0) | (s16[1] ? 4 : 0);
     const dim3 grid(static_cast<unsigned>(p->n), static_cast<unsigned>(std::min(65535, (p->Wo + 255) / 256)));
@@ -267,7 +324,7 @@ cudaError_t combine_up(hmv_plan_s *p, const int32_t **out, int *width, bool *is1
     p->launches_total++;
     *out = p->combined;
     *width = p->Wo;
-    *is16 = false;
+    *digit_bytes = 4;
     return cudaGetLastError();
 }
 
@@ -307,18 +364,20 @@ hmv_status split_plan_create(hmv_plan_s *p, const hmv_desc &d, int digit_levels)
     return HMV_OK;
 }
 
-// Seven unsplit children of s + 4 bits (|E_t| < 15 * 2^s), s = the limb
-// boundary nearest above b/4.
-hmv_status toom4_plan_create(hmv_plan_s *p, const hmv_desc &d) {
-    p->toom4 = true;
-    p->split_bits = 32 * ((p->L32 + 3) / 4);
-    for (int t = 0; t < 7; ++t) {
+// 2K-1 unsplit children of s + g bits (|E_t| < 15 * 2^s for K = 4, 364 * 2^s
+// for K = 6), s = the limb boundary nearest above b/K.
+hmv_status toom_plan_create(hmv_plan_s *p, const hmv_desc &d, int K) {
+    p->toom = K;
+    const int P = 2 * K - 1, grow = (K == 4) ? 4 : 9;
+    p->split_bits = 32 * ((p->L32 + K - 1) / K);
+    for (int t = 0; t < P; ++t) {
         hmv_desc cd = d;
-        cd.b = p->split_bits + 4;
+        cd.b = p->split_bits + grow;
         cd.nrhs = 1;
         cd.kind = HMV_HANKEL;  // the parent maps the kind onto the Hankel sequence
         cd.method = HMV_KARATSUBA;
-        cd.flags &= ~(HMV_FLAG_TIMING | HMV_FLAG_DIGIT_SPLIT1 | HMV_FLAG_DIGIT_SPLIT2 | HMV_FLAG_DIGIT_TOOM4);
+        cd.flags &= ~(HMV_FLAG_TIMING | HMV_FLAG_DIGIT_SPLIT1 | HMV_FLAG_DIGIT_SPLIT2 | HMV_FLAG_DIGIT_TOOM4 |
+                      HMV_FLAG_DIGIT_TOOM6);
         if (p->tn == 128) cd.flags |= HMV_FLAG_TILE128;
         cd.levels = -1;
         hmv_plan_s *c = nullptr;
@@ -326,12 +385,9 @@ hmv_status toom4_plan_create(hmv_plan_s *p, const hmv_desc &d) {
         if (st != HMV_OK) return st;
         p->children.push_back(c);
         p->device_bytes += c->device_bytes;
-        // the combine's int32 sums: at most 6960 (the three largest rows of
-        // the interpolation matrix) times 510 * 2^L per digit
-        if (c->L > 9) return HMV_EUNSUPPORTED;
     }
-    // 360 Z spans the six shifted products plus one child row and the factor 360
-    p->Wo = 6 * (p->split_bits / 8) + p->children[0]->Wo + 4;
+    // Den Z spans the 2K-2 shifted products plus one child row and the factor Den
+    p->Wo = (2 * K - 2) * (p->split_bits / 8) + p->children[0]->Wo + 4;
     p->ZW = p->Wo / 4;
     double macs = 0, issued = 0;
     for (hmv_plan_s *c : p->children) {
@@ -434,12 +490,15 @@ cudaError_t split_post(hmv_plan_s *p, int rhs) {
             e = launch_postpass(c, l, c->post[(l + 1) % 2], c->post[l % 2]);
     }
     const int32_t *z = nullptr;
-    int w = 0;
-    bool z16 = false;
-    if (e == cudaSuccess) e = combine_up(p, &z, &w, &z16);
-    if (e == cudaSuccess) e = launch_final_normalize(p, z, rhs, z16, !p->toom4);
-    if (e == cudaSuccess && p->toom4) {  // the rows are 360 Z: divide, then take the bit lengths
-        k_div_exact<<<(p->n + 127) / 128, 128, 0, p->stream>>>(p->zmag, p->zbits, p->n, p->ZW, p->dstat, rhs * p->n);
+    int w = 0, zb = 4;
+    if (e == cudaSuccess) e = combine_up(p, &z, &w, &zb);
+    if (e == cudaSuccess) e = launch_final_normalize(p, z, rhs, zb, p->toom == 0);
+    if (e == cudaSuccess && p->toom) {  // the rows are Den Z: divide, then take the bit lengths
+        const unsigned blocks = static_cast<unsigned>((p->n + 127) / 128);
+        if (p->toom == 4)
+            k_div_exact<4><<<blocks, 128, 0, p->stream>>>(p->zmag, p->zbits, p->n, p->ZW, p->dstat, rhs * p->n);
+        else
+            k_div_exact<6><<<blocks, 128, 0, p->stream>>>(p->zmag, p->zbits, p->n, p->ZW, p->dstat, rhs * p->n);
         p->launches_total++;
         e = cudaGetLastError();
     }

@@ -56,12 +56,16 @@ def test_plan_rejects_bad_descriptors_without_gpu(lib, field, value):
 
 @pytest.mark.parametrize("b,flags,method", [(4096, hmv.FLAG_DIGIT_TOOM4 | hmv.FLAG_DIGIT_SPLIT1, 0),
                                            (4096, hmv.FLAG_DIGIT_TOOM4 | hmv.FLAG_DIGIT_SPLIT2, 0),
-                                           (96, hmv.FLAG_DIGIT_TOOM4, 0),
+                                           (4096, hmv.FLAG_DIGIT_TOOM4 | hmv.FLAG_DIGIT_TOOM6, 0),
+                                           (4096, hmv.FLAG_DIGIT_TOOM6 | hmv.FLAG_DIGIT_SPLIT1, 0),
+                                           (96, hmv.FLAG_DIGIT_TOOM4, 0), (160, hmv.FLAG_DIGIT_TOOM6, 0),
                                            (4096, hmv.FLAG_DIGIT_TOOM4 | hmv.FLAG_SIMT_LEAF, 0),
-                                           (4096, hmv.FLAG_DIGIT_TOOM4, 3), (4096, hmv.FLAG_DIGIT_TOOM4, 1)])
-def test_toom4_rejects_bad_combinations_without_gpu(lib, b, flags, method):
-    """Toom-4 needs four parts of at least one limb, the integer tensor-core
-    path and no second digit split."""
+                                           (4096, hmv.FLAG_DIGIT_TOOM6 | hmv.FLAG_SIMT_LEAF, 0),
+                                           (4096, hmv.FLAG_DIGIT_TOOM4, 3), (4096, hmv.FLAG_DIGIT_TOOM4, 1),
+                                           (4096, hmv.FLAG_DIGIT_TOOM6, 3)])
+def test_toom_rejects_bad_combinations_without_gpu(lib, b, flags, method):
+    """Toom-K needs K parts of at least one limb, the integer tensor-core path
+    and no second digit split."""
     d = hmv.Desc(16, b, 1, 0, method, -1, flags, 0)
     out = ctypes.c_void_p()
     assert lib.hmv_plan(ctypes.byref(d), None, ctypes.byref(out)) == 1

@@ -1,4 +1,4 @@
-"""Toom-Cook 4-way split of the mantissas (HMV_FLAG_DIGIT_TOOM4): bit-exact
+"""Toom-Cook splits of the mantissas (HMV_FLAG_DIGIT_TOOM4/6): bit-exact
 parity with the oracle on every row, for every matrix kind, at worst-case
 digits, and equality with the Karatsuba split at full size."""
 import numpy as np
@@ -14,6 +14,7 @@ from test_gpu_parity import assert_same, oracle_matvec, sampled_parity
 pytestmark = pytest.mark.gpu
 
 T4 = hmv.FLAG_DIGIT_TOOM4
+TOOMS = [(hmv.FLAG_DIGIT_TOOM4, 7), (hmv.FLAG_DIGIT_TOOM6, 11)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -28,60 +29,73 @@ def run(n, b, h, x, flags=T4, kind=hmv.HANKEL, nrhs=1, method=hmv.AUTO):
         return p.matvec(x), p.stats()
 
 
-# b: the narrowest split (four one-limb parts), ragged top parts, several tiles
-@pytest.mark.parametrize("n,b", [(64, 2048), (100, 700), (1, 128), (7, 129), (30, 4100), (140, 1000), (3, 97)])
-def test_toom4_all_rows(n, b):
+# b: the narrowest splits (one-limb parts), ragged top parts, several tiles
+@pytest.mark.parametrize("flags,products", TOOMS)
+@pytest.mark.parametrize("n,b", [(64, 2048), (100, 700), (1, 192), (7, 257), (30, 4100), (140, 1000), (3, 193)])
+def test_toom_all_rows(flags, products, n, b):
     h = uniform_vec(70 + n, 0, 2 * n - 1, b, 1)
     x = uniform_vec(70 + n, 1, n, b, -1)
-    y, st = run(n, b, h, x)
-    assert st["digit_products"] == 7
+    y, st = run(n, b, h, x, flags=flags)
+    assert st["digit_products"] == products
     assert_same(y, oracle_matvec(oracle.HANKEL, n, h, x))
 
 
+def test_toom4_narrowest():
+    n, b = 9, 97  # four parts: three full limbs and one bit
+    h = uniform_vec(71, 0, 2 * n - 1, b)
+    x = uniform_vec(71, 1, n, b)
+    assert_same(run(n, b, h, x)[0], oracle_matvec(oracle.HANKEL, n, h, x))
+
+
+@pytest.mark.parametrize("flags,products", TOOMS)
 @pytest.mark.parametrize("kind", [hmv.TOEPLITZ, hmv.CIRCULANT])
-def test_toom4_toeplitz_circulant(kind):
+def test_toom_toeplitz_circulant(flags, products, kind):
     n, b = 90, 600
     hlen = n if kind == hmv.CIRCULANT else 2 * n - 1
     h = uniform_vec(73, 0, hlen, b)
     x = uniform_vec(73, 1, n, b)
     ok = oracle.TOEPLITZ if kind == hmv.TOEPLITZ else oracle.CIRCULANT
-    assert_same(run(n, b, h, x, kind=kind)[0], oracle_matvec(ok, n, h, x))
+    assert_same(run(n, b, h, x, flags=flags, kind=kind)[0], oracle_matvec(ok, n, h, x))
 
 
-def test_toom4_block_rhs_and_method_karatsuba():
+@pytest.mark.parametrize("flags,products", TOOMS)
+def test_toom_block_rhs_and_method_karatsuba(flags, products):
     n, b, k = 40, 900, 3
     h = uniform_vec(75, 0, 2 * n - 1, b)
     x = uniform_vec(75, 1, n * k, b)
-    y, _ = run(n, b, h, x, nrhs=k, method=hmv.KARATSUBA)
+    y, _ = run(n, b, h, x, flags=flags, nrhs=k, method=hmv.KARATSUBA)
     y0, _ = run(n, b, h, x, flags=0, nrhs=k, method=hmv.KARATSUBA)
     assert_same(y, y0)
 
 
-def test_toom4_worst_case_digits():
+@pytest.mark.parametrize("flags,products", TOOMS)
+def test_toom_worst_case_digits(flags, products):
     """All-ones and 0x8080.. mantissas with mixed signs: every evaluation
     point at its largest magnitude."""
     n, b = 70, 2046
     for m in (int("80" * ((b + 7) // 8), 16) & ((1 << b) - 1), (1 << b) - 1):
         h = FixedVec.from_ints([m if k % 3 else -m for k in range(2 * n - 1)], b, 0)
         x = FixedVec.from_ints([-m if j % 2 else m for j in range(n)], b, 0)
-        assert_same(run(n, b, h, x)[0], oracle_matvec(oracle.HANKEL, n, h, x))
+        assert_same(run(n, b, h, x, flags=flags)[0], oracle_matvec(oracle.HANKEL, n, h, x))
         h = FixedVec.from_ints([-m] * (2 * n - 1), b, 0)
         x = FixedVec.from_ints([-m] * n, b, 0)
-        assert_same(run(n, b, h, x)[0], oracle_matvec(oracle.HANKEL, n, h, x))
+        assert_same(run(n, b, h, x, flags=flags)[0], oracle_matvec(oracle.HANKEL, n, h, x))
 
 
-def test_toom4_zero_vector():
+@pytest.mark.parametrize("flags,products", TOOMS)
+def test_toom_zero_vector(flags, products):
     n, b = 20, 512
     h = uniform_vec(77, 0, 2 * n - 1, b)
     x = FixedVec.from_ints([0] * n, b, -3)
-    assert_same(run(n, b, h, x)[0], oracle_matvec(oracle.HANKEL, n, h, x))
+    assert_same(run(n, b, h, x, flags=flags)[0], oracle_matvec(oracle.HANKEL, n, h, x))
 
 
-def test_toom4_large_workload_matches_karatsuba_split():
+def test_toom_large_workload_matches_karatsuba_split():
     n, b, h, x = workload("large")
-    y, st = run(n, b, h, x)
-    assert st["digit_products"] == 7
     y2, st2 = run(n, b, h, x, flags=hmv.FLAG_DIGIT_SPLIT2)
     assert st2["digit_products"] == 9
-    assert_same(y, y2)
+    for flags, products in TOOMS:
+        y, st = run(n, b, h, x, flags=flags)
+        assert st["digit_products"] == products
+        assert_same(y, y2)
     sampled_parity(oracle.HANKEL, n, h, x, y, 3, 13)
