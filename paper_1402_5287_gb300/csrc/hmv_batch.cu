@@ -378,7 +378,8 @@ extern "C" hmv_status hmv_matvec_many(int32_t count, hmv_plan_t *const *plans, c
         if (!p) return HMV_EINVAL;
         for (int k = 0; k < i; ++k)
             if (plans[k] == p) return HMV_EINVAL;  // a plan holds one product at a time
-        if (p->method != HMV_KARATSUBA || !p->hrev || p->external_scratch || p->nrhs != 1) return HMV_EUNSUPPORTED;
+        if (p->method != HMV_KARATSUBA || p->external_scratch || p->nrhs != 1) return HMV_EUNSUPPORTED;
+        if (p->children.empty() && !p->hrev) return HMV_EUNSUPPORTED;  // CUDA-core leaves
         if (!p->loaded) return HMV_ENOTLOADED;
         const hmv_vec &x = xs[i], &y = ys[i];
         if (x.len != p->n || x.nrhs != 1 || x.b != p->b || !x.limbs || !x.neg || x.reserved ||
@@ -406,20 +407,26 @@ extern "C" hmv_status hmv_matvec_many(int32_t count, hmv_plan_t *const *plans, c
         }
         if (e == cudaSuccess) e = cudaMemsetAsync(p->dstat, 0, 8 * sizeof(int32_t), s);
         if (e == cudaSuccess) e = launch_validate(p, xl, p->n);
+        if (!p->children.empty()) {  // digit split: the vector side of every unsplit descendant
+            if (e == cudaSuccess) e = split_vector_side(p, xl, xn);
+            continue;
+        }
         if (e == cudaSuccess) e = launch_encode(p, xl, xn, p->n, 0, p->x_lvl[0]);
         for (int l = 0; l < p->L && e == cudaSuccess; ++l)
             e = launch_prepass(p, l, false, p->x_lvl[l % 2], p->x_lvl[(l + 1) % 2]);
         if (e == cudaSuccess) e = launch_pack_vector(p, p->x_lvl[p->L % 2]);
     }
+    std::vector<hmv_plan_s *> leafplans;  // every unsplit plan, split plans contributing their descendants
+    for (int i = 0; i < count; ++i) collect_leaf_plans(plans[i], leafplans);
     // one persistent launch per tile width present (normally one)
     for (int tn : {256, 128}) {
         std::vector<LeafProblem> gp;
         std::vector<Tile> gt;
-        for (int i = 0; i < count; ++i) {
-            if (plans[i]->tn != tn) continue;
+        for (hmv_plan_s *c : leafplans) {
+            if (c->tn != tn) continue;
             const int idx = static_cast<int>(gp.size());
-            gp.push_back(plans[i]->hprob);
-            for (Tile t : plans[i]->tiles) {
+            gp.push_back(c->hprob);
+            for (Tile t : c->tiles) {
                 t.prob = idx;
                 gt.push_back(t);
             }
@@ -444,10 +451,14 @@ extern "C" hmv_status hmv_matvec_many(int32_t count, hmv_plan_t *const *plans, c
     }
     for (int i = 0; i < count && e == cudaSuccess; ++i) {
         hmv_plan_s *p = plans[i];
-        e = launch_leaf_normalize(p, p->post[p->L % 2]);
-        for (int l = p->L - 1; l >= 0 && e == cudaSuccess; --l)
-            e = launch_postpass(p, l, p->post[(l + 1) % 2], p->post[l % 2]);
-        if (e == cudaSuccess) e = launch_final_normalize(p, p->post[0], 0, p->post16 ? 2 : 4);
+        if (!p->children.empty()) {
+            e = split_post(p, 0);
+        } else {
+            e = launch_leaf_normalize(p, p->post[p->L % 2]);
+            for (int l = p->L - 1; l >= 0 && e == cudaSuccess; --l)
+                e = launch_postpass(p, l, p->post[(l + 1) % 2], p->post[l % 2]);
+            if (e == cudaSuccess) e = launch_final_normalize(p, p->post[0], 0, p->post16 ? 2 : 4);
+        }
         uint32_t *yl = ys[i].on_device ? ys[i].limbs : p->y_limbs_d;
         uint8_t *yn = ys[i].on_device ? ys[i].neg : p->y_neg_d;
         if (e == cudaSuccess) e = launch_round(p, p->n, p->e_h + xs[i].exponent, yl, yn);

@@ -160,6 +160,8 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
 cudaError_t launch_validate(hmv_plan_s *p, const uint32_t *limbs, int rows);
 cudaError_t launch_colsum_normalize(hmv_plan_s *p, int rhs);
 cudaError_t leaf_tc_prepare();
+// the unsplit plans under p (p itself when it is not split)
+void collect_leaf_plans(hmv_plan_s *p, std::vector<hmv_plan_s *> &out);
 hmv_status split_plan_create(hmv_plan_s *p, const hmv_desc &d, int digit_levels);
 hmv_status toom_plan_create(hmv_plan_s *p, const hmv_desc &d, int K);
 hmv_status split_load_matrix(hmv_plan_s *p, const uint32_t *h_limbs, const uint8_t *h_neg);

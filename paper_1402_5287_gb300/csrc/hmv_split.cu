@@ -235,13 +235,6 @@ __global__ void k_div_exact(uint32_t *__restrict__ zmag, int32_t *__restrict__ z
     atomicMax(dstat + 1, bits);
 }
 
-void collect_leaf_plans(hmv_plan_s *p, std::vector<hmv_plan_s *> &out) {
-    if (p->children.empty()) {
-        out.push_back(p);
-        return;
-    }
-    for (hmv_plan_s *c : p->children) collect_leaf_plans(c, out);
-}
 
 // Split rows of a vector into the three children's staging buffers,
 // recursively down to the unsplit plans.
@@ -329,6 +322,14 @@ cudaError_t combine_up(hmv_plan_s *p, const int32_t **out, int *width, int *digi
 }
 
 }  // namespace
+
+void collect_leaf_plans(hmv_plan_s *p, std::vector<hmv_plan_s *> &out) {
+    if (p->children.empty()) {
+        out.push_back(p);
+        return;
+    }
+    for (hmv_plan_s *c : p->children) collect_leaf_plans(c, out);
+}
 
 // Children of a split plan (called from plan_create).
 hmv_status split_plan_create(hmv_plan_s *p, const hmv_desc &d, int digit_levels) {

@@ -99,3 +99,35 @@ def test_toom_large_workload_matches_karatsuba_split():
         assert st["digit_products"] == products
         assert_same(y, y2)
     sampled_parity(oracle.HANKEL, n, h, x, y, 3, 13)
+
+
+def test_matvec_many_mixes_split_and_unsplit_plans():
+    """hmv_matvec_many with Toom, Karatsuba-split and unsplit plans in one
+    step (the serving path): every result equals the plan's own matvec."""
+    import torch
+    dev = torch.device("cuda", 0)
+    cases = [(60, 3000, hmv.FLAG_DIGIT_TOOM6, hmv.HANKEL), (45, 2000, hmv.FLAG_DIGIT_TOOM4, hmv.TOEPLITZ),
+             (50, 1500, hmv.FLAG_DIGIT_SPLIT1, hmv.HANKEL), (30, 700, 0, hmv.CIRCULANT), (20, 300, 0, hmv.HANKEL)]
+    plans, keep, xp, yp, exps, want = [], [], [], [], [], []
+    for i, (n, b, flags, kind) in enumerate(cases):
+        hlen = n if kind == hmv.CIRCULANT else 2 * n - 1
+        h = uniform_vec(300 + i, 0, hlen, b, 1)
+        x = uniform_vec(300 + i, 1, n, b, -2)
+        want.append(run(n, b, h, x, flags=flags, kind=kind, method=hmv.KARATSUBA)[0])
+        p = hmv.Plan(n, b, kind=kind, method=hmv.KARATSUBA, flags=flags)
+        p.load_matrix(h)
+        xl = torch.from_numpy(x.limbs.view(np.int32)).to(dev)
+        xn = torch.from_numpy(x.neg).to(dev)
+        yl, yn = torch.empty_like(xl), torch.empty_like(xn)
+        plans.append(p)
+        keep.append((xl, xn, yl, yn, b))
+        xp.append((xl.data_ptr(), xn.data_ptr()))
+        yp.append((yl.data_ptr(), yn.data_ptr()))
+        exps.append(x.exponent)
+    for _ in range(2):  # twice: the descendants' buffers are reused
+        out = hmv.matvec_many_device(plans, xp, yp, exps)
+        torch.cuda.synchronize()
+        for (xl, xn, yl, yn, b), e, w in zip(keep, out, want):
+            assert_same(FixedVec(yl.cpu().numpy().view(np.uint32), yn.cpu().numpy(), b, e), w)
+    for p in plans:
+        p.close()
