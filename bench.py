@@ -370,7 +370,7 @@ def compare_kernels(hmv, h, x, n, b, stream):
 
 
 LEAF_SOURCES = ["paper_1402_5287_gb300/csrc/hmv_leaf_tc.cu", "paper_1402_5287_gb300/csrc/tc_ptx.cuh",
-                "paper_1402_5287_gb300/csrc/hmv_internal.h"]
+                "paper_1402_5287_gb300/csrc/hmv_leaf.h"]
 
 
 DIGIT_SPLIT_NAMES = {1: "none", 3: "karatsuba, one level", 9: "karatsuba, two levels", 7: "toom-4",

@@ -570,45 +570,66 @@ __global__ void k_round_check(const uint32_t *__restrict__ zmag, const int32_t *
     if (half) atomicExch(dstat + 2, 1);  // an all-ones mantissa is odd: a half rounds up
 }
 
-__global__ void k_round(const uint32_t *__restrict__ zmag, const uint8_t *__restrict__ zneg, int n, int nrhs, int ZW,
-                        int b, int L32, int e_in, int reverse, int32_t *dstat, uint32_t *__restrict__ y,
-                        uint8_t *__restrict__ yneg) {
-    int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n * nrhs) return;
+// One warp per output row: the lanes cut the b-bit mantissa limbs out of |Z|
+// and OR the bits below the rounding position in parallel; the rare carry of
+// a round-up runs through the limbs on lane 0.
+__global__ void __launch_bounds__(256) k_round(const uint32_t *__restrict__ zmag, const uint8_t *__restrict__ zneg,
+                                               int n, int nrhs, int ZW, int b, int L32, int e_in, int reverse,
+                                               int32_t *dstat, uint32_t *__restrict__ y, uint8_t *__restrict__ yneg) {
+    const int lane = threadIdx.x & 31;
+    const int idx = static_cast<int>((static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
+    if (idx >= n * nrhs) return;  // warp-uniform
     if (dstat[0] != DEV_OK) return;  // an earlier stage failed: write nothing
     const int rhs = idx / n, i = idx % n;
     const int orow = rhs * n + (reverse ? (n - 1 - i) : i);
     uint32_t *o = y + static_cast<size_t>(orow) * L32;
     const int B = dstat[1];
     if (B == 0) {
-        for (int w = 0; w < L32; ++w) o[w] = 0;
-        yneg[orow] = 0;
-        if (idx == 0) dstat[3] = e_in;
+        for (int w = lane; w < L32; w += 32) o[w] = 0;
+        if (lane == 0) {
+            yneg[orow] = 0;
+            if (idx == 0) dstat[3] = e_in;
+        }
         return;
     }
     const long long t = static_cast<long long>(B) - b + dstat[2];
     const uint32_t *z = zmag + static_cast<size_t>(idx) * ZW;
     const int topbits = b - 32 * (L32 - 1);
-    uint32_t any = 0;
-    for (int w = 0; w < L32; ++w) {
+    uint32_t first = 0;  // lane 0: limb 0 of the truncated mantissa
+    for (int w = lane; w < L32; w += 32) {
         uint32_t v = zword(z, ZW, t + 32LL * w);
         if (w == L32 - 1 && topbits < 32) v &= (1u << topbits) - 1u;
         o[w] = v;
+        if (w == 0) first = v;
     }
     if (t > 0) {
-        uint32_t half, sticky;
-        round_bits(z, ZW, t, half, sticky);
-        if (half && (sticky || (o[0] & 1u))) {
+        const uint32_t half = zbit(z, ZW, t - 1);
+        // sticky: any bit of |Z| below position t - 1
+        const long long below = t - 1;
+        const long long full = min(below >> 5, static_cast<long long>(ZW));
+        uint32_t st = 0;
+        for (long long w = lane; w < full; w += 32) st |= z[w];
+        const int rem = static_cast<int>(below & 31);
+        if (lane == 0 && rem && full < ZW) st |= z[full] & ((1u << rem) - 1u);
+        const bool sticky = __any_sync(0xffffffffu, st != 0);
+        const uint32_t lsb = __shfl_sync(0xffffffffu, first, 0) & 1u;
+        __syncwarp();  // the lanes' limbs are in place before lane 0 carries through them
+        if (lane == 0 && half && (sticky || lsb)) {
             for (int w = 0; w < L32; ++w) {
                 o[w] += 1u;
                 if (o[w] != 0) break;
             }
             if (topbits < 32 && (o[L32 - 1] >> topbits)) atomicExch(dstat, DEV_OVERFLOW);
         }
+        __syncwarp();
     }
-    for (int w = 0; w < L32; ++w) any |= o[w];
-    yneg[orow] = (any && zneg[idx]) ? 1 : 0;
-    if (idx == 0) dstat[3] = static_cast<int32_t>(e_in + t - b);
+    uint32_t any = 0;
+    for (int w = lane; w < L32; w += 32) any |= o[w];
+    const bool nonzero = __any_sync(0xffffffffu, any != 0);
+    if (lane == 0) {
+        yneg[orow] = (nonzero && zneg[idx]) ? 1 : 0;
+        if (idx == 0) dstat[3] = static_cast<int32_t>(e_in + t - b);
+    }
 }
 
 }  // namespace
@@ -716,8 +737,9 @@ cudaError_t launch_colsum_normalize(hmv_plan_s *p, int rhs) {
 
 cudaError_t launch_round(hmv_plan_s *p, int rows, int e_in, uint32_t *y_limbs, uint8_t *y_neg) {
     k_round_check<<<blocks_for(rows, 128), 128, 0, p->stream>>>(p->zmag, p->zbits, rows, p->ZW, p->b, p->dstat);
-    k_round<<<blocks_for(rows, 128), 128, 0, p->stream>>>(p->zmag, p->zneg, p->n, p->nrhs, p->ZW, p->b, p->L32, e_in,
-                                                          p->kind != HMV_HANKEL ? 1 : 0, p->dstat, y_limbs, y_neg);
+    k_round<<<static_cast<unsigned>((rows + 7) / 8), 256, 0, p->stream>>>(  // a warp per row
+        p->zmag, p->zneg, p->n, p->nrhs, p->ZW, p->b, p->L32, e_in, p->kind != HMV_HANKEL ? 1 : 0, p->dstat, y_limbs,
+        y_neg);
     p->launches_total += 2;
     return cudaGetLastError();
 }
@@ -729,7 +751,8 @@ cudaError_t launch_colsum_round_raw(const __int128 *colsum, int n, int L32, uint
                                     uint32_t *y, uint8_t *yneg, cudaStream_t stream) {
     k_colsum_normalize<<<blocks_for(n, 128), 128, 0, stream>>>(colsum, n, 2 * L32, zmag, zneg, zbits, ZW, dstat, 0);
     k_round_check<<<blocks_for(n, 128), 128, 0, stream>>>(zmag, zbits, n, ZW, b, dstat);
-    k_round<<<blocks_for(n, 128), 128, 0, stream>>>(zmag, zneg, n, 1, ZW, b, L32, e_in, reverse, dstat, y, yneg);
+    k_round<<<static_cast<unsigned>((n + 7) / 8), 256, 0, stream>>>(zmag, zneg, n, 1, ZW, b, L32, e_in, reverse, dstat,
+                                                                    y, yneg);  // a warp per row
     return cudaGetLastError();
 }
 

@@ -197,13 +197,13 @@ __global__ void k_toom_combine(ToomChildren ch, int in16_mask, int Wc, int ds, i
             if (v >= Wc) continue;
 #pragma unroll
             for (int t = 0; t < P; ++t) {
-                const long long c = Toom<K>::interp(mm, t);
+                const int c = Toom<K>::interp(mm, t);  // |c| < 2^31, |d| < 2^31: 32 x 32 -> 64-bit products
                 if (c == 0) continue;
                 const int4 d = child4(ch.z[t], (in16_mask >> t) & 1, i, Wc, v);
-                a0 += c * d.x;
-                a1 += c * d.y;
-                a2 += c * d.z;
-                a3 += c * d.w;
+                a0 += static_cast<long long>(c) * d.x;
+                a1 += static_cast<long long>(c) * d.y;
+                a2 += static_cast<long long>(c) * d.z;
+                a3 += static_cast<long long>(c) * d.w;
             }
         }
         int64_t *o = out + static_cast<size_t>(i) * Wp + u;
@@ -213,28 +213,55 @@ __global__ void k_toom_combine(ToomChildren ch, int in16_mask, int Wc, int ds, i
 }
 
 // |Den Z| limbs -> |Z| limbs (exact: a nonzero remainder is an internal
-// error), with the bit length and the maximum over rows.
+// error), with the bit length and the maximum over rows.  One warp per row.
+// Long division from the top limb carries the remainder r -> (r 2^32 + z_w)
+// mod Den, an affine map of r modulo Den; each lane composes the maps of its
+// segment of limbs, a warp scan composes the segments, and then every lane
+// divides its own segment starting from the remainder that enters it.
 template <int K>
-__global__ void k_div_exact(uint32_t *__restrict__ zmag, int32_t *__restrict__ zbits, int n, int ZW, int32_t *dstat,
-                            int row_offset) {
+__global__ void __launch_bounds__(256) k_div_exact(uint32_t *__restrict__ zmag, int32_t *__restrict__ zbits, int n,
+                                                   int ZW, int32_t *dstat, int row_offset) {
     constexpr uint64_t Den = Toom<K>::Den;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    constexpr uint64_t K32 = (uint64_t(1) << 32) % Den;
+    const int lane = threadIdx.x & 31;
+    const int i = static_cast<int>((static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
+    if (i >= n) return;  // warp-uniform
     uint32_t *z = zmag + static_cast<size_t>(row_offset + i) * ZW;
-    uint64_t r = 0;
+    // lane l: limbs [lo, hi), lane 0 the most significant segment
+    const int seg = (ZW + 31) / 32;
+    const int hi = max(0, ZW - lane * seg), lo = max(0, ZW - (lane + 1) * seg);
+    uint64_t A = 1, B = 0;  // this segment's map r -> (A r + B) mod Den
+    for (int w = hi - 1; w >= lo; --w) {
+        A = (A * K32) % Den;
+        B = (B * K32 + z[w]) % Den;
+    }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {  // inclusive scan: maps of lanes 0..l, applied in lane order
+        const uint64_t pa = __shfl_up_sync(0xffffffffu, A, off);
+        const uint64_t pb = __shfl_up_sync(0xffffffffu, B, off);
+        if (lane >= off) {
+            B = (A * pb + B) % Den;
+            A = (A * pa) % Den;
+        }
+    }
+    uint64_t r = __shfl_up_sync(0xffffffffu, B, 1);  // remainder entering this segment
+    if (lane == 0) r = 0;
     int bits = 0;
-    for (int w = ZW - 1; w >= 0; --w) {
+    for (int w = hi - 1; w >= lo; --w) {
         const uint64_t cur = (r << 32) | z[w];  // r < Den < 2^20: no overflow
         const uint64_t q = cur / Den;
         r = cur - q * Den;
         z[w] = static_cast<uint32_t>(q);
         if (bits == 0 && q != 0) bits = 32 * w + (32 - __clz(static_cast<uint32_t>(q)));
     }
-    if (r != 0) atomicExch(dstat, DEV_OVERFLOW);
-    zbits[row_offset + i] = bits;
-    atomicMax(dstat + 1, bits);
+    if (lane == 31 && r != 0) atomicExch(dstat, DEV_OVERFLOW);  // the lowest segment ends the division
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) bits = max(bits, __shfl_xor_sync(0xffffffffu, bits, off));
+    if (lane == 0) {
+        zbits[row_offset + i] = bits;
+        atomicMax(dstat + 1, bits);
+    }
 }
-
 
 // Split rows of a vector into the three children's staging buffers,
 // recursively down to the unsplit plans.
@@ -495,11 +522,11 @@ cudaError_t split_post(hmv_plan_s *p, int rhs) {
     if (e == cudaSuccess) e = combine_up(p, &z, &w, &zb);
     if (e == cudaSuccess) e = launch_final_normalize(p, z, rhs, zb, p->toom == 0);
     if (e == cudaSuccess && p->toom) {  // the rows are Den Z: divide, then take the bit lengths
-        const unsigned blocks = static_cast<unsigned>((p->n + 127) / 128);
+        const unsigned blocks = static_cast<unsigned>((p->n + 7) / 8);  // a warp per row
         if (p->toom == 4)
-            k_div_exact<4><<<blocks, 128, 0, p->stream>>>(p->zmag, p->zbits, p->n, p->ZW, p->dstat, rhs * p->n);
+            k_div_exact<4><<<blocks, 256, 0, p->stream>>>(p->zmag, p->zbits, p->n, p->ZW, p->dstat, rhs * p->n);
         else
-            k_div_exact<6><<<blocks, 128, 0, p->stream>>>(p->zmag, p->zbits, p->n, p->ZW, p->dstat, rhs * p->n);
+            k_div_exact<6><<<blocks, 256, 0, p->stream>>>(p->zmag, p->zbits, p->n, p->ZW, p->dstat, rhs * p->n);
         p->launches_total++;
         e = cudaGetLastError();
     }
