@@ -357,21 +357,20 @@ __global__ void k_leaf_normalize(const uint8_t *__restrict__ dig, const int32_t 
     const uint32_t *d = reinterpret_cast<const uint32_t *>(dig + r * Uo);
     const int32_t *cy = carry + r * NUB;
     T *o = out + (static_cast<size_t>(leaf) * rowsX + row) * Wo;
-    for (int g = threadIdx.x; g < Wo / 4; g += blockDim.x) {
-        const int u0 = 4 * g;
-        int4 v = make_int4(0, 0, 0, 0);
-        if (u0 < Uo) {
-            const uint32_t w = d[g];
-            v = make_int4(w & 0xFF, (w >> 8) & 0xFF, (w >> 16) & 0xFF, w >> 24);
-        }
+    for (int g8 = threadIdx.x; g8 < Wo / 8; g8 += blockDim.x) {  // 8 digits per step; Uo, Wo multiples of 8
+        const int u0 = 8 * g8;
+        const uint2 w = (u0 < Uo) ? reinterpret_cast<const uint2 *>(d)[g8] : make_uint2(0, 0);
+        int4 v0 = make_int4(w.x & 0xFF, (w.x >> 8) & 0xFF, (w.x >> 16) & 0xFF, w.x >> 24);
+        const int4 v1 = make_int4(w.y & 0xFF, (w.y >> 8) & 0xFF, (w.y >> 16) & 0xFF, w.y >> 24);
         if (u0 > 0 && u0 <= Uo && u0 % tn == 0) {
             const int32_t c = cy[u0 / tn - 1];
-            v.x += c & 0xFF;
-            v.y += (c >> 8) & 0xFF;
-            v.z += (c >> 16) & 0xFF;
-            v.w += c >> 24;  // arithmetic shift: the signed top part
+            v0.x += c & 0xFF;
+            v0.y += (c >> 8) & 0xFF;
+            v0.z += (c >> 16) & 0xFF;
+            v0.w += c >> 24;  // arithmetic shift: the signed top part
         }
-        store4<T>(o, g, v);
+        store4<T>(o, 2 * g8, v0);
+        store4<T>(o, 2 * g8 + 1, v1);
     }
 }
 

@@ -184,11 +184,13 @@ __device__ __forceinline__ int4 child4(const int32_t *z, bool is16, size_t row, 
 struct ToomChildren {
     const int32_t *z[11];
 };
+// One block per row: the row's children windows are re-read by the shifted
+// terms while they are still in L1/L2.
 template <int K>
 __global__ void k_toom_combine(ToomChildren ch, int in16_mask, int Wc, int ds, int64_t *__restrict__ out, int Wp) {
     constexpr int P = Toom<K>::P;
     const int i = blockIdx.x;
-    for (int g = blockIdx.y * blockDim.x + threadIdx.x; g < Wp / 4; g += gridDim.y * blockDim.x) {
+    for (int g = threadIdx.x; g < Wp / 4; g += blockDim.x) {
         const int u = 4 * g;
         long long a0 = 0, a1 = 0, a2 = 0, a3 = 0;
         for (int mm = 0; mm < P; ++mm) {
@@ -317,7 +319,7 @@ cudaError_t combine_up(hmv_plan_s *p, const int32_t **out, int *width, int *digi
             mask |= c->post16 ? (1 << t) : 0;
             wc = c->Wo;
         }
-        const dim3 grid(static_cast<unsigned>(p->n), static_cast<unsigned>(std::min(65535, (p->Wo / 4 + 255) / 256)));
+        const unsigned grid = static_cast<unsigned>(p->n);  // one block per row
         if (p->toom == 4)
             k_toom_combine<4><<<grid, 256, 0, p->stream>>>(ch, mask, wc, p->split_bits / 8, p->combined64, p->Wo);
         else
