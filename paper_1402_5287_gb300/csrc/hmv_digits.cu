@@ -18,6 +18,16 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// Per-plan buffers of a group of plans with the same geometry (the products
+// of a digit split), one launch for all of them: blockIdx.y (z for
+// pack_vector) selects the plan.  A single plan is a group of one.
+constexpr int kMaxGroup = 12;
+struct PlanPtrs {
+    const void *in[kMaxGroup];
+    const void *in2[kMaxGroup];
+    void *out[kMaxGroup];
+};
+
 inline int blocks_for(long long work, int threads = kThreads) {
     return static_cast<int>((work + threads - 1) / threads);
 }
@@ -101,9 +111,11 @@ __device__ __forceinline__ void store_lane_digits(const int (&d)[kDigitsPerLane]
 // circ_n > 0: row k takes entry (circ_n - 1 - k) mod circ_n (circulant ->
 // Toeplitz sequence); otherwise row k takes entry k.
 // One warp per row, windows of 32 x kDigitsPerLane digits (8 limbs per lane).
-__global__ void __launch_bounds__(256) k_encode(const uint32_t *__restrict__ limbs, const uint8_t *__restrict__ neg,
-                                                int rows, int L32, int b, int circ_n, int8_t *__restrict__ out, int Dp,
+__global__ void __launch_bounds__(256) k_encode(PlanPtrs g, int rows, int L32, int b, int circ_n, int Dp,
                                                 int32_t *dstat) {
+    const uint32_t *__restrict__ limbs = static_cast<const uint32_t *>(g.in[blockIdx.y]);
+    const uint8_t *__restrict__ neg = static_cast<const uint8_t *>(g.in2[blockIdx.y]);
+    int8_t *__restrict__ out = static_cast<int8_t *>(g.out[blockIdx.y]);
     const int lane = threadIdx.x & 31;
     const int k = static_cast<int>((static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
     if (k >= rows) return;  // warp-uniform
@@ -146,10 +158,11 @@ __device__ __forceinline__ void load_slice64(const int8_t *r, bool on, int u, in
     for (int h = 0; h < 4; ++h)
         v[h] = (on && u + 16 * h < Dp) ? *reinterpret_cast<const uint4 *>(r + u + 16 * h) : make_uint4(0, 0, 0, 0);
 }
-__global__ void __launch_bounds__(128) k_prepass(const int8_t *__restrict__ in, int in_rows,
-                                                 const int *__restrict__ in_size, int8_t *__restrict__ out,
+__global__ void __launch_bounds__(128) k_prepass(PlanPtrs g, int in_rows, const int *__restrict__ in_size,
                                                  int out_rows, const int *__restrict__ out_size, int nchildren, int Dp,
                                                  int matrix_side, int32_t *dstat) {
+    const int8_t *__restrict__ in = static_cast<const int8_t *>(g.in[blockIdx.y]);
+    int8_t *__restrict__ out = static_cast<int8_t *>(g.out[blockIdx.y]);
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
     const int child = w / out_rows, k = w % out_rows;
     if (child >= nchildren) return;
@@ -253,9 +266,10 @@ __global__ void k_pack_matrix(const int8_t *__restrict__ leafd, int rowsA, const
 // rows from two aligned 8-byte words (consecutive threads store consecutive
 // rows).
 constexpr int kPackSeg = 128;
-__global__ void __launch_bounds__(128) k_pack_vector(const int8_t *__restrict__ leafd, int rowsX,
-                                                     const int *__restrict__ size, uint16_t *__restrict__ xg, int RX,
+__global__ void __launch_bounds__(128) k_pack_vector(PlanPtrs g, int rowsX, const int *__restrict__ size, int RX,
                                                      int Dp, int seg) {
+    const int8_t *__restrict__ leafd = static_cast<const int8_t *>(g.in[blockIdx.z]);
+    uint16_t *__restrict__ xg = static_cast<uint16_t *>(g.out[blockIdx.z]);
     __shared__ __align__(16) uint64_t s[kPackSeg + 2];
     const int leaf = blockIdx.x / RX, j = blockIdx.x % RX;
     const int chunks = Dp / 8 + 1;
@@ -348,9 +362,11 @@ __device__ __forceinline__ void store4<int16_t>(int16_t *o, int g, int4 v) {
                                                  (static_cast<uint32_t>(v.z) & 0xFFFFu) | (static_cast<uint32_t>(v.w) << 16));
 }
 template <class T>
-__global__ void k_leaf_normalize(const uint8_t *__restrict__ dig, const int32_t *__restrict__ carry,
-                                 const int *__restrict__ size, int MT, int Uo, int NUB, T *__restrict__ out, int rowsX,
-                                 int Wo, int tn) {
+__global__ void k_leaf_normalize(PlanPtrs g, const int *__restrict__ size, int MT, int Uo, int NUB, int rowsX, int Wo,
+                                 int tn) {
+    const uint8_t *__restrict__ dig = static_cast<const uint8_t *>(g.in[blockIdx.y]);
+    const int32_t *__restrict__ carry = static_cast<const int32_t *>(g.in2[blockIdx.y]);
+    T *__restrict__ out = static_cast<T *>(g.out[blockIdx.y]);
     const int leaf = blockIdx.x / rowsX, row = blockIdx.x % rowsX;
     if (row >= size[leaf]) return;
     const size_t r = static_cast<size_t>(leaf) * MT * TM + row;
@@ -379,8 +395,9 @@ __global__ void k_leaf_normalize(const uint8_t *__restrict__ dig, const int32_t 
 // digit-wise without carries (digits grow by at most one bit per level).
 // One block per output row, 16 bytes of digits per thread and step.
 template <class T>
-__global__ void k_postpass(const T *__restrict__ in, int rows_in, T *__restrict__ out, int rows_out,
-                           const int *__restrict__ parent_size, int Wo) {
+__global__ void k_postpass(PlanPtrs g, int rows_in, int rows_out, const int *__restrict__ parent_size, int Wo) {
+    const T *__restrict__ in = static_cast<const T *>(g.in[blockIdx.y]);
+    T *__restrict__ out = static_cast<T *>(g.out[blockIdx.y]);
     const int nu = blockIdx.x / rows_out, i = blockIdx.x % rows_out;
     if (i >= parent_size[nu]) return;
     const int k = i >> 1;
@@ -634,23 +651,71 @@ __global__ void __launch_bounds__(256) k_round(const uint32_t *__restrict__ zmag
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
-cudaError_t launch_encode(hmv_plan_s *p, const uint32_t *limbs, const uint8_t *neg, int rows, int circulant_n,
-                          int8_t *out) {
-    k_encode<<<static_cast<unsigned>((rows + 7) / 8), 256, 0, p->stream>>>(limbs, neg, rows, p->L32, p->b,
-                                                                           circulant_n, out, p->Dp, p->dstat);  // a warp per row
+namespace {
+cudaError_t encode_group(hmv_plan_s *p, const PlanPtrs &g, int G, int rows, int circulant_n) {
+    k_encode<<<dim3(static_cast<unsigned>((rows + 7) / 8), G), 256, 0, p->stream>>>(  // a warp per row
+        g, rows, p->L32, p->b, circulant_n, p->Dp, p->dstat);
     p->launches_total++;
     return cudaGetLastError();
 }
-
-cudaError_t launch_prepass(hmv_plan_s *p, int level, bool matrix_side, const int8_t *in, int8_t *out) {
+cudaError_t prepass_group(hmv_plan_s *p, const PlanPtrs &g, int G, int level, bool matrix_side) {
     const LevelGeom &pl = p->lv[level], &cl = p->lv[level + 1];
     const int in_rows = matrix_side ? pl.rowsA : pl.rowsX;
     const int out_rows = matrix_side ? cl.rowsA : cl.rowsX;
     const long long rows = static_cast<long long>(cl.nodes) * out_rows;  // one thread per child row
-    k_prepass<<<blocks_for(rows, 128), 128, 0, p->stream>>>(in, in_rows, pl.d_size, out, out_rows, cl.d_size,
-                                                            cl.nodes, p->Dp, matrix_side ? 1 : 0, p->dstat);
+    k_prepass<<<dim3(blocks_for(rows, 128), G), 128, 0, p->stream>>>(g, in_rows, pl.d_size, out_rows, cl.d_size,
+                                                                     cl.nodes, p->Dp, matrix_side ? 1 : 0, p->dstat);
     p->launches_total++;
     return cudaGetLastError();
+}
+cudaError_t pack_vector_group(hmv_plan_s *p, const PlanPtrs &g, int G) {
+    const LevelGeom &ll = p->lv[p->L];
+    const int chunks = p->Dp / 8 + 1;
+    const int nseg = (chunks + kPackSeg - 1) / kPackSeg;
+    const int seg = (chunks + nseg - 1) / nseg;  // balanced segments of at most kPackSeg chunks
+    const dim3 grid(static_cast<unsigned>(ll.nodes) * p->RX, nseg, G);
+    k_pack_vector<<<grid, 128, 0, p->stream>>>(g, ll.rowsX, ll.d_size, p->RX, p->Dp, seg);
+    p->launches_total++;
+    return cudaGetLastError();
+}
+cudaError_t leaf_normalize_group(hmv_plan_s *p, const PlanPtrs &g, int G) {
+    const LevelGeom &ll = p->lv[p->L];
+    const dim3 grid(static_cast<unsigned>(ll.nodes) * ll.rowsX, G);  // one block per leaf row
+    if (p->post16)
+        k_leaf_normalize<int16_t><<<grid, 128, 0, p->stream>>>(g, ll.d_size, p->MT, p->Uo, p->NUB, ll.rowsX, p->Wo,
+                                                               p->tn);
+    else
+        k_leaf_normalize<int32_t><<<grid, 128, 0, p->stream>>>(g, ll.d_size, p->MT, p->Uo, p->NUB, ll.rowsX, p->Wo,
+                                                               p->tn);
+    p->launches_total++;
+    return cudaGetLastError();
+}
+cudaError_t postpass_group(hmv_plan_s *p, const PlanPtrs &g, int G, int level) {
+    const LevelGeom &pl = p->lv[level], &cl = p->lv[level + 1];
+    const dim3 grid(static_cast<unsigned>(pl.nodes) * pl.rowsX, G);  // one block per output row
+    if (p->post16)
+        k_postpass<int16_t><<<grid, 128, 0, p->stream>>>(g, cl.rowsX, pl.rowsX, pl.d_size, p->Wo);
+    else
+        k_postpass<int32_t><<<grid, 128, 0, p->stream>>>(g, cl.rowsX, pl.rowsX, pl.d_size, p->Wo);
+    p->launches_total++;
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_encode(hmv_plan_s *p, const uint32_t *limbs, const uint8_t *neg, int rows, int circulant_n,
+                          int8_t *out) {
+    PlanPtrs g{};
+    g.in[0] = limbs;
+    g.in2[0] = neg;
+    g.out[0] = out;
+    return encode_group(p, g, 1, rows, circulant_n);
+}
+
+cudaError_t launch_prepass(hmv_plan_s *p, int level, bool matrix_side, const int8_t *in, int8_t *out) {
+    PlanPtrs g{};
+    g.in[0] = in;
+    g.out[0] = out;
+    return prepass_group(p, g, 1, level, matrix_side);
 }
 
 cudaError_t launch_pack_matrix(hmv_plan_s *p, const int8_t *leaf_digits) {
@@ -663,14 +728,10 @@ cudaError_t launch_pack_matrix(hmv_plan_s *p, const int8_t *leaf_digits) {
 }
 
 cudaError_t launch_pack_vector(hmv_plan_s *p, const int8_t *leaf_digits) {
-    const LevelGeom &ll = p->lv[p->L];
-    const int chunks = p->Dp / 8 + 1;
-    const int nseg = (chunks + kPackSeg - 1) / kPackSeg;
-    const int seg = (chunks + nseg - 1) / nseg;  // balanced segments of at most kPackSeg chunks
-    const dim3 grid(static_cast<unsigned>(ll.nodes) * p->RX, nseg);
-    k_pack_vector<<<grid, 128, 0, p->stream>>>(leaf_digits, ll.rowsX, ll.d_size, p->xg, p->RX, p->Dp, seg);
-    p->launches_total++;
-    return cudaGetLastError();
+    PlanPtrs g{};
+    g.in[0] = leaf_digits;
+    g.out[0] = p->xg;
+    return pack_vector_group(p, g, 1);
 }
 
 cudaError_t launch_leaf_simt(hmv_plan_s *p, const int8_t *a_leaf, const int8_t *x_leaf) {
@@ -685,29 +746,84 @@ cudaError_t launch_leaf_simt(hmv_plan_s *p, const int8_t *a_leaf, const int8_t *
 }
 
 cudaError_t launch_leaf_normalize(hmv_plan_s *p, int32_t *out) {
-    const LevelGeom &ll = p->lv[p->L];
-    const unsigned blocks = static_cast<unsigned>(ll.nodes) * ll.rowsX;
-    if (p->post16)
-        k_leaf_normalize<int16_t><<<blocks, 128, 0, p->stream>>>(p->leaf_dig, p->leaf_carry, ll.d_size, p->MT, p->Uo,
-                                                                 p->NUB, reinterpret_cast<int16_t *>(out), ll.rowsX,
-                                                                 p->Wo, p->tn);
-    else
-        k_leaf_normalize<int32_t><<<blocks, 128, 0, p->stream>>>(p->leaf_dig, p->leaf_carry, ll.d_size, p->MT, p->Uo,
-                                                                 p->NUB, out, ll.rowsX, p->Wo, p->tn);
-    p->launches_total++;
-    return cudaGetLastError();
+    PlanPtrs g{};
+    g.in[0] = p->leaf_dig;
+    g.in2[0] = p->leaf_carry;
+    g.out[0] = out;
+    return leaf_normalize_group(p, g, 1);
 }
 
 cudaError_t launch_postpass(hmv_plan_s *p, int level, const int32_t *in, int32_t *out) {
-    const LevelGeom &pl = p->lv[level], &cl = p->lv[level + 1];
-    const unsigned blocks = static_cast<unsigned>(pl.nodes) * pl.rowsX;  // one block per output row
-    if (p->post16)
-        k_postpass<int16_t><<<blocks, 128, 0, p->stream>>>(reinterpret_cast<const int16_t *>(in), cl.rowsX,
-                                                           reinterpret_cast<int16_t *>(out), pl.rowsX, pl.d_size, p->Wo);
-    else
-        k_postpass<int32_t><<<blocks, 128, 0, p->stream>>>(in, cl.rowsX, out, pl.rowsX, pl.d_size, p->Wo);
-    p->launches_total++;
-    return cudaGetLastError();
+    PlanPtrs g{};
+    g.in[0] = in;
+    g.out[0] = out;
+    return postpass_group(p, g, 1, level);
+}
+
+// The vector side (encode of each plan's staged x, every pre-pass level, the
+// shifted bf16 copies) and the post side (leaf normalise, every post-pass
+// level) of up to kMaxGroup plans with the same geometry, one launch per
+// kernel and level for all of them, on ps[0]'s stream.
+cudaError_t launch_vector_side_group(hmv_plan_s *const *ps, int G) {
+    if (G < 1 || G > kMaxGroup) return cudaErrorInvalidValue;
+    hmv_plan_s *p = ps[0];
+    PlanPtrs g{};
+    for (int k = 0; k < G; ++k) {
+        g.in[k] = ps[k]->x_limbs_d;
+        g.in2[k] = ps[k]->x_neg_d;
+        g.out[k] = ps[k]->x_lvl[0];
+    }
+    cudaError_t e = encode_group(p, g, G, p->n, 0);
+    for (int l = 0; l < p->L && e == cudaSuccess; ++l) {
+        for (int k = 0; k < G; ++k) {
+            g.in[k] = ps[k]->x_lvl[l % 2];
+            g.out[k] = ps[k]->x_lvl[(l + 1) % 2];
+        }
+        e = prepass_group(p, g, G, l, false);
+    }
+    if (e == cudaSuccess) {
+        for (int k = 0; k < G; ++k) {
+            g.in[k] = ps[k]->x_lvl[p->L % 2];
+            g.out[k] = ps[k]->xg;
+        }
+        e = pack_vector_group(p, g, G);
+    }
+    return e;
+}
+
+cudaError_t launch_post_group(hmv_plan_s *const *ps, int G) {
+    if (G < 1 || G > kMaxGroup) return cudaErrorInvalidValue;
+    hmv_plan_s *p = ps[0];
+    PlanPtrs g{};
+    for (int k = 0; k < G; ++k) {
+        g.in[k] = ps[k]->leaf_dig;
+        g.in2[k] = ps[k]->leaf_carry;
+        g.out[k] = ps[k]->post[p->L % 2];
+    }
+    cudaError_t e = leaf_normalize_group(p, g, G);
+    for (int l = p->L - 1; l >= 0 && e == cudaSuccess; --l) {
+        for (int k = 0; k < G; ++k) {
+            g.in[k] = ps[k]->post[(l + 1) % 2];
+            g.out[k] = ps[k]->post[l % 2];
+        }
+        e = postpass_group(p, g, G, l);
+    }
+    return e;
+}
+
+// Plans that one grouped launch can serve together.
+bool same_geometry(hmv_plan_s *const *ps, int G) {
+    if (G < 1 || G > kMaxGroup) return false;
+    const hmv_plan_s *a = ps[0];
+    if (!a->xg || a->L < 0 || static_cast<int>(a->lv.size()) != a->L + 1) return false;
+    for (int k = 1; k < G; ++k) {
+        const hmv_plan_s *c = ps[k];
+        if (!c->xg || c->n != a->n || c->L != a->L || c->L32 != a->L32 || c->b != a->b || c->Dp != a->Dp ||
+            c->RX != a->RX || c->MT != a->MT || c->Uo != a->Uo || c->NUB != a->NUB || c->Wo != a->Wo ||
+            c->tn != a->tn || c->post16 != a->post16)
+            return false;
+    }
+    return true;
 }
 cudaError_t launch_final_normalize(hmv_plan_s *p, const int32_t *in, int rhs, int digit_bytes, bool track_max) {
     const unsigned blocks = static_cast<unsigned>((p->n + 7) / 8);  // a warp per row

@@ -141,6 +141,12 @@ cudaError_t encode_tensor_map_B(hmv_plan_s *p, uint16_t *xg, CUtensorMap *map);
 void fill_leaf_problem(hmv_plan_s *p, LeafProblem &lp);
 cudaError_t launch_leaf_simt(hmv_plan_s *p, const int8_t *a_leaf, const int8_t *x_leaf);
 cudaError_t launch_leaf_normalize(hmv_plan_s *p, int32_t *out);
+// grouped launches for plans of one geometry (same_geometry): the vector side
+// from each plan's staged x to its bf16 copies, and leaf normalise plus the
+// post-pass down to each plan's level-0 rows
+bool same_geometry(hmv_plan_s *const *ps, int G);
+cudaError_t launch_vector_side_group(hmv_plan_s *const *ps, int G);
+cudaError_t launch_post_group(hmv_plan_s *const *ps, int G);
 cudaError_t launch_postpass(hmv_plan_s *p, int level, const int32_t *in, int32_t *out);
 // digit_bytes: 2 (a plan's post buffers with post16), 4 or 8 (int64 Toom sums);
 // track_max: also fold the rows' bit lengths into the plan's maximum

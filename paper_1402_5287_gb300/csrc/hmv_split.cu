@@ -460,6 +460,9 @@ cudaError_t split_vector_side(hmv_plan_s *p, const uint32_t *xl, const uint8_t *
     cudaError_t e = split_down(p, xl, xn, p->n, false);
     std::vector<hmv_plan_s *> leaves;
     collect_leaf_plans(p, leaves);
+    for (hmv_plan_s *c : leaves) c->stream = p->stream;
+    if (e == cudaSuccess && same_geometry(leaves.data(), static_cast<int>(leaves.size())))
+        return launch_vector_side_group(leaves.data(), static_cast<int>(leaves.size()));
     for (hmv_plan_s *c : leaves) {
         if (e != cudaSuccess) break;
         c->stream = p->stream;
@@ -513,11 +516,15 @@ cudaError_t split_post(hmv_plan_s *p, int rhs) {
     std::vector<hmv_plan_s *> leaves;
     collect_leaf_plans(p, leaves);
     cudaError_t e = cudaSuccess;
-    for (hmv_plan_s *c : leaves) {
-        if (e != cudaSuccess) break;
-        e = launch_leaf_normalize(c, c->post[c->L % 2]);
-        for (int l = c->L - 1; l >= 0 && e == cudaSuccess; --l)
-            e = launch_postpass(c, l, c->post[(l + 1) % 2], c->post[l % 2]);
+    if (same_geometry(leaves.data(), static_cast<int>(leaves.size()))) {
+        e = launch_post_group(leaves.data(), static_cast<int>(leaves.size()));
+    } else {
+        for (hmv_plan_s *c : leaves) {
+            if (e != cudaSuccess) break;
+            e = launch_leaf_normalize(c, c->post[c->L % 2]);
+            for (int l = c->L - 1; l >= 0 && e == cudaSuccess; --l)
+                e = launch_postpass(c, l, c->post[(l + 1) % 2], c->post[l % 2]);
+        }
     }
     const int32_t *z = nullptr;
     int w = 0, zb = 4;
