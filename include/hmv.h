@@ -260,6 +260,40 @@ hmv_status hmv_schoolbook_noalloc(int32_t n, int32_t b, int32_t kind,
                                   const uint32_t *x_limbs, const uint8_t *x_neg, int32_t x_exponent,
                                   uint32_t *y_limbs, uint8_t *y_neg, int32_t *y_exponent, void *stream);
 
+/* ---- Exact vector operations for Krylov drivers (Lanczos) --------------
+ * The paper's introduction motivates fast multiprecision Hankel products by
+ * Lanczos-type iterations on these matrices; the two calls below are the
+ * vector operations such an iteration needs next to hmv_matvec, with the
+ * same exactness contract: every result is the exact one before a single
+ * rounding.  Both run on the plan's stream, take device vectors (on_device =
+ * 1) of the plan's n and b with nrhs = 1, and return when the result is
+ * ready.  The paper describes neither call; they serve the driver in
+ * paper_1402_5287_gb300/lanczos.py. */
+
+/* A b-bit scalar: value = (neg ? -1 : 1) * M * 2^exponent, M = sum_q limbs[q]
+ * 2^(32 q) (host memory, 1 <= nlimbs <= ceil(b/32) + 1). */
+typedef struct {
+    const uint32_t *limbs;
+    int32_t nlimbs;
+    int32_t neg;
+    int32_t exponent;
+} hmv_scalar;
+
+/* Exact inner product sum_i X_i Y_i of the signed mantissas of x and y (its
+ * value is that integer times 2^(x.exponent + y.exponent - 2b)), written to
+ * z (host, zl >= 2*ceil(b/32) + 2 limbs, little-endian magnitude) and
+ * *z_neg.  HMV_EINVAL for mismatched vectors or a short z. */
+hmv_status hmv_dot(hmv_plan_t *plan, const hmv_vec *x, const hmv_vec *y, uint32_t *z, int32_t zl,
+                   uint8_t *z_neg);
+
+/* y = sum_{k<count} c[k] * xs[k] (count 1..3), exact, then rounded to b bits
+ * with the least shared exponent and round-half-even (the same rule as
+ * hmv_matvec); y->exponent is written.  y may be one of the xs[k]: every
+ * term is read before y is written.
+ * HMV_EUNSUPPORTED when two terms differ in scale by more than 128 ceil(b/32)
+ * bits. */
+hmv_status hmv_lincomb(hmv_plan_t *plan, int32_t count, const hmv_scalar *c, const hmv_vec *xs, hmv_vec *y);
+
 /* Static description of a status code. */
 const char *hmv_status_string(hmv_status s);
 

@@ -1,0 +1,215 @@
+// Exact vector operations for Krylov drivers on top of the resident-matrix
+// products: the inner product of two b-bit block vectors and a short linear
+// combination rounded once to b bits.  A Lanczos iteration on the Hankel
+// matrix (the consumer of fast multiprecision Hankel products named in the
+// introduction of Beliakov, arXiv:1402.5287) needs exactly these next to
+// y = A x.
+//
+// Both are schoolbook sums of 32-bit limb products in signed 128-bit column
+// sums (the same representation as the plain product kernel), normalised to
+// limbs by k_colsum_normalize.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "hmv_internal.h"
+
+namespace hmv {
+namespace {
+
+constexpr int kDotRows = 64;  // rows summed by one thread of the inner product
+
+// partial[c][w] = sum over rows i of chunk c of s_i * sum_a X_i[a] Y_i[w - a]
+// (s_i = +-1 from the two signs), for limb columns w in [0, 2 L32).
+__global__ void k_dot_partial(const uint32_t *__restrict__ x, const uint8_t *__restrict__ xn,
+                              const uint32_t *__restrict__ y, const uint8_t *__restrict__ yn, int n, int L32,
+                              __int128 *__restrict__ partial) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    const int W = 2 * L32;
+    if (w >= W) return;
+    const int i0 = c * kDotRows, i1 = min(n, i0 + kDotRows);
+    const int a0 = max(0, w - (L32 - 1)), a1 = min(L32 - 1, w);
+    unsigned __int128 pos = 0, neg = 0;
+    for (int i = i0; i < i1; ++i) {
+        const uint32_t *xr = x + static_cast<size_t>(i) * L32;
+        const uint32_t *yr = y + static_cast<size_t>(i) * L32;
+        unsigned __int128 acc = 0;
+        for (int a = a0; a <= a1; ++a) acc += static_cast<unsigned long long>(xr[a]) * yr[w - a];
+        if (xn[i] != yn[i]) neg += acc;
+        else pos += acc;
+    }
+    partial[static_cast<size_t>(c) * W + w] = static_cast<__int128>(pos) - static_cast<__int128>(neg);
+}
+
+// out[w] = sum_c partial[c][w]
+__global__ void k_dot_reduce(const __int128 *__restrict__ partial, int chunks, int W, __int128 *__restrict__ out) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= W) return;
+    __int128 s = 0;
+    for (int c = 0; c < chunks; ++c) s += partial[static_cast<size_t>(c) * W + w];
+    out[w] = s;
+}
+
+// Up to three terms c_k x_k: scalar k has nl[k] limbs (already shifted left by
+// its bit residue), sign sneg[k], and enters at limb offset off[k].
+struct LinTerms {
+    const uint32_t *x[3];
+    const uint8_t *xn[3];
+    const uint32_t *c[3];  // device copies of the scalar limbs
+    int nl[3], off[3], sneg[3];
+    int count;
+};
+
+// colsum[i][w] = sum_k sign * sum_a C_k[a] X_k,i[w - off_k - a]; grid (rows,
+// column blocks).  The scalar limbs are read by every thread of a block and
+// stay in the read-only cache.
+__global__ void k_lincomb_colsum(LinTerms t, int n, int L32, int W, __int128 *__restrict__ colsum) {
+    const int i = blockIdx.x;
+    const int w = blockIdx.y * blockDim.x + threadIdx.x;
+    if (i >= n || w >= W) return;
+    unsigned __int128 pos = 0, neg = 0;
+    for (int k = 0; k < t.count; ++k) {
+        const uint32_t *xr = t.x[k] + static_cast<size_t>(i) * L32;
+        const uint32_t *cr = t.c[k];
+        const int v = w - t.off[k];  // column within C_k * X_k,i
+        if (v < 0) continue;
+        const int a0 = max(0, v - (L32 - 1)), a1 = min(t.nl[k] - 1, v);
+        unsigned __int128 acc = 0;
+        for (int a = a0; a <= a1; ++a) acc += static_cast<unsigned long long>(__ldg(cr + a)) * xr[v - a];
+        if ((t.xn[k][i] != 0) != (t.sneg[k] != 0)) neg += acc;
+        else pos += acc;
+    }
+    colsum[static_cast<size_t>(i) * W + w] = static_cast<__int128>(pos) - static_cast<__int128>(neg);
+}
+
+bool device_vec(const hmv_vec *v, int n, int b) {
+    return v && v->len == n && v->nrhs == 1 && v->b == b && v->limbs && v->neg && v->on_device == 1 && !v->reserved;
+}
+
+}  // namespace
+}  // namespace hmv
+
+using namespace hmv;
+
+extern "C" hmv_status hmv_dot(hmv_plan_t *p, const hmv_vec *x, const hmv_vec *y, uint32_t *z, int32_t zl,
+                              uint8_t *z_neg) {
+    if (!p || !z || !z_neg) return HMV_EINVAL;
+    const int n = p->n, L32 = p->L32, W = 2 * L32;
+    if (!device_vec(x, n, p->b) || !device_vec(y, n, p->b) || zl < W + 2) return HMV_EINVAL;
+    const int chunks = (n + kDotRows - 1) / kDotRows;
+    cudaStream_t s = p->stream;
+    __int128 *partial = nullptr, *cols = nullptr;
+    uint32_t *mag = nullptr;
+    uint8_t *zn = nullptr;
+    int32_t *zb = nullptr, *st = nullptr;
+    const int ZW = W + 2;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&partial), static_cast<size_t>(chunks) * W * 16, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&cols), static_cast<size_t>(W) * 16, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&mag), static_cast<size_t>(ZW) * 4, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&zn), 16, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&zb), 16, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&st), 8 * sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, 8 * sizeof(int32_t), s);
+    if (e == cudaSuccess) {
+        k_dot_partial<<<dim3((W + 127) / 128, chunks), 128, 0, s>>>(x->limbs, x->neg, y->limbs, y->neg, n, L32,
+                                                                   partial);
+        k_dot_reduce<<<(W + 127) / 128, 128, 0, s>>>(partial, chunks, W, cols);
+        e = launch_colsum_normalize_cols(cols, 1, W, mag, zn, zb, ZW, st, s);
+        p->launches_total += 3;
+    }
+    int32_t status[8] = {0};
+    uint8_t sign = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(z, mag, static_cast<size_t>(ZW) * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&sign, zn, 1, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(status, st, sizeof status, cudaMemcpyDeviceToHost, s);
+    for (void *ptr : {static_cast<void *>(partial), static_cast<void *>(cols), static_cast<void *>(mag),
+                      static_cast<void *>(zn), static_cast<void *>(zb), static_cast<void *>(st)})
+        if (ptr) cudaFreeAsync(ptr, s);
+    const cudaError_t se = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = se;
+    if (e != cudaSuccess) { cudaGetLastError(); return HMV_ECUDA; }
+    if (status[0] != DEV_OK) return HMV_ECUDA;
+    for (int w = ZW; w < zl; ++w) z[w] = 0;
+    *z_neg = sign;
+    return HMV_OK;
+}
+
+extern "C" hmv_status hmv_lincomb(hmv_plan_t *p, int32_t count, const hmv_scalar *c, const hmv_vec *xs, hmv_vec *y) {
+    if (!p || !c || !xs || !y || count < 1 || count > 3) return HMV_EINVAL;
+    const int n = p->n, b = p->b, L32 = p->L32;
+    if (!device_vec(y, n, b)) return HMV_EINVAL;
+    // term k: value C_k * M_k,i * 2^(s_k), s_k = c_k.exponent + x_k.exponent - b
+    long long smin = 0;
+    for (int k = 0; k < count; ++k) {
+        if (!device_vec(&xs[k], n, b) || !c[k].limbs || c[k].nlimbs < 1 || c[k].nlimbs > L32 + 1) return HMV_EINVAL;
+        const long long sk = static_cast<long long>(c[k].exponent) + xs[k].exponent - b;
+        smin = (k == 0) ? sk : std::min(smin, sk);
+    }
+    LinTerms t;
+    memset(&t, 0, sizeof t);
+    t.count = count;
+    std::vector<std::vector<uint32_t>> shifted(count);
+    int W = 0;
+    for (int k = 0; k < count; ++k) {
+        const long long shift = static_cast<long long>(c[k].exponent) + xs[k].exponent - b - smin;
+        if (shift > 4LL * 32 * L32) return HMV_EUNSUPPORTED;  // terms too far apart in scale
+        const int off = static_cast<int>(shift / 32), r = static_cast<int>(shift % 32);
+        std::vector<uint32_t> &v = shifted[k];  // C_k << r
+        v.assign(c[k].nlimbs + 1, 0u);
+        for (int q = 0; q < c[k].nlimbs; ++q) {
+            const uint64_t wv = static_cast<uint64_t>(c[k].limbs[q]) << r;
+            v[q] |= static_cast<uint32_t>(wv);
+            v[q + 1] |= static_cast<uint32_t>(wv >> 32);
+        }
+        while (v.size() > 1 && v.back() == 0) v.pop_back();
+        t.x[k] = xs[k].limbs;
+        t.xn[k] = xs[k].neg;
+        t.nl[k] = static_cast<int>(v.size());
+        t.off[k] = off;
+        t.sneg[k] = c[k].neg ? 1 : 0;
+        W = std::max(W, off + t.nl[k] + L32);
+    }
+    W += 1;
+    const int ZW = W + 3;
+    cudaStream_t s = p->stream;
+    uint32_t *dc = nullptr, *mag = nullptr;
+    __int128 *cols = nullptr;
+    uint8_t *zn = nullptr;
+    int32_t *zb = nullptr, *st = nullptr;
+    int total = 0;
+    for (int k = 0; k < count; ++k) total += t.nl[k];
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&dc), static_cast<size_t>(total) * 4, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&cols), static_cast<size_t>(n) * W * 16, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&mag), static_cast<size_t>(n) * ZW * 4, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&zn), n, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&zb), static_cast<size_t>(n) * 4, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&st), 8 * sizeof(int32_t), s);
+    std::vector<uint32_t> flat;
+    for (int k = 0; k < count; ++k) flat.insert(flat.end(), shifted[k].begin(), shifted[k].end());
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dc, flat.data(), flat.size() * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, 8 * sizeof(int32_t), s);
+    if (e == cudaSuccess) {
+        int o = 0;
+        for (int k = 0; k < count; ++k) {
+            t.c[k] = dc + o;
+            o += t.nl[k];
+        }
+        k_lincomb_colsum<<<dim3(n, (W + 127) / 128), 128, 0, s>>>(t, n, L32, W, cols);
+        // value = S * 2^smin = S * 2^(e_in - 2b)
+        e = launch_colsum_round_cols(cols, n, W, L32, mag, zn, zb, ZW, st, b, static_cast<int>(smin + 2LL * b),
+                                     y->limbs, y->neg, s);
+        p->launches_total += 4;
+    }
+    int32_t status[8] = {0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(status, st, sizeof status, cudaMemcpyDeviceToHost, s);
+    for (void *ptr : {static_cast<void *>(dc), static_cast<void *>(cols), static_cast<void *>(mag),
+                      static_cast<void *>(zn), static_cast<void *>(zb), static_cast<void *>(st)})
+        if (ptr) cudaFreeAsync(ptr, s);
+    const cudaError_t se = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = se;
+    if (e != cudaSuccess) { cudaGetLastError(); return HMV_ECUDA; }
+    if (status[0] != DEV_OK) return HMV_ECUDA;
+    y->exponent = status[3];
+    return HMV_OK;
+}

@@ -861,6 +861,24 @@ cudaError_t launch_round(hmv_plan_s *p, int rows, int e_in, uint32_t *y_limbs, u
 
 // Normalisation and rounding on caller-given buffers (used by the
 // scratch-free entry point); dstat must start zeroed.
+// Signed 128-bit column sums with ncols columns per row: normalise to |Z|
+// limbs (ZW >= ncols + 3), and optionally round each row to b bits with the
+// least shared exponent (value = Z * 2^(e_in - 2b)).
+cudaError_t launch_colsum_normalize_cols(const __int128 *colsum, int n, int ncols, uint32_t *zmag, uint8_t *zneg,
+                                         int32_t *zbits, int ZW, int32_t *dstat, cudaStream_t stream) {
+    k_colsum_normalize<<<blocks_for(n, 128), 128, 0, stream>>>(colsum, n, ncols, zmag, zneg, zbits, ZW, dstat, 0);
+    return cudaGetLastError();
+}
+cudaError_t launch_colsum_round_cols(const __int128 *colsum, int n, int ncols, int L32, uint32_t *zmag, uint8_t *zneg,
+                                     int32_t *zbits, int ZW, int32_t *dstat, int b, int e_in, uint32_t *y,
+                                     uint8_t *yneg, cudaStream_t stream) {
+    k_colsum_normalize<<<blocks_for(n, 128), 128, 0, stream>>>(colsum, n, ncols, zmag, zneg, zbits, ZW, dstat, 0);
+    k_round_check<<<blocks_for(n, 128), 128, 0, stream>>>(zmag, zbits, n, ZW, b, dstat);
+    k_round<<<static_cast<unsigned>((n + 7) / 8), 256, 0, stream>>>(zmag, zneg, n, 1, ZW, b, L32, e_in, 0, dstat, y,
+                                                                    yneg);  // a warp per row
+    return cudaGetLastError();
+}
+
 cudaError_t launch_colsum_round_raw(const __int128 *colsum, int n, int L32, uint32_t *zmag, uint8_t *zneg,
                                     int32_t *zbits, int ZW, int32_t *dstat, int b, int e_in, int reverse,
                                     uint32_t *y, uint8_t *yneg, cudaStream_t stream) {

@@ -145,6 +145,11 @@ cudaError_t launch_leaf_normalize(hmv_plan_s *p, int32_t *out);
 // from each plan's staged x to its bf16 copies, and leaf normalise plus the
 // post-pass down to each plan's level-0 rows
 bool same_geometry(hmv_plan_s *const *ps, int G);
+cudaError_t launch_colsum_normalize_cols(const __int128 *colsum, int n, int ncols, uint32_t *zmag, uint8_t *zneg,
+                                         int32_t *zbits, int ZW, int32_t *dstat, cudaStream_t stream);
+cudaError_t launch_colsum_round_cols(const __int128 *colsum, int n, int ncols, int L32, uint32_t *zmag, uint8_t *zneg,
+                                     int32_t *zbits, int ZW, int32_t *dstat, int b, int e_in, uint32_t *y,
+                                     uint8_t *yneg, cudaStream_t stream);
 cudaError_t launch_vector_side_group(hmv_plan_s *const *ps, int G);
 cudaError_t launch_post_group(hmv_plan_s *const *ps, int G);
 cudaError_t launch_postpass(hmv_plan_s *p, int level, const int32_t *in, int32_t *out);

@@ -58,6 +58,11 @@ class Stats(ctypes.Structure):
                 ("leaf_tile_digits", ctypes.c_int32), ("digit_products", ctypes.c_int32)]
 
 
+class Scalar(ctypes.Structure):
+    _fields_ = [("limbs", ctypes.POINTER(ctypes.c_uint32)), ("nlimbs", ctypes.c_int32), ("neg", ctypes.c_int32),
+                ("exponent", ctypes.c_int32)]
+
+
 class BatchInfo(ctypes.Structure):
     _fields_ = [("matrices", ctypes.c_int32), ("pairs", ctypes.c_int32), ("waves", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("leaf_tiles", ctypes.c_int64), ("leaf_macs", ctypes.c_double),
@@ -110,6 +115,11 @@ def load_library(path: str = LIB_PATH):
         lib.hmv_plan_bytes.restype = ctypes.c_int
         lib.hmv_matvec_many.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(Vec), ctypes.POINTER(Vec)]
         lib.hmv_matvec_many.restype = ctypes.c_int
+        lib.hmv_dot.argtypes = [vp, ctypes.POINTER(Vec), ctypes.POINTER(Vec), ctypes.POINTER(ctypes.c_uint32), i32,
+                                ctypes.POINTER(ctypes.c_uint8)]
+        lib.hmv_dot.restype = ctypes.c_int
+        lib.hmv_lincomb.argtypes = [vp, i32, ctypes.POINTER(Scalar), ctypes.POINTER(Vec), ctypes.POINTER(Vec)]
+        lib.hmv_lincomb.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -164,6 +174,44 @@ def matvec_many_device(plans, xs_ptrs, ys_ptrs, x_exponents) -> list[int]:
         ya[i] = Vec(p.n, 1, p.b, 0, ys_ptrs[i][0], ys_ptrs[i][1], 1, 0)
     _check(lib.hmv_matvec_many(n, pa, xa, ya), "hmv_matvec_many")
     return [int(ya[i].exponent) for i in range(n)]
+
+
+def _device_vec(plan, ptrs, exponent=0):
+    """Vec for a device vector (limbs pointer, sign pointer) of the plan's n and b."""
+    return Vec(plan.n, 1, plan.b, exponent, ptrs[0], ptrs[1], 1, 0)
+
+
+def dot_device(plan, x_ptrs, y_ptrs) -> int:
+    """hmv_dot: the exact integer sum_i X_i Y_i of two device vectors' signed
+    mantissas (its value is that integer times 2^(E_x + E_y - 2b))."""
+    lib = load_library()
+    zl = 2 * plan.L32 + 2
+    z = (ctypes.c_uint32 * zl)()
+    zn = ctypes.c_uint8()
+    xv, yv = _device_vec(plan, x_ptrs), _device_vec(plan, y_ptrs)
+    _check(lib.hmv_dot(plan.handle, ctypes.byref(xv), ctypes.byref(yv), z, zl, ctypes.byref(zn)), "hmv_dot")
+    m = int.from_bytes(bytes(z), "little")
+    return -m if zn.value else m
+
+
+def lincomb_device(plan, terms, y_ptrs) -> int:
+    """hmv_lincomb: y = RNE_b(sum c * x) over terms [(c_int, c_exponent,
+    (limbs_ptr, neg_ptr), x_exponent)]; returns y's exponent."""
+    lib = load_library()
+    k = len(terms)
+    cs = (Scalar * k)()
+    xs = (Vec * k)()
+    keep = []
+    for i, (c, ce, xp, xe) in enumerate(terms):
+        mag = abs(int(c))
+        nl = max(1, (mag.bit_length() + 31) // 32)
+        arr = (ctypes.c_uint32 * nl).from_buffer_copy(mag.to_bytes(4 * nl, "little"))
+        keep.append(arr)
+        cs[i] = Scalar(ctypes.cast(arr, ctypes.POINTER(ctypes.c_uint32)), nl, 1 if c < 0 else 0, ce)
+        xs[i] = _device_vec(plan, xp, xe)
+    yv = _device_vec(plan, y_ptrs)
+    _check(lib.hmv_lincomb(plan.handle, k, cs, xs, ctypes.byref(yv)), "hmv_lincomb")
+    return int(yv.exponent)
 
 
 class Plan:

@@ -1,0 +1,132 @@
+"""Lanczos driver on a device-resident Hankel matrix.
+
+The paper's introduction motivates fast multiprecision Hankel products by
+Lanczos-type iterations on these matrices; this module runs that iteration on
+top of a loaded plan.  It uses the unnormalised three-term recurrence for the
+symmetric A = A_H (no square roots):
+
+    w            = A v_k
+    alpha_k      = <v_k, w> / <v_k, v_k>
+    w            = w - alpha_k v_k - beta_k v_{k-1}
+    beta_{k+1}   = <w, w> / <v_k, v_k>
+    v_{k+1}      = w
+
+with v_{-1} = 0 and beta_0 = 0.  The symmetric tridiagonal matrix with
+diagonal alpha and off-diagonal sqrt(beta_{k+1}) is the Lanczos matrix; its
+eigenvalues (the Ritz values) are the caller's business.
+
+Arithmetic: every vector is b-bit block fixed point; A v and the update of w
+are exact and then rounded once (hmv_matvec, hmv_lincomb: least shared
+exponent, ties to even); the inner products are exact (hmv_dot); alpha and
+beta are the exact ratios rounded to b-bit floating point, ties to even, on
+the host.  Every step is deterministic, so a run is reproducible bit for bit.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import hmv
+from .inputs import FixedVec
+
+
+def round_ratio(num: int, den: int, shift: int, b: int) -> tuple[int, int]:
+    """(m, e) with m * 2^e = RNE_b(num / den * 2^shift), 2^(b-1) <= |m| < 2^b
+    (m = 0, e = 0 for a zero numerator)."""
+    if den == 0:
+        raise ZeroDivisionError("zero denominator")
+    if num == 0:
+        return 0, 0
+    neg = (num < 0) != (den < 0)
+    n, d = abs(num), abs(den)
+    t = b - 1 - (n.bit_length() - d.bit_length())  # n 2^t / d in [2^(b-2), 2^b)
+    while True:
+        q, r = divmod(n << t, d) if t >= 0 else divmod(n, d << -t)
+        dd = d if t >= 0 else d << -t
+        if q >= 1 << (b - 1):
+            break
+        t += 1
+    if 2 * r > dd or (2 * r == dd and q & 1):
+        q += 1
+        if q == 1 << b:
+            q >>= 1
+            t -= 1
+    return (-q if neg else q), shift - t
+
+
+class Lanczos:
+    """Runs the recurrence for the plan's matrix from a start vector; keeps
+    v_{k-1}, v_k and w on the device (torch tensors on the plan's device)."""
+
+    def __init__(self, plan: hmv.Plan, x0: FixedVec, device=None):
+        import torch
+        self.torch = torch
+        self.plan = plan
+        self.b = plan.b
+        dev = device or torch.device("cuda", torch.cuda.current_device())
+        self.dev = dev
+
+        def buf(v=None):
+            if v is None:
+                limbs = torch.zeros((plan.n, plan.L32), dtype=torch.int32, device=dev)
+                neg = torch.zeros(plan.n, dtype=torch.uint8, device=dev)
+            else:
+                limbs = torch.from_numpy(v.limbs.view(np.int32)).to(dev)
+                neg = torch.from_numpy(v.neg).to(dev)
+            return [limbs, neg]
+
+        self.v, self.ev = buf(x0), x0.exponent
+        self.u, self.eu = buf(), 0
+        self.w = buf()
+        self.beta = (0, 0)
+        self.dvv = None
+        self.k = 0
+
+    @staticmethod
+    def _ptrs(t):
+        return t[0].data_ptr(), t[1].data_ptr()
+
+    def step(self) -> tuple[tuple[int, int], tuple[int, int]]:
+        """One iteration: returns alpha_k and beta_{k+1} as (mantissa, exponent)."""
+        p, b = self.plan, self.b
+        P = self._ptrs
+        self.torch.cuda.synchronize()
+        if self.dvv is None:
+            self.dvv = hmv.dot_device(p, P(self.v), P(self.v))
+        if self.dvv == 0:
+            raise ArithmeticError("Lanczos breakdown: v_k = 0")
+        ew = p.matvec_device(*P(self.v), self.ev, *P(self.w))
+        self.torch.cuda.synchronize()
+        dvw = hmv.dot_device(p, P(self.v), P(self.w))
+        alpha = round_ratio(dvw, self.dvv, ew - self.ev, b)
+        terms = [(1, 0, P(self.w), ew), (-alpha[0], alpha[1], P(self.v), self.ev)]
+        if self.k > 0 and self.beta[0] != 0:
+            terms.append((-self.beta[0], self.beta[1], P(self.u), self.eu))
+        ew2 = hmv.lincomb_device(p, terms, P(self.w))  # w is read before it is written
+        dww = hmv.dot_device(p, P(self.w), P(self.w))
+        beta = round_ratio(dww, self.dvv, 2 * ew2 - 2 * self.ev, b) if dww else (0, 0)
+        # rotate: u <- v, v <- w, w <- the old u's storage
+        self.u, self.v, self.w = self.v, self.w, self.u
+        self.eu, self.ev = self.ev, ew2
+        self.beta = beta
+        self.dvv = dww
+        self.k += 1
+        return alpha, beta
+
+    def run(self, steps: int):
+        """Up to `steps` iterations (fewer if the recurrence breaks down):
+        lists of alpha_k and beta_{k+1}."""
+        alphas, betas = [], []
+        for _ in range(steps):
+            if self.dvv == 0:
+                break
+            a, bt = self.step()
+            alphas.append(a)
+            betas.append(bt)
+            if bt[0] == 0:
+                break
+        return alphas, betas
+
+    def vector(self) -> FixedVec:
+        """The current v_k as a host FixedVec."""
+        self.torch.cuda.synchronize()
+        return FixedVec(self.v[0].cpu().numpy().view(np.uint32), self.v[1].cpu().numpy(), self.b, self.ev)
