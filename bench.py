@@ -478,6 +478,46 @@ def run_batched(args):
     return 0
 
 
+def run_lanczos(args):
+    """Lanczos steps on the n=8000, b=33220 matrix (one step: A v, two exact
+    inner products, one exact three-term update rounded to b bits, alpha and
+    beta on the host), on the cost model's plan."""
+    import time
+
+    import torch
+
+    import paper_1402_5287_gb300 as pkg
+    from paper_1402_5287_gb300 import hmv
+    from paper_1402_5287_gb300.lanczos import Lanczos
+    pkg.build()
+    n, b, h, x = load_workload(args)
+    plan = hmv.Plan(n, b, flags=hmv.FLAG_TIMING)
+    plan.load_matrix(h)
+    lz = Lanczos(plan, x)
+    for _ in range(args.warmup):
+        lz.step()
+    plan.reset_stats()
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            lz.step()
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+    st = plan.stats()
+    mv_ms = st["ms_total"] / max(st["matvecs"], 1)
+    out = {"metric": "Lanczos steps/s at n=8000, 10^4 digits", "value": args.steps / secs, "unit": "steps/s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+           "config": {"workload": WORKLOAD_DESC + "; Lanczos from x, unnormalised three-term recurrence",
+                      "n": n, "b": b, "digit_products": st["digit_products"],
+                      "per_step": "1 matvec + 2 exact inner products + 1 exact 3-term update, wall clock"},
+           "matvec_ms": mv_ms, "vector_ops_ms": secs / args.steps * 1e3 - mv_ms, "clocks": clocks.summary()}
+    print(json.dumps(out))
+    plan.close()
+    return 0
+
+
 def run_serving(args):
     import random
 
@@ -494,7 +534,8 @@ def run_serving(args):
         n = rng.randint(64, 4096)
         b = rng.choice([2048, 8192, 33220])
         reqs.append(Request(i, n, b, uniform_vec(BASE_SEED + 4, 2 * i, 2 * n - 1, b, 0),
-                            uniform_vec(BASE_SEED + 4, 2 * i + 1, n, b, 0), args.matvecs_per_request, arrival=t))
+                            uniform_vec(BASE_SEED + 4, 2 * i + 1, n, b, 0), args.matvecs_per_request, arrival=t,
+                            lanczos=not args.serve_chains))
     srv = Server(memory_budget=args.serve_gb << 30)
     with ClockSampler(torch.cuda.current_device()) as clocks:
         st = srv.run(reqs)
@@ -502,8 +543,11 @@ def run_serving(args):
             "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "vs_baseline": None, "dtype": "bf16",
             "data": "synthetic", "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
             "config": {"workload": f"{args.requests} requests, Poisson arrivals at {args.rate}/s, n ~ U[64,4096], "
-                                   f"b in {{2048,8192,33220}}, {args.matvecs_per_request} chained matvecs per "
-                                   f"request against a resident A (cap on the 2n of a full Lanczos run)",
+                                   f"b in {{2048,8192,33220}}, "
+                                   + (f"{args.matvecs_per_request} chained matvecs" if args.serve_chains else
+                                      f"{args.matvecs_per_request} Lanczos steps (one matvec, two exact inner "
+                                      f"products and one exact update each)")
+                                   + " per request against a resident A (cap on the 2n of a full Lanczos run)",
                        "memory_budget_gb": args.serve_gb},
             "serving": st, "clocks": clocks.summary()}
     print(json.dumps(line), flush=True)
@@ -528,14 +572,17 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="matrix order (profiling runs; default 8000)")
     ap.add_argument("--b", type=int, default=None, help="mantissa bits (profiling runs; default 33220)")
-    ap.add_argument("--workload", choices=["matvec", "batched", "serving"], default="matvec",
+    ap.add_argument("--workload", choices=["matvec", "batched", "serving", "lanczos"], default="matvec",
                     help="matvec: the n=8000 metric; batched: 64 matrices x 8 RHS per graph launch; "
-                         "serving: Poisson requests with continuous batching")
+                         "serving: Poisson requests with continuous batching; lanczos: Lanczos steps on the "
+                         "n=8000 matrix")
     ap.add_argument("--wave-gb", type=int, default=48, help="batched: device memory per wave")
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=4.0, help="serving: Poisson arrival rate (requests/s)")
     ap.add_argument("--matvecs-per-request", type=int, default=16)
     ap.add_argument("--serve-gb", type=int, default=200, help="serving: device memory budget")
+    ap.add_argument("--serve-chains", action="store_true",
+                    help="serving: plain chains v <- A v instead of Lanczos steps")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
@@ -545,6 +592,8 @@ def main(argv=None):
         return run_batched(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "lanczos":
+        return run_lanczos(args)
     return run_ours(args)
 
 

@@ -85,17 +85,22 @@ class Lanczos:
     def _ptrs(t):
         return t[0].data_ptr(), t[1].data_ptr()
 
-    def step(self) -> tuple[tuple[int, int], tuple[int, int]]:
-        """One iteration: returns alpha_k and beta_{k+1} as (mantissa, exponent)."""
-        p, b = self.plan, self.b
-        P = self._ptrs
+    def operands(self):
+        """The next product w = A v_k as ((v limbs, v sign), E_v, (w limbs, w sign))
+        device pointers, for a caller that runs it (hmv_matvec_many) itself."""
+        p = self.plan
         self.torch.cuda.synchronize()
         if self.dvv is None:
-            self.dvv = hmv.dot_device(p, P(self.v), P(self.v))
+            self.dvv = hmv.dot_device(p, self._ptrs(self.v), self._ptrs(self.v))
         if self.dvv == 0:
             raise ArithmeticError("Lanczos breakdown: v_k = 0")
-        ew = p.matvec_device(*P(self.v), self.ev, *P(self.w))
-        self.torch.cuda.synchronize()
+        return self._ptrs(self.v), self.ev, self._ptrs(self.w)
+
+    def finish(self, ew: int) -> tuple[tuple[int, int], tuple[int, int]]:
+        """The rest of the step once w = A v_k (exponent ew) is in place:
+        returns alpha_k and beta_{k+1} as (mantissa, exponent)."""
+        p, b = self.plan, self.b
+        P = self._ptrs
         dvw = hmv.dot_device(p, P(self.v), P(self.w))
         alpha = round_ratio(dvw, self.dvv, ew - self.ev, b)
         terms = [(1, 0, P(self.w), ew), (-alpha[0], alpha[1], P(self.v), self.ev)]
@@ -111,6 +116,11 @@ class Lanczos:
         self.dvv = dww
         self.k += 1
         return alpha, beta
+
+    def step(self) -> tuple[tuple[int, int], tuple[int, int]]:
+        """One iteration: returns alpha_k and beta_{k+1} as (mantissa, exponent)."""
+        vp, ev, wp = self.operands()
+        return self.finish(self.plan.matvec_device(*vp, ev, *wp))
 
     def run(self, steps: int):
         """Up to `steps` iterations (fewer if the recurrence breaks down):

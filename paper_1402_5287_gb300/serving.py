@@ -1,10 +1,11 @@
-"""Continuous-batching server for Lanczos-style clients of the exact Hankel
-product.
+"""Continuous-batching server for Lanczos clients of the exact Hankel product.
 
-Each request brings a matrix (its h) and a start vector and asks for a chain
-of products v_{k+1} = A v_k against its device-resident A, the access
-pattern of a Krylov/Lanczos driver (the eigenvalue and orthogonalisation
-stages are the client's, not this engine's).  The server
+Each request brings a matrix (its h) and a start vector and asks for a
+number of steps against its device-resident A: either Lanczos steps (the
+driver of paper_1402_5287_gb300/lanczos.py: the product, two exact inner
+products and the exact three-term update; the request keeps the alpha and
+beta sequence) or a plain chain v_{k+1} = A v_k.  The eigenvalue stage of a
+Lanczos run is the client's.  The server
 
   * admits arrived requests in order while the device memory its plans need
     (hmv_plan_bytes, computed without allocating) fits the budget,
@@ -40,11 +41,14 @@ class Request:
     matvecs: int
     arrival: float = 0.0
     kind: int = hmv.HANKEL
+    lanczos: bool = False            # Lanczos steps instead of a plain chain
     # filled by the server
     admitted: float | None = None
     finished: float | None = None
     latencies: list = field(default_factory=list)
-    result: FixedVec | None = None
+    result: FixedVec | None = None   # the last vector (chain: A^k x; Lanczos: v_k)
+    alphas: list = field(default_factory=list)
+    betas: list = field(default_factory=list)
     footprint: int = 0
 
 
@@ -68,21 +72,29 @@ class Server:
         torch = self.torch
         r.plan = hmv.Plan(r.n, r.b, kind=r.kind, stream=self.stream.cuda_stream)
         r.plan.load_matrix(r.h)
+        r.done = 0
+        r.admitted = now
+        if r.lanczos:
+            from .lanczos import Lanczos
+            r.lz = Lanczos(r.plan, r.x0, device=self.dev)
+            return
         with torch.cuda.stream(self.stream):
             r.xl = torch.from_numpy(r.x0.limbs.view(np.int32)).to(self.dev)
             r.xn = torch.from_numpy(r.x0.neg).to(self.dev)
             r.yl = torch.empty_like(r.xl)
             r.yn = torch.empty_like(r.xn)
         r.x_exp = r.x0.exponent
-        r.done = 0
-        r.admitted = now
 
     def _finish(self, r: Request, now: float):
         self.stream.synchronize()
-        r.result = FixedVec(r.xl.cpu().numpy().view(np.uint32), r.xn.cpu().numpy(), r.b, r.x_exp)
+        if r.lanczos:
+            r.result = r.lz.vector()
+            del r.lz
+        else:
+            r.result = FixedVec(r.xl.cpu().numpy().view(np.uint32), r.xn.cpu().numpy(), r.b, r.x_exp)
+            del r.xl, r.xn, r.yl, r.yn
         r.plan.close()
         r.plan = None
-        del r.xl, r.xn, r.yl, r.yn
         r.finished = now
 
     def run(self, requests: list[Request]) -> dict:
@@ -112,10 +124,21 @@ class Server:
                 if pending:
                     time.sleep(max(0.0, min(pending[0].arrival - (self.clock() - t0), 0.05)))
                 continue
-            exps = hmv.matvec_many_device([r.plan for r in active],
-                                          [(r.xl.data_ptr(), r.xn.data_ptr()) for r in active],
-                                          [(r.yl.data_ptr(), r.yn.data_ptr()) for r in active],
-                                          [r.x_exp for r in active])
+            xs, es, ys = [], [], []
+            for r in active:
+                if r.lanczos:
+                    vp, ev, wp = r.lz.operands()
+                else:
+                    vp, ev, wp = (r.xl.data_ptr(), r.xn.data_ptr()), r.x_exp, (r.yl.data_ptr(), r.yn.data_ptr())
+                xs.append(vp)
+                es.append(ev)
+                ys.append(wp)
+            exps = hmv.matvec_many_device([r.plan for r in active], xs, ys, es)
+            for r, e in zip(active, exps):  # the rest of each Lanczos step
+                if r.lanczos:
+                    a, bt = r.lz.finish(e)
+                    r.alphas.append(a)
+                    r.betas.append(bt)
             t_end = self.clock() - t0
             steps += 1
             step_sizes.append(len(active))
@@ -123,11 +146,12 @@ class Server:
             for r, e in zip(active, exps):
                 r.latencies.append(t_end - r.ready)
                 r.ready = t_end
-                r.xl, r.yl = r.yl, r.xl
-                r.xn, r.yn = r.yn, r.xn
-                r.x_exp = e
+                if not r.lanczos:
+                    r.xl, r.yl = r.yl, r.xl
+                    r.xn, r.yn = r.yn, r.xn
+                    r.x_exp = e
                 r.done += 1
-                if r.done == r.matvecs:
+                if r.done == r.matvecs or (r.lanczos and r.betas[-1][0] == 0):
                     self._finish(r, t_end)
                     used -= r.footprint
                 else:
@@ -136,7 +160,7 @@ class Server:
         total = self.clock() - t0
         lat = [v for r in requests for v in r.latencies]
         req_lat = [r.finished - r.arrival for r in requests]
-        nmv = sum(r.matvecs for r in requests)
+        nmv = sum(r.done for r in requests)  # a Lanczos run that breaks down stops early
         return {"matvecs": nmv, "seconds": total, "matvecs_per_s": nmv / total if total > 0 else None,
                 "p50_ms": percentile(lat, 50) * 1e3, "p99_ms": percentile(lat, 99) * 1e3,
                 "request_p50_s": percentile(req_lat, 50), "request_p99_s": percentile(req_lat, 99),

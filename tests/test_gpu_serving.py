@@ -81,3 +81,30 @@ def test_served_results_same_alone_and_in_the_mix(tight):
     for r, (n, b, kind, h, x) in zip(reqs, probs):
         assert len(r.latencies) == k
         assert_same(r.result, chain_alone(n, b, kind, h, x, k))
+
+
+def test_served_lanczos_drivers_equal_solo_runs():
+    """Lanczos requests in the continuous-batching loop: each request's alpha,
+    beta and final vector equal the same driver run alone, and the oracle's."""
+    torch = pytest.importorskip("torch")
+    from oracle import lanczos as ol
+    from paper_1402_5287_gb300.lanczos import Lanczos
+    from paper_1402_5287_gb300.serving import Request, Server
+    probs = make(500)
+    k = 3
+    reqs = [Request(i, n, b, h, x, k, arrival=0.0, kind=kind, lanczos=True)
+            for i, (n, b, kind, h, x) in enumerate(probs) if kind == hmv.HANKEL]
+    sizes = [hmv.plan_bytes(r.n, r.b) for r in reqs]
+    stats = Server(memory_budget=max(max(sizes), sum(sizes) // 2)).run(reqs)
+    assert stats["matvecs"] == sum(len(r.alphas) for r in reqs)
+    for r in reqs:
+        with hmv.Plan(r.n, r.b) as p:
+            p.load_matrix(r.h)
+            solo = Lanczos(p, r.x0)
+            a, bt = solo.run(k)
+            v = solo.vector()
+        assert r.alphas == a and r.betas == bt
+        assert r.result.exponent == v.exponent and np.array_equal(r.result.limbs, v.limbs)
+        if r.n <= 64:  # the oracle's recurrence on the smaller ones
+            oa, ob, _ = ol.lanczos(r.h, r.x0, k)
+            assert r.alphas == oa and r.betas == ob
