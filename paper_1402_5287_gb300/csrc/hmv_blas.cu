@@ -17,38 +17,87 @@
 namespace hmv {
 namespace {
 
-constexpr int kDotRows = 64;  // rows summed by one thread of the inner product
+constexpr int kDotRows = 8;  // rows summed by one thread of the inner product
+
+// One limb product added into a 96-bit column sum (a0, a1, a2) with the carry
+// chain of the integer multiply-add.
+__device__ __forceinline__ void mac96(uint32_t &a0, uint32_t &a1, uint32_t &a2, uint32_t u, uint32_t v) {
+    asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
+        "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
+        "addc.u32 %2, %2, 0;"
+        : "+r"(a0), "+r"(a1), "+r"(a2)
+        : "r"(u), "r"(v));
+}
+
+// Four consecutive columns v0..v0+3 of the product of a limb string C (nl
+// limbs) and a row X (L32 limbs), out[q] = sum_a C[a] X[v0 + q - a], with a
+// sliding window of X limbs: one new X limb and one C limb per four products.
+__device__ __forceinline__ void cols4(const uint32_t *__restrict__ cr, int nl, const uint32_t *__restrict__ xr,
+                                      int L32, int v0, unsigned __int128 (&out)[4]) {
+    const int a_lo = max(0, v0 - (L32 - 1)), a_hi = min(nl - 1, v0 + 3);
+    uint32_t s0[4] = {0, 0, 0, 0}, s1[4] = {0, 0, 0, 0}, s2[4] = {0, 0, 0, 0};
+    uint32_t win[4];  // win[q] = X[v0 + q - a] (0 outside the row)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int j = v0 + q - a_lo;
+        win[q] = (j >= 0 && j < L32) ? xr[j] : 0u;
+    }
+    for (int a = a_lo; a <= a_hi; ++a) {
+        const uint32_t ca = __ldg(cr + a);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) mac96(s0[q], s1[q], s2[q], ca, win[q]);
+        win[3] = win[2];
+        win[2] = win[1];
+        win[1] = win[0];
+        const int j = v0 - a - 1;
+        win[0] = (j >= 0 && j < L32) ? xr[j] : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        out[q] = (static_cast<unsigned __int128>(s2[q]) << 64) |
+                 (static_cast<unsigned __int128>(s1[q]) << 32) | s0[q];
+}
 
 // partial[c][w] = sum over rows i of chunk c of s_i * sum_a X_i[a] Y_i[w - a]
-// (s_i = +-1 from the two signs), for limb columns w in [0, 2 L32).
+// (s_i = +-1 from the two signs), for limb columns w in [0, 2 L32); four
+// consecutive columns per thread.
 __global__ void k_dot_partial(const uint32_t *__restrict__ x, const uint8_t *__restrict__ xn,
                               const uint32_t *__restrict__ y, const uint8_t *__restrict__ yn, int n, int L32,
                               __int128 *__restrict__ partial) {
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    const int c = blockIdx.y;
     const int W = 2 * L32;
-    if (w >= W) return;
+    const int w0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int c = blockIdx.y;
+    if (w0 >= W) return;
     const int i0 = c * kDotRows, i1 = min(n, i0 + kDotRows);
-    const int a0 = max(0, w - (L32 - 1)), a1 = min(L32 - 1, w);
-    unsigned __int128 pos = 0, neg = 0;
+    __int128 tot[4] = {0, 0, 0, 0};
     for (int i = i0; i < i1; ++i) {
-        const uint32_t *xr = x + static_cast<size_t>(i) * L32;
-        const uint32_t *yr = y + static_cast<size_t>(i) * L32;
-        unsigned __int128 acc = 0;
-        for (int a = a0; a <= a1; ++a) acc += static_cast<unsigned long long>(xr[a]) * yr[w - a];
-        if (xn[i] != yn[i]) neg += acc;
-        else pos += acc;
+        unsigned __int128 v[4];
+        cols4(x + static_cast<size_t>(i) * L32, L32, y + static_cast<size_t>(i) * L32, L32, w0, v);
+        const bool neg = xn[i] != yn[i];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tot[q] += neg ? -static_cast<__int128>(v[q]) : static_cast<__int128>(v[q]);
     }
-    partial[static_cast<size_t>(c) * W + w] = static_cast<__int128>(pos) - static_cast<__int128>(neg);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (w0 + q < W) partial[static_cast<size_t>(c) * W + w0 + q] = tot[q];
 }
 
-// out[w] = sum_c partial[c][w]
-__global__ void k_dot_reduce(const __int128 *__restrict__ partial, int chunks, int W, __int128 *__restrict__ out) {
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= W) return;
+// out[w] = sum_c partial[c][w]; a block of 32 x 8 threads covers 32 columns,
+// the 8 lanes of a column take every 8th chunk and meet in shared memory.
+__global__ void __launch_bounds__(256) k_dot_reduce(const __int128 *__restrict__ partial, int chunks, int W,
+                                                    __int128 *__restrict__ out) {
+    __shared__ __int128 red[8][32];
+    const int w = blockIdx.x * 32 + threadIdx.x;
     __int128 s = 0;
-    for (int c = 0; c < chunks; ++c) s += partial[static_cast<size_t>(c) * W + w];
-    out[w] = s;
+    if (w < W)
+        for (int c = threadIdx.y; c < chunks; c += 8) s += partial[static_cast<size_t>(c) * W + w];
+    red[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && w < W) {
+#pragma unroll
+        for (int l = 1; l < 8; ++l) s += red[l][threadIdx.x];
+        out[w] = s;
+    }
 }
 
 // Up to three terms c_k x_k: scalar k has nl[k] limbs (already shifted left by
@@ -62,25 +111,28 @@ struct LinTerms {
 };
 
 // colsum[i][w] = sum_k sign * sum_a C_k[a] X_k,i[w - off_k - a]; grid (rows,
-// column blocks).  The scalar limbs are read by every thread of a block and
-// stay in the read-only cache.
+// column blocks), four consecutive columns per thread with a sliding window
+// of X limbs (as the inner product); the scalar limbs are read by every
+// thread of a block and stay in the read-only cache.
 __global__ void k_lincomb_colsum(LinTerms t, int n, int L32, int W, __int128 *__restrict__ colsum) {
     const int i = blockIdx.x;
-    const int w = blockIdx.y * blockDim.x + threadIdx.x;
-    if (i >= n || w >= W) return;
-    unsigned __int128 pos = 0, neg = 0;
-    for (int k = 0; k < t.count; ++k) {
-        const uint32_t *xr = t.x[k] + static_cast<size_t>(i) * L32;
-        const uint32_t *cr = t.c[k];
-        const int v = w - t.off[k];  // column within C_k * X_k,i
-        if (v < 0) continue;
-        const int a0 = max(0, v - (L32 - 1)), a1 = min(t.nl[k] - 1, v);
-        unsigned __int128 acc = 0;
-        for (int a = a0; a <= a1; ++a) acc += static_cast<unsigned long long>(__ldg(cr + a)) * xr[v - a];
-        if ((t.xn[k][i] != 0) != (t.sneg[k] != 0)) neg += acc;
-        else pos += acc;
+    const int w0 = 4 * (blockIdx.y * blockDim.x + threadIdx.x);
+    if (i >= n || w0 >= W) return;
+    __int128 tot[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (k >= t.count) break;
+        const int v0 = w0 - t.off[k];  // first column within C_k * X_k,i
+        if (v0 + 3 < 0) continue;
+        unsigned __int128 v[4];
+        cols4(t.c[k], t.nl[k], t.x[k] + static_cast<size_t>(i) * L32, L32, v0, v);
+        const bool neg = (t.xn[k][i] != 0) != (t.sneg[k] != 0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tot[q] += neg ? -static_cast<__int128>(v[q]) : static_cast<__int128>(v[q]);
     }
-    colsum[static_cast<size_t>(i) * W + w] = static_cast<__int128>(pos) - static_cast<__int128>(neg);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (w0 + q < W) colsum[static_cast<size_t>(i) * W + w0 + q] = tot[q];
 }
 
 bool device_vec(const hmv_vec *v, int n, int b) {
@@ -112,9 +164,9 @@ extern "C" hmv_status hmv_dot(hmv_plan_t *p, const hmv_vec *x, const hmv_vec *y,
     if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&st), 8 * sizeof(int32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, 8 * sizeof(int32_t), s);
     if (e == cudaSuccess) {
-        k_dot_partial<<<dim3((W + 127) / 128, chunks), 128, 0, s>>>(x->limbs, x->neg, y->limbs, y->neg, n, L32,
-                                                                   partial);
-        k_dot_reduce<<<(W + 127) / 128, 128, 0, s>>>(partial, chunks, W, cols);
+        k_dot_partial<<<dim3((W / 4 + 127) / 128 + 1, chunks), 128, 0, s>>>(x->limbs, x->neg, y->limbs, y->neg, n,
+                                                                           L32, partial);  // 4 columns per thread
+        k_dot_reduce<<<(W + 31) / 32, dim3(32, 8), 0, s>>>(partial, chunks, W, cols);
         e = launch_colsum_normalize_cols(cols, 1, W, mag, zn, zb, ZW, st, s);
         p->launches_total += 3;
     }
@@ -195,7 +247,7 @@ extern "C" hmv_status hmv_lincomb(hmv_plan_t *p, int32_t count, const hmv_scalar
             t.c[k] = dc + o;
             o += t.nl[k];
         }
-        k_lincomb_colsum<<<dim3(n, (W + 127) / 128), 128, 0, s>>>(t, n, L32, W, cols);
+        k_lincomb_colsum<<<dim3(n, (W / 4 + 127) / 128 + 1), 128, 0, s>>>(t, n, L32, W, cols);  // 4 columns/thread
         // value = S * 2^smin = S * 2^(e_in - 2b)
         e = launch_colsum_round_cols(cols, n, W, L32, mag, zn, zb, ZW, st, b, static_cast<int>(smin + 2LL * b),
                                      y->limbs, y->neg, s);

@@ -518,22 +518,39 @@ __global__ void __launch_bounds__(256) k_final_normalize(const T *__restrict__ i
 __global__ void k_colsum_normalize(const __int128 *__restrict__ cs, int n, int ncols, uint32_t *__restrict__ zmag,
                                    uint8_t *__restrict__ zneg, int32_t *__restrict__ zbits, int ZW, int32_t *dstat,
                                    int row_offset) {
+    // one thread per row; the columns are read eight at a time, ahead of the
+    // carry chain that consumes them, so the chain does not wait on each load
+    constexpr int G = 8;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const __int128 *d = cs + static_cast<size_t>(i) * ncols;
     __int128 c = 0;
-    for (int w = 0; w < ncols; ++w) c = (d[w] + c) >> 32;
+    for (int w0 = 0; w0 < ncols; w0 += G) {
+        __int128 v[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) v[q] = (w0 + q < ncols) ? d[w0 + q] : static_cast<__int128>(0);
+#pragma unroll
+        for (int q = 0; q < G; ++q) c = (v[q] + c) >> 32;
+    }
     const int sgn = (c < 0) ? -1 : 1;
     c = 0;
     uint32_t *z = zmag + static_cast<size_t>(row_offset + i) * ZW;
     int top = -1;
     uint32_t topv = 0;
-    for (int w = 0; w < ZW; ++w) {
-        __int128 t = (w < ncols ? (sgn < 0 ? -d[w] : d[w]) : static_cast<__int128>(0)) + c;
-        uint32_t limb = static_cast<uint32_t>(static_cast<unsigned __int128>(t) & 0xFFFFFFFFu);
-        c = t >> 32;
-        z[w] = limb;
-        if (limb) { top = w; topv = limb; }
+    for (int w0 = 0; w0 < ZW; w0 += G) {
+        __int128 v[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) v[q] = (w0 + q < ncols) ? d[w0 + q] : static_cast<__int128>(0);
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            const int w = w0 + q;
+            if (w >= ZW) break;
+            const __int128 t = (sgn < 0 ? -v[q] : v[q]) + c;
+            const uint32_t limb = static_cast<uint32_t>(static_cast<unsigned __int128>(t) & 0xFFFFFFFFu);
+            c = t >> 32;
+            z[w] = limb;
+            if (limb) { top = w; topv = limb; }
+        }
     }
     if (c != 0) atomicExch(dstat, DEV_OVERFLOW);
     int bits = (top < 0) ? 0 : 32 * top + (32 - __clz(topv));

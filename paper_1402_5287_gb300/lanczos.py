@@ -29,15 +29,8 @@ from . import hmv
 from .inputs import FixedVec
 
 
-def round_ratio(num: int, den: int, shift: int, b: int) -> tuple[int, int]:
-    """(m, e) with m * 2^e = RNE_b(num / den * 2^shift), 2^(b-1) <= |m| < 2^b
-    (m = 0, e = 0 for a zero numerator)."""
-    if den == 0:
-        raise ZeroDivisionError("zero denominator")
-    if num == 0:
-        return 0, 0
-    neg = (num < 0) != (den < 0)
-    n, d = abs(num), abs(den)
+def _round_ratio_exact(n: int, d: int, b: int) -> tuple[int, int]:
+    """(q, t) with q = RNE(n 2^t / d), 2^(b-1) <= q < 2^b, for n, d > 0."""
     t = b - 1 - (n.bit_length() - d.bit_length())  # n 2^t / d in [2^(b-2), 2^b)
     while True:
         q, r = divmod(n << t, d) if t >= 0 else divmod(n, d << -t)
@@ -50,6 +43,60 @@ def round_ratio(num: int, den: int, shift: int, b: int) -> tuple[int, int]:
         if q == 1 << b:
             q >>= 1
             t -= 1
+    return q, t
+
+
+_GUARD = 64  # guard bits of the truncated quotient
+
+
+def _round_ratio_fast(n: int, d: int, b: int):
+    """(q, t) as _round_ratio_exact from the leading b + 2G bits of n and d
+    (G guard bits), or None when the truncated quotient cannot decide the
+    rounding.  With N' = floor(n / 2^kn) and D' = floor(d / 2^kd) both at
+    least 2^(b+2G-1) (or exact), the quotient Q = floor(N' 2^E / D') of the
+    scaled ratio y = n 2^(t+G) / d satisfies |y - N' 2^E / D'| < 2^(2-G), so
+    floor(y) is Q - 1, Q or Q + 1; the rounding at b bits is decided unless
+    the G low bits of Q lie within 3 of one half (or Q within 3 of the
+    normalisation boundary)."""
+    G = _GUARD
+    keep = b + 2 * G
+    kn = max(0, n.bit_length() - keep)
+    kd = max(0, d.bit_length() - keep)
+    N, D = n >> kn, d >> kd
+    t = b - (n.bit_length() - d.bit_length())  # n 2^t / d in [2^(b-1), 2^(b+1))
+    E = t + G + kn - kd
+    Q = (N << E) // D if E >= 0 else N // (D << -E)
+    top = 1 << (b + G)
+    if abs(Q - top) <= 4 or Q < (top >> 1) + 4:
+        return None
+    if Q > top:  # the value at t is above 2^b: one bit less
+        Q >>= 1
+        t -= 1
+        if abs(Q - top) <= 4 or Q < (top >> 1) + 4:
+            return None
+    half = 1 << (G - 1)
+    frac = Q & ((1 << G) - 1)
+    if abs(frac - half) <= 3:
+        return None
+    q = (Q >> G) + (1 if frac > half else 0)
+    if q == 1 << b:
+        q >>= 1
+        t -= 1
+    return q, t
+
+
+def round_ratio(num: int, den: int, shift: int, b: int) -> tuple[int, int]:
+    """(m, e) with m * 2^e = RNE_b(num / den * 2^shift), 2^(b-1) <= |m| < 2^b
+    (m = 0, e = 0 for a zero numerator).  Decided from the leading bits of
+    num and den when that is enough, else by the exact division."""
+    if den == 0:
+        raise ZeroDivisionError("zero denominator")
+    if num == 0:
+        return 0, 0
+    neg = (num < 0) != (den < 0)
+    n, d = abs(num), abs(den)
+    r = _round_ratio_fast(n, d, b)
+    q, t = r if r is not None else _round_ratio_exact(n, d, b)
     return (-q if neg else q), shift - t
 
 
