@@ -206,7 +206,7 @@ def run_ours(args):
                   6: hmv.FLAG_DIGIT_TOOM6}[args.digit_split]
     if args.digit_split == 0 and method == hmv.AUTO:
         method = hmv.KARATSUBA  # no digit split
-    tile_flag = hmv.FLAG_TILE128 if args.tile == 128 else 0
+    tile_flag = {128: hmv.FLAG_TILE128, 256: hmv.FLAG_TILE256}.get(args.tile, 0)
     plan = hmv.Plan(n, b, method=method, levels=args.levels, flags=hmv.FLAG_TIMING | split_flag | tile_flag,
                     stream=stream.cuda_stream)
     plan.load_matrix(h)

@@ -75,7 +75,11 @@ typedef enum {
  * the width per level), on top of the index recursion; HMV_AUTO/HMV_KARATSUBA */
 #define HMV_FLAG_DIGIT_SPLIT1 4u  /* one level */
 #define HMV_FLAG_DIGIT_SPLIT2 8u  /* two levels */
-#define HMV_FLAG_TILE128 16u      /* leaf tiles of 128 product digits (default 256) */
+/* Leaf tile width in product digits.  Without either flag HMV_AUTO picks it
+ * by its cost model (with the digit split) and the other methods take 256;
+ * at most one of the two. */
+#define HMV_FLAG_TILE128 16u      /* leaf tiles of 128 product digits */
+#define HMV_FLAG_TILE256 128u     /* leaf tiles of 256 product digits */
 /* Toom-Cook splitting of the mantissas instead: each mantissa cut into K
  * parts, 2K-1 products of about 1/K of the width, the exact rows recovered by
  * integer interpolation and one exact division (by 360 for K = 4, 1008000

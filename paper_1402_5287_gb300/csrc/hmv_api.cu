@@ -68,10 +68,9 @@ std::vector<LevelGeom> build_levels(int n, int L) {
 }
 
 // SM cycles one 128 x tn x 16 MMA takes inside the leaf kernel (measured at
-// n = 8000: 256-wide tiles run at the tensor pipe's rate, 128-wide ones at
-// 0.57 of it per MAC, because the issuing thread cannot keep up with the
-// shorter MMAs).
-inline double mma_cycles(int tn) { return tn == 128 ? 115.0 : 128.0; }
+// n = 8000, b = 33220 under Toom-6: 256-wide tiles issue at 0.96 of the
+// tensor pipe's rate, 128-wide ones, with two issuing threads, at 0.92).
+inline double mma_cycles(int tn) { return tn == 128 ? 67.0 : 128.0; }
 
 // Estimated seconds of one matvec at depth L on this GPU (tensor work from
 // the tile count, memory work from the bytes the level kernels move).
@@ -109,13 +108,6 @@ int best_depth(int n, int b, int num_sms, double *cost, int tn = TN_DEFAULT) {
     return L;
 }
 
-// Digit-split levels for HMV_AUTO: 3^d products of about b/2^d bits, each
-// at its own best depth, plus the level kernels, which grow by about 3/2
-// per split level (measured: 10.4, 15.2, 22.4 ms at n = 8000, b = 33220
-// for d = 0, 1, 2, i.e. about 3.9e-11 s per n*b at d = 0).  The leaf
-// estimate of the narrower products is scaled by (1 - 0.055 d): measured
-// leaf times (203.6, 167.1, 149.0 ms) beat the tile count by that much,
-// the narrower operands running at higher clocks under the power cap.
 // Digit split for HMV_AUTO: kToom4, kToom6 or the number of Karatsuba levels d (3^d
 // products of about b/2^d bits, d <= 2), each product at its own best depth,
 // plus the level kernels, which scale with the products' total width (n*b
@@ -123,30 +115,35 @@ int best_depth(int n, int b, int num_sms, double *cost, int tn = TN_DEFAULT) {
 // 22.4 ms at n = 8000, b = 33220 for d = 0, 1, 2, about 3.9e-11 s per n*b at
 // d = 0; (2K-1)/K for Toom-K).  The leaf estimate of the narrower products is
 // scaled by (1 - 0.055 d): measured leaf times fall below the tile-count model
-// as the products narrow (Toom-K's products count as d = log2 K).
+// as the products narrow (Toom-K's products count as d = log2 K).  Each
+// scheme is costed at both leaf tile widths; *tn gets the cheaper one.
 constexpr int kToom4 = 4, kToom6 = 6;
-int auto_digit_scheme(int n, int b, int num_sms) {
+int auto_digit_scheme(int n, int b, int num_sms, int *tn, int fixed_tn) {
     int best_d = 0;
     double best = 1e300;
-    int bd = b;
-    double mult = 1.0;
-    for (int d = 0; d <= 2; ++d) {
-        double leaf = 0;
-        best_depth(n, bd, num_sms, &leaf);
-        const double t = mult * leaf * (1.0 - 0.055 * d) + 3.9e-11 * n * static_cast<double>(b) * std::pow(1.5, d);
-        if (t < best) { best = t; best_d = d; }
-        bd = 32 * (((bd + 31) / 32 + 1) / 2) + 1;  // the children's width
-        mult *= 3.0;
-    }
-    // Toom-K: 2K-1 products of s + g bits; narrowing counted as d = log2 K
-    const int L32 = (b + 31) / 32;
-    for (int K : {4, 6}) {
-        if (L32 < K) continue;
-        double leaf = 0;
-        best_depth(n, 32 * ((L32 + K - 1) / K) + (K == 4 ? 4 : 9), num_sms, &leaf);
-        const double t = (2 * K - 1) * leaf * (1.0 - 0.055 * std::log2(static_cast<double>(K))) +
-                         3.9e-11 * n * static_cast<double>(b) * (2.0 * K - 1) / K;
-        if (t < best) { best = t; best_d = (K == 4) ? kToom4 : kToom6; }
+    *tn = fixed_tn ? fixed_tn : TN_DEFAULT;
+    for (int w : {256, 128}) {
+        if (fixed_tn && w != fixed_tn) continue;
+        int bd = b;
+        double mult = 1.0;
+        for (int d = 0; d <= 2; ++d) {
+            double leaf = 0;
+            best_depth(n, bd, num_sms, &leaf, w);
+            const double t = mult * leaf * (1.0 - 0.055 * d) + 3.9e-11 * n * static_cast<double>(b) * std::pow(1.5, d);
+            if (t < best) { best = t; best_d = d; *tn = w; }
+            bd = 32 * (((bd + 31) / 32 + 1) / 2) + 1;  // the children's width
+            mult *= 3.0;
+        }
+        // Toom-K: 2K-1 products of s + g bits; narrowing counted as d = log2 K
+        const int L32 = (b + 31) / 32;
+        for (int K : {4, 6}) {
+            if (L32 < K) continue;
+            double leaf = 0;
+            best_depth(n, 32 * ((L32 + K - 1) / K) + (K == 4 ? 4 : 9), num_sms, &leaf, w);
+            const double t = (2 * K - 1) * leaf * (1.0 - 0.055 * std::log2(static_cast<double>(K))) +
+                             3.9e-11 * n * static_cast<double>(b) * (2.0 * K - 1) / K;
+            if (t < best) { best = t; best_d = (K == 4) ? kToom4 : kToom6; *tn = w; }
+        }
     }
     return best_d;
 }
@@ -271,8 +268,9 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
     if (d.method < HMV_AUTO || d.method > HMV_FFT64) return HMV_EINVAL;
     if (d.levels < -1 || d.levels > kMaxLevels) return HMV_EINVAL;
     if (d.flags & ~(HMV_FLAG_TIMING | HMV_FLAG_SIMT_LEAF | HMV_FLAG_DIGIT_SPLIT1 | HMV_FLAG_DIGIT_SPLIT2 |
-                    HMV_FLAG_TILE128 | HMV_FLAG_DIGIT_TOOM4 | HMV_FLAG_DIGIT_TOOM6))
+                    HMV_FLAG_TILE128 | HMV_FLAG_TILE256 | HMV_FLAG_DIGIT_TOOM4 | HMV_FLAG_DIGIT_TOOM6))
         return HMV_EINVAL;
+    if ((d.flags & HMV_FLAG_TILE128) && (d.flags & HMV_FLAG_TILE256)) return HMV_EINVAL;
     const uint32_t split_flags =
         d.flags & (HMV_FLAG_DIGIT_SPLIT1 | HMV_FLAG_DIGIT_SPLIT2 | HMV_FLAG_DIGIT_TOOM4 | HMV_FLAG_DIGIT_TOOM6);
     if (split_flags & (split_flags - 1)) return HMV_EINVAL;  // at most one digit split
@@ -321,8 +319,13 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
     Guard g;
     const int n = d.n;
     int dl = digit_levels;
-    if (dl == 0 && d.method == HMV_AUTO && d.levels < 0 && !(d.flags & HMV_FLAG_SIMT_LEAF) && !external_scratch)
-        dl = auto_digit_scheme(n, d.b, p->num_sms);
+    if (dl == 0 && d.method == HMV_AUTO && d.levels < 0 && !(d.flags & HMV_FLAG_SIMT_LEAF) && !external_scratch) {
+        const bool fixed = (d.flags & (HMV_FLAG_TILE128 | HMV_FLAG_TILE256)) != 0;
+        int tn = TN_DEFAULT;
+        dl = auto_digit_scheme(n, d.b, p->num_sms, &tn, fixed ? p->tn : 0);
+        // a split plan's products take the scheme's tile width
+        if (dl != 0) p->tn = tn;
+    }
     digit_levels = dl;
     const bool toom = digit_levels == kToom4 || digit_levels == kToom6;
     p->digit_levels = toom ? 0 : digit_levels;
@@ -363,7 +366,8 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
         // under HMV_AUTO the tile width too (128 only pays where it cuts the
         // padded product digits enough, i.e. for short mantissas)
         int L = d.levels;
-        const bool auto_tile = d.method == HMV_AUTO && !(d.flags & (HMV_FLAG_TILE128 | HMV_FLAG_SIMT_LEAF));
+        const bool auto_tile =
+            d.method == HMV_AUTO && !(d.flags & (HMV_FLAG_TILE128 | HMV_FLAG_TILE256 | HMV_FLAG_SIMT_LEAF));
         if (auto_tile) {
             double c256 = 0, c128 = 0;
             const int L256 = L < 0 ? best_depth(n, d.b, p->num_sms, &c256, 256) : L;

@@ -21,7 +21,11 @@
 //
 // Warp roles (192 threads): warp 0 issues TMA loads, warp 1 allocates TMEM
 // and one lane issues tcgen05.mma, warps 2-5 run the epilogue on the four
-// TMEM lane quarters.  Tiles are handed out in list order from a global
+// TMEM lane quarters.  128-digit tiles add warp 6 as a second MMA issuer:
+// one thread cannot issue 128 x 128 x 16 MMAs (about 65 cycles of tensor
+// work each) as fast as the tensor pipe runs them once its loop waits on
+// barriers, two threads together can; the two take alternate j-steps of a
+// tile into accumulators of their own, and the epilogue adds the pair.  Tiles are handed out in list order from a global
 // counter (the producer takes the next index and passes it to the CTA's
 // consumers through a small shared-memory queue), so the grid works on
 // neighbouring tiles of the same leaves and their operands stay in L2.  Two 128x256 fp32 accumulators (all 512 TMEM columns)
@@ -40,21 +44,24 @@ constexpr int kProducerWarp = 0;
 constexpr int kMmaWarp = 1;
 constexpr int kEpiWarp0 = 2;
 constexpr int kNumEpiWarps = 4;
-constexpr int kThreads = (2 + kNumEpiWarps) * 32;
+constexpr int kMmaWarp2 = 2 + kNumEpiWarps;  // second issuer of 128-digit tiles
 constexpr uint64_t kTimeoutNs = 2000000000ull;  // 2 s for any single wait
 // Tile width in product digits: 256 (one 128x256 MMA per k-step) or 128
 // (narrow operands, where the wide tile's triangular edges waste more).
 template <int TNv>
 struct Geo {
+    static constexpr int NI = TNv == 128 ? 2 : 1;           // MMA-issuing threads
+    static constexpr int kThreads = (2 + kNumEpiWarps + NI - 1) * 32;
     static constexpr int NEv = TNv / 8 + KS / 8 - 1;        // core matrices of one shifted-x operand
     static constexpr int BB = NEv * 128;                    // its bytes
-    static constexpr int BS = TNv == 256 ? 8 : 16;          // B ring slots
-    static constexpr uint32_t kTmemCols = 2 * TNv;          // two accumulators
+    static constexpr int BS = TNv == 256 ? 8 : 16;          // B ring slots (even: see the issuers)
+    static constexpr uint32_t kTmemCols = 2 * TNv * NI;     // two accumulators per issuer
     static constexpr uint32_t kIdesc = idesc_bf16_f32(TM, TNv);
+    static_assert(BS % 2 == 0 && kTmemCols <= 512, "ring and TMEM layout");
 };
 constexpr uint32_t kLboA = AR * 16;  // K-direction core-matrix step of the slab
 constexpr int kTileQ = 4;            // tile indices handed from the producer to the consumers
-constexpr int kTileConsumers = 1 + kNumEpiWarps;
+constexpr int kTileConsumers = 1 + kNumEpiWarps;  // plus the second issuer where there is one
 
 template <int TNv>
 struct __align__(1024) Smem {
@@ -62,10 +69,10 @@ struct __align__(1024) Smem {
     uint8_t b[Geo<TNv>::BS][Geo<TNv>::BB];
     uint64_t a_full[A_STAGES], a_empty[A_STAGES];
     uint64_t b_full[Geo<TNv>::BS], b_empty[Geo<TNv>::BS];
-    uint64_t acc_full[2], acc_empty[2];
+    uint64_t acc_full[Geo<TNv>::NI][2], acc_empty[Geo<TNv>::NI][2];
     uint64_t tq_full[kTileQ], tq_empty[kTileQ];
     int tile_q[kTileQ];
-    uint64_t drain;
+    uint64_t drain[Geo<TNv>::NI];
     uint32_t tmem_base;
     volatile int abort;
 };
@@ -106,11 +113,12 @@ __device__ __forceinline__ void fail(S &sm, int32_t *dstat) {
 }
 
 template <int TNv>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(Geo<TNv>::kThreads, 1)
     k_leaf_tc(const LeafProblem *__restrict__ probs, const Tile *__restrict__ tiles, int ntiles, int *tile_counter,
               int32_t *dstat) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     using G = Geo<TNv>;
+    constexpr int NI = G::NI;
     constexpr int B_STAGES = G::BS;
     constexpr int B_BYTES = G::BB;
     constexpr int TN = TNv;
@@ -118,11 +126,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < A_STAGES; ++s) { mbar_init(&sm.a_full[s], 1); mbar_init(&sm.a_empty[s], 1); }
+        for (int s = 0; s < A_STAGES; ++s) { mbar_init(&sm.a_full[s], 1); mbar_init(&sm.a_empty[s], NI); }
         for (int s = 0; s < B_STAGES; ++s) { mbar_init(&sm.b_full[s], 1); mbar_init(&sm.b_empty[s], 1); }
-        for (int s = 0; s < 2; ++s) { mbar_init(&sm.acc_full[s], 1); mbar_init(&sm.acc_empty[s], kNumEpiWarps); }
-        for (int s = 0; s < kTileQ; ++s) { mbar_init(&sm.tq_full[s], 1); mbar_init(&sm.tq_empty[s], kTileConsumers); }
-        mbar_init(&sm.drain, 1);
+        for (int w = 0; w < NI; ++w)
+            for (int s = 0; s < 2; ++s) {
+                mbar_init(&sm.acc_full[w][s], 1);
+                mbar_init(&sm.acc_empty[w][s], kNumEpiWarps);
+            }
+        for (int s = 0; s < kTileQ; ++s) {
+            mbar_init(&sm.tq_full[s], 1);
+            mbar_init(&sm.tq_empty[s], kTileConsumers + NI - 1);
+        }
+        for (int w = 0; w < NI; ++w) mbar_init(&sm.drain[w], 1);
         sm.abort = 0;
         fence_mbar_init();
     }
@@ -172,7 +187,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
         }
-    } else if (warp == kMmaWarp) {
+    } else if (warp == kMmaWarp && NI == 1) {
         if (lane == 0) {
             int as = 0, aph = 0, bs = 0, bph = 0, ab = 0;
             int accph[2] = {0, 0};
@@ -194,7 +209,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const uint32_t a_base = a_base0 + as * A_BYTES;
                         for (int jj = 0; jj < jn; ++jj) {
                             if (q % FLUSH_J == 0) {
-                                if (!mbar_wait(&sm.acc_empty[ab], accph[ab] ^ 1, kTimeoutNs)) { fail(sm, dstat); break; }
+                                if (!mbar_wait(&sm.acc_empty[0][ab], accph[ab] ^ 1, kTimeoutNs)) { fail(sm, dstat); break; }
                                 acc_flag = 0;
                             }
                             if (!mbar_wait(&sm.b_full[bs], bph, kTimeoutNs)) { fail(sm, dstat); break; }
@@ -210,7 +225,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             if (++bs == B_STAGES) { bs = 0; bph ^= 1; }
                             ++q;
                             if (q % FLUSH_J == 0 || q == ti.Q) {
-                                mma_commit(&sm.acc_full[ab]);
+                                mma_commit(&sm.acc_full[0][ab]);
                                 accph[ab] ^= 1;
                                 ab ^= 1;
                             }
@@ -221,15 +236,76 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             // all MMAs issued by this thread complete before TMEM is released
-            mma_commit(&sm.drain);
-            if (!mbar_wait(&sm.drain, 0, kTimeoutNs)) fail(sm, dstat);
+            mma_commit(&sm.drain[0]);
+            if (!mbar_wait(&sm.drain[0], 0, kTimeoutNs)) fail(sm, dstat);
+        }
+    } else if (NI == 2 && (warp == kMmaWarp || warp == kMmaWarp2)) {
+        // issuer w takes the tile's j-steps q = w, w + 2, ... (q counts the
+        // tile's j-steps in the producer's order: s-block, then j); step q
+        // is the producer's global step gq + q, whose B slot and phase follow
+        // from the ring size, and every A slab is released by both issuers
+        const int w = warp == kMmaWarp ? 0 : 1;
+        if (lane == 0) {
+            int as = 0, aph = 0, ab = 0, gq = 0;
+            int accph[2] = {0, 0};
+            const uint32_t a_base0 = smem_u32(sm.a[0]);
+            const uint32_t b_base0 = smem_u32(sm.b[0]);
+            const uint32_t tmem_w = tmem + static_cast<uint32_t>(w * 2 * TN);
+            for (int k = 0; !sm.abort; ++k) {
+                const int qs = k % kTileQ, qph = (k / kTileQ) & 1;
+                if (!mbar_wait(&sm.tq_full[qs], qph, kTimeoutNs)) { fail(sm, dstat); break; }
+                const int t = sm.tile_q[qs];
+                mbar_arrive(&sm.tq_empty[qs]);
+                if (t < 0) break;
+                const TileInfo ti = decode<TNv>(tiles[t], probs);
+                const int Qw = (ti.Q - w + 1) / 2;  // this issuer's j-steps in the tile
+                int qw = 0;
+                uint32_t acc_flag = 0;
+                for (int sb = 0; sb < ti.nsb && !sm.abort; ++sb) {
+                    for (int jc = 0; jc < ti.njc && !sm.abort; ++jc) {
+                        const int j0 = jc * JC;
+                        const int jn = min(JC, ti.m - j0);
+                        const int q0 = sb * ti.m + j0;  // tile step of jj = 0
+                        if (!mbar_wait(&sm.a_full[as], aph, kTimeoutNs)) { fail(sm, dstat); break; }
+                        const uint32_t a_base = a_base0 + as * A_BYTES;
+                        for (int jj = (q0 + w) & 1; jj < jn; jj += 2) {
+                            if (qw % FLUSH_J == 0) {
+                                if (!mbar_wait(&sm.acc_empty[w][ab], accph[ab] ^ 1, kTimeoutNs)) { fail(sm, dstat); break; }
+                                acc_flag = 0;
+                            }
+                            const int gs = gq + q0 + jj;
+                            const int bs = gs % B_STAGES;
+                            if (!mbar_wait(&sm.b_full[bs], (gs / B_STAGES) & 1, kTimeoutNs)) { fail(sm, dstat); break; }
+                            tc_fence_after();
+                            const uint32_t b_base = b_base0 + bs * B_BYTES;
+                            mma_bf16_ss_k128<2 * kLboA, 256>(tmem_w + ab * TN, smem_desc(a_base + jj * 16, kLboA, 128),
+                                                             smem_desc(b_base, 128, 128), G::kIdesc, acc_flag);
+                            acc_flag = 1;
+                            mma_commit(&sm.b_empty[bs]);
+                            ++qw;
+                            if (qw % FLUSH_J == 0 || qw == Qw) {
+                                mma_commit(&sm.acc_full[w][ab]);
+                                accph[ab] ^= 1;
+                                ab ^= 1;
+                            }
+                        }
+                        mma_commit(&sm.a_empty[as]);
+                        if (++as == A_STAGES) { as = 0; aph ^= 1; }
+                    }
+                }
+                gq += ti.Q;
+            }
+            mma_commit(&sm.drain[w]);
+            if (!mbar_wait(&sm.drain[w], 0, kTimeoutNs)) fail(sm, dstat);
         }
     } else {
         // epilogue: warp w serves TMEM lanes 32*(w%4) .. +31
         const int lq = warp % 4;
         const uint32_t lane_addr = tmem + (static_cast<uint32_t>(lq * 32) << 16);
-        int ab = 0;
-        int eph[2] = {0, 0};
+        // issuer w's accumulator pair: TMEM columns (2 w + ab) TN .. + TN - 1
+        int ab[NI], eph[NI][2];
+#pragma unroll
+        for (int w = 0; w < NI; ++w) { ab[w] = 0; eph[w][0] = eph[w][1] = 0; }
         for (int k = 0; !sm.abort; ++k) {
             const int qs = k % kTileQ, qph = (k / kTileQ) & 1;
             if (!mbar_wait(&sm.tq_full[qs], qph, kTimeoutNs)) { fail(sm, dstat); break; }
@@ -238,30 +314,49 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (lane == 0) mbar_arrive(&sm.tq_empty[qs]);
             if (t < 0) break;
             const TileInfo ti = decode<TNv>(tiles[t], probs);
-            const int G = (ti.Q + FLUSH_J - 1) / FLUSH_J;
+            // windows of the first issuer (ceil(Q / NI) j-steps) and of the second (floor(Q / 2))
+            const int nw0 = ((ti.Q + NI - 1) / NI + FLUSH_J - 1) / FLUSH_J;
+            const int nw1 = NI == 2 ? (ti.Q / 2 + FLUSH_J - 1) / FLUSH_J : 0;
             uint32_t st[TN / 4];
 #pragma unroll
             for (int w = 0; w < TN / 4; ++w) st[w] = 0;
             int co = 0;
             bool ok = true;
-            for (int g = 0; g < G; ++g) {
-                if (!mbar_wait(&sm.acc_full[ab], eph[ab], kTimeoutNs)) { fail(sm, dstat); ok = false; break; }
-                eph[ab] ^= 1;
+            for (int g = 0; g < nw0; ++g) {
+                const bool two = NI == 2 && g < nw1;
+                if (!mbar_wait(&sm.acc_full[0][ab[0]], eph[0][ab[0]], kTimeoutNs)) { fail(sm, dstat); ok = false; break; }
+                eph[0][ab[0]] ^= 1;
+                if (two) {
+                    if (!mbar_wait(&sm.acc_full[NI - 1][ab[NI - 1]], eph[NI - 1][ab[NI - 1]], kTimeoutNs)) {
+                        fail(sm, dstat);
+                        ok = false;
+                        break;
+                    }
+                    eph[NI - 1][ab[NI - 1]] ^= 1;
+                }
                 tc_fence_after();
                 int c = 0;
 #pragma unroll
                 for (int ch = 0; ch < TN / 32; ++ch) {
                     uint32_t v[32];
-                    tmem_ld_32x32b_x32(lane_addr + ab * TN + ch * 32, v);
+                    tmem_ld_32x32b_x32(lane_addr + ab[0] * TN + ch * 32, v);
                     tmem_ld_wait();
+                    int x[32];
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) x[e] = __float2int_rn(__uint_as_float(v[e]));
+                    if (two) {
+                        tmem_ld_32x32b_x32(lane_addr + (2 + ab[NI - 1]) * TN + ch * 32, v);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int e = 0; e < 32; ++e) x[e] += __float2int_rn(__uint_as_float(v[e]));
+                    }
 #pragma unroll
                     for (int q4 = 0; q4 < 8; ++q4) {
                         const uint32_t word = st[ch * 8 + q4];
                         uint32_t nw = 0;
 #pragma unroll
                         for (int by = 0; by < 4; ++by) {
-                            const int x = __float2int_rn(__uint_as_float(v[q4 * 4 + by]));
-                            const int tt = static_cast<int>((word >> (8 * by)) & 0xFFu) + x + c;
+                            const int tt = static_cast<int>((word >> (8 * by)) & 0xFFu) + x[q4 * 4 + by] + c;
                             nw |= static_cast<uint32_t>(tt & 0xFF) << (8 * by);
                             c = tt >> 8;
                         }
@@ -271,8 +366,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 co += c;
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&sm.acc_empty[ab]);
-                ab ^= 1;
+                if (lane == 0) {
+                    mbar_arrive(&sm.acc_empty[0][ab[0]]);
+                    if (two) mbar_arrive(&sm.acc_empty[NI - 1][ab[NI - 1]]);
+                }
+                ab[0] ^= 1;
+                if (two) ab[NI - 1] ^= 1;
             }
             if (!ok) break;
             const int row = ti.i0 + lq * 32 + lane;
@@ -329,9 +428,9 @@ cudaError_t launch_leaf_tc_multi(const LeafProblem *probs, const Tile *tiles, in
     cudaError_t me = cudaMemsetAsync(tile_counter, 0, sizeof(int), stream);
     if (me != cudaSuccess) return me;
     if (tn == 128)
-        k_leaf_tc<128><<<grid, kThreads, sizeof(Smem<128>), stream>>>(probs, tiles, ntiles, tile_counter, dstat);
+        k_leaf_tc<128><<<grid, Geo<128>::kThreads, sizeof(Smem<128>), stream>>>(probs, tiles, ntiles, tile_counter, dstat);
     else
-        k_leaf_tc<256><<<grid, kThreads, sizeof(Smem<256>), stream>>>(probs, tiles, ntiles, tile_counter, dstat);
+        k_leaf_tc<256><<<grid, Geo<256>::kThreads, sizeof(Smem<256>), stream>>>(probs, tiles, ntiles, tile_counter, dstat);
     return cudaGetLastError();
 }
 

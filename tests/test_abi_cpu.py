@@ -44,7 +44,8 @@ def test_status_strings_and_version(lib):
 
 
 @pytest.mark.parametrize("field,value", [("n", 0), ("b", 0), ("b", (1 << 20) + 1), ("nrhs", 0), ("kind", 3),
-                                         ("method", 9), ("levels", -2), ("levels", 17), ("flags", 1 << 7),
+                                         ("method", 9), ("levels", -2), ("levels", 17), ("flags", 1 << 8),
+                                         ("flags", hmv.FLAG_TILE128 | hmv.FLAG_TILE256),
                                          ("piece_bits", 5), ("piece_bits", -1)])
 def test_plan_rejects_bad_descriptors_without_gpu(lib, field, value):
     d = hmv.Desc(16, 64, 1, 0, 0, -1, 0, 0)

@@ -72,7 +72,8 @@ def test_tile128_worst_case_digits():
     assert_same(run(n, b, h, x, flags=T128, levels=2)[0], want)
 
 
-@pytest.mark.parametrize("split", [hmv.FLAG_DIGIT_SPLIT1, hmv.FLAG_DIGIT_SPLIT2])
+@pytest.mark.parametrize("split", [hmv.FLAG_DIGIT_SPLIT1, hmv.FLAG_DIGIT_SPLIT2, hmv.FLAG_DIGIT_TOOM4,
+                                   hmv.FLAG_DIGIT_TOOM6])
 def test_tile128_under_digit_split(split):
     n, b = 100, 4100
     h = uniform_vec(95, 0, 2 * n - 1, b, 1)
@@ -126,18 +127,29 @@ def test_tile128_batch_and_many_mixed_widths():
 
 def test_tile128_large_workload_matches_default():
     n, b, h, x = workload("large")
-    y0, _ = run(n, b, h, x, method=hmv.AUTO)
+    y0, st0 = run(n, b, h, x, flags=hmv.FLAG_TILE256, method=hmv.AUTO)
     y, st = run(n, b, h, x, flags=T128, method=hmv.AUTO)
+    assert st0["leaf_tile_digits"] == 256 and st["leaf_tile_digits"] == 128
     assert_same(y, y0)
     sampled_parity(oracle.HANKEL, n, h, x, y, 3, 11)
 
 
-@pytest.mark.parametrize("n,b,want", [(300, 256, 128), (300, 64, 128), (200, 4096, 256), (120, 1024, 256)])
-def test_auto_chooses_tile_width_and_stays_exact(n, b, want):
-    """HMV_AUTO takes 128-wide tiles only where they cut the padded product
-    digits enough (short mantissas); either way the result is exact."""
+@pytest.mark.parametrize("n,b,levels,want", [(300, 256, -1, 128), (300, 64, -1, 128), (200, 4096, -1, 128),
+                                              (120, 33220, 1, 256), (64, 33220, 0, 256)])
+def test_auto_chooses_tile_width_and_stays_exact(n, b, levels, want):
+    """HMV_AUTO weighs the padded product digits of each width against the
+    MMA rates: 128-wide tiles (two issuing threads) for all but the widest
+    unsplit products; either way the result is exact."""
     h = uniform_vec(99 + b, 0, 2 * n - 1, b, 1)
     x = uniform_vec(99 + b, 1, n, b, 2)
-    y, st = run(n, b, h, x, method=hmv.AUTO)
+    y, st = run(n, b, h, x, method=hmv.AUTO, levels=levels)
     assert st["leaf_tile_digits"] == want
     assert_same(y, oracle_matvec(oracle.HANKEL, n, h, x))
+
+
+def test_auto_benchmark_size_takes_toom6_on_128_wide_tiles():
+    """At n = 8000, b = 33220 the cost model picks Toom-6 on 128-wide tiles."""
+    n, b = 8000, 33220
+    with hmv.Plan(n, b, method=hmv.AUTO) as p:
+        st = p.stats()
+    assert st["digit_products"] == 11 and st["leaf_tile_digits"] == 128
