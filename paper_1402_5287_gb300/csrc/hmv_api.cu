@@ -72,10 +72,43 @@ std::vector<LevelGeom> build_levels(int n, int L) {
 // tensor pipe's rate, 128-wide ones, with two issuing threads, at 0.92).
 inline double mma_cycles(int tn) { return tn == 128 ? 67.0 : 128.0; }
 
+// Node orders of every level as (order, count) pairs: a level holds 3^l nodes
+// but only a few distinct orders, so the cost model runs in time independent
+// of 3^l (building the node lists of deep levels for every candidate depth
+// and split dominated plan creation).
+struct OrderHist {
+    std::vector<std::pair<int, double>> order;  // distinct orders and their node counts
+    int smax = 0;
+    double nodes = 0;
+};
+
+std::vector<OrderHist> order_hists(int n, int L) {
+    std::vector<OrderHist> h(L + 1);
+    h[0].order = {{n, 1.0}};
+    for (int l = 0; l < L; ++l) {
+        std::vector<std::pair<int, double>> &ch = h[l + 1].order;
+        auto add = [&ch](int s, double c) {
+            for (auto &e : ch)
+                if (e.first == s) { e.second += c; return; }
+            ch.push_back({s, c});
+        };
+        for (const auto &e : h[l].order) {
+            add((e.first + 1) / 2, 2 * e.second);
+            add((e.first + 2) / 2, e.second);
+        }
+    }
+    for (auto &g : h)
+        for (const auto &e : g.order) {
+            g.smax = std::max(g.smax, e.first);
+            g.nodes += e.second;
+        }
+    return h;
+}
+
 // Estimated seconds of one matvec at depth L on this GPU (tensor work from
-// the tile count, memory work from the bytes the level kernels move).
-double cost_model(int n, int b, int L, int num_sms, int tn = TN_DEFAULT) {
-    std::vector<LevelGeom> lv = build_levels(n, L);
+// the tile count, memory work from the bytes the level kernels move); hs
+// holds the order histograms of at least L + 1 levels.
+double cost_model(const std::vector<OrderHist> &hs, int b, int L, int num_sms, int tn) {
     const int Dl = ceil_div(b + L + 2, 8);
     const long long Dp = round_up(Dl, 16);
     const int Uo = static_cast<int>(round_up(2LL * Dl - 1, tn));
@@ -85,23 +118,29 @@ double cost_model(int n, int b, int L, int num_sms, int tn = TN_DEFAULT) {
         const int u0 = ub * tn;
         const int s_min = std::max(0, u0 - (Dl - 1)), s_max = std::min(Dl - 1, u0 + tn - 1);
         const int nsb = (s_max >= s_min) ? (s_max - s_min / 8 * 8 + KS) / KS : 0;
-        for (int s : lv[L].size) ksteps += static_cast<double>(ceil_div(s, TM)) * nsb * s * (KS / 16);
+        for (const auto &e : hs[L].order)
+            ksteps += e.second * static_cast<double>(ceil_div(e.first, TM)) * nsb * e.first * (KS / 16);
     }
     const double mma_s = ksteps * mma_cycles(tn) / (static_cast<double>(num_sms) * 1.9e9);
     double bytes = 0;
-    for (int l = 0; l <= L; ++l)
-        bytes += static_cast<double>(lv[l].nodes) * lv[l].rowsX * (Dp * 2.0 + (Uo + 8) * 4.0 * 4.0);
-    bytes += static_cast<double>(lv[L].nodes) * lv[L].rowsX * Dp * 16.0 * 2.0;
+    for (int l = 0; l <= L; ++l) bytes += hs[l].nodes * hs[l].smax * (Dp * 2.0 + (Uo + 8) * 4.0 * 4.0);
+    bytes += hs[L].nodes * hs[L].smax * Dp * 16.0 * 2.0;
     return mma_s + bytes / 5.0e12;
 }
 
-// Cheapest index depth for (n, b) and its estimated seconds.
+double cost_model(int n, int b, int L, int num_sms, int tn = TN_DEFAULT) {
+    return cost_model(order_hists(n, L), b, L, num_sms, tn);
+}
+
+// Cheapest index depth for (n, b) and its estimated seconds (depths stop
+// once the leaves have order <= 2).
 int best_depth(int n, int b, int num_sms, double *cost, int tn = TN_DEFAULT) {
+    const std::vector<OrderHist> hs = order_hists(n, kMaxLevels);
     int L = 0;
     double best = 1e300;
     for (int t = 0; t <= kMaxLevels; ++t) {
-        if (t > 0 && build_levels(n, t - 1).back().smax <= 2) break;
-        const double c = cost_model(n, b, t, num_sms, tn);
+        if (t > 0 && hs[t - 1].smax <= 2) break;
+        const double c = cost_model(hs, b, t, num_sms, tn);
         if (c < best) { best = c; L = t; }
     }
     if (cost) *cost = best;
