@@ -196,6 +196,11 @@ hmv_status hmv_reset_stats(hmv_plan_t *plan);
  * CUDA graph holding every wave and every level kernel.  wave_bytes bounds
  * the device memory of one wave's leaf operands and outputs (pairs are
  * grouped in order; a pair larger than the budget gets a wave of its own).
+ * Matrices whose mantissas HMV_AUTO would split (or whose flags ask for a
+ * digit split) keep the buffers of a single plan, outside wave_bytes, and
+ * run in one round per right-hand side: every such matrix's vector side,
+ * one persistent launch over all their digit products per tile width, then
+ * their interpolation.
  * stream: as for hmv_plan; NULL makes the batch create its own stream
  * (the legacy default stream cannot be captured).  Results are bit-identical
  * to hmv_matvec on each matrix alone.
@@ -204,9 +209,9 @@ typedef struct hmv_batch_s hmv_batch_t;
 typedef struct {
     int32_t matrices;          /* count */
     int32_t pairs;             /* sum of nrhs */
-    int32_t waves;             /* persistent leaf launches per call */
+    int32_t waves;             /* persistent leaf launches per call (waves plus split rounds) */
     int32_t reserved;
-    int64_t leaf_tiles;        /* 128 x 256 leaf tiles per call */
+    int64_t leaf_tiles;        /* leaf tiles per call */
     double leaf_macs;          /* useful digit multiply-adds per call */
     int64_t device_bytes;      /* device memory held by the batch */
     int64_t graph_launches;    /* graph launches so far (one per hmv_batch_matvec) */

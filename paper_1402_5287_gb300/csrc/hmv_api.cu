@@ -227,6 +227,11 @@ void share_status(hmv_plan_s *p, int32_t *dstat) {
 
 }  // namespace
 
+int choose_digit_split(int n, int b, int num_sms, int fixed_tn) {
+    int tn = TN_DEFAULT;
+    return auto_digit_scheme(n, b, num_sms, &tn, fixed_tn);
+}
+
 cudaError_t launch_validate(hmv_plan_s *p, const uint32_t *limbs, int rows) {
     k_validate<<<ceil_div(rows, 128), 128, 0, p->stream>>>(limbs, rows, p->L32, p->b, p->dstat);
     p->launches_total++;

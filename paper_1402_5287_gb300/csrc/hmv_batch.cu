@@ -12,6 +12,13 @@
 // pairs, since they are used one pair after another.  The whole sequence
 // (every wave, every pair, the rounding of every matrix) is captured once in
 // a CUDA graph and replayed by each hmv_batch_matvec.
+//
+// Members whose mantissas the cost model splits (Karatsuba or Toom-Cook on
+// the digits, the same choice a single HMV_AUTO plan makes) keep their own
+// buffers, outside the wave budget: they run in rounds, one per right-hand
+// side, each round the vector side of every such member, ONE persistent leaf
+// launch over all their digit products (per tile width), and the post-pass
+// with the interpolation of every member.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -50,6 +57,17 @@ struct hmv_batch_s {
     int64_t tiles_total = 0;
     int64_t graph_launches = 0, kernels_per_launch = 0;
     int num_sms = 0;
+    // members run as split plans (own buffers), and per round r (right-hand
+    // side r) and tile width the combined leaf problems of their products
+    std::vector<char> split;
+    int split_rounds = 0;
+    struct SplitLaunch {
+        int round, tn, ntiles;
+        hmv::LeafProblem *probs;
+        hmv::Tile *tiles;
+    };
+    std::vector<SplitLaunch> split_launches;
+    hmv_plan_s *split_first = nullptr;  // status word and tile counter of the split launches
 };
 
 namespace hmv {
@@ -119,6 +137,30 @@ cudaError_t issue(hmv_batch_s *B) {
             kernels += 2 + p->L;
         }
     }
+    // split members: a round per right-hand side
+    for (int r = 0; r < B->split_rounds && e == cudaSuccess; ++r) {
+        for (size_t i = 0; i < B->plans.size() && e == cudaSuccess; ++i) {
+            hmv_plan_s *p = B->plans[i];
+            if (!B->split[i] || r >= p->nrhs) continue;
+            const int64_t before = p->launches_total;
+            e = split_vector_side(p, p->x_limbs_d + static_cast<size_t>(r) * p->n * p->L32,
+                                  p->x_neg_d + static_cast<size_t>(r) * p->n);
+            kernels += p->launches_total - before;
+        }
+        for (const auto &sl : B->split_launches) {
+            if (sl.round != r || e != cudaSuccess) continue;
+            e = launch_leaf_tc_multi(sl.probs, sl.tiles, sl.ntiles, B->split_first->dstat, B->split_first->d_counter,
+                                     B->stream, B->num_sms, sl.tn);
+            ++kernels;
+        }
+        for (size_t i = 0; i < B->plans.size() && e == cudaSuccess; ++i) {
+            hmv_plan_s *p = B->plans[i];
+            if (!B->split[i] || r >= p->nrhs) continue;
+            const int64_t before = p->launches_total;
+            e = split_post(p, r);
+            kernels += p->launches_total - before;
+        }
+    }
     for (hmv_plan_s *p : B->plans) {
         if (e == cudaSuccess)
             e = launch_round(p, p->n * p->nrhs, p->e_h + p->batch_x_exponent, p->y_limbs_d, p->y_neg_d);
@@ -139,7 +181,12 @@ void hmv_batch_free(hmv_batch_t *B) {
     if (!B) return;
     if (B->stream) cudaStreamSynchronize(B->stream);
     if (B->exec) cudaGraphExecDestroy(B->exec);
-    for (hmv_plan_s *p : B->plans) {
+    for (size_t i = 0; i < B->plans.size(); ++i) {
+        hmv_plan_s *p = B->plans[i];
+        if (i < B->split.size() && B->split[i]) {  // a split member owns all its buffers
+            hmv_free(p);
+            continue;
+        }
         // the batch owns the shared buffers these point to
         p->x_lvl[0] = p->x_lvl[1] = nullptr;
         p->a_lvl[0] = p->a_lvl[1] = nullptr;
@@ -172,18 +219,45 @@ hmv_status hmv_batch_create(int32_t count, const hmv_desc *descs, void *stream, 
         }
         B->own_stream = true;
     }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&B->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        hmv_batch_free(B);
+        return HMV_ECUDA;
+    }
+    const uint32_t kSplitFlags =
+        HMV_FLAG_DIGIT_SPLIT1 | HMV_FLAG_DIGIT_SPLIT2 | HMV_FLAG_DIGIT_TOOM4 | HMV_FLAG_DIGIT_TOOM6;
     for (int i = 0; i < count; ++i) {
         hmv_desc d = descs[i];
         d.flags &= ~HMV_FLAG_TIMING;  // no host-side event syncs inside a graph
+        // split the mantissas where a single HMV_AUTO plan would (or the flags ask)
+        bool split = (d.flags & kSplitFlags) != 0;
+        if (!split && d.method == HMV_AUTO && d.levels < 0) {
+            const int fixed = (d.flags & HMV_FLAG_TILE128) ? 128 : ((d.flags & HMV_FLAG_TILE256) ? 256 : 0);
+            split = choose_digit_split(d.n, d.b, B->num_sms, fixed) != 0;
+        }
         hmv_plan_s *p = nullptr;
-        hmv_status st = plan_create(&d, B->stream, true, &p);
+        hmv_status st = plan_create(&d, B->stream, !split, &p);
+        if (st == HMV_OK && split && p->children.empty()) {  // not split after all: join the waves
+            hmv_free(p);
+            p = nullptr;
+            split = false;
+            st = plan_create(&d, B->stream, true, &p);
+        }
         if (st != HMV_OK) { hmv_batch_free(B); return st; }
         B->plans.push_back(p);
+        B->split.push_back(split ? 1 : 0);
+        if (split) {
+            B->split_rounds = std::max(B->split_rounds, p->nrhs);
+            if (!B->split_first) B->split_first = p;
+        }
     }
-    B->num_sms = B->plans[0]->num_sms;
     cudaError_t e = cudaSuccess;
     size_t mA = 0, mX = 0, mP = 0;
-    for (hmv_plan_s *p : B->plans) {
+    for (int i = 0; i < count; ++i) {
+        if (B->split[i]) continue;
+        const hmv_plan_s *p = B->plans[i];
         mA = std::max(mA, p->bytes_a_lvl);
         mX = std::max(mX, p->bytes_x_lvl);
         mP = std::max(mP, p->bytes_post);
@@ -197,6 +271,7 @@ hmv_status hmv_batch_create(int32_t count, const hmv_desc *descs, void *stream, 
     // wave, so one width per wave), a new wave when the budget would be exceeded
     std::vector<size_t> wave_size;
     for (int i = 0; i < count; ++i) {
+        if (B->split[i]) continue;
         B->plans[i]->a_lvl[0] = B->a_lvl[0];
         B->plans[i]->a_lvl[1] = B->a_lvl[1];
     }
@@ -204,7 +279,7 @@ hmv_status hmv_batch_create(int32_t count, const hmv_desc *descs, void *stream, 
         bool fresh = true;
         for (int i = 0; i < count; ++i) {
             hmv_plan_s *p = B->plans[i];
-            if (p->tn != tn) continue;
+            if (B->split[i] || p->tn != tn) continue;
             for (int r = 0; r < p->nrhs; ++r) {
                 const size_t sz = pair_bytes(p);
                 if (fresh || (wave_size.back() + sz > wave_bytes && wave_size.back() > 0)) {
@@ -218,7 +293,7 @@ hmv_status hmv_batch_create(int32_t count, const hmv_desc *descs, void *stream, 
         }
     }
     B->nwaves = static_cast<int>(wave_size.size());
-    const size_t arena_bytes = *std::max_element(wave_size.begin(), wave_size.end());
+    const size_t arena_bytes = wave_size.empty() ? 0 : *std::max_element(wave_size.begin(), wave_size.end());
     uint8_t *arena = nullptr;
     if (e == cudaSuccess) e = balloc(B, reinterpret_cast<void **>(&arena), arena_bytes);
     // carve each wave's pairs out of the arena (waves reuse it in turn)
@@ -266,6 +341,40 @@ hmv_status hmv_batch_create(int32_t count, const hmv_desc *descs, void *stream, 
         B->d_tiles.push_back(dt);
         B->ntiles.push_back(static_cast<int>(tiles.size()));
         B->tiles_total += static_cast<int64_t>(tiles.size());
+    }
+    // split members: per round and tile width, the leaf problems of every
+    // unsplit descendant (their own TMA descriptors and buffers) in one list
+    for (int r = 0; r < B->split_rounds && e == cudaSuccess; ++r) {
+        for (int tn : {256, 128}) {
+            std::vector<LeafProblem> probs;
+            std::vector<Tile> tiles;
+            for (int i = 0; i < count; ++i) {
+                hmv_plan_s *p = B->plans[i];
+                if (!B->split[i] || r >= p->nrhs) continue;
+                std::vector<hmv_plan_s *> leaves;
+                collect_leaf_plans(p, leaves);
+                for (hmv_plan_s *c : leaves) {
+                    if (c->tn != tn) continue;
+                    const int idx = static_cast<int>(probs.size());
+                    probs.push_back(c->hprob);
+                    for (Tile t : c->tiles) {
+                        t.prob = idx;
+                        tiles.push_back(t);
+                    }
+                    B->leaf_macs += c->leaf_macs;
+                }
+            }
+            if (tiles.empty()) continue;
+            hmv_batch_s::SplitLaunch sl{r, tn, static_cast<int>(tiles.size()), nullptr, nullptr};
+            e = balloc(B, reinterpret_cast<void **>(&sl.probs), probs.size() * sizeof(LeafProblem));
+            if (e == cudaSuccess)
+                e = cudaMemcpy(sl.probs, probs.data(), probs.size() * sizeof(LeafProblem), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = balloc(B, reinterpret_cast<void **>(&sl.tiles), tiles.size() * sizeof(Tile));
+            if (e == cudaSuccess)
+                e = cudaMemcpy(sl.tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice);
+            B->split_launches.push_back(sl);
+            B->tiles_total += static_cast<int64_t>(tiles.size());
+        }
     }
     if (e != cudaSuccess) {
         hmv_status st = (e == cudaErrorMemoryAllocation) ? HMV_ENOMEM : HMV_ECUDA;
@@ -354,8 +463,8 @@ hmv_status hmv_batch_get_info(const hmv_batch_t *B, hmv_batch_info *o) {
     if (!B || !o) return HMV_EINVAL;
     memset(o, 0, sizeof *o);
     o->matrices = static_cast<int32_t>(B->plans.size());
-    o->pairs = static_cast<int32_t>(B->pairs.size());
-    o->waves = B->nwaves;
+    for (const hmv_plan_s *p : B->plans) o->pairs += p->nrhs;
+    o->waves = B->nwaves + static_cast<int32_t>(B->split_launches.size());
     o->leaf_tiles = B->tiles_total;
     o->leaf_macs = B->leaf_macs;
     o->device_bytes = B->device_bytes;

@@ -127,6 +127,9 @@ cudaError_t leaf_tc_prepare();
 // the unsplit plans under p (p itself when it is not split)
 void collect_leaf_plans(hmv_plan_s *p, std::vector<hmv_plan_s *> &out);
 hmv_status split_plan_create(hmv_plan_s *p, const hmv_desc &d, int digit_levels);
+// HMV_AUTO's digit split for (n, b): 0 (none), Karatsuba levels 1-2, or 4 / 6
+// (Toom-K); fixed_tn = 0 lets the tile width vary with the split
+int choose_digit_split(int n, int b, int num_sms, int fixed_tn);
 hmv_status toom_plan_create(hmv_plan_s *p, const hmv_desc &d, int K);
 hmv_status split_load_matrix(hmv_plan_s *p, const uint32_t *h_limbs, const uint8_t *h_neg);
 cudaError_t split_vector_side(hmv_plan_s *p, const uint32_t *xl, const uint8_t *xn);

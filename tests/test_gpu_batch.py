@@ -81,3 +81,63 @@ def test_batch_against_oracle():
         yl, yn, e = oracle.round_rows(np.concatenate([z[0] for z in zs]), np.concatenate([z[1] for z in zs]),
                                       pr["b"], h.exponent + x.exponent)
         assert_same(y, FixedVec(yl, yn, pr["b"], e))
+
+
+# members the cost model splits (Toom-6 at b = 33220), members with explicit
+# digit-split flags, and unsplit members in one batch
+SPLIT_PROBLEMS = [dict(n=32, b=33220, nrhs=2), dict(n=45, b=5000, nrhs=1, flags=hmv.FLAG_DIGIT_TOOM4),
+                  dict(n=50, b=3000, nrhs=3, kind=hmv.TOEPLITZ, flags=hmv.FLAG_DIGIT_SPLIT1),
+                  dict(n=33, b=4096, nrhs=2), dict(n=20, b=700, nrhs=1, kind=hmv.CIRCULANT),
+                  dict(n=24, b=2000, nrhs=2, kind=hmv.CIRCULANT, flags=hmv.FLAG_DIGIT_TOOM6)]
+
+
+def split_inputs(seed):
+    hs, xs = [], []
+    for i, pr in enumerate(SPLIT_PROBLEMS):
+        kind = pr.get("kind", hmv.HANKEL)
+        hlen = pr["n"] if kind == hmv.CIRCULANT else 2 * pr["n"] - 1
+        hs.append(uniform_vec(seed + i, 0, hlen, pr["b"], i % 3))
+        xs.append(uniform_vec(seed + i, 1, pr["n"] * pr["nrhs"], pr["b"], -(i % 2)))
+    return hs, xs
+
+
+def single_flags(pr, h, x):
+    with hmv.Plan(pr["n"], pr["b"], kind=pr.get("kind", hmv.HANKEL), nrhs=pr["nrhs"], method=hmv.AUTO,
+                  flags=pr.get("flags", 0)) as p:
+        p.load_matrix(h)
+        return p.matvec(x), p.stats()
+
+
+def test_batch_with_digit_split_members():
+    """Split members run in rounds (one per right-hand side) with one leaf
+    launch per round and tile width; every result equals the member's own
+    single-plan product, over two graph replays, and the oracle's."""
+    hs, xs = split_inputs(970)
+    with hmv.Batch(SPLIT_PROBLEMS) as bt:
+        for i, h in enumerate(hs):
+            bt.load_matrix(i, h)
+        ys = bt.matvec(xs)
+        _, xs2 = split_inputs(971)
+        ys2 = bt.matvec(xs2)
+        info = bt.info()
+    assert info["pairs"] == sum(pr["nrhs"] for pr in SPLIT_PROBLEMS) and info["graph_launches"] == 2
+    unsplit_widths, split_rounds = set(), {}
+    for pr, h, x, y, x2, y2 in zip(SPLIT_PROBLEMS, hs, xs, ys, xs2, ys2):
+        y1, st = single_flags(pr, h, x)
+        assert_same(y, y1)
+        assert_same(y2, single_flags(pr, h, x2)[0])
+        if st["digit_products"] > 1:
+            for r in range(pr["nrhs"]):
+                split_rounds.setdefault(r, set()).add(st["leaf_tile_digits"])
+        else:
+            unsplit_widths.add(st["leaf_tile_digits"])
+    assert split_rounds, "the batch has split members"
+    assert info["waves"] == len(unsplit_widths) + sum(len(w) for w in split_rounds.values())
+    # the Toom-6 member against the oracle
+    pr, h, x, y = SPLIT_PROBLEMS[0], hs[0], xs[0], ys[0]
+    n, k = pr["n"], pr["nrhs"]
+    parts = [FixedVec(x.limbs[r * n:(r + 1) * n], x.neg[r * n:(r + 1) * n], x.b, x.exponent) for r in range(k)]
+    zs = [oracle.exact_rows(oracle.HANKEL, n, pr["b"], h, part, None, 8) for part in parts]
+    yl, yn, e = oracle.round_rows(np.concatenate([z[0] for z in zs]), np.concatenate([z[1] for z in zs]),
+                                  pr["b"], h.exponent + x.exponent)
+    assert_same(y, FixedVec(yl, yn, pr["b"], e))
