@@ -30,8 +30,10 @@ def run(n, b, h, x, flags=0, kind=hmv.HANKEL, method=hmv.KARATSUBA, levels=-1, n
 
 # sizes: one tile, several tiles with a ragged tail in both dimensions, the
 # narrowest digit counts (b = 1, 33) and digit counts just past a tile edge
+# (1, 64, 0): one j-step per tile, so the second MMA issuer has none;
+# (17, 64, 0): 17 j-steps, 2 windows of the first issuer against 1 of the second
 @pytest.mark.parametrize("n,b,levels", [(64, 2048, 1), (129, 1000, 2), (7, 33, 0), (30, 1, 0), (200, 520, 3),
-                                        (1, 64, 0), (45, 4100, 2), (300, 264, -1)])
+                                        (1, 64, 0), (17, 64, 0), (45, 4100, 2), (300, 264, -1)])
 def test_tile128_all_rows(n, b, levels):
     h = uniform_vec(80 + n, 0, 2 * n - 1, b, 2)
     x = uniform_vec(80 + n, 1, n, b, -3)
