@@ -670,8 +670,7 @@ hmv_status hmv_matvec(hmv_plan_t *p, const hmv_vec *x, hmv_vec *y) {
             if (p->xg) g(launch_leaf_tc(p));
             else g(launch_leaf_simt(p, p->a_leaf, x_leaf));
             timing_mark(p, 3);
-            g(launch_leaf_normalize(p, p->post[p->L % 2]));
-            for (int l = p->L - 1; l >= 0; --l) g(launch_postpass(p, l, p->post[(l + 1) % 2], p->post[l % 2]));
+            g(launch_post_group(&p, 1));  // leaf normalise and every post-pass level
             g(launch_final_normalize(p, p->post[0], r, p->post16 ? 2 : 4));
             timing_mark(p, 4);
         }

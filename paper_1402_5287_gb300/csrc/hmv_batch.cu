@@ -130,11 +130,9 @@ cudaError_t issue(hmv_batch_s *B) {
             if (pr.wave != w || e != cudaSuccess) continue;
             hmv_plan_s *p = B->plans[pr.plan];
             bind(B, p, pr);
-            e = launch_leaf_normalize(p, p->post[p->L % 2]);
-            for (int l = p->L - 1; l >= 0 && e == cudaSuccess; --l)
-                e = launch_postpass(p, l, p->post[(l + 1) % 2], p->post[l % 2]);
+            e = launch_post_group(&p, 1);  // leaf normalise and every post-pass level
             if (e == cudaSuccess) e = launch_final_normalize(p, p->post[0], pr.rhs, p->post16 ? 2 : 4);
-            kernels += 2 + p->L;
+            kernels += 1 + std::max(p->L, 1);
         }
     }
     // split members: a round per right-hand side
@@ -563,9 +561,7 @@ extern "C" hmv_status hmv_matvec_many(int32_t count, hmv_plan_t *const *plans, c
         if (!p->children.empty()) {
             e = split_post(p, 0);
         } else {
-            e = launch_leaf_normalize(p, p->post[p->L % 2]);
-            for (int l = p->L - 1; l >= 0 && e == cudaSuccess; --l)
-                e = launch_postpass(p, l, p->post[(l + 1) % 2], p->post[l % 2]);
+            e = launch_post_group(&p, 1);  // leaf normalise and every post-pass level
             if (e == cudaSuccess) e = launch_final_normalize(p, p->post[0], 0, p->post16 ? 2 : 4);
         }
         uint32_t *yl = ys[i].on_device ? ys[i].limbs : p->y_limbs_d;

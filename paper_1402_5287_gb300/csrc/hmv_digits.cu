@@ -390,6 +390,51 @@ __global__ void k_leaf_normalize(PlanPtrs g, const int *__restrict__ size, int M
     }
 }
 
+// The leaf normalise fused into the deepest post-pass level: output row i of
+// a level-(L-1) node is p_k -/+ (q_k or r_k), k = i / 2, each of the two leaf
+// rows read as its block digits plus its block carries spread as above, so
+// the carry-save leaf rows are never written out.  Digits of the result are
+// within [-638, 1020], as after the two separate kernels.  One block per
+// output row.
+template <class T>
+__global__ void k_leaf_post(PlanPtrs g, const int *__restrict__ parent_size, int MT, int Uo, int NUB, int rows_out,
+                            int Wo, int tn) {
+    const uint8_t *__restrict__ dig = static_cast<const uint8_t *>(g.in[blockIdx.y]);
+    const int32_t *__restrict__ carry = static_cast<const int32_t *>(g.in2[blockIdx.y]);
+    T *__restrict__ out = static_cast<T *>(g.out[blockIdx.y]);
+    const int nu = blockIdx.x / rows_out, i = blockIdx.x % rows_out;
+    if (i >= parent_size[nu]) return;
+    const int k = i >> 1;
+    const int other = (i & 1) ? 2 : 1;
+    const size_t ra = static_cast<size_t>(3 * nu) * MT * TM + k;
+    const size_t rb = static_cast<size_t>(3 * nu + other) * MT * TM + k;
+    const uint2 *da = reinterpret_cast<const uint2 *>(dig + ra * Uo);
+    const uint2 *db = reinterpret_cast<const uint2 *>(dig + rb * Uo);
+    const int32_t *ca = carry + ra * NUB, *cb = carry + rb * NUB;
+    T *o = out + (static_cast<size_t>(nu) * rows_out + i) * Wo;
+    const int sg = (i & 1) ? 1 : -1;
+    for (int g8 = threadIdx.x; g8 < Wo / 8; g8 += blockDim.x) {  // 8 digits per step; Uo, Wo multiples of 8
+        const int u0 = 8 * g8;
+        const uint2 wa = (u0 < Uo) ? da[g8] : make_uint2(0, 0);
+        const uint2 wb = (u0 < Uo) ? db[g8] : make_uint2(0, 0);
+        int v[8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            v[q] = static_cast<int>((wa.x >> (8 * q)) & 0xFF) + sg * static_cast<int>((wb.x >> (8 * q)) & 0xFF);
+            v[4 + q] = static_cast<int>((wa.y >> (8 * q)) & 0xFF) + sg * static_cast<int>((wb.y >> (8 * q)) & 0xFF);
+        }
+        if (u0 > 0 && u0 <= Uo && u0 % tn == 0) {
+            const int32_t a = ca[u0 / tn - 1], b = cb[u0 / tn - 1];
+            v[0] += (a & 0xFF) + sg * (b & 0xFF);
+            v[1] += ((a >> 8) & 0xFF) + sg * ((b >> 8) & 0xFF);
+            v[2] += ((a >> 16) & 0xFF) + sg * ((b >> 16) & 0xFF);
+            v[3] += (a >> 24) + sg * (b >> 24);  // arithmetic shifts: the signed top parts
+        }
+        store4<T>(o, 2 * g8, make_int4(v[0], v[1], v[2], v[3]));
+        store4<T>(o, 2 * g8 + 1, make_int4(v[4], v[5], v[6], v[7]));
+    }
+}
+
 // ------------------------------------------------------------------ post-pass
 // Algorithm 1, step 8 (0-based): y_{2k} = p_k - q_k, y_{2k+1} = p_k + r_k,
 // digit-wise without carries (digits grow by at most one bit per level).
@@ -707,6 +752,16 @@ cudaError_t leaf_normalize_group(hmv_plan_s *p, const PlanPtrs &g, int G) {
     p->launches_total++;
     return cudaGetLastError();
 }
+cudaError_t leaf_post_group(hmv_plan_s *p, const PlanPtrs &g, int G) {
+    const LevelGeom &pl = p->lv[p->L - 1];
+    const dim3 grid(static_cast<unsigned>(pl.nodes) * pl.rowsX, G);  // one block per output row
+    if (p->post16)
+        k_leaf_post<int16_t><<<grid, 128, 0, p->stream>>>(g, pl.d_size, p->MT, p->Uo, p->NUB, pl.rowsX, p->Wo, p->tn);
+    else
+        k_leaf_post<int32_t><<<grid, 128, 0, p->stream>>>(g, pl.d_size, p->MT, p->Uo, p->NUB, pl.rowsX, p->Wo, p->tn);
+    p->launches_total++;
+    return cudaGetLastError();
+}
 cudaError_t postpass_group(hmv_plan_s *p, const PlanPtrs &g, int G, int level) {
     const LevelGeom &pl = p->lv[level], &cl = p->lv[level + 1];
     const dim3 grid(static_cast<unsigned>(pl.nodes) * pl.rowsX, G);  // one block per output row
@@ -762,21 +817,6 @@ cudaError_t launch_leaf_simt(hmv_plan_s *p, const int8_t *a_leaf, const int8_t *
     return cudaGetLastError();
 }
 
-cudaError_t launch_leaf_normalize(hmv_plan_s *p, int32_t *out) {
-    PlanPtrs g{};
-    g.in[0] = p->leaf_dig;
-    g.in2[0] = p->leaf_carry;
-    g.out[0] = out;
-    return leaf_normalize_group(p, g, 1);
-}
-
-cudaError_t launch_postpass(hmv_plan_s *p, int level, const int32_t *in, int32_t *out) {
-    PlanPtrs g{};
-    g.in[0] = in;
-    g.out[0] = out;
-    return postpass_group(p, g, 1, level);
-}
-
 // The vector side (encode of each plan's staged x, every pre-pass level, the
 // shifted bf16 copies) and the post side (leaf normalise, every post-pass
 // level) of up to kMaxGroup plans with the same geometry, one launch per
@@ -812,13 +852,18 @@ cudaError_t launch_post_group(hmv_plan_s *const *ps, int G) {
     if (G < 1 || G > kMaxGroup) return cudaErrorInvalidValue;
     hmv_plan_s *p = ps[0];
     PlanPtrs g{};
+    // leaf normalise alone at depth 0, else fused into the deepest post-pass level
     for (int k = 0; k < G; ++k) {
         g.in[k] = ps[k]->leaf_dig;
         g.in2[k] = ps[k]->leaf_carry;
-        g.out[k] = ps[k]->post[p->L % 2];
+        g.out[k] = ps[k]->post[(p->L + 1) % 2];
     }
-    cudaError_t e = leaf_normalize_group(p, g, G);
-    for (int l = p->L - 1; l >= 0 && e == cudaSuccess; --l) {
+    if (p->L == 0) {
+        for (int k = 0; k < G; ++k) g.out[k] = ps[k]->post[0];
+        return leaf_normalize_group(p, g, G);
+    }
+    cudaError_t e = leaf_post_group(p, g, G);  // writes level L - 1 into post[(L - 1) % 2]
+    for (int l = p->L - 2; l >= 0 && e == cudaSuccess; --l) {
         for (int k = 0; k < G; ++k) {
             g.in[k] = ps[k]->post[(l + 1) % 2];
             g.out[k] = ps[k]->post[l % 2];

@@ -143,7 +143,6 @@ cudaError_t encode_tensor_map_A(hmv_plan_s *p, CUtensorMap *map);
 cudaError_t encode_tensor_map_B(hmv_plan_s *p, uint16_t *xg, CUtensorMap *map);
 void fill_leaf_problem(hmv_plan_s *p, LeafProblem &lp);
 cudaError_t launch_leaf_simt(hmv_plan_s *p, const int8_t *a_leaf, const int8_t *x_leaf);
-cudaError_t launch_leaf_normalize(hmv_plan_s *p, int32_t *out);
 // grouped launches for plans of one geometry (same_geometry): the vector side
 // from each plan's staged x to its bf16 copies, and leaf normalise plus the
 // post-pass down to each plan's level-0 rows
@@ -155,7 +154,6 @@ cudaError_t launch_colsum_round_cols(const __int128 *colsum, int n, int ncols, i
                                      uint8_t *yneg, cudaStream_t stream);
 cudaError_t launch_vector_side_group(hmv_plan_s *const *ps, int G);
 cudaError_t launch_post_group(hmv_plan_s *const *ps, int G);
-cudaError_t launch_postpass(hmv_plan_s *p, int level, const int32_t *in, int32_t *out);
 // digit_bytes: 2 (a plan's post buffers with post16), 4 or 8 (int64 Toom sums);
 // track_max: also fold the rows' bit lengths into the plan's maximum
 cudaError_t launch_final_normalize(hmv_plan_s *p, const int32_t *in, int rhs, int digit_bytes, bool track_max = true);

@@ -521,9 +521,7 @@ cudaError_t split_post(hmv_plan_s *p, int rhs) {
     } else {
         for (hmv_plan_s *c : leaves) {
             if (e != cudaSuccess) break;
-            e = launch_leaf_normalize(c, c->post[c->L % 2]);
-            for (int l = c->L - 1; l >= 0 && e == cudaSuccess; --l)
-                e = launch_postpass(c, l, c->post[(l + 1) % 2], c->post[l % 2]);
+            e = launch_post_group(&c, 1);  // leaf normalise and every post-pass level
         }
     }
     const int32_t *z = nullptr;
