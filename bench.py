@@ -317,6 +317,11 @@ def run_ours(args):
                      "issued_over_useful": st["leaf_macs_issued"] / st["leaf_macs"] if st["leaf_macs"] else None},
         "stage_ms": {"prepass": st["ms_prepass"] / max(st["matvecs"], 1), "leaf": leaf_ms,
                      "post": st["ms_post"] / max(st["matvecs"], 1), "round": st["ms_round"] / max(st["matvecs"], 1)},
+        # the plain definition's work (n^2 products of D = ceil(b/8)-digit numbers, D^2 digit
+        # multiply-adds each, x 2 flops) over the matvec time: exceeds the tensor peak because
+        # Algorithm 1 and the digit split do less work than the definition
+        "schoolbook_equivalent": {"tflops": 2.0 * n * n * ((b + 7) // 8) ** 2 / (secs_max / args.steps) / 1e12,
+                                  "unit": "TFLOP/s"},
         "gpu_launches": int(st["launches_total"]),
         "clocks": clocks.summary(),
         "e2e": e2e,
