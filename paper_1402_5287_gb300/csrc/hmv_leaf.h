@@ -35,7 +35,7 @@ struct Tile {
 // Everything the leaf kernel needs to know about one leaf problem (one
 // matrix tree with one right-hand side).  Lives in device memory; the TMA
 // descriptors are read from here by the kernel.
-struct __align__(64) LeafProblem {
+struct __align__(128) LeafProblem {  // CUtensorMap is 128-byte aligned
     CUtensorMap mapA;   // bf16 Hankel slabs of the matrix leaves
     CUtensorMap mapB;   // bf16 shifted copies of the vector leaves
     const int *size;    // leaf orders
