@@ -242,9 +242,12 @@ def run_ours(args):
     value = aggregate_rate(args.steps, world, secs_max)
 
     # roofline of the dominant kernel (leaf products): useful digit MACs x 2 per
-    # launch over its mean CUDA-event duration on the plan's stream
+    # launch over its mean CUDA-event duration (the library's events bracket the
+    # leaf launches of each matvec: one launch, or two back to back on the
+    # plan's two streams when a Toom plan runs its products in two halves)
+    launches_per_mv = st["launches_leaf"] / max(st["matvecs"], 1)
     leaf_ms = st["ms_leaf"] / max(st["launches_leaf"], 1)
-    flops_per_launch = 2.0 * st["leaf_macs"]
+    flops_per_launch = 2.0 * st["leaf_macs"] / max(launches_per_mv, 1)
     achieved_tflops = flops_per_launch / (leaf_ms / 1e3) / 1e12 if leaf_ms > 0 else 0.0
     peaks = {}
     try:
@@ -314,8 +317,9 @@ def run_ours(args):
                      "frac": achieved_tflops / peak if peak else None, "traffic": traffic,
                      "kernel": "k_leaf_tc", "peak_source": peak_src,
                      "flops_per_launch": flops_per_launch, "launch_ms": leaf_ms,
+                     "launches_per_matvec": launches_per_mv,
                      "issued_over_useful": st["leaf_macs_issued"] / st["leaf_macs"] if st["leaf_macs"] else None},
-        "stage_ms": {"prepass": st["ms_prepass"] / max(st["matvecs"], 1), "leaf": leaf_ms,
+        "stage_ms": {"prepass": st["ms_prepass"] / max(st["matvecs"], 1), "leaf": st["ms_leaf"] / max(st["matvecs"], 1),
                      "post": st["ms_post"] / max(st["matvecs"], 1), "round": st["ms_round"] / max(st["matvecs"], 1)},
         # the plain definition's work (n^2 products of D = ceil(b/8)-digit numbers, D^2 digit
         # multiply-adds each, x 2 flops) over the matvec time: exceeds the tensor peak because
