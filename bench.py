@@ -203,7 +203,7 @@ def run_ours(args):
 
     method = {"auto": hmv.AUTO, "karatsuba": hmv.KARATSUBA, "fft64": hmv.FFT64, "schoolbook": hmv.SCHOOLBOOK}[args.method]
     split_flag = {-1: 0, 0: 0, 1: hmv.FLAG_DIGIT_SPLIT1, 2: hmv.FLAG_DIGIT_SPLIT2, 4: hmv.FLAG_DIGIT_TOOM4,
-                  6: hmv.FLAG_DIGIT_TOOM6}[args.digit_split]
+                  6: hmv.FLAG_DIGIT_TOOM6, 8: hmv.FLAG_DIGIT_TOOM8}[args.digit_split]
     if args.digit_split == 0 and method == hmv.AUTO:
         method = hmv.KARATSUBA  # no digit split
     tile_flag = {128: hmv.FLAG_TILE128, 256: hmv.FLAG_TILE256}.get(args.tile, 0)
@@ -383,7 +383,7 @@ LEAF_SOURCES = ["paper_1402_5287_gb300/csrc/hmv_leaf_tc.cu", "paper_1402_5287_gb
 
 
 DIGIT_SPLIT_NAMES = {1: "none", 3: "karatsuba, one level", 9: "karatsuba, two levels", 7: "toom-4",
-                     11: "toom-6"}
+                     11: "toom-6", 15: "toom-8"}
 
 
 def leaf_sources_hash() -> str:
@@ -570,7 +570,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--levels", type=int, default=-1, help="Karatsuba depth (-1: cost model)")
-    ap.add_argument("--digit-split", type=int, choices=[-1, 0, 1, 2, 4, 6], default=-1,
+    ap.add_argument("--digit-split", type=int, choices=[-1, 0, 1, 2, 4, 6, 8], default=-1,
                     help="split of the mantissas on top of the index recursion: Karatsuba levels 1 or 2, "
                          "Toom-4 or Toom-6 (4, 6), none (0) or the cost model's choice (-1)")
     ap.add_argument("--method", choices=["auto", "karatsuba", "fft64", "schoolbook"], default="auto",

@@ -82,13 +82,17 @@ typedef enum {
 #define HMV_FLAG_TILE256 128u     /* leaf tiles of 256 product digits */
 /* Toom-Cook splitting of the mantissas instead: each mantissa cut into K
  * parts, 2K-1 products of about 1/K of the width, the exact rows recovered by
- * integer interpolation and one exact division (by 360 for K = 4, 1008000
- * for K = 6).  K = 4 evaluates at 0, 1, -1, 2, -2, 1/2 and infinity; K = 6
- * adds -1/2, 3, -3 and 1/3.  HMV_AUTO/HMV_KARATSUBA; at most one digit-split
- * flag.  Without one, HMV_AUTO picks the digit split (none, Karatsuba one or
- * two levels, Toom-4, Toom-6) by its cost model. */
+ * integer interpolation and an exact division (by 360 for K = 4, 1008000
+ * for K = 6, 54486432000 for K = 8).  K = 4 evaluates at 0, 1, -1, 2, -2,
+ * 1/2 and infinity; K = 6 adds -1/2, 3, -3 and 1/3; K = 8 adds -1/3, 3/2,
+ * -3/2 and 2/3.  HMV_AUTO/HMV_KARATSUBA; at most one digit-split flag.
+ * Without one, HMV_AUTO picks the digit split (none, Karatsuba one or two
+ * levels, Toom-4, Toom-6, Toom-8) by its cost model.  Toom-8 returns
+ * HMV_EUNSUPPORTED where its 64-bit interpolation sums could overflow (index
+ * depths above 7, n beyond about 30000). */
 #define HMV_FLAG_DIGIT_TOOM4 32u  /* needs b > 96 */
 #define HMV_FLAG_DIGIT_TOOM6 64u  /* needs b > 160 */
+#define HMV_FLAG_DIGIT_TOOM8 256u /* needs b > 224 */
 
 typedef struct {
     int32_t n;        /* matrix order, n >= 1 */

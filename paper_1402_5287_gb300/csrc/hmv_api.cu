@@ -147,7 +147,7 @@ int best_depth(int n, int b, int num_sms, double *cost, int tn = TN_DEFAULT) {
     return L;
 }
 
-// Digit split for HMV_AUTO: kToom4, kToom6 or the number of Karatsuba levels d (3^d
+// Digit split for HMV_AUTO: kToom4, kToom6, kToom8 or the number of Karatsuba levels d (3^d
 // products of about b/2^d bits, d <= 2), each product at its own best depth,
 // plus the level kernels, which scale with the products' total width (n*b
 // times 1, 3/2, 9/4 for d = 0, 1, 2 and 7/4 for Toom-4; measured 10.4, 15.2,
@@ -156,8 +156,14 @@ int best_depth(int n, int b, int num_sms, double *cost, int tn = TN_DEFAULT) {
 // scaled by (1 - 0.055 d): measured leaf times fall below the tile-count model
 // as the products narrow (Toom-K's products count as d = log2 K).  Each
 // scheme is costed at both leaf tile widths; *tn gets the cheaper one.
-constexpr int kToom4 = 4, kToom6 = 6;
-int auto_digit_scheme(int n, int b, int num_sms, int *tn, int fixed_tn) {
+// Toom-8 is left out where its products would need index depth > 7 (its
+// int64 interpolation sums are bounded for depths up to 7).
+constexpr int kToom4 = 4, kToom6 = 6, kToom8 = 8;
+inline bool is_toom(int dl) { return dl == kToom4 || dl == kToom6 || dl == kToom8; }
+inline int toom_grow(int K) { return K == 4 ? 4 : (K == 6 ? 9 : 13); }  // bits of |E_t| above s
+// only_scheme >= 0 restricts the choice to that scheme (a split the caller
+// fixed), leaving only the tile width to choose.
+int auto_digit_scheme(int n, int b, int num_sms, int *tn, int fixed_tn, int only_scheme = -1) {
     int best_d = 0;
     double best = 1e300;
     *tn = fixed_tn ? fixed_tn : TN_DEFAULT;
@@ -169,19 +175,20 @@ int auto_digit_scheme(int n, int b, int num_sms, int *tn, int fixed_tn) {
             double leaf = 0;
             best_depth(n, bd, num_sms, &leaf, w);
             const double t = mult * leaf * (1.0 - 0.055 * d) + 3.9e-11 * n * static_cast<double>(b) * std::pow(1.5, d);
-            if (t < best) { best = t; best_d = d; *tn = w; }
+            if (t < best && (only_scheme < 0 || only_scheme == d)) { best = t; best_d = d; *tn = w; }
             bd = 32 * (((bd + 31) / 32 + 1) / 2) + 1;  // the children's width
             mult *= 3.0;
         }
         // Toom-K: 2K-1 products of s + g bits; narrowing counted as d = log2 K
         const int L32 = (b + 31) / 32;
-        for (int K : {4, 6}) {
-            if (L32 < K) continue;
+        for (int K : {4, 6, 8}) {
+            if (L32 < K || (only_scheme >= 0 && only_scheme != K)) continue;
             double leaf = 0;
-            best_depth(n, 32 * ((L32 + K - 1) / K) + (K == 4 ? 4 : 9), num_sms, &leaf, w);
+            const int L = best_depth(n, 32 * ((L32 + K - 1) / K) + toom_grow(K), num_sms, &leaf, w);
+            if (K == 8 && L > 7 && only_scheme != K) continue;
             const double t = (2 * K - 1) * leaf * (1.0 - 0.055 * std::log2(static_cast<double>(K))) +
                              3.9e-11 * n * static_cast<double>(b) * (2.0 * K - 1) / K;
-            if (t < best) { best = t; best_d = (K == 4) ? kToom4 : kToom6; *tn = w; }
+            if (t < best) { best = t; best_d = K; *tn = w; }
         }
     }
     return best_d;
@@ -312,18 +319,21 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
     if (d.method < HMV_AUTO || d.method > HMV_FFT64) return HMV_EINVAL;
     if (d.levels < -1 || d.levels > kMaxLevels) return HMV_EINVAL;
     if (d.flags & ~(HMV_FLAG_TIMING | HMV_FLAG_SIMT_LEAF | HMV_FLAG_DIGIT_SPLIT1 | HMV_FLAG_DIGIT_SPLIT2 |
-                    HMV_FLAG_TILE128 | HMV_FLAG_TILE256 | HMV_FLAG_DIGIT_TOOM4 | HMV_FLAG_DIGIT_TOOM6))
+                    HMV_FLAG_TILE128 | HMV_FLAG_TILE256 | HMV_FLAG_DIGIT_TOOM4 | HMV_FLAG_DIGIT_TOOM6 |
+                    HMV_FLAG_DIGIT_TOOM8))
         return HMV_EINVAL;
     if ((d.flags & HMV_FLAG_TILE128) && (d.flags & HMV_FLAG_TILE256)) return HMV_EINVAL;
     const uint32_t split_flags =
-        d.flags & (HMV_FLAG_DIGIT_SPLIT1 | HMV_FLAG_DIGIT_SPLIT2 | HMV_FLAG_DIGIT_TOOM4 | HMV_FLAG_DIGIT_TOOM6);
+        d.flags & (HMV_FLAG_DIGIT_SPLIT1 | HMV_FLAG_DIGIT_SPLIT2 | HMV_FLAG_DIGIT_TOOM4 | HMV_FLAG_DIGIT_TOOM6 |
+                   HMV_FLAG_DIGIT_TOOM8);
     if (split_flags & (split_flags - 1)) return HMV_EINVAL;  // at most one digit split
     int digit_levels = (d.flags & HMV_FLAG_DIGIT_SPLIT2) ? 2 : ((d.flags & HMV_FLAG_DIGIT_SPLIT1) ? 1 : 0);
     if (d.flags & HMV_FLAG_DIGIT_TOOM4) digit_levels = kToom4;
     if (d.flags & HMV_FLAG_DIGIT_TOOM6) digit_levels = kToom6;
+    if (d.flags & HMV_FLAG_DIGIT_TOOM8) digit_levels = kToom8;
     if (digit_levels && ((d.method != HMV_AUTO && d.method != HMV_KARATSUBA) || (d.flags & HMV_FLAG_SIMT_LEAF)))
         return HMV_EINVAL;
-    if ((digit_levels == kToom4 || digit_levels == kToom6) && (d.b + 31) / 32 < digit_levels)
+    if (is_toom(digit_levels) && (d.b + 31) / 32 < digit_levels)
         return HMV_EINVAL;  // K parts of at least one limb
     if (d.method == HMV_FFT64 ? (d.piece_bits != 0 && (d.piece_bits < 4 || d.piece_bits > 16)) : d.piece_bits != 0)
         return HMV_EINVAL;
@@ -363,15 +373,16 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
     Guard g;
     const int n = d.n;
     int dl = digit_levels;
-    if (dl == 0 && d.method == HMV_AUTO && d.levels < 0 && !(d.flags & HMV_FLAG_SIMT_LEAF) && !external_scratch) {
+    if (d.method == HMV_AUTO && d.levels < 0 && !(d.flags & HMV_FLAG_SIMT_LEAF) && !external_scratch) {
         const bool fixed = (d.flags & (HMV_FLAG_TILE128 | HMV_FLAG_TILE256)) != 0;
         int tn = TN_DEFAULT;
-        dl = auto_digit_scheme(n, d.b, p->num_sms, &tn, fixed ? p->tn : 0);
+        // the split by the cost model, or the caller's split with the cost model's tile width
+        dl = auto_digit_scheme(n, d.b, p->num_sms, &tn, fixed ? p->tn : 0, dl == 0 ? -1 : dl);
         // a split plan's products take the scheme's tile width
         if (dl != 0) p->tn = tn;
     }
     digit_levels = dl;
-    const bool toom = digit_levels == kToom4 || digit_levels == kToom6;
+    const bool toom = is_toom(digit_levels);
     p->digit_levels = toom ? 0 : digit_levels;
     if (digit_levels && !external_scratch) {
         hmv_status st = toom ? toom_plan_create(p, d, digit_levels) : split_plan_create(p, d, digit_levels);
@@ -384,8 +395,8 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
             const int P = static_cast<int>(p->children.size());
             g(dalloc(p, &p->toom_ptrs, 2 * P));
             g(dalloc(p, &p->toom_neg_ptrs, 2 * P));
-            uint32_t *tl[22];
-            uint8_t *tn[22];
+            uint32_t *tl[30];
+            uint8_t *tn[30];
             for (int t = 0; t < P; ++t) {
                 tl[t] = p->children[t]->h_limbs_d;
                 tn[t] = p->children[t]->h_neg_d;

@@ -225,7 +225,7 @@ hmv_status hmv_batch_create(int32_t count, const hmv_desc *descs, void *stream, 
         return HMV_ECUDA;
     }
     const uint32_t kSplitFlags =
-        HMV_FLAG_DIGIT_SPLIT1 | HMV_FLAG_DIGIT_SPLIT2 | HMV_FLAG_DIGIT_TOOM4 | HMV_FLAG_DIGIT_TOOM6;
+        HMV_FLAG_DIGIT_SPLIT1 | HMV_FLAG_DIGIT_SPLIT2 | HMV_FLAG_DIGIT_TOOM4 | HMV_FLAG_DIGIT_TOOM6 | HMV_FLAG_DIGIT_TOOM8;
     for (int i = 0; i < count; ++i) {
         hmv_desc d = descs[i];
         d.flags &= ~HMV_FLAG_TIMING;  // no host-side event syncs inside a graph

@@ -21,7 +21,7 @@ constexpr int kThreads = 256;
 // Per-plan buffers of a group of plans with the same geometry (the products
 // of a digit split), one launch for all of them: blockIdx.y (z for
 // pack_vector) selects the plan.  A single plan is a group of one.
-constexpr int kMaxGroup = 12;
+constexpr int kMaxGroup = 16;  // plans per grouped launch (the 15 Toom-8 products)
 struct PlanPtrs {
     const void *in[kMaxGroup];
     const void *in2[kMaxGroup];

@@ -15,6 +15,7 @@
 // digit shifts (s is a multiple of 32 bits), then normalised and rounded
 // once, exactly like an unsplit plan.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 
 #include "hmv_internal.h"
@@ -84,6 +85,10 @@ __global__ void k_combine(const int32_t *__restrict__ z00, const int32_t *__rest
 //   K = 4: points 0, 1, -1, 2, -2, 1/2, inf; Den = 360; |E| < 15 * 2^s.
 //   K = 6: points 0, 1, -1, 2, -2, 1/2, -1/2, 3, -3, 1/3, inf; Den = 1008000;
 //          |E| < 364 * 2^s.
+//   K = 8: points 0, 1, -1, 2, -2, 1/2, -1/2, 3, -3, 1/3, -1/3, 3/2, -3/2,
+//          2/3, inf (the set with the smallest interpolation constants among
+//          those tried); Den = 54486432000 = 7776000 * 7007, |N| < 2^44;
+//          |E| < 6305 * 2^s.
 __constant__ int16_t kToom4Eval[7][4] = {{1, 0, 0, 0}, {1, 1, 1, 1},   {1, -1, 1, -1}, {1, 2, 4, 8},
                                          {1, -2, 4, -8}, {8, 4, 2, 1}, {0, 0, 0, 1}};
 __constant__ int32_t kToom4Interp[7][7] = {{360, 0, 0, 0, 0, 0, 0},
@@ -109,21 +114,61 @@ __constant__ int32_t kToom6Interp[11][11] = {
     {112000, 28000, 28000, -2240, -2240, -80, -80, 160, 160, 0, -14364000},
     {-336000, 42000, -21000, -1344, 960, -480, 96, 60, -48, 12, -336000},
     {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1008000}};
+__constant__ int16_t kToom8Eval[15][8] = {{1, 0, 0, 0, 0, 0, 0, 0},
+{1, 1, 1, 1, 1, 1, 1, 1},
+{1, -1, 1, -1, 1, -1, 1, -1},
+{1, 2, 4, 8, 16, 32, 64, 128},
+{1, -2, 4, -8, 16, -32, 64, -128},
+{128, 64, 32, 16, 8, 4, 2, 1},
+{128, -64, 32, -16, 8, -4, 2, -1},
+{1, 3, 9, 27, 81, 243, 729, 2187},
+{1, -3, 9, -27, 81, -243, 729, -2187},
+{2187, 729, 243, 81, 27, 9, 3, 1},
+{2187, -729, 243, -81, 27, -9, 3, -1},
+{128, 192, 288, 432, 648, 972, 1458, 2187},
+{128, -192, 288, -432, 648, -972, 1458, -2187},
+{2187, 1458, 972, 648, 432, 288, 192, 128},
+{0, 0, 0, 0, 0, 0, 0, 1}};
+#define HMV_TOOM8_INTERP {{54486432000LL, 0LL, 0LL, 0LL, 0LL, 0LL, 0LL, 0LL, 0LL, 0LL, 0LL, 0LL, 0LL, 0LL, 0LL},\
+{-81729648000LL, -6129723600LL, -1225944720LL, -10007712LL, -5003856LL, -17513496LL, 2501928LL, 30888LL, 19656LL, 75816LL, -25272LL, 14040LL, 5400LL, 19440LL, -81729648000LL},\
+{-806701896000LL, 3064861800LL, 3064861800LL, 10007712LL, 10007712LL, -8756748LL, -8756748LL, -36036LL, -36036LL, 113724LL, 113724LL, -11700LL, -11700LL, 0LL, 122594472000LL},\
+{1210052844000LL, 93818825100LL, 15085930860LL, 153173592LL, 69081012LL, 241783542LL, -19528938LL, -469326LL, -279006LL, -781326LL, 32994LL, -215670LL, -72150LL, -287820LL, 1210052844000LL},\
+{3294579288000LL, -42312119850LL, -42312119850LL, -145667808LL, -145667808LL, 94621527LL, 94621527LL, 529529LL, 529529LL, -660231LL, -660231LL, 168025LL, 168025LL, 0LL, -1815079266000LL},\
+{-4941868932000LL, -412952289750LL, -31815914130LL, -677960712LL, -229729500LL, -869728860LL, -37961352LL, 2044185LL, 1012011LL, 2603601LL, 452595LL, 960960LL, 214500LL, 1175460LL, -4941868932000LL},\
+{-4256500248000LL, 143007965100LL, 143007965100LL, 568709856LL, 568709856LL, -150999849LL, -150999849LL, -2120118LL, -2120118LL, 934362LL, 934362LL, -632775LL, -632775LL, 0LL, 7412803398000LL},\
+{6384750372000LL, 621864243000LL, -47236709520LL, 1066161096LL, 106548156LL, 1066161096LL, 106548156LL, -3119688LL, -828828LL, -3119688LL, -828828LL, -1518660LL, 0LL, -1518660LL, 6384750372000LL},\
+{2092178088000LL, -96420173850LL, -96420173850LL, -639628704LL, -639628704LL, 80081001LL, 80081001LL, 2579577LL, 2579577LL, -474903LL, -474903LL, 632775LL, 632775LL, 0LL, -9577125558000LL},\
+{-3138267132000LL, -331790208750LL, 49346166870LL, -704091960LL, 127675548LL, -512323812LL, -64092600LL, 2045901LL, -105105LL, 1486485LL, 454311LL, 960960LL, -214500LL, 746460LL, -3138267132000LL},\
+{-402257856000LL, 21264843600LL, 21264843600LL, 224370432LL, 224370432LL, -15918903LL, -15918903LL, -1097096LL, -1097096LL, 92664LL, 92664LL, -168025LL, -168025LL, 0LL, 4707400698000LL},\
+{603386784000LL, 66518852400LL, -12214041840LL, 186069312LL, -75243168LL, 97459362LL, 13366782LL, -593736LL, 220584LL, -281736LL, -91416LL, -215670LL, 72150LL, -143520LL, 603386784000LL},\
+{24216192000LL, -1362160800LL, -1362160800LL, -17791488LL, -17791488LL, 972972LL, 972972LL, 144144LL, 144144LL, -5616LL, -5616LL, 11700LL, 11700LL, 0LL, -905080176000LL},\
+{-36324288000LL, -4086482400LL, 817296480LL, -13343616LL, 6671808LL, -5837832LL, -833976LL, 61776LL, -39312LL, 16848LL, 5616LL, 14040LL, -5400LL, 8640LL, -36324288000LL},\
+{0LL, 0LL, 0LL, 0LL, 0LL, 0LL, 0LL, 0LL, 0LL, 0LL, 0LL, 0LL, 0LL, 0LL, 54486432000LL}}
+__constant__ long long kToom8Interp[15][15] = HMV_TOOM8_INTERP;
+constexpr long long kToom8InterpHost[15][15] = HMV_TOOM8_INTERP;  // for the plan-time overflow bound
+#undef HMV_TOOM8_INTERP
 template <int K>
 struct Toom;
 template <>
 struct Toom<4> {
     static constexpr int P = 7;
-    static constexpr uint64_t Den = 360;
+    static constexpr uint64_t Den1 = 360, Den2 = 1;  // Den = Den1 Den2, divided in that order
     __device__ static int eval(int t, int k) { return kToom4Eval[t][k]; }
-    __device__ static int interp(int m, int t) { return kToom4Interp[m][t]; }
+    __device__ static long long interp(int m, int t) { return kToom4Interp[m][t]; }
 };
 template <>
 struct Toom<6> {
     static constexpr int P = 11;
-    static constexpr uint64_t Den = 1008000;
+    static constexpr uint64_t Den1 = 1008000, Den2 = 1;
     __device__ static int eval(int t, int k) { return kToom6Eval[t][k]; }
-    __device__ static int interp(int m, int t) { return kToom6Interp[m][t]; }
+    __device__ static long long interp(int m, int t) { return kToom6Interp[m][t]; }
+};
+template <>
+struct Toom<8> {
+    static constexpr int P = 15;
+    static constexpr uint64_t Den1 = 7776000, Den2 = 7007;
+    __device__ static int eval(int t, int k) { return kToom8Eval[t][k]; }
+    __device__ static long long interp(int m, int t) { return kToom8Interp[m][t]; }
 };
 
 // Sign-magnitude rows (L32 limbs) -> the children's rows (Lc limbs): child t
@@ -182,7 +227,7 @@ __device__ __forceinline__ int4 child4(const int32_t *z, bool is16, size_t row, 
     return *reinterpret_cast<const int4 *>(z + row * Wc + v);
 }
 struct ToomChildren {
-    const int32_t *z[11];
+    const int32_t *z[15];
 };
 // One block per row: the row's children windows are re-read by the shifted
 // terms while they are still in L1/L2.
@@ -199,13 +244,14 @@ __global__ void k_toom_combine(ToomChildren ch, int in16_mask, int Wc, int ds, i
             if (v >= Wc) continue;
 #pragma unroll
             for (int t = 0; t < P; ++t) {
-                const int c = Toom<K>::interp(mm, t);  // |c| < 2^31, |d| < 2^31: 32 x 32 -> 64-bit products
+                // |c| < 2^44, |d| <= 510 * 2^L: toom_plan_create checks that the sums stay below 2^62
+                const long long c = Toom<K>::interp(mm, t);
                 if (c == 0) continue;
                 const int4 d = child4(ch.z[t], (in16_mask >> t) & 1, i, Wc, v);
-                a0 += static_cast<long long>(c) * d.x;
-                a1 += static_cast<long long>(c) * d.y;
-                a2 += static_cast<long long>(c) * d.z;
-                a3 += static_cast<long long>(c) * d.w;
+                a0 += c * d.x;
+                a1 += c * d.y;
+                a2 += c * d.z;
+                a3 += c * d.w;
             }
         }
         int64_t *o = out + static_cast<size_t>(i) * Wp + u;
@@ -214,16 +260,17 @@ __global__ void k_toom_combine(ToomChildren ch, int in16_mask, int Wc, int ds, i
     }
 }
 
-// |Den Z| limbs -> |Z| limbs (exact: a nonzero remainder is an internal
-// error), with the bit length and the maximum over rows.  One warp per row.
+// |Den Z| limbs -> |Z Den / Den'| limbs for one factor Den' < 2^24 of Den
+// (exact: a nonzero remainder is an internal error); with kBits (the last
+// factor) also the bit length and the maximum over rows.  One warp per row.
 // Long division from the top limb carries the remainder r -> (r 2^32 + z_w)
 // mod Den, an affine map of r modulo Den; each lane composes the maps of its
 // segment of limbs, a warp scan composes the segments, and then every lane
 // divides its own segment starting from the remainder that enters it.
-template <int K>
+template <uint64_t Den, bool kBits>
 __global__ void __launch_bounds__(256) k_div_exact(uint32_t *__restrict__ zmag, int32_t *__restrict__ zbits, int n,
                                                    int ZW, int32_t *dstat, int row_offset) {
-    constexpr uint64_t Den = Toom<K>::Den;
+    static_assert(Den > 1 && Den < (1ull << 24), "r 2^32 + z must fit 64 bits");
     constexpr uint64_t K32 = (uint64_t(1) << 32) % Den;
     const int lane = threadIdx.x & 31;
     const int i = static_cast<int>((static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
@@ -250,13 +297,14 @@ __global__ void __launch_bounds__(256) k_div_exact(uint32_t *__restrict__ zmag, 
     if (lane == 0) r = 0;
     int bits = 0;
     for (int w = hi - 1; w >= lo; --w) {
-        const uint64_t cur = (r << 32) | z[w];  // r < Den < 2^20: no overflow
+        const uint64_t cur = (r << 32) | z[w];  // r < Den < 2^24: no overflow
         const uint64_t q = cur / Den;
         r = cur - q * Den;
         z[w] = static_cast<uint32_t>(q);
         if (bits == 0 && q != 0) bits = 32 * w + (32 - __clz(static_cast<uint32_t>(q)));
     }
     if (lane == 31 && r != 0) atomicExch(dstat, DEV_OVERFLOW);  // the lowest segment ends the division
+    if (!kBits) return;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) bits = max(bits, __shfl_xor_sync(0xffffffffu, bits, off));
     if (lane == 0) {
@@ -274,12 +322,13 @@ cudaError_t split_down(hmv_plan_s *p, const uint32_t *limbs, const uint8_t *neg,
         uint32_t *const *ddst = p->toom_ptrs + (matrix ? 0 : P);  // the same rows, uploaded at plan creation
         uint8_t *const *dn = p->toom_neg_ptrs + (matrix ? 0 : P);
         const unsigned blocks = static_cast<unsigned>((static_cast<long long>(rows) * P + 127) / 128);
+        const int sl = p->split_bits / 32, Lc = p->children[0]->L32;
         if (p->toom == 4)
-            k_toom_split<4><<<blocks, 128, 0, p->stream>>>(limbs, neg, rows, p->L32, p->split_bits / 32,
-                                                           p->children[0]->L32, ddst, dn);
+            k_toom_split<4><<<blocks, 128, 0, p->stream>>>(limbs, neg, rows, p->L32, sl, Lc, ddst, dn);
+        else if (p->toom == 6)
+            k_toom_split<6><<<blocks, 128, 0, p->stream>>>(limbs, neg, rows, p->L32, sl, Lc, ddst, dn);
         else
-            k_toom_split<6><<<blocks, 128, 0, p->stream>>>(limbs, neg, rows, p->L32, p->split_bits / 32,
-                                                           p->children[0]->L32, ddst, dn);
+            k_toom_split<8><<<blocks, 128, 0, p->stream>>>(limbs, neg, rows, p->L32, sl, Lc, ddst, dn);
         p->launches_total++;
         return cudaGetLastError();
     }
@@ -320,10 +369,13 @@ cudaError_t combine_up(hmv_plan_s *p, const int32_t **out, int *width, int *digi
             wc = c->Wo;
         }
         const unsigned grid = static_cast<unsigned>(p->n);  // one block per row
+        const int ds = p->split_bits / 8;
         if (p->toom == 4)
-            k_toom_combine<4><<<grid, 256, 0, p->stream>>>(ch, mask, wc, p->split_bits / 8, p->combined64, p->Wo);
+            k_toom_combine<4><<<grid, 256, 0, p->stream>>>(ch, mask, wc, ds, p->combined64, p->Wo);
+        else if (p->toom == 6)
+            k_toom_combine<6><<<grid, 256, 0, p->stream>>>(ch, mask, wc, ds, p->combined64, p->Wo);
         else
-            k_toom_combine<6><<<grid, 256, 0, p->stream>>>(ch, mask, wc, p->split_bits / 8, p->combined64, p->Wo);
+            k_toom_combine<8><<<grid, 256, 0, p->stream>>>(ch, mask, wc, ds, p->combined64, p->Wo);
         p->launches_total++;
         *out = reinterpret_cast<const int32_t *>(p->combined64);
         *width = p->Wo;
@@ -395,10 +447,10 @@ hmv_status split_plan_create(hmv_plan_s *p, const hmv_desc &d, int digit_levels)
 }
 
 // 2K-1 unsplit children of s + g bits (|E_t| < 15 * 2^s for K = 4, 364 * 2^s
-// for K = 6), s = the limb boundary nearest above b/K.
+// for K = 6, 6305 * 2^s for K = 8), s = the limb boundary nearest above b/K.
 hmv_status toom_plan_create(hmv_plan_s *p, const hmv_desc &d, int K) {
     p->toom = K;
-    const int P = 2 * K - 1, grow = (K == 4) ? 4 : 9;
+    const int P = 2 * K - 1, grow = (K == 4) ? 4 : ((K == 6) ? 9 : 13);
     p->split_bits = 32 * ((p->L32 + K - 1) / K);
     for (int t = 0; t < P; ++t) {
         hmv_desc cd = d;
@@ -407,7 +459,7 @@ hmv_status toom_plan_create(hmv_plan_s *p, const hmv_desc &d, int K) {
         cd.kind = HMV_HANKEL;  // the parent maps the kind onto the Hankel sequence
         cd.method = HMV_KARATSUBA;
         cd.flags &= ~(HMV_FLAG_TIMING | HMV_FLAG_DIGIT_SPLIT1 | HMV_FLAG_DIGIT_SPLIT2 | HMV_FLAG_DIGIT_TOOM4 |
-                      HMV_FLAG_DIGIT_TOOM6);
+                      HMV_FLAG_DIGIT_TOOM6 | HMV_FLAG_DIGIT_TOOM8 | HMV_FLAG_TILE256);
         if (p->tn == 128) cd.flags |= HMV_FLAG_TILE128;
         cd.levels = -1;
         hmv_plan_s *c = nullptr;
@@ -415,6 +467,19 @@ hmv_status toom_plan_create(hmv_plan_s *p, const hmv_desc &d, int K) {
         if (st != HMV_OK) return st;
         p->children.push_back(c);
         p->device_bytes += c->device_bytes;
+    }
+    if (K == 8) {
+        // the int64 interpolation sums: at most ceil(Wc / ds) shifted products
+        // meet at a digit, each sum_t |N[m][t]| |d| with |d| <= 510 * 2^L
+        const hmv_plan_s *c = p->children[0];
+        double rowsum = 0;
+        for (const auto &row : kToom8InterpHost) {
+            double r = 0;
+            for (long long v : row) r += std::fabs(static_cast<double>(v));
+            rowsum = std::max(rowsum, r);
+        }
+        const double overlap = std::ceil(static_cast<double>(c->Wo) / (p->split_bits / 8)) + 1;
+        if (overlap * rowsum * 510.0 * std::ldexp(1.0, c->L) >= std::ldexp(1.0, 62)) return HMV_EUNSUPPORTED;
     }
     // Den Z spans the 2K-2 shifted products plus one child row and the factor Den
     p->Wo = (2 * K - 2) * (p->split_bits / 8) + p->children[0]->Wo + 4;
@@ -530,10 +595,16 @@ cudaError_t split_post(hmv_plan_s *p, int rhs) {
     if (e == cudaSuccess) e = launch_final_normalize(p, z, rhs, zb, p->toom == 0);
     if (e == cudaSuccess && p->toom) {  // the rows are Den Z: divide, then take the bit lengths
         const unsigned blocks = static_cast<unsigned>((p->n + 7) / 8);  // a warp per row
-        if (p->toom == 4)
-            k_div_exact<4><<<blocks, 256, 0, p->stream>>>(p->zmag, p->zbits, p->n, p->ZW, p->dstat, rhs * p->n);
-        else
-            k_div_exact<6><<<blocks, 256, 0, p->stream>>>(p->zmag, p->zbits, p->n, p->ZW, p->dstat, rhs * p->n);
+        const int ro = rhs * p->n;
+        if (p->toom == 4) {
+            k_div_exact<Toom<4>::Den1, true><<<blocks, 256, 0, p->stream>>>(p->zmag, p->zbits, p->n, p->ZW, p->dstat, ro);
+        } else if (p->toom == 6) {
+            k_div_exact<Toom<6>::Den1, true><<<blocks, 256, 0, p->stream>>>(p->zmag, p->zbits, p->n, p->ZW, p->dstat, ro);
+        } else {
+            k_div_exact<Toom<8>::Den1, false><<<blocks, 256, 0, p->stream>>>(p->zmag, p->zbits, p->n, p->ZW, p->dstat, ro);
+            k_div_exact<Toom<8>::Den2, true><<<blocks, 256, 0, p->stream>>>(p->zmag, p->zbits, p->n, p->ZW, p->dstat, ro);
+            p->launches_total++;
+        }
         p->launches_total++;
         e = cudaGetLastError();
     }

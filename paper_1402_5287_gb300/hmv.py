@@ -15,7 +15,7 @@ from .inputs import FixedVec
 HANKEL, TOEPLITZ, CIRCULANT = 0, 1, 2
 AUTO, SCHOOLBOOK, KARATSUBA, FFT64 = 0, 1, 2, 3
 FLAG_TIMING, FLAG_SIMT_LEAF, FLAG_DIGIT_SPLIT1, FLAG_DIGIT_SPLIT2, FLAG_TILE128 = 1, 2, 4, 8, 16
-FLAG_DIGIT_TOOM4, FLAG_DIGIT_TOOM6 = 32, 64
+FLAG_DIGIT_TOOM4, FLAG_DIGIT_TOOM6, FLAG_DIGIT_TOOM8 = 32, 64, 256
 FLAG_TILE256 = 128
 STATUS = {0: "HMV_OK", 1: "HMV_EINVAL", 2: "HMV_ENOMEM", 3: "HMV_ECUDA", 4: "HMV_ETIMEOUT",
           5: "HMV_ENOTLOADED", 6: "HMV_EFFTBOUND", 7: "HMV_EUNSUPPORTED"}

@@ -63,7 +63,10 @@ def test_plan_rejects_bad_descriptors_without_gpu(lib, field, value):
                                            (4096, hmv.FLAG_DIGIT_TOOM4 | hmv.FLAG_SIMT_LEAF, 0),
                                            (4096, hmv.FLAG_DIGIT_TOOM6 | hmv.FLAG_SIMT_LEAF, 0),
                                            (4096, hmv.FLAG_DIGIT_TOOM4, 3), (4096, hmv.FLAG_DIGIT_TOOM4, 1),
-                                           (4096, hmv.FLAG_DIGIT_TOOM6, 3)])
+                                           (4096, hmv.FLAG_DIGIT_TOOM6, 3), (224, hmv.FLAG_DIGIT_TOOM8, 0),
+                                           (4096, hmv.FLAG_DIGIT_TOOM8 | hmv.FLAG_DIGIT_TOOM6, 0),
+                                           (4096, hmv.FLAG_DIGIT_TOOM8 | hmv.FLAG_SIMT_LEAF, 0),
+                                           (4096, hmv.FLAG_DIGIT_TOOM8, 3)])
 def test_toom_rejects_bad_combinations_without_gpu(lib, b, flags, method):
     """Toom-K needs K parts of at least one limb, the integer tensor-core path
     and no second digit split."""

@@ -75,7 +75,7 @@ def test_tile128_worst_case_digits():
 
 
 @pytest.mark.parametrize("split", [hmv.FLAG_DIGIT_SPLIT1, hmv.FLAG_DIGIT_SPLIT2, hmv.FLAG_DIGIT_TOOM4,
-                                   hmv.FLAG_DIGIT_TOOM6])
+                                   hmv.FLAG_DIGIT_TOOM6, hmv.FLAG_DIGIT_TOOM8])
 def test_tile128_under_digit_split(split):
     n, b = 100, 4100
     h = uniform_vec(95, 0, 2 * n - 1, b, 1)
@@ -149,9 +149,13 @@ def test_auto_chooses_tile_width_and_stays_exact(n, b, levels, want):
     assert_same(y, oracle_matvec(oracle.HANKEL, n, h, x))
 
 
-def test_auto_benchmark_size_takes_toom6_on_128_wide_tiles():
-    """At n = 8000, b = 33220 the cost model picks Toom-6 on 128-wide tiles."""
+def test_auto_benchmark_size_takes_toom8_on_128_wide_tiles():
+    """At n = 8000, b = 33220 the cost model picks Toom-8 on 128-wide tiles; a
+    caller-fixed split still gets the cost model's tile width."""
     n, b = 8000, 33220
     with hmv.Plan(n, b, method=hmv.AUTO) as p:
+        st = p.stats()
+    assert st["digit_products"] == 15 and st["leaf_tile_digits"] == 128
+    with hmv.Plan(n, b, method=hmv.AUTO, flags=hmv.FLAG_DIGIT_TOOM6) as p:
         st = p.stats()
     assert st["digit_products"] == 11 and st["leaf_tile_digits"] == 128

@@ -14,7 +14,7 @@ from test_gpu_parity import assert_same, oracle_matvec, sampled_parity
 pytestmark = pytest.mark.gpu
 
 T4 = hmv.FLAG_DIGIT_TOOM4
-TOOMS = [(hmv.FLAG_DIGIT_TOOM4, 7), (hmv.FLAG_DIGIT_TOOM6, 11)]
+TOOMS = [(hmv.FLAG_DIGIT_TOOM4, 7), (hmv.FLAG_DIGIT_TOOM6, 11), (hmv.FLAG_DIGIT_TOOM8, 15)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -31,10 +31,16 @@ def run(n, b, h, x, flags=T4, kind=hmv.HANKEL, nrhs=1, method=hmv.AUTO):
 
 # b: the narrowest splits (one-limb parts), ragged top parts, several tiles
 @pytest.mark.parametrize("flags,products", TOOMS)
-@pytest.mark.parametrize("n,b", [(64, 2048), (100, 700), (1, 192), (7, 257), (30, 4100), (140, 1000), (3, 193)])
+@pytest.mark.parametrize("n,b", [(64, 2048), (100, 700), (1, 192), (7, 257), (30, 4100), (140, 1000), (3, 193),
+                                 (5, 225), (2, 300)])
 def test_toom_all_rows(flags, products, n, b):
     h = uniform_vec(70 + n, 0, 2 * n - 1, b, 1)
     x = uniform_vec(70 + n, 1, n, b, -1)
+    K = (products + 1) // 2
+    if (b + 31) // 32 < K:  # fewer limbs than parts: refused
+        with pytest.raises(hmv.HmvError):
+            run(n, b, h, x, flags=flags)
+        return
     y, st = run(n, b, h, x, flags=flags)
     assert st["digit_products"] == products
     assert_same(y, oracle_matvec(oracle.HANKEL, n, h, x))

@@ -1,4 +1,4 @@
-"""Toom-Cook splits of the mantissas (HMV_FLAG_DIGIT_TOOM4/6), on the CPU.
+"""Toom-Cook splits of the mantissas (HMV_FLAG_DIGIT_TOOM4/6/8), on the CPU.
 
 The exact rows are bilinear in (h, x), so with every mantissa cut into K
 parts V = sum_k V_k 2^(ks) the rows are a polynomial of degree 2K-2 in
@@ -8,6 +8,7 @@ two).  2K-1 products at the chosen points (fractions homogenised, plus
 infinity) fix the C_m.  These tests derive the interpolation here, by exact
 elimination over the rationals, and check the whole scheme against the
 oracle's direct products, independently of the CUDA tables."""
+import math
 from fractions import Fraction
 
 import numpy as np
@@ -18,9 +19,11 @@ from paper_1402_5287_gb300.inputs import FixedVec, uniform_vec
 
 # (num, den): t = num/den, (1, 0) = infinity
 POINTS = {4: [(0, 1), (1, 1), (-1, 1), (2, 1), (-2, 1), (1, 2), (1, 0)],
-          6: [(0, 1), (1, 1), (-1, 1), (2, 1), (-2, 1), (1, 2), (-1, 2), (3, 1), (-3, 1), (1, 3), (1, 0)]}
-DEN = {4: 360, 6: 1008000}
-GROW = {4: 4, 6: 9}  # bits the evaluated parts can exceed s by
+          6: [(0, 1), (1, 1), (-1, 1), (2, 1), (-2, 1), (1, 2), (-1, 2), (3, 1), (-3, 1), (1, 3), (1, 0)],
+          8: [(0, 1), (1, 1), (-1, 1), (2, 1), (-2, 1), (1, 2), (-1, 2), (3, 1), (-3, 1), (1, 3), (-1, 3),
+              (3, 2), (-3, 2), (2, 3), (1, 0)]}
+DEN = {4: 360, 6: 1008000, 8: 54486432000}
+GROW = {4: 4, 6: 9, 8: 13}  # bits the evaluated parts can exceed s by
 
 
 def evaluation_matrix(K):
@@ -44,7 +47,7 @@ def inverse(M):
     return [row[n:] for row in A]
 
 
-@pytest.mark.parametrize("K", [4, 6])
+@pytest.mark.parametrize("K", [4, 6, 8])
 def test_interpolation_denominator_and_recovery(K):
     P_ = 2 * K - 1
     M = evaluation_matrix(K)
@@ -52,7 +55,7 @@ def test_interpolation_denominator_and_recovery(K):
     den = 1
     for row in Mi:
         for v in row:
-            den = den * v.denominator // np.gcd(den, v.denominator)
+            den = den * v.denominator // math.gcd(den, v.denominator)
     assert den == DEN[K]
     rng = np.random.default_rng(4)
     for _ in range(20):
@@ -77,7 +80,7 @@ def evaluate(vals, s, point, K):
 
 
 @pytest.mark.parametrize("K,n,b", [(4, 5, 130), (4, 9, 257), (4, 16, 1000), (4, 1, 200),
-                                   (6, 5, 200), (6, 7, 1000), (6, 3, 161)])
+                                   (6, 5, 200), (6, 7, 1000), (6, 3, 161), (8, 5, 300), (8, 6, 1500), (8, 2, 225)])
 def test_toom_rows_equal_direct_rows(K, n, b):
     h = uniform_vec(500 + n, 0, 2 * n - 1, b, 0)
     x = uniform_vec(500 + n, 1, n, b, 0)
@@ -99,8 +102,22 @@ def test_toom_rows_equal_direct_rows(K, n, b):
         assert sum(int(c) << (m * s) for m, c in enumerate(C)) == want[i]
 
 
-@pytest.mark.parametrize("K", [4, 6])
+@pytest.mark.parametrize("K", [4, 6, 8])
 def test_evaluated_parts_fit_the_child_width(K):
     """The largest evaluation is sum_k |p|^k |q|^(K-1-k) times 2^s - 1 parts: below 2^GROW."""
     worst = max(sum(abs(num) ** k * abs(den) ** (K - 1 - k) for k in range(K)) for num, den in POINTS[K])
     assert worst < 2 ** GROW[K] and worst >= 2 ** (GROW[K] - 1)
+
+
+def test_toom8_interpolation_sums_fit_int64_through_depth_7():
+    """Den C_m is summed in int64 from int16/int32 post-pass digits |d| <= 510 * 2^L:
+    with at most four shifted products meeting at a digit, the bound stays
+    below 2^62 for index depths up to 7 (the plan refuses deeper ones)."""
+    M = evaluation_matrix(8)
+    Mi = inverse(M)
+    N = [[int(v * DEN[8]) for v in row] for row in Mi]
+    assert all((v * DEN[8]).denominator == 1 for row in Mi for v in row)
+    rowsum = max(sum(abs(v) for v in row) for row in N)
+    assert 4 * rowsum * 510 * 2 ** 7 < 2 ** 62
+    assert 4 * rowsum * 510 * 2 ** 8 >= 2 ** 62
+    assert DEN[8] == 7776000 * 7007 and 7776000 < 2 ** 24 and 7007 < 2 ** 24
