@@ -89,7 +89,7 @@ typedef enum {
  * Without one, HMV_AUTO picks the digit split (none, Karatsuba one or two
  * levels, Toom-4, Toom-6, Toom-8) by its cost model.  Toom-8 returns
  * HMV_EUNSUPPORTED where its 64-bit interpolation sums could overflow (index
- * depths above 7, n beyond about 30000). */
+ * depths above 7, n beyond about 16000). */
 #define HMV_FLAG_DIGIT_TOOM4 32u  /* needs b > 96 */
 #define HMV_FLAG_DIGIT_TOOM6 64u  /* needs b > 160 */
 #define HMV_FLAG_DIGIT_TOOM8 256u /* needs b > 224 */

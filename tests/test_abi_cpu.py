@@ -96,3 +96,13 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(hmv.Vec) == 40
     assert hmv.Vec.limbs.offset == 16 and hmv.Vec.neg.offset == 24 and hmv.Vec.on_device.offset == 32
     assert ctypes.sizeof(hmv.Stats) == 4 * 4 + 8 + 8 * 2 + 8 + 8 * 5 + 8 * 3 + 4 * 2 + 8 * 5 + 4 * 2
+
+
+def test_toom8_depth_bound_without_gpu(lib):
+    """Toom-8's int64 interpolation sums are bounded for index depths up to 7:
+    the plan refuses the split where its products need depth 8 (n = 20000),
+    and HMV_AUTO then picks another split."""
+    assert hmv.plan_bytes(8000, 33220, flags=hmv.FLAG_DIGIT_TOOM8) > 0
+    with pytest.raises(hmv.HmvError):
+        hmv.plan_bytes(20000, 33220, flags=hmv.FLAG_DIGIT_TOOM8)
+    assert hmv.plan_bytes(20000, 33220) > 0
