@@ -124,6 +124,7 @@ class Lanczos:
         self.v, self.ev = buf(x0), x0.exponent
         self.u, self.eu = buf(), 0
         self.w = buf()
+        torch.cuda.current_stream(dev).synchronize()  # the copies land before the plan's stream reads them
         self.beta = (0, 0)
         self.dvv = None
         self.k = 0
@@ -136,7 +137,7 @@ class Lanczos:
         """The next product w = A v_k as ((v limbs, v sign), E_v, (w limbs, w sign))
         device pointers, for a caller that runs it (hmv_matvec_many) itself."""
         p = self.plan
-        self.torch.cuda.synchronize()
+        # the previous step's device calls have finished on the plan's stream
         if self.dvv is None:
             self.dvv = hmv.dot_device(p, self._ptrs(self.v), self._ptrs(self.v))
         if self.dvv == 0:

@@ -8,7 +8,9 @@ beta sequence) or a plain chain v_{k+1} = A v_k.  The eigenvalue stage of a
 Lanczos run is the client's.  The server
 
   * admits arrived requests in order while the device memory its plans need
-    (hmv_plan_bytes, computed without allocating) fits the budget,
+    (hmv_plan_bytes, computed without allocating) fits the budget; a request's
+    plan is created and its matrix loaded on a worker thread while the
+    current step runs, and it joins the first step that starts after that,
   * keeps every admitted matrix resident (one plan per request),
   * runs steps: each step advances EVERY active request by one product with
     one hmv_matvec_many call, whose leaf products share one persistent
@@ -23,6 +25,7 @@ alone or in any mix.
 from __future__ import annotations
 
 import time
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -69,7 +72,11 @@ class Server:
         self.clock = clock
 
     def _admit(self, r: Request, now: float):
+        # runs on the admission thread: the plan's kernels go to the server
+        # stream, the vectors' copies to this thread's stream, which is
+        # synchronised before the request can join a step
         torch = self.torch
+        torch.cuda.set_device(self.dev)
         r.plan = hmv.Plan(r.n, r.b, kind=r.kind, stream=self.stream.cuda_stream)
         r.plan.load_matrix(r.h)
         r.done = 0
@@ -77,13 +84,13 @@ class Server:
         if r.lanczos:
             from .lanczos import Lanczos
             r.lz = Lanczos(r.plan, r.x0, device=self.dev)
-            return
-        with torch.cuda.stream(self.stream):
+        else:
             r.xl = torch.from_numpy(r.x0.limbs.view(np.int32)).to(self.dev)
             r.xn = torch.from_numpy(r.x0.neg).to(self.dev)
             r.yl = torch.empty_like(r.xl)
             r.yn = torch.empty_like(r.xn)
-        r.x_exp = r.x0.exponent
+            r.x_exp = r.x0.exponent
+        torch.cuda.current_stream(self.dev).synchronize()
 
     def _finish(self, r: Request, now: float):
         self.stream.synchronize()
@@ -104,24 +111,36 @@ class Server:
             if r.footprint > self.budget:
                 raise ValueError(f"request {r.rid} needs {r.footprint} bytes, more than the whole budget")
         active: list[Request] = []
+        admitting: list[Request] = []
         used = 0
         steps, step_sizes, peak_active, peak_used = 0, [], 0, 0
+        pool = ThreadPoolExecutor(max_workers=1)
         t0 = self.clock()
-        while pending or active:
+        while pending or active or admitting:
             now = self.clock() - t0
-            while pending and pending[0].arrival <= now and len(active) < self.max_active:
+            while pending and pending[0].arrival <= now and len(active) + len(admitting) < self.max_active:
                 r = pending[0]
                 if used + r.footprint > self.budget:
                     break  # in order: wait for memory to free up
                 pending.pop(0)
-                self._admit(r, now)
-                r.ready = r.arrival
                 used += r.footprint
-                active.append(r)
+                r.admission = pool.submit(self._admit, r, now)
+                admitting.append(r)
+            waiting = []
+            for r in admitting:  # admitted requests join this step
+                if r.admission.done():
+                    r.admission.result()  # an admission's error ends the run here
+                    r.ready = r.arrival
+                    active.append(r)
+                else:
+                    waiting.append(r)
+            admitting = waiting
             peak_active = max(peak_active, len(active))
             peak_used = max(peak_used, used)
             if not active:
-                if pending:
+                if admitting:
+                    admitting[0].admission.result()
+                elif pending:
                     time.sleep(max(0.0, min(pending[0].arrival - (self.clock() - t0), 0.05)))
                 continue
             xs, es, ys = [], [], []
@@ -158,6 +177,7 @@ class Server:
                     still.append(r)
             active = still
         total = self.clock() - t0
+        pool.shutdown(wait=True)
         lat = [v for r in requests for v in r.latencies]
         req_lat = [r.finished - r.arrival for r in requests]
         nmv = sum(r.done for r in requests)  # a Lanczos run that breaks down stops early
