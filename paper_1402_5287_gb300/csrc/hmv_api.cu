@@ -105,6 +105,19 @@ std::vector<OrderHist> order_hists(int n, int L) {
     return h;
 }
 
+// K = 16 MMA groups per j-step that a tile over product digits [u0, u0 + tn)
+// issues, summed over its s-blocks (as the leaf kernel decodes them: blocks of
+// KS digits from s_min rounded down to 8); 128-wide tiles leave out the
+// leading groups of the last block that lie wholly above s_max.
+int tile_kgroups(int u0, int Dl, int tn) {
+    const int s_min = std::max(0, u0 - (Dl - 1)), s_max = std::min(Dl - 1, u0 + tn - 1);
+    if (s_max < s_min) return 0;
+    const int s_base = s_min / 8 * 8;
+    const int nsb = (s_max - s_base + KS) / KS;
+    const int kk0 = (s_base + nsb * KS - 1 - s_max) / 16;
+    return nsb * (KS / 16) - (tn == 128 ? kk0 : 0);
+}
+
 // Estimated seconds of one matvec at depth L on this GPU (tensor work from
 // the tile count, memory work from the bytes the level kernels move); hs
 // holds the order histograms of at least L + 1 levels.
@@ -115,11 +128,8 @@ double cost_model(const std::vector<OrderHist> &hs, int b, int L, int num_sms, i
     const int NUB = Uo / tn;
     double ksteps = 0;  // 128 x tn x 16 MMAs
     for (int ub = 0; ub < NUB; ++ub) {
-        const int u0 = ub * tn;
-        const int s_min = std::max(0, u0 - (Dl - 1)), s_max = std::min(Dl - 1, u0 + tn - 1);
-        const int nsb = (s_max >= s_min) ? (s_max - s_min / 8 * 8 + KS) / KS : 0;
-        for (const auto &e : hs[L].order)
-            ksteps += e.second * static_cast<double>(ceil_div(e.first, TM)) * nsb * e.first * (KS / 16);
+        const int kg = tile_kgroups(ub * tn, Dl, tn);
+        for (const auto &e : hs[L].order) ksteps += e.second * static_cast<double>(ceil_div(e.first, TM)) * kg * e.first;
     }
     const double mma_s = ksteps * mma_cycles(tn) / (static_cast<double>(num_sms) * 1.9e9);
     double bytes = 0;
@@ -491,11 +501,9 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
             std::vector<Tile> lt;
             for (int mt = 0; mt < ceil_div(m, TM); ++mt)
                 for (int ub = 0; ub < p->NUB; ++ub) {
-                    const int u0 = ub * p->tn;
-                    const int s_min = std::max(0, u0 - (p->Dl - 1)), s_max = std::min(p->Dl - 1, u0 + p->tn - 1);
-                    const int nsb = (s_max >= s_min) ? (s_max - s_min / 8 * 8 + KS) / KS : 0;  // as the kernel
-                    lt.push_back(Tile{lf, mt * TM, ub, nsb * m, 0});
-                    issued += static_cast<double>(TM) * p->tn * KS * nsb * m;
+                    const int kg = tile_kgroups(ub * p->tn, p->Dl, p->tn);  // as the kernel
+                    lt.push_back(Tile{lf, mt * TM, ub, kg * m, 0});
+                    issued += static_cast<double>(TM) * p->tn * 16 * kg * m;
                 }
             std::stable_sort(lt.begin(), lt.end(), [](const Tile &a, const Tile &b2) { return a.cost > b2.cost; });
             tiles.insert(tiles.end(), lt.begin(), lt.end());

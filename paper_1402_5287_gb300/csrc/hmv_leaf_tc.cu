@@ -80,6 +80,7 @@ struct __align__(1024) Smem {
 struct TileInfo {
     const LeafProblem *pr;
     int leaf, i0, ub, u0, m, s_base, nsb, njc, Q, Dl, Dp;
+    int kk0;  // leading K = 16 groups of the last s-block lying wholly above s_max (zero products)
 };
 
 template <int TNv>
@@ -101,6 +102,7 @@ __device__ __forceinline__ TileInfo decode(const Tile &t, const LeafProblem *pro
     const int s_max = min(Dl - 1, ti.u0 + TNv - 1);
     ti.s_base = s_min / 8 * 8;
     ti.nsb = (s_max >= s_min) ? (s_max - ti.s_base + KS) / KS : 0;
+    ti.kk0 = ti.nsb ? (ti.s_base + ti.nsb * KS - 1 - s_max) / 16 : 0;  // groups of digits above s_max
     ti.njc = (ti.m + JC - 1) / JC;
     ti.Q = ti.nsb * ti.m;
     return ti;
@@ -278,8 +280,15 @@ __global__ void __launch_bounds__(Geo<TNv>::kThreads, 1)
                             if (!mbar_wait(&sm.b_full[bs], (gs / B_STAGES) & 1, kTimeoutNs)) { fail(sm, dstat); break; }
                             tc_fence_after();
                             const uint32_t b_base = b_base0 + bs * B_BYTES;
-                            mma_bf16_ss_k128<2 * kLboA, 256>(tmem_w + ab * TN, smem_desc(a_base + jj * 16, kLboA, 128),
-                                                             smem_desc(b_base, 128, 128), G::kIdesc, acc_flag);
+                            // the last s-block leaves out its K groups above s_max (zero products)
+                            if (sb + 1 < ti.nsb || ti.kk0 == 0)
+                                mma_bf16_ss_k128<2 * kLboA, 256>(tmem_w + ab * TN, smem_desc(a_base + jj * 16, kLboA, 128),
+                                                                 smem_desc(b_base, 128, 128), G::kIdesc, acc_flag);
+                            else
+                                mma_bf16_ss_k128_skip<2 * kLboA, 256>(tmem_w + ab * TN,
+                                                                      smem_desc(a_base + jj * 16, kLboA, 128),
+                                                                      smem_desc(b_base, 128, 128), G::kIdesc, acc_flag,
+                                                                      ti.kk0);
                             acc_flag = 1;
                             mma_commit(&sm.b_empty[bs]);
                             ++qw;

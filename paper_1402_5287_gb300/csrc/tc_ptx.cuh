@@ -132,6 +132,161 @@ __device__ __forceinline__ void mma_bf16_ss_k128(uint32_t d_tmem, uint64_t adesc
         "n"(7 * A_STEP / 16), "n"(7 * B_STEP / 16)
         : "memory");
 }
+// MMAs KK0..7 of the eight above in one asm block, the leading KK0 left out
+// (their K groups hold only zero products); the first one issued accumulates
+// into D when accumulate != 0.
+template <uint32_t A_STEP, uint32_t B_STEP, int KK0>
+struct MmaFrom;
+template <uint32_t A_STEP, uint32_t B_STEP>
+struct MmaFrom<A_STEP, B_STEP, 1> {
+    static __device__ __forceinline__ void run(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                               uint32_t accumulate) {
+        asm volatile(
+        "{\n\t.reg .pred p, t;\n\t.reg .b64 a, b;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\tsetp.eq.u32 t, 0, 0;\n\t"
+        "add.s64 a, %1, %5;\n\tadd.s64 b, %2, %6;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, p;\n\t"
+        "add.s64 a, %1, %7;\n\tadd.s64 b, %2, %8;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
+        "add.s64 a, %1, %9;\n\tadd.s64 b, %2, %10;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
+        "add.s64 a, %1, %11;\n\tadd.s64 b, %2, %12;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
+        "add.s64 a, %1, %13;\n\tadd.s64 b, %2, %14;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
+        "add.s64 a, %1, %15;\n\tadd.s64 b, %2, %16;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
+        "add.s64 a, %1, %17;\n\tadd.s64 b, %2, %18;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
+        "}\n" ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate), "n"(1 * A_STEP / 16), "n"(1 * B_STEP / 16), "n"(2 * A_STEP / 16), "n"(2 * B_STEP / 16), "n"(3 * A_STEP / 16), "n"(3 * B_STEP / 16), "n"(4 * A_STEP / 16), "n"(4 * B_STEP / 16), "n"(5 * A_STEP / 16), "n"(5 * B_STEP / 16), "n"(6 * A_STEP / 16), "n"(6 * B_STEP / 16), "n"(7 * A_STEP / 16), "n"(7 * B_STEP / 16)
+        : "memory");
+    }
+};
+template <uint32_t A_STEP, uint32_t B_STEP>
+struct MmaFrom<A_STEP, B_STEP, 2> {
+    static __device__ __forceinline__ void run(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                               uint32_t accumulate) {
+        asm volatile(
+        "{\n\t.reg .pred p, t;\n\t.reg .b64 a, b;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\tsetp.eq.u32 t, 0, 0;\n\t"
+        "add.s64 a, %1, %5;\n\tadd.s64 b, %2, %6;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, p;\n\t"
+        "add.s64 a, %1, %7;\n\tadd.s64 b, %2, %8;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
+        "add.s64 a, %1, %9;\n\tadd.s64 b, %2, %10;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
+        "add.s64 a, %1, %11;\n\tadd.s64 b, %2, %12;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
+        "add.s64 a, %1, %13;\n\tadd.s64 b, %2, %14;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
+        "add.s64 a, %1, %15;\n\tadd.s64 b, %2, %16;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
+        "}\n" ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate), "n"(2 * A_STEP / 16), "n"(2 * B_STEP / 16), "n"(3 * A_STEP / 16), "n"(3 * B_STEP / 16), "n"(4 * A_STEP / 16), "n"(4 * B_STEP / 16), "n"(5 * A_STEP / 16), "n"(5 * B_STEP / 16), "n"(6 * A_STEP / 16), "n"(6 * B_STEP / 16), "n"(7 * A_STEP / 16), "n"(7 * B_STEP / 16)
+        : "memory");
+    }
+};
+template <uint32_t A_STEP, uint32_t B_STEP>
+struct MmaFrom<A_STEP, B_STEP, 3> {
+    static __device__ __forceinline__ void run(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                               uint32_t accumulate) {
+        asm volatile(
+        "{\n\t.reg .pred p, t;\n\t.reg .b64 a, b;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\tsetp.eq.u32 t, 0, 0;\n\t"
+        "add.s64 a, %1, %5;\n\tadd.s64 b, %2, %6;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, p;\n\t"
+        "add.s64 a, %1, %7;\n\tadd.s64 b, %2, %8;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
+        "add.s64 a, %1, %9;\n\tadd.s64 b, %2, %10;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
+        "add.s64 a, %1, %11;\n\tadd.s64 b, %2, %12;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
+        "add.s64 a, %1, %13;\n\tadd.s64 b, %2, %14;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
+        "}\n" ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate), "n"(3 * A_STEP / 16), "n"(3 * B_STEP / 16), "n"(4 * A_STEP / 16), "n"(4 * B_STEP / 16), "n"(5 * A_STEP / 16), "n"(5 * B_STEP / 16), "n"(6 * A_STEP / 16), "n"(6 * B_STEP / 16), "n"(7 * A_STEP / 16), "n"(7 * B_STEP / 16)
+        : "memory");
+    }
+};
+template <uint32_t A_STEP, uint32_t B_STEP>
+struct MmaFrom<A_STEP, B_STEP, 4> {
+    static __device__ __forceinline__ void run(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                               uint32_t accumulate) {
+        asm volatile(
+        "{\n\t.reg .pred p, t;\n\t.reg .b64 a, b;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\tsetp.eq.u32 t, 0, 0;\n\t"
+        "add.s64 a, %1, %5;\n\tadd.s64 b, %2, %6;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, p;\n\t"
+        "add.s64 a, %1, %7;\n\tadd.s64 b, %2, %8;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
+        "add.s64 a, %1, %9;\n\tadd.s64 b, %2, %10;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
+        "add.s64 a, %1, %11;\n\tadd.s64 b, %2, %12;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
+        "}\n" ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate), "n"(4 * A_STEP / 16), "n"(4 * B_STEP / 16), "n"(5 * A_STEP / 16), "n"(5 * B_STEP / 16), "n"(6 * A_STEP / 16), "n"(6 * B_STEP / 16), "n"(7 * A_STEP / 16), "n"(7 * B_STEP / 16)
+        : "memory");
+    }
+};
+template <uint32_t A_STEP, uint32_t B_STEP>
+struct MmaFrom<A_STEP, B_STEP, 5> {
+    static __device__ __forceinline__ void run(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                               uint32_t accumulate) {
+        asm volatile(
+        "{\n\t.reg .pred p, t;\n\t.reg .b64 a, b;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\tsetp.eq.u32 t, 0, 0;\n\t"
+        "add.s64 a, %1, %5;\n\tadd.s64 b, %2, %6;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, p;\n\t"
+        "add.s64 a, %1, %7;\n\tadd.s64 b, %2, %8;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
+        "add.s64 a, %1, %9;\n\tadd.s64 b, %2, %10;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
+        "}\n" ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate), "n"(5 * A_STEP / 16), "n"(5 * B_STEP / 16), "n"(6 * A_STEP / 16), "n"(6 * B_STEP / 16), "n"(7 * A_STEP / 16), "n"(7 * B_STEP / 16)
+        : "memory");
+    }
+};
+template <uint32_t A_STEP, uint32_t B_STEP>
+struct MmaFrom<A_STEP, B_STEP, 6> {
+    static __device__ __forceinline__ void run(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                               uint32_t accumulate) {
+        asm volatile(
+        "{\n\t.reg .pred p, t;\n\t.reg .b64 a, b;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\tsetp.eq.u32 t, 0, 0;\n\t"
+        "add.s64 a, %1, %5;\n\tadd.s64 b, %2, %6;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, p;\n\t"
+        "add.s64 a, %1, %7;\n\tadd.s64 b, %2, %8;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
+        "}\n" ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate), "n"(6 * A_STEP / 16), "n"(6 * B_STEP / 16), "n"(7 * A_STEP / 16), "n"(7 * B_STEP / 16)
+        : "memory");
+    }
+};
+template <uint32_t A_STEP, uint32_t B_STEP>
+struct MmaFrom<A_STEP, B_STEP, 7> {
+    static __device__ __forceinline__ void run(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                               uint32_t accumulate) {
+        asm volatile(
+        "{\n\t.reg .pred p, t;\n\t.reg .b64 a, b;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\tsetp.eq.u32 t, 0, 0;\n\t"
+        "add.s64 a, %1, %5;\n\tadd.s64 b, %2, %6;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, p;\n\t"
+        "}\n" ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate), "n"(7 * A_STEP / 16), "n"(7 * B_STEP / 16)
+        : "memory");
+    }
+};
+// The same with the count of left-out MMAs (0..7) known at run time: one
+// branch per call, then a block of 8 - kk0 MMAs.
+template <uint32_t A_STEP, uint32_t B_STEP>
+__device__ __forceinline__ void mma_bf16_ss_k128_skip(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                                      uint32_t accumulate, int kk0) {
+    static_assert(A_STEP % 16 == 0 && B_STEP % 16 == 0, "descriptor steps are 16-byte units");
+    switch (kk0) {
+        case 0: mma_bf16_ss_k128<A_STEP, B_STEP>(d_tmem, adesc, bdesc, idesc, accumulate); break;
+        case 1: MmaFrom<A_STEP, B_STEP, 1>::run(d_tmem, adesc, bdesc, idesc, accumulate); break;
+        case 2: MmaFrom<A_STEP, B_STEP, 2>::run(d_tmem, adesc, bdesc, idesc, accumulate); break;
+        case 3: MmaFrom<A_STEP, B_STEP, 3>::run(d_tmem, adesc, bdesc, idesc, accumulate); break;
+        case 4: MmaFrom<A_STEP, B_STEP, 4>::run(d_tmem, adesc, bdesc, idesc, accumulate); break;
+        case 5: MmaFrom<A_STEP, B_STEP, 5>::run(d_tmem, adesc, bdesc, idesc, accumulate); break;
+        case 6: MmaFrom<A_STEP, B_STEP, 6>::run(d_tmem, adesc, bdesc, idesc, accumulate); break;
+        default: MmaFrom<A_STEP, B_STEP, 7>::run(d_tmem, adesc, bdesc, idesc, accumulate); break;
+    }
+}
 // Arrive on bar once every MMA issued so far by this thread has completed.
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
