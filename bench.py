@@ -572,7 +572,7 @@ def main(argv=None):
     ap.add_argument("--levels", type=int, default=-1, help="Karatsuba depth (-1: cost model)")
     ap.add_argument("--digit-split", type=int, choices=[-1, 0, 1, 2, 4, 6, 8], default=-1,
                     help="split of the mantissas on top of the index recursion: Karatsuba levels 1 or 2, "
-                         "Toom-4 or Toom-6 (4, 6), none (0) or the cost model's choice (-1)")
+                         "Toom-4, Toom-6 or Toom-8 (4, 6, 8), none (0) or the cost model's choice (-1)")
     ap.add_argument("--method", choices=["auto", "karatsuba", "fft64", "schoolbook"], default="auto",
                     help="product method (profiling runs; the metric uses auto = Karatsuba + tcgen05)")
     ap.add_argument("--tile", type=int, choices=[0, 128, 256], default=0,
