@@ -108,6 +108,20 @@ __device__ __forceinline__ TileInfo decode(const Tile &t, const LeafProblem *pro
     return ti;
 }
 
+// Exact accumulation windows of 128-wide tiles: a j-step of s-block sb
+// issues step_groups K = 16 groups (16 products per column each); an fp32
+// window takes kWinGroups of them (1024 products), so a window spans
+// window_span consecutive j-steps of one s-block, half of them (alternate
+// steps) each issuer's.  Short steps (the trimmed last block) thus get long
+// windows, and both issuers' windows cover the same steps.
+constexpr int kWinGroups = FLUSH_J * (KS / 16);
+__device__ __forceinline__ int step_groups(const TileInfo &ti, int sb) {
+    return (sb + 1 < ti.nsb) ? KS / 16 : KS / 16 - ti.kk0;
+}
+__device__ __forceinline__ int window_span(const TileInfo &ti, int sb) {
+    return 2 * (kWinGroups / step_groups(ti, sb));
+}
+
 template <class S>
 __device__ __forceinline__ void fail(S &sm, int32_t *dstat) {
     sm.abort = 1;
@@ -260,10 +274,11 @@ __global__ void __launch_bounds__(Geo<TNv>::kThreads, 1)
                 mbar_arrive(&sm.tq_empty[qs]);
                 if (t < 0) break;
                 const TileInfo ti = decode<TNv>(tiles[t], probs);
-                const int Qw = (ti.Q - w + 1) / 2;  // this issuer's j-steps in the tile
-                int qw = 0;
+                bool open = false;  // this issuer has a window open
                 uint32_t acc_flag = 0;
                 for (int sb = 0; sb < ti.nsb && !sm.abort; ++sb) {
+                    const int span = window_span(ti, sb);
+                    int wend = 0;  // j at which the open window ends (its s-block's windows start at multiples of span)
                     for (int jc = 0; jc < ti.njc && !sm.abort; ++jc) {
                         const int j0 = jc * JC;
                         const int jn = min(JC, ti.m - j0);
@@ -271,9 +286,16 @@ __global__ void __launch_bounds__(Geo<TNv>::kThreads, 1)
                         if (!mbar_wait(&sm.a_full[as], aph, kTimeoutNs)) { fail(sm, dstat); break; }
                         const uint32_t a_base = a_base0 + as * A_BYTES;
                         for (int jj = (q0 + w) & 1; jj < jn; jj += 2) {
-                            if (qw % FLUSH_J == 0) {
+                            if (j0 + jj >= wend) {  // close the open window, open the next (own steps are 2 apart, span >= 16)
+                                if (open) {
+                                    mma_commit(&sm.acc_full[w][ab]);
+                                    accph[ab] ^= 1;
+                                    ab ^= 1;
+                                }
                                 if (!mbar_wait(&sm.acc_empty[w][ab], accph[ab] ^ 1, kTimeoutNs)) { fail(sm, dstat); break; }
                                 acc_flag = 0;
+                                open = true;
+                                wend += span;
                             }
                             const int gs = gq + q0 + jj;
                             const int bs = gs % B_STAGES;
@@ -291,16 +313,15 @@ __global__ void __launch_bounds__(Geo<TNv>::kThreads, 1)
                                                                       ti.kk0);
                             acc_flag = 1;
                             mma_commit(&sm.b_empty[bs]);
-                            ++qw;
-                            if (qw % FLUSH_J == 0 || qw == Qw) {
-                                mma_commit(&sm.acc_full[w][ab]);
-                                accph[ab] ^= 1;
-                                ab ^= 1;
-                            }
                         }
                         mma_commit(&sm.a_empty[as]);
                         if (++as == A_STAGES) { as = 0; aph ^= 1; }
                     }
+                }
+                if (open && !sm.abort) {  // the tile's last window
+                    mma_commit(&sm.acc_full[w][ab]);
+                    accph[ab] ^= 1;
+                    ab ^= 1;
                 }
                 gq += ti.Q;
             }
@@ -323,18 +344,34 @@ __global__ void __launch_bounds__(Geo<TNv>::kThreads, 1)
             if (lane == 0) mbar_arrive(&sm.tq_empty[qs]);
             if (t < 0) break;
             const TileInfo ti = decode<TNv>(tiles[t], probs);
-            // windows of the first issuer (ceil(Q / NI) j-steps) and of the second (floor(Q / 2))
-            const int nw0 = ((ti.Q + NI - 1) / NI + FLUSH_J - 1) / FLUSH_J;
-            const int nw1 = NI == 2 ? (ti.Q / 2 + FLUSH_J - 1) / FLUSH_J : 0;
+            // the tile's windows in order: one issuer, FLUSH_J j-steps each; two
+            // issuers, window_span j-steps of one s-block each, of which either
+            // issuer may have none (the next window starts at j-step wa of s-block wsb)
+            const int nw_one = (ti.Q + FLUSH_J - 1) / FLUSH_J;
+            int wsb = 0, wa = 0;
             uint32_t st[TN / 4];
 #pragma unroll
             for (int w = 0; w < TN / 4; ++w) st[w] = 0;
             int co = 0;
             bool ok = true;
-            for (int g = 0; g < nw0; ++g) {
-                const bool two = NI == 2 && g < nw1;
-                if (!mbar_wait(&sm.acc_full[0][ab[0]], eph[0][ab[0]], kTimeoutNs)) { fail(sm, dstat); ok = false; break; }
-                eph[0][ab[0]] ^= 1;
+            for (int g = 0;; ++g) {
+                bool one = true, two = false;  // issuer 0's / issuer 1's accumulator holds this window
+                if (NI == 1) {
+                    if (g >= nw_one) break;
+                } else {
+                    while (wsb < ti.nsb && wa >= ti.m) { ++wsb; wa = 0; }
+                    if (wsb >= ti.nsb) break;
+                    const int span = window_span(ti, wsb);
+                    const int len = min(span, ti.m - wa);
+                    const int p0 = (wsb * ti.m + wa) & 1;  // issuer of the window's first j-step
+                    one = (len + (p0 == 0 ? 1 : 0)) / 2 > 0;
+                    two = (len + (p0 == 1 ? 1 : 0)) / 2 > 0;
+                    wa += span;
+                }
+                if (one) {
+                    if (!mbar_wait(&sm.acc_full[0][ab[0]], eph[0][ab[0]], kTimeoutNs)) { fail(sm, dstat); ok = false; break; }
+                    eph[0][ab[0]] ^= 1;
+                }
                 if (two) {
                     if (!mbar_wait(&sm.acc_full[NI - 1][ab[NI - 1]], eph[NI - 1][ab[NI - 1]], kTimeoutNs)) {
                         fail(sm, dstat);
@@ -348,11 +385,15 @@ __global__ void __launch_bounds__(Geo<TNv>::kThreads, 1)
 #pragma unroll
                 for (int ch = 0; ch < TN / 32; ++ch) {
                     uint32_t v[32];
-                    tmem_ld_32x32b_x32(lane_addr + ab[0] * TN + ch * 32, v);
-                    tmem_ld_wait();
                     int x[32];
 #pragma unroll
-                    for (int e = 0; e < 32; ++e) x[e] = __float2int_rn(__uint_as_float(v[e]));
+                    for (int e = 0; e < 32; ++e) x[e] = 0;
+                    if (one) {
+                        tmem_ld_32x32b_x32(lane_addr + ab[0] * TN + ch * 32, v);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int e = 0; e < 32; ++e) x[e] = __float2int_rn(__uint_as_float(v[e]));
+                    }
                     if (two) {
                         tmem_ld_32x32b_x32(lane_addr + (2 + ab[NI - 1]) * TN + ch * 32, v);
                         tmem_ld_wait();
@@ -376,10 +417,10 @@ __global__ void __launch_bounds__(Geo<TNv>::kThreads, 1)
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) {
-                    mbar_arrive(&sm.acc_empty[0][ab[0]]);
+                    if (one) mbar_arrive(&sm.acc_empty[0][ab[0]]);
                     if (two) mbar_arrive(&sm.acc_empty[NI - 1][ab[NI - 1]]);
                 }
-                ab[0] ^= 1;
+                if (one) ab[0] ^= 1;
                 if (two) ab[NI - 1] ^= 1;
             }
             if (!ok) break;
