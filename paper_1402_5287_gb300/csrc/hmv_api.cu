@@ -284,6 +284,7 @@ const char *hmv_status_string(hmv_status s) {
         case HMV_ENOTLOADED: return "matrix not loaded";
         case HMV_EFFTBOUND: return "FFT error bound not below 1/2";
         case HMV_EUNSUPPORTED: return "unsupported configuration";
+        case HMV_EINTERNAL: return "internal consistency check failed";
     }
     return "unknown status";
 }
@@ -612,7 +613,7 @@ hmv_status hmv_load_matrix(hmv_plan_t *p, const hmv_vec *h) {
     g(cudaStreamSynchronize(p->stream));
     if (g.err != cudaSuccess) return from_cuda(g.err);
     if (st[0] == DEV_BADINPUT) return HMV_EINVAL;
-    if (st[0] != DEV_OK) return HMV_ECUDA;
+    if (st[0] != DEV_OK) return HMV_EINTERNAL;
     if (p->method == HMV_FFT64) {
         unsigned long long sq = 0;
         if (!g(cudaMemcpy(&sq, p->fft_sumsq, sizeof sq, cudaMemcpyDeviceToHost))) return from_cuda(g.err);
@@ -713,7 +714,7 @@ hmv_status hmv_matvec(hmv_plan_t *p, const hmv_vec *x, hmv_vec *y) {
     if (g.err != cudaSuccess) return from_cuda(g.err);
     if (st[0] == DEV_BADINPUT) return HMV_EINVAL;
     if (st[0] == DEV_TIMEOUT) return HMV_ETIMEOUT;
-    if (st[0] != DEV_OK) return HMV_ECUDA;
+    if (st[0] != DEV_OK) return HMV_EINTERNAL;
     if (!y->on_device) {
         g(cudaMemcpyAsync(y->limbs, yl, rows * p->L32 * sizeof(uint32_t), cudaMemcpyDeviceToHost, p->stream));
         g(cudaMemcpyAsync(y->neg, yn, rows, cudaMemcpyDeviceToHost, p->stream));

@@ -442,7 +442,7 @@ hmv_status hmv_batch_matvec(hmv_batch_t *B, const hmv_vec *xs, hmv_vec *ys) {
     for (int i = 0; i < count; ++i) {
         if (st[8 * i] == DEV_BADINPUT) return HMV_EINVAL;
         if (st[8 * i] == DEV_TIMEOUT) return HMV_ETIMEOUT;
-        if (st[8 * i] != DEV_OK) return HMV_ECUDA;
+        if (st[8 * i] != DEV_OK) return HMV_EINTERNAL;
     }
     for (int i = 0; i < count && e == cudaSuccess; ++i) {
         hmv_plan_s *p = B->plans[i];
@@ -579,7 +579,7 @@ extern "C" hmv_status hmv_matvec_many(int32_t count, hmv_plan_t *const *plans, c
     for (int i = 0; i < count; ++i) {
         if (st[8 * i] == DEV_BADINPUT) return HMV_EINVAL;
         if (st[8 * i] == DEV_TIMEOUT) return HMV_ETIMEOUT;
-        if (st[8 * i] != DEV_OK) return HMV_ECUDA;
+        if (st[8 * i] != DEV_OK) return HMV_EINTERNAL;
     }
     for (int i = 0; i < count && e == cudaSuccess; ++i) {
         hmv_plan_s *p = plans[i];

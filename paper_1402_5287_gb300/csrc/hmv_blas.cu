@@ -181,7 +181,7 @@ extern "C" hmv_status hmv_dot(hmv_plan_t *p, const hmv_vec *x, const hmv_vec *y,
     const cudaError_t se = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = se;
     if (e != cudaSuccess) { cudaGetLastError(); return HMV_ECUDA; }
-    if (status[0] != DEV_OK) return HMV_ECUDA;
+    if (status[0] != DEV_OK) return HMV_EINTERNAL;
     for (int w = ZW; w < zl; ++w) z[w] = 0;
     *z_neg = sign;
     return HMV_OK;
@@ -261,7 +261,7 @@ extern "C" hmv_status hmv_lincomb(hmv_plan_t *p, int32_t count, const hmv_scalar
     const cudaError_t se = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = se;
     if (e != cudaSuccess) { cudaGetLastError(); return HMV_ECUDA; }
-    if (status[0] != DEV_OK) return HMV_ECUDA;
+    if (status[0] != DEV_OK) return HMV_EINTERNAL;
     y->exponent = status[3];
     return HMV_OK;
 }

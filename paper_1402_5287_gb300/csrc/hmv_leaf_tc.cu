@@ -42,7 +42,6 @@ namespace {
 
 constexpr int kProducerWarp = 0;
 constexpr int kMmaWarp = 1;
-constexpr int kEpiWarp0 = 2;
 constexpr int kNumEpiWarps = 4;
 constexpr int kMmaWarp2 = 2 + kNumEpiWarps;  // second issuer of 128-digit tiles
 constexpr uint64_t kTimeoutNs = 2000000000ull;  // 2 s for any single wait

@@ -116,7 +116,7 @@ extern "C" hmv_status hmv_schoolbook_noalloc(int32_t n, int32_t b, int32_t kind,
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return HMV_ECUDA;
     if (hs[0] == DEV_BADINPUT) return HMV_EINVAL;
-    if (hs[0] != DEV_OK) return HMV_ECUDA;
+    if (hs[0] != DEV_OK) return HMV_EINTERNAL;
     *y_exponent = hs[3];
     return HMV_OK;
 }

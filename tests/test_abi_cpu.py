@@ -39,12 +39,23 @@ def test_every_declared_symbol_is_exported(lib):
 def test_status_strings_and_version(lib):
     assert lib.hmv_status_string(0) == b"ok"
     assert lib.hmv_status_string(1) == b"invalid argument"
+    assert lib.hmv_status_string(7) == b"unsupported configuration"
+    assert lib.hmv_status_string(8) == b"internal consistency check failed"
     assert lib.hmv_status_string(99) == b"unknown status"
     assert lib.hmv_version() >= 100
 
 
+def test_status_codes_match_the_header():
+    """Every hmv_status value in include/hmv.h has its name in the binding's table."""
+    text = open(os.path.join(ROOT, "include", "hmv.h")).read()
+    body = re.search(r"typedef enum \{(.*?)\} hmv_status;", text, flags=re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    codes = {int(v): k for k, v in re.findall(r"(HMV_\w+)\s*=\s*(\d+)", body)}
+    assert codes == hmv.STATUS
+
+
 @pytest.mark.parametrize("field,value", [("n", 0), ("b", 0), ("b", (1 << 20) + 1), ("nrhs", 0), ("kind", 3),
-                                         ("method", 9), ("levels", -2), ("levels", 17), ("flags", 1 << 8),
+                                         ("method", 9), ("levels", -2), ("levels", 17), ("flags", 1 << 9),
                                          ("flags", hmv.FLAG_TILE128 | hmv.FLAG_TILE256),
                                          ("piece_bits", 5), ("piece_bits", -1)])
 def test_plan_rejects_bad_descriptors_without_gpu(lib, field, value):
