@@ -17,7 +17,6 @@ constexpr int KS = 128;
 constexpr int JC = 64;
 constexpr int AR = TM + JC;                   // rows of one staged Hankel slab
 static_assert(TM % 32 == 0 && JC % 32 == 0 && AR / 32 <= 256, "A slabs are whole 32-row groups");
-constexpr int A_BYTES = AR * KS * 2;          // bf16 slab bytes
 constexpr int A_STAGES = 2;
 // j-steps per exact fp32 accumulation window: FLUSH_J * KS products of
 // magnitude <= 2^14 keep every partial sum within 2^24.

@@ -30,6 +30,10 @@
 // consumers through a small shared-memory queue), so the grid works on
 // neighbouring tiles of the same leaves and their operands stay in L2.  Two 128x256 fp32 accumulators (all 512 TMEM columns)
 // let the MMAs of one window overlap the epilogue of the previous one.
+// On 128-wide tiles each staged s-block is a frame of KS + 32 digits, so a
+// tile's last s-block, when it holds only one or two K = 16 groups below
+// s_max, is issued with the block below it (j-steps of 9 or 10 MMAs instead
+// of separate steps of 1 or 2, which the issuing threads cannot keep up with).
 // Every wait is bounded; on a timeout the kernel records DEV_TIMEOUT, drains
 // and frees its TMEM, and returns.
 #include <cstring>
@@ -51,7 +55,14 @@ template <int TNv>
 struct Geo {
     static constexpr int NI = TNv == 128 ? 2 : 1;           // MMA-issuing threads
     static constexpr int kThreads = (2 + kNumEpiWarps + NI - 1) * 32;
-    static constexpr int NEv = TNv / 8 + KS / 8 - 1;        // core matrices of one shifted-x operand
+    // Digits of one staged s-block frame: KS, and on 128-wide tiles 32 more
+    // above them, so that a last s-block of at most two K = 16 groups joins
+    // the block below it (10-group frame) instead of making j-steps of one or
+    // two MMAs.  A normal block issues the frame's groups G0 .. G0 + 7.
+    static constexpr int KF = TNv == 128 ? KS + 32 : KS;
+    static constexpr int G0 = (KF - KS) / 16;
+    static constexpr int AB = AR * KF * 2;                  // bf16 bytes of one staged Hankel slab
+    static constexpr int NEv = TNv / 8 + KF / 8 - 1;        // core matrices of one shifted-x operand
     static constexpr int BB = NEv * 128;                    // its bytes
     static constexpr int BS = TNv == 256 ? 8 : 16;          // B ring slots (even: see the issuers)
     static constexpr uint32_t kTmemCols = 2 * TNv * NI;     // two accumulators per issuer
@@ -64,7 +75,7 @@ constexpr int kTileConsumers = 1 + kNumEpiWarps;  // plus the second issuer wher
 
 template <int TNv>
 struct __align__(1024) Smem {
-    uint8_t a[A_STAGES][A_BYTES];
+    uint8_t a[A_STAGES][Geo<TNv>::AB];
     uint8_t b[Geo<TNv>::BS][Geo<TNv>::BB];
     uint64_t a_full[A_STAGES], a_empty[A_STAGES];
     uint64_t b_full[Geo<TNv>::BS], b_empty[Geo<TNv>::BS];
@@ -79,7 +90,7 @@ struct __align__(1024) Smem {
 struct TileInfo {
     const LeafProblem *pr;
     int leaf, i0, ub, u0, m, s_base, nsb, njc, Q, Dl, Dp;
-    int kk0;  // leading K = 16 groups of the last s-block lying wholly above s_max (zero products)
+    int fg;  // first frame group the last s-block issues (those above lie wholly above s_max: zero products)
 };
 
 template <int TNv>
@@ -101,7 +112,14 @@ __device__ __forceinline__ TileInfo decode(const Tile &t, const LeafProblem *pro
     const int s_max = min(Dl - 1, ti.u0 + TNv - 1);
     ti.s_base = s_min / 8 * 8;
     ti.nsb = (s_max >= s_min) ? (s_max - ti.s_base + KS) / KS : 0;
-    ti.kk0 = ti.nsb ? (ti.s_base + ti.nsb * KS - 1 - s_max) / 16 : 0;  // groups of digits above s_max
+    const int kk0 = ti.nsb ? (ti.s_base + ti.nsb * KS - 1 - s_max) / 16 : 0;  // groups of digits above s_max
+    using G = Geo<TNv>;
+    if (G::G0 > 0 && ti.nsb >= 2 && KS / 16 - kk0 <= G::G0) {
+        --ti.nsb;  // the last block's groups ride on the block below, in its frame's top G0 groups
+        ti.fg = G::G0 - (KS / 16 - kk0);
+    } else {
+        ti.fg = G::G0 + kk0;
+    }
     ti.njc = (ti.m + JC - 1) / JC;
     ti.Q = ti.nsb * ti.m;
     return ti;
@@ -115,7 +133,7 @@ __device__ __forceinline__ TileInfo decode(const Tile &t, const LeafProblem *pro
 // windows, and both issuers' windows cover the same steps.
 constexpr int kWinGroups = FLUSH_J * (KS / 16);
 __device__ __forceinline__ int step_groups(const TileInfo &ti, int sb) {
-    return (sb + 1 < ti.nsb) ? KS / 16 : KS / 16 - ti.kk0;
+    return (sb + 1 < ti.nsb) ? KS / 16 : Geo<128>::KF / 16 - ti.fg;
 }
 __device__ __forceinline__ int window_span(const TileInfo &ti, int sb) {
     return 2 * (kWinGroups / step_groups(ti, sb));
@@ -187,14 +205,14 @@ __global__ void __launch_bounds__(Geo<TNv>::kThreads, 1)
                         const int j0 = jc * JC;
                         const int jn = min(JC, ti.m - j0);
                         if (!mbar_wait(&sm.a_empty[as], aph ^ 1, kTimeoutNs)) { fail(sm, dstat); break; }
-                        mbar_arrive_expect_tx(&sm.a_full[as], A_BYTES);
-                        tma_load_4d(sm.a[as], mapA, &sm.a_full[as], 0, (ti.i0 + j0) / 32, (Dp - s_lo - KS) / 8,
+                        mbar_arrive_expect_tx(&sm.a_full[as], G::AB);
+                        tma_load_4d(sm.a[as], mapA, &sm.a_full[as], 0, (ti.i0 + j0) / 32, (Dp - s_lo - G::KF) / 8,
                                     ti.leaf);
                         if (++as == A_STAGES) { as = 0; aph ^= 1; }
                         for (int jj = 0; jj < jn; ++jj) {
                             if (!mbar_wait(&sm.b_empty[bs], bph ^ 1, kTimeoutNs)) { fail(sm, dstat); break; }
                             mbar_arrive_expect_tx(&sm.b_full[bs], B_BYTES);
-                            tma_load_4d(sm.b[bs], mapB, &sm.b_full[bs], 0, (ti.u0 - s_lo - KS) / 8 + 1, j0 + jj,
+                            tma_load_4d(sm.b[bs], mapB, &sm.b_full[bs], 0, (ti.u0 - s_lo - G::KF) / 8 + 1, j0 + jj,
                                         ti.leaf);
                             if (++bs == B_STAGES) { bs = 0; bph ^= 1; }
                         }
@@ -221,7 +239,7 @@ __global__ void __launch_bounds__(Geo<TNv>::kThreads, 1)
                     for (int jc = 0; jc < ti.njc && !sm.abort; ++jc) {
                         const int jn = min(JC, ti.m - jc * JC);
                         if (!mbar_wait(&sm.a_full[as], aph, kTimeoutNs)) { fail(sm, dstat); break; }
-                        const uint32_t a_base = a_base0 + as * A_BYTES;
+                        const uint32_t a_base = a_base0 + as * G::AB;
                         for (int jj = 0; jj < jn; ++jj) {
                             if (q % FLUSH_J == 0) {
                                 if (!mbar_wait(&sm.acc_empty[0][ab], accph[ab] ^ 1, kTimeoutNs)) { fail(sm, dstat); break; }
@@ -278,14 +296,17 @@ __global__ void __launch_bounds__(Geo<TNv>::kThreads, 1)
                 for (int sb = 0; sb < ti.nsb && !sm.abort; ++sb) {
                     const int span = window_span(ti, sb);
                     int wend = 0;  // j at which the open window ends (its s-block's windows start at multiples of span)
+                    // frame groups this block issues: G0 .. G0 + 7, or fg .. KF / 16 - 1 in the last block
+                    const int g0 = (sb + 1 < ti.nsb) ? G::G0 : ti.fg;
+                    const int ng = G::KF / 16 - g0;
                     for (int jc = 0; jc < ti.njc && !sm.abort; ++jc) {
                         const int j0 = jc * JC;
                         const int jn = min(JC, ti.m - j0);
                         const int q0 = sb * ti.m + j0;  // tile step of jj = 0
                         if (!mbar_wait(&sm.a_full[as], aph, kTimeoutNs)) { fail(sm, dstat); break; }
-                        const uint32_t a_base = a_base0 + as * A_BYTES;
+                        const uint32_t a_base = a_base0 + as * G::AB;
                         for (int jj = (q0 + w) & 1; jj < jn; jj += 2) {
-                            if (j0 + jj >= wend) {  // close the open window, open the next (own steps are 2 apart, span >= 16)
+                            if (j0 + jj >= wend) {  // close the open window, open the next (own steps are 2 apart, span >= 12)
                                 if (open) {
                                     mma_commit(&sm.acc_full[w][ab]);
                                     accph[ab] ^= 1;
@@ -301,15 +322,12 @@ __global__ void __launch_bounds__(Geo<TNv>::kThreads, 1)
                             if (!mbar_wait(&sm.b_full[bs], (gs / B_STAGES) & 1, kTimeoutNs)) { fail(sm, dstat); break; }
                             tc_fence_after();
                             const uint32_t b_base = b_base0 + bs * B_BYTES;
-                            // the last s-block leaves out its K groups above s_max (zero products)
-                            if (sb + 1 < ti.nsb || ti.kk0 == 0)
-                                mma_bf16_ss_k128<2 * kLboA, 256>(tmem_w + ab * TN, smem_desc(a_base + jj * 16, kLboA, 128),
-                                                                 smem_desc(b_base, 128, 128), G::kIdesc, acc_flag);
-                            else
-                                mma_bf16_ss_k128_skip<2 * kLboA, 256>(tmem_w + ab * TN,
-                                                                      smem_desc(a_base + jj * 16, kLboA, 128),
-                                                                      smem_desc(b_base, 128, 128), G::kIdesc, acc_flag,
-                                                                      ti.kk0);
+                            const uint64_t ad = smem_desc(a_base + jj * 16 + g0 * 2 * kLboA, kLboA, 128);
+                            const uint64_t bd = smem_desc(b_base + g0 * 256, 128, 128);
+                            if (ng == 8)
+                                mma_bf16_ss_k128<2 * kLboA, 256>(tmem_w + ab * TN, ad, bd, G::kIdesc, acc_flag);
+                            else  // the last s-block: without its groups above s_max, or with the next block's
+                                mma_bf16_ss_run<2 * kLboA, 256>(tmem_w + ab * TN, ad, bd, G::kIdesc, acc_flag, ng);
                             acc_flag = 1;
                             mma_commit(&sm.b_empty[bs]);
                         }
@@ -509,6 +527,7 @@ EncodeTiledFn get_encode() {
 }  // namespace
 
 cudaError_t encode_tensor_map_A(hmv_plan_s *p, CUtensorMap *map) {
+    const int KF = p->tn == 128 ? Geo<128>::KF : Geo<256>::KF;
     EncodeTiledFn enc = get_encode();
     if (!enc) return cudaErrorNotSupported;
     const int nleaves = p->lv[p->L].nodes;
@@ -519,7 +538,7 @@ cudaError_t encode_tensor_map_A(hmv_plan_s *p, CUtensorMap *map) {
     // lands in shared memory in the same order as 8-element rows would.
     cuuint64_t dims[4] = {256, static_cast<cuuint64_t>(p->RA / 32), chunks, static_cast<cuuint64_t>(nleaves)};
     cuuint64_t strides[3] = {512, static_cast<cuuint64_t>(p->RA) * 16, chunks * p->RA * 16};
-    cuuint32_t box[4] = {256, static_cast<cuuint32_t>(AR / 32), static_cast<cuuint32_t>(KS / 8), 1};
+    cuuint32_t box[4] = {256, static_cast<cuuint32_t>(AR / 32), static_cast<cuuint32_t>(KF / 8), 1};
     cuuint32_t es[4] = {1, 1, 1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, p->hrev, dims, strides, box, es,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -528,6 +547,7 @@ cudaError_t encode_tensor_map_A(hmv_plan_s *p, CUtensorMap *map) {
 }
 
 cudaError_t encode_tensor_map_B(hmv_plan_s *p, uint16_t *xg, CUtensorMap *map) {
+    const int KF = p->tn == 128 ? Geo<128>::KF : Geo<256>::KF;
     EncodeTiledFn enc = get_encode();
     if (!enc) return cudaErrorNotSupported;
     const int nleaves = p->lv[p->L].nodes;
@@ -536,7 +556,7 @@ cudaError_t encode_tensor_map_B(hmv_plan_s *p, uint16_t *xg, CUtensorMap *map) {
     const cuuint64_t xc = static_cast<cuuint64_t>(p->Dp / 8 + 1);
     cuuint64_t dims[4] = {64, xc, static_cast<cuuint64_t>(p->RX), static_cast<cuuint64_t>(nleaves)};
     cuuint64_t strides[3] = {128, xc * 128, static_cast<cuuint64_t>(p->RX) * xc * 128};
-    cuuint32_t box[4] = {64, static_cast<cuuint32_t>(p->tn / 8 + KS / 8 - 1), 1, 1};
+    cuuint32_t box[4] = {64, static_cast<cuuint32_t>(p->tn / 8 + KF / 8 - 1), 1, 1};
     cuuint32_t es[4] = {1, 1, 1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, xg, dims, strides, box, es,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,

@@ -97,194 +97,89 @@ __device__ __forceinline__ void mma_bf16_ss(uint32_t d_tmem, uint64_t adesc, uin
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
-// Eight MMAs along K (K = 128 in all) from one asm block: MMA k reads A at
+// N consecutive MMAs along K from one asm block: MMA k reads A at
 // adesc + k * A_STEP bytes and B at bdesc + k * B_STEP bytes (the descriptor
 // start-address field counts 16-byte units; both start fields must stay
 // below 2^14 after the additions).  The first MMA accumulates into D when
-// accumulate != 0, the other seven always do.  One block rather than eight
-// separate statements measurably shortens the issue path of the thread.
+// accumulate != 0, the others always do.  One block rather than N separate
+// statements measurably shortens the issue path of the thread.
+#define HMV_MMA_HEAD                                       \
+    "{\n\t.reg .pred p, t;\n\t.reg .b64 a, b;\n\t"         \
+    "setp.ne.b32 p, %4, 0;\n\tsetp.eq.u32 t, 0, 0;\n\t"    \
+    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t"
+#define HMV_MMA_NEXT(ia, ib)                                                  \
+    "add.s64 a, %1, %" #ia ";\n\tadd.s64 b, %2, %" #ib ";\n\t" \
+    "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
+#define HMV_MMA_ARGS "r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+#define HMV_MMA_OFF(k) "n"((k) * A_STEP / 16), "n"((k) * B_STEP / 16)
+#define HMV_MMA_N2 HMV_MMA_NEXT(5, 6)
+#define HMV_MMA_N3 HMV_MMA_N2 HMV_MMA_NEXT(7, 8)
+#define HMV_MMA_N4 HMV_MMA_N3 HMV_MMA_NEXT(9, 10)
+#define HMV_MMA_N5 HMV_MMA_N4 HMV_MMA_NEXT(11, 12)
+#define HMV_MMA_N6 HMV_MMA_N5 HMV_MMA_NEXT(13, 14)
+#define HMV_MMA_N7 HMV_MMA_N6 HMV_MMA_NEXT(15, 16)
+#define HMV_MMA_N8 HMV_MMA_N7 HMV_MMA_NEXT(17, 18)
+#define HMV_MMA_N9 HMV_MMA_N8 HMV_MMA_NEXT(19, 20)
+#define HMV_MMA_N10 HMV_MMA_N9 HMV_MMA_NEXT(21, 22)
+#define HMV_MMA_O2 HMV_MMA_OFF(1)
+#define HMV_MMA_O3 HMV_MMA_O2, HMV_MMA_OFF(2)
+#define HMV_MMA_O4 HMV_MMA_O3, HMV_MMA_OFF(3)
+#define HMV_MMA_O5 HMV_MMA_O4, HMV_MMA_OFF(4)
+#define HMV_MMA_O6 HMV_MMA_O5, HMV_MMA_OFF(5)
+#define HMV_MMA_O7 HMV_MMA_O6, HMV_MMA_OFF(6)
+#define HMV_MMA_O8 HMV_MMA_O7, HMV_MMA_OFF(7)
+#define HMV_MMA_O9 HMV_MMA_O8, HMV_MMA_OFF(8)
+#define HMV_MMA_O10 HMV_MMA_O9, HMV_MMA_OFF(9)
+template <uint32_t A_STEP, uint32_t B_STEP, int N>
+struct MmaRun;
+template <uint32_t A_STEP, uint32_t B_STEP>
+struct MmaRun<A_STEP, B_STEP, 1> {
+    static __device__ __forceinline__ void run(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                               uint32_t accumulate) {
+        asm volatile(HMV_MMA_HEAD "}\n" ::HMV_MMA_ARGS : "memory");
+    }
+};
+#define HMV_MMA_RUN(N)                                                                                           \
+    template <uint32_t A_STEP, uint32_t B_STEP>                                                                  \
+    struct MmaRun<A_STEP, B_STEP, N> {                                                                           \
+        static_assert(A_STEP % 16 == 0 && B_STEP % 16 == 0, "descriptor steps are 16-byte units");             \
+        static __device__ __forceinline__ void run(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, \
+                                                   uint32_t accumulate) {                                        \
+            asm volatile(HMV_MMA_HEAD HMV_MMA_N##N "}\n" ::HMV_MMA_ARGS, HMV_MMA_O##N : "memory");              \
+        }                                                                                                        \
+    };
+HMV_MMA_RUN(2)
+HMV_MMA_RUN(3)
+HMV_MMA_RUN(4)
+HMV_MMA_RUN(5)
+HMV_MMA_RUN(6)
+HMV_MMA_RUN(7)
+HMV_MMA_RUN(8)
+HMV_MMA_RUN(9)
+HMV_MMA_RUN(10)
+#undef HMV_MMA_RUN
+// Eight MMAs: one j-step of a full K = 128 s-block.
 template <uint32_t A_STEP, uint32_t B_STEP>
 __device__ __forceinline__ void mma_bf16_ss_k128(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                                  uint32_t accumulate) {
-    static_assert(A_STEP % 16 == 0 && B_STEP % 16 == 0, "descriptor steps are 16-byte units");
-    asm volatile(
-        "{\n\t.reg .pred p, t;\n\t.reg .b64 a, b;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "setp.eq.u32 t, 0, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t"
-        "add.s64 a, %1, %5;\n\tadd.s64 b, %2, %6;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
-        "add.s64 a, %1, %7;\n\tadd.s64 b, %2, %8;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
-        "add.s64 a, %1, %9;\n\tadd.s64 b, %2, %10;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
-        "add.s64 a, %1, %11;\n\tadd.s64 b, %2, %12;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
-        "add.s64 a, %1, %13;\n\tadd.s64 b, %2, %14;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
-        "add.s64 a, %1, %15;\n\tadd.s64 b, %2, %16;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
-        "add.s64 a, %1, %17;\n\tadd.s64 b, %2, %18;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t}\n" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate), "n"(1 * A_STEP / 16), "n"(1 * B_STEP / 16),
-        "n"(2 * A_STEP / 16), "n"(2 * B_STEP / 16), "n"(3 * A_STEP / 16), "n"(3 * B_STEP / 16), "n"(4 * A_STEP / 16),
-        "n"(4 * B_STEP / 16), "n"(5 * A_STEP / 16), "n"(5 * B_STEP / 16), "n"(6 * A_STEP / 16), "n"(6 * B_STEP / 16),
-        "n"(7 * A_STEP / 16), "n"(7 * B_STEP / 16)
-        : "memory");
+    MmaRun<A_STEP, B_STEP, 8>::run(d_tmem, adesc, bdesc, idesc, accumulate);
 }
-// MMAs KK0..7 of the eight above in one asm block, the leading KK0 left out
-// (their K groups hold only zero products); the first one issued accumulates
-// into D when accumulate != 0.
-template <uint32_t A_STEP, uint32_t B_STEP, int KK0>
-struct MmaFrom;
+// 1 <= count <= 10 MMAs with the count known at run time: one branch per
+// call, then one block.
 template <uint32_t A_STEP, uint32_t B_STEP>
-struct MmaFrom<A_STEP, B_STEP, 1> {
-    static __device__ __forceinline__ void run(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                               uint32_t accumulate) {
-        asm volatile(
-        "{\n\t.reg .pred p, t;\n\t.reg .b64 a, b;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\tsetp.eq.u32 t, 0, 0;\n\t"
-        "add.s64 a, %1, %5;\n\tadd.s64 b, %2, %6;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, p;\n\t"
-        "add.s64 a, %1, %7;\n\tadd.s64 b, %2, %8;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
-        "add.s64 a, %1, %9;\n\tadd.s64 b, %2, %10;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
-        "add.s64 a, %1, %11;\n\tadd.s64 b, %2, %12;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
-        "add.s64 a, %1, %13;\n\tadd.s64 b, %2, %14;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
-        "add.s64 a, %1, %15;\n\tadd.s64 b, %2, %16;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
-        "add.s64 a, %1, %17;\n\tadd.s64 b, %2, %18;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
-        "}\n" ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate), "n"(1 * A_STEP / 16), "n"(1 * B_STEP / 16), "n"(2 * A_STEP / 16), "n"(2 * B_STEP / 16), "n"(3 * A_STEP / 16), "n"(3 * B_STEP / 16), "n"(4 * A_STEP / 16), "n"(4 * B_STEP / 16), "n"(5 * A_STEP / 16), "n"(5 * B_STEP / 16), "n"(6 * A_STEP / 16), "n"(6 * B_STEP / 16), "n"(7 * A_STEP / 16), "n"(7 * B_STEP / 16)
-        : "memory");
-    }
-};
-template <uint32_t A_STEP, uint32_t B_STEP>
-struct MmaFrom<A_STEP, B_STEP, 2> {
-    static __device__ __forceinline__ void run(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                               uint32_t accumulate) {
-        asm volatile(
-        "{\n\t.reg .pred p, t;\n\t.reg .b64 a, b;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\tsetp.eq.u32 t, 0, 0;\n\t"
-        "add.s64 a, %1, %5;\n\tadd.s64 b, %2, %6;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, p;\n\t"
-        "add.s64 a, %1, %7;\n\tadd.s64 b, %2, %8;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
-        "add.s64 a, %1, %9;\n\tadd.s64 b, %2, %10;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
-        "add.s64 a, %1, %11;\n\tadd.s64 b, %2, %12;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
-        "add.s64 a, %1, %13;\n\tadd.s64 b, %2, %14;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
-        "add.s64 a, %1, %15;\n\tadd.s64 b, %2, %16;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
-        "}\n" ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate), "n"(2 * A_STEP / 16), "n"(2 * B_STEP / 16), "n"(3 * A_STEP / 16), "n"(3 * B_STEP / 16), "n"(4 * A_STEP / 16), "n"(4 * B_STEP / 16), "n"(5 * A_STEP / 16), "n"(5 * B_STEP / 16), "n"(6 * A_STEP / 16), "n"(6 * B_STEP / 16), "n"(7 * A_STEP / 16), "n"(7 * B_STEP / 16)
-        : "memory");
-    }
-};
-template <uint32_t A_STEP, uint32_t B_STEP>
-struct MmaFrom<A_STEP, B_STEP, 3> {
-    static __device__ __forceinline__ void run(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                               uint32_t accumulate) {
-        asm volatile(
-        "{\n\t.reg .pred p, t;\n\t.reg .b64 a, b;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\tsetp.eq.u32 t, 0, 0;\n\t"
-        "add.s64 a, %1, %5;\n\tadd.s64 b, %2, %6;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, p;\n\t"
-        "add.s64 a, %1, %7;\n\tadd.s64 b, %2, %8;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
-        "add.s64 a, %1, %9;\n\tadd.s64 b, %2, %10;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
-        "add.s64 a, %1, %11;\n\tadd.s64 b, %2, %12;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
-        "add.s64 a, %1, %13;\n\tadd.s64 b, %2, %14;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
-        "}\n" ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate), "n"(3 * A_STEP / 16), "n"(3 * B_STEP / 16), "n"(4 * A_STEP / 16), "n"(4 * B_STEP / 16), "n"(5 * A_STEP / 16), "n"(5 * B_STEP / 16), "n"(6 * A_STEP / 16), "n"(6 * B_STEP / 16), "n"(7 * A_STEP / 16), "n"(7 * B_STEP / 16)
-        : "memory");
-    }
-};
-template <uint32_t A_STEP, uint32_t B_STEP>
-struct MmaFrom<A_STEP, B_STEP, 4> {
-    static __device__ __forceinline__ void run(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                               uint32_t accumulate) {
-        asm volatile(
-        "{\n\t.reg .pred p, t;\n\t.reg .b64 a, b;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\tsetp.eq.u32 t, 0, 0;\n\t"
-        "add.s64 a, %1, %5;\n\tadd.s64 b, %2, %6;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, p;\n\t"
-        "add.s64 a, %1, %7;\n\tadd.s64 b, %2, %8;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
-        "add.s64 a, %1, %9;\n\tadd.s64 b, %2, %10;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
-        "add.s64 a, %1, %11;\n\tadd.s64 b, %2, %12;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
-        "}\n" ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate), "n"(4 * A_STEP / 16), "n"(4 * B_STEP / 16), "n"(5 * A_STEP / 16), "n"(5 * B_STEP / 16), "n"(6 * A_STEP / 16), "n"(6 * B_STEP / 16), "n"(7 * A_STEP / 16), "n"(7 * B_STEP / 16)
-        : "memory");
-    }
-};
-template <uint32_t A_STEP, uint32_t B_STEP>
-struct MmaFrom<A_STEP, B_STEP, 5> {
-    static __device__ __forceinline__ void run(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                               uint32_t accumulate) {
-        asm volatile(
-        "{\n\t.reg .pred p, t;\n\t.reg .b64 a, b;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\tsetp.eq.u32 t, 0, 0;\n\t"
-        "add.s64 a, %1, %5;\n\tadd.s64 b, %2, %6;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, p;\n\t"
-        "add.s64 a, %1, %7;\n\tadd.s64 b, %2, %8;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
-        "add.s64 a, %1, %9;\n\tadd.s64 b, %2, %10;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
-        "}\n" ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate), "n"(5 * A_STEP / 16), "n"(5 * B_STEP / 16), "n"(6 * A_STEP / 16), "n"(6 * B_STEP / 16), "n"(7 * A_STEP / 16), "n"(7 * B_STEP / 16)
-        : "memory");
-    }
-};
-template <uint32_t A_STEP, uint32_t B_STEP>
-struct MmaFrom<A_STEP, B_STEP, 6> {
-    static __device__ __forceinline__ void run(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                               uint32_t accumulate) {
-        asm volatile(
-        "{\n\t.reg .pred p, t;\n\t.reg .b64 a, b;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\tsetp.eq.u32 t, 0, 0;\n\t"
-        "add.s64 a, %1, %5;\n\tadd.s64 b, %2, %6;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, p;\n\t"
-        "add.s64 a, %1, %7;\n\tadd.s64 b, %2, %8;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
-        "}\n" ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate), "n"(6 * A_STEP / 16), "n"(6 * B_STEP / 16), "n"(7 * A_STEP / 16), "n"(7 * B_STEP / 16)
-        : "memory");
-    }
-};
-template <uint32_t A_STEP, uint32_t B_STEP>
-struct MmaFrom<A_STEP, B_STEP, 7> {
-    static __device__ __forceinline__ void run(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                               uint32_t accumulate) {
-        asm volatile(
-        "{\n\t.reg .pred p, t;\n\t.reg .b64 a, b;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\tsetp.eq.u32 t, 0, 0;\n\t"
-        "add.s64 a, %1, %5;\n\tadd.s64 b, %2, %6;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, p;\n\t"
-        "}\n" ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate), "n"(7 * A_STEP / 16), "n"(7 * B_STEP / 16)
-        : "memory");
-    }
-};
-// The same with the count of left-out MMAs (0..7) known at run time: one
-// branch per call, then a block of 8 - kk0 MMAs.
-template <uint32_t A_STEP, uint32_t B_STEP>
-__device__ __forceinline__ void mma_bf16_ss_k128_skip(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                                      uint32_t accumulate, int kk0) {
-    static_assert(A_STEP % 16 == 0 && B_STEP % 16 == 0, "descriptor steps are 16-byte units");
-    switch (kk0) {
-        case 0: mma_bf16_ss_k128<A_STEP, B_STEP>(d_tmem, adesc, bdesc, idesc, accumulate); break;
-        case 1: MmaFrom<A_STEP, B_STEP, 1>::run(d_tmem, adesc, bdesc, idesc, accumulate); break;
-        case 2: MmaFrom<A_STEP, B_STEP, 2>::run(d_tmem, adesc, bdesc, idesc, accumulate); break;
-        case 3: MmaFrom<A_STEP, B_STEP, 3>::run(d_tmem, adesc, bdesc, idesc, accumulate); break;
-        case 4: MmaFrom<A_STEP, B_STEP, 4>::run(d_tmem, adesc, bdesc, idesc, accumulate); break;
-        case 5: MmaFrom<A_STEP, B_STEP, 5>::run(d_tmem, adesc, bdesc, idesc, accumulate); break;
-        case 6: MmaFrom<A_STEP, B_STEP, 6>::run(d_tmem, adesc, bdesc, idesc, accumulate); break;
-        default: MmaFrom<A_STEP, B_STEP, 7>::run(d_tmem, adesc, bdesc, idesc, accumulate); break;
+__device__ __forceinline__ void mma_bf16_ss_run(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                                uint32_t accumulate, int count) {
+    switch (count) {
+        case 1: MmaRun<A_STEP, B_STEP, 1>::run(d_tmem, adesc, bdesc, idesc, accumulate); break;
+        case 2: MmaRun<A_STEP, B_STEP, 2>::run(d_tmem, adesc, bdesc, idesc, accumulate); break;
+        case 3: MmaRun<A_STEP, B_STEP, 3>::run(d_tmem, adesc, bdesc, idesc, accumulate); break;
+        case 4: MmaRun<A_STEP, B_STEP, 4>::run(d_tmem, adesc, bdesc, idesc, accumulate); break;
+        case 5: MmaRun<A_STEP, B_STEP, 5>::run(d_tmem, adesc, bdesc, idesc, accumulate); break;
+        case 6: MmaRun<A_STEP, B_STEP, 6>::run(d_tmem, adesc, bdesc, idesc, accumulate); break;
+        case 7: MmaRun<A_STEP, B_STEP, 7>::run(d_tmem, adesc, bdesc, idesc, accumulate); break;
+        case 8: MmaRun<A_STEP, B_STEP, 8>::run(d_tmem, adesc, bdesc, idesc, accumulate); break;
+        case 9: MmaRun<A_STEP, B_STEP, 9>::run(d_tmem, adesc, bdesc, idesc, accumulate); break;
+        default: MmaRun<A_STEP, B_STEP, 10>::run(d_tmem, adesc, bdesc, idesc, accumulate); break;
     }
 }
 // Arrive on bar once every MMA issued so far by this thread has completed.

@@ -31,9 +31,13 @@ def run(n, b, h, x, flags=0, kind=hmv.HANKEL, method=hmv.KARATSUBA, levels=-1, n
 # sizes: one tile, several tiles with a ragged tail in both dimensions, the
 # narrowest digit counts (b = 1, 33) and digit counts just past a tile edge
 # (1, 64, 0): one j-step per tile, so the second MMA issuer has none;
-# (17, 64, 0): 17 j-steps, 2 windows of the first issuer against 1 of the second
+# (17, 64, 0): 17 j-steps, 2 windows of the first issuer against 1 of the second;
+# (70, 2140, 1) and (90, 4178, 2): 268 and 523 digits, where tiles' last
+# s-blocks of one and of two K groups ride on the block below (j-steps of 9
+# and 10 MMAs); (64, 2048, 1) and (45, 4100, 2) have only the one-group kind
 @pytest.mark.parametrize("n,b,levels", [(64, 2048, 1), (129, 1000, 2), (7, 33, 0), (30, 1, 0), (200, 520, 3),
-                                        (1, 64, 0), (17, 64, 0), (45, 4100, 2), (300, 264, -1)])
+                                        (1, 64, 0), (17, 64, 0), (45, 4100, 2), (300, 264, -1), (70, 2140, 1),
+                                        (90, 4178, 2)])
 def test_tile128_all_rows(n, b, levels):
     h = uniform_vec(80 + n, 0, 2 * n - 1, b, 2)
     x = uniform_vec(80 + n, 1, n, b, -3)
@@ -63,9 +67,11 @@ def test_tile128_block_rhs():
     assert_same(y, y256)
 
 
-def test_tile128_worst_case_digits():
-    """All-(-128) balanced digits: every product +2^14, full windows 2^24."""
-    n, b = 80, 2046
+@pytest.mark.parametrize("b", [2046, 2140])
+def test_tile128_worst_case_digits(b):
+    """All-(-128) balanced digits: every product +2^14, full windows 2^24
+    (b = 2140: 268 digits, windows of 9- and 10-MMA j-steps)."""
+    n = 80
     m = int("80" * ((b + 7) // 8), 16) & ((1 << b) - 1)
     h = FixedVec.from_ints([-m] * (2 * n - 1), b, 0)
     x = FixedVec.from_ints([-m] * n, b, 0)
