@@ -283,6 +283,11 @@ __global__ void __launch_bounds__(Geo<TNv>::kThreads, 1)
             int accph[2] = {0, 0};
             const uint32_t a_base0 = smem_u32(sm.a[0]);
             const uint32_t b_base0 = smem_u32(sm.b[0]);
+            // descriptors of the rings' first slots; the start-address field
+            // counts 16-byte units (a shift j of the Hankel slab is + j), and
+            // every address stays below 2^18, so offsets add without carry
+            const uint64_t adesc0 = smem_desc(a_base0, kLboA, 128);
+            const uint64_t bdesc0 = smem_desc(b_base0, 128, 128);
             const uint32_t tmem_w = tmem + static_cast<uint32_t>(w * 2 * TN);
             for (int k = 0; !sm.abort; ++k) {
                 const int qs = k % kTileQ, qph = (k / kTileQ) & 1;
@@ -304,7 +309,7 @@ __global__ void __launch_bounds__(Geo<TNv>::kThreads, 1)
                         const int jn = min(JC, ti.m - j0);
                         const int q0 = sb * ti.m + j0;  // tile step of jj = 0
                         if (!mbar_wait(&sm.a_full[as], aph, kTimeoutNs)) { fail(sm, dstat); break; }
-                        const uint32_t a_base = a_base0 + as * G::AB;
+                        const uint64_t adesc_s = adesc0 + static_cast<uint32_t>(as * G::AB + g0 * 2 * kLboA) / 16;
                         for (int jj = (q0 + w) & 1; jj < jn; jj += 2) {
                             if (j0 + jj >= wend) {  // close the open window, open the next (own steps are 2 apart, span >= 12)
                                 if (open) {
@@ -317,13 +322,12 @@ __global__ void __launch_bounds__(Geo<TNv>::kThreads, 1)
                                 open = true;
                                 wend += span;
                             }
-                            const int gs = gq + q0 + jj;
-                            const int bs = gs % B_STAGES;
-                            if (!mbar_wait(&sm.b_full[bs], (gs / B_STAGES) & 1, kTimeoutNs)) { fail(sm, dstat); break; }
+                            const unsigned gs = static_cast<unsigned>(gq + q0 + jj);
+                            const unsigned bs = gs % B_STAGES;
+                            if (!mbar_wait(&sm.b_full[bs], (gs / B_STAGES) & 1u, kTimeoutNs)) { fail(sm, dstat); break; }
                             tc_fence_after();
-                            const uint32_t b_base = b_base0 + bs * B_BYTES;
-                            const uint64_t ad = smem_desc(a_base + jj * 16 + g0 * 2 * kLboA, kLboA, 128);
-                            const uint64_t bd = smem_desc(b_base + g0 * 256, 128, 128);
+                            const uint64_t ad = adesc_s + jj;
+                            const uint64_t bd = bdesc0 + (bs * B_BYTES + g0 * 256) / 16;
                             if (ng == 8)
                                 mma_bf16_ss_k128<2 * kLboA, 256>(tmem_w + ab * TN, ad, bd, G::kIdesc, acc_flag);
                             else  // the last s-block: without its groups above s_max, or with the next block's
