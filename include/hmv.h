@@ -52,7 +52,7 @@ typedef enum {
     HMV_ETIMEOUT = 4,      /* a bounded device-side wait gave up (kernel returned early) */
     HMV_ENOTLOADED = 5,    /* hmv_matvec before hmv_load_matrix */
     HMV_EFFTBOUND = 6,     /* FFT path: error bound not below 1/2 (no result written) */
-    HMV_EUNSUPPORTED = 7,  /* method or configuration not available in this build */
+    HMV_EUNSUPPORTED = 7,  /* method or configuration the library does not support */
     HMV_EINTERNAL = 8      /* a device-side consistency check failed (a carry or an exact
                               division's remainder out of range): no result is written; this
                               indicates a defect in the library, not in the arguments */
