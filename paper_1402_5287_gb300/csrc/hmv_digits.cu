@@ -390,48 +390,60 @@ __global__ void k_leaf_normalize(PlanPtrs g, const int *__restrict__ size, int M
     }
 }
 
-// The leaf normalise fused into the deepest post-pass level: output row i of
-// a level-(L-1) node is p_k -/+ (q_k or r_k), k = i / 2, each of the two leaf
-// rows read as its block digits plus its block carries spread as above, so
+// The leaf normalise fused into the deepest post-pass level: output rows
+// 2k and 2k+1 of a level-(L-1) node are p_k - q_k and p_k + r_k, each leaf
+// row read as its block digits plus its block carries spread as above, so
 // the carry-save leaf rows are never written out.  Digits of the result are
 // within [-638, 1020], as after the two separate kernels.  One block per
-// output row.
+// pair of output rows (they share p_k: three leaf rows read, not four).
+__device__ __forceinline__ void leaf_digits8(uint2 w, int (&v)[8]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        v[q] = static_cast<int>((w.x >> (8 * q)) & 0xFF);
+        v[4 + q] = static_cast<int>((w.y >> (8 * q)) & 0xFF);
+    }
+}
+__device__ __forceinline__ void add_block_carry(int (&v)[8], int32_t c, int sg) {
+    v[0] += sg * (c & 0xFF);
+    v[1] += sg * ((c >> 8) & 0xFF);
+    v[2] += sg * ((c >> 16) & 0xFF);
+    v[3] += sg * (c >> 24);  // arithmetic shift: the signed top part
+}
 template <class T>
 __global__ void k_leaf_post(PlanPtrs g, const int *__restrict__ parent_size, int MT, int Uo, int NUB, int rows_out,
                             int Wo, int tn) {
     const uint8_t *__restrict__ dig = static_cast<const uint8_t *>(g.in[blockIdx.y]);
     const int32_t *__restrict__ carry = static_cast<const int32_t *>(g.in2[blockIdx.y]);
     T *__restrict__ out = static_cast<T *>(g.out[blockIdx.y]);
-    const int nu = blockIdx.x / rows_out, i = blockIdx.x % rows_out;
-    if (i >= parent_size[nu]) return;
-    const int k = i >> 1;
-    const int other = (i & 1) ? 2 : 1;
-    const size_t ra = static_cast<size_t>(3 * nu) * MT * TM + k;
-    const size_t rb = static_cast<size_t>(3 * nu + other) * MT * TM + k;
-    const uint2 *da = reinterpret_cast<const uint2 *>(dig + ra * Uo);
-    const uint2 *db = reinterpret_cast<const uint2 *>(dig + rb * Uo);
-    const int32_t *ca = carry + ra * NUB, *cb = carry + rb * NUB;
-    T *o = out + (static_cast<size_t>(nu) * rows_out + i) * Wo;
-    const int sg = (i & 1) ? 1 : -1;
+    const int pairs = (rows_out + 1) / 2;
+    const int nu = blockIdx.x / pairs, k = blockIdx.x % pairs;
+    const int size = parent_size[nu];
+    if (2 * k >= size) return;
+    const bool odd = 2 * k + 1 < size;  // the node has output row 2k+1
+    size_t r[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) r[c] = static_cast<size_t>(3 * nu + c) * MT * TM + k;  // p_k, q_k, r_k
+    T *o0 = out + (static_cast<size_t>(nu) * rows_out + 2 * k) * Wo;
+    T *o1 = o0 + Wo;
     for (int g8 = threadIdx.x; g8 < Wo / 8; g8 += blockDim.x) {  // 8 digits per step; Uo, Wo multiples of 8
         const int u0 = 8 * g8;
-        const uint2 wa = (u0 < Uo) ? da[g8] : make_uint2(0, 0);
-        const uint2 wb = (u0 < Uo) ? db[g8] : make_uint2(0, 0);
-        int v[8];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            v[q] = static_cast<int>((wa.x >> (8 * q)) & 0xFF) + sg * static_cast<int>((wb.x >> (8 * q)) & 0xFF);
-            v[4 + q] = static_cast<int>((wa.y >> (8 * q)) & 0xFF) + sg * static_cast<int>((wb.y >> (8 * q)) & 0xFF);
-        }
+        const bool in = u0 < Uo;
+        int vp[8], vq[8], vr[8];
+        leaf_digits8(in ? reinterpret_cast<const uint2 *>(dig + r[0] * Uo)[g8] : make_uint2(0, 0), vp);
+        leaf_digits8(in ? reinterpret_cast<const uint2 *>(dig + r[1] * Uo)[g8] : make_uint2(0, 0), vq);
+        leaf_digits8(in && odd ? reinterpret_cast<const uint2 *>(dig + r[2] * Uo)[g8] : make_uint2(0, 0), vr);
         if (u0 > 0 && u0 <= Uo && u0 % tn == 0) {
-            const int32_t a = ca[u0 / tn - 1], b = cb[u0 / tn - 1];
-            v[0] += (a & 0xFF) + sg * (b & 0xFF);
-            v[1] += ((a >> 8) & 0xFF) + sg * ((b >> 8) & 0xFF);
-            v[2] += ((a >> 16) & 0xFF) + sg * ((b >> 16) & 0xFF);
-            v[3] += (a >> 24) + sg * (b >> 24);  // arithmetic shifts: the signed top parts
+            const int cb = u0 / tn - 1;
+            add_block_carry(vp, carry[r[0] * NUB + cb], 1);
+            add_block_carry(vq, carry[r[1] * NUB + cb], 1);
+            if (odd) add_block_carry(vr, carry[r[2] * NUB + cb], 1);
         }
-        store4<T>(o, 2 * g8, make_int4(v[0], v[1], v[2], v[3]));
-        store4<T>(o, 2 * g8 + 1, make_int4(v[4], v[5], v[6], v[7]));
+        store4<T>(o0, 2 * g8, make_int4(vp[0] - vq[0], vp[1] - vq[1], vp[2] - vq[2], vp[3] - vq[3]));
+        store4<T>(o0, 2 * g8 + 1, make_int4(vp[4] - vq[4], vp[5] - vq[5], vp[6] - vq[6], vp[7] - vq[7]));
+        if (odd) {
+            store4<T>(o1, 2 * g8, make_int4(vp[0] + vr[0], vp[1] + vr[1], vp[2] + vr[2], vp[3] + vr[3]));
+            store4<T>(o1, 2 * g8 + 1, make_int4(vp[4] + vr[4], vp[5] + vr[5], vp[6] + vr[6], vp[7] + vr[7]));
+        }
     }
 }
 
@@ -754,11 +766,15 @@ cudaError_t leaf_normalize_group(hmv_plan_s *p, const PlanPtrs &g, int G) {
 }
 cudaError_t leaf_post_group(hmv_plan_s *p, const PlanPtrs &g, int G) {
     const LevelGeom &pl = p->lv[p->L - 1];
-    const dim3 grid(static_cast<unsigned>(pl.nodes) * pl.rowsX, G);  // one block per output row
+    const dim3 grid(static_cast<unsigned>(pl.nodes) * ((pl.rowsX + 1) / 2), G);  // one block per output row pair
+    const int steps = (p->Wo / 8 + 31) / 32 * 32;  // threads: one step of 8 digits each, at most 256
+    const int threads = steps < 256 ? steps : 256;
     if (p->post16)
-        k_leaf_post<int16_t><<<grid, 128, 0, p->stream>>>(g, pl.d_size, p->MT, p->Uo, p->NUB, pl.rowsX, p->Wo, p->tn);
+        k_leaf_post<int16_t><<<grid, threads, 0, p->stream>>>(g, pl.d_size, p->MT, p->Uo, p->NUB, pl.rowsX, p->Wo,
+                                                               p->tn);
     else
-        k_leaf_post<int32_t><<<grid, 128, 0, p->stream>>>(g, pl.d_size, p->MT, p->Uo, p->NUB, pl.rowsX, p->Wo, p->tn);
+        k_leaf_post<int32_t><<<grid, threads, 0, p->stream>>>(g, pl.d_size, p->MT, p->Uo, p->NUB, pl.rowsX, p->Wo,
+                                                               p->tn);
     p->launches_total++;
     return cudaGetLastError();
 }
