@@ -18,8 +18,9 @@ constexpr int JC = 64;
 constexpr int AR = TM + JC;                   // rows of one staged Hankel slab
 static_assert(TM % 32 == 0 && JC % 32 == 0 && AR / 32 <= 256, "A slabs are whole 32-row groups");
 constexpr int A_STAGES = 2;
-// j-steps per exact fp32 accumulation window: FLUSH_J * KS products of
-// magnitude <= 2^14 keep every partial sum within 2^24.
+// j-steps per exact fp32 accumulation window of 256-wide tiles: FLUSH_J * KS
+// products of magnitude <= 2^14 keep every partial sum within 2^24 (128-wide
+// tiles size their windows by the same 1024 products, counted in K groups).
 constexpr int FLUSH_J = 1024 / KS;
 constexpr int EXTRA_DIGITS = 8;               // room above the leaf product for carries
 constexpr int TN_DEFAULT = 256;

@@ -25,11 +25,13 @@
 // one thread cannot issue 128 x 128 x 16 MMAs (about 65 cycles of tensor
 // work each) as fast as the tensor pipe runs them once its loop waits on
 // barriers, two threads together can; the two take alternate j-steps of a
-// tile into accumulators of their own, and the epilogue adds the pair.  Tiles are handed out in list order from a global
-// counter (the producer takes the next index and passes it to the CTA's
-// consumers through a small shared-memory queue), so the grid works on
-// neighbouring tiles of the same leaves and their operands stay in L2.  Two 128x256 fp32 accumulators (all 512 TMEM columns)
-// let the MMAs of one window overlap the epilogue of the previous one.
+// tile into accumulators of their own, and the epilogue adds the pair.
+// Tiles are handed out in list order from a global counter (the producer
+// takes the next index and passes it to the CTA's consumers through a small
+// shared-memory queue), so the grid works on neighbouring tiles of the same
+// leaves and their operands stay in L2.  Two fp32 accumulators per issuer
+// (all 512 TMEM columns: 2 x 256, or 2 x 2 x 128 on 128-wide tiles) let the
+// MMAs of one window overlap the epilogue of the previous one.
 // On 128-wide tiles each staged s-block is a frame of KS + 32 digits, so a
 // tile's last s-block, when it holds only one or two K = 16 groups below
 // s_max, is issued with the block below it (j-steps of 9 or 10 MMAs instead
