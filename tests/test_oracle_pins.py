@@ -261,6 +261,103 @@ def test_rounding_ties_and_carry_into_exponent():
     assert oracle_round_ints([5, -3], b, 0) == ([5 << 5, -(3 << 5)], -5 - b)
 
 
+# ---------------------------------------------------------------- rounding at a given shift
+
+def oracle_round_fixed_ints(z_ints, b, shift):
+    zl = max(1, max(abs(v).bit_length() for v in z_ints) // 32 + 1)
+    fv = FixedVec.from_ints(z_ints, 32 * zl, 0)
+    y, yn = oracle.round_rows_fixed(fv.limbs, fv.neg, b, shift)
+    return oracle.limbs_to_ints(y, yn), [int(v) for v in yn]
+
+
+def fraction_round_at(z_ints, shift):
+    """RNE(|Z| / 2^shift) with Z's sign, by exact rationals; +0 for zero."""
+    out = []
+    for v in z_ints:
+        m = rne_fraction(Fraction(abs(v)) / Fraction(2) ** shift)
+        out.append(-m if (v < 0 and m) else m)
+    return out
+
+
+@pytest.mark.parametrize("b", [1, 5, 8, 31, 32, 33, 64, 97])
+def test_fixed_shift_rounding_matches_fraction_rne(b):
+    """round_rows_fixed against Fraction round-half-even for random rows and
+    shifts, t <= 0 (exact left shifts) included."""
+    rng = random.Random(7000 + b)
+    for trial in range(80):
+        shift = rng.randint(-40, 3 * b + 40)
+        cap = b + shift  # a row may use at most b + shift bits
+        if cap < 1:
+            continue
+        count = rng.randint(1, 6)
+        z = []
+        for _ in range(count):
+            width = rng.randint(0, cap)
+            v = rng.getrandbits(width) if width else 0
+            z.append(rng.choice((-1, 1)) * v)
+        want = fraction_round_at(z, shift)
+        if any(abs(w) >= (1 << b) for w in want):
+            with pytest.raises(RuntimeError):
+                oracle_round_fixed_ints(z, b, shift)
+            continue
+        got, neg = oracle_round_fixed_ints(z, b, shift)
+        assert got == want, (z, b, shift)
+        assert neg == [1 if w < 0 else 0 for w in want]
+
+
+def test_fixed_shift_rounding_ties_signs_and_overflow():
+    b, t = 8, 6
+    # ties to even in both signs: q even stays, q odd goes up in magnitude
+    z = [(0b1011010 << t) + (1 << (t - 1)), -((0b1011010 << t) + (1 << (t - 1))),
+         (0b1011011 << t) + (1 << (t - 1)), -((0b1011011 << t) + (1 << (t - 1)))]
+    got, neg = oracle_round_fixed_ints(z, b, t)
+    assert got == [0b1011010, -0b1011010, 0b1011100, -0b1011100] and neg == [0, 1, 0, 1]
+    # just above and just below a tie
+    z = [(5 << t) + (1 << (t - 1)) + 1, -((5 << t) + (1 << (t - 1)) - 1)]
+    assert oracle_round_fixed_ints(z, b, t)[0] == [6, -5]
+    # a negative row that rounds to zero carries no sign
+    got, neg = oracle_round_fixed_ints([-(1 << (t - 1)), -((1 << (t - 1)) + 1), 0], b, t)
+    assert got == [0, -1, 0] and neg == [0, 1, 0]
+    # t <= 0: an exact left shift, no rounding
+    assert oracle_round_fixed_ints([3, -1], b, -4)[0] == [48, -16]
+    assert oracle_round_fixed_ints([255, -255], b, 0)[0] == [255, -255]
+    # overflow guard: a row with more than b + t bits is refused ...
+    with pytest.raises(RuntimeError):
+        oracle_round_fixed_ints([1 << (b + t)], b, t)
+    # ... the largest row with b + t bits is accepted ...
+    assert oracle_round_fixed_ints([(1 << (b + t)) - (1 << t)], b, t)[0] == [255]
+    # ... and one that rounds up to 2^b is refused as well
+    with pytest.raises(RuntimeError):
+        oracle_round_fixed_ints([(1 << (b + t)) - (1 << (t - 1))], b, t)
+    # the same guard for left shifts: 127 << 1 fits in b bits, 128 << 1 does not
+    assert oracle_round_fixed_ints([127], b, -1)[0] == [254]
+    with pytest.raises(RuntimeError):
+        oracle_round_fixed_ints([128], b, -1)
+    with pytest.raises(RuntimeError):
+        oracle_round_fixed_ints([256], b, 0)
+
+
+@pytest.mark.parametrize("b", [1, 7, 32, 33, 100, 256])
+def test_fixed_shift_equals_least_exponent_rounding_at_its_shift(b):
+    """At the shift that the least-exponent rule chooses, rounding at a given
+    shift returns the same mantissas and signs for every row and for any
+    subset of the rows."""
+    rng = random.Random(b)
+    for trial in range(40):
+        width = rng.randint(1, 3 * b + 40)
+        z = rand_ints(rng, rng.randint(1, 8), width)
+        if all(v == 0 for v in z):
+            continue
+        e_in = rng.randint(-30, 30)
+        want, e = oracle_round_ints(z, b, e_in)
+        shift = e + b - e_in
+        got, _ = oracle_round_fixed_ints(z, b, shift)
+        assert got == want
+        sub = sorted(rng.sample(range(len(z)), rng.randint(1, len(z))))
+        got_sub, _ = oracle_round_fixed_ints([z[k] for k in sub], b, shift)
+        assert got_sub == [want[k] for k in sub]
+
+
 # ---------------------------------------------------------------- closed form
 
 def test_hilbert_hankel_closed_form():
