@@ -62,7 +62,9 @@ typedef enum { HMV_HANKEL = 0, HMV_TOEPLITZ = 1, HMV_CIRCULANT = 2 } hmv_kind;
 
 typedef enum {
     HMV_AUTO = 0,          /* Karatsuba recursion; with levels = -1 and no split flag the
-                              cost model also picks the digit-split depth (0-2) */
+                              cost model also picks the split of the mantissas (none,
+                              Karatsuba one or two levels, Toom-4, Toom-6 or Toom-8) and
+                              the leaf tile width */
     HMV_SCHOOLBOOK = 1,    /* plain schoolbook on 32-bit limbs, CUDA cores */
     HMV_KARATSUBA = 2,     /* Algorithm 1 to the given depth, tensor-core leaves */
     HMV_FFT64 = 3          /* split-FP64 FFT with a proven rounding bound; when the bound
@@ -99,7 +101,9 @@ typedef enum {
 
 typedef struct {
     int32_t n;        /* matrix order, n >= 1 */
-    int32_t b;        /* mantissa bits, 1 <= b <= 1<<20 */
+    int32_t b;        /* mantissa bits, 1 <= b <= 1<<20 (HMV_SCHOOLBOOK: one row's operands,
+                         8 ceil(b/32) bytes, must fit the device's opt-in shared memory per
+                         block, else hmv_plan returns HMV_EINVAL) */
     int32_t nrhs;     /* right-hand sides per hmv_matvec, >= 1 */
     int32_t kind;     /* hmv_kind */
     int32_t method;   /* hmv_method */
@@ -146,7 +150,8 @@ typedef struct {
     double ms_fft;           /* with HMV_FLAG_TIMING: time in the FFT path */
     int32_t leaf_tile_digits; /* product digits per leaf tile (256, or 128 with HMV_FLAG_TILE128
                                  or when HMV_AUTO's cost model prefers it); 0 without tiles */
-    int32_t digit_products;  /* products the digit split runs (1; 3 or 9 Karatsuba; 7 or 11 Toom) */
+    int32_t digit_products;  /* products the digit split runs (1; 3 or 9 Karatsuba; 7, 11 or 15
+                                for Toom-4, Toom-6 or Toom-8) */
 } hmv_stats;
 
 /* Create a plan: checks the descriptor, chooses the recursion depth and
@@ -259,12 +264,19 @@ void hmv_batch_free(hmv_batch_t *batch);
  * synchronisation (to read E_y back).
  * Limit: with L = ceil(b/32), it needs at most
  *     n * (32 L + 8 L + 13) + 1536  bytes  <=  HMV_NOALLOC_SCRATCH_BYTES
- * (for example n <= 3200 at b = 1024, n <= 100 at b = 33220); larger
- * problems return HMV_EINVAL and do nothing.  Bits at or above b in h or x
- * also return HMV_EINVAL and leave y unwritten.
+ * (for example n <= 3200 at b = 1024, n <= 100 at b = 33220), and one row's
+ * operands, 8 ceil(b/32) bytes, must fit the device's opt-in shared memory
+ * per block (227 KB on GB300: b up to about 929,000); larger problems return
+ * HMV_EINVAL and do nothing.  Bits at or above b in h or x also return
+ * HMV_EINVAL and leave y unwritten.
  * Set-up: the first call on each device looks the scratch array's device
- * address up (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.
+ * address up (cudaGetSymbolAddress) with that device current and keeps it
+ * for the life of the process; after a cudaDeviceReset of that device the
+ * kept address is no longer valid, so do not call this entry point on it
+ * again in the same process.
+ * Streams: the call copies E_y to host memory and synchronises the stream,
+ * so it must never be made on a stream that is being captured into a CUDA
+ * graph; on a capturing stream it returns HMV_EINVAL before queuing work.
  * Sharing: all calls on a device use the same scratch array, which keeps
  * the last call's contents (the call clears what must start at zero).
  * Calls whose work overlaps on the GPU (other streams, other threads) race
@@ -309,6 +321,20 @@ hmv_status hmv_dot(hmv_plan_t *plan, const hmv_vec *x, const hmv_vec *y, uint32_
  * HMV_EUNSUPPORTED when two terms differ in scale by more than 128 ceil(b/32)
  * bits. */
 hmv_status hmv_lincomb(hmv_plan_t *plan, int32_t count, const hmv_scalar *c, const hmv_vec *xs, hmv_vec *y);
+
+/* ---- Test hook for the failure path --------------------------------------
+ * Not part of the method and not for production use: it lets tests run the
+ * tensor-core leaf kernel's failure path without faulting anything.  The
+ * next `launches` leaf launches made directly on a stream (launches captured
+ * into a batch's CUDA graph never take it) run with every wait limited to
+ * wait_ns nanoseconds (1e6 .. 2e9; the normal limit is 2 s) and with one
+ * epilogue warp holding back one release of an accumulator, so that an
+ * MMA-issuing thread's wait for it runs out.  The kernel then records a
+ * timeout, waits for its own MMAs and for the TMA loads it has in flight,
+ * frees its tensor memory and returns; the call that launched it returns
+ * HMV_ETIMEOUT and writes no output, and the plan stays usable.
+ * launches = 0 disarms the hook.  HMV_EINVAL for arguments out of range. */
+hmv_status hmv_test_leaf_stall(int32_t launches, int64_t wait_ns);
 
 /* Static description of a status code. */
 const char *hmv_status_string(hmv_status s);

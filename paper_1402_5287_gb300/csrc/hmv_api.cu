@@ -231,7 +231,7 @@ __global__ void k_validate(const uint32_t *limbs, int rows, int L32, int b, int3
     if (k >= rows) return;
     const int topbits = b - 32 * (L32 - 1);
     if (topbits < 32 && (limbs[static_cast<size_t>(k) * L32 + L32 - 1] >> topbits) != 0)
-        atomicExch(dstat, DEV_BADINPUT);
+        set_status(dstat, DEV_BADINPUT);
 }
 
 // Descendants of a split plan report into the top plan's status word.
@@ -375,6 +375,10 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
         if (!dry_run) { delete p; return from_cuda(ce); }
         cudaGetLastError();
         p->num_sms = 152;  // footprint query without a device: GB300's SM count
+    }
+    if (p->method == HMV_SCHOOLBOOK && !dry_run && !schoolbook_smem_fits(p->L32)) {
+        delete p;
+        return HMV_EINVAL;  // one row's operands do not fit the kernel's shared memory
     }
     if (p->timing && !dry_run)
         for (auto &e : p->ev) cudaEventCreate(&e);

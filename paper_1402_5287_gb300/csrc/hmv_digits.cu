@@ -89,7 +89,7 @@ __device__ __forceinline__ void store_lane_digits(const int (&d)[kDigitsPerLane]
                                                   int32_t *dstat) {
 #pragma unroll
     for (int q = 0; q < kDigitsPerLane; ++q)
-        if (ub + q >= Dp && d[q] != 0) atomicExch(dstat, DEV_OVERFLOW);
+        if (ub + q >= Dp && d[q] != 0) set_status(dstat, DEV_OVERFLOW);
 #pragma unroll
     for (int h = 0; h < kDigitsPerLane / 16; ++h) {
         const int uh = ub + 16 * h;  // Dp is a multiple of 16
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(256) k_encode(PlanPtrs g, int rows, int L32, i
     if (circ_n > 0) src = ((circ_n - 1 - k) % circ_n + circ_n) % circ_n;
     const uint32_t *m = limbs + static_cast<size_t>(src) * L32;
     const int topbits = b - 32 * (L32 - 1);
-    if (lane == 0 && topbits < 32 && (m[L32 - 1] >> topbits) != 0) atomicExch(dstat, DEV_BADINPUT);
+    if (lane == 0 && topbits < 32 && (m[L32 - 1] >> topbits) != 0) set_status(dstat, DEV_BADINPUT);
     const int sgn = neg[src] ? -1 : 1;
     int8_t *o = out + static_cast<size_t>(k) * Dp;
     int wcarry = 0;
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(256) k_encode(PlanPtrs g, int rows, int L32, i
         warp_balance(d, lane, wcarry);
         store_lane_digits(d, ub, Dp, o, dstat);
     }
-    if (lane == 0 && wcarry != 0) atomicExch(dstat, DEV_OVERFLOW);
+    if (lane == 0 && wcarry != 0) set_status(dstat, DEV_OVERFLOW);
 }
 
 // ------------------------------------------------------------------ pre-pass
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(128) k_prepass(PlanPtrs g, int in_rows, const 
             *reinterpret_cast<uint4 *>(o + u0 + 16 * h) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
         }
     }
-    if (carry != 0) atomicExch(dstat, DEV_OVERFLOW);
+    if (carry != 0) set_status(dstat, DEV_OVERFLOW);
 }
 
 // ------------------------------------------------------------------ packing
@@ -336,7 +336,7 @@ __global__ void k_leaf_simt(const int8_t *__restrict__ A, int rowsA, const int8_
             o[q] = static_cast<uint8_t>(t & 255);
             c = t >> 8;
         }
-        if (c > INT32_MAX || c < INT32_MIN) atomicExch(dstat, DEV_OVERFLOW);
+        if (c > INT32_MAX || c < INT32_MIN) set_status(dstat, DEV_OVERFLOW);
         carry[(static_cast<size_t>(tl.leaf) * MT * TM + i) * NUB + tl.ub] = static_cast<int32_t>(c);
     }
 }
@@ -563,7 +563,7 @@ __global__ void __launch_bounds__(256) k_final_normalize(const T *__restrict__ i
     for (int w = Wo / 4 + lane; w < ZW; w += 32) z[w] = 0u;  // limbs above the row's digits
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) bits = max(bits, __shfl_xor_sync(0xffffffffu, bits, off));
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicExch(dstat, DEV_OVERFLOW);
+    if (__any_sync(0xffffffffu, bad) && lane == 0) set_status(dstat, DEV_OVERFLOW);
     if (lane == 0) {
         zbits[row_offset + i] = bits;
         zneg[row_offset + i] = (bits > 0 && sgn < 0) ? 1 : 0;
@@ -609,7 +609,7 @@ __global__ void k_colsum_normalize(const __int128 *__restrict__ cs, int n, int n
             if (limb) { top = w; topv = limb; }
         }
     }
-    if (c != 0) atomicExch(dstat, DEV_OVERFLOW);
+    if (c != 0) set_status(dstat, DEV_OVERFLOW);
     int bits = (top < 0) ? 0 : 32 * top + (32 - __clz(topv));
     zbits[row_offset + i] = bits;
     zneg[row_offset + i] = (bits > 0 && sgn < 0) ? 1 : 0;
@@ -709,7 +709,7 @@ __global__ void __launch_bounds__(256) k_round(const uint32_t *__restrict__ zmag
                 o[w] += 1u;
                 if (o[w] != 0) break;
             }
-            if (topbits < 32 && (o[L32 - 1] >> topbits)) atomicExch(dstat, DEV_OVERFLOW);
+            if (topbits < 32 && (o[L32 - 1] >> topbits)) set_status(dstat, DEV_OVERFLOW);
         }
         __syncwarp();
     }

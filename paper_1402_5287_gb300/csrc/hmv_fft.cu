@@ -82,7 +82,7 @@ __global__ void k_pieces(const uint32_t *__restrict__ limbs, const uint8_t *__re
             o[p] = make_double2(static_cast<double>(t), 0.0);
             sq += static_cast<unsigned long long>(t * t);
         }
-        if (carry != 0) atomicExch(dstat, DEV_OVERFLOW);
+        if (carry != 0) set_status(dstat, DEV_OVERFLOW);
     }
     // warp sum, one atomic per warp
     for (int d = 16; d > 0; d >>= 1) sq += __shfl_down_sync(0xFFFFFFFFu, sq, d);
@@ -194,7 +194,7 @@ __global__ void k_fft_extract(const double2 *__restrict__ c, int n, int S, int P
         if (li < ZW) z[li] |= dig << off;
         if (off + w > 32 && li + 1 < ZW) z[li + 1] |= dig >> (32 - off);
     }
-    if (carry != 0) atomicExch(dstat, DEV_OVERFLOW);
+    if (carry != 0) set_status(dstat, DEV_OVERFLOW);
     int top = -1;
     uint32_t topv = 0;
     for (int q = ZW - 1; q >= 0; --q)

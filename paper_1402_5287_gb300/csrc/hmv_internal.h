@@ -158,6 +158,7 @@ cudaError_t launch_post_group(hmv_plan_s *const *ps, int G);
 // track_max: also fold the rows' bit lengths into the plan's maximum
 cudaError_t launch_final_normalize(hmv_plan_s *p, const int32_t *in, int rhs, int digit_bytes, bool track_max = true);
 cudaError_t launch_schoolbook(hmv_plan_s *p, const uint32_t *x_limbs, const uint8_t *x_neg, int rhs);
+bool schoolbook_smem_fits(int L32);
 cudaError_t launch_round(hmv_plan_s *p, int rows, int e_in, uint32_t *y_limbs, uint8_t *y_neg);
 cudaError_t make_tensor_maps(hmv_plan_s *p);
 // FFT path (hmv_fft.cu)

@@ -28,6 +28,11 @@ constexpr int TN_DEFAULT = 256;
 // Device error codes written to the plan's status word.
 enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BADINPUT = 2, DEV_OVERFLOW = 3 };
 
+// Records a failure in the status word; the first failure of a call stays
+// (kernels that run after a failed stage may meet inconsistent data and must
+// not replace the code of the failure that caused it).
+__device__ __forceinline__ void set_status(int32_t *dstat, int code) { atomicCAS(dstat, DEV_OK, code); }
+
 struct Tile {
     int leaf, i0, ub, cost, prob;  // prob: index into the launch's LeafProblem array
 };

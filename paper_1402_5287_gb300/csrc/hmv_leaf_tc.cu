@@ -36,8 +36,11 @@
 // tile's last s-block, when it holds only one or two K = 16 groups below
 // s_max, is issued with the block below it (j-steps of 9 or 10 MMAs instead
 // of separate steps of 1 or 2, which the issuing threads cannot keep up with).
-// Every wait is bounded; on a timeout the kernel records DEV_TIMEOUT, drains
-// and frees its TMEM, and returns.
+// Every wait is bounded (wait_ns, 2 s by default) and gives up early once
+// another role of the CTA has failed; on a timeout the kernel records
+// DEV_TIMEOUT, waits for its own MMAs and for the TMA loads it has issued to
+// complete, frees its TMEM and returns.
+#include <atomic>
 #include <cstring>
 
 #include "hmv_internal.h"
@@ -50,7 +53,6 @@ constexpr int kProducerWarp = 0;
 constexpr int kMmaWarp = 1;
 constexpr int kNumEpiWarps = 4;
 constexpr int kMmaWarp2 = 2 + kNumEpiWarps;  // second issuer of 128-digit tiles
-constexpr uint64_t kTimeoutNs = 2000000000ull;  // 2 s for any single wait
 // Tile width in product digits: 256 (one 128x256 MMA per k-step) or 128
 // (narrow operands, where the wide tile's triangular edges waste more).
 template <int TNv>
@@ -144,13 +146,23 @@ __device__ __forceinline__ int window_span(const TileInfo &ti, int sb) {
 template <class S>
 __device__ __forceinline__ void fail(S &sm, int32_t *dstat) {
     sm.abort = 1;
-    atomicExch(dstat, DEV_TIMEOUT);
+    set_status(dstat, DEV_TIMEOUT);
+}
+
+// Bounded wait for the latest TMA load issued into each slot marked in
+// `pending` (bit s; its phase parity is bit s of `phases`): copies still in
+// flight after an abort must land before the shared memory is released.
+// Earlier loads into a slot have landed: the slot was released before reuse.
+__device__ __forceinline__ void wait_issued_loads(uint64_t *full, uint32_t pending, uint32_t phases, uint64_t wait_ns,
+                                                  int32_t *dstat) {
+    for (int s = 0; pending >> s; ++s)
+        if (((pending >> s) & 1u) && !mbar_wait(&full[s], (phases >> s) & 1u, wait_ns)) set_status(dstat, DEV_TIMEOUT);
 }
 
 template <int TNv>
 __global__ void __launch_bounds__(Geo<TNv>::kThreads, 1)
     k_leaf_tc(const LeafProblem *__restrict__ probs, const Tile *__restrict__ tiles, int ntiles, int *tile_counter,
-              int32_t *dstat) {
+              int32_t *dstat, uint64_t wait_ns, int stall) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     using G = Geo<TNv>;
     constexpr int NI = G::NI;
@@ -188,10 +200,13 @@ __global__ void __launch_bounds__(Geo<TNv>::kThreads, 1)
     if (warp == kProducerWarp) {
         if (lane == 0) {
             int as = 0, aph = 0, bs = 0, bph = 0;
+            // slots whose latest load was issued (bit s) and that load's phase parity
+            uint32_t a_pend = 0, a_phs = 0, b_pend = 0, b_phs = 0;
+            static_assert(A_STAGES <= 32 && B_STAGES <= 32, "one bit per ring slot");
             for (int k = 0; !sm.abort; ++k) {
                 // next tile in list order for the whole grid, handed to this CTA's consumers
                 const int qs = k % kTileQ, qph = (k / kTileQ) & 1;
-                if (!mbar_wait(&sm.tq_empty[qs], qph ^ 1, kTimeoutNs)) { fail(sm, dstat); break; }
+                if (!mbar_wait(&sm.tq_empty[qs], qph ^ 1, wait_ns, &sm.abort)) { fail(sm, dstat); break; }
                 int t = atomicAdd(tile_counter, 1);
                 if (t >= ntiles) t = -1;
                 sm.tile_q[qs] = t;
@@ -206,21 +221,30 @@ __global__ void __launch_bounds__(Geo<TNv>::kThreads, 1)
                     for (int jc = 0; jc < ti.njc && !sm.abort; ++jc) {
                         const int j0 = jc * JC;
                         const int jn = min(JC, ti.m - j0);
-                        if (!mbar_wait(&sm.a_empty[as], aph ^ 1, kTimeoutNs)) { fail(sm, dstat); break; }
+                        if (!mbar_wait(&sm.a_empty[as], aph ^ 1, wait_ns, &sm.abort)) { fail(sm, dstat); break; }
                         mbar_arrive_expect_tx(&sm.a_full[as], G::AB);
                         tma_load_4d(sm.a[as], mapA, &sm.a_full[as], 0, (ti.i0 + j0) / 32, (Dp - s_lo - G::KF) / 8,
                                     ti.leaf);
+                        a_pend |= 1u << as;
+                        a_phs = (a_phs & ~(1u << as)) | (static_cast<uint32_t>(aph) << as);
                         if (++as == A_STAGES) { as = 0; aph ^= 1; }
                         for (int jj = 0; jj < jn; ++jj) {
-                            if (!mbar_wait(&sm.b_empty[bs], bph ^ 1, kTimeoutNs)) { fail(sm, dstat); break; }
+                            if (!mbar_wait(&sm.b_empty[bs], bph ^ 1, wait_ns, &sm.abort)) { fail(sm, dstat); break; }
                             mbar_arrive_expect_tx(&sm.b_full[bs], B_BYTES);
                             tma_load_4d(sm.b[bs], mapB, &sm.b_full[bs], 0, (ti.u0 - s_lo - G::KF) / 8 + 1, j0 + jj,
                                         ti.leaf);
+                            b_pend |= 1u << bs;
+                            b_phs = (b_phs & ~(1u << bs)) | (static_cast<uint32_t>(bph) << bs);
                             if (++bs == B_STAGES) { bs = 0; bph ^= 1; }
                         }
                     }
                 }
             }
+            // every load issued has landed before the shared memory is released
+            // (without an abort the issuers have waited for all of them already;
+            // another role may abort after this thread has left its loop)
+            wait_issued_loads(sm.a_full, a_pend, a_phs, wait_ns, dstat);
+            wait_issued_loads(sm.b_full, b_pend, b_phs, wait_ns, dstat);
         }
     } else if (warp == kMmaWarp && NI == 1) {
         if (lane == 0) {
@@ -230,7 +254,7 @@ __global__ void __launch_bounds__(Geo<TNv>::kThreads, 1)
             const uint32_t b_base0 = smem_u32(sm.b[0]);
             for (int k = 0; !sm.abort; ++k) {
                 const int qs = k % kTileQ, qph = (k / kTileQ) & 1;
-                if (!mbar_wait(&sm.tq_full[qs], qph, kTimeoutNs)) { fail(sm, dstat); break; }
+                if (!mbar_wait(&sm.tq_full[qs], qph, wait_ns, &sm.abort)) { fail(sm, dstat); break; }
                 const int t = sm.tile_q[qs];
                 mbar_arrive(&sm.tq_empty[qs]);
                 if (t < 0) break;
@@ -240,14 +264,14 @@ __global__ void __launch_bounds__(Geo<TNv>::kThreads, 1)
                 for (int sb = 0; sb < ti.nsb && !sm.abort; ++sb) {
                     for (int jc = 0; jc < ti.njc && !sm.abort; ++jc) {
                         const int jn = min(JC, ti.m - jc * JC);
-                        if (!mbar_wait(&sm.a_full[as], aph, kTimeoutNs)) { fail(sm, dstat); break; }
+                        if (!mbar_wait(&sm.a_full[as], aph, wait_ns, &sm.abort)) { fail(sm, dstat); break; }
                         const uint32_t a_base = a_base0 + as * G::AB;
                         for (int jj = 0; jj < jn; ++jj) {
                             if (q % FLUSH_J == 0) {
-                                if (!mbar_wait(&sm.acc_empty[0][ab], accph[ab] ^ 1, kTimeoutNs)) { fail(sm, dstat); break; }
+                                if (!mbar_wait(&sm.acc_empty[0][ab], accph[ab] ^ 1, wait_ns, &sm.abort)) { fail(sm, dstat); break; }
                                 acc_flag = 0;
                             }
-                            if (!mbar_wait(&sm.b_full[bs], bph, kTimeoutNs)) { fail(sm, dstat); break; }
+                            if (!mbar_wait(&sm.b_full[bs], bph, wait_ns, &sm.abort)) { fail(sm, dstat); break; }
                             tc_fence_after();
                             const uint32_t b_base = b_base0 + bs * B_BYTES;
                             const uint32_t d_tmem = tmem + ab * TN;
@@ -272,7 +296,7 @@ __global__ void __launch_bounds__(Geo<TNv>::kThreads, 1)
             }
             // all MMAs issued by this thread complete before TMEM is released
             mma_commit(&sm.drain[0]);
-            if (!mbar_wait(&sm.drain[0], 0, kTimeoutNs)) fail(sm, dstat);
+            if (!mbar_wait(&sm.drain[0], 0, wait_ns)) fail(sm, dstat);
         }
     } else if (NI == 2 && (warp == kMmaWarp || warp == kMmaWarp2)) {
         // issuer w takes the tile's j-steps q = w, w + 2, ... (q counts the
@@ -293,7 +317,7 @@ __global__ void __launch_bounds__(Geo<TNv>::kThreads, 1)
             const uint32_t tmem_w = tmem + static_cast<uint32_t>(w * 2 * TN);
             for (int k = 0; !sm.abort; ++k) {
                 const int qs = k % kTileQ, qph = (k / kTileQ) & 1;
-                if (!mbar_wait(&sm.tq_full[qs], qph, kTimeoutNs)) { fail(sm, dstat); break; }
+                if (!mbar_wait(&sm.tq_full[qs], qph, wait_ns, &sm.abort)) { fail(sm, dstat); break; }
                 const int t = sm.tile_q[qs];
                 mbar_arrive(&sm.tq_empty[qs]);
                 if (t < 0) break;
@@ -310,7 +334,7 @@ __global__ void __launch_bounds__(Geo<TNv>::kThreads, 1)
                         const int j0 = jc * JC;
                         const int jn = min(JC, ti.m - j0);
                         const int q0 = sb * ti.m + j0;  // tile step of jj = 0
-                        if (!mbar_wait(&sm.a_full[as], aph, kTimeoutNs)) { fail(sm, dstat); break; }
+                        if (!mbar_wait(&sm.a_full[as], aph, wait_ns, &sm.abort)) { fail(sm, dstat); break; }
                         const uint64_t adesc_s = adesc0 + static_cast<uint32_t>(as * G::AB + g0 * 2 * kLboA) / 16;
                         for (int jj = (q0 + w) & 1; jj < jn; jj += 2) {
                             if (j0 + jj >= wend) {  // close the open window, open the next (own steps are 2 apart, span >= 12)
@@ -319,14 +343,14 @@ __global__ void __launch_bounds__(Geo<TNv>::kThreads, 1)
                                     accph[ab] ^= 1;
                                     ab ^= 1;
                                 }
-                                if (!mbar_wait(&sm.acc_empty[w][ab], accph[ab] ^ 1, kTimeoutNs)) { fail(sm, dstat); break; }
+                                if (!mbar_wait(&sm.acc_empty[w][ab], accph[ab] ^ 1, wait_ns, &sm.abort)) { fail(sm, dstat); break; }
                                 acc_flag = 0;
                                 open = true;
                                 wend += span;
                             }
                             const unsigned gs = static_cast<unsigned>(gq + q0 + jj);
                             const unsigned bs = gs % B_STAGES;
-                            if (!mbar_wait(&sm.b_full[bs], (gs / B_STAGES) & 1u, kTimeoutNs)) { fail(sm, dstat); break; }
+                            if (!mbar_wait(&sm.b_full[bs], (gs / B_STAGES) & 1u, wait_ns, &sm.abort)) { fail(sm, dstat); break; }
                             tc_fence_after();
                             const uint64_t ad = adesc_s + jj;
                             const uint64_t bd = bdesc0 + (bs * B_BYTES + g0 * 256) / 16;
@@ -349,7 +373,7 @@ __global__ void __launch_bounds__(Geo<TNv>::kThreads, 1)
                 gq += ti.Q;
             }
             mma_commit(&sm.drain[w]);
-            if (!mbar_wait(&sm.drain[w], 0, kTimeoutNs)) fail(sm, dstat);
+            if (!mbar_wait(&sm.drain[w], 0, wait_ns)) fail(sm, dstat);
         }
     } else {
         // epilogue: warp w serves TMEM lanes 32*(w%4) .. +31
@@ -359,9 +383,11 @@ __global__ void __launch_bounds__(Geo<TNv>::kThreads, 1)
         int ab[NI], eph[NI][2];
 #pragma unroll
         for (int w = 0; w < NI; ++w) { ab[w] = 0; eph[w][0] = eph[w][1] = 0; }
-        for (int k = 0; !sm.abort; ++k) {
+        // the warp's 32 lanes wait together and take every decision together
+        // (the TMEM loads below are warp-collective): results are voted
+        for (int k = 0; !__any_sync(0xffffffffu, sm.abort); ++k) {
             const int qs = k % kTileQ, qph = (k / kTileQ) & 1;
-            if (!mbar_wait(&sm.tq_full[qs], qph, kTimeoutNs)) { fail(sm, dstat); break; }
+            if (!__all_sync(0xffffffffu, mbar_wait(&sm.tq_full[qs], qph, wait_ns, &sm.abort))) { fail(sm, dstat); break; }
             const int t = sm.tile_q[qs];
             __syncwarp();
             if (lane == 0) mbar_arrive(&sm.tq_empty[qs]);
@@ -392,11 +418,16 @@ __global__ void __launch_bounds__(Geo<TNv>::kThreads, 1)
                     wa += span;
                 }
                 if (one) {
-                    if (!mbar_wait(&sm.acc_full[0][ab[0]], eph[0][ab[0]], kTimeoutNs)) { fail(sm, dstat); ok = false; break; }
+                    if (!__all_sync(0xffffffffu, mbar_wait(&sm.acc_full[0][ab[0]], eph[0][ab[0]], wait_ns, &sm.abort))) {
+                        fail(sm, dstat);
+                        ok = false;
+                        break;
+                    }
                     eph[0][ab[0]] ^= 1;
                 }
                 if (two) {
-                    if (!mbar_wait(&sm.acc_full[NI - 1][ab[NI - 1]], eph[NI - 1][ab[NI - 1]], kTimeoutNs)) {
+                    if (!__all_sync(0xffffffffu, mbar_wait(&sm.acc_full[NI - 1][ab[NI - 1]], eph[NI - 1][ab[NI - 1]],
+                                                           wait_ns, &sm.abort))) {
                         fail(sm, dstat);
                         ok = false;
                         break;
@@ -440,7 +471,11 @@ __global__ void __launch_bounds__(Geo<TNv>::kThreads, 1)
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) {
-                    if (one) mbar_arrive(&sm.acc_empty[0][ab[0]]);
+                    // test hook (stall != 0): the first epilogue warp of the CTA that takes
+                    // tile 0 keeps issuer 0's first accumulator, so that issuer's wait for
+                    // it runs out and the abort path runs; never set outside tests
+                    const bool keep = stall && t == 0 && g == 0 && warp == 2;
+                    if (one && !keep) mbar_arrive(&sm.acc_empty[0][ab[0]]);
                     if (two) mbar_arrive(&sm.acc_empty[NI - 1][ab[NI - 1]]);
                 }
                 if (one) ab[0] ^= 1;
@@ -460,13 +495,9 @@ __global__ void __launch_bounds__(Geo<TNv>::kThreads, 1)
         }
     }
 
+    // every role has left its loop: the issuers' MMAs have completed (drain
+    // barriers) and, after an abort, so have the producer's loads in flight
     tc_fence_before();
-    __syncthreads();
-    if (sm.abort && threadIdx.x == 0) {
-        // let copies still in flight land before the shared memory goes away
-        const uint64_t t0 = global_ns();
-        while (global_ns() - t0 < 20000000ull) { }
-    }
     __syncthreads();
     tc_fence_after();
     if (warp == kMmaWarp) tmem_dealloc(tmem, G::kTmemCols);
@@ -492,6 +523,14 @@ cudaError_t leaf_tc_prepare() {
     return e;
 }
 
+namespace {
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s for any single wait
+// Test hook state (hmv_test_leaf_stall): launches still to run with the
+// stall, and their wait limit.
+std::atomic<int> g_stall_launches{0};
+std::atomic<uint64_t> g_stall_wait_ns{kWaitNs};
+}  // namespace
+
 cudaError_t launch_leaf_tc_multi(const LeafProblem *probs, const Tile *tiles, int ntiles, int32_t *dstat,
                                  int *tile_counter, cudaStream_t stream, int num_sms, int tn) {
     cudaError_t pe = leaf_tc_prepare();
@@ -500,10 +539,23 @@ cudaError_t launch_leaf_tc_multi(const LeafProblem *probs, const Tile *tiles, in
     if (grid <= 0) return cudaSuccess;
     cudaError_t me = cudaMemsetAsync(tile_counter, 0, sizeof(int), stream);
     if (me != cudaSuccess) return me;
+    int stall = 0;
+    uint64_t wait_ns = kWaitNs;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) cap = cudaStreamCaptureStatusActive;
+    // a captured launch would keep the hook in every replay of its graph: only direct launches take it
+    for (int left = cap == cudaStreamCaptureStatusNone ? g_stall_launches.load() : 0; left > 0;)
+        if (g_stall_launches.compare_exchange_weak(left, left - 1)) {
+            stall = 1;
+            wait_ns = g_stall_wait_ns.load();
+            break;
+        }
     if (tn == 128)
-        k_leaf_tc<128><<<grid, Geo<128>::kThreads, sizeof(Smem<128>), stream>>>(probs, tiles, ntiles, tile_counter, dstat);
+        k_leaf_tc<128><<<grid, Geo<128>::kThreads, sizeof(Smem<128>), stream>>>(probs, tiles, ntiles, tile_counter, dstat,
+                                                                                wait_ns, stall);
     else
-        k_leaf_tc<256><<<grid, Geo<256>::kThreads, sizeof(Smem<256>), stream>>>(probs, tiles, ntiles, tile_counter, dstat);
+        k_leaf_tc<256><<<grid, Geo<256>::kThreads, sizeof(Smem<256>), stream>>>(probs, tiles, ntiles, tile_counter, dstat,
+                                                                                wait_ns, stall);
     return cudaGetLastError();
 }
 
@@ -597,3 +649,10 @@ cudaError_t make_tensor_maps(hmv_plan_s *p) {
 }
 
 }  // namespace hmv
+
+extern "C" hmv_status hmv_test_leaf_stall(int32_t launches, int64_t wait_ns) {
+    if (launches < 0 || wait_ns < 1000000 || wait_ns > 2000000000) return HMV_EINVAL;
+    hmv::g_stall_wait_ns.store(static_cast<uint64_t>(wait_ns));
+    hmv::g_stall_launches.store(launches);
+    return HMV_OK;
+}

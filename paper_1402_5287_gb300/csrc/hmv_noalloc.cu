@@ -54,11 +54,13 @@ __global__ void k_check_bits(const uint32_t *limbs, int rows, int L32, int b, in
     if (k >= rows) return;
     const int topbits = b - 32 * (L32 - 1);
     if (topbits < 32 && (limbs[static_cast<size_t>(k) * L32 + L32 - 1] >> topbits) != 0)
-        atomicExch(dstat, DEV_BADINPUT);
+        set_status(dstat, DEV_BADINPUT);
 }
 
 // Device address of g_scratch on the current device, looked up once per
-// device (host code cannot use the symbol's name as an address).
+// device, on the first call made with that device current (host code cannot
+// use the symbol's name as an address).  A cudaDeviceReset unloads the
+// module, so the cached address is not valid after one: the header says so.
 cudaError_t scratch_address(void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -89,12 +91,18 @@ extern "C" hmv_status hmv_schoolbook_noalloc(int32_t n, int32_t b, int32_t kind,
     const int L32 = (b + 31) / 32;
     const Layout l = layout(n, L32);
     if (l.total > HMV_NOALLOC_SCRATCH_BYTES) return HMV_EINVAL;  // beyond the compiled-in scratch
+    if (!schoolbook_smem_fits(L32)) return HMV_EINVAL;           // a row's operands exceed shared memory
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the call copies to host memory and synchronises the stream, neither of
+    // which a capturing stream allows: refuse before queuing anything
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return HMV_ECUDA;
+    if (cap != cudaStreamCaptureStatusNone) return HMV_EINVAL;
     void *base = nullptr;
     cudaError_t e = scratch_address(&base);
     if (e != cudaSuccess) return HMV_ECUDA;
     unsigned char *s = static_cast<unsigned char *>(base);
     int32_t *dstat = reinterpret_cast<int32_t *>(s + l.dstat);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int hlen = (kind == HMV_CIRCULANT) ? n : 2 * n - 1;
     // the status words must start at zero; everything else is fully written
     e = cudaMemsetAsync(dstat, 0, 16 * sizeof(int32_t), st);

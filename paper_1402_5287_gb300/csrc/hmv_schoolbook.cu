@@ -61,6 +61,18 @@ cudaError_t launch_schoolbook(hmv_plan_s *p, const uint32_t *x_limbs, const uint
     return cudaGetLastError();
 }
 
+// Whether the kernel's dynamic shared memory (both operands' limbs of one
+// row, 2 L32 words) fits the current device's opt-in limit per block.
+bool schoolbook_smem_fits(int L32) {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return static_cast<size_t>(2) * L32 * sizeof(uint32_t) <= static_cast<size_t>(optin);
+}
+
 // Same kernel on caller-given buffers (used by the scratch-free entry point).
 cudaError_t launch_schoolbook_raw(const uint32_t *hl, const uint8_t *hn, const uint32_t *xl, const uint8_t *xn, int n,
                                   int L32, int circ, __int128 *colsum, cudaStream_t stream) {

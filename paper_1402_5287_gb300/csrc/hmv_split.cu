@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(256) k_div_exact(uint32_t *__restrict__ zmag, 
         z[w] = static_cast<uint32_t>(q);
         if (bits == 0 && q != 0) bits = 32 * w + (32 - __clz(static_cast<uint32_t>(q)));
     }
-    if (lane == 31 && r != 0) atomicExch(dstat, DEV_OVERFLOW);  // the lowest segment ends the division
+    if (lane == 31 && r != 0) set_status(dstat, DEV_OVERFLOW);  // the lowest segment ends the division
     if (!kBits) return;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) bits = max(bits, __shfl_xor_sync(0xffffffffu, bits, off));

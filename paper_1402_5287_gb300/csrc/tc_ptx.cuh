@@ -55,6 +55,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64
         if (global_ns() - t0 > timeout_ns) return false;
     }
 }
+// The same wait, which also gives up as soon as *abort is set (another role
+// of the CTA has failed, so the phase it waits for may never complete).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t timeout_ns,
+                                          const volatile int *abort) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort || global_ns() - t0 > timeout_ns) return false;
+    }
+}
 
 // ------------------------------------------------------------------ TMA
 __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,

@@ -114,6 +114,8 @@ def load_library(path: str = LIB_PATH):
         lib.hmv_batch_free.restype = None
         lib.hmv_plan_bytes.argtypes = [ctypes.POINTER(Desc), ctypes.POINTER(ctypes.c_uint64)]
         lib.hmv_plan_bytes.restype = ctypes.c_int
+        lib.hmv_test_leaf_stall.argtypes = [i32, ctypes.c_int64]
+        lib.hmv_test_leaf_stall.restype = ctypes.c_int
         lib.hmv_matvec_many.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(Vec), ctypes.POINTER(Vec)]
         lib.hmv_matvec_many.restype = ctypes.c_int
         lib.hmv_dot.argtypes = [vp, ctypes.POINTER(Vec), ctypes.POINTER(Vec), ctypes.POINTER(ctypes.c_uint32), i32,
@@ -151,6 +153,13 @@ def schoolbook_noalloc(n: int, b: int, kind: int, h_ptrs: tuple[int, int], h_exp
                                       x_exponent, y_ptrs[0], y_ptrs[1], ctypes.byref(e), s),
            "hmv_schoolbook_noalloc")
     return int(e.value)
+
+
+def arm_leaf_stall(launches: int, wait_ns: int = 20_000_000) -> None:
+    """hmv_test_leaf_stall: the next `launches` direct leaf launches hold back
+    one accumulator release and limit every wait to wait_ns (tests of the
+    failure path only; 0 disarms)."""
+    _check(load_library().hmv_test_leaf_stall(launches, wait_ns), "hmv_test_leaf_stall")
 
 
 def plan_bytes(n: int, b: int, kind: int = HANKEL, method: int = AUTO, levels: int = -1, nrhs: int = 1,

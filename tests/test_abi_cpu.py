@@ -117,3 +117,12 @@ def test_toom8_depth_bound_without_gpu(lib):
     with pytest.raises(hmv.HmvError):
         hmv.plan_bytes(20000, 33220, flags=hmv.FLAG_DIGIT_TOOM8)
     assert hmv.plan_bytes(20000, 33220) > 0
+
+
+def test_leaf_stall_hook_checks_its_arguments(lib):
+    """The failure-path test hook validates its arguments on the host (no GPU
+    work is queued by it)."""
+    assert lib.hmv_test_leaf_stall(-1, 20_000_000) == 1
+    assert lib.hmv_test_leaf_stall(1, 10) == 1            # below the 1 ms floor
+    assert lib.hmv_test_leaf_stall(1, 3_000_000_000) == 1  # above the 2 s default
+    assert lib.hmv_test_leaf_stall(0, 20_000_000) == 0     # disarmed

@@ -170,6 +170,23 @@ def test_block_rhs_shares_one_exponent():
     assert_same(Y, FixedVec(yl, yn, b, e))
 
 
+@pytest.mark.parametrize("n,b,flags", [(300, 4096, 0), (257, 2048, hmv.FLAG_DIGIT_TOOM4)])
+def test_block_of_eight_rhs_all_rows(n, b, flags):
+    """A block of eight right-hand sides (block Lanczos) on the cost model's
+    plan: every row of every vector against the oracle, one shared exponent."""
+    k = 8
+    h = rand_vec(61 + n, 0, 2 * n - 1, b)
+    parts = [rand_vec(61 + n + r, 1, n, b) for r in range(k)]
+    X = FixedVec(np.concatenate([p.limbs for p in parts]), np.concatenate([p.neg for p in parts]), b, 0)
+    with hmv.Plan(n, b, nrhs=k, flags=flags) as p:
+        p.load_matrix(h)
+        Y = p.matvec(X)
+    zs = [oracle.exact_rows(oracle.HANKEL, n, b, h, part, None, THREADS) for part in parts]
+    yl, yn, e = oracle.round_rows(np.concatenate([zz[0] for zz in zs]), np.concatenate([zz[1] for zz in zs]),
+                                  b, h.exponent)
+    assert_same(Y, FixedVec(yl, yn, b, e))
+
+
 def test_invalid_inputs_are_rejected():
     n, b = 10, 70
     h = rand_vec(41, 0, 2 * n - 1, b)
@@ -222,26 +239,45 @@ def test_device_pointer_api_matches_host_api():
 
 # ---------------------------------------------------------------- full-size workloads, sampled rows
 
-def sampled_parity(kind, n, h, x, y: FixedVec, nsample, seed):
+def sample_rows(n, nsample, seed, extra=(), residues=0):
+    """Seeded random rows plus rows 0 and n-1, the given extra rows and, with
+    residues = 2^L, at least one row of every class i mod 2^L (the output
+    rows of one class take the same path through L levels of Algorithm 1)."""
+    rng = random.Random(seed)
+    rows = set(rng.sample(range(n), min(nsample, n))) | {0, n - 1} | set(extra)
+    for r in range(min(residues, n)):
+        if not any(i % residues == r for i in rows):
+            rows.add(r + residues * rng.randrange((n - 1 - r) // residues + 1))
+    return sorted(rows)
+
+
+def sampled_parity(kind, n, h, x, y: FixedVec, nsample, seed, residues=0):
     """Bit-exact check of sampled rows, including every row that attains the
     largest output mantissa (so the exponent choice is checked too)."""
     b = h.b
-    rng = random.Random(seed)
     mags = [int.from_bytes(y.limbs[i].tobytes(), "little") for i in range(n)]
     top = max(mags)
-    rows = sorted(set(rng.sample(range(n), min(nsample, n)) + [0, n - 1] + [i for i in range(n) if mags[i] == top][:4]))
+    rows = sample_rows(n, nsample, seed, [i for i in range(n) if mags[i] == top][:4], residues)
     z, zn = oracle.exact_rows(kind, n, b, h, x, rows, THREADS)
     shift = y.exponent + b - (h.exponent + x.exponent)
     yl, yn = oracle.round_rows_fixed(z, zn, b, shift)
-    assert np.array_equal(yl, y.limbs[rows]) and np.array_equal(yn, y.neg[rows])
+    bad = [rows[k] for k in range(len(rows)) if not (np.array_equal(yl[k], y.limbs[rows[k]]) and yn[k] == y.neg[rows[k]])]
+    assert not bad, f"{len(bad)} of {len(rows)} sampled rows differ, first {bad[:10]}"
     yl2, yn2, e2 = oracle.round_rows(z, zn, b, h.exponent + x.exponent)
     assert e2 == y.exponent
+    return rows
 
 
-def test_hilbert_workload_sampled():
+def test_hilbert_workload_all_rows():
+    """n = 1024, b = 33220 (the Hilbert Hankel h_k = 1/(k+1)) on the cost
+    model's plan: every row against the oracle."""
     n, b, h, x = workload("hilbert")
-    y = run(n, b, h, x)
-    sampled_parity(oracle.HANKEL, n, h, x, y, 12, 1)
+    with hmv.Plan(n, b) as p:
+        p.load_matrix(h)
+        y = p.matvec(x)
+        st = p.stats()
+    assert st["digit_products"] > 1  # the cost model splits the mantissas here
+    assert_same(y, oracle_matvec(oracle.HANKEL, n, h, x))
     # the closed form: |y_i| < sum_j |x_j|/(i+j+1) + slack <= H_n, so E_y <= 3
     assert y.exponent <= 3
 
@@ -261,7 +297,8 @@ def test_large_workload_sampled_hankel_and_toeplitz():
         y = p.matvec(x)
         st = p.stats()
     assert st["levels"] == 6 and st["leaf_rows_max"] <= 128
-    sampled_parity(oracle.HANKEL, n, h, x, y, 10, 2)
+    rows = sampled_parity(oracle.HANKEL, n, h, x, y, 256, 2, residues=1 << st["levels"])
+    assert len(rows) >= 256 and len({i % 64 for i in rows}) == 64
     with hmv.Plan(n, b, kind=hmv.TOEPLITZ) as p:
         p.load_matrix(h)
         yt = p.matvec(x)

@@ -23,7 +23,9 @@ def plan_schoolbook(n, b, kind, h, x):
         return p.matvec(x)
 
 
-def noalloc(n, b, kind, h, x):
+def noalloc_call(n, b, kind, h, x, stream=None):
+    """Calls the entry point on device copies of h and x with y preset to a
+    fill pattern; returns (status, E_y or None, y limbs, y signs)."""
     torch = pytest.importorskip("torch")
     dev = torch.device("cuda:0")
     hl = torch.from_numpy(h.limbs.view(np.int32)).to(dev)
@@ -33,10 +35,22 @@ def noalloc(n, b, kind, h, x):
     yl = torch.full_like(xl, -1)
     yn = torch.full_like(xn, 7)
     torch.cuda.synchronize()
-    e = hmv.schoolbook_noalloc(n, b, kind, (hl.data_ptr(), hn.data_ptr()), h.exponent,
-                               (xl.data_ptr(), xn.data_ptr()), x.exponent, (yl.data_ptr(), yn.data_ptr()),
-                               torch.cuda.current_stream().cuda_stream)
-    return FixedVec(yl.cpu().numpy().view(np.uint32), yn.cpu().numpy(), b, e)
+    s = torch.cuda.current_stream().cuda_stream if stream is None else stream
+    try:
+        e = hmv.schoolbook_noalloc(n, b, kind, (hl.data_ptr(), hn.data_ptr()), h.exponent,
+                                   (xl.data_ptr(), xn.data_ptr()), x.exponent, (yl.data_ptr(), yn.data_ptr()), s)
+        status = 0
+    except hmv.HmvError as err:
+        e, status = None, err.status
+    torch.cuda.synchronize()
+    return status, e, yl.cpu().numpy().view(np.uint32), yn.cpu().numpy()
+
+
+def noalloc(n, b, kind, h, x):
+    status, e, yl, yn = noalloc_call(n, b, kind, h, x)
+    if status:
+        raise hmv.HmvError(status, "hmv_schoolbook_noalloc")
+    return FixedVec(yl, yn, b, e)
 
 
 def same(a, b):
@@ -69,3 +83,31 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     h = uniform_vec(10, 0, 2 * n - 1, b)
     x = uniform_vec(10, 1, n, b)
     assert same(noalloc(n, b, hmv.HANKEL, h, x), plan_schoolbook(n, b, hmv.HANKEL, h, x))
+
+
+def test_noalloc_rejects_bits_at_or_above_b_and_writes_nothing():
+    pkg.build()
+    n, b = 20, 300
+    h = uniform_vec(11, 0, 2 * n - 1, b)
+    x = uniform_vec(11, 1, n, b)
+    bad = FixedVec(x.limbs.copy(), x.neg, b, 0)
+    bad.limbs[7, -1] |= np.uint32(1 << (b % 32))  # bit b of entry 7
+    status, e, yl, yn = noalloc_call(n, b, hmv.HANKEL, h, bad)
+    assert status == 1 and e is None
+    assert (yl == 0xFFFFFFFF).all() and (yn == 7).all()
+    badh = FixedVec(h.limbs.copy(), h.neg, b, 0)
+    badh.limbs[2 * n - 2, -1] |= np.uint32(1 << 31)
+    status, e, yl, yn = noalloc_call(n, b, hmv.TOEPLITZ, badh, x)
+    assert status == 1 and (yl == 0xFFFFFFFF).all() and (yn == 7).all()
+    assert same(noalloc(n, b, hmv.HANKEL, h, x), plan_schoolbook(n, b, hmv.HANKEL, h, x))
+
+
+def test_noalloc_rejects_rows_beyond_shared_memory():
+    """b = 2^20 with n = 1 fits the scratch array, but one row's operands
+    (8 * 32768 bytes) exceed the 227 KB of shared memory a block may use."""
+    pkg.build()
+    n, b = 1, 1 << 20
+    h = uniform_vec(12, 0, 1, b)
+    x = uniform_vec(12, 1, 1, b)
+    status, e, yl, yn = noalloc_call(n, b, hmv.HANKEL, h, x)
+    assert status == 1 and (yl == 0xFFFFFFFF).all() and (yn == 7).all()
