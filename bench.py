@@ -7,6 +7,12 @@ JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+The default line (N = 1) also carries the comparisons a user of the library
+asks for, each measured in the same run: the plain schoolbook GPU kernel on
+the same inputs (vs_plain_kernel), the batched workload of 64 matrices x 8
+right-hand sides (batched) and a short Poisson serving run (serving);
+--no-extras leaves them out.
+
 --impl reference times the CPU oracle (the plain schoolbook definition,
 threaded over rows) on a bounded sample of rows of the same workload.
 """
@@ -255,10 +261,15 @@ def run_ours(args):
             peaks = json.load(f)
     except OSError:
         pass
-    peak = peaks.get("bf16_tflops_sustained")
-    peak_src = "measured sustained bf16 (MEASURED_PEAKS.json)"
+    # the leaf is one launch of about 55 ms per matvec, timed launch by launch:
+    # the burst figure is its denominator; the sustained one (a seconds-long
+    # cuBLAS loop under the power cap) is reported beside it
+    peak = peaks.get("bf16_tflops")
+    peak_src = "of measured: burst bf16 (MEASURED_PEAKS.json)"
     if peak is None:
-        peak, peak_src = 1700.0, "fallback sustained bf16"
+        peak, peak_src = 1900.0, "of fallback: burst bf16"
+    peak_sust = peaks.get("bf16_tflops_sustained") or 1700.0
+    issued_over_useful = st["leaf_macs_issued"] / st["leaf_macs"] if st["leaf_macs"] else None
 
     traffic = leaf_traffic(st["leaf_tiles"], n, b)
 
@@ -272,10 +283,12 @@ def run_ours(args):
         xv = hmv.Vec(n, 1, b, x.exponent, pin_x_l.data_ptr(), pin_x_n.data_ptr(), 0, 0)
         yv = hmv.Vec(n, 1, b, 0, pin_y_l.data_ptr(), pin_y_n.data_ptr(), 0, 0)
         import ctypes
-        for _ in range(1):
+        for _ in range(max(args.warmup, 1)):
             plan.lib.hmv_matvec(plan.handle, ctypes.byref(xv), ctypes.byref(yv))
-        k2 = max(1, min(args.steps, 5))
+        k2 = max(1, args.steps)
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
         t0 = time.perf_counter()
         for _ in range(k2):
             rc = plan.lib.hmv_matvec(plan.handle, ctypes.byref(xv), ctypes.byref(yv))
@@ -283,8 +296,9 @@ def run_ours(args):
                 raise RuntimeError(f"hmv_matvec failed: {rc}")
         t_e2e = time.perf_counter() - t0
         t_e2e = reduce_max(dist, t_e2e)
-        e2e = {"value": aggregate_rate(k2, world, t_e2e), "unit": UNIT,
-               "h2d_bytes_per_step": n * L32 * 4 + n, "d2h_bytes_per_step": n * L32 * 4 + n}
+        e2e = {"value": aggregate_rate(k2, world, t_e2e), "unit": UNIT, "steps": k2,
+               "h2d_bytes_per_step": n * L32 * 4 + n, "d2h_bytes_per_step": n * L32 * 4 + n,
+               "timing": "wall clock around synchronous hmv_matvec calls with pinned host x and y"}
     plan.close()
 
     comparisons = {}
@@ -297,6 +311,15 @@ def run_ours(args):
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{rows} random rows of the n={n}, b={b} product ({t_used:.1f} s on {cores} threads); "
                          f"matvecs/s extrapolated from rows/s"}
+
+    extras = {}
+    if rank == 0 and world == 1 and not args.no_extras and (n, b) == (8000, 33220):
+        plain = measure_plain_kernel(hmv, h, x, n, b, stream)
+        plain["factor"] = value / plain["value"]
+        extras["vs_plain_kernel"] = plain
+        extras["batched"] = measure_batched(3, 1, args.wave_gb)
+        extras["serving"] = measure_serving(args.extra_requests, args.rate, args.matvecs_per_request,
+                                            args.serve_gb, False)
 
     if rank != 0:
         return 0
@@ -319,7 +342,10 @@ def run_ours(args):
                      "kernel": "k_leaf_tc", "peak_source": peak_src,
                      "flops_per_launch": flops_per_launch, "launch_ms": leaf_ms,
                      "launches_per_matvec": launches_per_mv,
-                     "issued_over_useful": st["leaf_macs_issued"] / st["leaf_macs"] if st["leaf_macs"] else None},
+                     "issued_over_useful": issued_over_useful,
+                     # the MMAs the tensor pipe actually ran (band edges included)
+                     "frac_issued": achieved_tflops * issued_over_useful / peak if issued_over_useful else None,
+                     "peak_sustained": peak_sust, "frac_of_sustained": achieved_tflops / peak_sust},
         "stage_ms": {"prepass": st["ms_prepass"] / max(st["matvecs"], 1), "leaf": st["ms_leaf"] / max(st["matvecs"], 1),
                      "post": st["ms_post"] / max(st["matvecs"], 1), "round": st["ms_round"] / max(st["matvecs"], 1)},
         # the plain definition's work (n^2 products of D = ceil(b/8)-digit numbers, D^2 digit
@@ -332,6 +358,7 @@ def run_ours(args):
         "e2e": e2e,
         "cpu_baseline": cpu,
     }
+    line.update(extras)
     if comparisons:
         line["comparisons"] = comparisons
     print(json.dumps(line), flush=True)
@@ -441,17 +468,17 @@ def batched_workload(count=64, nrhs=8):
     return probs
 
 
-def run_batched(args):
+def measure_batched(steps, warmup, wave_gb):
+    """Config 4: 64 matrices x 8 right-hand sides per hmv_batch_matvec call
+    (one CUDA graph launch), device-resident inputs; wall clock per call."""
     import torch
 
-    import paper_1402_5287_gb300 as pkg
     from paper_1402_5287_gb300 import hmv
-    pkg.build()
     nrhs = 8
     probs = batched_workload(64, nrhs)
     specs = [dict(n=n, b=b, nrhs=nrhs) for n, b, _, _ in probs]
     stream = torch.cuda.Stream()
-    bt = hmv.Batch(specs, stream=stream.cuda_stream, wave_bytes=args.wave_gb << 30)
+    bt = hmv.Batch(specs, stream=stream.cuda_stream, wave_bytes=wave_gb << 30)
     for i, (_, _, h, _) in enumerate(probs):
         bt.load_matrix(i, h)
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -463,27 +490,37 @@ def run_batched(args):
     yp = [(a.data_ptr(), c.data_ptr()) for a, c in ys]
     ex = [x.exponent for *_, x in probs]
     torch.cuda.synchronize()
-    for _ in range(max(args.warmup, 1)):
+    for _ in range(max(warmup, 1)):
         bt.matvec_device(xp, yp, ex)
     t0 = time.perf_counter()
     with ClockSampler(torch.cuda.current_device()) as clocks:
-        for _ in range(args.steps):
+        for _ in range(steps):
             bt.matvec_device(xp, yp, ex)
     secs = time.perf_counter() - t0
     info = bt.info()
     bt.close()
-    mv = 64 * nrhs * args.steps
-    line = {"metric": "batched Hankel matvecs/s (64 matrices x 8 right-hand sides)", "value": mv / secs,
-            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 1),
-            "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+    mv = 64 * nrhs * steps
+    return {"value": mv / secs, "unit": UNIT, "steps": steps, "warmup": max(warmup, 1),
+            "ms_per_step": secs / steps * 1e3,
+            "workload": "64 Hankel matrices, n ~ U[32,2048], b in {4096,16384,33220}, 8 RHS each, "
+                        "uniform fixed-point in (-1,1); one CUDA graph launch per step",
+            "waves": info["waves"], "pairs": info["pairs"], "leaf_tiles": info["leaf_tiles"],
+            "kernels_per_graph": info["kernels_per_graph"], "wave_budget_gb": wave_gb,
+            "device_gb": info["device_bytes"] / 1e9,
+            "useful_leaf_tflops": 2 * info["leaf_macs"] * steps / secs / 1e12, "clocks": clocks.summary()}
+
+
+def run_batched(args):
+    import paper_1402_5287_gb300 as pkg
+    pkg.build()
+    r = measure_batched(args.steps, args.warmup, args.wave_gb)
+    line = {"metric": "batched Hankel matvecs/s (64 matrices x 8 right-hand sides)", "value": r["value"],
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": r["warmup"],
+            "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": "64 Hankel matrices, n ~ U[32,2048], b in {4096,16384,33220}, 8 RHS each, "
-                                   "uniform fixed-point in (-1,1); one CUDA graph launch per step",
-                       "waves": info["waves"], "pairs": info["pairs"], "leaf_tiles": info["leaf_tiles"],
-                       "kernels_per_graph": info["kernels_per_graph"], "wave_budget_gb": args.wave_gb,
-                       "device_gb": info["device_bytes"] / 1e9},
-            "useful_leaf_tflops": 2 * info["leaf_macs"] * args.steps / secs / 1e12,
-            "graph_launches_per_step": 1, "clocks": clocks.summary()}
+            "config": {k: r[k] for k in ("workload", "waves", "pairs", "leaf_tiles", "kernels_per_graph",
+                                         "wave_budget_gb", "device_gb")},
+            "useful_leaf_tflops": r["useful_leaf_tflops"], "graph_launches_per_step": 1, "clocks": r["clocks"]}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -528,40 +565,77 @@ def run_lanczos(args):
     return 0
 
 
-def run_serving(args):
+def measure_serving(requests, rate, matvecs_per_request, serve_gb, chains):
+    """Config 5: Poisson arrivals of Lanczos (or chain) requests, continuous
+    batching; matvecs/s and p50/p99 latency per matvec."""
     import random
 
     import torch
 
-    import paper_1402_5287_gb300 as pkg
     from paper_1402_5287_gb300.inputs import BASE_SEED, uniform_vec
     from paper_1402_5287_gb300.serving import Request, Server
-    pkg.build()
     rng = random.Random(BASE_SEED + 4)
     reqs, t = [], 0.0
-    for i in range(args.requests):
-        t += rng.expovariate(args.rate)
+    for i in range(requests):
+        t += rng.expovariate(rate)
         n = rng.randint(64, 4096)
         b = rng.choice([2048, 8192, 33220])
         reqs.append(Request(i, n, b, uniform_vec(BASE_SEED + 4, 2 * i, 2 * n - 1, b, 0),
-                            uniform_vec(BASE_SEED + 4, 2 * i + 1, n, b, 0), args.matvecs_per_request, arrival=t,
-                            lanczos=not args.serve_chains))
-    srv = Server(memory_budget=args.serve_gb << 30)
+                            uniform_vec(BASE_SEED + 4, 2 * i + 1, n, b, 0), matvecs_per_request, arrival=t,
+                            lanczos=not chains))
+    srv = Server(memory_budget=serve_gb << 30)
     with ClockSampler(torch.cuda.current_device()) as clocks:
         st = srv.run(reqs)
-    line = {"metric": "served Hankel matvecs/s with p50/p99 matvec latency", "value": st["matvecs_per_s"],
+    desc = (f"{requests} requests, Poisson arrivals at {rate}/s, n ~ U[64,4096], b in {{2048,8192,33220}}, "
+            + (f"{matvecs_per_request} chained matvecs" if chains else
+               f"{matvecs_per_request} Lanczos steps (one matvec, two exact inner products and one exact "
+               f"update each)")
+            + " per request against a resident A (cap on the 2n of a full Lanczos run)")
+    return {"value": st["matvecs_per_s"], "unit": UNIT, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+            "workload": desc, "memory_budget_gb": serve_gb, "serving": st, "clocks": clocks.summary()}
+
+
+def run_serving(args):
+    import paper_1402_5287_gb300 as pkg
+    pkg.build()
+    r = measure_serving(args.requests, args.rate, args.matvecs_per_request, args.serve_gb, args.serve_chains)
+    line = {"metric": "served Hankel matvecs/s with p50/p99 matvec latency", "value": r["value"],
             "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "vs_baseline": None, "dtype": "bf16",
-            "data": "synthetic", "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-            "config": {"workload": f"{args.requests} requests, Poisson arrivals at {args.rate}/s, n ~ U[64,4096], "
-                                   f"b in {{2048,8192,33220}}, "
-                                   + (f"{args.matvecs_per_request} chained matvecs" if args.serve_chains else
-                                      f"{args.matvecs_per_request} Lanczos steps (one matvec, two exact inner "
-                                      f"products and one exact update each)")
-                                   + " per request against a resident A (cap on the 2n of a full Lanczos run)",
-                       "memory_budget_gb": args.serve_gb},
-            "serving": st, "clocks": clocks.summary()}
+            "data": "synthetic", "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"],
+            "config": {"workload": r["workload"], "memory_budget_gb": r["memory_budget_gb"]},
+            "serving": r["serving"], "clocks": r["clocks"]}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def measure_plain_kernel(hmv, h, x, n, b, stream):
+    """One timed matvec of the plain schoolbook kernel (32-bit limbs, CUDA
+    cores) on the benchmark workload, after a warm-up on a small problem."""
+    import torch
+    from paper_1402_5287_gb300.inputs import uniform_vec
+    hs, xs = uniform_vec(5, 0, 127, 2048, 0), uniform_vec(5, 1, 64, 2048, 0)
+    with hmv.Plan(64, 2048, method=hmv.SCHOOLBOOK, stream=stream.cuda_stream) as p:
+        p.load_matrix(hs)
+        p.matvec(xs)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    plan = hmv.Plan(n, b, method=hmv.SCHOOLBOOK, stream=stream.cuda_stream)
+    plan.load_matrix(h)
+    with torch.cuda.stream(stream):
+        xl = torch.from_numpy(x.limbs.view(np.int32)).to(dev)
+        xn = torch.from_numpy(x.neg).to(dev)
+        yl = torch.empty_like(xl)
+        yn = torch.empty_like(xn)
+    stream.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plan.matvec_device(xl.data_ptr(), xn.data_ptr(), x.exponent, yl.data_ptr(), yn.data_ptr())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plan.close()
+    s = e0.elapsed_time(e1) / 1e3
+    return {"value": 1.0 / s, "unit": UNIT, "ms_per_matvec": s * 1e3, "steps": 1,
+            "kernel": "k_schoolbook (32-bit limbs, CUDA cores), same inputs"}
 
 
 def main(argv=None):
@@ -580,6 +654,10 @@ def main(argv=None):
                     help="leaf tile width in product digits (profiling runs; 0: the plan's default)")
     ap.add_argument("--compare", action="store_true", help="also time the schoolbook comparison kernels")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="leave out the plain-kernel, batched and serving keys of the default line")
+    ap.add_argument("--extra-requests", type=int, default=40,
+                    help="requests of the short serving run in the default line")
     ap.add_argument("--n", type=int, default=None, help="matrix order (profiling runs; default 8000)")
     ap.add_argument("--b", type=int, default=None, help="mantissa bits (profiling runs; default 33220)")
     ap.add_argument("--workload", choices=["matvec", "batched", "serving", "lanczos"], default="matvec",
