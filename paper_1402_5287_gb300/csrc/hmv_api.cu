@@ -296,6 +296,7 @@ void hmv_free(hmv_plan_t *p) {
     if (p->stream) cudaStreamSynchronize(p->stream);
     for (hmv_plan_s *c : p->children) hmv_free(c);
     for (void *a : p->allocations) cudaFree(a);
+    for (hmv::GrowBuf *g : {&p->dot_buf, &p->lin_buf, &p->many_dev, &p->many_host}) hmv::release(*g);
     for (auto &g : p->lv)
         if (g.d_size) cudaFree(g.d_size);
     if (p->timing)
@@ -320,6 +321,29 @@ hmv_status hmv_plan_bytes(const hmv_desc *desc, uint64_t *bytes) {
 }  // extern "C"
 
 namespace hmv {
+
+cudaError_t grow(GrowBuf &g, size_t bytes) {
+    if (bytes <= g.bytes) return cudaSuccess;
+    if (g.ptr) cudaDeviceSynchronize();  // work queued earlier may still use the old buffer
+    release(g);
+    const size_t want = bytes + bytes / 4;  // some room, so that slowly growing calls do not reallocate each time
+    cudaError_t e = g.pinned ? cudaMallocHost(&g.ptr, want) : cudaMalloc(&g.ptr, want);
+    if (e != cudaSuccess) {
+        g.ptr = nullptr;
+        return e;
+    }
+    g.bytes = want;
+    return cudaSuccess;
+}
+
+void release(GrowBuf &g) {
+    if (g.ptr) {
+        if (g.pinned) cudaFreeHost(g.ptr);
+        else cudaFree(g.ptr);
+    }
+    g.ptr = nullptr;
+    g.bytes = 0;
+}
 
 hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch, hmv_plan_s **out,
                        bool dry_run) {

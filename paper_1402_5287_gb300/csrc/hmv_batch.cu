@@ -525,36 +525,49 @@ extern "C" hmv_status hmv_matvec_many(int32_t count, hmv_plan_t *const *plans, c
     }
     std::vector<hmv_plan_s *> leafplans;  // every unsplit plan, split plans contributing their descendants
     for (int i = 0; i < count; ++i) collect_leaf_plans(plans[i], leafplans);
-    // one persistent launch per tile width present (normally one)
-    for (int tn : {256, 128}) {
-        std::vector<LeafProblem> gp;
-        std::vector<Tile> gt;
+    // one persistent launch per tile width present (normally one); the
+    // step's problem and tile lists are staged in pinned host memory and
+    // copied into device memory, both kept by plans[0] and grown on demand
+    // (the previous call ended with a stream synchronisation, so neither is
+    // still in use)
+    std::vector<LeafProblem> gp[2];
+    std::vector<Tile> gt[2];
+    size_t off_p[2], off_t[2], total = 0;
+    auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+    for (int w = 0; w < 2; ++w) {
+        const int tn = w == 0 ? 256 : 128;
         for (hmv_plan_s *c : leafplans) {
             if (c->tn != tn) continue;
-            const int idx = static_cast<int>(gp.size());
-            gp.push_back(c->hprob);
+            const int idx = static_cast<int>(gp[w].size());
+            gp[w].push_back(c->hprob);
             for (Tile t : c->tiles) {
                 t.prob = idx;
-                gt.push_back(t);
+                gt[w].push_back(t);
             }
         }
-        if (gp.empty() || e != cudaSuccess) continue;
-        LeafProblem *dp = nullptr;
-        Tile *dt = nullptr;
-        e = cudaMallocAsync(reinterpret_cast<void **>(&dp), gp.size() * sizeof(LeafProblem), s);
-        if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&dt), gt.size() * sizeof(Tile), s);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(dp, gp.data(), gp.size() * sizeof(LeafProblem), cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dt, gt.data(), gt.size() * sizeof(Tile), cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) {
-            e = launch_leaf_tc_multi(dp, dt, static_cast<int>(gt.size()), plans[0]->dstat, plans[0]->d_counter, s,
-                                     plans[0]->num_sms, tn);
-            plans[0]->launches_leaf++;
+        off_p[w] = total;
+        total += al(gp[w].size() * sizeof(LeafProblem));
+        off_t[w] = total;
+        total += al(gt[w].size() * sizeof(Tile));
+    }
+    hmv_plan_s *lead = plans[0];
+    if (e == cudaSuccess) e = grow(lead->many_dev, total);
+    if (e == cudaSuccess) e = grow(lead->many_host, total);
+    if (e == cudaSuccess) {
+        char *hb = static_cast<char *>(lead->many_host.ptr);
+        for (int w = 0; w < 2; ++w) {
+            memcpy(hb + off_p[w], gp[w].data(), gp[w].size() * sizeof(LeafProblem));
+            memcpy(hb + off_t[w], gt[w].data(), gt[w].size() * sizeof(Tile));
         }
-        // pageable host vectors: the copies above must finish before they go away
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (dp) cudaFreeAsync(dp, s);
-        if (dt) cudaFreeAsync(dt, s);
+        e = cudaMemcpyAsync(lead->many_dev.ptr, hb, total, cudaMemcpyHostToDevice, s);
+    }
+    for (int w = 0; w < 2 && e == cudaSuccess; ++w) {
+        if (gt[w].empty()) continue;
+        char *db = static_cast<char *>(lead->many_dev.ptr);
+        e = launch_leaf_tc_multi(reinterpret_cast<LeafProblem *>(db + off_p[w]), reinterpret_cast<Tile *>(db + off_t[w]),
+                                 static_cast<int>(gt[w].size()), lead->dstat, lead->d_counter, s, lead->num_sms,
+                                 w == 0 ? 256 : 128);
+        lead->launches_leaf++;
     }
     for (int i = 0; i < count && e == cudaSuccess; ++i) {
         hmv_plan_s *p = plans[i];

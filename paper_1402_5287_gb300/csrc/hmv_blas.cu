@@ -135,6 +135,17 @@ __global__ void k_lincomb_colsum(LinTerms t, int n, int L32, int W, __int128 *__
         if (w0 + q < W) colsum[static_cast<size_t>(i) * W + w0 + q] = tot[q];
 }
 
+// Consecutive 256-byte aligned pieces of one buffer.
+struct Carve {
+    size_t off = 0;
+    template <class T>
+    T *take(void *base, size_t count) {
+        T *p = base ? reinterpret_cast<T *>(static_cast<char *>(base) + off) : nullptr;
+        off += (count * sizeof(T) + 255) / 256 * 256;
+        return p;
+    }
+};
+
 bool device_vec(const hmv_vec *v, int n, int b) {
     return v && v->len == n && v->nrhs == 1 && v->b == b && v->limbs && v->neg && v->on_device == 1 && !v->reserved;
 }
@@ -156,13 +167,25 @@ extern "C" hmv_status hmv_dot(hmv_plan_t *p, const hmv_vec *x, const hmv_vec *y,
     uint8_t *zn = nullptr;
     int32_t *zb = nullptr, *st = nullptr;
     const int ZW = W + 2;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&partial), static_cast<size_t>(chunks) * W * 16, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&cols), static_cast<size_t>(W) * 16, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&mag), static_cast<size_t>(ZW) * 4, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&zn), 16, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&zb), 16, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&st), 8 * sizeof(int32_t), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, 8 * sizeof(int32_t), s);
+    // working memory from the plan (allocated by the first call, reused after)
+    Carve size;
+    size.take<__int128>(nullptr, static_cast<size_t>(chunks) * W);
+    size.take<__int128>(nullptr, W);
+    size.take<uint32_t>(nullptr, ZW);
+    size.take<uint8_t>(nullptr, 16);
+    size.take<int32_t>(nullptr, 4);
+    size.take<int32_t>(nullptr, 8);
+    cudaError_t e = grow(p->dot_buf, size.off);
+    if (e == cudaSuccess) {
+        Carve c;
+        partial = c.take<__int128>(p->dot_buf.ptr, static_cast<size_t>(chunks) * W);
+        cols = c.take<__int128>(p->dot_buf.ptr, W);
+        mag = c.take<uint32_t>(p->dot_buf.ptr, ZW);
+        zn = c.take<uint8_t>(p->dot_buf.ptr, 16);
+        zb = c.take<int32_t>(p->dot_buf.ptr, 4);
+        st = c.take<int32_t>(p->dot_buf.ptr, 8);
+        e = cudaMemsetAsync(st, 0, 8 * sizeof(int32_t), s);
+    }
     if (e == cudaSuccess) {
         k_dot_partial<<<dim3((W / 4 + 127) / 128 + 1, chunks), 128, 0, s>>>(x->limbs, x->neg, y->limbs, y->neg, n,
                                                                            L32, partial);  // 4 columns per thread
@@ -175,12 +198,9 @@ extern "C" hmv_status hmv_dot(hmv_plan_t *p, const hmv_vec *x, const hmv_vec *y,
     if (e == cudaSuccess) e = cudaMemcpyAsync(z, mag, static_cast<size_t>(ZW) * 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&sign, zn, 1, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(status, st, sizeof status, cudaMemcpyDeviceToHost, s);
-    for (void *ptr : {static_cast<void *>(partial), static_cast<void *>(cols), static_cast<void *>(mag),
-                      static_cast<void *>(zn), static_cast<void *>(zb), static_cast<void *>(st)})
-        if (ptr) cudaFreeAsync(ptr, s);
     const cudaError_t se = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = se;
-    if (e != cudaSuccess) { cudaGetLastError(); return HMV_ECUDA; }
+    if (e != cudaSuccess) { cudaGetLastError(); return e == cudaErrorMemoryAllocation ? HMV_ENOMEM : HMV_ECUDA; }
     if (status[0] != DEV_OK) return HMV_EINTERNAL;
     for (int w = ZW; w < zl; ++w) z[w] = 0;
     *z_neg = sign;
@@ -231,12 +251,24 @@ extern "C" hmv_status hmv_lincomb(hmv_plan_t *p, int32_t count, const hmv_scalar
     int32_t *zb = nullptr, *st = nullptr;
     int total = 0;
     for (int k = 0; k < count; ++k) total += t.nl[k];
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&dc), static_cast<size_t>(total) * 4, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&cols), static_cast<size_t>(n) * W * 16, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&mag), static_cast<size_t>(n) * ZW * 4, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&zn), n, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&zb), static_cast<size_t>(n) * 4, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&st), 8 * sizeof(int32_t), s);
+    // working memory from the plan (grown when a call needs more, reused after)
+    Carve size;
+    size.take<uint32_t>(nullptr, total);
+    size.take<__int128>(nullptr, static_cast<size_t>(n) * W);
+    size.take<uint32_t>(nullptr, static_cast<size_t>(n) * ZW);
+    size.take<uint8_t>(nullptr, n);
+    size.take<int32_t>(nullptr, n);
+    size.take<int32_t>(nullptr, 8);
+    cudaError_t e = grow(p->lin_buf, size.off);
+    if (e == cudaSuccess) {
+        Carve c;
+        dc = c.take<uint32_t>(p->lin_buf.ptr, total);
+        cols = c.take<__int128>(p->lin_buf.ptr, static_cast<size_t>(n) * W);
+        mag = c.take<uint32_t>(p->lin_buf.ptr, static_cast<size_t>(n) * ZW);
+        zn = c.take<uint8_t>(p->lin_buf.ptr, n);
+        zb = c.take<int32_t>(p->lin_buf.ptr, n);
+        st = c.take<int32_t>(p->lin_buf.ptr, 8);
+    }
     std::vector<uint32_t> flat;
     for (int k = 0; k < count; ++k) flat.insert(flat.end(), shifted[k].begin(), shifted[k].end());
     if (e == cudaSuccess) e = cudaMemcpyAsync(dc, flat.data(), flat.size() * 4, cudaMemcpyHostToDevice, s);
@@ -255,12 +287,9 @@ extern "C" hmv_status hmv_lincomb(hmv_plan_t *p, int32_t count, const hmv_scalar
     }
     int32_t status[8] = {0};
     if (e == cudaSuccess) e = cudaMemcpyAsync(status, st, sizeof status, cudaMemcpyDeviceToHost, s);
-    for (void *ptr : {static_cast<void *>(dc), static_cast<void *>(cols), static_cast<void *>(mag),
-                      static_cast<void *>(zn), static_cast<void *>(zb), static_cast<void *>(st)})
-        if (ptr) cudaFreeAsync(ptr, s);
     const cudaError_t se = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = se;
-    if (e != cudaSuccess) { cudaGetLastError(); return HMV_ECUDA; }
+    if (e != cudaSuccess) { cudaGetLastError(); return e == cudaErrorMemoryAllocation ? HMV_ENOMEM : HMV_ECUDA; }
     if (status[0] != DEV_OK) return HMV_EINTERNAL;
     y->exponent = status[3];
     return HMV_OK;

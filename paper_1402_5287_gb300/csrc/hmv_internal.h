@@ -21,6 +21,21 @@ struct LevelGeom {
 
 }  // namespace hmv
 
+namespace hmv {
+// Working memory that a call needs beyond the plan's fixed buffers, kept by
+// the plan and grown on demand: the first call of a size allocates (and a
+// larger one reallocates, which synchronises the device); later calls reuse
+// it, so the product, inner-product and update calls of a Krylov loop or a
+// serving step allocate nothing.
+struct GrowBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    bool pinned = false;  // host memory from cudaMallocHost instead of device memory
+};
+cudaError_t grow(GrowBuf &g, size_t bytes);
+void release(GrowBuf &g);
+}  // namespace hmv
+
 struct hmv_plan_s {
     hmv_desc desc;
     cudaStream_t stream = nullptr;
@@ -91,6 +106,9 @@ struct hmv_plan_s {
     int num_sms = 0;
     int64_t device_bytes = 0;
     std::vector<void *> allocations;
+    // per-call working memory, grown on demand (hmv_dot, hmv_lincomb, and the
+    // problem and tile lists of an hmv_matvec_many step led by this plan)
+    hmv::GrowBuf dot_buf, lin_buf, many_dev, many_host{nullptr, 0, true};
 
     // split-FP64 FFT path
     int fft_w = 0, fft_P = 0, fft_S = 0, fft_K = 0;

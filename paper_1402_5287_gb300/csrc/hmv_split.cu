@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "hmv_carry.cuh"
 #include "hmv_internal.h"
 
 namespace hmv {
@@ -144,32 +145,59 @@ __constant__ int16_t kToom8Eval[15][8] = {{1, 0, 0, 0, 0, 0, 0, 0},
 {24216192000LL, -1362160800LL, -1362160800LL, -17791488LL, -17791488LL, 972972LL, 972972LL, 144144LL, 144144LL, -5616LL, -5616LL, 11700LL, 11700LL, 0LL, -905080176000LL},\
 {-36324288000LL, -4086482400LL, 817296480LL, -13343616LL, 6671808LL, -5837832LL, -833976LL, 61776LL, -39312LL, 16848LL, 5616LL, 14040LL, -5400LL, 8640LL, -36324288000LL},\
 {0LL, 0LL, 0LL, 0LL, 0LL, 0LL, 0LL, 0LL, 0LL, 0LL, 0LL, 0LL, 0LL, 0LL, 54486432000LL}}
-__constant__ long long kToom8Interp[15][15] = HMV_TOOM8_INTERP;
 constexpr long long kToom8InterpHost[15][15] = HMV_TOOM8_INTERP;  // for the plan-time overflow bound
 #undef HMV_TOOM8_INTERP
+// Toom-8's interpolation constants (|N| < 2^44) as N = hi 2^32 + lo with lo
+// and hi signed 32-bit integers, so that every product with a child digit is
+// one 32 x 32 -> 64-bit multiply-add (and the int64 sum lo + hi 2^32 is formed
+// once per digit).
+struct InterpSplit {
+    int32_t lo[15][15], hi[15][15];
+};
+constexpr InterpSplit split_interp8() {
+    InterpSplit r{};
+    for (int m = 0; m < 15; ++m)
+        for (int t = 0; t < 15; ++t) {
+            const long long c = kToom8InterpHost[m][t];
+            long long low = c & 0xFFFFFFFFLL;
+            if (low >= (1LL << 31)) low -= (1LL << 32);
+            r.lo[m][t] = static_cast<int32_t>(low);
+            r.hi[m][t] = static_cast<int32_t>((c - low) / (1LL << 32));
+        }
+    return r;
+}
+__constant__ InterpSplit kToom8Split = split_interp8();
 template <int K>
 struct Toom;
 template <>
 struct Toom<4> {
     static constexpr int P = 7;
     static constexpr uint64_t Den1 = 360, Den2 = 1;  // Den = Den1 Den2, divided in that order
+    static constexpr bool kWide = false;             // constants fit 32 bits: no high halves
     __device__ static int eval(int t, int k) { return kToom4Eval[t][k]; }
-    __device__ static long long interp(int m, int t) { return kToom4Interp[m][t]; }
+    __device__ static int32_t lo(int m, int t) { return kToom4Interp[m][t]; }
+    __device__ static int32_t hi(int, int) { return 0; }
 };
 template <>
 struct Toom<6> {
     static constexpr int P = 11;
     static constexpr uint64_t Den1 = 1008000, Den2 = 1;
+    static constexpr bool kWide = false;
     __device__ static int eval(int t, int k) { return kToom6Eval[t][k]; }
-    __device__ static long long interp(int m, int t) { return kToom6Interp[m][t]; }
+    __device__ static int32_t lo(int m, int t) { return kToom6Interp[m][t]; }
+    __device__ static int32_t hi(int, int) { return 0; }
 };
 template <>
 struct Toom<8> {
     static constexpr int P = 15;
     static constexpr uint64_t Den1 = 7776000, Den2 = 7007;
+    static constexpr bool kWide = true;
     __device__ static int eval(int t, int k) { return kToom8Eval[t][k]; }
-    __device__ static long long interp(int m, int t) { return kToom8Interp[m][t]; }
+    __device__ static int32_t lo(int m, int t) { return kToom8Split.lo[m][t]; }
+    __device__ static int32_t hi(int m, int t) { return kToom8Split.hi[m][t]; }
 };
+static_assert(split_interp8().hi[1][0] * (1LL << 32) + split_interp8().lo[1][0] == kToom8InterpHost[1][0],
+              "split of the interpolation constants");
 
 // Sign-magnitude rows (L32 limbs) -> the children's rows (Lc limbs): child t
 // gets E_t = sum_k eval(t, k) V_k times the entry's sign, as a sign and a
@@ -215,74 +243,46 @@ __global__ void k_toom_split(const uint32_t *__restrict__ limbs, const uint8_t *
     dneg[t][k] = (any && eneg) ? 1 : 0;
 }
 
-// Den Z as int64 carry-save digits: z[u] = sum_m sum_t N[m][t] P_t[u - m ds],
-// four digits per thread (ds and the children's widths are multiples of 4).
-// The children's digits are int16 (bit t of in16_mask) or int32.
-__device__ __forceinline__ int4 child4(const int32_t *z, bool is16, size_t row, int Wc, int v) {
+// The children's exact rows are carry-save digit vectors of int16 (bit t of
+// in16_mask) or int32 digits; four consecutive digits from digit v (a
+// multiple of 4, as are the row widths).
+__device__ __forceinline__ int4 child4(const int32_t *z, bool is16, size_t at) {
     if (is16) {
-        const uint2 w = *reinterpret_cast<const uint2 *>(reinterpret_cast<const int16_t *>(z) + row * Wc + v);
+        const uint2 w = *reinterpret_cast<const uint2 *>(reinterpret_cast<const int16_t *>(z) + at);
         return make_int4(static_cast<int16_t>(w.x & 0xFFFFu), static_cast<int>(w.x) >> 16,
                          static_cast<int16_t>(w.y & 0xFFFFu), static_cast<int>(w.y) >> 16);
     }
-    return *reinterpret_cast<const int4 *>(z + row * Wc + v);
+    return *reinterpret_cast<const int4 *>(z + at);
 }
 struct ToomChildren {
     const int32_t *z[15];
 };
-// One block per row: the row's children windows are re-read by the shifted
-// terms while they are still in L1/L2.
-template <int K>
-__global__ void k_toom_combine(ToomChildren ch, int in16_mask, int Wc, int ds, int64_t *__restrict__ out, int Wp) {
-    constexpr int P = Toom<K>::P;
-    const int i = blockIdx.x;
-    for (int g = threadIdx.x; g < Wp / 4; g += blockDim.x) {
-        const int u = 4 * g;
-        long long a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-        for (int mm = 0; mm < P; ++mm) {
-            const int v = u - mm * ds;
-            if (v < 0) break;
-            if (v >= Wc) continue;
-#pragma unroll
-            for (int t = 0; t < P; ++t) {
-                // |c| < 2^44, |d| <= 510 * 2^L: toom_plan_create checks that the sums stay below 2^62
-                const long long c = Toom<K>::interp(mm, t);
-                if (c == 0) continue;
-                const int4 d = child4(ch.z[t], (in16_mask >> t) & 1, i, Wc, v);
-                a0 += c * d.x;
-                a1 += c * d.y;
-                a2 += c * d.z;
-                a3 += c * d.w;
-            }
-        }
-        int64_t *o = out + static_cast<size_t>(i) * Wp + u;
-        reinterpret_cast<longlong2 *>(o)[0] = make_longlong2(a0, a1);
-        reinterpret_cast<longlong2 *>(o)[1] = make_longlong2(a2, a3);
-    }
-}
 
-// |Den Z| limbs -> |Z Den / Den'| limbs for one factor Den' < 2^24 of Den
-// (exact: a nonzero remainder is an internal error); with kBits (the last
-// factor) also the bit length and the maximum over rows.  One warp per row.
-// Long division from the top limb carries the remainder r -> (r 2^32 + z_w)
-// mod Den, an affine map of r modulo Den; each lane composes the maps of its
-// segment of limbs, a warp scan composes the segments, and then every lane
-// divides its own segment starting from the remainder that enters it.
-template <uint64_t Den, bool kBits>
-__global__ void __launch_bounds__(256) k_div_exact(uint32_t *__restrict__ zmag, int32_t *__restrict__ zbits, int n,
-                                                   int ZW, int32_t *dstat, int row_offset) {
+// Exact division of the limbs z[0 .. nl) (little-endian) by Den < 2^24 by one
+// warp.  Long division from the top limb carries the remainder
+// r -> (r 2^32 + z_w) mod Den, an affine map of r modulo Den: each lane
+// composes the maps of its segment of limbs (lane 0 the most significant
+// segment), a warp scan composes the segments, and every lane then divides its
+// own segment from the remainder that enters it.  Returns (on every lane)
+// whether the remainder is zero.
+template <uint64_t Den>
+__device__ bool warp_div_exact(uint32_t *z, int nl, int lane) {
     static_assert(Den > 1 && Den < (1ull << 24), "r 2^32 + z must fit 64 bits");
     constexpr uint64_t K32 = (uint64_t(1) << 32) % Den;
-    const int lane = threadIdx.x & 31;
-    const int i = static_cast<int>((static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
-    if (i >= n) return;  // warp-uniform
-    uint32_t *z = zmag + static_cast<size_t>(row_offset + i) * ZW;
-    // lane l: limbs [lo, hi), lane 0 the most significant segment
-    const int seg = (ZW + 31) / 32;
-    const int hi = max(0, ZW - lane * seg), lo = max(0, ZW - (lane + 1) * seg);
-    uint64_t A = 1, B = 0;  // this segment's map r -> (A r + B) mod Den
-    for (int w = hi - 1; w >= lo; --w) {
-        A = (A * K32) % Den;
-        B = (B * K32 + z[w]) % Den;
+    const int seg = (nl + 31) / 32;
+    const int hi = max(0, nl - lane * seg), lo = max(0, nl - (lane + 1) * seg);
+    constexpr int kPre = 8;  // limbs loaded ahead of the serial chains (the row lives in L2)
+    uint64_t A = 1, B = 0;   // this segment's map r -> (A r + B) mod Den
+    for (int w0 = hi - 1; w0 >= lo; w0 -= kPre) {
+        uint32_t zz[kPre];
+#pragma unroll
+        for (int k = 0; k < kPre; ++k) zz[k] = (w0 - k >= lo) ? z[w0 - k] : 0u;
+#pragma unroll
+        for (int k = 0; k < kPre; ++k)
+            if (w0 - k >= lo) {
+                A = (A * K32) % Den;
+                B = (B * K32 + zz[k]) % Den;
+            }
     }
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {  // inclusive scan: maps of lanes 0..l, applied in lane order
@@ -295,22 +295,187 @@ __global__ void __launch_bounds__(256) k_div_exact(uint32_t *__restrict__ zmag, 
     }
     uint64_t r = __shfl_up_sync(0xffffffffu, B, 1);  // remainder entering this segment
     if (lane == 0) r = 0;
-    int bits = 0;
-    for (int w = hi - 1; w >= lo; --w) {
-        const uint64_t cur = (r << 32) | z[w];  // r < Den < 2^24: no overflow
-        const uint64_t q = cur / Den;
-        r = cur - q * Den;
-        z[w] = static_cast<uint32_t>(q);
-        if (bits == 0 && q != 0) bits = 32 * w + (32 - __clz(static_cast<uint32_t>(q)));
+    for (int w0 = hi - 1; w0 >= lo; w0 -= kPre) {
+        uint32_t zz[kPre];
+#pragma unroll
+        for (int k = 0; k < kPre; ++k) zz[k] = (w0 - k >= lo) ? z[w0 - k] : 0u;
+#pragma unroll
+        for (int k = 0; k < kPre; ++k)
+            if (w0 - k >= lo) {
+                const uint64_t cur = (r << 32) | zz[k];  // r < Den < 2^24: no overflow
+                const uint64_t q = cur / Den;
+                r = cur - q * Den;
+                z[w0 - k] = static_cast<uint32_t>(q);
+            }
     }
-    if (lane == 31 && r != 0) set_status(dstat, DEV_OVERFLOW);  // the lowest segment ends the division
-    if (!kBits) return;
+    // lane 31 holds the lowest segment (or none, and the whole remainder)
+    return __shfl_sync(0xffffffffu, r, 31) == 0;
+}
+
+// Den Z as int64 carry-save digits: z[u] = sum_m sum_t N[m][t] P_t[u - m ds]
+// (|z[u]| < 2^62, checked when the plan is made), one block per row, four
+// digits per thread; every product of a constant half with a child digit is
+// one 32 x 32 -> 64-bit multiply-add.
+template <int K>
+__global__ void __launch_bounds__(256) k_toom_combine(ToomChildren ch, int in16_mask, int Wc, int ds,
+                                                      int64_t *__restrict__ out, int Wp) {
+    constexpr int P = Toom<K>::P;
+    const int i = blockIdx.x;
+    const size_t crow = static_cast<size_t>(i) * Wc;
+    for (int g = threadIdx.x; g < Wp / 4; g += blockDim.x) {
+        const int u = 4 * g;
+        long long l0 = 0, l1 = 0, l2 = 0, l3 = 0, h0 = 0, h1 = 0, h2 = 0, h3 = 0;
+        const int m_lo = max(0, (u - Wc) / ds), m_hi = min(P - 1, u / ds);
+        for (int mm = m_lo; mm <= m_hi; ++mm) {
+            const int v = u - mm * ds;
+            if (v < 0 || v >= Wc) continue;
+#pragma unroll
+            for (int t = 0; t < P; ++t) {
+                const int32_t cl = Toom<K>::lo(mm, t), chh = Toom<K>::hi(mm, t);
+                if (cl == 0 && chh == 0) continue;
+                const int4 d = child4(ch.z[t], (in16_mask >> t) & 1, crow + v);
+                l0 += static_cast<long long>(cl) * d.x;
+                l1 += static_cast<long long>(cl) * d.y;
+                l2 += static_cast<long long>(cl) * d.z;
+                l3 += static_cast<long long>(cl) * d.w;
+                if (Toom<K>::kWide) {
+                    h0 += static_cast<long long>(chh) * d.x;
+                    h1 += static_cast<long long>(chh) * d.y;
+                    h2 += static_cast<long long>(chh) * d.z;
+                    h3 += static_cast<long long>(chh) * d.w;
+                }
+            }
+        }
+        constexpr long long k32 = 1LL << 32;
+        int64_t *o = out + static_cast<size_t>(i) * Wp + u;
+        reinterpret_cast<longlong2 *>(o)[0] = make_longlong2(l0 + h0 * k32, l1 + h1 * k32);
+        reinterpret_cast<longlong2 *>(o)[1] = make_longlong2(l2 + h2 * k32, l3 + h3 * k32);
+    }
+}
+
+// The rest of a Toom plan's rows, one warp per row, in one pass over Den Z's
+// int64 digits (k_toom_combine):
+//   1. the carry into base-256 digits (warp_carry), a window of 1024 digits
+//      at a time (each lane reads 32 consecutive digits), packed into limbs
+//      of the row; a final carry of -1 means Den Z < 0 and the limbs hold its
+//      two's complement, which is negated in place;
+//   2. the exact division by Den, in factors below 2^24;
+//   3. the bit length of |Z| and its maximum over rows.
+constexpr int kTailWarps = 8;
+constexpr int kTailWin = 32 * kDigitsPerLane;  // digits per window
+template <int K>
+__global__ void __launch_bounds__(32 * kTailWarps) k_toom_finish(const int64_t *__restrict__ in, int Wo, int n,
+                                                                 uint32_t *__restrict__ zmag,
+                                                                 uint8_t *__restrict__ zneg,
+                                                                 int32_t *__restrict__ zbits, int ZW, int32_t *dstat,
+                                                                 int row_offset) {
+    const int lane = threadIdx.x & 31;
+    const int i = static_cast<int>((static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
+    if (i >= n) return;  // warp-uniform
+    const int64_t *row = in + static_cast<size_t>(i) * Wo;
+    uint32_t *z = zmag + static_cast<size_t>(row_offset + i) * ZW;
+    const int WL = Wo / 4;  // limbs of Den Z
+    long long wc = 0;
+    bool bad = false;
+    // limbs past the row's WL (windows end at multiples of kTailWin): all zero
+    // for Den Z >= 0, all ones (the sign extension) for Den Z < 0
+    bool above_nonzero = false, above_not_ones = false;
+    for (int u0 = 0; u0 < Wo; u0 += kTailWin) {
+        long long d[kDigitsPerLane];
+        const int ub0 = u0 + kDigitsPerLane * lane;
+#pragma unroll
+        for (int g = 0; g < kDigitsPerLane / 2; ++g) {  // Wo is a multiple of 4
+            const longlong2 w = (ub0 + 2 * g < Wo) ? *reinterpret_cast<const longlong2 *>(row + ub0 + 2 * g)
+                                                   : make_longlong2(0, 0);
+            d[2 * g] = w.x;
+            d[2 * g + 1] = w.y;
+        }
+        warp_carry<false, long long>(d, lane, wc);
+        const int ub = u0 + kDigitsPerLane * lane;
+#pragma unroll
+        for (int w = 0; w < kDigitsPerLane / 4; ++w) {
+            const uint32_t limb = static_cast<uint32_t>(d[4 * w]) | (static_cast<uint32_t>(d[4 * w + 1]) << 8) |
+                                  (static_cast<uint32_t>(d[4 * w + 2]) << 16) |
+                                  (static_cast<uint32_t>(d[4 * w + 3]) << 24);
+            const int li = ub / 4 + w;
+            if (li < WL) {
+                z[li] = limb;
+            } else {
+                above_nonzero |= limb != 0u;
+                above_not_ones |= limb != 0xFFFFFFFFu;
+            }
+        }
+    }
+    for (int w = WL + lane; w < ZW; w += 32) z[w] = 0u;
+    // wc is the same on every lane: 0 (Den Z >= 0) or -1 (the limbs below WL
+    // are 2^(32 WL) + Den Z); anything else, or limbs above WL that are not the
+    // sign extension, means Den Z does not fit the row
+    const bool negative = wc == -1;
+    if (wc != 0 && wc != -1) bad = true;
+    if (negative ? above_not_ones : above_nonzero) bad = true;
+    __syncwarp();
+    if (negative) {
+        int k0 = WL;  // lowest non-zero limb
+        for (int w = lane; w < WL; w += 32)
+            if (z[w]) { k0 = w; break; }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) k0 = min(k0, __shfl_xor_sync(0xffffffffu, k0, off));
+        if (k0 == WL) bad = true;  // -2^(32 WL) does not fit
+        for (int w = lane; w < WL; w += 32) {
+            if (w == k0) z[w] = ~z[w] + 1u;
+            else if (w > k0) z[w] = ~z[w];
+        }
+        __syncwarp();
+    }
+    bool exact = warp_div_exact<Toom<K>::Den1>(z, WL, lane);
+    __syncwarp();
+    if constexpr (Toom<K>::Den2 > 1) {
+        exact = warp_div_exact<Toom<K>::Den2>(z, WL, lane) && exact;
+        __syncwarp();
+    }
+    int bits = 0;
+    for (int w = lane; w < WL; w += 32)
+        if (z[w]) bits = 32 * w + (32 - __clz(z[w]));
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) bits = max(bits, __shfl_xor_sync(0xffffffffu, bits, off));
+    if ((__any_sync(0xffffffffu, bad) || !exact) && lane == 0) set_status(dstat, DEV_OVERFLOW);
     if (lane == 0) {
         zbits[row_offset + i] = bits;
+        zneg[row_offset + i] = (bits > 0 && negative) ? 1 : 0;
         atomicMax(dstat + 1, bits);
     }
+}
+
+// Interpolation (k_toom_combine), then normalisation, exact division and bit
+// lengths of a Toom plan's rows (k_toom_finish).
+cudaError_t launch_toom_tail(hmv_plan_s *p, int rhs) {
+    ToomChildren ch;
+    int mask = 0, wc = 0;
+    for (size_t t = 0; t < p->children.size(); ++t) {
+        hmv_plan_s *c = p->children[t];  // unsplit children
+        ch.z[t] = c->post[0];
+        mask |= c->post16 ? (1 << t) : 0;
+        wc = c->Wo;
+    }
+    const int ds = p->split_bits / 8;
+    const unsigned rows = static_cast<unsigned>(p->n);  // one block per row
+    const unsigned blocks = static_cast<unsigned>((p->n + kTailWarps - 1) / kTailWarps);  // a warp per row
+    const int ro = rhs * p->n;
+    if (p->toom == 4) {
+        k_toom_combine<4><<<rows, 256, 0, p->stream>>>(ch, mask, wc, ds, p->combined64, p->Wo);
+        k_toom_finish<4><<<blocks, 32 * kTailWarps, 0, p->stream>>>(p->combined64, p->Wo, p->n, p->zmag, p->zneg,
+                                                                    p->zbits, p->ZW, p->dstat, ro);
+    } else if (p->toom == 6) {
+        k_toom_combine<6><<<rows, 256, 0, p->stream>>>(ch, mask, wc, ds, p->combined64, p->Wo);
+        k_toom_finish<6><<<blocks, 32 * kTailWarps, 0, p->stream>>>(p->combined64, p->Wo, p->n, p->zmag, p->zneg,
+                                                                    p->zbits, p->ZW, p->dstat, ro);
+    } else {
+        k_toom_combine<8><<<rows, 256, 0, p->stream>>>(ch, mask, wc, ds, p->combined64, p->Wo);
+        k_toom_finish<8><<<blocks, 32 * kTailWarps, 0, p->stream>>>(p->combined64, p->Wo, p->n, p->zmag, p->zneg,
+                                                                    p->zbits, p->ZW, p->dstat, ro);
+    }
+    p->launches_total += 2;
+    return cudaGetLastError();
 }
 
 // Split rows of a vector into the three children's staging buffers,
@@ -359,29 +524,7 @@ cudaError_t combine_up(hmv_plan_s *p, const int32_t **out, int *width, int *digi
         *digit_bytes = p->post16 ? 2 : 4;
         return cudaSuccess;
     }
-    if (p->toom) {
-        ToomChildren ch;
-        int mask = 0, wc = 0;
-        for (size_t t = 0; t < p->children.size(); ++t) {
-            hmv_plan_s *c = p->children[t];  // unsplit children
-            ch.z[t] = c->post[0];
-            mask |= c->post16 ? (1 << t) : 0;
-            wc = c->Wo;
-        }
-        const unsigned grid = static_cast<unsigned>(p->n);  // one block per row
-        const int ds = p->split_bits / 8;
-        if (p->toom == 4)
-            k_toom_combine<4><<<grid, 256, 0, p->stream>>>(ch, mask, wc, ds, p->combined64, p->Wo);
-        else if (p->toom == 6)
-            k_toom_combine<6><<<grid, 256, 0, p->stream>>>(ch, mask, wc, ds, p->combined64, p->Wo);
-        else
-            k_toom_combine<8><<<grid, 256, 0, p->stream>>>(ch, mask, wc, ds, p->combined64, p->Wo);
-        p->launches_total++;
-        *out = reinterpret_cast<const int32_t *>(p->combined64);
-        *width = p->Wo;
-        *digit_bytes = 8;
-        return cudaGetLastError();
-    }
+    if (p->toom) return cudaErrorNotSupported;  // Toom plans finish in launch_toom_tail
     const int32_t *z[3];
     int w[3];
     bool s16[3];
@@ -589,24 +732,15 @@ cudaError_t split_post(hmv_plan_s *p, int rhs) {
             e = launch_post_group(&c, 1);  // leaf normalise and every post-pass level
         }
     }
-    const int32_t *z = nullptr;
-    int w = 0, zb = 4;
-    if (e == cudaSuccess) e = combine_up(p, &z, &w, &zb);
-    if (e == cudaSuccess) e = launch_final_normalize(p, z, rhs, zb, p->toom == 0);
-    if (e == cudaSuccess && p->toom) {  // the rows are Den Z: divide, then take the bit lengths
-        const unsigned blocks = static_cast<unsigned>((p->n + 7) / 8);  // a warp per row
-        const int ro = rhs * p->n;
-        if (p->toom == 4) {
-            k_div_exact<Toom<4>::Den1, true><<<blocks, 256, 0, p->stream>>>(p->zmag, p->zbits, p->n, p->ZW, p->dstat, ro);
-        } else if (p->toom == 6) {
-            k_div_exact<Toom<6>::Den1, true><<<blocks, 256, 0, p->stream>>>(p->zmag, p->zbits, p->n, p->ZW, p->dstat, ro);
+    if (e == cudaSuccess) {
+        if (p->toom) {
+            e = launch_toom_tail(p, rhs);
         } else {
-            k_div_exact<Toom<8>::Den1, false><<<blocks, 256, 0, p->stream>>>(p->zmag, p->zbits, p->n, p->ZW, p->dstat, ro);
-            k_div_exact<Toom<8>::Den2, true><<<blocks, 256, 0, p->stream>>>(p->zmag, p->zbits, p->n, p->ZW, p->dstat, ro);
-            p->launches_total++;
+            const int32_t *z = nullptr;
+            int w = 0, zb = 4;
+            e = combine_up(p, &z, &w, &zb);
+            if (e == cudaSuccess) e = launch_final_normalize(p, z, rhs, zb);
         }
-        p->launches_total++;
-        e = cudaGetLastError();
     }
     for (hmv_plan_s *c : leaves) {
         p->launches_total += c->launches_total;
