@@ -451,29 +451,13 @@ def load_workload(args):
     return n, b, uniform_vec(BASE_SEED + 2, 0, 2 * n - 1, b, 0), uniform_vec(BASE_SEED + 2, 1, n, b, 0)
 
 
-def batched_workload(count=64, nrhs=8):
-    """64 Hankel matrices, n ~ U[32, 2048], b from {4096, 16384, 33220}, 8
-    right-hand sides each, entries uniform in (-1, 1)."""
-    import random
-
-    from paper_1402_5287_gb300.inputs import BASE_SEED, uniform_vec
-    rng = random.Random(BASE_SEED + 3)
-    probs = []
-    for i in range(count):
-        n = rng.randint(32, 2048)
-        b = rng.choice([4096, 16384, 33220])
-        h = uniform_vec(BASE_SEED + 3, 2 * i, 2 * n - 1, b, 0)
-        x = uniform_vec(BASE_SEED + 3, 2 * i + 1, n * nrhs, b, 0)
-        probs.append((n, b, h, x))
-    return probs
-
-
 def measure_batched(steps, warmup, wave_gb):
     """Config 4: 64 matrices x 8 right-hand sides per hmv_batch_matvec call
     (one CUDA graph launch), device-resident inputs; wall clock per call."""
     import torch
 
     from paper_1402_5287_gb300 import hmv
+    from paper_1402_5287_gb300.inputs import batched_workload
     nrhs = 8
     probs = batched_workload(64, nrhs)
     specs = [dict(n=n, b=b, nrhs=nrhs) for n, b, _, _ in probs]

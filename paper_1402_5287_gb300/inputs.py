@@ -162,3 +162,20 @@ def workload(name: str):
         raise KeyError(name)
     x = uniform_vec(BASE_SEED + c, 1, n, b, 0)
     return n, b, h, x
+
+
+def batched_workload(count: int = 64, nrhs: int = 8):
+    """The batched workload: `count` Hankel matrices with n ~ U[32, 2048] and
+    b drawn from {4096, 16384, 33220}, each with a block of `nrhs`
+    right-hand sides, entries uniform in (-1, 1).  Returns [(n, b, h, x)]
+    with x holding the nrhs vectors one after another."""
+    import random
+    rng = random.Random(BASE_SEED + 3)
+    probs = []
+    for i in range(count):
+        n = rng.randint(32, 2048)
+        b = rng.choice([4096, 16384, 33220])
+        h = uniform_vec(BASE_SEED + 3, 2 * i, 2 * n - 1, b, 0)
+        x = uniform_vec(BASE_SEED + 3, 2 * i + 1, n * nrhs, b, 0)
+        probs.append((n, b, h, x))
+    return probs

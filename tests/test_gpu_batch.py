@@ -141,3 +141,41 @@ def test_batch_with_digit_split_members():
     yl, yn, e = oracle.round_rows(np.concatenate([z[0] for z in zs]), np.concatenate([z[1] for z in zs]),
                                   pr["b"], h.exponent + x.exponent)
     assert_same(y, FixedVec(yl, yn, pr["b"], e))
+
+
+def test_batched_workload_at_its_own_shape_sampled_rows():
+    """The batched workload itself (64 matrices, n ~ U[32, 2048], b from
+    {4096, 16384, 33220}, 8 right-hand sides each, one graph launch): for
+    every matrix, 8 seeded (right-hand side, row) pairs plus the row with the
+    largest output mantissa of the block against the oracle, bit for bit,
+    and the block's shared exponent from those rows."""
+    import random
+
+    from paper_1402_5287_gb300.inputs import batched_workload
+    from test_gpu_parity import THREADS
+    nrhs = 8
+    probs = batched_workload(64, nrhs)
+    bt = hmv.Batch([dict(n=n, b=b, nrhs=nrhs) for n, b, _, _ in probs], wave_bytes=48 << 30)
+    try:
+        for i, (_, _, h, _) in enumerate(probs):
+            bt.load_matrix(i, h)
+        ys = bt.matvec([x for *_, x in probs])
+        info = bt.info()
+    finally:
+        bt.close()
+    assert info["pairs"] == 64 * nrhs
+    rng = random.Random(20260)
+    for (n, b, h, x), y in zip(probs, ys):
+        mags = [int.from_bytes(y.limbs[k].tobytes(), "little") for k in range(n * nrhs)]
+        top = max(range(n * nrhs), key=lambda k: mags[k])
+        picks = sorted({rng.randrange(n * nrhs) for _ in range(8)} | {top})
+        for r in sorted({k // n for k in picks}):
+            rows = [k % n for k in picks if k // n == r]
+            xr = FixedVec(x.limbs[r * n:(r + 1) * n], x.neg[r * n:(r + 1) * n], b, x.exponent)
+            z, zn = oracle.exact_rows(oracle.HANKEL, n, b, h, xr, rows, THREADS)
+            shift = y.exponent + b - (h.exponent + x.exponent)
+            yl, yn = oracle.round_rows_fixed(z, zn, b, shift)
+            got = [r * n + i for i in rows]
+            assert np.array_equal(yl, y.limbs[got]) and np.array_equal(yn, y.neg[got]), (n, b, r, rows)
+            if top in got:  # the least exponent is decided by the largest row
+                assert oracle.round_rows(z, zn, b, h.exponent + x.exponent)[2] == y.exponent
