@@ -271,7 +271,8 @@ def run_ours(args):
     peak_sust = peaks.get("bf16_tflops_sustained") or 1700.0
     issued_over_useful = st["leaf_macs_issued"] / st["leaf_macs"] if st["leaf_macs"] else None
 
-    traffic = leaf_traffic(st["leaf_tiles"], n, b)
+    traffic = leaf_traffic(st["leaf_tiles"], n, b, DIGIT_SPLIT_NAMES.get(st["digit_products"]),
+                           st["leaf_tile_digits"])
 
     # end to end through the public API: host x in, host y out, copies inside the timed region
     e2e = None
@@ -423,19 +424,22 @@ def leaf_sources_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def leaf_traffic(tiles, n, b):
+def leaf_traffic(tiles, n, b, digit_split, tile_digits):
     """DRAM bytes per launch of the leaf kernel from the committed ncu capture
-    (profiles/k_leaf_tc_traffic.json), or None when the capture is for another
-    workload or the kernel has changed since."""
+    of a small case (profiles/k_leaf_tc_traffic.json), scaled to this launch
+    by its tile count (the capture shows bytes per tile constant across
+    sizes); None when the capture is for another b, digit split or tile width,
+    or the kernel has changed since."""
     try:
         with open(os.path.join(ROOT, "profiles", "k_leaf_tc_traffic.json")) as f:
             rec = json.load(f)
     except (OSError, ValueError):
         return None
-    if (rec.get("sources_sha256_16") != leaf_sources_hash() or rec.get("n") != n or rec.get("b") != b
-            or rec.get("leaf_tiles") != tiles):
+    if (rec.get("sources_sha256_16") != leaf_sources_hash() or rec.get("b") != b
+            or rec.get("digit_split") != digit_split or rec.get("leaf_tile_digits") != tile_digits):
         return None
-    return rec.get("dram_bytes_per_launch")
+    cap = rec["captures"][0]
+    return (cap["dram_bytes_read"] + cap["dram_bytes_write"]) * tiles / cap["leaf_tiles"]
 
 
 def load_workload(args):
