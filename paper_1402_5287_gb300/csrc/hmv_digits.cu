@@ -33,11 +33,22 @@ inline int blocks_for(long long work, int threads = kThreads) {
     return static_cast<int>((work + threads - 1) / threads);
 }
 
-// balanced digit of t (|t| <= 257) with its carry: t = d + 256*carry
-__device__ __forceinline__ int balance(int t, int &carry) {
-    int c = (t + 128) >> 8;  // floor((t + 128) / 256)
-    carry = c;
-    return t - (c << 8);
+
+// Four balanced digits in one word, a little-endian byte each (two's
+// complement, [-128, 127]): their value sum_i d_i 256^i is the unsigned
+// reading U less 256^(i+1) for every negative digit, U - 2 (U & 0x80808080).
+__device__ __forceinline__ long long word_value(uint32_t w) {
+    return static_cast<long long>(w) - 2 * static_cast<long long>(w & 0x80808080u);
+}
+// v + carry (|v| < 2^33) written as four balanced digits and a new carry:
+// adding 128 to every digit position makes each digit plus 128 a byte in
+// [0, 255], so the low word of v + carry + 0x80808080 holds them (XOR 0x80
+// takes each back to d_i) and the bits above it are the carry out.  The
+// balanced representation is unique, so this is the digit-by-digit chain.
+__device__ __forceinline__ uint32_t balanced_word(long long v, long long &carry) {
+    const long long t = v + carry + 0x80808080LL;
+    carry = t >> 32;  // arithmetic: floor
+    return static_cast<uint32_t>(t) ^ 0x80808080u;
 }
 
 __device__ __forceinline__ uint16_t bf16_bits_of_small_int(int v) {
@@ -116,29 +127,72 @@ __global__ void __launch_bounds__(256) k_encode(PlanPtrs g, int rows, int L32, i
 //   matrix side  c_k = a_{2k} + a_{2k+1},  d_k = a_{2k+1},  e_k = a_{2k}
 //   vector side  h_k = x_{2k},  f_k = x_{2k} - x_{2k+1},  g_k = x_{2k-1} - x_{2k}
 // with a_q = 0 for q >= 2s-1 and x_q = 0 for q < 0 or q >= s.
-// One thread per child row, 64 digits per step; the next step's 64-byte
-// slices of both parent rows are loaded before this step's carry chain runs,
-// so the chain (carries in {-1, 0, 1}) never waits on memory.
-__device__ __forceinline__ void load_slice64(const int8_t *r, bool on, int u, int Dp, uint4 (&v)[4]) {
-#pragma unroll
-    for (int h = 0; h < 4; ++h)
-        v[h] = (on && u + 16 * h < Dp) ? *reinterpret_cast<const uint4 *>(r + u + 16 * h) : make_uint4(0, 0, 0, 0);
+// A block of 128 threads makes 128 consecutive rows k0 .. k0 + 127 of one
+// child, each thread one row, its carry chain running over words of four
+// balanced digits (balanced_word).  Those rows read parent rows
+// 2k0 - 1 .. 2k0 + 255 only, kept in shared memory as even rows E[a] = parent
+// 2k0 + 2a and odd rows O[j] = parent 2k0 - 1 + 2j (so that thread a finds
+// 2k at E[a], 2k + 1 at O[a + 1] and 2k - 1 at O[a], all conflict-free with an
+// 80-byte pitch), 64 digits at a time, loaded coalesced with cp.async into two
+// stages: the next 64 digits land while the current carry chains run.  Each
+// thread's 64 output digits go to a shared tile that the block then stores
+// coalesced.  Parent rows outside the node are zero.  Blocks are ordered
+// row block first, so the three children of a parent row block are
+// neighbours and share its rows in L2.
+constexpr int kPreRows = 128;
+constexpr int kPreDig = 64;                 // digits per stage
+constexpr int kPrePitch = kPreDig + 16;     // bytes per staged row: an odd number of 16-byte units
+constexpr int kPrePieces = kPreDig / 16;    // 16-byte pieces per staged row
+constexpr int kPreStage = (kPreRows + kPreRows + 1) * kPrePitch;
+constexpr int kPreSmem = 2 * kPreStage + kPreRows * kPrePitch;
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid) {
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    const int src_bytes = valid ? 16 : 0;  // 0: the 16 bytes are filled with zeros, nothing is read
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
 }
-__global__ void __launch_bounds__(128) k_prepass(PlanPtrs g, int in_rows, const int *__restrict__ in_size,
-                                                 int out_rows, const int *__restrict__ out_size, int nchildren, int Dp,
-                                                 int matrix_side, int32_t *dstat) {
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__global__ void __launch_bounds__(kPreRows) k_prepass_staged(PlanPtrs g, int in_rows, const int *__restrict__ in_size,
+                                                            int out_rows, const int *__restrict__ out_size,
+                                                            int nchildren, int Dp, int matrix_side, int32_t *dstat) {
+    extern __shared__ __align__(16) uint8_t pre_smem[];
     const int8_t *__restrict__ in = static_cast<const int8_t *>(g.in[blockIdx.y]);
     int8_t *__restrict__ out = static_cast<int8_t *>(g.out[blockIdx.y]);
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    const int child = w / out_rows, k = w % out_rows;
-    if (child >= nchildren) return;
+    const int child = blockIdx.x % nchildren, rb = blockIdx.x / nchildren;
     const int parent = child / 3, t = child % 3;
     const int s = in_size[parent];
     const int cs = out_size[child];
     const int cnt = matrix_side ? 2 * cs - 1 : cs;
-    if (k >= cnt) return;
+    const int k0 = rb * kPreRows;
+    if (k0 >= cnt) return;  // the whole block
     const int len = matrix_side ? 2 * s - 1 : s;
-    int q1, q2, s1, s2;
+    // which parent rows the child reads: 2k (even set), 2k+1 and 2k-1 (odd set)
+    const bool needE = !(matrix_side && t == 1);
+    const bool needO = matrix_side ? (t != 2) : (t != 0);
+    const int8_t *pbase = in + static_cast<size_t>(parent) * in_rows * Dp;
+    const int tid = threadIdx.x;
+    auto stage_in = [&](int st, int u0) {
+        uint8_t *E = pre_smem + st * kPreStage;
+        uint8_t *O = E + kPreRows * kPrePitch;
+        // 16-byte pieces (row, piece), even rows first
+        const int nE = needE ? kPreRows * kPrePieces : 0, nO = needO ? (kPreRows + 1) * kPrePieces : 0;
+        for (int c = tid; c < nE + nO; c += kPreRows) {
+            const bool even = c < nE;
+            const int cc = even ? c : c - nE;
+            const int r = cc / kPrePieces, pc = cc % kPrePieces;
+            const int q = even ? 2 * k0 + 2 * r : 2 * k0 - 1 + 2 * r;  // parent row
+            const int u = u0 + 16 * pc;
+            const bool valid = q >= 0 && q < len && u < Dp;
+            const int8_t *src = pbase + static_cast<size_t>(valid ? q : 0) * Dp + (valid ? u : 0);
+            cp_async16((even ? E : O) + r * kPrePitch + 16 * pc, src, valid);
+        }
+        cp_async_commit();
+    };
+    int q1, q2, s1, s2;  // this thread's parent rows and signs, as in k_prepass
+    const int k = k0 + tid;
     if (matrix_side) {
         if (t == 0) { q1 = 2 * k; s1 = 1; q2 = 2 * k + 1; s2 = 1; }
         else if (t == 1) { q1 = 2 * k + 1; s1 = 1; q2 = 0; s2 = 0; }
@@ -148,43 +202,51 @@ __global__ void __launch_bounds__(128) k_prepass(PlanPtrs g, int in_rows, const 
         else if (t == 1) { q1 = 2 * k; s1 = 1; q2 = 2 * k + 1; s2 = -1; }
         else { q1 = 2 * k - 1; s1 = 1; q2 = 2 * k; s2 = -1; }
     }
-    if (q1 < 0 || q1 >= len) s1 = 0;
-    if (q2 < 0 || q2 >= len) s2 = 0;
-    const int8_t *r1 = in + (static_cast<size_t>(parent) * in_rows + (s1 ? q1 : 0)) * Dp;
-    const int8_t *r2 = in + (static_cast<size_t>(parent) * in_rows + (s2 ? q2 : 0)) * Dp;
-    int8_t *o = out + (static_cast<size_t>(child) * out_rows + k) * Dp;
-    uint4 n1[4], n2[4];
-    load_slice64(r1, s1 != 0, 0, Dp, n1);
-    load_slice64(r2, s2 != 0, 0, Dp, n2);
-    int carry = 0;
-    for (int u0 = 0; u0 < Dp; u0 += 64) {
-        uint4 v1[4], v2[4];
+    // staged row of parent q (rows outside the node are zero-filled in shared memory)
+    auto srow = [&](int st, int q) -> const uint8_t * {
+        const uint8_t *E = pre_smem + st * kPreStage;
+        const uint8_t *O = E + kPreRows * kPrePitch;
+        const int d = q - 2 * k0;  // -1 .. 255
+        return (d & 1) ? O + ((d + 1) >> 1) * kPrePitch : E + (d >> 1) * kPrePitch;
+    };
+    uint8_t *T = pre_smem + 2 * kPreStage;  // output tile
+    long long carry = 0;
+    const int nst = (Dp + kPreDig - 1) / kPreDig;
+    stage_in(0, 0);
+    for (int c = 0; c < nst; ++c) {
+        const int u0 = c * kPreDig;
+        if (c + 1 < nst) {
+            stage_in((c + 1) & 1, u0 + kPreDig);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const int st = c & 1;
+        const uint8_t *r1 = srow(st, s1 ? q1 : 2 * k0);
+        const uint8_t *r2 = srow(st, s2 ? q2 : 2 * k0);
 #pragma unroll
-        for (int h = 0; h < 4; ++h) { v1[h] = n1[h]; v2[h] = n2[h]; }
-        load_slice64(r1, s1 != 0, u0 + 64, Dp, n1);
-        load_slice64(r2, s2 != 0, u0 + 64, Dp, n2);
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            if (u0 + 16 * h >= Dp) break;  // Dp is a multiple of 16
-            const uint32_t a1[4] = {v1[h].x, v1[h].y, v1[h].z, v1[h].w};
-            const uint32_t a2[4] = {v2[h].x, v2[h].y, v2[h].z, v2[h].w};
+        for (int h = 0; h < kPrePieces; ++h) {
+            if (u0 + 16 * h >= Dp) break;  // Dp is a multiple of 16: the carry out of digit Dp - 1 is checked
+            const uint4 v1 = *reinterpret_cast<const uint4 *>(r1 + 16 * h);
+            const uint4 v2 = *reinterpret_cast<const uint4 *>(r2 + 16 * h);
+            const uint32_t a1[4] = {v1.x, v1.y, v1.z, v1.w};
+            const uint32_t a2[4] = {v2.x, v2.y, v2.z, v2.w};
             uint32_t packed[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                uint32_t pk = 0;
-#pragma unroll
-                for (int by = 0; by < 4; ++by) {
-                    const int d1 = static_cast<int8_t>((a1[q] >> (8 * by)) & 0xFFu);
-                    const int d2 = static_cast<int8_t>((a2[q] >> (8 * by)) & 0xFFu);
-                    const int d = balance(s1 * d1 + s2 * d2 + carry, carry);
-                    pk |= (static_cast<uint32_t>(d) & 0xFFu) << (8 * by);
-                }
-                packed[q] = pk;
-            }
-            *reinterpret_cast<uint4 *>(o + u0 + 16 * h) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+            for (int qq = 0; qq < 4; ++qq) packed[qq] = balanced_word(s1 * word_value(a1[qq]) + s2 * word_value(a2[qq]), carry);
+            *reinterpret_cast<uint4 *>(T + tid * kPrePitch + 16 * h) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        }
+        __syncthreads();  // the tile is complete, and stage st may be refilled
+        for (int pcs = tid; pcs < kPreRows * kPrePieces; pcs += kPreRows) {
+            const int r = pcs / kPrePieces, pc = pcs % kPrePieces;
+            const int u = u0 + 16 * pc;
+            if (k0 + r < cnt && u < Dp)
+                *reinterpret_cast<uint4 *>(out + (static_cast<size_t>(child) * out_rows + k0 + r) * Dp + u) =
+                    *reinterpret_cast<const uint4 *>(T + r * kPrePitch + 16 * pc);
         }
     }
-    if (carry != 0) set_status(dstat, DEV_OVERFLOW);
+    if (k < cnt && carry != 0) set_status(dstat, DEV_OVERFLOW);
 }
 
 // ------------------------------------------------------------------ packing
@@ -702,9 +764,16 @@ cudaError_t prepass_group(hmv_plan_s *p, const PlanPtrs &g, int G, int level, bo
     const LevelGeom &pl = p->lv[level], &cl = p->lv[level + 1];
     const int in_rows = matrix_side ? pl.rowsA : pl.rowsX;
     const int out_rows = matrix_side ? cl.rowsA : cl.rowsX;
-    const long long rows = static_cast<long long>(cl.nodes) * out_rows;  // one thread per child row
-    k_prepass<<<dim3(blocks_for(rows, 128), G), 128, 0, p->stream>>>(g, in_rows, pl.d_size, out_rows, cl.d_size,
-                                                                     cl.nodes, p->Dp, matrix_side ? 1 : 0, p->dstat);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_prepass_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, kPreSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    // a block per 128 rows of a child, row block major (siblings are neighbours)
+    const long long blocks = static_cast<long long>((out_rows + kPreRows - 1) / kPreRows) * cl.nodes;
+    k_prepass_staged<<<dim3(static_cast<unsigned>(blocks), G), kPreRows, kPreSmem, p->stream>>>(
+        g, in_rows, pl.d_size, out_rows, cl.d_size, cl.nodes, p->Dp, matrix_side ? 1 : 0, p->dstat);
     p->launches_total++;
     return cudaGetLastError();
 }
