@@ -201,46 +201,96 @@ static_assert(split_interp8().hi[1][0] * (1LL << 32) + split_interp8().lo[1][0] 
 
 // Sign-magnitude rows (L32 limbs) -> the children's rows (Lc limbs): child t
 // gets E_t = sum_k eval(t, k) V_k times the entry's sign, as a sign and a
-// magnitude (|E_t| < 2^(32 Lc)).  One thread per (row, point).
+// magnitude (|E_t| < 2^(32 Lc)).  One warp per (row, point): limb q of E_t
+// is first the int64 sum sum_k eval(t, k) V_k[q] (|.| < 2^45), then the warp
+// carries base 2^32 (4 consecutive limbs per lane, carries passed up one
+// lane per round until none is left), a window of 128 limbs at a time; a
+// final carry of -1 means E_t < 0 and the limbs, its two's complement, are
+// negated in place.
+constexpr int kSplitLimbs = 4;  // limbs per lane per window
+__device__ __forceinline__ void warp_carry32(long long (&v)[kSplitLimbs], uint32_t (&o)[kSplitLimbs], int lane,
+                                             long long &wcarry) {
+    long long c = (lane == 0) ? wcarry : 0;
+#pragma unroll
+    for (int i = 0; i < kSplitLimbs; ++i) {
+        const long long t = v[i] + c;
+        o[i] = static_cast<uint32_t>(t);
+        c = t >> 32;  // arithmetic: floor
+    }
+    long long pending = c, out = 0;
+    for (int round = 0; round <= 32; ++round) {
+        out += __shfl_sync(0xffffffffu, pending, 31);
+        long long incoming = __shfl_up_sync(0xffffffffu, pending, 1);
+        if (lane == 0) incoming = 0;
+        if (!__any_sync(0xffffffffu, incoming != 0)) break;
+        c = incoming;
+#pragma unroll
+        for (int i = 0; i < kSplitLimbs; ++i) {
+            const long long t = static_cast<long long>(o[i]) + c;
+            o[i] = static_cast<uint32_t>(t);
+            c = t >> 32;
+        }
+        pending = c;
+    }
+    wcarry = out;
+}
 template <int K>
-__global__ void k_toom_split(const uint32_t *__restrict__ limbs, const uint8_t *__restrict__ neg, int rows, int L32,
-                             int sl, int Lc, uint32_t *const *__restrict__ dst, uint8_t *const *__restrict__ dneg) {
+__global__ void __launch_bounds__(256) k_toom_split(const uint32_t *__restrict__ limbs, const uint8_t *__restrict__ neg,
+                                                    int rows, int L32, int sl, int Lc, uint32_t *const *__restrict__ dst,
+                                                    uint8_t *const *__restrict__ dneg) {
     constexpr int P = Toom<K>::P;
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= rows * P) return;
-    const int k = idx / P, t = idx % P;
+    const int lane = threadIdx.x & 31;
+    const long long w = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    if (w >= static_cast<long long>(rows) * P) return;  // warp-uniform
+    const int k = static_cast<int>(w / P), t = static_cast<int>(w % P);
     const uint32_t *m = limbs + static_cast<size_t>(k) * L32;
     uint32_t *o = dst[t] + static_cast<size_t>(k) * Lc;
     int c[K];
 #pragma unroll
     for (int p = 0; p < K; ++p) c[p] = Toom<K>::eval(t, p);
-    long long carry = 0;
-    for (int q = 0; q < Lc; ++q) {
-        long long e = carry;
+    long long wc = 0;
+    for (int q0 = 0; q0 < Lc; q0 += 32 * kSplitLimbs) {
+        long long v[kSplitLimbs];
+        uint32_t r[kSplitLimbs];
 #pragma unroll
-        for (int p = 0; p < K; ++p) {
-            const int li = p * sl + q;  // limb q of V_p
-            const uint32_t v = (q < sl && li < L32) ? m[li] : 0u;
-            e += static_cast<long long>(c[p]) * v;
+        for (int i = 0; i < kSplitLimbs; ++i) {
+            const int q = q0 + kSplitLimbs * lane + i;  // limb q of every part V_p
+            long long e = 0;
+#pragma unroll
+            for (int p = 0; p < K; ++p) {
+                const int li = p * sl + q;
+                if (q < sl && li < L32) e += static_cast<long long>(c[p]) * m[li];
+            }
+            v[i] = e;
         }
-        o[q] = static_cast<uint32_t>(e);
-        carry = e >> 32;  // arithmetic: floor
+        warp_carry32(v, r, lane, wc);
+#pragma unroll
+        for (int i = 0; i < kSplitLimbs; ++i) {
+            const int q = q0 + kSplitLimbs * lane + i;
+            if (q < Lc) o[q] = r[i];
+        }
     }
-    // carry is 0 or -1 here (the value fits Lc limbs): -1 means E < 0
+    __syncwarp();
+    // wc: 0 (E >= 0) or -1 (the limbs are 2^(32 Lc) + E); |E| < 2^(32 Lc) by the children's width
+    if (wc < 0) {
+        int q0 = Lc;  // lowest non-zero limb
+        for (int q = lane; q < Lc; q += 32)
+            if (o[q]) { q0 = q; break; }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) q0 = min(q0, __shfl_xor_sync(0xffffffffu, q0, off));
+        for (int q = lane; q < Lc; q += 32) {
+            if (q == q0) o[q] = ~o[q] + 1u;
+            else if (q > q0) o[q] = ~o[q];
+        }
+        __syncwarp();
+    }
     bool any = false;
-    if (carry < 0) {
-        unsigned long long cc = 1;  // |E| = ~E + 1
-        for (int q = 0; q < Lc; ++q) {
-            cc += static_cast<unsigned long long>(~o[q]);
-            o[q] = static_cast<uint32_t>(cc);
-            cc >>= 32;
-            any |= o[q] != 0;
-        }
-    } else {
-        for (int q = 0; q < Lc; ++q) any |= o[q] != 0;
+    for (int q = lane; q < Lc; q += 32) any |= o[q] != 0;
+    any = __any_sync(0xffffffffu, any);
+    if (lane == 0) {
+        const bool eneg = (wc < 0) != (neg[k] != 0);
+        dneg[t][k] = (any && eneg) ? 1 : 0;
     }
-    const bool eneg = (carry < 0) != (neg[k] != 0);
-    dneg[t][k] = (any && eneg) ? 1 : 0;
 }
 
 // The children's exact rows are carry-save digit vectors of int16 (bit t of
@@ -486,14 +536,14 @@ cudaError_t split_down(hmv_plan_s *p, const uint32_t *limbs, const uint8_t *neg,
         const int P = static_cast<int>(p->children.size());
         uint32_t *const *ddst = p->toom_ptrs + (matrix ? 0 : P);  // the same rows, uploaded at plan creation
         uint8_t *const *dn = p->toom_neg_ptrs + (matrix ? 0 : P);
-        const unsigned blocks = static_cast<unsigned>((static_cast<long long>(rows) * P + 127) / 128);
+        const unsigned blocks = static_cast<unsigned>((static_cast<long long>(rows) * P + 7) / 8);  // a warp per (row, point)
         const int sl = p->split_bits / 32, Lc = p->children[0]->L32;
         if (p->toom == 4)
-            k_toom_split<4><<<blocks, 128, 0, p->stream>>>(limbs, neg, rows, p->L32, sl, Lc, ddst, dn);
+            k_toom_split<4><<<blocks, 256, 0, p->stream>>>(limbs, neg, rows, p->L32, sl, Lc, ddst, dn);
         else if (p->toom == 6)
-            k_toom_split<6><<<blocks, 128, 0, p->stream>>>(limbs, neg, rows, p->L32, sl, Lc, ddst, dn);
+            k_toom_split<6><<<blocks, 256, 0, p->stream>>>(limbs, neg, rows, p->L32, sl, Lc, ddst, dn);
         else
-            k_toom_split<8><<<blocks, 128, 0, p->stream>>>(limbs, neg, rows, p->L32, sl, Lc, ddst, dn);
+            k_toom_split<8><<<blocks, 256, 0, p->stream>>>(limbs, neg, rows, p->L32, sl, Lc, ddst, dn);
         p->launches_total++;
         return cudaGetLastError();
     }
