@@ -514,6 +514,83 @@ __global__ void k_postpass(PlanPtrs g, int rows_in, int rows_out, const int *__r
     }
 }
 
+// Two levels of step 8 in one pass: rows 4m .. 4m+3 of a level-l node nu
+// from row m of its nine grandchildren 9 nu + c (level l + 2), the middle
+// level never written.  With A_c = grandchild 9 nu + c, row m (0-based, as
+// in k_postpass: level-(l+1) row k of node mu is p - q (k even) or p + r
+// (k odd) of mu's children):
+//   y_4m   = (A_0 - A_1) - (A_3 - A_4)     y_4m+1 = (A_0 - A_1) + (A_6 - A_7)
+//   y_4m+2 = (A_0 + A_2) - (A_3 + A_5)     y_4m+3 = (A_0 + A_2) + (A_6 + A_8)
+// Only the rows of outputs inside the node are read (they lie inside the
+// grandchildren's orders).  Digits stay carry-save; the two levels' growth is
+// within the post-pass digit bound.  One block per group of four output
+// rows, 16 bytes of digits per thread and step.
+template <class T>
+__device__ __forceinline__ void unpack16B(int4 w, int (&d)[16 / sizeof(T)]) {
+    const int v[4] = {w.x, w.y, w.z, w.w};
+    if (sizeof(T) == 4) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) d[q] = v[q];
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            d[2 * q] = static_cast<int16_t>(v[q] & 0xFFFF);
+            d[2 * q + 1] = v[q] >> 16;
+        }
+    }
+}
+template <class T>
+__device__ __forceinline__ int4 pack16B(const int (&d)[16 / sizeof(T)]) {
+    if (sizeof(T) == 4) return make_int4(d[0], d[1], d[2], d[3]);
+    int v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        v[q] = static_cast<int>((static_cast<uint32_t>(d[2 * q]) & 0xFFFFu) | (static_cast<uint32_t>(d[2 * q + 1]) << 16));
+    return make_int4(v[0], v[1], v[2], v[3]);
+}
+template <class T>
+__global__ void k_postpass2(PlanPtrs g, int rows_in, int rows_out, const int *__restrict__ parent_size, int Wo) {
+    constexpr int ND = 16 / sizeof(T);  // digits per 16 bytes
+    const T *__restrict__ in = static_cast<const T *>(g.in[blockIdx.y]);
+    T *__restrict__ out = static_cast<T *>(g.out[blockIdx.y]);
+    const int quads = (rows_out + 3) / 4;
+    const int nu = blockIdx.x / quads, m = blockIdx.x % quads;
+    const int size = parent_size[nu];
+    const int i0 = 4 * m;
+    if (i0 >= size) return;
+    bool has[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) has[j] = i0 + j < size;
+    // grandchild c is read when one of its outputs exists
+    const bool need[9] = {true, has[0] || has[1], has[2] || has[3], has[0] || has[2], has[0],
+                          has[2], has[1] || has[3], has[1], has[3]};
+    const int4 *a[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c)
+        a[c] = reinterpret_cast<const int4 *>(in + (static_cast<size_t>(9 * nu + c) * rows_in + m) * Wo);
+    int4 *y = reinterpret_cast<int4 *>(out + (static_cast<size_t>(nu) * rows_out + i0) * Wo);
+    const int groups = Wo * static_cast<int>(sizeof(T)) / 16;  // Wo is a multiple of 8
+    const size_t ystride = static_cast<size_t>(Wo) * sizeof(T) / 16;
+    for (int gi = threadIdx.x; gi < groups; gi += blockDim.x) {
+        int d[9][ND];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) unpack16B<T>(need[c] ? a[c][gi] : make_int4(0, 0, 0, 0), d[c]);
+        int r[ND];
+#pragma unroll
+        for (int q = 0; q < ND; ++q) r[q] = (d[0][q] - d[1][q]) - (d[3][q] - d[4][q]);
+        if (has[0]) y[gi] = pack16B<T>(r);
+#pragma unroll
+        for (int q = 0; q < ND; ++q) r[q] = (d[0][q] - d[1][q]) + (d[6][q] - d[7][q]);
+        if (has[1]) y[ystride + gi] = pack16B<T>(r);
+#pragma unroll
+        for (int q = 0; q < ND; ++q) r[q] = (d[0][q] + d[2][q]) - (d[3][q] + d[5][q]);
+        if (has[2]) y[2 * ystride + gi] = pack16B<T>(r);
+#pragma unroll
+        for (int q = 0; q < ND; ++q) r[q] = (d[0][q] + d[2][q]) + (d[6][q] + d[8][q]);
+        if (has[3]) y[3 * ystride + gi] = pack16B<T>(r);
+    }
+}
+
 // ------------------------------------------------------------------ final normalise
 // Row digit vector (int32 digits, radix 256) -> |Z| as 32-bit limbs, sign, bit
 // length.  One warp per row: a first pass of carry propagation gives the sign
@@ -813,6 +890,16 @@ cudaError_t leaf_post_group(hmv_plan_s *p, const PlanPtrs &g, int G) {
     p->launches_total++;
     return cudaGetLastError();
 }
+cudaError_t postpass2_group(hmv_plan_s *p, const PlanPtrs &g, int G, int level) {
+    const LevelGeom &pl = p->lv[level], &gl = p->lv[level + 2];
+    const dim3 grid(static_cast<unsigned>(pl.nodes) * ((pl.rowsX + 3) / 4), G);  // one block per four output rows
+    if (p->post16)
+        k_postpass2<int16_t><<<grid, 128, 0, p->stream>>>(g, gl.rowsX, pl.rowsX, pl.d_size, p->Wo);
+    else
+        k_postpass2<int32_t><<<grid, 128, 0, p->stream>>>(g, gl.rowsX, pl.rowsX, pl.d_size, p->Wo);
+    p->launches_total++;
+    return cudaGetLastError();
+}
 cudaError_t postpass_group(hmv_plan_s *p, const PlanPtrs &g, int G, int level) {
     const LevelGeom &pl = p->lv[level], &cl = p->lv[level + 1];
     const dim3 grid(static_cast<unsigned>(pl.nodes) * pl.rowsX, G);  // one block per output row
@@ -913,13 +1000,23 @@ cudaError_t launch_post_group(hmv_plan_s *const *ps, int G) {
         for (int k = 0; k < G; ++k) g.out[k] = ps[k]->post[0];
         return leaf_normalize_group(p, g, G);
     }
-    cudaError_t e = leaf_post_group(p, g, G);  // writes level L - 1 into post[(L - 1) % 2]
-    for (int l = p->L - 2; l >= 0 && e == cudaSuccess; --l) {
+    // levels L-1 .. 0: two at a time (k_postpass2) while two are left, then one;
+    // the buffers alternate, and leaf_post starts in the one that makes level 0
+    // land in post[0]
+    int steps = 0;
+    for (int c = p->L - 1; c > 0; c -= (c >= 2 ? 2 : 1)) ++steps;
+    int cur = steps % 2;
+    for (int k = 0; k < G; ++k) g.out[k] = ps[k]->post[cur];
+    cudaError_t e = leaf_post_group(p, g, G);  // level L - 1
+    for (int c = p->L - 1; c > 0 && e == cudaSuccess;) {
+        const int l = c >= 2 ? c - 2 : c - 1;
         for (int k = 0; k < G; ++k) {
-            g.in[k] = ps[k]->post[(l + 1) % 2];
-            g.out[k] = ps[k]->post[l % 2];
+            g.in[k] = ps[k]->post[cur];
+            g.out[k] = ps[k]->post[1 - cur];
         }
-        e = postpass_group(p, g, G, l);
+        e = (c - l == 2) ? postpass2_group(p, g, G, l) : postpass_group(p, g, G, l);
+        cur = 1 - cur;
+        c = l;
     }
     return e;
 }
