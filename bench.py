@@ -207,7 +207,8 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
 
-    method = {"auto": hmv.AUTO, "karatsuba": hmv.KARATSUBA, "fft64": hmv.FFT64, "schoolbook": hmv.SCHOOLBOOK}[args.method]
+    method = {"auto": hmv.AUTO, "karatsuba": hmv.KARATSUBA, "fft64": hmv.FFT64, "schoolbook": hmv.SCHOOLBOOK,
+              "ntt": hmv.NTT}[args.method]
     split_flag = {-1: 0, 0: 0, 1: hmv.FLAG_DIGIT_SPLIT1, 2: hmv.FLAG_DIGIT_SPLIT2, 4: hmv.FLAG_DIGIT_TOOM4,
                   6: hmv.FLAG_DIGIT_TOOM6, 8: hmv.FLAG_DIGIT_TOOM8}[args.digit_split]
     if args.digit_split == 0 and method == hmv.AUTO:
@@ -373,7 +374,8 @@ def compare_kernels(hmv, h, x, n, b, stream):
     import numpy as np
     import torch
     out = {}
-    for name, method, levels, w in (("split_fp64_fft_auto_width", hmv.FFT64, -1, 0),
+    for name, method, levels, w in (("exact_ntt_two_primes", hmv.NTT, -1, 0),
+                                    ("split_fp64_fft_auto_width", hmv.FFT64, -1, 0),
                                     ("split_fp64_fft_16bit_pieces", hmv.FFT64, -1, 16),
                                     ("tensor_core_schoolbook_L0", hmv.KARATSUBA, 0, 0),
                                     ("plain_schoolbook_cuda_cores", hmv.SCHOOLBOOK, -1, 0)):
@@ -636,7 +638,7 @@ def main(argv=None):
     ap.add_argument("--digit-split", type=int, choices=[-1, 0, 1, 2, 4, 6, 8], default=-1,
                     help="split of the mantissas on top of the index recursion: Karatsuba levels 1 or 2, "
                          "Toom-4, Toom-6 or Toom-8 (4, 6, 8), none (0) or the cost model's choice (-1)")
-    ap.add_argument("--method", choices=["auto", "karatsuba", "fft64", "schoolbook"], default="auto",
+    ap.add_argument("--method", choices=["auto", "karatsuba", "fft64", "schoolbook", "ntt"], default="auto",
                     help="product method (profiling runs; the metric uses auto = Karatsuba + tcgen05)")
     ap.add_argument("--tile", type=int, choices=[0, 128, 256], default=0,
                     help="leaf tile width in product digits (profiling runs; 0: the plan's default)")

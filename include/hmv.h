@@ -67,10 +67,16 @@ typedef enum {
                               the leaf tile width */
     HMV_SCHOOLBOOK = 1,    /* plain schoolbook on 32-bit limbs, CUDA cores */
     HMV_KARATSUBA = 2,     /* Algorithm 1 to the given depth, tensor-core leaves */
-    HMV_FFT64 = 3          /* split-FP64 FFT with a proven rounding bound; when the bound
+    HMV_FFT64 = 3,         /* split-FP64 FFT with a proven rounding bound; when the bound
                               for the actual data is not below 1/2 the call computes the
                               product with the Karatsuba path instead (counted in
                               hmv_stats.fft_fallbacks) */
+    HMV_NTT = 4            /* the same decomposition into 16-bit pieces and one cyclic
+                              convolution (Secs. 1-2), done exactly with number-theoretic
+                              transforms modulo two 31-bit primes: no error bound to check.
+                              Needs (2n-1)(2 ceil(b/16) - 1) <= 2^26 (e.g. n <= 8079 at
+                              b = 33220), else hmv_plan returns HMV_EUNSUPPORTED; levels
+                              must be -1 or 0 and flags hold no split or tile flag */
 } hmv_method;
 
 /* flags for hmv_desc.flags */
@@ -140,8 +146,8 @@ typedef struct {
     /* with HMV_FLAG_TIMING: accumulated milliseconds and launch counts */
     double ms_prepass, ms_leaf, ms_post, ms_round, ms_total;
     int64_t launches_leaf, launches_total, matvecs;
-    /* HMV_FFT64 plans */
-    int32_t fft_piece_bits;  /* w */
+    /* HMV_FFT64 and HMV_NTT plans */
+    int32_t fft_piece_bits;  /* w (16 for HMV_NTT) */
     int32_t fft_log2_len;    /* K: cyclic convolution length 2^K */
     double fft_bound;        /* error bound of the last matvec (the result is exact when < 1/2) */
     double fft_max_dist;     /* largest |c - round(c)| seen in the last FFT matvec */

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhmv.so")
-SOURCES = ["hmv_api.cu", "hmv_digits.cu", "hmv_leaf_tc.cu", "hmv_schoolbook.cu", "hmv_noalloc.cu", "hmv_fft.cu", "hmv_batch.cu", "hmv_split.cu", "hmv_blas.cu"]
+SOURCES = ["hmv_api.cu", "hmv_digits.cu", "hmv_leaf_tc.cu", "hmv_schoolbook.cu", "hmv_noalloc.cu", "hmv_fft.cu", "hmv_ntt.cu", "hmv_batch.cu", "hmv_split.cu", "hmv_blas.cu"]
 GENCODE = "-gencode=arch=compute_103a,code=sm_103a"
 
 

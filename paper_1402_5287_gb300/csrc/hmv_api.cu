@@ -351,7 +351,7 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
     const hmv_desc &d = *desc;
     if (d.n < 1 || d.b < 1 || d.b > kMaxBits || d.nrhs < 1) return HMV_EINVAL;
     if (d.kind < HMV_HANKEL || d.kind > HMV_CIRCULANT) return HMV_EINVAL;
-    if (d.method < HMV_AUTO || d.method > HMV_FFT64) return HMV_EINVAL;
+    if (d.method < HMV_AUTO || d.method > HMV_NTT) return HMV_EINVAL;
     if (d.levels < -1 || d.levels > kMaxLevels) return HMV_EINVAL;
     if (d.flags & ~(HMV_FLAG_TIMING | HMV_FLAG_SIMT_LEAF | HMV_FLAG_DIGIT_SPLIT1 | HMV_FLAG_DIGIT_SPLIT2 |
                     HMV_FLAG_TILE128 | HMV_FLAG_TILE256 | HMV_FLAG_DIGIT_TOOM4 | HMV_FLAG_DIGIT_TOOM6 |
@@ -373,6 +373,11 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
     if (d.method == HMV_FFT64 ? (d.piece_bits != 0 && (d.piece_bits < 4 || d.piece_bits > 16)) : d.piece_bits != 0)
         return HMV_EINVAL;
     if (static_cast<long long>(d.n) * d.nrhs > (1LL << 30)) return HMV_EINVAL;
+    if (d.method == HMV_NTT) {
+        if (d.levels > 0 || (d.flags & ~HMV_FLAG_TIMING)) return HMV_EINVAL;
+        int P, S, K;
+        if (!ntt_geometry(d.n, d.b, P, S, K)) return HMV_EUNSUPPORTED;
+    }
 
     hmv_plan_s *p = new (std::nothrow) hmv_plan_s();
     if (!p) return HMV_ENOMEM;
@@ -455,6 +460,15 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
         p->L = 0;
         p->ZW = 2 * p->L32 + 2;
         g(dalloc(p, &p->colsum, static_cast<size_t>(n) * 2 * p->L32));
+    } else if (p->method == HMV_NTT) {
+        p->L = 0;
+        p->ZW = 2 * p->L32 + 2;  // |Z| < n 2^(2b)
+        ntt_geometry(n, d.b, p->ntt_P, p->ntt_S, p->ntt_K);
+        p->ntt_N = 1LL << p->ntt_K;
+        g(dalloc(p, &p->ntt_a, static_cast<size_t>(p->ntt_N)));
+        g(dalloc(p, &p->ntt_x, static_cast<size_t>(p->ntt_N)));
+        g(dalloc(p, &p->ntt_tw, static_cast<size_t>(4) << 13));
+        if (g.err == cudaSuccess && !dry_run) g(ntt_init(p));
     } else {
         // depth: explicit, or the cheapest by the cost model (node order >= 2);
         // under HMV_AUTO the tile width too (128 only pays where it cuts the
@@ -628,7 +642,7 @@ hmv_status hmv_load_matrix(hmv_plan_t *p, const hmv_vec *h) {
         p->loaded = true;
         return HMV_OK;
     }
-    if (p->method != HMV_SCHOOLBOOK) {
+    if (p->method != HMV_SCHOOLBOOK && p->method != HMV_NTT) {
         // level 0 holds the Hankel sequence (circulant: the wrapped Toeplitz sequence)
         g(launch_encode(p, p->h_limbs_d, p->h_neg_d, 2 * p->n - 1, p->kind == HMV_CIRCULANT ? p->n : 0, p->a_lvl[0]));
         for (int l = 0; l < p->L; ++l) g(launch_prepass(p, l, true, p->a_lvl[l % 2], p->a_lvl[(l + 1) % 2]));
@@ -636,6 +650,7 @@ hmv_status hmv_load_matrix(hmv_plan_t *p, const hmv_vec *h) {
         if (p->hrev) g(launch_pack_matrix(p, p->a_leaf));
     }
     if (p->method == HMV_FFT64) g(fft_load_matrix(p));
+    if (p->method == HMV_NTT) g(ntt_load_matrix(p));
     int32_t st[8] = {0};
     g(cudaMemcpyAsync(st, p->dstat, sizeof st, cudaMemcpyDeviceToHost, p->stream));
     g(cudaStreamSynchronize(p->stream));
@@ -701,6 +716,12 @@ hmv_status hmv_matvec(hmv_plan_t *p, const hmv_vec *x, hmv_vec *y) {
             timing_mark(p, 2);
             g(cudaMemsetAsync(p->fft_maxdist, 0, sizeof(unsigned long long), p->stream));
             g(fft_vector_product(p, r));
+            timing_mark(p, 3);
+            timing_mark(p, 4);
+        } else if (p->method == HMV_NTT) {
+            timing_mark(p, 2);
+            g(ntt_vector_product(p, xr, xnr, r));
+            p->ntt_matvecs++;
             timing_mark(p, 3);
             timing_mark(p, 4);
         } else if (p->method == HMV_SCHOOLBOOK) {
@@ -793,8 +814,8 @@ hmv_status hmv_get_stats(const hmv_plan_t *p, hmv_stats *o) {
     o->launches_leaf = p->launches_leaf;
     o->launches_total = p->launches_total;
     o->matvecs = p->matvecs;
-    o->fft_piece_bits = p->fft_w;
-    o->fft_log2_len = p->fft_K;
+    o->fft_piece_bits = p->method == HMV_NTT ? 16 : p->fft_w;
+    o->fft_log2_len = p->method == HMV_NTT ? p->ntt_K : p->fft_K;
     o->fft_bound = p->fft_bound;
     o->fft_max_dist = p->fft_maxdist_h;
     o->fft_matvecs = p->fft_matvecs;

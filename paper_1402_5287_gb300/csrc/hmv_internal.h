@@ -110,6 +110,14 @@ struct hmv_plan_s {
     // problem and tile lists of an hmv_matvec_many step led by this plan)
     hmv::GrowBuf dot_buf, lin_buf, many_dev, many_host{nullptr, 0, true};
 
+    // exact NTT path (two primes): geometry, the matrix spectrum / N, the
+    // vector's work array, twiddle tables
+    int ntt_P = 0, ntt_S = 0, ntt_K = 0;
+    long long ntt_N = 0;
+    uint2 *ntt_a = nullptr, *ntt_x = nullptr;
+    uint32_t *ntt_tw = nullptr;
+    int64_t ntt_matvecs = 0;
+
     // split-FP64 FFT path
     int fft_w = 0, fft_P = 0, fft_S = 0, fft_K = 0;
     long long fft_N = 0;
@@ -141,6 +149,10 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
                        bool dry_run = false);
 cudaError_t launch_validate(hmv_plan_s *p, const uint32_t *limbs, int rows);
 cudaError_t launch_colsum_normalize(hmv_plan_s *p, int rhs);
+bool ntt_geometry(int n, int b, int &P, int &S, int &K);
+cudaError_t ntt_init(hmv_plan_s *p);
+cudaError_t ntt_load_matrix(hmv_plan_s *p);
+cudaError_t ntt_vector_product(hmv_plan_s *p, const uint32_t *xl, const uint8_t *xn, int rhs);
 cudaError_t leaf_tc_prepare();
 // the unsplit plans under p (p itself when it is not split)
 void collect_leaf_plans(hmv_plan_s *p, std::vector<hmv_plan_s *> &out);

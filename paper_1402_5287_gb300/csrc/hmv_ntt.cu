@@ -1,0 +1,447 @@
+// Exact number-theoretic-transform path (the decomposition of Beliakov,
+// arXiv:1402.5287, Secs. 1-2: the multiprecision numbers split into standard
+// precision pieces and the Hankel product done as ONE cyclic convolution),
+// with the floating-point FFT replaced by transforms modulo two primes, so
+// that the convolution is exact with no error bound to check.
+//
+// Packing (Kronecker substitution, as in the split-FP64 path): every entry is
+// cut into P = ceil(b / 16) pieces of 16 bits carrying the entry's sign,
+// v = sum_p v_p 2^(16 p), |v_p| < 2^16.  With slot stride S = 2P - 1,
+//     a[k S + p] = piece p of h_k,          k = 0..2n-2
+//     c[(n-1-j) S + q] = piece q of x_j,    j = 0..n-1
+// and the cyclic convolution of length N = 2^K >= (2n-1) S holds in slot
+// n-1+i the sums z_i[t] = sum_j sum_{p+q=t} h_{i+j}[p] x_j[q], t < 2P-1, of
+// y_i = sum_t z_i[t] 2^(16 t); no wrapped term reaches those slots.
+//
+// Exactness: |z_i[t]| < n P 2^32 <= 2^57 (N <= 2^26 bounds n P), below half
+// the product of the primes p1 = 15 2^27 + 1 and p2 = 27 2^26 + 1 (about
+// 2^61.7), so the Chinese remainder of the two residues, taken in
+// (-p1 p2 / 2, p1 p2 / 2), is the coefficient itself.  Both primes have
+// 2^26 | p - 1, which bounds N to 2^26.
+//
+// Arithmetic: Montgomery multiplication modulo each prime with R = 2^32
+// (p < 2^31, so sums of two residues fit 32 bits); twiddles are kept in
+// Montgomery form in two small tables per prime (w^m = T_hi[m >> 13] T_lo[m
+// & 8191]), data in normal form.  Radix-2 transforms, forward by decimation
+// in frequency (natural order in, bit-reversed out), inverse by decimation
+// in time (bit-reversed in, natural out), so no permutation pass; up to 9
+// stages per pass in shared memory, both primes in one pass (a uint2 per
+// point).  The matrix's spectrum is kept per plan, scaled by 1/N.
+#include <cstring>
+#include <vector>
+
+#include "hmv_internal.h"
+
+namespace hmv {
+
+constexpr uint32_t kNttP0 = 2013265921u, kNttP1 = 1811939329u;  // 15 2^27 + 1, 27 2^26 + 1
+constexpr uint32_t kNttP[2] = {kNttP0, kNttP1};
+constexpr uint32_t kNttRoot[2] = {31u, 13u};                // primitive roots
+constexpr int kNttMaxK = 26;
+constexpr int kNttPieceBits = 16;
+constexpr int kTwLoBits = 13;
+
+namespace {
+
+constexpr int kNttMaxR = 9;   // radix-2 stages per pass
+constexpr int kNttCols = 16;  // sub-transforms per block (16 x 8 bytes: 128-byte rows)
+static_assert(kNttCols == 16, "the pass indexes columns with e & 15 and e >> 4");
+
+struct NttConst {
+    uint32_t p[2], pinv[2];  // pinv = -p^-1 mod 2^32
+    const uint32_t *tlo[2], *thi[2];
+};
+
+__device__ __forceinline__ uint32_t mont_mul(uint32_t a, uint32_t b, uint32_t p, uint32_t pinv) {
+    const uint64_t t = static_cast<uint64_t>(a) * b;  // < p^2 < 2^62
+    const uint32_t m = static_cast<uint32_t>(t) * pinv;
+    const uint32_t u = static_cast<uint32_t>((t + static_cast<uint64_t>(m) * p) >> 32);  // < 2p
+    return u >= p ? u - p : u;
+}
+__device__ __forceinline__ uint32_t mod_add(uint32_t a, uint32_t b, uint32_t p) {
+    const uint32_t s = a + b;  // < 2p < 2^32
+    return s >= p ? s - p : s;
+}
+__device__ __forceinline__ uint32_t mod_sub(uint32_t a, uint32_t b, uint32_t p) { return a >= b ? a - b : a + p - b; }
+
+// w_N^m (forward) or w_N^-m (inverse) in Montgomery form, 0 <= m < N/2;
+// w^-m = -w^(N/2 - m) for m > 0
+__device__ __forceinline__ uint32_t table_power(const NttConst &c, int k, int m) {
+    return mont_mul(__ldg(c.thi[k] + (m >> kTwLoBits)), __ldg(c.tlo[k] + (m & ((1 << kTwLoBits) - 1))), c.p[k],
+                    c.pinv[k]);
+}
+__device__ __forceinline__ uint32_t twiddle(const NttConst &c, int k, int m, int inverse, int half) {
+    if (!inverse || m == 0) return table_power(c, k, m);
+    return c.p[k] - table_power(c, k, half - m);  // a unit: never 0
+}
+
+// 16-bit pieces of sign-magnitude rows as residues modulo both primes, piece
+// p of row k at slot(k) S + p; slot(k) = k (matrix side) or n-1-k (vector
+// side); circ_n > 0 maps row k to entry (circ_n-1-k) mod circ_n.  One thread
+// per limb (two pieces).
+__global__ void k_ntt_pieces(const uint32_t *__restrict__ limbs, const uint8_t *__restrict__ neg, int rows, int L32,
+                             int P, int S, int reverse_n, int circ_n, uint2 *__restrict__ out, int32_t *dstat) {
+    const long long id = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (id >= static_cast<long long>(rows) * L32) return;
+    const int k = static_cast<int>(id / L32), q = static_cast<int>(id % L32);
+    int src = k;
+    if (circ_n > 0) src = ((circ_n - 1 - k) % circ_n + circ_n) % circ_n;
+    const uint32_t limb = limbs[static_cast<size_t>(src) * L32 + q];
+    const bool sg = neg[src] != 0;
+    const long long slot = reverse_n > 0 ? (reverse_n - 1 - k) : k;
+    uint2 *o = out + slot * S;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int pc = 2 * q + h;
+        const uint32_t v = (limb >> (16 * h)) & 0xFFFFu;
+        if (pc >= P) {
+            if (v) set_status(dstat, DEV_BADINPUT);  // bits beyond the pieces (cannot happen for valid input)
+            continue;
+        }
+        o[pc] = (sg && v) ? make_uint2(kNttP0 - v, kNttP1 - v) : make_uint2(v, v);
+    }
+}
+
+// One pass of radix-2 stages on sub-transforms of 2^r points spaced
+// st = 2^(s_lo-1) apart inside blocks of 2^s_hi points (the split-FP64 path's
+// pass structure):
+//   forward (decimation in frequency), stages s_hi down to s_lo:
+//     (u, v) -> (u + v, (u - v) w_{2^s}^j)
+//   inverse (decimation in time), stages s_lo up to s_hi:
+//     (u, v) -> (u + w_{2^s}^-j v, u - w_{2^s}^-j v)
+// with j = (index of u) mod 2^(s-1) and w_{2^s}^j = w_N^(j 2^(K-s)).
+__global__ void __launch_bounds__(256) k_ntt_pass(uint2 *__restrict__ d, NttConst c, int K, int s_hi, int r,
+                                                  int inverse) {
+    extern __shared__ uint2 nsm[];  // [2^r][kNttCols]
+    // every index fits 32 bits (N <= 2^26) and every span is a power of two:
+    // shifts and masks only
+    const int s_lo = s_hi - r + 1;
+    const int lst = s_lo - 1;  // log2 of the point spacing st
+    const int half = 1 << (K - 1);
+    const int lC = lst >= 4 ? 4 : lst;  // log2 of C, the columns of one block of 2^s_hi points
+    int blk0, low0;
+    if (lst >= 4) {
+        const int lgroups = lst - 4;
+        blk0 = static_cast<int>(blockIdx.x) >> lgroups;
+        low0 = (static_cast<int>(blockIdx.x) & ((1 << lgroups) - 1)) << 4;
+    } else {
+        blk0 = static_cast<int>(blockIdx.x) << (4 - lC);
+        low0 = 0;
+    }
+    const int cmask = (1 << lC) - 1;
+    const int pts = 1 << r;
+    auto gidx = [&](int t, int q) -> int { return ((blk0 + (q >> lC)) << s_hi) + low0 + (q & cmask) + (t << lst); };
+    for (int e = threadIdx.x; e < pts * kNttCols; e += blockDim.x) nsm[e] = d[gidx(e >> 4, e & 15)];
+    __syncthreads();
+    const int nbf = (pts / 2) * kNttCols;
+    const int q = threadIdx.x & 15;  // the thread's column in every stage (blockDim is a multiple of 16)
+    for (int st_i = 0; st_i < r; ++st_i) {
+        const int s = inverse ? (s_lo + st_i) : (s_hi - st_i);
+        const int lh = s - s_lo;  // log2 of the span in sub-transform units
+        const int ht = 1 << lh;
+        // The thread's butterflies bf = (tid >> 4) + 16 it have u at point
+        // tlow = bf mod ht of their half block, so j = low0 + q + tlow st and
+        // the twiddle exponent m = j 2^(K-s) = mb + tlow 2^lw: constant over it
+        // when ht <= 16, else a geometric sequence in steps of 16 tlow that
+        // restarts every ht / 16 butterflies.  One table lookup per stage.
+        const int lw = K - 1 - lh;
+        const int mb = (low0 + (q & cmask)) << (K - s);
+        const int tl0 = (threadIdx.x >> 4) & (ht - 1);
+        const int per = ht > 16 ? (ht >> 4) : 1;
+        uint32_t w0[2], ws[2], w[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            w0[k] = twiddle(c, k, mb + (tl0 << lw), inverse, half);
+            ws[k] = per > 1 ? twiddle(c, k, 16 << lw, inverse, half) : 0u;
+            w[k] = w0[k];
+        }
+        int it = 0;
+        for (int e = threadIdx.x; e < nbf; e += blockDim.x, ++it) {
+            const int bf = e >> 4;
+            const int tlow = bf & (ht - 1);                  // position inside the half block
+            const int t = ((bf >> lh) << (lh + 1)) + tlow;   // u's point
+            if (it > 0) {
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+                    w[k] = (it & (per - 1)) == 0 ? w0[k] : mont_mul(w[k], ws[k], c.p[k], c.pinv[k]);
+            }
+            const uint2 u = nsm[(t << 4) + q], v = nsm[((t + ht) << 4) + q];
+            uint32_t uo[2] = {u.x, u.y}, vo[2] = {v.x, v.y};
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const uint32_t p = c.p[k], pinv = c.pinv[k];
+                if (!inverse) {
+                    const uint32_t a = mod_add(uo[k], vo[k], p);
+                    vo[k] = mont_mul(mod_sub(uo[k], vo[k], p), w[k], p, pinv);
+                    uo[k] = a;
+                } else {
+                    const uint32_t tv = mont_mul(vo[k], w[k], p, pinv);
+                    vo[k] = mod_sub(uo[k], tv, p);
+                    uo[k] = mod_add(uo[k], tv, p);
+                }
+            }
+            nsm[(t << 4) + q] = make_uint2(uo[0], uo[1]);
+            nsm[((t + ht) << 4) + q] = make_uint2(vo[0], vo[1]);
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < pts * kNttCols; e += blockDim.x) d[gidx(e >> 4, e & 15)] = nsm[e];
+}
+
+// x <- x * a pointwise (a: the matrix spectrum times 1/N, in Montgomery form)
+__global__ void k_ntt_pointwise(uint2 *__restrict__ x, const uint2 *__restrict__ a, long long N, NttConst c) {
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const uint2 u = x[i], v = a[i];
+        x[i] = make_uint2(mont_mul(u.x, v.x, c.p[0], c.pinv[0]), mont_mul(u.y, v.y, c.p[1], c.pinv[1]));
+    }
+}
+
+// a <- a * f (f = R^2 / N mod p: the spectrum in Montgomery form, times 1/N)
+__global__ void k_ntt_scale(uint2 *__restrict__ a, long long N, NttConst c, uint32_t f0, uint32_t f1) {
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const uint2 u = a[i];
+        a[i] = make_uint2(mont_mul(u.x, f0, c.p[0], c.pinv[0]), mont_mul(u.y, f1, c.p[1], c.pinv[1]));
+    }
+}
+
+// Row i of the product: the coefficients z[t] = c[(i+n-1) S + t], t < 2P-1,
+// each the Chinese remainder of its two residues taken in (-p1 p2/2,
+// p1 p2/2), then Z_i = sum_t z[t] 2^(16 t) as |Z| limbs, sign and bit length
+// (as the other paths).  One warp per row, a window of 1024 positions at a
+// time, 32 consecutive positions per lane: a carry chain base 2^16 per lane,
+// then the carries passed up one lane per round until none is left; two
+// positions make a limb.  A final carry of -1 means Z < 0: the limbs hold its
+// two's complement and are negated in place.
+__device__ __forceinline__ long long ntt_crt(uint2 r, const NttConst &c, uint32_t inv1R) {
+    const uint32_t p1 = c.p[0], p2 = c.p[1];
+    const uint32_t r1m = r.x >= p2 ? r.x - p2 : r.x;  // r1 < p1 < 2 p2
+    const uint32_t x = mont_mul(mod_sub(r.y, r1m, p2), inv1R, p2, c.pinv[1]);  // (r2 - r1) / p1 mod p2
+    const unsigned long long M = static_cast<unsigned long long>(p1) * p2;
+    const unsigned long long v = r.x + static_cast<unsigned long long>(p1) * x;  // in [0, p1 p2)
+    return v > M / 2 ? static_cast<long long>(v) - static_cast<long long>(M) : static_cast<long long>(v);
+}
+constexpr int kPosPerLane = 32;
+__global__ void __launch_bounds__(256) k_ntt_extract(const uint2 *__restrict__ cvec, int n, int S, int T, NttConst c,
+                                                     uint32_t inv1R, uint32_t *__restrict__ zmag,
+                                                     uint8_t *__restrict__ zneg, int32_t *__restrict__ zbits, int ZW,
+                                                     int32_t *dstat, int row_offset) {
+    const int lane = threadIdx.x & 31;
+    const int i = static_cast<int>((static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
+    if (i >= n) return;  // warp-uniform
+    const uint2 *row = cvec + static_cast<long long>(i + n - 1) * S;
+    uint32_t *z = zmag + static_cast<size_t>(row_offset + i) * ZW;
+    const int span = max(T, 2 * ZW);  // every limb of the row is written
+    long long wc = 0;
+    bool above_nonzero = false, above_not_ones = false;
+    for (int t0 = 0; t0 < span; t0 += 32 * kPosPerLane) {
+        const int tb = t0 + kPosPerLane * lane;
+        long long v[kPosPerLane];
+#pragma unroll
+        for (int k = 0; k < kPosPerLane; ++k) v[k] = (tb + k < T) ? ntt_crt(row[tb + k], c, inv1R) : 0;
+        long long cy = (lane == 0) ? wc : 0;
+#pragma unroll
+        for (int k = 0; k < kPosPerLane; ++k) {
+            const long long s = v[k] + cy;
+            v[k] = s & 0xFFFF;
+            cy = s >> 16;  // arithmetic: floor
+        }
+        long long pending = cy, out = 0;
+        for (int round = 0; round <= 32; ++round) {
+            out += __shfl_sync(0xffffffffu, pending, 31);
+            long long incoming = __shfl_up_sync(0xffffffffu, pending, 1);
+            if (lane == 0) incoming = 0;
+            if (!__any_sync(0xffffffffu, incoming != 0)) break;
+            cy = incoming;
+#pragma unroll
+            for (int k = 0; k < kPosPerLane; ++k) {
+                const long long s = v[k] + cy;
+                v[k] = s & 0xFFFF;
+                cy = s >> 16;
+            }
+            pending = cy;
+        }
+        wc = out;
+#pragma unroll
+        for (int k = 0; k < kPosPerLane / 2; ++k) {
+            const uint32_t limb = static_cast<uint32_t>(v[2 * k]) | (static_cast<uint32_t>(v[2 * k + 1]) << 16);
+            const int li = tb / 2 + k;
+            if (li < ZW) {
+                z[li] = limb;
+            } else {
+                above_nonzero |= limb != 0u;
+                above_not_ones |= limb != 0xFFFFFFFFu;
+            }
+        }
+    }
+    // wc: 0 (Z >= 0) or -1 (the limbs are 2^(32 ZW) + Z); otherwise Z does not fit
+    const bool negative = wc == -1;
+    bool bad = (wc != 0 && wc != -1) || (negative ? above_not_ones : above_nonzero);
+    __syncwarp();
+    if (negative) {
+        int k0 = ZW;  // lowest non-zero limb
+        for (int w = lane; w < ZW; w += 32)
+            if (z[w]) { k0 = w; break; }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) k0 = min(k0, __shfl_xor_sync(0xffffffffu, k0, off));
+        if (k0 == ZW) bad = true;
+        for (int w = lane; w < ZW; w += 32) {
+            if (w == k0) z[w] = ~z[w] + 1u;
+            else if (w > k0) z[w] = ~z[w];
+        }
+        __syncwarp();
+    }
+    int bits = 0;
+    for (int w = lane; w < ZW; w += 32)
+        if (z[w]) bits = 32 * w + (32 - __clz(z[w]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) bits = max(bits, __shfl_xor_sync(0xffffffffu, bits, off));
+    if (__any_sync(0xffffffffu, bad) && lane == 0) set_status(dstat, DEV_OVERFLOW);
+    if (lane == 0) {
+        zbits[row_offset + i] = bits;
+        zneg[row_offset + i] = (bits > 0 && negative) ? 1 : 0;
+        atomicMax(dstat + 1, bits);
+    }
+}
+
+uint64_t mulmod(uint64_t a, uint64_t b, uint64_t p) { return (a * b) % p; }  // a, b < p < 2^31
+uint64_t powmod(uint64_t a, uint64_t e, uint64_t p) {
+    uint64_t r = 1;
+    for (a %= p; e; e >>= 1, a = mulmod(a, a, p))
+        if (e & 1) r = mulmod(r, a, p);
+    return r;
+}
+
+NttConst ntt_const(const hmv_plan_s *p) {
+    NttConst c;
+    for (int k = 0; k < 2; ++k) {
+        c.p[k] = kNttP[k];
+        uint32_t inv = 1;  // p^-1 mod 2^32 by Newton's iteration (p odd)
+        for (int it = 0; it < 5; ++it) inv *= 2u - kNttP[k] * inv;
+        c.pinv[k] = 0u - inv;
+        c.tlo[k] = p->ntt_tw + (2 * k) * (1 << kTwLoBits);
+        c.thi[k] = p->ntt_tw + (2 * k + 1) * (1 << kTwLoBits);
+    }
+    return c;
+}
+
+int grid_for(long long work, int threads = 256) {
+    const long long g = (work + threads - 1) / threads;
+    return static_cast<int>(g < 65535LL * 32 ? g : 65535LL * 32);
+}
+
+cudaError_t run_ntt(hmv_plan_s *p, uint2 *data, bool inverse) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_ntt_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(kNttCols * (1u << kNttMaxR) * sizeof(uint2)));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int K = p->ntt_K;
+    const NttConst c = ntt_const(p);
+    int bounds[8][2], np = 0;  // passes from the top stage down, up to kNttMaxR stages each
+    for (int s_hi = K; s_hi >= 1; s_hi -= kNttMaxR) {
+        bounds[np][0] = s_hi;
+        bounds[np][1] = s_hi >= kNttMaxR ? kNttMaxR : s_hi;
+        ++np;
+    }
+    for (int k = 0; k < np; ++k) {
+        const int idx = inverse ? (np - 1 - k) : k;
+        const int s_hi = bounds[idx][0], r = bounds[idx][1];
+        const long long blocks = (p->ntt_N >> r) / kNttCols;
+        const size_t smem = static_cast<size_t>(kNttCols) * (1u << r) * sizeof(uint2);
+        k_ntt_pass<<<static_cast<unsigned>(blocks), 256, smem, p->stream>>>(data, c, K, s_hi, r, inverse ? 1 : 0);
+        p->launches_total++;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+// Geometry of the NTT path: P pieces of 16 bits, slot stride S = 2P - 1,
+// N = 2^K >= (2n - 1) S; false when N would exceed 2^26.
+bool ntt_geometry(int n, int b, int &P, int &S, int &K) {
+    P = (b + kNttPieceBits - 1) / kNttPieceBits;
+    S = 2 * P - 1;
+    const long long need = static_cast<long long>(2 * n - 1) * S;
+    K = kNttMaxR + 4;  // at least one block of 16 sub-transforms in the first pass
+    while ((1LL << K) < need) ++K;
+    return K <= kNttMaxK;
+}
+
+// Twiddle tables (Montgomery form, R = 2^32) for both primes: T_lo[i] =
+// w^i, T_hi[i] = w^(i 2^13), w a primitive 2^K-th root of unity.
+cudaError_t ntt_init(hmv_plan_s *p) {
+    const int TS = 1 << kTwLoBits;
+    std::vector<uint32_t> tab(4 * static_cast<size_t>(TS));
+    for (int k = 0; k < 2; ++k) {
+        const uint64_t P = kNttP[k];
+        const uint64_t w = powmod(kNttRoot[k], (P - 1) >> p->ntt_K, P);
+        const uint64_t R = (uint64_t(1) << 32) % P;
+        uint64_t lo = R, hi = R;  // w^0 R
+        const uint64_t wstep = powmod(w, TS, P);
+        for (int i = 0; i < TS; ++i) {
+            tab[(2 * k) * TS + i] = static_cast<uint32_t>(lo);
+            tab[(2 * k + 1) * TS + i] = static_cast<uint32_t>(hi);
+            lo = mulmod(lo, w, P);
+            hi = mulmod(hi, wstep, P);
+        }
+    }
+    return cudaMemcpyAsync(p->ntt_tw, tab.data(), tab.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, p->stream);
+}
+
+// Matrix side: pieces of h, forward transform, scaling to Montgomery form / N.
+cudaError_t ntt_load_matrix(hmv_plan_s *p) {
+    const NttConst c = ntt_const(p);
+    cudaError_t e = cudaMemsetAsync(p->ntt_a, 0, p->ntt_N * sizeof(uint2), p->stream);
+    if (e != cudaSuccess) return e;
+    const int rows = 2 * p->n - 1;
+    k_ntt_pieces<<<grid_for(static_cast<long long>(rows) * p->L32), 256, 0, p->stream>>>(
+        p->h_limbs_d, p->h_neg_d, rows, p->L32, p->ntt_P, p->ntt_S, 0, p->kind == HMV_CIRCULANT ? p->n : 0, p->ntt_a,
+        p->dstat);
+    p->launches_total++;
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = run_ntt(p, p->ntt_a, false);
+    if (e != cudaSuccess) return e;
+    uint32_t f[2];
+    for (int k = 0; k < 2; ++k) {  // R^2 / N mod p: mont_mul(A, f) = A R / N, the Montgomery form of A / N
+        const uint64_t P = kNttP[k];
+        const uint64_t R = (uint64_t(1) << 32) % P;
+        f[k] = static_cast<uint32_t>(mulmod(mulmod(R, R, P), powmod(p->ntt_N % P, P - 2, P), P));
+    }
+    k_ntt_scale<<<grid_for(p->ntt_N), 256, 0, p->stream>>>(p->ntt_a, p->ntt_N, c, f[0], f[1]);
+    p->launches_total++;
+    return cudaGetLastError();
+}
+
+// Vector side for right-hand side rhs: pieces, forward transform, pointwise
+// product, inverse transform, exact rows into zmag/zneg/zbits.
+cudaError_t ntt_vector_product(hmv_plan_s *p, const uint32_t *xl, const uint8_t *xn, int rhs) {
+    const NttConst c = ntt_const(p);
+    cudaError_t e = cudaMemsetAsync(p->ntt_x, 0, p->ntt_N * sizeof(uint2), p->stream);
+    if (e != cudaSuccess) return e;
+    k_ntt_pieces<<<grid_for(static_cast<long long>(p->n) * p->L32), 256, 0, p->stream>>>(
+        xl, xn, p->n, p->L32, p->ntt_P, p->ntt_S, p->n, 0, p->ntt_x, p->dstat);
+    p->launches_total++;
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = run_ntt(p, p->ntt_x, false);
+    if (e != cudaSuccess) return e;
+    k_ntt_pointwise<<<grid_for(p->ntt_N), 256, 0, p->stream>>>(p->ntt_x, p->ntt_a, p->ntt_N, c);
+    p->launches_total++;
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = run_ntt(p, p->ntt_x, true);
+    if (e != cudaSuccess) return e;
+    const uint64_t P2 = kNttP[1];
+    const uint32_t inv1R =
+        static_cast<uint32_t>(mulmod(powmod(kNttP[0] % P2, P2 - 2, P2), (uint64_t(1) << 32) % P2, P2));
+    k_ntt_extract<<<static_cast<unsigned>((p->n + 7) / 8), 256, 0, p->stream>>>(
+        p->ntt_x, p->n, p->ntt_S, 2 * p->ntt_P - 1, c, inv1R, p->zmag, p->zneg, p->zbits, p->ZW, p->dstat, rhs * p->n);
+    p->launches_total++;
+    return cudaGetLastError();
+}
+
+}  // namespace hmv

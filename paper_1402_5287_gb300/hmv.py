@@ -13,7 +13,7 @@ import numpy as np
 from .inputs import FixedVec
 
 HANKEL, TOEPLITZ, CIRCULANT = 0, 1, 2
-AUTO, SCHOOLBOOK, KARATSUBA, FFT64 = 0, 1, 2, 3
+AUTO, SCHOOLBOOK, KARATSUBA, FFT64, NTT = 0, 1, 2, 3, 4
 FLAG_TIMING, FLAG_SIMT_LEAF, FLAG_DIGIT_SPLIT1, FLAG_DIGIT_SPLIT2, FLAG_TILE128 = 1, 2, 4, 8, 16
 FLAG_DIGIT_TOOM4, FLAG_DIGIT_TOOM6, FLAG_DIGIT_TOOM8 = 32, 64, 256
 FLAG_TILE256 = 128
