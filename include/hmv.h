@@ -342,6 +342,14 @@ hmv_status hmv_lincomb(hmv_plan_t *plan, int32_t count, const hmv_scalar *c, con
  * launches = 0 disarms the hook.  HMV_EINVAL for arguments out of range. */
 hmv_status hmv_test_leaf_stall(int32_t launches, int64_t wait_ns);
 
+/* ---- Measurement --------------------------------------------------------
+ * The rate of independent 32-bit Montgomery products (modulo the HMV_NTT
+ * path's first prime) that this GPU sustains, from a short timed kernel on
+ * `stream` (the best of three launches): the arithmetic that bounds the
+ * NTT path's transform stages, used as that path's roofline.  Allocates
+ * and frees a small buffer; synchronous. */
+hmv_status hmv_measure_montgomery_rate(void *stream, double *products_per_s);
+
 /* Static description of a status code. */
 const char *hmv_status_string(hmv_status s);
 

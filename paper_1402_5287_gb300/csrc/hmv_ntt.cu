@@ -110,29 +110,35 @@ __global__ void k_ntt_pieces(const uint32_t *__restrict__ limbs, const uint8_t *
 //   inverse (decimation in time), stages s_lo up to s_hi:
 //     (u, v) -> (u + w_{2^s}^-j v, u - w_{2^s}^-j v)
 // with j = (index of u) mod 2^(s-1) and w_{2^s}^j = w_N^(j 2^(K-s)).
-__global__ void __launch_bounds__(256) k_ntt_pass(uint2 *__restrict__ d, NttConst c, int K, int s_hi, int r,
-                                                  int inverse) {
-    extern __shared__ uint2 nsm[];  // [2^r][kNttCols]
-    // every index fits 32 bits (N <= 2^26) and every span is a power of two:
-    // shifts and masks only
-    const int s_lo = s_hi - r + 1;
-    const int lst = s_lo - 1;  // log2 of the point spacing st
-    const int half = 1 << (K - 1);
-    const int lC = lst >= 4 ? 4 : lst;  // log2 of C, the columns of one block of 2^s_hi points
-    int blk0, low0;
-    if (lst >= 4) {
-        const int lgroups = lst - 4;
-        blk0 = static_cast<int>(blockIdx.x) >> lgroups;
-        low0 = (static_cast<int>(blockIdx.x) & ((1 << lgroups) - 1)) << 4;
-    } else {
-        blk0 = static_cast<int>(blockIdx.x) << (4 - lC);
-        low0 = 0;
+// A block holds 16 sub-transforms (16 x 8 bytes: every row of its tile is
+// one 128-byte line of d).
+struct PassGeo {
+    int s_hi, s_lo, lst, lC, cmask, blk0, low0;
+    __device__ PassGeo(int s_hi_, int r) : s_hi(s_hi_) {
+        // every index fits 32 bits (N <= 2^26) and every span is a power of two:
+        // shifts and masks only
+        s_lo = s_hi - r + 1;
+        lst = s_lo - 1;  // log2 of the point spacing st
+        lC = lst >= 4 ? 4 : lst;  // log2 of C, the columns of one block of 2^s_hi points
+        if (lst >= 4) {
+            const int lgroups = lst - 4;
+            blk0 = static_cast<int>(blockIdx.x) >> lgroups;
+            low0 = (static_cast<int>(blockIdx.x) & ((1 << lgroups) - 1)) << 4;
+        } else {
+            blk0 = static_cast<int>(blockIdx.x) << (4 - lC);
+            low0 = 0;
+        }
+        cmask = (1 << lC) - 1;
     }
-    const int cmask = (1 << lC) - 1;
+    __device__ int gidx(int t, int q) const { return ((blk0 + (q >> lC)) << s_hi) + low0 + (q & cmask) + (t << lst); }
+};
+
+// The radix-2 stages of one pass on the tile in shared memory (ends with a
+// __syncthreads).
+__device__ __forceinline__ void ntt_stages(uint2 *nsm, const NttConst &c, const PassGeo &g, int K, int r, int inverse) {
     const int pts = 1 << r;
-    auto gidx = [&](int t, int q) -> int { return ((blk0 + (q >> lC)) << s_hi) + low0 + (q & cmask) + (t << lst); };
-    for (int e = threadIdx.x; e < pts * kNttCols; e += blockDim.x) nsm[e] = d[gidx(e >> 4, e & 15)];
-    __syncthreads();
+    const int s_hi = g.s_hi, s_lo = g.s_lo, lst = g.lst, low0 = g.low0, cmask = g.cmask;
+    const int half = 1 << (K - 1);
     const int nbf = (pts / 2) * kNttCols;
     const int q = threadIdx.x & 15;  // the thread's column in every stage (blockDim is a multiple of 16)
     for (int st_i = 0; st_i < r; ++st_i) {
@@ -185,16 +191,39 @@ __global__ void __launch_bounds__(256) k_ntt_pass(uint2 *__restrict__ d, NttCons
         }
         __syncthreads();
     }
-    for (int e = threadIdx.x; e < pts * kNttCols; e += blockDim.x) d[gidx(e >> 4, e & 15)] = nsm[e];
 }
 
-// x <- x * a pointwise (a: the matrix spectrum times 1/N, in Montgomery form)
-__global__ void k_ntt_pointwise(uint2 *__restrict__ x, const uint2 *__restrict__ a, long long N, NttConst c) {
-    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
-         i += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const uint2 u = x[i], v = a[i];
-        x[i] = make_uint2(mont_mul(u.x, v.x, c.p[0], c.pinv[0]), mont_mul(u.y, v.y, c.p[1], c.pinv[1]));
+// One pass of radix-2 stages (see ntt_stages) from global memory and back.
+__global__ void __launch_bounds__(256) k_ntt_pass(uint2 *__restrict__ d, NttConst c, int K, int s_hi, int r,
+                                                  int inverse) {
+    extern __shared__ uint2 nsm[];  // [2^r][kNttCols]
+    const PassGeo g(s_hi, r);
+    const int pts = 1 << r;
+    for (int e = threadIdx.x; e < pts * kNttCols; e += blockDim.x) nsm[e] = d[g.gidx(e >> 4, e & 15)];
+    __syncthreads();
+    ntt_stages(nsm, c, g, K, r, inverse);
+    for (int e = threadIdx.x; e < pts * kNttCols; e += blockDim.x) d[g.gidx(e >> 4, e & 15)] = nsm[e];
+}
+
+// The lowest forward stages r .. 1, the pointwise product with the matrix
+// spectrum a (Montgomery form, times 1/N) and the lowest inverse stages
+// 1 .. r in one pass: blocks of 2^r consecutive points stay in shared memory
+// (both transforms visit them in the same bit-reversed order).
+__global__ void __launch_bounds__(256) k_ntt_mid(uint2 *__restrict__ d, const uint2 *__restrict__ a, NttConst c, int K,
+                                                 int r) {
+    extern __shared__ uint2 nsm[];
+    const PassGeo g(r, r);
+    const int pts = 1 << r;
+    for (int e = threadIdx.x; e < pts * kNttCols; e += blockDim.x) nsm[e] = d[g.gidx(e >> 4, e & 15)];
+    __syncthreads();
+    ntt_stages(nsm, c, g, K, r, 0);
+    for (int e = threadIdx.x; e < pts * kNttCols; e += blockDim.x) {
+        const uint2 u = nsm[e], v = a[g.gidx(e >> 4, e & 15)];
+        nsm[e] = make_uint2(mont_mul(u.x, v.x, c.p[0], c.pinv[0]), mont_mul(u.y, v.y, c.p[1], c.pinv[1]));
     }
+    __syncthreads();
+    ntt_stages(nsm, c, g, K, r, 1);
+    for (int e = threadIdx.x; e < pts * kNttCols; e += blockDim.x) d[g.gidx(e >> 4, e & 15)] = nsm[e];
 }
 
 // a <- a * f (f = R^2 / N mod p: the spectrum in Montgomery form, times 1/N)
@@ -331,33 +360,65 @@ int grid_for(long long work, int threads = 256) {
     return static_cast<int>(g < 65535LL * 32 ? g : 65535LL * 32);
 }
 
-cudaError_t run_ntt(hmv_plan_s *p, uint2 *data, bool inverse) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_ntt_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(kNttCols * (1u << kNttMaxR) * sizeof(uint2)));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    const int K = p->ntt_K;
-    const NttConst c = ntt_const(p);
-    int bounds[8][2], np = 0;  // passes from the top stage down, up to kNttMaxR stages each
+// Pass boundaries, from the top stage down, up to kNttMaxR stages each; the
+// last pass ends with stage 1.
+int ntt_passes(int K, int (&bounds)[8][2]) {
+    int np = 0;
     for (int s_hi = K; s_hi >= 1; s_hi -= kNttMaxR) {
         bounds[np][0] = s_hi;
         bounds[np][1] = s_hi >= kNttMaxR ? kNttMaxR : s_hi;
         ++np;
     }
-    for (int k = 0; k < np; ++k) {
-        const int idx = inverse ? (np - 1 - k) : k;
-        const int s_hi = bounds[idx][0], r = bounds[idx][1];
+    return np;
+}
+
+cudaError_t ntt_attrs() {
+    static bool attr = false;
+    if (attr) return cudaSuccess;
+    const int smem = static_cast<int>(kNttCols * (1u << kNttMaxR) * sizeof(uint2));
+    cudaError_t e = cudaFuncSetAttribute(k_ntt_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) attr = true;
+    return e;
+}
+
+cudaError_t launch_pass(hmv_plan_s *p, uint2 *data, const NttConst &c, int s_hi, int r, int inverse) {
+    const long long blocks = (p->ntt_N >> r) / kNttCols;
+    const size_t smem = static_cast<size_t>(kNttCols) * (1u << r) * sizeof(uint2);
+    k_ntt_pass<<<static_cast<unsigned>(blocks), 256, smem, p->stream>>>(data, c, p->ntt_K, s_hi, r, inverse);
+    p->launches_total++;
+    return cudaGetLastError();
+}
+
+// Forward transform (matrix side).
+cudaError_t run_ntt_forward(hmv_plan_s *p, uint2 *data) {
+    cudaError_t e = ntt_attrs();
+    const NttConst c = ntt_const(p);
+    int bounds[8][2];
+    const int np = ntt_passes(p->ntt_K, bounds);
+    for (int k = 0; k < np && e == cudaSuccess; ++k) e = launch_pass(p, data, c, bounds[k][0], bounds[k][1], 0);
+    return e;
+}
+
+// Forward transform, product with the matrix spectrum and inverse transform
+// (vector side): the last forward pass, the product and the first inverse
+// pass share one kernel.
+cudaError_t run_ntt_product(hmv_plan_s *p, uint2 *data) {
+    cudaError_t e = ntt_attrs();
+    const NttConst c = ntt_const(p);
+    int bounds[8][2];
+    const int np = ntt_passes(p->ntt_K, bounds);
+    for (int k = 0; k + 1 < np && e == cudaSuccess; ++k) e = launch_pass(p, data, c, bounds[k][0], bounds[k][1], 0);
+    if (e == cudaSuccess) {
+        const int r = bounds[np - 1][1];  // s_hi = r: blocks of 2^r consecutive points
         const long long blocks = (p->ntt_N >> r) / kNttCols;
         const size_t smem = static_cast<size_t>(kNttCols) * (1u << r) * sizeof(uint2);
-        k_ntt_pass<<<static_cast<unsigned>(blocks), 256, smem, p->stream>>>(data, c, K, s_hi, r, inverse ? 1 : 0);
+        k_ntt_mid<<<static_cast<unsigned>(blocks), 256, smem, p->stream>>>(data, p->ntt_a, c, p->ntt_K, r);
         p->launches_total++;
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+        e = cudaGetLastError();
     }
-    return cudaSuccess;
+    for (int k = np - 2; k >= 0 && e == cudaSuccess; --k) e = launch_pass(p, data, c, bounds[k][0], bounds[k][1], 1);
+    return e;
 }
 
 }  // namespace
@@ -405,7 +466,7 @@ cudaError_t ntt_load_matrix(hmv_plan_s *p) {
         p->dstat);
     p->launches_total++;
     e = cudaGetLastError();
-    if (e == cudaSuccess) e = run_ntt(p, p->ntt_a, false);
+    if (e == cudaSuccess) e = run_ntt_forward(p, p->ntt_a);
     if (e != cudaSuccess) return e;
     uint32_t f[2];
     for (int k = 0; k < 2; ++k) {  // R^2 / N mod p: mont_mul(A, f) = A R / N, the Montgomery form of A / N
@@ -428,12 +489,7 @@ cudaError_t ntt_vector_product(hmv_plan_s *p, const uint32_t *xl, const uint8_t 
         xl, xn, p->n, p->L32, p->ntt_P, p->ntt_S, p->n, 0, p->ntt_x, p->dstat);
     p->launches_total++;
     e = cudaGetLastError();
-    if (e == cudaSuccess) e = run_ntt(p, p->ntt_x, false);
-    if (e != cudaSuccess) return e;
-    k_ntt_pointwise<<<grid_for(p->ntt_N), 256, 0, p->stream>>>(p->ntt_x, p->ntt_a, p->ntt_N, c);
-    p->launches_total++;
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = run_ntt(p, p->ntt_x, true);
+    if (e == cudaSuccess) e = run_ntt_product(p, p->ntt_x);
     if (e != cudaSuccess) return e;
     const uint64_t P2 = kNttP[1];
     const uint32_t inv1R =
@@ -445,3 +501,61 @@ cudaError_t ntt_vector_product(hmv_plan_s *p, const uint32_t *xl, const uint8_t 
 }
 
 }  // namespace hmv
+
+// ---------------------------------------------------------------- measurement
+namespace hmv {
+namespace {
+// Chains of independent Montgomery products modulo the first prime: the
+// rate that bounds the transform stages.
+__global__ void k_mont_rate(uint32_t *out, int iters, uint32_t w) {
+    constexpr int ILP = 8;
+    uint32_t pinv = 1;
+    for (int i = 0; i < 5; ++i) pinv *= 2u - kNttP0 * pinv;
+    pinv = 0u - pinv;
+    uint32_t x[ILP];
+#pragma unroll
+    for (int i = 0; i < ILP; ++i) x[i] = (threadIdx.x * 7919u + blockIdx.x * 104729u + i) % kNttP0;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < ILP; ++i) x[i] = mont_mul(x[i], w, kNttP0, pinv);
+    }
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < ILP; ++i) s ^= x[i];
+    out[static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x] = s;  // keeps the chains live
+}
+}  // namespace
+}  // namespace hmv
+
+extern "C" hmv_status hmv_measure_montgomery_rate(void *stream, double *products_per_s) {
+    if (!products_per_s) return HMV_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                   cudaSuccess)
+        return HMV_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int blocks = sms * 8, threads = 256, iters = 4096;
+    uint32_t *out = nullptr;
+    if (cudaMalloc(&out, sizeof(uint32_t) * blocks * threads) != cudaSuccess) return HMV_ENOMEM;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best = 0;
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+        hmv::k_mont_rate<<<blocks, threads, 0, st>>>(out, iters, 12345u);  // warm-up, then timed
+        e = cudaEventRecord(e0, st);
+        hmv::k_mont_rate<<<blocks, threads, 0, st>>>(out, iters, 12345u);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && (best == 0 || ms < best)) best = ms;
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(out);
+    if (e != cudaSuccess || best <= 0) return HMV_ECUDA;
+    *products_per_s = static_cast<double>(blocks) * threads * iters * 8 / (best * 1e-3);
+    return HMV_OK;
+}

@@ -114,6 +114,8 @@ def load_library(path: str = LIB_PATH):
         lib.hmv_batch_free.restype = None
         lib.hmv_plan_bytes.argtypes = [ctypes.POINTER(Desc), ctypes.POINTER(ctypes.c_uint64)]
         lib.hmv_plan_bytes.restype = ctypes.c_int
+        lib.hmv_measure_montgomery_rate.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+        lib.hmv_measure_montgomery_rate.restype = ctypes.c_int
         lib.hmv_test_leaf_stall.argtypes = [i32, ctypes.c_int64]
         lib.hmv_test_leaf_stall.restype = ctypes.c_int
         lib.hmv_matvec_many.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(Vec), ctypes.POINTER(Vec)]
@@ -153,6 +155,14 @@ def schoolbook_noalloc(n: int, b: int, kind: int, h_ptrs: tuple[int, int], h_exp
                                       x_exponent, y_ptrs[0], y_ptrs[1], ctypes.byref(e), s),
            "hmv_schoolbook_noalloc")
     return int(e.value)
+
+
+def measure_montgomery_rate(stream=None) -> float:
+    """Montgomery products per second this GPU sustains (the NTT path's roofline)."""
+    r = ctypes.c_double(0)
+    _check(load_library().hmv_measure_montgomery_rate(ctypes.c_void_p(0 if stream is None else int(stream)),
+                                                      ctypes.byref(r)), "hmv_measure_montgomery_rate")
+    return r.value
 
 
 def arm_leaf_stall(launches: int, wait_ns: int = 20_000_000) -> None:
