@@ -166,10 +166,14 @@ __device__ __forceinline__ void ntt_stages(uint2 *nsm, const NttConst &c, const 
             const int bf = e >> 4;
             const int tlow = bf & (ht - 1);                  // position inside the half block
             const int t = ((bf >> lh) << (lh + 1)) + tlow;   // u's point
-            if (it > 0) {
+            if (per > 1 && it > 0) {  // warp-uniform: it and per are the same on every lane
+                if ((it & (per - 1)) == 0) {
+                    w[0] = w0[0];
+                    w[1] = w0[1];
+                } else {
 #pragma unroll
-                for (int k = 0; k < 2; ++k)
-                    w[k] = (it & (per - 1)) == 0 ? w0[k] : mont_mul(w[k], ws[k], c.p[k], c.pinv[k]);
+                    for (int k = 0; k < 2; ++k) w[k] = mont_mul(w[k], ws[k], c.p[k], c.pinv[k]);
+                }
             }
             const uint2 u = nsm[(t << 4) + q], v = nsm[((t + ht) << 4) + q];
             uint32_t uo[2] = {u.x, u.y}, vo[2] = {v.x, v.y};
