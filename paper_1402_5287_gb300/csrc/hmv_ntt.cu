@@ -230,6 +230,140 @@ __global__ void __launch_bounds__(256) k_ntt_mid(uint2 *__restrict__ d, const ui
     for (int e = threadIdx.x; e < pts * kNttCols; e += blockDim.x) d[g.gidx(e >> 4, e & 15)] = nsm[e];
 }
 
+// ---------------------------------------------------------------- register-blocked passes
+// The same passes with the points in registers.  Thread (q, g) = (tid & 15,
+// tid >> 4) owns NP = 2^(r-4) points of column q, in one of two layouts:
+//   A: points g + 16 k (k < NP): the stages of span 16 .. 2^(r-1) points
+//      pair k with k + span/16, inside the thread;
+//   B: points NP g + k: the stages of span 1 .. 8 pair k with k + span.
+// A pass runs its stages of one layout, transposes the tile once through
+// shared memory, and runs the rest: one shared-memory round trip and one
+// barrier per pass instead of one per stage.  A stage's twiddles for the
+// thread form a geometric sequence: base w^(mb + lowest tlow 2^lw), step
+// w^(tlow step 2^lw), as in ntt_stages.
+template <int NP, int LH, bool A>  // span 2^LH points, LH known at compile time
+__device__ __forceinline__ void ntt_reg_stage(uint2 (&x)[NP], const NttConst &c, const PassGeo &g, int K, int inverse,
+                                              int gq) {
+    // A: span 16 HK points is HK register steps, tlow = gq + 16 (i mod HK);
+    // B: span HK points is HK register steps, tlow = i mod HK
+    constexpr int HK = A ? (1 << (LH - 4)) : (1 << LH);
+    static_assert(HK >= 1 && 2 * HK <= NP, "the pairs lie in the thread's points");
+    const int s = g.s_lo + LH;
+    const int half = 1 << (K - 1);
+    const int lw = K - 1 - LH;
+    const int q = threadIdx.x & 15;
+    const int mb = (g.low0 + (q & g.cmask)) << (K - s);
+    uint32_t wb[2], wst[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        wb[k] = twiddle(c, k, mb + ((A ? gq : 0) << lw), inverse, half);
+        wst[k] = HK > 1 ? twiddle(c, k, (A ? 16 : 1) << lw, inverse, half) : 0u;
+    }
+    uint32_t w[2] = {wb[0], wb[1]};
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        if (i & HK) continue;  // pairs (i, i + HK), in increasing i
+        if ((i & (HK - 1)) == 0) {
+            w[0] = wb[0];
+            w[1] = wb[1];
+        } else {
+            w[0] = mont_mul(w[0], wst[0], c.p[0], c.pinv[0]);
+            w[1] = mont_mul(w[1], wst[1], c.p[1], c.pinv[1]);
+        }
+        uint32_t uo[2] = {x[i].x, x[i].y}, vo[2] = {x[i + HK].x, x[i + HK].y};
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const uint32_t p = c.p[k], pinv = c.pinv[k];
+            if (!inverse) {
+                const uint32_t a = mod_add(uo[k], vo[k], p);
+                vo[k] = mont_mul(mod_sub(uo[k], vo[k], p), w[k], p, pinv);
+                uo[k] = a;
+            } else {
+                const uint32_t tv = mont_mul(vo[k], w[k], p, pinv);
+                vo[k] = mod_sub(uo[k], tv, p);
+                uo[k] = mod_add(uo[k], tv, p);
+            }
+        }
+        x[i] = make_uint2(uo[0], uo[1]);
+        x[i + HK] = make_uint2(vo[0], vo[1]);
+    }
+}
+// Stages LH, LH + STEP, ..., LAST of one layout.
+template <int NP, int LH, bool A, int LAST, int STEP>
+__device__ __forceinline__ void ntt_reg_stages(uint2 (&x)[NP], const NttConst &c, const PassGeo &g, int K, int inverse,
+                                               int gq) {
+    ntt_reg_stage<NP, LH, A>(x, c, g, K, inverse, gq);
+    if constexpr (LH != LAST) ntt_reg_stages<NP, LH + STEP, A, LAST, STEP>(x, c, g, K, inverse, gq);
+}
+// A -> B (toB) or B -> A through the tile in shared memory [2^r][16].
+template <int NP>
+__device__ __forceinline__ void ntt_reg_transpose(uint2 (&x)[NP], uint2 *tile, bool toB) {
+    const int q = threadIdx.x & 15, gq = threadIdx.x >> 4;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) tile[((toB ? gq + 16 * k : NP * gq + k) << 4) + q] = x[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NP; ++k) x[k] = tile[((toB ? NP * gq + k : gq + 16 * k) << 4) + q];
+    __syncthreads();
+}
+template <int NP>
+__device__ __forceinline__ void ntt_reg_forward(uint2 (&x)[NP], uint2 *tile, const NttConst &c, const PassGeo &g,
+                                                int K) {
+    constexpr int R = NP == 32 ? 9 : 8;
+    const int gq = threadIdx.x >> 4;
+    ntt_reg_stages<NP, R - 1, true, 4, -1>(x, c, g, K, 0, gq);  // spans 2^(R-1) .. 16, layout A
+    ntt_reg_transpose<NP>(x, tile, true);
+    ntt_reg_stages<NP, 3, false, 0, -1>(x, c, g, K, 0, gq);  // spans 8 .. 1, layout B
+}
+template <int NP>
+__device__ __forceinline__ void ntt_reg_inverse(uint2 (&x)[NP], uint2 *tile, const NttConst &c, const PassGeo &g,
+                                                int K) {
+    constexpr int R = NP == 32 ? 9 : 8;
+    const int gq = threadIdx.x >> 4;
+    ntt_reg_stages<NP, 0, false, 3, 1>(x, c, g, K, 1, gq);  // spans 1 .. 8, layout B
+    ntt_reg_transpose<NP>(x, tile, false);
+    ntt_reg_stages<NP, 4, true, R - 1, 1>(x, c, g, K, 1, gq);  // spans 16 .. 2^(R-1), layout A
+}
+
+// A pass of r = log2(16 NP) stages; forward passes load in layout A and
+// store in layout B, inverse passes the other way round.
+template <int NP>
+__global__ void __launch_bounds__(256) k_ntt_rpass(uint2 *__restrict__ d, NttConst c, int K, int s_hi, int inverse) {
+    extern __shared__ uint2 tile[];  // [16 NP][16]
+    constexpr int r = NP == 32 ? 9 : 8;
+    const PassGeo g(s_hi, r);
+    const int q = threadIdx.x & 15, gq = threadIdx.x >> 4;
+    uint2 x[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) x[k] = d[g.gidx(inverse ? NP * gq + k : gq + 16 * k, q)];
+    if (!inverse) ntt_reg_forward<NP>(x, tile, c, g, K);
+    else ntt_reg_inverse<NP>(x, tile, c, g, K);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) d[g.gidx(inverse ? gq + 16 * k : NP * gq + k, q)] = x[k];
+}
+
+// The lowest forward stages, the product with the matrix spectrum and the
+// lowest inverse stages (k_ntt_mid) with the points in registers.
+template <int NP>
+__global__ void __launch_bounds__(256) k_ntt_rmid(uint2 *__restrict__ d, const uint2 *__restrict__ a, NttConst c, int K) {
+    extern __shared__ uint2 tile[];
+    constexpr int r = NP == 32 ? 9 : 8;
+    const PassGeo g(r, r);
+    const int q = threadIdx.x & 15, gq = threadIdx.x >> 4;
+    uint2 x[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) x[k] = d[g.gidx(gq + 16 * k, q)];
+    ntt_reg_forward<NP>(x, tile, c, g, K);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {  // layout B
+        const uint2 v = a[g.gidx(NP * gq + k, q)];
+        x[k] = make_uint2(mont_mul(x[k].x, v.x, c.p[0], c.pinv[0]), mont_mul(x[k].y, v.y, c.p[1], c.pinv[1]));
+    }
+    ntt_reg_inverse<NP>(x, tile, c, g, K);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) d[g.gidx(gq + 16 * k, q)] = x[k];
+}
+
 // a <- a * f (f = R^2 / N mod p: the spectrum in Montgomery form, times 1/N)
 __global__ void k_ntt_scale(uint2 *__restrict__ a, long long N, NttConst c, uint32_t f0, uint32_t f1) {
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
@@ -364,16 +498,29 @@ int grid_for(long long work, int threads = 256) {
     return static_cast<int>(g < 65535LL * 32 ? g : 65535LL * 32);
 }
 
-// Pass boundaries, from the top stage down, up to kNttMaxR stages each; the
-// last pass ends with stage 1.
+// Pass boundaries, from the top stage down; the last pass ends with stage 1.
+// Passes of 9 or 8 stages run with the points in registers (k_ntt_rpass,
+// k_ntt_rmid), so K is split into 9s and 8s where it can be (K = 26: 9, 9, 8)
+// and otherwise into 9s and one shorter pass at the bottom.
 int ntt_passes(int K, int (&bounds)[8][2]) {
-    int np = 0;
-    for (int s_hi = K; s_hi >= 1; s_hi -= kNttMaxR) {
-        bounds[np][0] = s_hi;
-        bounds[np][1] = s_hi >= kNttMaxR ? kNttMaxR : s_hi;
-        ++np;
+    int rs[8], nr = 0;
+    int b8 = -1;
+    for (int b = 0; b <= 3 && b8 < 0; ++b)
+        if (K - 8 * b >= 0 && (K - 8 * b) % 9 == 0) b8 = b;
+    if (b8 >= 0) {
+        for (int i = 0; i < (K - 8 * b8) / 9; ++i) rs[nr++] = 9;
+        for (int i = 0; i < b8; ++i) rs[nr++] = 8;
+    } else {
+        for (int i = 0; i < K / 9; ++i) rs[nr++] = 9;
+        rs[nr++] = K % 9;
     }
-    return np;
+    int s_hi = K;
+    for (int i = 0; i < nr; ++i) {
+        bounds[i][0] = s_hi;
+        bounds[i][1] = rs[i];
+        s_hi -= rs[i];
+    }
+    return nr;
 }
 
 cudaError_t ntt_attrs() {
@@ -382,14 +529,21 @@ cudaError_t ntt_attrs() {
     const int smem = static_cast<int>(kNttCols * (1u << kNttMaxR) * sizeof(uint2));
     cudaError_t e = cudaFuncSetAttribute(k_ntt_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt_rpass<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt_rmid<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) attr = true;
     return e;
 }
 
 cudaError_t launch_pass(hmv_plan_s *p, uint2 *data, const NttConst &c, int s_hi, int r, int inverse) {
-    const long long blocks = (p->ntt_N >> r) / kNttCols;
+    const unsigned blocks = static_cast<unsigned>((p->ntt_N >> r) / kNttCols);
     const size_t smem = static_cast<size_t>(kNttCols) * (1u << r) * sizeof(uint2);
-    k_ntt_pass<<<static_cast<unsigned>(blocks), 256, smem, p->stream>>>(data, c, p->ntt_K, s_hi, r, inverse);
+    if (r == 9)
+        k_ntt_rpass<32><<<blocks, 256, smem, p->stream>>>(data, c, p->ntt_K, s_hi, inverse);
+    else if (r == 8)
+        k_ntt_rpass<16><<<blocks, 256, smem, p->stream>>>(data, c, p->ntt_K, s_hi, inverse);
+    else
+        k_ntt_pass<<<blocks, 256, smem, p->stream>>>(data, c, p->ntt_K, s_hi, r, inverse);
     p->launches_total++;
     return cudaGetLastError();
 }
@@ -415,9 +569,14 @@ cudaError_t run_ntt_product(hmv_plan_s *p, uint2 *data) {
     for (int k = 0; k + 1 < np && e == cudaSuccess; ++k) e = launch_pass(p, data, c, bounds[k][0], bounds[k][1], 0);
     if (e == cudaSuccess) {
         const int r = bounds[np - 1][1];  // s_hi = r: blocks of 2^r consecutive points
-        const long long blocks = (p->ntt_N >> r) / kNttCols;
+        const unsigned blocks = static_cast<unsigned>((p->ntt_N >> r) / kNttCols);
         const size_t smem = static_cast<size_t>(kNttCols) * (1u << r) * sizeof(uint2);
-        k_ntt_mid<<<static_cast<unsigned>(blocks), 256, smem, p->stream>>>(data, p->ntt_a, c, p->ntt_K, r);
+        if (r == 9)
+            k_ntt_rmid<32><<<blocks, 256, smem, p->stream>>>(data, p->ntt_a, c, p->ntt_K);
+        else if (r == 8)
+            k_ntt_rmid<16><<<blocks, 256, smem, p->stream>>>(data, p->ntt_a, c, p->ntt_K);
+        else
+            k_ntt_mid<<<blocks, 256, smem, p->stream>>>(data, p->ntt_a, c, p->ntt_K, r);
         p->launches_total++;
         e = cudaGetLastError();
     }

@@ -1,0 +1,191 @@
+"""CPU replica of the NTT path's pass schedule (no GPU): the register-blocked
+passes' assignment of points to threads (layouts A and B with one transpose),
+their geometric twiddle sequences and the split of the K stages into passes
+must reproduce a textbook radix-2 transform.  Forward: decimation in
+frequency, natural order in, bit-reversed out; inverse: decimation in time,
+back to natural order, times N.  Arithmetic modulo the path's first prime.
+"""
+import numpy as np
+import pytest
+
+P1 = 2013265921  # 15 * 2^27 + 1
+ROOT1 = 31
+
+
+def root(K):
+    return pow(ROOT1, (P1 - 1) >> K, P1)
+
+
+def passes(K):
+    """The library's split of stages K .. 1 into passes (9s and 8s where it can)."""
+    for b in range(4):
+        if K - 8 * b >= 0 and (K - 8 * b) % 9 == 0:
+            rs = [9] * ((K - 8 * b) // 9) + [8] * b
+            break
+    else:
+        rs = [9] * (K // 9) + [K % 9]
+    out, s_hi = [], K
+    for r in rs:
+        out.append((s_hi, r))
+        s_hi -= r
+    return out
+
+
+def geo(bx, s_hi, r):
+    s_lo = s_hi - r + 1
+    lst = s_lo - 1
+    lC = min(4, lst)
+    if lst >= 4:
+        blk0, low0 = bx >> (lst - 4), (bx & ((1 << (lst - 4)) - 1)) << 4
+    else:
+        blk0, low0 = bx << (4 - lC), 0
+    cmask = (1 << lC) - 1
+    return dict(s_lo=s_lo, lst=lst, lC=lC, blk0=blk0, low0=low0, cmask=cmask, s_hi=s_hi)
+
+
+def gidx(g, t, q):
+    return ((g["blk0"] + (q >> g["lC"])) << g["s_hi"]) + g["low0"] + (q & g["cmask"]) + (t << g["lst"])
+
+
+def wpow(K, m, inverse):
+    w = root(K)
+    return pow(w, (-m) % (1 << K) if inverse else m, P1)
+
+
+def reg_stage(xs, g, K, LH, A, inverse, NP):
+    """One stage on every thread's registers, as ntt_reg_stage: twiddles by
+    the base-and-step sequence, checked against the direct exponent."""
+    HK = (1 << (LH - 4)) if A else (1 << LH)
+    s = g["s_lo"] + LH
+    lw = K - 1 - LH
+    for tid in range(256):
+        q, gq = tid & 15, tid >> 4
+        mb = (g["low0"] + (q & g["cmask"])) << (K - s)
+        wb = wpow(K, mb + ((gq if A else 0) << lw), inverse)
+        ws = wpow(K, (16 if A else 1) << lw, inverse)
+        x = xs[tid]
+        w = wb
+        for i in range(NP):
+            if i & HK:
+                continue
+            w = wb if (i & (HK - 1)) == 0 else w * ws % P1
+            t = (gq + 16 * i) if A else (NP * gq + i)
+            tlow = t % (1 << LH)
+            assert w == wpow(K, mb + (tlow << lw), inverse)
+            u, v = x[i], x[i + HK]
+            if not inverse:
+                x[i], x[i + HK] = (u + v) % P1, (u - v) * w % P1
+            else:
+                tv = v * w % P1
+                x[i], x[i + HK] = (u + tv) % P1, (u - tv) % P1
+
+
+def run_rpass(d, K, s_hi, r, inverse, spectrum=None):
+    """k_ntt_rpass (spectrum None) or k_ntt_rmid (with the pointwise product)."""
+    NP = 1 << (r - 4)
+    N = len(d)
+    for bx in range((N >> r) // 16):
+        g = geo(bx, s_hi, r)
+        load_b = inverse and spectrum is None
+        xs = [[d[gidx(g, (NP * (tid >> 4) + k) if load_b else ((tid >> 4) + 16 * k), tid & 15)] for k in range(NP)]
+              for tid in range(256)]
+
+        def transpose(to_b):
+            tile = {}
+            for tid in range(256):
+                q, gq = tid & 15, tid >> 4
+                for k in range(NP):
+                    tile[(gq + 16 * k if to_b else NP * gq + k, q)] = xs[tid][k]
+            for tid in range(256):
+                q, gq = tid & 15, tid >> 4
+                xs[tid] = [tile[(NP * gq + k if to_b else gq + 16 * k, q)] for k in range(NP)]
+
+        def forward():
+            for LH in range(r - 1, 3, -1):
+                reg_stage(xs, g, K, LH, True, False, NP)
+            transpose(True)
+            for LH in range(3, -1, -1):
+                reg_stage(xs, g, K, LH, False, False, NP)
+
+        def inverse_stages():
+            for LH in range(0, 4):
+                reg_stage(xs, g, K, LH, False, True, NP)
+            transpose(False)
+            for LH in range(4, r):
+                reg_stage(xs, g, K, LH, True, True, NP)
+
+        if spectrum is not None:
+            forward()
+            for tid in range(256):
+                q, gq = tid & 15, tid >> 4
+                xs[tid] = [xs[tid][k] * spectrum[gidx(g, NP * gq + k, q)] % P1 for k in range(NP)]
+            inverse_stages()
+            store_a = True
+        elif not inverse:
+            forward()
+            store_a = False
+        else:
+            inverse_stages()
+            store_a = True
+        for tid in range(256):
+            q, gq = tid & 15, tid >> 4
+            for k in range(NP):
+                d[gidx(g, (gq + 16 * k) if store_a else (NP * gq + k), q)] = xs[tid][k]
+
+
+def dif_reference(a, K):
+    a = np.array(a, dtype=object)
+    N = 1 << K
+    for s in range(K, 0, -1):
+        half = 1 << (s - 1)
+        wj = [wpow(K, j << (K - s), False) for j in range(half)]
+        for b0 in range(0, N, 2 * half):
+            for j in range(half):
+                u, v = a[b0 + j], a[b0 + j + half]
+                a[b0 + j] = (u + v) % P1
+                a[b0 + j + half] = (u - v) * wj[j] % P1
+    return list(a)
+
+
+@pytest.mark.parametrize("K", [16, 17])
+def test_register_passes_equal_radix2_transform(K):
+    rng = np.random.default_rng(K)
+    N = 1 << K
+    x = [int(v) for v in rng.integers(0, P1, N)]
+    plan = passes(K)
+    assert all(r in (8, 9) for _, r in plan)  # the register kernels cover these sizes
+    d = list(x)
+    for s_hi, r in plan:
+        run_rpass(d, K, s_hi, r, False)
+    assert d == dif_reference(x, K)
+    # the inverse passes (last pass first) bring it back, times N
+    for s_hi, r in reversed(plan):
+        run_rpass(d, K, s_hi, r, True)
+    assert d == [v * N % P1 for v in x]
+
+
+def test_middle_pass_is_forward_product_inverse():
+    """k_ntt_rmid: the last forward pass, the pointwise product and the first
+    inverse pass in one, equal to the three done apart."""
+    K = 16
+    rng = np.random.default_rng(5)
+    N = 1 << K
+    x = [int(v) for v in rng.integers(0, P1, N)]
+    spec = [int(v) for v in rng.integers(0, P1, N)]
+    (s0, r0), (s1, r1) = passes(K)
+    a = list(x)
+    run_rpass(a, K, s0, r0, False)
+    b = list(a)
+    run_rpass(a, K, s1, r1, False, spectrum=spec)
+    run_rpass(b, K, s1, r1, False)
+    b = [u * v % P1 for u, v in zip(b, spec)]
+    run_rpass(b, K, s1, r1, True)
+    assert a == b
+
+
+def test_pass_split():
+    assert passes(26) == [(26, 9), (17, 9), (8, 8)]
+    assert passes(24) == [(24, 8), (16, 8), (8, 8)]
+    assert passes(13) == [(13, 9), (4, 4)]
+    for K in range(13, 27):
+        assert sum(r for _, r in passes(K)) == K and passes(K)[-1][0] == passes(K)[-1][1]
