@@ -326,9 +326,11 @@ __device__ __forceinline__ void ntt_reg_inverse(uint2 (&x)[NP], uint2 *tile, con
 }
 
 // A pass of r = log2(16 NP) stages; forward passes load in layout A and
-// store in layout B, inverse passes the other way round.
+// store in layout B, inverse passes the other way round.  Two blocks per SM
+// (at most 128 registers a thread) for 32 points a thread: measured 3.58
+// instead of 4.14 ms per matvec at one block per SM.
 template <int NP>
-__global__ void __launch_bounds__(256) k_ntt_rpass(uint2 *__restrict__ d, NttConst c, int K, int s_hi, int inverse) {
+__global__ void __launch_bounds__(256, NP == 32 ? 2 : 3) k_ntt_rpass(uint2 *__restrict__ d, NttConst c, int K, int s_hi, int inverse) {
     extern __shared__ uint2 tile[];  // [16 NP][16]
     constexpr int r = NP == 32 ? 9 : 8;
     const PassGeo g(s_hi, r);
@@ -345,7 +347,7 @@ __global__ void __launch_bounds__(256) k_ntt_rpass(uint2 *__restrict__ d, NttCon
 // The lowest forward stages, the product with the matrix spectrum and the
 // lowest inverse stages (k_ntt_mid) with the points in registers.
 template <int NP>
-__global__ void __launch_bounds__(256) k_ntt_rmid(uint2 *__restrict__ d, const uint2 *__restrict__ a, NttConst c, int K) {
+__global__ void __launch_bounds__(256, NP == 32 ? 2 : 3) k_ntt_rmid(uint2 *__restrict__ d, const uint2 *__restrict__ a, NttConst c, int K) {
     extern __shared__ uint2 tile[];
     constexpr int r = NP == 32 ? 9 : 8;
     const PassGeo g(r, r);
