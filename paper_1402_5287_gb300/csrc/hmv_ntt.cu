@@ -231,22 +231,24 @@ __global__ void __launch_bounds__(256) k_ntt_mid(uint2 *__restrict__ d, const ui
 }
 
 // ---------------------------------------------------------------- register-blocked passes
-// The same passes with the points in registers.  Thread (q, g) = (tid & 15,
-// tid >> 4) owns NP = 2^(r-4) points of column q, in one of two layouts:
-//   A: points g + 16 k (k < NP): the stages of span 16 .. 2^(r-1) points
-//      pair k with k + span/16, inside the thread;
-//   B: points NP g + k: the stages of span 1 .. 8 pair k with k + span.
+// The same passes with the points in registers.  A block holds 16 columns
+// of 2^r points; thread (q, g) = (tid & 15, tid >> 4), g < G = 2^LG
+// threads per column, owns NP = 2^r / G points of column q, in one of two
+// layouts:
+//   A: points g + G k (k < NP): the stages of span G .. 2^(r-1) points pair
+//      k with k + span/G, inside the thread;
+//   B: points NP g + k: the stages of span 1 .. G/2 pair k with k + span.
 // A pass runs its stages of one layout, transposes the tile once through
 // shared memory, and runs the rest: one shared-memory round trip and one
 // barrier per pass instead of one per stage.  A stage's twiddles for the
 // thread form a geometric sequence: base w^(mb + lowest tlow 2^lw), step
 // w^(tlow step 2^lw), as in ntt_stages.
-template <int NP, int LH, bool A>  // span 2^LH points, LH known at compile time
+template <int NP, int LG, int LH, bool A>  // span 2^LH points, LH known at compile time
 __device__ __forceinline__ void ntt_reg_stage(uint2 (&x)[NP], const NttConst &c, const PassGeo &g, int K, int inverse,
                                               int gq) {
-    // A: span 16 HK points is HK register steps, tlow = gq + 16 (i mod HK);
+    // A: span G HK points is HK register steps, tlow = gq + G (i mod HK);
     // B: span HK points is HK register steps, tlow = i mod HK
-    constexpr int HK = A ? (1 << (LH - 4)) : (1 << LH);
+    constexpr int HK = A ? (1 << (LH - LG)) : (1 << LH);
     static_assert(HK >= 1 && 2 * HK <= NP, "the pairs lie in the thread's points");
     const int s = g.s_lo + LH;
     const int half = 1 << (K - 1);
@@ -257,7 +259,7 @@ __device__ __forceinline__ void ntt_reg_stage(uint2 (&x)[NP], const NttConst &c,
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         wb[k] = twiddle(c, k, mb + ((A ? gq : 0) << lw), inverse, half);
-        wst[k] = HK > 1 ? twiddle(c, k, (A ? 16 : 1) << lw, inverse, half) : 0u;
+        wst[k] = HK > 1 ? twiddle(c, k, (A ? (1 << LG) : 1) << lw, inverse, half) : 0u;
     }
     uint32_t w[2] = {wb[0], wb[1]};
 #pragma unroll
@@ -289,81 +291,84 @@ __device__ __forceinline__ void ntt_reg_stage(uint2 (&x)[NP], const NttConst &c,
     }
 }
 // Stages LH, LH + STEP, ..., LAST of one layout.
-template <int NP, int LH, bool A, int LAST, int STEP>
+template <int NP, int LG, int LH, bool A, int LAST, int STEP>
 __device__ __forceinline__ void ntt_reg_stages(uint2 (&x)[NP], const NttConst &c, const PassGeo &g, int K, int inverse,
                                                int gq) {
-    ntt_reg_stage<NP, LH, A>(x, c, g, K, inverse, gq);
-    if constexpr (LH != LAST) ntt_reg_stages<NP, LH + STEP, A, LAST, STEP>(x, c, g, K, inverse, gq);
+    ntt_reg_stage<NP, LG, LH, A>(x, c, g, K, inverse, gq);
+    if constexpr (LH != LAST) ntt_reg_stages<NP, LG, LH + STEP, A, LAST, STEP>(x, c, g, K, inverse, gq);
 }
 // A -> B (toB) or B -> A through the tile in shared memory [2^r][16].
-template <int NP>
+template <int NP, int LG>
 __device__ __forceinline__ void ntt_reg_transpose(uint2 (&x)[NP], uint2 *tile, bool toB) {
     const int q = threadIdx.x & 15, gq = threadIdx.x >> 4;
 #pragma unroll
-    for (int k = 0; k < NP; ++k) tile[((toB ? gq + 16 * k : NP * gq + k) << 4) + q] = x[k];
+    for (int k = 0; k < NP; ++k) tile[((toB ? gq + (k << LG) : NP * gq + k) << 4) + q] = x[k];
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < NP; ++k) x[k] = tile[((toB ? NP * gq + k : gq + 16 * k) << 4) + q];
+    for (int k = 0; k < NP; ++k) x[k] = tile[((toB ? NP * gq + k : gq + (k << LG)) << 4) + q];
     __syncthreads();
 }
-template <int NP>
+template <int NP, int LG>
 __device__ __forceinline__ void ntt_reg_forward(uint2 (&x)[NP], uint2 *tile, const NttConst &c, const PassGeo &g,
                                                 int K) {
-    constexpr int R = NP == 32 ? 9 : 8;
+    constexpr int R = __builtin_ctz(NP) + LG;
     const int gq = threadIdx.x >> 4;
-    ntt_reg_stages<NP, R - 1, true, 4, -1>(x, c, g, K, 0, gq);  // spans 2^(R-1) .. 16, layout A
-    ntt_reg_transpose<NP>(x, tile, true);
-    ntt_reg_stages<NP, 3, false, 0, -1>(x, c, g, K, 0, gq);  // spans 8 .. 1, layout B
+    ntt_reg_stages<NP, LG, R - 1, true, LG, -1>(x, c, g, K, 0, gq);  // spans 2^(R-1) .. G, layout A
+    ntt_reg_transpose<NP, LG>(x, tile, true);
+    ntt_reg_stages<NP, LG, LG - 1, false, 0, -1>(x, c, g, K, 0, gq);  // spans G/2 .. 1, layout B
 }
-template <int NP>
+template <int NP, int LG>
 __device__ __forceinline__ void ntt_reg_inverse(uint2 (&x)[NP], uint2 *tile, const NttConst &c, const PassGeo &g,
                                                 int K) {
-    constexpr int R = NP == 32 ? 9 : 8;
+    constexpr int R = __builtin_ctz(NP) + LG;
     const int gq = threadIdx.x >> 4;
-    ntt_reg_stages<NP, 0, false, 3, 1>(x, c, g, K, 1, gq);  // spans 1 .. 8, layout B
-    ntt_reg_transpose<NP>(x, tile, false);
-    ntt_reg_stages<NP, 4, true, R - 1, 1>(x, c, g, K, 1, gq);  // spans 16 .. 2^(R-1), layout A
+    ntt_reg_stages<NP, LG, 0, false, LG - 1, 1>(x, c, g, K, 1, gq);  // spans 1 .. G/2, layout B
+    ntt_reg_transpose<NP, LG>(x, tile, false);
+    ntt_reg_stages<NP, LG, LG, true, R - 1, 1>(x, c, g, K, 1, gq);  // spans G .. 2^(R-1), layout A
 }
 
-// A pass of r = log2(16 NP) stages; forward passes load in layout A and
-// store in layout B, inverse passes the other way round.  Two blocks per SM
-// (at most 128 registers a thread) for 32 points a thread: measured 3.58
-// instead of 4.14 ms per matvec at one block per SM.
-template <int NP>
-__global__ void __launch_bounds__(256, NP == 32 ? 2 : 3) k_ntt_rpass(uint2 *__restrict__ d, NttConst c, int K, int s_hi, int inverse) {
-    extern __shared__ uint2 tile[];  // [16 NP][16]
-    constexpr int r = NP == 32 ? 9 : 8;
+// A pass of r = log2(NP G) stages with 16 G threads; forward passes load in
+// layout A and store in layout B, inverse passes the other way round.  At
+// most 128 registers a thread for 32 points (two 256-thread blocks per SM):
+// measured 3.58 instead of 4.14 ms per matvec at one block per SM.
+template <int NP, int LG>
+__global__ void __launch_bounds__(16 << LG, NP == 32 ? 2 : 3) k_ntt_rpass(uint2 *__restrict__ d, NttConst c, int K,
+                                                                             int s_hi, int inverse) {
+    extern __shared__ uint2 tile[];  // [NP G][16]
+    constexpr int r = __builtin_ctz(NP) + LG;
     const PassGeo g(s_hi, r);
     const int q = threadIdx.x & 15, gq = threadIdx.x >> 4;
     uint2 x[NP];
 #pragma unroll
-    for (int k = 0; k < NP; ++k) x[k] = d[g.gidx(inverse ? NP * gq + k : gq + 16 * k, q)];
-    if (!inverse) ntt_reg_forward<NP>(x, tile, c, g, K);
-    else ntt_reg_inverse<NP>(x, tile, c, g, K);
+    for (int k = 0; k < NP; ++k) x[k] = d[g.gidx(inverse ? NP * gq + k : gq + (k << LG), q)];
+    if (!inverse) ntt_reg_forward<NP, LG>(x, tile, c, g, K);
+    else ntt_reg_inverse<NP, LG>(x, tile, c, g, K);
 #pragma unroll
-    for (int k = 0; k < NP; ++k) d[g.gidx(inverse ? gq + 16 * k : NP * gq + k, q)] = x[k];
+    for (int k = 0; k < NP; ++k) d[g.gidx(inverse ? gq + (k << LG) : NP * gq + k, q)] = x[k];
 }
 
 // The lowest forward stages, the product with the matrix spectrum and the
 // lowest inverse stages (k_ntt_mid) with the points in registers.
-template <int NP>
-__global__ void __launch_bounds__(256, NP == 32 ? 2 : 3) k_ntt_rmid(uint2 *__restrict__ d, const uint2 *__restrict__ a, NttConst c, int K) {
+template <int NP, int LG>
+__global__ void __launch_bounds__(16 << LG, NP == 32 ? 2 : 3) k_ntt_rmid(uint2 *__restrict__ d,
+                                                                            const uint2 *__restrict__ a, NttConst c,
+                                                                            int K) {
     extern __shared__ uint2 tile[];
-    constexpr int r = NP == 32 ? 9 : 8;
+    constexpr int r = __builtin_ctz(NP) + LG;
     const PassGeo g(r, r);
     const int q = threadIdx.x & 15, gq = threadIdx.x >> 4;
     uint2 x[NP];
 #pragma unroll
-    for (int k = 0; k < NP; ++k) x[k] = d[g.gidx(gq + 16 * k, q)];
-    ntt_reg_forward<NP>(x, tile, c, g, K);
+    for (int k = 0; k < NP; ++k) x[k] = d[g.gidx(gq + (k << LG), q)];
+    ntt_reg_forward<NP, LG>(x, tile, c, g, K);
 #pragma unroll
     for (int k = 0; k < NP; ++k) {  // layout B
         const uint2 v = a[g.gidx(NP * gq + k, q)];
         x[k] = make_uint2(mont_mul(x[k].x, v.x, c.p[0], c.pinv[0]), mont_mul(x[k].y, v.y, c.p[1], c.pinv[1]));
     }
-    ntt_reg_inverse<NP>(x, tile, c, g, K);
+    ntt_reg_inverse<NP, LG>(x, tile, c, g, K);
 #pragma unroll
-    for (int k = 0; k < NP; ++k) d[g.gidx(gq + 16 * k, q)] = x[k];
+    for (int k = 0; k < NP; ++k) d[g.gidx(gq + (k << LG), q)] = x[k];
 }
 
 // a <- a * f (f = R^2 / N mod p: the spectrum in Montgomery form, times 1/N)
@@ -531,8 +536,8 @@ cudaError_t ntt_attrs() {
     const int smem = static_cast<int>(kNttCols * (1u << kNttMaxR) * sizeof(uint2));
     cudaError_t e = cudaFuncSetAttribute(k_ntt_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt_rpass<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt_rmid<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt_rpass<32, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt_rmid<32, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) attr = true;
     return e;
 }
@@ -540,10 +545,11 @@ cudaError_t ntt_attrs() {
 cudaError_t launch_pass(hmv_plan_s *p, uint2 *data, const NttConst &c, int s_hi, int r, int inverse) {
     const unsigned blocks = static_cast<unsigned>((p->ntt_N >> r) / kNttCols);
     const size_t smem = static_cast<size_t>(kNttCols) * (1u << r) * sizeof(uint2);
-    if (r == 9)
-        k_ntt_rpass<32><<<blocks, 256, smem, p->stream>>>(data, c, p->ntt_K, s_hi, inverse);
-    else if (r == 8)
-        k_ntt_rpass<16><<<blocks, 256, smem, p->stream>>>(data, c, p->ntt_K, s_hi, inverse);
+    if (r == 9)  // 32 points a thread: 16 columns x 16 threads
+        k_ntt_rpass<32, 4><<<blocks, 256, smem, p->stream>>>(data, c, p->ntt_K, s_hi, inverse);
+    else if (r == 8)  // 16 points a thread: 16 columns x 16 threads (8 threads a column with 32 points each
+                      // measured slower: 3.87 vs 3.58 ms per matvec)
+        k_ntt_rpass<16, 4><<<blocks, 256, smem, p->stream>>>(data, c, p->ntt_K, s_hi, inverse);
     else
         k_ntt_pass<<<blocks, 256, smem, p->stream>>>(data, c, p->ntt_K, s_hi, r, inverse);
     p->launches_total++;
@@ -574,9 +580,9 @@ cudaError_t run_ntt_product(hmv_plan_s *p, uint2 *data) {
         const unsigned blocks = static_cast<unsigned>((p->ntt_N >> r) / kNttCols);
         const size_t smem = static_cast<size_t>(kNttCols) * (1u << r) * sizeof(uint2);
         if (r == 9)
-            k_ntt_rmid<32><<<blocks, 256, smem, p->stream>>>(data, p->ntt_a, c, p->ntt_K);
+            k_ntt_rmid<32, 4><<<blocks, 256, smem, p->stream>>>(data, p->ntt_a, c, p->ntt_K);
         else if (r == 8)
-            k_ntt_rmid<16><<<blocks, 256, smem, p->stream>>>(data, p->ntt_a, c, p->ntt_K);
+            k_ntt_rmid<16, 4><<<blocks, 256, smem, p->stream>>>(data, p->ntt_a, c, p->ntt_K);
         else
             k_ntt_mid<<<blocks, 256, smem, p->stream>>>(data, p->ntt_a, c, p->ntt_K, r);
         p->launches_total++;

@@ -52,24 +52,25 @@ def wpow(K, m, inverse):
     return pow(w, (-m) % (1 << K) if inverse else m, P1)
 
 
-def reg_stage(xs, g, K, LH, A, inverse, NP):
+def reg_stage(xs, g, K, LH, A, inverse, NP, LG):
     """One stage on every thread's registers, as ntt_reg_stage: twiddles by
     the base-and-step sequence, checked against the direct exponent."""
-    HK = (1 << (LH - 4)) if A else (1 << LH)
+    G = 1 << LG
+    HK = (1 << (LH - LG)) if A else (1 << LH)
     s = g["s_lo"] + LH
     lw = K - 1 - LH
-    for tid in range(256):
+    for tid in range(16 * G):
         q, gq = tid & 15, tid >> 4
         mb = (g["low0"] + (q & g["cmask"])) << (K - s)
         wb = wpow(K, mb + ((gq if A else 0) << lw), inverse)
-        ws = wpow(K, (16 if A else 1) << lw, inverse)
+        ws = wpow(K, (G if A else 1) << lw, inverse)
         x = xs[tid]
         w = wb
         for i in range(NP):
             if i & HK:
                 continue
             w = wb if (i & (HK - 1)) == 0 else w * ws % P1
-            t = (gq + 16 * i) if A else (NP * gq + i)
+            t = (gq + G * i) if A else (NP * gq + i)
             tlow = t % (1 << LH)
             assert w == wpow(K, mb + (tlow << lw), inverse)
             u, v = x[i], x[i + HK]
@@ -81,44 +82,54 @@ def reg_stage(xs, g, K, LH, A, inverse, NP):
 
 
 def run_rpass(d, K, s_hi, r, inverse, spectrum=None):
-    """k_ntt_rpass (spectrum None) or k_ntt_rmid (with the pointwise product)."""
-    NP = 1 << (r - 4)
+    """k_ntt_rpass (spectrum None) or k_ntt_rmid (with the pointwise product)
+    as the library launches them: 16 columns a block, 16 threads a column,
+    32 points a thread for r = 9 and 16 for r = 8."""
+    NP, LG = (32 if r == 9 else 16), 4
+    G = 1 << LG
+    T = 16 * G
     N = len(d)
+
+    def pa(gq, k):
+        return gq + G * k
+
+    def pb(gq, k):
+        return NP * gq + k
+
     for bx in range((N >> r) // 16):
         g = geo(bx, s_hi, r)
         load_b = inverse and spectrum is None
-        xs = [[d[gidx(g, (NP * (tid >> 4) + k) if load_b else ((tid >> 4) + 16 * k), tid & 15)] for k in range(NP)]
-              for tid in range(256)]
+        xs = [[d[gidx(g, (pb if load_b else pa)(tid >> 4, k), tid & 15)] for k in range(NP)] for tid in range(T)]
 
         def transpose(to_b):
             tile = {}
-            for tid in range(256):
+            for tid in range(T):
                 q, gq = tid & 15, tid >> 4
                 for k in range(NP):
-                    tile[(gq + 16 * k if to_b else NP * gq + k, q)] = xs[tid][k]
-            for tid in range(256):
+                    tile[((pa if to_b else pb)(gq, k), q)] = xs[tid][k]
+            for tid in range(T):
                 q, gq = tid & 15, tid >> 4
-                xs[tid] = [tile[(NP * gq + k if to_b else gq + 16 * k, q)] for k in range(NP)]
+                xs[tid] = [tile[((pb if to_b else pa)(gq, k), q)] for k in range(NP)]
 
         def forward():
-            for LH in range(r - 1, 3, -1):
-                reg_stage(xs, g, K, LH, True, False, NP)
+            for LH in range(r - 1, LG - 1, -1):
+                reg_stage(xs, g, K, LH, True, False, NP, LG)
             transpose(True)
-            for LH in range(3, -1, -1):
-                reg_stage(xs, g, K, LH, False, False, NP)
+            for LH in range(LG - 1, -1, -1):
+                reg_stage(xs, g, K, LH, False, False, NP, LG)
 
         def inverse_stages():
-            for LH in range(0, 4):
-                reg_stage(xs, g, K, LH, False, True, NP)
+            for LH in range(0, LG):
+                reg_stage(xs, g, K, LH, False, True, NP, LG)
             transpose(False)
-            for LH in range(4, r):
-                reg_stage(xs, g, K, LH, True, True, NP)
+            for LH in range(LG, r):
+                reg_stage(xs, g, K, LH, True, True, NP, LG)
 
         if spectrum is not None:
             forward()
-            for tid in range(256):
+            for tid in range(T):
                 q, gq = tid & 15, tid >> 4
-                xs[tid] = [xs[tid][k] * spectrum[gidx(g, NP * gq + k, q)] % P1 for k in range(NP)]
+                xs[tid] = [xs[tid][k] * spectrum[gidx(g, pb(gq, k), q)] % P1 for k in range(NP)]
             inverse_stages()
             store_a = True
         elif not inverse:
@@ -127,10 +138,10 @@ def run_rpass(d, K, s_hi, r, inverse, spectrum=None):
         else:
             inverse_stages()
             store_a = True
-        for tid in range(256):
+        for tid in range(T):
             q, gq = tid & 15, tid >> 4
             for k in range(NP):
-                d[gidx(g, (gq + 16 * k) if store_a else (NP * gq + k), q)] = xs[tid][k]
+                d[gidx(g, (pa if store_a else pb)(gq, k), q)] = xs[tid][k]
 
 
 def dif_reference(a, K):
