@@ -28,6 +28,7 @@
 // stages per pass in shared memory, both primes in one pass (a uint2 per
 // point).  The matrix's spectrum is kept per plan, scaled by 1/N.
 #include <cstring>
+#include <utility>
 #include <vector>
 
 #include "hmv_internal.h"
@@ -297,16 +298,57 @@ __device__ __forceinline__ void ntt_reg_stages(uint2 (&x)[NP], const NttConst &c
     ntt_reg_stage<NP, LG, LH, A>(x, c, g, K, inverse, gq);
     if constexpr (LH != LAST) ntt_reg_stages<NP, LG, LH + STEP, A, LAST, STEP>(x, c, g, K, inverse, gq);
 }
-// A -> B (toB) or B -> A through the tile in shared memory [2^r][16].
+// The register passes' tile in shared memory: point t of column q at
+// t * kTilePitch + q; the padding makes both a column-major and a row-major
+// sweep conflict-free.
+constexpr int kTilePitch = 17;
+// A -> B (toB) or B -> A through the tile.
 template <int NP, int LG>
 __device__ __forceinline__ void ntt_reg_transpose(uint2 (&x)[NP], uint2 *tile, bool toB) {
     const int q = threadIdx.x & 15, gq = threadIdx.x >> 4;
 #pragma unroll
-    for (int k = 0; k < NP; ++k) tile[((toB ? gq + (k << LG) : NP * gq + k) << 4) + q] = x[k];
+    for (int k = 0; k < NP; ++k) tile[(toB ? gq + (k << LG) : NP * gq + k) * kTilePitch + q] = x[k];
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < NP; ++k) x[k] = tile[((toB ? NP * gq + k : gq + (k << LG)) << 4) + q];
+    for (int k = 0; k < NP; ++k) x[k] = tile[(toB ? NP * gq + k : gq + (k << LG)) * kTilePitch + q];
     __syncthreads();
+}
+// Loads and stores of a pass's points in layout A (layoutA) or B.  Where the
+// 16 columns are 16 consecutive runs of 2^r points (the lowest pass, st = 1)
+// a warp's points would fall in 16 separate pieces of memory: there the
+// block copies its whole contiguous range through the tile instead.
+template <int NP, int LG>
+__device__ __forceinline__ void ntt_reg_load(uint2 (&x)[NP], const uint2 *__restrict__ d, uint2 *tile, const PassGeo &g,
+                                             bool layoutA) {
+    constexpr int r = __builtin_ctz(NP) + LG;
+    const int q = threadIdx.x & 15, gq = threadIdx.x >> 4;
+    if (g.lst == 0) {
+        const uint2 *src = d + (static_cast<size_t>(g.blk0) << r);
+        for (int e = threadIdx.x; e < (16 << r); e += blockDim.x) tile[(e & ((1 << r) - 1)) * kTilePitch + (e >> r)] = src[e];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < NP; ++k) x[k] = tile[(layoutA ? gq + (k << LG) : NP * gq + k) * kTilePitch + q];
+        __syncthreads();
+    } else {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) x[k] = d[g.gidx(layoutA ? gq + (k << LG) : NP * gq + k, q)];
+    }
+}
+template <int NP, int LG>
+__device__ __forceinline__ void ntt_reg_store(const uint2 (&x)[NP], uint2 *__restrict__ d, uint2 *tile,
+                                              const PassGeo &g, bool layoutA) {
+    constexpr int r = __builtin_ctz(NP) + LG;
+    const int q = threadIdx.x & 15, gq = threadIdx.x >> 4;
+    if (g.lst == 0) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) tile[(layoutA ? gq + (k << LG) : NP * gq + k) * kTilePitch + q] = x[k];
+        __syncthreads();
+        uint2 *dst = d + (static_cast<size_t>(g.blk0) << r);
+        for (int e = threadIdx.x; e < (16 << r); e += blockDim.x) dst[e] = tile[(e & ((1 << r) - 1)) * kTilePitch + (e >> r)];
+    } else {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) d[g.gidx(layoutA ? gq + (k << LG) : NP * gq + k, q)] = x[k];
+    }
 }
 template <int NP, int LG>
 __device__ __forceinline__ void ntt_reg_forward(uint2 (&x)[NP], uint2 *tile, const NttConst &c, const PassGeo &g,
@@ -334,17 +376,14 @@ __device__ __forceinline__ void ntt_reg_inverse(uint2 (&x)[NP], uint2 *tile, con
 template <int NP, int LG>
 __global__ void __launch_bounds__(16 << LG, NP == 32 ? 2 : 3) k_ntt_rpass(uint2 *__restrict__ d, NttConst c, int K,
                                                                              int s_hi, int inverse) {
-    extern __shared__ uint2 tile[];  // [NP G][16]
+    extern __shared__ uint2 tile[];  // [NP G][kTilePitch]
     constexpr int r = __builtin_ctz(NP) + LG;
     const PassGeo g(s_hi, r);
-    const int q = threadIdx.x & 15, gq = threadIdx.x >> 4;
     uint2 x[NP];
-#pragma unroll
-    for (int k = 0; k < NP; ++k) x[k] = d[g.gidx(inverse ? NP * gq + k : gq + (k << LG), q)];
+    ntt_reg_load<NP, LG>(x, d, tile, g, !inverse);
     if (!inverse) ntt_reg_forward<NP, LG>(x, tile, c, g, K);
     else ntt_reg_inverse<NP, LG>(x, tile, c, g, K);
-#pragma unroll
-    for (int k = 0; k < NP; ++k) d[g.gidx(inverse ? gq + (k << LG) : NP * gq + k, q)] = x[k];
+    ntt_reg_store<NP, LG>(x, d, tile, g, inverse);
 }
 
 // The lowest forward stages, the product with the matrix spectrum and the
@@ -356,19 +395,36 @@ __global__ void __launch_bounds__(16 << LG, NP == 32 ? 2 : 3) k_ntt_rmid(uint2 *
     extern __shared__ uint2 tile[];
     constexpr int r = __builtin_ctz(NP) + LG;
     const PassGeo g(r, r);
-    const int q = threadIdx.x & 15, gq = threadIdx.x >> 4;
     uint2 x[NP];
-#pragma unroll
-    for (int k = 0; k < NP; ++k) x[k] = d[g.gidx(gq + (k << LG), q)];
+    ntt_reg_load<NP, LG>(x, d, tile, g, true);
     ntt_reg_forward<NP, LG>(x, tile, c, g, K);
+    // layout B; the spectrum is stored in this kernel's register order
+    // (point k of thread tid of block bx at (bx NP + k) 16 G + tid), so the
+    // reads are coalesced
+    const uint2 *ab = a + (static_cast<size_t>(blockIdx.x) * NP << (4 + LG)) + threadIdx.x;
 #pragma unroll
-    for (int k = 0; k < NP; ++k) {  // layout B
-        const uint2 v = a[g.gidx(NP * gq + k, q)];
+    for (int k = 0; k < NP; ++k) {
+        const uint2 v = ab[k << (4 + LG)];
         x[k] = make_uint2(mont_mul(x[k].x, v.x, c.p[0], c.pinv[0]), mont_mul(x[k].y, v.y, c.p[1], c.pinv[1]));
     }
     ntt_reg_inverse<NP, LG>(x, tile, c, g, K);
-#pragma unroll
-    for (int k = 0; k < NP; ++k) d[g.gidx(gq + (k << LG), q)] = x[k];
+    ntt_reg_store<NP, LG>(x, d, tile, g, true);
+}
+
+// dst <- src * f in the register order of k_ntt_rmid<NP, 4> for a last pass
+// of r stages: entry (bx NP + k) 256 + tid holds point NP (tid >> 4) + k of
+// column tid & 15 of that kernel's block bx.
+__global__ void k_ntt_scale_perm(const uint2 *__restrict__ src, uint2 *__restrict__ dst, long long N, int r, int lnp,
+                                 NttConst c, uint32_t f0, uint32_t f1) {
+    for (long long o = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; o < N;
+         o += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long bx = o >> (lnp + 8);
+        const int rem = static_cast<int>(o & ((1LL << (lnp + 8)) - 1));
+        const int k = rem >> 8, tid = rem & 255;
+        const int q = tid & 15, gq = tid >> 4;
+        const uint2 u = src[((bx * 16 + q) << r) + (static_cast<long long>(gq) << lnp) + k];
+        dst[o] = make_uint2(mont_mul(u.x, f0, c.p[0], c.pinv[0]), mont_mul(u.y, f1, c.p[1], c.pinv[1]));
+    }
 }
 
 // a <- a * f (f = R^2 / N mod p: the spectrum in Montgomery form, times 1/N)
@@ -534,17 +590,18 @@ cudaError_t ntt_attrs() {
     static bool attr = false;
     if (attr) return cudaSuccess;
     const int smem = static_cast<int>(kNttCols * (1u << kNttMaxR) * sizeof(uint2));
+    const int rsmem = static_cast<int>(kTilePitch * (1u << 9) * sizeof(uint2));
     cudaError_t e = cudaFuncSetAttribute(k_ntt_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt_rpass<32, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt_rmid<32, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt_rpass<32, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, rsmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt_rmid<32, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, rsmem);
     if (e == cudaSuccess) attr = true;
     return e;
 }
 
 cudaError_t launch_pass(hmv_plan_s *p, uint2 *data, const NttConst &c, int s_hi, int r, int inverse) {
     const unsigned blocks = static_cast<unsigned>((p->ntt_N >> r) / kNttCols);
-    const size_t smem = static_cast<size_t>(kNttCols) * (1u << r) * sizeof(uint2);
+    const size_t smem = static_cast<size_t>(r >= 8 ? kTilePitch : kNttCols) * (1u << r) * sizeof(uint2);
     if (r == 9)  // 32 points a thread: 16 columns x 16 threads
         k_ntt_rpass<32, 4><<<blocks, 256, smem, p->stream>>>(data, c, p->ntt_K, s_hi, inverse);
     else if (r == 8)  // 16 points a thread: 16 columns x 16 threads (8 threads a column with 32 points each
@@ -578,7 +635,7 @@ cudaError_t run_ntt_product(hmv_plan_s *p, uint2 *data) {
     if (e == cudaSuccess) {
         const int r = bounds[np - 1][1];  // s_hi = r: blocks of 2^r consecutive points
         const unsigned blocks = static_cast<unsigned>((p->ntt_N >> r) / kNttCols);
-        const size_t smem = static_cast<size_t>(kNttCols) * (1u << r) * sizeof(uint2);
+        const size_t smem = static_cast<size_t>(r >= 8 ? kTilePitch : kNttCols) * (1u << r) * sizeof(uint2);
         if (r == 9)
             k_ntt_rmid<32, 4><<<blocks, 256, smem, p->stream>>>(data, p->ntt_a, c, p->ntt_K);
         else if (r == 8)
@@ -645,7 +702,15 @@ cudaError_t ntt_load_matrix(hmv_plan_s *p) {
         const uint64_t R = (uint64_t(1) << 32) % P;
         f[k] = static_cast<uint32_t>(mulmod(mulmod(R, R, P), powmod(p->ntt_N % P, P - 2, P), P));
     }
-    k_ntt_scale<<<grid_for(p->ntt_N), 256, 0, p->stream>>>(p->ntt_a, p->ntt_N, c, f[0], f[1]);
+    int bounds[8][2];
+    const int last_r = bounds[ntt_passes(p->ntt_K, bounds) - 1][1];
+    if (last_r == 9 || last_r == 8) {  // the register middle pass reads the spectrum in its own order
+        k_ntt_scale_perm<<<grid_for(p->ntt_N), 256, 0, p->stream>>>(p->ntt_a, p->ntt_x, p->ntt_N, last_r,
+                                                                    last_r == 9 ? 5 : 4, c, f[0], f[1]);
+        std::swap(p->ntt_a, p->ntt_x);  // the vector side's work array is free until the next matvec
+    } else {
+        k_ntt_scale<<<grid_for(p->ntt_N), 256, 0, p->stream>>>(p->ntt_a, p->ntt_N, c, f[0], f[1]);
+    }
     p->launches_total++;
     return cudaGetLastError();
 }
