@@ -467,7 +467,7 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
         p->ntt_N = 1LL << p->ntt_K;
         g(dalloc(p, &p->ntt_a, static_cast<size_t>(p->ntt_N)));
         g(dalloc(p, &p->ntt_x, static_cast<size_t>(p->ntt_N)));
-        g(dalloc(p, &p->ntt_tw, static_cast<size_t>(4) << 13));
+        g(dalloc(p, &p->ntt_tw, ntt_table_words()));
         if (g.err == cudaSuccess && !dry_run) g(ntt_init(p));
     } else {
         // depth: explicit, or the cheapest by the cost model (node order >= 2);

@@ -150,6 +150,7 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
 cudaError_t launch_validate(hmv_plan_s *p, const uint32_t *limbs, int rows);
 cudaError_t launch_colsum_normalize(hmv_plan_s *p, int rhs);
 bool ntt_geometry(int n, int b, int &P, int &S, int &K);
+size_t ntt_table_words();  // uint32 words of the plan's twiddle tables (ntt_tw)
 cudaError_t ntt_init(hmv_plan_s *p);
 cudaError_t ntt_load_matrix(hmv_plan_s *p);
 cudaError_t ntt_vector_product(hmv_plan_s *p, const uint32_t *xl, const uint8_t *xn, int rhs);

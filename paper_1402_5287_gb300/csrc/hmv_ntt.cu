@@ -41,6 +41,7 @@ constexpr uint32_t kNttRoot[2] = {31u, 13u};                // primitive roots
 constexpr int kNttMaxK = 26;
 constexpr int kNttPieceBits = 16;
 constexpr int kTwLoBits = 13;
+constexpr int kNttRootWords = 2 * 256 * 2;  // w_512^(+-j), j < 256, both primes
 
 namespace {
 
@@ -51,19 +52,32 @@ static_assert(kNttCols == 16, "the pass indexes columns with e & 15 and e >> 4")
 struct NttConst {
     uint32_t p[2], pinv[2];  // pinv = -p^-1 mod 2^32
     const uint32_t *tlo[2], *thi[2];
+    // w_16^e (w16[0]) and w_16^-e (w16[1]), Montgomery form, [direction][prime][e]:
+    // the register passes' twiddles of span 1, 2, 4 and 8, read as
+    // kernel-parameter constants
+    uint32_t w16[2][2][8];
+    // w_512^j and w_512^-j, j < 256, as (prime 0, prime 1) pairs in Montgomery
+    // form, [direction][j]: the register passes' wider spans
+    const uint2 *rt;
 };
 
+// a b / 2^32 mod p for a < 2p, b < p: t + m p < 2 p^2 + 2^32 p < 2^64 and
+// (t + m p) / 2^32 < 2p, one conditional subtraction (the unsigned minimum
+// of u and u - p: u - p wraps above u when u < p).
 __device__ __forceinline__ uint32_t mont_mul(uint32_t a, uint32_t b, uint32_t p, uint32_t pinv) {
-    const uint64_t t = static_cast<uint64_t>(a) * b;  // < p^2 < 2^62
+    const uint64_t t = static_cast<uint64_t>(a) * b;
     const uint32_t m = static_cast<uint32_t>(t) * pinv;
-    const uint32_t u = static_cast<uint32_t>((t + static_cast<uint64_t>(m) * p) >> 32);  // < 2p
-    return u >= p ? u - p : u;
+    const uint32_t u = static_cast<uint32_t>((t + static_cast<uint64_t>(m) * p) >> 32);
+    return umin(u, u - p);
 }
 __device__ __forceinline__ uint32_t mod_add(uint32_t a, uint32_t b, uint32_t p) {
     const uint32_t s = a + b;  // < 2p < 2^32
-    return s >= p ? s - p : s;
+    return umin(s, s - p);
 }
-__device__ __forceinline__ uint32_t mod_sub(uint32_t a, uint32_t b, uint32_t p) { return a >= b ? a - b : a + p - b; }
+__device__ __forceinline__ uint32_t mod_sub(uint32_t a, uint32_t b, uint32_t p) {
+    const uint32_t d = a - b;  // a - b, or a - b + 2^32 when a < b, where d + p wraps to a - b + p < p
+    return umin(d, d + p);
+}
 
 // w_N^m (forward) or w_N^-m (inverse) in Montgomery form, 0 <= m < N/2;
 // w^-m = -w^(N/2 - m) for m > 0
@@ -241,63 +255,135 @@ __global__ void __launch_bounds__(256) k_ntt_mid(uint2 *__restrict__ d, const ui
 //   B: points NP g + k: the stages of span 1 .. G/2 pair k with k + span.
 // A pass runs its stages of one layout, transposes the tile once through
 // shared memory, and runs the rest: one shared-memory round trip and one
-// barrier per pass instead of one per stage.  A stage's twiddles for the
-// thread form a geometric sequence: base w^(mb + lowest tlow 2^lw), step
-// w^(tlow step 2^lw), as in ntt_stages.
-template <int NP, int LG, int LH, bool A>  // span 2^LH points, LH known at compile time
-__device__ __forceinline__ void ntt_reg_stage(uint2 (&x)[NP], const NttConst &c, const PassGeo &g, int K, int inverse,
-                                              int gq) {
-    // A: span G HK points is HK register steps, tlow = gq + G (i mod HK);
-    // B: span HK points is HK register steps, tlow = i mod HK
-    constexpr int HK = A ? (1 << (LH - LG)) : (1 << LH);
-    static_assert(HK >= 1 && 2 * HK <= NP, "the pairs lie in the thread's points");
-    const int s = g.s_lo + LH;
-    const int half = 1 << (K - 1);
-    const int lw = K - 1 - LH;
-    const int q = threadIdx.x & 15;
-    const int mb = (g.low0 + (q & g.cmask)) << (K - s);
-    uint32_t wb[2], wst[2];
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        wb[k] = twiddle(c, k, mb + ((A ? gq : 0) << lw), inverse, half);
-        wst[k] = HK > 1 ? twiddle(c, k, (A ? (1 << LG) : 1) << lw, inverse, half) : 0u;
+// barrier per pass instead of one per stage.
+//
+// Twiddles, in the four-step form of a pass.  Point t of column c (c the
+// offset below the point spacing 2^lst) meets at stage s = s_lo + i (span
+// 2^i points of the column) the twiddle w_{2^s}^(c + (t mod 2^i) 2^lst), the
+// product of
+//   an inner twiddle  w_{2^(i+1)}^(t mod 2^i), the same for every column, and
+//   a column factor   w_{2^s}^c, on the lower output of every butterfly.
+// The column factor of stage i multiplies exactly the points with bit i of
+// t set, and the later stages combine only points that agree in that bit,
+// so the factors commute to the end of a forward pass (to the start of an
+// inverse one), where point t is multiplied once by
+//   Phi_c(t) = prod_{i : bit i of t} w_{2^(s_lo+i)}^c = (w_{2^s_hi}^c)^rev_r(t)
+// (rev_r: the r bits of t reversed).  Inner twiddles of spans 1..8 are
+// powers of w_16 fixed at compile time once the loops over the registers
+// are unrolled (kernel-parameter constants; the first butterfly of every
+// span has twiddle 1 and no product); those of wider spans are powers of
+// w_{2^r}, read from a 2^(r-1)-entry table in shared memory (one broadcast
+// load per butterfly).  The lowest pass has c = 0 and no column factors.
+
+// Both primes: DIF (u, v) -> (u + v, (u - v) w), DIT (u, v) -> (u + w v, u - w v).
+template <bool INV>
+__device__ __forceinline__ void ntt_bfly(uint2 &u, uint2 &v, uint2 w, const NttConst &c) {
+    if (!INV) {
+        const uint2 a = make_uint2(mod_add(u.x, v.x, c.p[0]), mod_add(u.y, v.y, c.p[1]));
+        // u - v + p < 2p: mont_mul's range
+        v = make_uint2(mont_mul(u.x + c.p[0] - v.x, w.x, c.p[0], c.pinv[0]),
+                       mont_mul(u.y + c.p[1] - v.y, w.y, c.p[1], c.pinv[1]));
+        u = a;
+    } else {
+        const uint2 t = make_uint2(mont_mul(v.x, w.x, c.p[0], c.pinv[0]), mont_mul(v.y, w.y, c.p[1], c.pinv[1]));
+        v = make_uint2(mod_sub(u.x, t.x, c.p[0]), mod_sub(u.y, t.y, c.p[1]));
+        u = make_uint2(mod_add(u.x, t.x, c.p[0]), mod_add(u.y, t.y, c.p[1]));
     }
-    uint32_t w[2] = {wb[0], wb[1]};
+}
+// Either direction with twiddle 1.
+__device__ __forceinline__ void ntt_bfly1(uint2 &u, uint2 &v, const NttConst &c) {
+    const uint2 a = make_uint2(mod_add(u.x, v.x, c.p[0]), mod_add(u.y, v.y, c.p[1]));
+    v = make_uint2(mod_sub(u.x, v.x, c.p[0]), mod_sub(u.y, v.y, c.p[1]));
+    u = a;
+}
+// Layout B, span 2^I (I < 4): pairs (k, k + 2^I), t mod 2^I = k mod 2^I
+// (NP g is a multiple of 16), twiddle w_{2^(I+1)}^(k mod 2^I) = w_16^e.
+template <int NP, int I, bool INV>
+__device__ __forceinline__ void ntt_b_stage(uint2 (&x)[NP], const NttConst &c) {
+    constexpr int HK = 1 << I;
+    static_assert(I <= 3 && 2 * HK <= NP && NP >= 16, "spans 1..8 inside the thread");
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
-        if (i & HK) continue;  // pairs (i, i + HK), in increasing i
-        if ((i & (HK - 1)) == 0) {
-            w[0] = wb[0];
-            w[1] = wb[1];
-        } else {
-            w[0] = mont_mul(w[0], wst[0], c.p[0], c.pinv[0]);
-            w[1] = mont_mul(w[1], wst[1], c.p[1], c.pinv[1]);
-        }
-        uint32_t uo[2] = {x[i].x, x[i].y}, vo[2] = {x[i + HK].x, x[i + HK].y};
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const uint32_t p = c.p[k], pinv = c.pinv[k];
-            if (!inverse) {
-                const uint32_t a = mod_add(uo[k], vo[k], p);
-                vo[k] = mont_mul(mod_sub(uo[k], vo[k], p), w[k], p, pinv);
-                uo[k] = a;
-            } else {
-                const uint32_t tv = mont_mul(vo[k], w[k], p, pinv);
-                vo[k] = mod_sub(uo[k], tv, p);
-                uo[k] = mod_add(uo[k], tv, p);
-            }
-        }
-        x[i] = make_uint2(uo[0], uo[1]);
-        x[i + HK] = make_uint2(vo[0], vo[1]);
+        if (i & HK) continue;
+        const int e = (i & (HK - 1)) << (3 - I);
+        if (e == 0) ntt_bfly1(x[i], x[i + HK], c);
+        else ntt_bfly<INV>(x[i], x[i + HK], make_uint2(c.w16[INV][0][e], c.w16[INV][1][e]), c);
     }
 }
-// Stages LH, LH + STEP, ..., LAST of one layout.
-template <int NP, int LG, int LH, bool A, int LAST, int STEP>
-__device__ __forceinline__ void ntt_reg_stages(uint2 (&x)[NP], const NttConst &c, const PassGeo &g, int K, int inverse,
-                                               int gq) {
-    ntt_reg_stage<NP, LG, LH, A>(x, c, g, K, inverse, gq);
-    if constexpr (LH != LAST) ntt_reg_stages<NP, LG, LH + STEP, A, LAST, STEP>(x, c, g, K, inverse, gq);
+// Layout A, span G 2^(I-LG) (I >= LG): pairs (k, k + 2^(I-LG)), t mod 2^I =
+// g + G (k mod 2^(I-LG)), twiddle w_{2^(I+1)}^m = rt[m 2^(r-1-I)].
+template <int NP, int LG, int I, bool INV>
+__device__ __forceinline__ void ntt_a_stage(uint2 (&x)[NP], const uint2 *rt, const NttConst &c, int gq) {
+    constexpr int R = __builtin_ctz(NP) + LG;
+    constexpr int HK = 1 << (I - LG);
+    constexpr int SH = R - 1 - I;
+    static_assert(I >= LG && I < R, "spans G .. 2^(r-1)");
+    const uint2 *tb = rt + (gq << SH);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        if (i & HK) continue;
+        ntt_bfly<INV>(x[i], x[i + HK], tb[(i & (HK - 1)) << (LG + SH)], c);
+    }
 }
+// Stages I, I + STEP, ..., LAST of one layout.
+template <int NP, int LG, int I, int LAST, int STEP, bool INV>
+__device__ __forceinline__ void ntt_a_stages(uint2 (&x)[NP], const uint2 *rt, const NttConst &c, int gq) {
+    ntt_a_stage<NP, LG, I, INV>(x, rt, c, gq);
+    if constexpr (I != LAST) ntt_a_stages<NP, LG, I + STEP, LAST, STEP, INV>(x, rt, c, gq);
+}
+template <int NP, int I, int LAST, int STEP, bool INV>
+__device__ __forceinline__ void ntt_b_stages(uint2 (&x)[NP], const NttConst &c) {
+    ntt_b_stage<NP, I, INV>(x, c);
+    if constexpr (I != LAST) ntt_b_stages<NP, I + STEP, LAST, STEP, INV>(x, c);
+}
+// w_N^m (or w_N^-m with inv), 0 <= m < N: w^(N/2) = -1, w^-m = w^(N-m).
+__device__ __forceinline__ uint32_t root_power(const NttConst &c, int k, int m, bool inv, int K) {
+    const int half = 1 << (K - 1);
+    if (inv && m != 0) m = 2 * half - m;
+    return m < half ? table_power(c, k, m) : c.p[k] - table_power(c, k, m - half);
+}
+constexpr int bit_reverse(int v, int bits) {
+    int r = 0;
+    for (int i = 0; i < bits; ++i) r |= ((v >> i) & 1) << (bits - 1 - i);
+    return r;
+}
+// x[k] *= Phi_c(t) (or its inverse) for the thread's points t = NP g + k of
+// layout B.  rev_r(t) = rev(k) G + rev(g), so Phi_c(t) = V^rev(g) (V^G)^rev(k)
+// with V = w_{2^s_hi}^c = w_N^(c 2^(K - s_hi)): the powers are stepped
+// through in the order of rev(k), one product per point, and applied, one
+// more.
+template <int NP, int LG, bool INV>
+__device__ __forceinline__ void ntt_column_factors(uint2 (&x)[NP], const NttConst &c, const PassGeo &g, int K) {
+    constexpr int LNP = __builtin_ctz(NP);
+    const int q = threadIdx.x & 15, gq = threadIdx.x >> 4;
+    const int col = g.low0 + (q & g.cmask);
+    const int sh = K - g.s_hi;
+    const int e0 = (col * static_cast<int>(__brev(static_cast<unsigned>(gq)) >> (32 - LG))) << sh;  // < 2^(K-LNP)
+    const int ez = col << (sh + LG);
+    uint32_t f[2], z[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        f[k] = root_power(c, k, e0, INV, K);
+        z[k] = root_power(c, k, ez, INV, K);
+    }
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        const int k = bit_reverse(j, LNP);
+        x[k] = make_uint2(mont_mul(x[k].x, f[0], c.p[0], c.pinv[0]), mont_mul(x[k].y, f[1], c.p[1], c.pinv[1]));
+        if (j + 1 < NP) {
+            f[0] = mont_mul(f[0], z[0], c.p[0], c.pinv[0]);
+            f[1] = mont_mul(f[1], z[1], c.p[1], c.pinv[1]);
+        }
+    }
+}
+// The inner twiddles w_{2^r}^j (or w_{2^r}^-j), j < 2^(r-1): entries j 2^(9-r)
+// of the w_512 table.  The caller synchronises before the first use.
+template <int R>
+__device__ __forceinline__ void ntt_load_roots(uint2 *rt, const NttConst &c, int inv) {
+    static_assert(R <= 9, "the table holds powers of w_512");
+    for (int j = threadIdx.x; j < (1 << (R - 1)); j += blockDim.x) rt[j] = c.rt[inv * 256 + (j << (9 - R))];
+}
+
 // The register passes' tile in shared memory: point t of column q at
 // t * kTilePitch + q; the padding makes both a column-major and a row-major
 // sweep conflict-free.
@@ -351,22 +437,24 @@ __device__ __forceinline__ void ntt_reg_store(const uint2 (&x)[NP], uint2 *__res
     }
 }
 template <int NP, int LG>
-__device__ __forceinline__ void ntt_reg_forward(uint2 (&x)[NP], uint2 *tile, const NttConst &c, const PassGeo &g,
-                                                int K) {
+__device__ __forceinline__ void ntt_reg_forward(uint2 (&x)[NP], uint2 *tile, const uint2 *rt, const NttConst &c,
+                                                const PassGeo &g, int K) {
     constexpr int R = __builtin_ctz(NP) + LG;
     const int gq = threadIdx.x >> 4;
-    ntt_reg_stages<NP, LG, R - 1, true, LG, -1>(x, c, g, K, 0, gq);  // spans 2^(R-1) .. G, layout A
+    ntt_a_stages<NP, LG, R - 1, LG, -1, false>(x, rt, c, gq);  // spans 2^(R-1) .. G, layout A
     ntt_reg_transpose<NP, LG>(x, tile, true);
-    ntt_reg_stages<NP, LG, LG - 1, false, 0, -1>(x, c, g, K, 0, gq);  // spans G/2 .. 1, layout B
+    ntt_b_stages<NP, LG - 1, 0, -1, false>(x, c);  // spans G/2 .. 1, layout B
+    if (g.lst > 0) ntt_column_factors<NP, LG, false>(x, c, g, K);
 }
 template <int NP, int LG>
-__device__ __forceinline__ void ntt_reg_inverse(uint2 (&x)[NP], uint2 *tile, const NttConst &c, const PassGeo &g,
-                                                int K) {
+__device__ __forceinline__ void ntt_reg_inverse(uint2 (&x)[NP], uint2 *tile, const uint2 *rt, const NttConst &c,
+                                                const PassGeo &g, int K) {
     constexpr int R = __builtin_ctz(NP) + LG;
     const int gq = threadIdx.x >> 4;
-    ntt_reg_stages<NP, LG, 0, false, LG - 1, 1>(x, c, g, K, 1, gq);  // spans 1 .. G/2, layout B
+    if (g.lst > 0) ntt_column_factors<NP, LG, true>(x, c, g, K);
+    ntt_b_stages<NP, 0, LG - 1, 1, true>(x, c);  // spans 1 .. G/2, layout B
     ntt_reg_transpose<NP, LG>(x, tile, false);
-    ntt_reg_stages<NP, LG, LG, true, R - 1, 1>(x, c, g, K, 1, gq);  // spans G .. 2^(R-1), layout A
+    ntt_a_stages<NP, LG, LG, R - 1, 1, true>(x, rt, c, gq);  // spans G .. 2^(R-1), layout A
 }
 
 // A pass of r = log2(NP G) stages with 16 G threads; forward passes load in
@@ -376,13 +464,16 @@ __device__ __forceinline__ void ntt_reg_inverse(uint2 (&x)[NP], uint2 *tile, con
 template <int NP, int LG>
 __global__ void __launch_bounds__(16 << LG, NP == 32 ? 2 : 3) k_ntt_rpass(uint2 *__restrict__ d, NttConst c, int K,
                                                                              int s_hi, int inverse) {
-    extern __shared__ uint2 tile[];  // [NP G][kTilePitch]
+    extern __shared__ uint2 tile[];  // [NP G][kTilePitch], then the 2^(r-1) inner twiddles
     constexpr int r = __builtin_ctz(NP) + LG;
+    uint2 *rt = tile + (NP << LG) * kTilePitch;
+    ntt_load_roots<r>(rt, c, inverse);
+    __syncthreads();
     const PassGeo g(s_hi, r);
     uint2 x[NP];
     ntt_reg_load<NP, LG>(x, d, tile, g, !inverse);
-    if (!inverse) ntt_reg_forward<NP, LG>(x, tile, c, g, K);
-    else ntt_reg_inverse<NP, LG>(x, tile, c, g, K);
+    if (!inverse) ntt_reg_forward<NP, LG>(x, tile, rt, c, g, K);
+    else ntt_reg_inverse<NP, LG>(x, tile, rt, c, g, K);
     ntt_reg_store<NP, LG>(x, d, tile, g, inverse);
 }
 
@@ -392,12 +483,16 @@ template <int NP, int LG>
 __global__ void __launch_bounds__(16 << LG, NP == 32 ? 2 : 3) k_ntt_rmid(uint2 *__restrict__ d,
                                                                             const uint2 *__restrict__ a, NttConst c,
                                                                             int K) {
-    extern __shared__ uint2 tile[];
+    extern __shared__ uint2 tile[];  // [NP G][kTilePitch], then the forward and inverse inner twiddles
     constexpr int r = __builtin_ctz(NP) + LG;
+    uint2 *rtf = tile + (NP << LG) * kTilePitch, *rti = rtf + (1 << (r - 1));
+    ntt_load_roots<r>(rtf, c, 0);
+    ntt_load_roots<r>(rti, c, 1);
+    __syncthreads();
     const PassGeo g(r, r);
     uint2 x[NP];
     ntt_reg_load<NP, LG>(x, d, tile, g, true);
-    ntt_reg_forward<NP, LG>(x, tile, c, g, K);
+    ntt_reg_forward<NP, LG>(x, tile, rtf, c, g, K);
     // layout B; the spectrum is stored in this kernel's register order
     // (point k of thread tid of block bx at (bx NP + k) 16 G + tid), so the
     // reads are coalesced
@@ -407,8 +502,14 @@ __global__ void __launch_bounds__(16 << LG, NP == 32 ? 2 : 3) k_ntt_rmid(uint2 *
         const uint2 v = ab[k << (4 + LG)];
         x[k] = make_uint2(mont_mul(x[k].x, v.x, c.p[0], c.pinv[0]), mont_mul(x[k].y, v.y, c.p[1], c.pinv[1]));
     }
-    ntt_reg_inverse<NP, LG>(x, tile, c, g, K);
+    ntt_reg_inverse<NP, LG>(x, tile, rti, c, g, K);
     ntt_reg_store<NP, LG>(x, d, tile, g, true);
+}
+
+// Shared memory of the register passes: the tile and the inner twiddles
+// (one direction for k_ntt_rpass, both for k_ntt_rmid).
+constexpr size_t ntt_rsmem(int r, bool mid) {
+    return (static_cast<size_t>(kTilePitch) * (1u << r) + (mid ? (1u << r) : (1u << (r - 1)))) * sizeof(uint2);
 }
 
 // dst <- src * f in the register order of k_ntt_rmid<NP, 4> for a last pass
@@ -552,7 +653,15 @@ NttConst ntt_const(const hmv_plan_s *p) {
         c.pinv[k] = 0u - inv;
         c.tlo[k] = p->ntt_tw + (2 * k) * (1 << kTwLoBits);
         c.thi[k] = p->ntt_tw + (2 * k + 1) * (1 << kTwLoBits);
+        const uint64_t P = kNttP[k];
+        const uint64_t w16 = powmod(kNttRoot[k], (P - 1) / 16, P);
+        const uint64_t R = (uint64_t(1) << 32) % P;
+        for (int e = 0; e < 8; ++e) {
+            c.w16[0][k][e] = static_cast<uint32_t>(mulmod(powmod(w16, e, P), R, P));
+            c.w16[1][k][e] = static_cast<uint32_t>(mulmod(powmod(w16, (16 - e) % 16, P), R, P));
+        }
     }
+    c.rt = reinterpret_cast<const uint2 *>(p->ntt_tw + 4 * (1 << kTwLoBits));
     return c;
 }
 
@@ -590,18 +699,21 @@ cudaError_t ntt_attrs() {
     static bool attr = false;
     if (attr) return cudaSuccess;
     const int smem = static_cast<int>(kNttCols * (1u << kNttMaxR) * sizeof(uint2));
-    const int rsmem = static_cast<int>(kTilePitch * (1u << 9) * sizeof(uint2));
     cudaError_t e = cudaFuncSetAttribute(k_ntt_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt_rpass<32, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, rsmem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt_rmid<32, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, rsmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_ntt_rpass<32, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(ntt_rsmem(9, false)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_ntt_rmid<32, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(ntt_rsmem(9, true)));
     if (e == cudaSuccess) attr = true;
     return e;
 }
 
 cudaError_t launch_pass(hmv_plan_s *p, uint2 *data, const NttConst &c, int s_hi, int r, int inverse) {
     const unsigned blocks = static_cast<unsigned>((p->ntt_N >> r) / kNttCols);
-    const size_t smem = static_cast<size_t>(r >= 8 ? kTilePitch : kNttCols) * (1u << r) * sizeof(uint2);
+    const size_t smem = r >= 8 ? ntt_rsmem(r, false) : kNttCols * (size_t(1) << r) * sizeof(uint2);
     if (r == 9)  // 32 points a thread: 16 columns x 16 threads
         k_ntt_rpass<32, 4><<<blocks, 256, smem, p->stream>>>(data, c, p->ntt_K, s_hi, inverse);
     else if (r == 8)  // 16 points a thread: 16 columns x 16 threads (8 threads a column with 32 points each
@@ -635,7 +747,7 @@ cudaError_t run_ntt_product(hmv_plan_s *p, uint2 *data) {
     if (e == cudaSuccess) {
         const int r = bounds[np - 1][1];  // s_hi = r: blocks of 2^r consecutive points
         const unsigned blocks = static_cast<unsigned>((p->ntt_N >> r) / kNttCols);
-        const size_t smem = static_cast<size_t>(r >= 8 ? kTilePitch : kNttCols) * (1u << r) * sizeof(uint2);
+        const size_t smem = r >= 8 ? ntt_rsmem(r, true) : kNttCols * (size_t(1) << r) * sizeof(uint2);
         if (r == 9)
             k_ntt_rmid<32, 4><<<blocks, 256, smem, p->stream>>>(data, p->ntt_a, c, p->ntt_K);
         else if (r == 8)
@@ -662,11 +774,14 @@ bool ntt_geometry(int n, int b, int &P, int &S, int &K) {
     return K <= kNttMaxK;
 }
 
+size_t ntt_table_words() { return 4 * (size_t(1) << kTwLoBits) + kNttRootWords; }
+
 // Twiddle tables (Montgomery form, R = 2^32) for both primes: T_lo[i] =
-// w^i, T_hi[i] = w^(i 2^13), w a primitive 2^K-th root of unity.
+// w^i, T_hi[i] = w^(i 2^13), w a primitive 2^K-th root of unity; then the
+// register passes' w_512 table.
 cudaError_t ntt_init(hmv_plan_s *p) {
     const int TS = 1 << kTwLoBits;
-    std::vector<uint32_t> tab(4 * static_cast<size_t>(TS));
+    std::vector<uint32_t> tab(ntt_table_words());
     for (int k = 0; k < 2; ++k) {
         const uint64_t P = kNttP[k];
         const uint64_t w = powmod(kNttRoot[k], (P - 1) >> p->ntt_K, P);
@@ -678,6 +793,18 @@ cudaError_t ntt_init(hmv_plan_s *p) {
             tab[(2 * k + 1) * TS + i] = static_cast<uint32_t>(hi);
             lo = mulmod(lo, w, P);
             hi = mulmod(hi, wstep, P);
+        }
+    }
+    // the register passes' inner twiddles: w_512^j and w_512^-j, j < 256, as
+    // (prime 0, prime 1) pairs, forward table first
+    for (int k = 0; k < 2; ++k) {
+        const uint64_t P = kNttP[k];
+        const uint64_t w512 = powmod(kNttRoot[k], (P - 1) / 512, P);
+        const uint64_t R = (uint64_t(1) << 32) % P;
+        for (int j = 0; j < 256; ++j) {
+            tab[4 * static_cast<size_t>(TS) + 2 * j + k] = static_cast<uint32_t>(mulmod(powmod(w512, j, P), R, P));
+            tab[4 * static_cast<size_t>(TS) + 512 + 2 * j + k] =
+                static_cast<uint32_t>(mulmod(powmod(w512, (512 - j) % 512, P), R, P));
         }
     }
     return cudaMemcpyAsync(p->ntt_tw, tab.data(), tab.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, p->stream);

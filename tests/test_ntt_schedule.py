@@ -1,7 +1,9 @@
 """CPU replica of the NTT path's pass schedule (no GPU): the register-blocked
 passes' assignment of points to threads (layouts A and B with one transpose),
-their geometric twiddle sequences and the split of the K stages into passes
-must reproduce a textbook radix-2 transform.  Forward: decimation in
+their four-step twiddles (inner twiddles per stage, one column factor per
+point at the end of a forward pass and the start of an inverse one) and the
+split of the K stages into passes must reproduce a textbook radix-2
+transform.  Forward: decimation in
 frequency, natural order in, bit-reversed out; inverse: decimation in time,
 back to natural order, times N.  Arithmetic modulo the path's first prime.
 """
@@ -52,27 +54,29 @@ def wpow(K, m, inverse):
     return pow(w, (-m) % (1 << K) if inverse else m, P1)
 
 
-def reg_stage(xs, g, K, LH, A, inverse, NP, LG):
-    """One stage on every thread's registers, as ntt_reg_stage: twiddles by
-    the base-and-step sequence, checked against the direct exponent."""
+def rev(v, bits):
+    return int(format(v, "0%db" % bits)[::-1], 2) if bits else 0
+
+
+def reg_stage(xs, r, I, A, inverse, NP, LG):
+    """One stage (span 2^I points of the column) on every thread's registers,
+    as ntt_a_stage / ntt_b_stage: inner twiddles only, from the w_{2^r} table
+    (layout A) or as powers of w_16 (layout B), checked against
+    w_{2^(I+1)}^(t mod 2^I)."""
     G = 1 << LG
-    HK = (1 << (LH - LG)) if A else (1 << LH)
-    s = g["s_lo"] + LH
-    lw = K - 1 - LH
+    HK = (1 << (I - LG)) if A else (1 << I)
     for tid in range(16 * G):
-        q, gq = tid & 15, tid >> 4
-        mb = (g["low0"] + (q & g["cmask"])) << (K - s)
-        wb = wpow(K, mb + ((gq if A else 0) << lw), inverse)
-        ws = wpow(K, (G if A else 1) << lw, inverse)
+        gq = tid >> 4
         x = xs[tid]
-        w = wb
         for i in range(NP):
             if i & HK:
                 continue
-            w = wb if (i & (HK - 1)) == 0 else w * ws % P1
+            if A:
+                w = wpow(r, (gq + G * (i & (HK - 1))) << (r - 1 - I), inverse)
+            else:
+                w = wpow(4, (i & (HK - 1)) << (3 - I), inverse)
             t = (gq + G * i) if A else (NP * gq + i)
-            tlow = t % (1 << LH)
-            assert w == wpow(K, mb + (tlow << lw), inverse)
+            assert w == wpow(I + 1, t % (1 << I), inverse)
             u, v = x[i], x[i + HK]
             if not inverse:
                 x[i], x[i + HK] = (u + v) % P1, (u - v) * w % P1
@@ -81,10 +85,30 @@ def reg_stage(xs, g, K, LH, A, inverse, NP, LG):
                 x[i], x[i + HK] = (u + tv) % P1, (u - tv) % P1
 
 
+def column_factors(xs, g, K, inverse, NP, LG):
+    """ntt_column_factors: point t = NP g + k of column c times
+    (w_{2^s_hi}^c)^rev_r(t), the powers stepped through in the order of
+    rev(k) from V^rev(g) by V^G."""
+    lnp = NP.bit_length() - 1
+    r = lnp + LG
+    sh = K - g["s_hi"]
+    for tid in range(16 << LG):
+        q, gq = tid & 15, tid >> 4
+        col = g["low0"] + (q & g["cmask"])
+        f = wpow(K, (col * rev(gq, LG)) << sh, inverse)
+        z = wpow(K, col << (sh + LG), inverse)
+        for j in range(NP):
+            k = rev(j, lnp)
+            assert f == wpow(K, (col * rev(NP * gq + k, r)) << sh, inverse)
+            xs[tid][k] = xs[tid][k] * f % P1
+            f = f * z % P1
+
+
 def run_rpass(d, K, s_hi, r, inverse, spectrum=None):
     """k_ntt_rpass (spectrum None) or k_ntt_rmid (with the pointwise product)
     as the library launches them: 16 columns a block, 16 threads a column,
-    32 points a thread for r = 9 and 16 for r = 8."""
+    32 points a thread for r = 9 and 16 for r = 8; inner stages, then the
+    column factors (forward), or the factors first (inverse)."""
     NP, LG = (32 if r == 9 else 16), 4
     G = 1 << LG
     T = 16 * G
@@ -112,18 +136,22 @@ def run_rpass(d, K, s_hi, r, inverse, spectrum=None):
                 xs[tid] = [tile[((pb if to_b else pa)(gq, k), q)] for k in range(NP)]
 
         def forward():
-            for LH in range(r - 1, LG - 1, -1):
-                reg_stage(xs, g, K, LH, True, False, NP, LG)
+            for I in range(r - 1, LG - 1, -1):
+                reg_stage(xs, r, I, True, False, NP, LG)
             transpose(True)
-            for LH in range(LG - 1, -1, -1):
-                reg_stage(xs, g, K, LH, False, False, NP, LG)
+            for I in range(LG - 1, -1, -1):
+                reg_stage(xs, r, I, False, False, NP, LG)
+            if g["lst"] > 0:
+                column_factors(xs, g, K, False, NP, LG)
 
         def inverse_stages():
-            for LH in range(0, LG):
-                reg_stage(xs, g, K, LH, False, True, NP, LG)
+            if g["lst"] > 0:
+                column_factors(xs, g, K, True, NP, LG)
+            for I in range(0, LG):
+                reg_stage(xs, r, I, False, True, NP, LG)
             transpose(False)
-            for LH in range(LG, r):
-                reg_stage(xs, g, K, LH, True, True, NP, LG)
+            for I in range(LG, r):
+                reg_stage(xs, r, I, True, True, NP, LG)
 
         if spectrum is not None:
             forward()
