@@ -540,11 +540,14 @@ __global__ void k_ntt_scale(uint2 *__restrict__ a, long long N, NttConst c, uint
 // Row i of the product: the coefficients z[t] = c[(i+n-1) S + t], t < 2P-1,
 // each the Chinese remainder of its two residues taken in (-p1 p2/2,
 // p1 p2/2), then Z_i = sum_t z[t] 2^(16 t) as |Z| limbs, sign and bit length
-// (as the other paths).  One warp per row, a window of 1024 positions at a
-// time, 32 consecutive positions per lane: a carry chain base 2^16 per lane,
-// then the carries passed up one lane per round until none is left; two
-// positions make a limb.  A final carry of -1 means Z < 0: the limbs hold its
-// two's complement and are negated in place.
+// (as the other paths).  One warp per row, a window of 512 positions at a
+// time: the residues are read coalesced (lane l: positions l + 32 k) and
+// their coefficients parked in shared memory, from where every lane takes
+// 16 consecutive positions; a carry chain base 2^16 per lane, then the
+// carries passed up one lane per round among the lanes that hold positions
+// of the row until none is left; two positions make a limb.  A final carry
+// of -1 means Z < 0: the limbs hold its two's complement and are negated in
+// place.
 __device__ __forceinline__ long long ntt_crt(uint2 r, const NttConst &c, uint32_t inv1R) {
     const uint32_t p1 = c.p[0], p2 = c.p[1];
     const uint32_t r1m = r.x >= p2 ? r.x - p2 : r.x;  // r1 < p1 < 2 p2
@@ -553,54 +556,64 @@ __device__ __forceinline__ long long ntt_crt(uint2 r, const NttConst &c, uint32_
     const unsigned long long v = r.x + static_cast<unsigned long long>(p1) * x;  // in [0, p1 p2)
     return v > M / 2 ? static_cast<long long>(v) - static_cast<long long>(M) : static_cast<long long>(v);
 }
-constexpr int kPosPerLane = 32;
-__global__ void __launch_bounds__(256) k_ntt_extract(const uint2 *__restrict__ cvec, int n, int S, int T, NttConst c,
-                                                     uint32_t inv1R, uint32_t *__restrict__ zmag,
-                                                     uint8_t *__restrict__ zneg, int32_t *__restrict__ zbits, int ZW,
-                                                     int32_t *dstat, int row_offset) {
+constexpr int kExPos = 16;               // consecutive positions a lane
+constexpr int kExWin = 32 * kExPos;      // positions a window
+constexpr int kExPitch = kExPos + 1;     // shared-memory words a lane (the padding spreads the banks)
+constexpr int kExWarps = 8;              // rows a block
+// digits base 2^16 of v + carry-in, in place; returns the carry out (floor)
+__device__ __forceinline__ long long ntt_chain(long long (&v)[kExPos], long long cy) {
+#pragma unroll
+    for (int k = 0; k < kExPos; ++k) {
+        const long long s = v[k] + cy;
+        v[k] = s & 0xFFFF;
+        cy = s >> 16;  // arithmetic: floor
+    }
+    return cy;
+}
+__global__ void __launch_bounds__(32 * kExWarps) k_ntt_extract(const uint2 *__restrict__ cvec, int n, int S, int T,
+                                                              NttConst c, uint32_t inv1R, uint32_t *__restrict__ zmag,
+                                                              uint8_t *__restrict__ zneg, int32_t *__restrict__ zbits,
+                                                              int ZW, int32_t *dstat, int row_offset) {
+    __shared__ long long win[kExWarps][32 * kExPitch];
     const int lane = threadIdx.x & 31;
-    const int i = static_cast<int>((static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
-    if (i >= n) return;  // warp-uniform
+    const int i = static_cast<int>(blockIdx.x) * kExWarps + static_cast<int>(threadIdx.x >> 5);
+    if (i >= n) return;  // warp-uniform; the warps share no data
+    long long *ws = win[threadIdx.x >> 5];
     const uint2 *row = cvec + static_cast<long long>(i + n - 1) * S;
     uint32_t *z = zmag + static_cast<size_t>(row_offset + i) * ZW;
     const int span = max(T, 2 * ZW);  // every limb of the row is written
     long long wc = 0;
     bool above_nonzero = false, above_not_ones = false;
-    for (int t0 = 0; t0 < span; t0 += 32 * kPosPerLane) {
-        const int tb = t0 + kPosPerLane * lane;
-        long long v[kPosPerLane];
+    for (int t0 = 0; t0 < span; t0 += kExWin) {
 #pragma unroll
-        for (int k = 0; k < kPosPerLane; ++k) v[k] = (tb + k < T) ? ntt_crt(row[tb + k], c, inv1R) : 0;
-        long long cy = (lane == 0) ? wc : 0;
-#pragma unroll
-        for (int k = 0; k < kPosPerLane; ++k) {
-            const long long s = v[k] + cy;
-            v[k] = s & 0xFFFF;
-            cy = s >> 16;  // arithmetic: floor
+        for (int k = 0; k < kExPos; ++k) {
+            const int e = lane + 32 * k;  // position t0 + e, kept by lane e / 16
+            const int t = t0 + e;
+            ws[(e >> 4) * kExPitch + (e & 15)] = t < T ? ntt_crt(row[t], c, inv1R) : 0;
         }
-        long long pending = cy, out = 0;
-        for (int round = 0; round <= 32; ++round) {
-            out += __shfl_sync(0xffffffffu, pending, 31);
-            long long incoming = __shfl_up_sync(0xffffffffu, pending, 1);
-            if (lane == 0) incoming = 0;
-            if (!__any_sync(0xffffffffu, incoming != 0)) break;
-            cy = incoming;
+        __syncwarp();
+        long long v[kExPos];
 #pragma unroll
-            for (int k = 0; k < kPosPerLane; ++k) {
-                const long long s = v[k] + cy;
-                v[k] = s & 0xFFFF;
-                cy = s >> 16;
-            }
-            pending = cy;
+        for (int k = 0; k < kExPos; ++k) v[k] = ws[lane * kExPitch + k];
+        __syncwarp();  // the next window's writes come after every lane's reads
+        const int tb = t0 + kExPos * lane;
+        const int last = min(31, (span - 1 - t0) / kExPos);  // the last lane with positions of the row
+        long long pending = ntt_chain(v, lane == 0 ? wc : 0), out = 0;
+        for (int round = 0; round <= 32; ++round) {
+            out += __shfl_sync(0xffffffffu, pending, last);
+            long long incoming = __shfl_up_sync(0xffffffffu, pending, 1);
+            if (lane == 0 || lane > last) incoming = 0;
+            if (!__any_sync(0xffffffffu, incoming != 0)) break;
+            pending = ntt_chain(v, incoming);
         }
         wc = out;
 #pragma unroll
-        for (int k = 0; k < kPosPerLane / 2; ++k) {
+        for (int k = 0; k < kExPos / 2; ++k) {
             const uint32_t limb = static_cast<uint32_t>(v[2 * k]) | (static_cast<uint32_t>(v[2 * k + 1]) << 16);
             const int li = tb / 2 + k;
             if (li < ZW) {
                 z[li] = limb;
-            } else {
+            } else if (lane <= last) {
                 above_nonzero |= limb != 0u;
                 above_not_ones |= limb != 0xFFFFFFFFu;
             }
@@ -857,7 +870,7 @@ cudaError_t ntt_vector_product(hmv_plan_s *p, const uint32_t *xl, const uint8_t 
     const uint64_t P2 = kNttP[1];
     const uint32_t inv1R =
         static_cast<uint32_t>(mulmod(powmod(kNttP[0] % P2, P2 - 2, P2), (uint64_t(1) << 32) % P2, P2));
-    k_ntt_extract<<<static_cast<unsigned>((p->n + 7) / 8), 256, 0, p->stream>>>(
+    k_ntt_extract<<<static_cast<unsigned>((p->n + kExWarps - 1) / kExWarps), 32 * kExWarps, 0, p->stream>>>(
         p->ntt_x, p->n, p->ntt_S, 2 * p->ntt_P - 1, c, inv1R, p->zmag, p->zneg, p->zbits, p->ZW, p->dstat, rhs * p->n);
     p->launches_total++;
     return cudaGetLastError();
