@@ -325,6 +325,8 @@ def run_ours(args):
         extras["batched"] = measure_batched(3, 1, args.wave_gb)
         extras["serving"] = measure_serving(args.extra_requests, args.rate, args.matvecs_per_request,
                                             args.serve_gb, False)
+        extras["serving_exact_ntt"] = measure_serving(args.extra_requests, args.rate, args.matvecs_per_request,
+                                                      args.serve_gb, False, "ntt")
 
     if rank != 0:
         return 0
@@ -558,9 +560,10 @@ def run_lanczos(args):
     return 0
 
 
-def measure_serving(requests, rate, matvecs_per_request, serve_gb, chains):
+def measure_serving(requests, rate, matvecs_per_request, serve_gb, chains, method="auto"):
     """Config 5: Poisson arrivals of Lanczos (or chain) requests, continuous
-    batching; matvecs/s and p50/p99 latency per matvec."""
+    batching; matvecs/s and p50/p99 latency per matvec.  method: "auto" (the
+    tensor-core Karatsuba path) or "ntt" (the exact NTT path)."""
     import random
 
     import torch
@@ -576,7 +579,8 @@ def measure_serving(requests, rate, matvecs_per_request, serve_gb, chains):
         reqs.append(Request(i, n, b, uniform_vec(BASE_SEED + 4, 2 * i, 2 * n - 1, b, 0),
                             uniform_vec(BASE_SEED + 4, 2 * i + 1, n, b, 0), matvecs_per_request, arrival=t,
                             lanczos=not chains))
-    srv = Server(memory_budget=serve_gb << 30)
+    from paper_1402_5287_gb300 import hmv
+    srv = Server(memory_budget=serve_gb << 30, method={"auto": hmv.AUTO, "ntt": hmv.NTT}[method])
     with ClockSampler(torch.cuda.current_device()) as clocks:
         st = srv.run(reqs)
     desc = (f"{requests} requests, Poisson arrivals at {rate}/s, n ~ U[64,4096], b in {{2048,8192,33220}}, "
@@ -584,18 +588,22 @@ def measure_serving(requests, rate, matvecs_per_request, serve_gb, chains):
                f"{matvecs_per_request} Lanczos steps (one matvec, two exact inner products and one exact "
                f"update each)")
             + " per request against a resident A (cap on the 2n of a full Lanczos run)")
+    path = ("exact NTT path (requests it cannot take: tensor-core path)" if method == "ntt"
+            else "tensor-core Karatsuba path")
     return {"value": st["matvecs_per_s"], "unit": UNIT, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-            "workload": desc, "memory_budget_gb": serve_gb, "serving": st, "clocks": clocks.summary()}
+            "workload": desc, "method": path, "memory_budget_gb": serve_gb, "serving": st,
+            "clocks": clocks.summary()}
 
 
 def run_serving(args):
     import paper_1402_5287_gb300 as pkg
     pkg.build()
-    r = measure_serving(args.requests, args.rate, args.matvecs_per_request, args.serve_gb, args.serve_chains)
+    r = measure_serving(args.requests, args.rate, args.matvecs_per_request, args.serve_gb, args.serve_chains,
+                        args.serve_method)
     line = {"metric": "served Hankel matvecs/s with p50/p99 matvec latency", "value": r["value"],
             "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "vs_baseline": None, "dtype": "bf16",
             "data": "synthetic", "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"],
-            "config": {"workload": r["workload"], "memory_budget_gb": r["memory_budget_gb"]},
+            "config": {"workload": r["workload"], "method": r["method"], "memory_budget_gb": r["memory_budget_gb"]},
             "serving": r["serving"], "clocks": r["clocks"]}
     print(json.dumps(line), flush=True)
     return 0
@@ -703,6 +711,8 @@ def main(argv=None):
     ap.add_argument("--rate", type=float, default=4.0, help="serving: Poisson arrival rate (requests/s)")
     ap.add_argument("--matvecs-per-request", type=int, default=16)
     ap.add_argument("--serve-gb", type=int, default=200, help="serving: device memory budget")
+    ap.add_argument("--serve-method", choices=["auto", "ntt"], default="auto",
+                    help="serving: the tensor-core Karatsuba path (auto) or the exact NTT path")
     ap.add_argument("--serve-chains", action="store_true",
                     help="serving: plain chains v <- A v instead of Lanczos steps")
     args = ap.parse_args(argv)

@@ -188,13 +188,15 @@ void hmv_free(hmv_plan_t *plan);
 hmv_status hmv_plan_bytes(const hmv_desc *desc, uint64_t *bytes);
 
 /* One product for each of `count` distinct loaded plans (Karatsuba
- * tensor-core path, nrhs = 1; orders and precisions may differ): every
- * leaf product of every plan runs in ONE persistent tensor-core launch, the
- * level kernels around it, all on plans[0]'s stream.  This is the step of a
- * continuous-batching server: the set of plans may change from call to
- * call.  xs[i], ys[i] as in hmv_matvec (all host or all device pointers);
- * every ys[i].exponent is written; the call returns when all are done.
- * Results are bit-identical to separate hmv_matvec calls. */
+ * tensor-core path with tensor-core leaves, or the exact NTT path; nrhs = 1;
+ * orders and precisions may differ): every leaf product of every Karatsuba
+ * plan runs in ONE persistent tensor-core launch, the level kernels around
+ * it, and every NTT plan runs its transforms, all on plans[0]'s stream.
+ * This is the step of a continuous-batching server: the set of plans may
+ * change from call to call.  xs[i], ys[i] as in hmv_matvec (all host or all
+ * device pointers); every ys[i].exponent is written; the call returns when
+ * all are done.  Results are bit-identical to separate hmv_matvec calls.
+ * Other methods, external scratch or nrhs != 1: HMV_EUNSUPPORTED. */
 hmv_status hmv_matvec_many(int32_t count, hmv_plan_t *const *plans, const hmv_vec *xs, hmv_vec *ys);
 
 /* Plan facts and (with HMV_FLAG_TIMING) stage times. */

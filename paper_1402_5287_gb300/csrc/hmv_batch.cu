@@ -477,7 +477,9 @@ hmv_status hmv_batch_get_info(const hmv_batch_t *B, hmv_batch_info *o) {
 // ---------------------------------------------------------------------------
 // One matvec for each of several independent plans, with every leaf product
 // in one persistent tensor-core launch: the step of a continuous-batching
-// server, whose set of plans changes from one call to the next.
+// server, whose set of plans changes from one call to the next.  Plans of
+// the exact NTT path take part with their own transforms on the same stream
+// (they have no leaf products).
 extern "C" hmv_status hmv_matvec_many(int32_t count, hmv_plan_t *const *plans, const hmv_vec *xs, hmv_vec *ys) {
     if (count < 1 || !plans || !xs || !ys) return HMV_EINVAL;
     for (int i = 0; i < count; ++i) {
@@ -485,8 +487,9 @@ extern "C" hmv_status hmv_matvec_many(int32_t count, hmv_plan_t *const *plans, c
         if (!p) return HMV_EINVAL;
         for (int k = 0; k < i; ++k)
             if (plans[k] == p) return HMV_EINVAL;  // a plan holds one product at a time
-        if (p->method != HMV_KARATSUBA || p->external_scratch || p->nrhs != 1) return HMV_EUNSUPPORTED;
-        if (p->children.empty() && !p->hrev) return HMV_EUNSUPPORTED;  // CUDA-core leaves
+        if ((p->method != HMV_KARATSUBA && p->method != HMV_NTT) || p->external_scratch || p->nrhs != 1)
+            return HMV_EUNSUPPORTED;
+        if (p->method == HMV_KARATSUBA && p->children.empty() && !p->hrev) return HMV_EUNSUPPORTED;  // CUDA-core leaves
         if (!p->loaded) return HMV_ENOTLOADED;
         const hmv_vec &x = xs[i], &y = ys[i];
         if (x.len != p->n || x.nrhs != 1 || x.b != p->b || !x.limbs || !x.neg || x.reserved ||
@@ -514,6 +517,11 @@ extern "C" hmv_status hmv_matvec_many(int32_t count, hmv_plan_t *const *plans, c
         }
         if (e == cudaSuccess) e = cudaMemsetAsync(p->dstat, 0, 8 * sizeof(int32_t), s);
         if (e == cudaSuccess) e = launch_validate(p, xl, p->n);
+        if (p->method == HMV_NTT) {  // the whole product: transforms, pointwise product, extraction
+            if (e == cudaSuccess) e = ntt_vector_product(p, xl, xn, 0);
+            p->ntt_matvecs++;
+            continue;
+        }
         if (!p->children.empty()) {  // digit split: the vector side of every unsplit descendant
             if (e == cudaSuccess) e = split_vector_side(p, xl, xn);
             continue;
@@ -524,10 +532,11 @@ extern "C" hmv_status hmv_matvec_many(int32_t count, hmv_plan_t *const *plans, c
         if (e == cudaSuccess) e = launch_pack_vector(p, p->x_lvl[p->L % 2]);
     }
     std::vector<hmv_plan_s *> leafplans;  // every unsplit plan, split plans contributing their descendants
-    for (int i = 0; i < count; ++i) collect_leaf_plans(plans[i], leafplans);
+    for (int i = 0; i < count; ++i)
+        if (plans[i]->method == HMV_KARATSUBA) collect_leaf_plans(plans[i], leafplans);
     // one persistent launch per tile width present (normally one); the
     // step's problem and tile lists are staged in pinned host memory and
-    // copied into device memory, both kept by plans[0] and grown on demand
+    // copied into device memory, both kept by the first Karatsuba plan and grown on demand
     // (the previous call ended with a stream synchronisation, so neither is
     // still in use)
     std::vector<LeafProblem> gp[2];
@@ -550,10 +559,12 @@ extern "C" hmv_status hmv_matvec_many(int32_t count, hmv_plan_t *const *plans, c
         off_t[w] = total;
         total += al(gt[w].size() * sizeof(Tile));
     }
-    hmv_plan_s *lead = plans[0];
-    if (e == cudaSuccess) e = grow(lead->many_dev, total);
-    if (e == cudaSuccess) e = grow(lead->many_host, total);
-    if (e == cudaSuccess) {
+    hmv_plan_s *lead = nullptr;  // the leaf launch's buffers, tile counter and status word: a Karatsuba plan's
+    for (int i = 0; i < count && !lead; ++i)
+        if (plans[i]->method == HMV_KARATSUBA) lead = plans[i];
+    if (e == cudaSuccess && total > 0) e = grow(lead->many_dev, total);
+    if (e == cudaSuccess && total > 0) e = grow(lead->many_host, total);
+    if (e == cudaSuccess && total > 0) {
         char *hb = static_cast<char *>(lead->many_host.ptr);
         for (int w = 0; w < 2; ++w) {
             memcpy(hb + off_p[w], gp[w].data(), gp[w].size() * sizeof(LeafProblem));
@@ -571,7 +582,9 @@ extern "C" hmv_status hmv_matvec_many(int32_t count, hmv_plan_t *const *plans, c
     }
     for (int i = 0; i < count && e == cudaSuccess; ++i) {
         hmv_plan_s *p = plans[i];
-        if (!p->children.empty()) {
+        if (p->method == HMV_NTT) {
+            // magnitudes, signs and bit lengths already written by the extraction
+        } else if (!p->children.empty()) {
             e = split_post(p, 0);
         } else {
             e = launch_post_group(&p, 1);  // leaf normalise and every post-pass level
@@ -588,7 +601,7 @@ extern "C" hmv_status hmv_matvec_many(int32_t count, hmv_plan_t *const *plans, c
     if (e == cudaSuccess) e = se;
     for (int i = 0; i < count; ++i) plans[i]->stream = saved[i];
     if (e != cudaSuccess) { cudaGetLastError(); return e == cudaErrorMemoryAllocation ? HMV_ENOMEM : HMV_ECUDA; }
-    // a leaf-kernel timeout is recorded in the first plan's status word
+    // a leaf-kernel timeout is recorded in the status word of the first Karatsuba plan
     for (int i = 0; i < count; ++i) {
         if (st[8 * i] == DEV_BADINPUT) return HMV_EINVAL;
         if (st[8 * i] == DEV_TIMEOUT) return HMV_ETIMEOUT;

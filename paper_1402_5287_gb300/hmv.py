@@ -19,6 +19,7 @@ FLAG_DIGIT_TOOM4, FLAG_DIGIT_TOOM6, FLAG_DIGIT_TOOM8 = 32, 64, 256
 FLAG_TILE256 = 128
 STATUS = {0: "HMV_OK", 1: "HMV_EINVAL", 2: "HMV_ENOMEM", 3: "HMV_ECUDA", 4: "HMV_ETIMEOUT",
           5: "HMV_ENOTLOADED", 6: "HMV_EFFTBOUND", 7: "HMV_EUNSUPPORTED", 8: "HMV_EINTERNAL"}
+EUNSUPPORTED = 7
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libhmv.so")
 EXPORTS = ["hmv_plan", "hmv_load_matrix", "hmv_matvec", "hmv_free", "hmv_get_stats", "hmv_reset_stats",

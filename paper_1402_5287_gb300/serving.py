@@ -14,7 +14,8 @@ Lanczos run is the client's.  The server
   * keeps every admitted matrix resident (one plan per request),
   * runs steps: each step advances EVERY active request by one product with
     one hmv_matvec_many call, whose leaf products share one persistent
-    tensor-core launch; requests that arrive during a step join at the next
+    tensor-core launch (requests on the exact NTT path run their transforms
+    in the same call); requests that arrive during a step join at the next
     one, finished requests leave and free their memory (continuous batching),
   * records, per product, the time from when it became ready (arrival for
     the first, the previous product's completion otherwise) to completion.
@@ -46,6 +47,7 @@ class Request:
     kind: int = hmv.HANKEL
     lanczos: bool = False            # Lanczos steps instead of a plain chain
     # filled by the server
+    method: int = hmv.AUTO           # the plan's method (the server's, or AUTO where that cannot take it)
     admitted: float | None = None
     finished: float | None = None
     latencies: list = field(default_factory=list)
@@ -55,6 +57,17 @@ class Request:
     footprint: int = 0
 
 
+def plan_choice(n: int, b: int, kind: int, method: int) -> tuple[int, int]:
+    """The method a request's plan gets and the device bytes it needs: the
+    server's method, or AUTO where the NTT path cannot take the size."""
+    try:
+        return method, hmv.plan_bytes(n, b, kind=kind, method=method)
+    except hmv.HmvError as err:
+        if method == hmv.AUTO or err.status != hmv.EUNSUPPORTED:
+            raise
+    return hmv.AUTO, hmv.plan_bytes(n, b, kind=kind)
+
+
 def percentile(values, q):
     if not values:
         return None
@@ -62,14 +75,21 @@ def percentile(values, q):
 
 
 class Server:
-    def __init__(self, memory_budget: int, max_active: int = 128, device: int = 0, clock=time.perf_counter):
+    """method: hmv.AUTO (the tensor-core Karatsuba path) or hmv.NTT (the exact
+    NTT path; a request whose size it cannot take gets AUTO)."""
+
+    def __init__(self, memory_budget: int, max_active: int = 128, device: int = 0, clock=time.perf_counter,
+                 method: int = hmv.AUTO):
         import torch
+        if method not in (hmv.AUTO, hmv.NTT):
+            raise ValueError("the server runs the tensor-core path (AUTO) or the exact NTT path (NTT)")
         self.torch = torch
         self.dev = torch.device("cuda", device)
         self.stream = torch.cuda.Stream(device=self.dev)
         self.budget = memory_budget
         self.max_active = max_active
         self.clock = clock
+        self.method = method
 
     def _admit(self, r: Request, now: float):
         # runs on the admission thread: the plan's kernels go to the server
@@ -77,7 +97,7 @@ class Server:
         # synchronised before the request can join a step
         torch = self.torch
         torch.cuda.set_device(self.dev)
-        r.plan = hmv.Plan(r.n, r.b, kind=r.kind, stream=self.stream.cuda_stream)
+        r.plan = hmv.Plan(r.n, r.b, kind=r.kind, method=r.method, stream=self.stream.cuda_stream)
         r.plan.load_matrix(r.h)
         r.done = 0
         r.admitted = now
@@ -107,7 +127,7 @@ class Server:
     def run(self, requests: list[Request]) -> dict:
         pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
         for r in pending:
-            r.footprint = hmv.plan_bytes(r.n, r.b, kind=r.kind)
+            r.method, r.footprint = plan_choice(r.n, r.b, r.kind, self.method)
             if r.footprint > self.budget:
                 raise ValueError(f"request {r.rid} needs {r.footprint} bytes, more than the whole budget")
         active: list[Request] = []

@@ -126,3 +126,15 @@ def test_leaf_stall_hook_checks_its_arguments(lib):
     assert lib.hmv_test_leaf_stall(1, 10) == 1            # below the 1 ms floor
     assert lib.hmv_test_leaf_stall(1, 3_000_000_000) == 1  # above the 2 s default
     assert lib.hmv_test_leaf_stall(0, 20_000_000) == 0     # disarmed
+
+
+def test_server_plan_choice_falls_back_beyond_the_ntt_size():
+    """A server on the NTT path gives a request the NTT plan where the
+    convolution fits 2^26 points, the tensor-core plan otherwise; footprints
+    from hmv_plan_bytes (no allocation)."""
+    from paper_1402_5287_gb300.serving import plan_choice
+    m, size = plan_choice(8000, 33220, hmv.HANKEL, hmv.NTT)
+    assert m == hmv.NTT and size == hmv.plan_bytes(8000, 33220, method=hmv.NTT)
+    m, size = plan_choice(9000, 33220, hmv.HANKEL, hmv.NTT)  # (2n-1)(2P-1) > 2^26
+    assert m == hmv.AUTO and size == hmv.plan_bytes(9000, 33220)
+    assert plan_choice(4096, 8192, hmv.TOEPLITZ, hmv.AUTO) == (hmv.AUTO, hmv.plan_bytes(4096, 8192, kind=hmv.TOEPLITZ))

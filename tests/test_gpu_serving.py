@@ -108,3 +108,55 @@ def test_served_lanczos_drivers_equal_solo_runs():
         if r.n <= 64:  # the oracle's recurrence on the smaller ones
             oa, ob, _ = ol.lanczos(r.h, r.x0, k)
             assert r.alphas == oa and r.betas == ob
+
+
+@pytest.mark.parametrize("ntt_every", [1, 2])
+def test_matvec_many_with_ntt_plans_equals_separate_products(ntt_every):
+    """NTT plans in a step: alone (ntt_every = 1: no leaf launch at all) or
+    mixed with tensor-core plans; bit-identical to separate products."""
+    torch = pytest.importorskip("torch")
+    probs = make(600)
+    stream = torch.cuda.Stream()
+    plans, xs, ys, want = [], [], [], []
+    for i, (n, b, kind, h, x) in enumerate(probs):
+        with hmv.Plan(n, b, kind=kind) as p1:
+            p1.load_matrix(h)
+            want.append(p1.matvec(x))
+        method = hmv.NTT if i % ntt_every == 0 else hmv.AUTO
+        p = hmv.Plan(n, b, kind=kind, method=method, stream=stream.cuda_stream)
+        p.load_matrix(h)
+        plans.append(p)
+        xs.append((torch.from_numpy(x.limbs.view(np.int32)).cuda(), torch.from_numpy(x.neg).cuda()))
+        ys.append((torch.zeros_like(xs[-1][0]), torch.zeros_like(xs[-1][1])))
+    torch.cuda.synchronize()
+    for _ in range(2):  # the step's buffers are reused by the next call
+        exps = hmv.matvec_many_device(plans, [(a.data_ptr(), b2.data_ptr()) for a, b2 in xs],
+                                      [(a.data_ptr(), b2.data_ptr()) for a, b2 in ys],
+                                      [x.exponent for *_, x in probs])
+        for (n, b, kind, h, x), (yl, yn), e, w in zip(probs, ys, exps, want):
+            assert_same(FixedVec(yl.cpu().numpy().view(np.uint32), yn.cpu().numpy(), b, e), w)
+    for p in plans:
+        p.close()
+
+
+def test_served_on_the_ntt_path_same_alone_and_in_the_mix():
+    """The server on the exact NTT path (Lanczos and chain requests, all at
+    once): the same results as the tensor-core path run alone."""
+    from paper_1402_5287_gb300.lanczos import Lanczos
+    from paper_1402_5287_gb300.serving import Request, Server
+    probs = make(700)
+    k = 3
+    reqs = [Request(i, n, b, h, x, k, arrival=0.0, kind=kind, lanczos=(kind == hmv.HANKEL and i % 2 == 0))
+            for i, (n, b, kind, h, x) in enumerate(probs)]
+    stats = Server(memory_budget=64 << 30, method=hmv.NTT).run(reqs)
+    assert stats["mean_step_batch"] > 1.0
+    for r, (n, b, kind, h, x) in zip(reqs, probs):
+        assert r.method == hmv.NTT
+        if r.lanczos:
+            with hmv.Plan(n, b, kind=kind) as p:
+                p.load_matrix(h)
+                solo = Lanczos(p, x)
+                a, bt = solo.run(k)
+            assert r.alphas == a and r.betas == bt
+        else:
+            assert_same(r.result, chain_alone(n, b, kind, h, x, k))
