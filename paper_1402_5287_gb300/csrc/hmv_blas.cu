@@ -7,7 +7,9 @@
 //
 // Both are schoolbook sums of 32-bit limb products in signed 128-bit column
 // sums (the same representation as the plain product kernel), normalised to
-// limbs by k_colsum_normalize.
+// limbs by k_colsum_normalize.  The inner product's products are
+// register-blocked over operands staged in shared memory; the linear
+// combination reads its scalars' limbs as broadcasts from the read-only cache.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -58,24 +60,119 @@ __device__ __forceinline__ void cols4(const uint32_t *__restrict__ cr, int nl, c
                  (static_cast<unsigned __int128>(s1[q]) << 32) | s0[q];
 }
 
+// Column sums of limb-string products on the CUDA cores.  A warp owns 128
+// consecutive columns w (4 a lane) and stages, in its own piece of shared
+// memory, the first operand A 1024 limbs at a time and the window of the
+// second operand B those columns meet (j = w - a), both zero-padded, so that
+// a lane reads four limbs with one 16-byte shared load and makes a
+// 4-column x 4-limb block of products per step, each added into a 96-bit
+// column sum (a row's sums stay below 2^(64 + 15), b <= 2^20).  Warps
+// synchronise only among their own lanes.
+constexpr int kBlasWarps = 4;                        // warps of a block (independent tasks)
+constexpr int kWarpCols = 128;                       // columns of one warp
+constexpr int kBlasTA = 1024;                        // limbs of A staged at a time
+constexpr int kBlasWin = kBlasTA + kWarpCols + 32;   // limbs of B's window
+struct BlasWarpSmem {
+    uint32_t A[kBlasTA + 4];
+    uint32_t B[kBlasWin];
+};
+static_assert((kBlasTA + 4) % 4 == 0 && kBlasWin % 4 == 0, "16-byte rows");
+// B'[j] sits at window index j + kBlasTA + 15 - c0 + a0: the index of
+// j = w0 - a - 3 is then a multiple of 4 for w0, c0, a, a0 multiples of 4.
+__device__ __forceinline__ int blas_win_off(int c0, int a0) { return kBlasTA + 15 - c0 + a0; }
+
+// A[a0, a0 + kBlasTA) (zeros from lenA) and the window of B' (B'[j] = B[j -
+// boff], zeros outside [boff, boff + lenB)) for the warp's columns from c0.
+__device__ __forceinline__ void blas_stage(BlasWarpSmem &sm, const uint32_t *__restrict__ A, int lenA,
+                                           const uint32_t *__restrict__ B, int lenB, int boff, int c0, int a0,
+                                           int lane) {
+    for (int e = lane; e < kBlasTA + 4; e += 32) {
+        const int a = a0 + e;
+        sm.A[e] = a < lenA ? A[a] : 0u;
+    }
+    const int jb = c0 - a0 - kBlasTA - 15 - boff;  // window entry e holds B[jb + e]
+    for (int e = lane; e < kBlasWin; e += 32) {
+        const int j = jb + e;
+        sm.B[e] = (j >= 0 && j < lenB) ? B[j] : 0u;
+    }
+}
+
+__device__ __forceinline__ uint4 lds4(const uint32_t *p) { return *reinterpret_cast<const uint4 *>(p); }
+
+// acc[q] += sum_{a = a_lo}^{a_hi + 3} A[a] B'[w0 + q - a], q < 4 (a_lo a
+// multiple of 4, a_hi <= a0 + kBlasTA - 1; products past the operands' ends
+// meet the zero padding).  Window: win[k] = B'[w0 - a - 3 + k].
+__device__ __forceinline__ void conv4x4(const uint32_t *A_s, const uint32_t *B_s, int w0, int c0, int a0, int a_lo,
+                                        int a_hi, uint32_t (&acc)[4][3]) {
+    int wb = w0 - a_lo - 3 + blas_win_off(c0, a0);
+    const uint4 l4 = lds4(B_s + wb), h4 = lds4(B_s + wb + 4);
+    uint32_t win[8] = {l4.x, l4.y, l4.z, l4.w, h4.x, h4.y, h4.z, h4.w};
+    for (int a = a_lo; a <= a_hi; a += 4) {
+        const uint4 av = lds4(A_s + (a - a0));
+        const uint32_t ar[4] = {av.x, av.y, av.z, av.w};
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) mac96(acc[q][0], acc[q][1], acc[q][2], ar[r], win[q - r + 3]);
+        wb -= 4;
+        const uint4 nw = lds4(B_s + wb);
+        win[7] = win[3];
+        win[6] = win[2];
+        win[5] = win[1];
+        win[4] = win[0];
+        win[0] = nw.x;
+        win[1] = nw.y;
+        win[2] = nw.z;
+        win[3] = nw.w;
+    }
+}
+// The warp's columns of one product A * B' (every staging of A it meets).
+__device__ __forceinline__ void warp_row_conv(BlasWarpSmem &sm, const uint32_t *__restrict__ A, int lenA,
+                                              const uint32_t *__restrict__ B, int lenB, int boff, int c0, int W,
+                                              int lane, uint32_t (&acc)[4][3]) {
+    const int w0 = c0 + 4 * lane;
+    const int LB = boff + lenB;
+    for (int a0 = 0; a0 < lenA; a0 += kBlasTA) {
+        if (a0 > c0 + kWarpCols - 1 || a0 + kBlasTA - 1 < c0 - (LB - 1)) continue;  // warp-uniform
+        __syncwarp();  // the previous products' reads are done
+        blas_stage(sm, A, lenA, B, lenB, boff, c0, a0, lane);
+        __syncwarp();
+        const int a_lo = max(a0, w0 - (LB - 1)) & ~3;
+        const int a_hi = min(min(a0 + kBlasTA, lenA) - 1, w0 + 3);
+        if (w0 < W && a_lo <= a_hi) conv4x4(sm.A, sm.B, w0, c0, a0, a_lo, a_hi, acc);
+    }
+}
+__device__ __forceinline__ void add_signed(__int128 (&tot)[4], const uint32_t (&acc)[4][3], bool neg) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const __int128 v = static_cast<__int128>((static_cast<unsigned __int128>(acc[q][2]) << 64) |
+                                                 (static_cast<unsigned __int128>(acc[q][1]) << 32) | acc[q][0]);
+        tot[q] += neg ? -v : v;
+    }
+}
+
 // partial[c][w] = sum over rows i of chunk c of s_i * sum_a X_i[a] Y_i[w - a]
-// (s_i = +-1 from the two signs), for limb columns w in [0, 2 L32); four
-// consecutive columns per thread.
-__global__ void k_dot_partial(const uint32_t *__restrict__ x, const uint8_t *__restrict__ xn,
-                              const uint32_t *__restrict__ y, const uint8_t *__restrict__ yn, int n, int L32,
-                              __int128 *__restrict__ partial) {
-    const int W = 2 * L32;
-    const int w0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int c = blockIdx.y;
-    if (w0 >= W) return;
+// (s_i = +-1 from the two signs), for limb columns w in [0, 2 L32): one warp
+// per (chunk, slice of 128 columns).
+__global__ void __launch_bounds__(32 * kBlasWarps) k_dot_partial(const uint32_t *__restrict__ x,
+                                                                  const uint8_t *__restrict__ xn,
+                                                                  const uint32_t *__restrict__ y,
+                                                                  const uint8_t *__restrict__ yn, int n, int L32,
+                                                                  int slices, int chunks,
+                                                                  __int128 *__restrict__ partial) {
+    __shared__ __align__(16) BlasWarpSmem sm[kBlasWarps];
+    const int warp = static_cast<int>(threadIdx.x >> 5), lane = static_cast<int>(threadIdx.x & 31);
+    const long long task = static_cast<long long>(blockIdx.x) * kBlasWarps + warp;
+    if (task >= static_cast<long long>(chunks) * slices) return;  // the whole warp; no block barrier follows
+    const int c = static_cast<int>(task / slices), c0 = static_cast<int>(task % slices) * kWarpCols;
+    const int W = 2 * L32, w0 = c0 + 4 * lane;
     const int i0 = c * kDotRows, i1 = min(n, i0 + kDotRows);
     __int128 tot[4] = {0, 0, 0, 0};
     for (int i = i0; i < i1; ++i) {
-        unsigned __int128 v[4];
-        cols4(x + static_cast<size_t>(i) * L32, L32, y + static_cast<size_t>(i) * L32, L32, w0, v);
-        const bool neg = xn[i] != yn[i];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) tot[q] += neg ? -static_cast<__int128>(v[q]) : static_cast<__int128>(v[q]);
+        uint32_t acc[4][3] = {};
+        warp_row_conv(sm[warp], x + static_cast<size_t>(i) * L32, L32, y + static_cast<size_t>(i) * L32, L32, 0, c0,
+                      W, lane, acc);
+        add_signed(tot, acc, xn[i] != yn[i]);
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q)
@@ -187,8 +284,10 @@ extern "C" hmv_status hmv_dot(hmv_plan_t *p, const hmv_vec *x, const hmv_vec *y,
         e = cudaMemsetAsync(st, 0, 8 * sizeof(int32_t), s);
     }
     if (e == cudaSuccess) {
-        k_dot_partial<<<dim3((W / 4 + 127) / 128 + 1, chunks), 128, 0, s>>>(x->limbs, x->neg, y->limbs, y->neg, n,
-                                                                           L32, partial);  // 4 columns per thread
+        const int slices = (W + kWarpCols - 1) / kWarpCols;
+        const long long tasks = static_cast<long long>(slices) * chunks;
+        k_dot_partial<<<static_cast<unsigned>((tasks + kBlasWarps - 1) / kBlasWarps), 32 * kBlasWarps, 0, s>>>(
+            x->limbs, x->neg, y->limbs, y->neg, n, L32, slices, chunks, partial);
         k_dot_reduce<<<(W + 31) / 32, dim3(32, 8), 0, s>>>(partial, chunks, W, cols);
         e = launch_colsum_normalize_cols(cols, 1, W, mag, zn, zb, ZW, st, s);
         p->launches_total += 3;
