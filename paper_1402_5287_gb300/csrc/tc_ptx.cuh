@@ -47,12 +47,26 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 }
 // Wait for the phase with the given parity to complete.  Gives up after
 // timeout_ns of wall time and returns false; never spins forever.
+// The waits count the time spent polling: the global timer's increments
+// between consecutive polls, each capped at kPollGapNs.  The timer keeps
+// running while a descheduled launch does not poll (a GPU time-sliced with
+// another context), and such a stretch counts as one capped gap, so it
+// cannot run a wait out by itself; every wait still ends, after at least
+// timeout_ns of polling.
+constexpr uint64_t kPollGapNs = 1000000;  // 1 ms: far above one poll
+__device__ __forceinline__ void poll_clock(uint64_t &last, uint64_t &waited) {
+    const uint64_t now = global_ns();
+    const uint64_t d = now - last;
+    waited += d < kPollGapNs ? d : kPollGapNs;
+    last = now;
+}
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t timeout_ns) {
     if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
+    uint64_t last = global_ns(), waited = 0;
     for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > timeout_ns) return false;
+        poll_clock(last, waited);
+        if (waited > timeout_ns) return false;
     }
 }
 // The same wait, which also gives up as soon as *abort is set (another role
@@ -60,10 +74,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t timeout_ns,
                                           const volatile int *abort) {
     if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
+    uint64_t last = global_ns(), waited = 0;
     for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (*abort || global_ns() - t0 > timeout_ns) return false;
+        poll_clock(last, waited);
+        if (*abort || waited > timeout_ns) return false;
     }
 }
 
