@@ -323,6 +323,7 @@ def run_ours(args):
         extras["exact_ntt"] = measure_ntt(hmv, h, x, n, b, stream, args.steps, args.warmup)
         extras["exact_ntt"]["vs_plain_kernel"] = extras["exact_ntt"]["value"] / plain["value"]
         extras["batched"] = measure_batched(3, 1, args.wave_gb)
+        extras["batched_exact_ntt"] = measure_batched(3, 1, args.wave_gb, "ntt")
         extras["serving"] = measure_serving(args.extra_requests, args.rate, args.matvecs_per_request,
                                             args.serve_gb, False)
         extras["serving_exact_ntt"] = measure_serving(args.extra_requests, args.rate, args.matvecs_per_request,
@@ -462,16 +463,19 @@ def load_workload(args):
     return n, b, uniform_vec(BASE_SEED + 2, 0, 2 * n - 1, b, 0), uniform_vec(BASE_SEED + 2, 1, n, b, 0)
 
 
-def measure_batched(steps, warmup, wave_gb):
+def measure_batched(steps, warmup, wave_gb, method="auto"):
     """Config 4: 64 matrices x 8 right-hand sides per hmv_batch_matvec call
-    (one CUDA graph launch), device-resident inputs; wall clock per call."""
+    (one CUDA graph launch), device-resident inputs; wall clock per call.
+    method: "auto" (the tensor-core Karatsuba path) or "ntt" (every member
+    on the exact NTT path)."""
     import torch
 
     from paper_1402_5287_gb300 import hmv
     from paper_1402_5287_gb300.inputs import batched_workload
     nrhs = 8
     probs = batched_workload(64, nrhs)
-    specs = [dict(n=n, b=b, nrhs=nrhs) for n, b, _, _ in probs]
+    mcode = {"auto": hmv.AUTO, "ntt": hmv.NTT}[method]
+    specs = [dict(n=n, b=b, nrhs=nrhs, method=mcode) for n, b, _, _ in probs]
     stream = torch.cuda.Stream()
     bt = hmv.Batch(specs, stream=stream.cuda_stream, wave_bytes=wave_gb << 30)
     for i, (_, _, h, _) in enumerate(probs):
@@ -499,6 +503,7 @@ def measure_batched(steps, warmup, wave_gb):
             "ms_per_step": secs / steps * 1e3,
             "workload": "64 Hankel matrices, n ~ U[32,2048], b in {4096,16384,33220}, 8 RHS each, "
                         "uniform fixed-point in (-1,1); one CUDA graph launch per step",
+            "method": "exact NTT path" if method == "ntt" else "tensor-core Karatsuba path",
             "waves": info["waves"], "pairs": info["pairs"], "leaf_tiles": info["leaf_tiles"],
             "kernels_per_graph": info["kernels_per_graph"], "wave_budget_gb": wave_gb,
             "device_gb": info["device_bytes"] / 1e9,
@@ -508,12 +513,12 @@ def measure_batched(steps, warmup, wave_gb):
 def run_batched(args):
     import paper_1402_5287_gb300 as pkg
     pkg.build()
-    r = measure_batched(args.steps, args.warmup, args.wave_gb)
+    r = measure_batched(args.steps, args.warmup, args.wave_gb, "ntt" if args.method == "ntt" else "auto")
     line = {"metric": "batched Hankel matvecs/s (64 matrices x 8 right-hand sides)", "value": r["value"],
             "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": r["warmup"],
             "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": {k: r[k] for k in ("workload", "waves", "pairs", "leaf_tiles", "kernels_per_graph",
+            "config": {k: r[k] for k in ("workload", "method", "waves", "pairs", "leaf_tiles", "kernels_per_graph",
                                          "wave_budget_gb", "device_gb")},
             "useful_leaf_tflops": r["useful_leaf_tflops"], "graph_launches_per_step": 1, "clocks": r["clocks"]}
     print(json.dumps(line), flush=True)

@@ -208,8 +208,8 @@ hmv_status hmv_reset_stats(hmv_plan_t *plan);
 /*
  * Batched products (block-Lanczos style workloads): `count` independent
  * Hankel/Toeplitz/circulant matrices, each with its own n, b, kind and
- * block of nrhs right-hand sides (descs[i]; method HMV_AUTO or
- * HMV_KARATSUBA, depth -1 for the cost model), advanced together.  Every
+ * block of nrhs right-hand sides (descs[i]; method HMV_AUTO, HMV_KARATSUBA
+ * or HMV_NTT, depth -1 for the cost model), advanced together.  Every
  * (matrix, right-hand side) pair is a leaf problem of Algorithm 1 (Sec. 3);
  * the leaf products of all pairs of a wave run in one persistent
  * tensor-core launch, and one hmv_batch_matvec call replays one captured
@@ -220,7 +220,9 @@ hmv_status hmv_reset_stats(hmv_plan_t *plan);
  * digit split) keep the buffers of a single plan, outside wave_bytes, and
  * run in one round per right-hand side: every such matrix's vector side,
  * one persistent launch over all their digit products per tile width, then
- * their interpolation.
+ * their interpolation.  HMV_NTT matrices (the exact NTT path; their size
+ * limit as for hmv_plan) keep their own buffers too and run their
+ * transforms for each right-hand side in the same graph.
  * stream: as for hmv_plan; NULL makes the batch create its own stream
  * (the legacy default stream cannot be captured).  Results are bit-identical
  * to hmv_matvec on each matrix alone.

@@ -18,7 +18,9 @@
 // buffers, outside the wave budget: they run in rounds, one per right-hand
 // side, each round the vector side of every such member, ONE persistent leaf
 // launch over all their digit products (per tile width), and the post-pass
-// with the interpolation of every member.
+// with the interpolation of every member.  Members on the exact NTT path
+// (method HMV_NTT) keep their own buffers too and run their transforms, one
+// right-hand side after another, in the same graph.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -68,6 +70,8 @@ struct hmv_batch_s {
     };
     std::vector<SplitLaunch> split_launches;
     hmv_plan_s *split_first = nullptr;  // status word and tile counter of the split launches
+    hmv_plan_s *wave_first = nullptr;   // the same for the waves' launches (a member run in waves)
+    std::vector<char> ntt;              // members on the exact NTT path (own buffers, no leaf products)
 };
 
 namespace hmv {
@@ -123,8 +127,8 @@ cudaError_t issue(hmv_batch_s *B) {
             kernels += 2 + p->L;
         }
         if (e == cudaSuccess)
-            e = launch_leaf_tc_multi(B->d_probs[w], B->d_tiles[w], B->ntiles[w], B->plans[0]->dstat,
-                                     B->plans[0]->d_counter, B->stream, B->num_sms, B->wave_tn[w]);
+            e = launch_leaf_tc_multi(B->d_probs[w], B->d_tiles[w], B->ntiles[w], B->wave_first->dstat,
+                                     B->wave_first->d_counter, B->stream, B->num_sms, B->wave_tn[w]);
         ++kernels;
         for (const Pair &pr : B->pairs) {
             if (pr.wave != w || e != cudaSuccess) continue;
@@ -134,6 +138,16 @@ cudaError_t issue(hmv_batch_s *B) {
             if (e == cudaSuccess) e = launch_final_normalize(p, p->post[0], pr.rhs, p->post16 ? 2 : 4);
             kernels += 1 + std::max(p->L, 1);
         }
+    }
+    // NTT members: transforms, pointwise product and extraction per right-hand side
+    for (size_t i = 0; i < B->plans.size() && e == cudaSuccess; ++i) {
+        hmv_plan_s *p = B->plans[i];
+        if (!B->ntt[i]) continue;
+        const int64_t before = p->launches_total;
+        for (int r = 0; r < p->nrhs && e == cudaSuccess; ++r)
+            e = ntt_vector_product(p, p->x_limbs_d + static_cast<size_t>(r) * p->n * p->L32,
+                                   p->x_neg_d + static_cast<size_t>(r) * p->n, r);
+        kernels += p->launches_total - before;
     }
     // split members: a round per right-hand side
     for (int r = 0; r < B->split_rounds && e == cudaSuccess; ++r) {
@@ -181,8 +195,8 @@ void hmv_batch_free(hmv_batch_t *B) {
     if (B->exec) cudaGraphExecDestroy(B->exec);
     for (size_t i = 0; i < B->plans.size(); ++i) {
         hmv_plan_s *p = B->plans[i];
-        if (i < B->split.size() && B->split[i]) {  // a split member owns all its buffers
-            hmv_free(p);
+        if ((i < B->split.size() && B->split[i]) || (i < B->ntt.size() && B->ntt[i])) {
+            hmv_free(p);  // a split or NTT member owns all its buffers
             continue;
         }
         // the batch owns the shared buffers these point to
@@ -204,7 +218,7 @@ hmv_status hmv_batch_create(int32_t count, const hmv_desc *descs, void *stream, 
     if (count < 1 || !descs || !out) return HMV_EINVAL;
     for (int i = 0; i < count; ++i) {
         const hmv_desc &d = descs[i];
-        if (d.method != HMV_AUTO && d.method != HMV_KARATSUBA) return HMV_EUNSUPPORTED;
+        if (d.method != HMV_AUTO && d.method != HMV_KARATSUBA && d.method != HMV_NTT) return HMV_EUNSUPPORTED;
         if (d.flags & HMV_FLAG_SIMT_LEAF) return HMV_EUNSUPPORTED;
     }
     hmv_batch_s *B = new (std::nothrow) hmv_batch_s();
@@ -229,6 +243,15 @@ hmv_status hmv_batch_create(int32_t count, const hmv_desc *descs, void *stream, 
     for (int i = 0; i < count; ++i) {
         hmv_desc d = descs[i];
         d.flags &= ~HMV_FLAG_TIMING;  // no host-side event syncs inside a graph
+        if (d.method == HMV_NTT) {
+            hmv_plan_s *p = nullptr;
+            const hmv_status st = plan_create(&d, B->stream, false, &p);
+            if (st != HMV_OK) { hmv_batch_free(B); return st; }
+            B->plans.push_back(p);
+            B->split.push_back(0);
+            B->ntt.push_back(1);
+            continue;
+        }
         // split the mantissas where a single HMV_AUTO plan would (or the flags ask)
         bool split = (d.flags & kSplitFlags) != 0;
         if (!split && d.method == HMV_AUTO && d.levels < 0) {
@@ -246,6 +269,7 @@ hmv_status hmv_batch_create(int32_t count, const hmv_desc *descs, void *stream, 
         if (st != HMV_OK) { hmv_batch_free(B); return st; }
         B->plans.push_back(p);
         B->split.push_back(split ? 1 : 0);
+        B->ntt.push_back(0);
         if (split) {
             B->split_rounds = std::max(B->split_rounds, p->nrhs);
             if (!B->split_first) B->split_first = p;
@@ -254,7 +278,7 @@ hmv_status hmv_batch_create(int32_t count, const hmv_desc *descs, void *stream, 
     cudaError_t e = cudaSuccess;
     size_t mA = 0, mX = 0, mP = 0;
     for (int i = 0; i < count; ++i) {
-        if (B->split[i]) continue;
+        if (B->split[i] || B->ntt[i]) continue;
         const hmv_plan_s *p = B->plans[i];
         mA = std::max(mA, p->bytes_a_lvl);
         mX = std::max(mX, p->bytes_x_lvl);
@@ -269,7 +293,7 @@ hmv_status hmv_batch_create(int32_t count, const hmv_desc *descs, void *stream, 
     // wave, so one width per wave), a new wave when the budget would be exceeded
     std::vector<size_t> wave_size;
     for (int i = 0; i < count; ++i) {
-        if (B->split[i]) continue;
+        if (B->split[i] || B->ntt[i]) continue;
         B->plans[i]->a_lvl[0] = B->a_lvl[0];
         B->plans[i]->a_lvl[1] = B->a_lvl[1];
     }
@@ -277,7 +301,7 @@ hmv_status hmv_batch_create(int32_t count, const hmv_desc *descs, void *stream, 
         bool fresh = true;
         for (int i = 0; i < count; ++i) {
             hmv_plan_s *p = B->plans[i];
-            if (B->split[i] || p->tn != tn) continue;
+            if (B->split[i] || B->ntt[i] || p->tn != tn) continue;
             for (int r = 0; r < p->nrhs; ++r) {
                 const size_t sz = pair_bytes(p);
                 if (fresh || (wave_size.back() + sz > wave_bytes && wave_size.back() > 0)) {
@@ -291,6 +315,7 @@ hmv_status hmv_batch_create(int32_t count, const hmv_desc *descs, void *stream, 
         }
     }
     B->nwaves = static_cast<int>(wave_size.size());
+    if (!B->pairs.empty()) B->wave_first = B->plans[B->pairs.front().plan];
     const size_t arena_bytes = wave_size.empty() ? 0 : *std::max_element(wave_size.begin(), wave_size.end());
     uint8_t *arena = nullptr;
     if (e == cudaSuccess) e = balloc(B, reinterpret_cast<void **>(&arena), arena_bytes);

@@ -310,12 +310,14 @@ class Batch:
     CUDA graph launch per call (hmv_batch_*)."""
 
     def __init__(self, problems, stream=None, wave_bytes: int = 32 << 30):
-        """problems: list of dicts with n, b and optionally kind, nrhs, levels, flags."""
+        """problems: list of dicts with n, b and optionally kind, nrhs, levels,
+        flags and method (AUTO, KARATSUBA or NTT)."""
         self.lib = load_library()
-        self.problems = [{"kind": HANKEL, "nrhs": 1, "levels": -1, "flags": 0, **pr} for pr in problems]
+        self.problems = [{"kind": HANKEL, "nrhs": 1, "levels": -1, "flags": 0, "method": AUTO, **pr}
+                         for pr in problems]
         arr = (Desc * len(problems))()
         for i, pr in enumerate(self.problems):
-            arr[i] = Desc(pr["n"], pr["b"], pr["nrhs"], pr["kind"], AUTO, pr["levels"], pr["flags"], 0)
+            arr[i] = Desc(pr["n"], pr["b"], pr["nrhs"], pr["kind"], pr["method"], pr["levels"], pr["flags"], 0)
         handle = ctypes.c_void_p()
         s = ctypes.c_void_p(0 if stream is None else int(stream))
         _check(self.lib.hmv_batch_create(len(problems), arr, s, wave_bytes, ctypes.byref(handle)), "hmv_batch_create")

@@ -143,11 +143,13 @@ def test_batch_with_digit_split_members():
     assert_same(y, FixedVec(yl, yn, pr["b"], e))
 
 
-def test_batched_workload_at_its_own_shape_sampled_rows():
+@pytest.mark.parametrize("method", [hmv.AUTO, hmv.NTT])
+def test_batched_workload_at_its_own_shape_sampled_rows(method):
     """The batched workload itself (64 matrices, n ~ U[32, 2048], b from
-    {4096, 16384, 33220}, 8 right-hand sides each, one graph launch): for
-    every matrix, 8 seeded (right-hand side, row) pairs plus the row with the
-    largest output mantissa of the block against the oracle, bit for bit,
+    {4096, 16384, 33220}, 8 right-hand sides each, one graph launch; every
+    member on the tensor-core path, or every member on the exact NTT path):
+    for every matrix, 8 seeded (right-hand side, row) pairs plus the row with
+    the largest output mantissa of the block against the oracle, bit for bit,
     and the block's shared exponent from those rows."""
     import random
 
@@ -155,7 +157,7 @@ def test_batched_workload_at_its_own_shape_sampled_rows():
     from test_gpu_parity import THREADS
     nrhs = 8
     probs = batched_workload(64, nrhs)
-    bt = hmv.Batch([dict(n=n, b=b, nrhs=nrhs) for n, b, _, _ in probs], wave_bytes=48 << 30)
+    bt = hmv.Batch([dict(n=n, b=b, nrhs=nrhs, method=method) for n, b, _, _ in probs], wave_bytes=48 << 30)
     try:
         for i, (_, _, h, _) in enumerate(probs):
             bt.load_matrix(i, h)
@@ -179,3 +181,27 @@ def test_batched_workload_at_its_own_shape_sampled_rows():
             assert np.array_equal(yl, y.limbs[got]) and np.array_equal(yn, y.neg[got]), (n, b, r, rows)
             if top in got:  # the least exponent is decided by the largest row
                 assert oracle.round_rows(z, zn, b, h.exponent + x.exponent)[2] == y.exponent
+
+
+@pytest.mark.parametrize("ntt_members", [(0, 2), (0, 1, 2, 3, 4)])
+def test_batch_with_ntt_members(ntt_members):
+    """Members on the exact NTT path beside members run in waves (or all of
+    them, with no leaf launch at all): each block equals its single-plan
+    product bit for bit, over two replays of the graph."""
+    hs, xs = inputs(970)
+    # an NTT plan has no Karatsuba depth to choose
+    specs = [dict({k: v for k, v in pr.items() if k != "levels"}, method=hmv.NTT) if i in ntt_members else pr
+             for i, pr in enumerate(PROBLEMS)]
+    with hmv.Batch(specs) as bt:
+        for i, h in enumerate(hs):
+            bt.load_matrix(i, h)
+        ys = bt.matvec(xs)
+        _, xs2 = inputs(971)
+        ys2 = bt.matvec(xs2)
+        info = bt.info()
+    assert info["graph_launches"] == 2
+    if len(ntt_members) == len(PROBLEMS):
+        assert info["waves"] == 0 and info["leaf_tiles"] == 0
+    for pr, h, x, y, x2, y2 in zip(PROBLEMS, hs, xs, ys, xs2, ys2):
+        assert_same(y, single(pr, h, x))
+        assert_same(y2, single(pr, h, x2))
