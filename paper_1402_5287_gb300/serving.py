@@ -9,14 +9,17 @@ Lanczos run is the client's.  The server
 
   * admits arrived requests in order while the device memory its plans need
     (hmv_plan_bytes, computed without allocating) fits the budget; a request's
-    plan is created and its matrix loaded on a worker thread while the
-    current step runs, and it joins the first step that starts after that,
+    plan is created and its matrix loaded on a worker thread, on a CUDA stream
+    of the request's own (so the load does not queue behind the running
+    step), and it joins the first step that starts after that,
   * keeps every admitted matrix resident (one plan per request),
   * runs steps: each step advances EVERY active request by one product with
     one hmv_matvec_many call, whose leaf products share one persistent
     tensor-core launch (requests on the exact NTT path run their transforms
     in the same call); requests that arrive during a step join at the next
-    one, finished requests leave and free their memory (continuous batching),
+    one, finished requests leave (continuous batching) and their plans are
+    released on the worker thread, before any admission that follows, so
+    that the loop does not wait for the device memory to be freed,
   * records, per product, the time from when it became ready (arrival for
     the first, the previous product's completion otherwise) to completion.
 
@@ -85,44 +88,54 @@ class Server:
             raise ValueError("the server runs the tensor-core path (AUTO) or the exact NTT path (NTT)")
         self.torch = torch
         self.dev = torch.device("cuda", device)
-        self.stream = torch.cuda.Stream(device=self.dev)
         self.budget = memory_budget
         self.max_active = max_active
         self.clock = clock
         self.method = method
 
     def _admit(self, r: Request, now: float):
-        # runs on the admission thread: the plan's kernels go to the server
-        # stream, the vectors' copies to this thread's stream, which is
-        # synchronised before the request can join a step
+        # runs on the admission thread: the plan's load and the vectors'
+        # copies go to the request's own stream, synchronised before the
+        # request can join a step (a step then runs every active plan on its
+        # lead plan's stream and synchronises it)
         torch = self.torch
         torch.cuda.set_device(self.dev)
-        r.plan = hmv.Plan(r.n, r.b, kind=r.kind, method=r.method, stream=self.stream.cuda_stream)
-        r.plan.load_matrix(r.h)
-        r.done = 0
-        r.admitted = now
-        if r.lanczos:
-            from .lanczos import Lanczos
-            r.lz = Lanczos(r.plan, r.x0, device=self.dev)
-        else:
-            r.xl = torch.from_numpy(r.x0.limbs.view(np.int32)).to(self.dev)
-            r.xn = torch.from_numpy(r.x0.neg).to(self.dev)
-            r.yl = torch.empty_like(r.xl)
-            r.yn = torch.empty_like(r.xn)
-            r.x_exp = r.x0.exponent
-        torch.cuda.current_stream(self.dev).synchronize()
+        r.stream = torch.cuda.Stream(device=self.dev)
+        with torch.cuda.stream(r.stream):
+            r.plan = hmv.Plan(r.n, r.b, kind=r.kind, method=r.method, stream=r.stream.cuda_stream)
+            r.plan.load_matrix(r.h)
+            r.done = 0
+            r.admitted = now
+            if r.lanczos:
+                from .lanczos import Lanczos
+                r.lz = Lanczos(r.plan, r.x0, device=self.dev)
+            else:
+                r.xl = torch.from_numpy(r.x0.limbs.view(np.int32)).to(self.dev)
+                r.xn = torch.from_numpy(r.x0.neg).to(self.dev)
+                r.yl = torch.empty_like(r.xl)
+                r.yn = torch.empty_like(r.xn)
+                r.x_exp = r.x0.exponent
+        r.stream.synchronize()
 
-    def _finish(self, r: Request, now: float):
-        self.stream.synchronize()
+    def _finish(self, r: Request, now: float, pool):
+        r.stream.synchronize()  # the request's last vector work (a step ends with its stream synchronised)
         if r.lanczos:
             r.result = r.lz.vector()
-            del r.lz
         else:
             r.result = FixedVec(r.xl.cpu().numpy().view(np.uint32), r.xn.cpu().numpy(), r.b, r.x_exp)
+        r.finished = now
+        r.retired = pool.submit(self._retire, r)
+
+    def _retire(self, r: Request):
+        # on the worker thread, in order with the admissions (the memory it
+        # frees is counted free from now on)
+        if r.lanczos:
+            del r.lz
+        else:
             del r.xl, r.xn, r.yl, r.yn
         r.plan.close()
         r.plan = None
-        r.finished = now
+        r.stream = None
 
     def run(self, requests: list[Request]) -> dict:
         pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
@@ -191,13 +204,15 @@ class Server:
                     r.x_exp = e
                 r.done += 1
                 if r.done == r.matvecs or (r.lanczos and r.betas[-1][0] == 0):
-                    self._finish(r, t_end)
+                    self._finish(r, t_end, pool)
                     used -= r.footprint
                 else:
                     still.append(r)
             active = still
         total = self.clock() - t0
         pool.shutdown(wait=True)
+        for r in requests:
+            r.retired.result()  # a release's error ends the run here
         lat = [v for r in requests for v in r.latencies]
         req_lat = [r.finished - r.arrival for r in requests]
         nmv = sum(r.done for r in requests)  # a Lanczos run that breaks down stops early
