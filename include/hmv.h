@@ -180,8 +180,16 @@ hmv_status hmv_load_matrix(hmv_plan_t *plan, const hmv_vec *h);
  * exponent has been read back (one stream synchronisation). */
 hmv_status hmv_matvec(hmv_plan_t *plan, const hmv_vec *x, hmv_vec *y);
 
-/* Release everything the plan holds.  NULL is ignored. */
+/* Release everything the plan holds.  NULL is ignored.  The plan's stream
+ * must still exist; the call waits for the plan's work on it.  The device
+ * memory goes back to the library's memory pool (kept for the next plan,
+ * without a device-wide synchronisation); hmv_trim_memory returns it to the
+ * device. */
 void hmv_free(hmv_plan_t *plan);
+
+/* Return the current device's unused pooled memory (freed plans' memory the
+ * library keeps for reuse) to the device.  Synchronises the device first. */
+hmv_status hmv_trim_memory(void);
 
 /* Device memory hmv_plan would allocate for this descriptor, computed
  * without allocating (admission control by memory footprint). */

@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "hmv_internal.h"
@@ -213,9 +214,12 @@ cudaError_t dalloc(hmv_plan_s *p, T **ptr, size_t count) {
         return cudaSuccess;
     }
     void *v = nullptr;
-    cudaError_t e = cudaMalloc(&v, count * sizeof(T));
+    cudaError_t e = pool_alloc(&v, count * sizeof(T), p->stream);
     if (e != cudaSuccess) return e;
     p->allocations.push_back(v);
+    // usable from every stream and by synchronous copies at once, as cudaMalloc's
+    e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return e;
     p->device_bytes += static_cast<int64_t>(count * sizeof(T));
     *ptr = static_cast<T *>(v);
     return cudaSuccess;
@@ -293,15 +297,20 @@ int32_t hmv_version(void) { return 100; }
 
 void hmv_free(hmv_plan_t *p) {
     if (!p) return;
-    if (p->stream) cudaStreamSynchronize(p->stream);
+    cudaStreamSynchronize(p->stream);  // the plan's work is done: its memory goes back to the pool at once
     for (hmv_plan_s *c : p->children) hmv_free(c);
-    for (void *a : p->allocations) cudaFree(a);
-    for (hmv::GrowBuf *g : {&p->dot_buf, &p->lin_buf, &p->many_dev, &p->many_host}) hmv::release(*g);
-    for (auto &g : p->lv)
-        if (g.d_size) cudaFree(g.d_size);
+    for (void *a : p->allocations) hmv::pool_free(a, p->stream);
+    for (hmv::GrowBuf *g : {&p->dot_buf, &p->lin_buf}) hmv::release(*g, p->stream);
     if (p->timing)
         for (auto &e : p->ev) cudaEventDestroy(e);
     delete p;
+}
+
+hmv_status hmv_trim_memory(void) {
+    cudaMemPool_t pool = nullptr;
+    if (hmv::library_pool(&pool) != cudaSuccess) return HMV_ECUDA;
+    cudaDeviceSynchronize();  // frees still pending in some stream's order complete first
+    return cudaMemPoolTrimTo(pool, 0) == cudaSuccess ? HMV_OK : HMV_ECUDA;
 }
 
 hmv_status hmv_plan(const hmv_desc *desc, void *stream, hmv_plan_t **out) {
@@ -322,12 +331,59 @@ hmv_status hmv_plan_bytes(const hmv_desc *desc, uint64_t *bytes) {
 
 namespace hmv {
 
-cudaError_t grow(GrowBuf &g, size_t bytes) {
+// The current device's pool: created on first use, with a release threshold
+// of all its memory (freed memory stays reserved for the next allocation).
+cudaError_t library_pool(cudaMemPool_t *out) {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof props);
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = UINT64_MAX;
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        int no = 0;  // reuse only memory whose free has completed: no hidden cross-stream dependencies
+        if (e == cudaSuccess) e = cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return e;
+        }
+        pools[dev] = pool;
+    }
+    *out = pools[dev];
+    return cudaSuccess;
+}
+
+cudaError_t pool_alloc(void **ptr, size_t bytes, cudaStream_t s) {
+    *ptr = nullptr;
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = library_pool(&pool);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(ptr, bytes ? bytes : 1, pool, s);
+    if (e != cudaSuccess) *ptr = nullptr;
+    return e;
+}
+
+void pool_free(void *ptr, cudaStream_t s) {
+    if (ptr) cudaFreeAsync(ptr, s);
+}
+
+cudaError_t grow(GrowBuf &g, size_t bytes, cudaStream_t s) {
     if (bytes <= g.bytes) return cudaSuccess;
-    if (g.ptr) cudaDeviceSynchronize();  // work queued earlier may still use the old buffer
-    release(g);
+    // the calls that used the old buffer ended with a synchronisation of s
+    release(g, s);
     const size_t want = bytes + bytes / 4;  // some room, so that slowly growing calls do not reallocate each time
-    cudaError_t e = g.pinned ? cudaMallocHost(&g.ptr, want) : cudaMalloc(&g.ptr, want);
+    cudaError_t e = g.pinned ? cudaMallocHost(&g.ptr, want) : pool_alloc(&g.ptr, want, s);
     if (e != cudaSuccess) {
         g.ptr = nullptr;
         return e;
@@ -336,10 +392,10 @@ cudaError_t grow(GrowBuf &g, size_t bytes) {
     return cudaSuccess;
 }
 
-void release(GrowBuf &g) {
+void release(GrowBuf &g, cudaStream_t s) {
     if (g.ptr) {
         if (g.pinned) cudaFreeHost(g.ptr);
-        else cudaFree(g.ptr);
+        else pool_free(g.ptr, s);
     }
     g.ptr = nullptr;
     g.bytes = 0;
@@ -509,8 +565,9 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
         }
         for (auto &lg : p->lv) {
             if (dry_run) { p->device_bytes += static_cast<int64_t>(lg.size.size() * sizeof(int)); continue; }
-            if (g(cudaMalloc(&lg.d_size, lg.size.size() * sizeof(int))))
-                g(cudaMemcpy(lg.d_size, lg.size.data(), lg.size.size() * sizeof(int), cudaMemcpyHostToDevice));
+            if (g(dalloc(p, &lg.d_size, lg.size.size())))
+                g(cudaMemcpyAsync(lg.d_size, lg.size.data(), lg.size.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                  p->stream));
         }
         const bool simt = (d.flags & HMV_FLAG_SIMT_LEAF) != 0;
         p->bytes_a_lvl = maxA;
@@ -600,6 +657,14 @@ hmv_status plan_create(const hmv_desc *desc, void *stream, bool external_scratch
         return st;
     }
     if (!p->children.empty()) share_status(p, p->dstat);
+    // the pool's allocations (and the copies above) are complete: every
+    // stream may use the plan's memory from now on
+    if (!dry_run && !g(cudaStreamSynchronize(p->stream))) {
+        hmv_status st = from_cuda(g.err);
+        hmv_free(p);
+        cudaGetLastError();
+        return st;
+    }
     *out = p;
     return HMV_OK;
 }

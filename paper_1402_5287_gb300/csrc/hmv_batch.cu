@@ -23,6 +23,7 @@
 // right-hand side after another, in the same graph.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "hmv_internal.h"
@@ -500,6 +501,23 @@ hmv_status hmv_batch_get_info(const hmv_batch_t *B, hmv_batch_info *o) {
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+namespace hmv {
+namespace {
+// hmv_matvec_many's staging of a step's problem and tile lists, per device.
+struct ManyStaging {
+    std::mutex mu;
+    GrowBuf dev;
+    GrowBuf host{nullptr, 0, true};
+};
+ManyStaging &many_staging() {
+    static ManyStaging st[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    return st[dev];
+}
+}  // namespace
+}  // namespace hmv
+
 // One matvec for each of several independent plans, with every leaf product
 // in one persistent tensor-core launch: the step of a continuous-batching
 // server, whose set of plans changes from one call to the next.  Plans of
@@ -561,9 +579,8 @@ extern "C" hmv_status hmv_matvec_many(int32_t count, hmv_plan_t *const *plans, c
         if (plans[i]->method == HMV_KARATSUBA) collect_leaf_plans(plans[i], leafplans);
     // one persistent launch per tile width present (normally one); the
     // step's problem and tile lists are staged in pinned host memory and
-    // copied into device memory, both kept by the first Karatsuba plan and grown on demand
-    // (the previous call ended with a stream synchronisation, so neither is
-    // still in use)
+    // copied into device memory, both the library's (per device, grown on
+    // demand, held by this call until its last synchronisation)
     std::vector<LeafProblem> gp[2];
     std::vector<Tile> gt[2];
     size_t off_p[2], off_t[2], total = 0;
@@ -584,22 +601,24 @@ extern "C" hmv_status hmv_matvec_many(int32_t count, hmv_plan_t *const *plans, c
         off_t[w] = total;
         total += al(gt[w].size() * sizeof(Tile));
     }
-    hmv_plan_s *lead = nullptr;  // the leaf launch's buffers, tile counter and status word: a Karatsuba plan's
+    hmv_plan_s *lead = nullptr;  // the leaf launch's tile counter and status word: a Karatsuba plan's
     for (int i = 0; i < count && !lead; ++i)
         if (plans[i]->method == HMV_KARATSUBA) lead = plans[i];
-    if (e == cudaSuccess && total > 0) e = grow(lead->many_dev, total);
-    if (e == cudaSuccess && total > 0) e = grow(lead->many_host, total);
+    ManyStaging &ms = many_staging();
+    std::unique_lock<std::mutex> staging_lock(ms.mu);
+    if (e == cudaSuccess && total > 0) e = grow(ms.dev, total, s);
+    if (e == cudaSuccess && total > 0) e = grow(ms.host, total, s);
     if (e == cudaSuccess && total > 0) {
-        char *hb = static_cast<char *>(lead->many_host.ptr);
+        char *hb = static_cast<char *>(ms.host.ptr);
         for (int w = 0; w < 2; ++w) {
             memcpy(hb + off_p[w], gp[w].data(), gp[w].size() * sizeof(LeafProblem));
             memcpy(hb + off_t[w], gt[w].data(), gt[w].size() * sizeof(Tile));
         }
-        e = cudaMemcpyAsync(lead->many_dev.ptr, hb, total, cudaMemcpyHostToDevice, s);
+        e = cudaMemcpyAsync(ms.dev.ptr, hb, total, cudaMemcpyHostToDevice, s);
     }
     for (int w = 0; w < 2 && e == cudaSuccess; ++w) {
         if (gt[w].empty()) continue;
-        char *db = static_cast<char *>(lead->many_dev.ptr);
+        char *db = static_cast<char *>(ms.dev.ptr);
         e = launch_leaf_tc_multi(reinterpret_cast<LeafProblem *>(db + off_p[w]), reinterpret_cast<Tile *>(db + off_t[w]),
                                  static_cast<int>(gt[w].size()), lead->dstat, lead->d_counter, s, lead->num_sms,
                                  w == 0 ? 256 : 128);

@@ -272,7 +272,7 @@ extern "C" hmv_status hmv_dot(hmv_plan_t *p, const hmv_vec *x, const hmv_vec *y,
     size.take<uint8_t>(nullptr, 16);
     size.take<int32_t>(nullptr, 4);
     size.take<int32_t>(nullptr, 8);
-    cudaError_t e = grow(p->dot_buf, size.off);
+    cudaError_t e = grow(p->dot_buf, size.off, p->stream);
     if (e == cudaSuccess) {
         Carve c;
         partial = c.take<__int128>(p->dot_buf.ptr, static_cast<size_t>(chunks) * W);
@@ -358,7 +358,7 @@ extern "C" hmv_status hmv_lincomb(hmv_plan_t *p, int32_t count, const hmv_scalar
     size.take<uint8_t>(nullptr, n);
     size.take<int32_t>(nullptr, n);
     size.take<int32_t>(nullptr, 8);
-    cudaError_t e = grow(p->lin_buf, size.off);
+    cudaError_t e = grow(p->lin_buf, size.off, p->stream);
     if (e == cudaSuccess) {
         Carve c;
         dc = c.take<uint32_t>(p->lin_buf.ptr, total);

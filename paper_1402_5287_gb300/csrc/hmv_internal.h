@@ -32,8 +32,17 @@ struct GrowBuf {
     size_t bytes = 0;
     bool pinned = false;  // host memory from cudaMallocHost instead of device memory
 };
-cudaError_t grow(GrowBuf &g, size_t bytes);
-void release(GrowBuf &g);
+// Device buffers come from the library's memory pool in the order of stream
+// s (see pool_alloc); the previous contents are not kept.
+cudaError_t grow(GrowBuf &g, size_t bytes, cudaStream_t s);
+void release(GrowBuf &g, cudaStream_t s);
+// The library's device memory pool (one per device): allocations in stream
+// order that keep freed memory for the next plan instead of returning it to
+// the device, so that creating and freeing plans neither maps memory nor
+// synchronises the device each time; hmv_trim_memory hands it back.
+cudaError_t library_pool(cudaMemPool_t *out);
+cudaError_t pool_alloc(void **ptr, size_t bytes, cudaStream_t s);
+void pool_free(void *ptr, cudaStream_t s);
 }  // namespace hmv
 
 struct hmv_plan_s {
@@ -105,10 +114,9 @@ struct hmv_plan_s {
     size_t bytes_a_lvl = 0, bytes_x_lvl = 0, bytes_post = 0, elems_xg = 0, bytes_dig = 0, elems_carry = 0;
     int num_sms = 0;
     int64_t device_bytes = 0;
-    std::vector<void *> allocations;
-    // per-call working memory, grown on demand (hmv_dot, hmv_lincomb, and the
-    // problem and tile lists of an hmv_matvec_many step led by this plan)
-    hmv::GrowBuf dot_buf, lin_buf, many_dev, many_host{nullptr, 0, true};
+    std::vector<void *> allocations;         // device memory from the library's pool (pool_free at hmv_free)
+    // per-call working memory of hmv_dot and hmv_lincomb, grown on demand
+    hmv::GrowBuf dot_buf, lin_buf;
 
     // exact NTT path (two primes): geometry, the matrix spectrum / N, the
     // vector's work array, twiddle tables

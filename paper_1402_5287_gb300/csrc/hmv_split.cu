@@ -748,15 +748,22 @@ cudaError_t split_leaf_launch(hmv_plan_s *p) {
                 tiles.push_back(t);
             }
         }
-        e = cudaMalloc(reinterpret_cast<void **>(&p->split_probs), probs.size() * sizeof(LeafProblem));
-        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&p->split_tiles), tiles.size() * sizeof(Tile));
-        if (e == cudaSuccess) {
-            p->allocations.push_back(p->split_probs);
-            p->allocations.push_back(p->split_tiles);
-            e = cudaMemcpy(p->split_probs, probs.data(), probs.size() * sizeof(LeafProblem), cudaMemcpyHostToDevice);
-        }
+        // from the library's pool in the plan's stream order; the host lists
+        // live until the stream has copied them
+        void *dp = nullptr, *dt = nullptr;
+        e = pool_alloc(&dp, probs.size() * sizeof(LeafProblem), p->stream);
+        if (e == cudaSuccess) p->allocations.push_back(dp);
+        if (e == cudaSuccess) e = pool_alloc(&dt, tiles.size() * sizeof(Tile), p->stream);
+        if (e == cudaSuccess) p->allocations.push_back(dt);
         if (e == cudaSuccess)
-            e = cudaMemcpy(p->split_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice);
+            e = cudaMemcpyAsync(dp, probs.data(), probs.size() * sizeof(LeafProblem), cudaMemcpyHostToDevice, p->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dt, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice, p->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+        if (e == cudaSuccess) {
+            p->split_probs = static_cast<LeafProblem *>(dp);
+            p->split_tiles = static_cast<Tile *>(dt);
+        }
         p->ntiles = static_cast<int>(tiles.size());
     }
     if (e == cudaSuccess) {

@@ -117,6 +117,8 @@ def load_library(path: str = LIB_PATH):
         lib.hmv_plan_bytes.restype = ctypes.c_int
         lib.hmv_measure_montgomery_rate.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
         lib.hmv_measure_montgomery_rate.restype = ctypes.c_int
+        lib.hmv_trim_memory.argtypes = []
+        lib.hmv_trim_memory.restype = ctypes.c_int
         lib.hmv_test_leaf_stall.argtypes = [i32, ctypes.c_int64]
         lib.hmv_test_leaf_stall.restype = ctypes.c_int
         lib.hmv_matvec_many.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(Vec), ctypes.POINTER(Vec)]
@@ -164,6 +166,11 @@ def measure_montgomery_rate(stream=None) -> float:
     _check(load_library().hmv_measure_montgomery_rate(ctypes.c_void_p(0 if stream is None else int(stream)),
                                                       ctypes.byref(r)), "hmv_measure_montgomery_rate")
     return r.value
+
+
+def trim_memory() -> None:
+    """hmv_trim_memory: hand the library's unused pooled device memory back."""
+    _check(load_library().hmv_trim_memory(), "hmv_trim_memory")
 
 
 def arm_leaf_stall(launches: int, wait_ns: int = 20_000_000) -> None:
