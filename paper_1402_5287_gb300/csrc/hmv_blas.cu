@@ -10,6 +10,9 @@
 // limbs by k_colsum_normalize.  The inner product's products are
 // register-blocked over operands staged in shared memory; the linear
 // combination reads its scalars' limbs as broadcasts from the read-only cache.
+#include <cublas_v2.h>
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -179,6 +182,85 @@ __global__ void __launch_bounds__(32 * kBlasWarps) k_dot_partial(const uint32_t 
         if (w0 + q < W) partial[static_cast<size_t>(c) * W + w0 + q] = tot[q];
 }
 
+// The inner product as one dense product on the tensor cores, for large
+// n and b: every entry is cut into D >= ceil(32 L32 / 6) digits of 6 bits
+// carrying its sign (|d| <= 63, exact in bf16), X and Y as n x D digit
+// matrices, and C = X^T Y (D x D, C[s][t] = sum_i X_i[s] Y_i[t]) by cuBLAS in
+// chunks of 4096 rows, so that every fp32 partial sum is an integer below
+// 4096 * 63^2 < 2^24 and exact in any order (7-bit digits allow chunks of
+// 1024 rows only: at n = 8000, b = 33220 eight GEMMs and eight D x D outputs
+// instead of two, 1.00 against 0.75 ms).  The product's digit column u
+// is the sum of C along the anti-diagonal s + t = u (int64), which becomes
+// the 128-bit limb column sums of the schoolbook kernels.
+constexpr int kDig = 6;               // bits of a digit
+constexpr int kGemmRows = 4096;       // rows of one exact fp32 GEMM chunk
+constexpr int kGemmMaxDigits = 8192;  // larger D: the CUDA-core kernel (C would pass 256 MB)
+constexpr int kDigMax = (1 << kDig) - 1;
+static_assert(static_cast<long long>(kGemmRows) * kDigMax * kDigMax < (1LL << 24), "exact fp32 chunk sums");
+
+__global__ void k_digits7(const uint32_t *__restrict__ limbs, const uint8_t *__restrict__ neg, int n, int L32, int D,
+                          __nv_bfloat16 *__restrict__ out) {
+    const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= static_cast<long long>(n) * D) return;
+    const int i = static_cast<int>(idx / D), s = static_cast<int>(idx - static_cast<long long>(i) * D);
+    const int bit = kDig * s, w = bit >> 5, r = bit & 31;
+    int d = 0;  // the padding digits past the entry's 32 L32 bits are 0
+    if (w < L32) {
+        const uint32_t *row = limbs + static_cast<size_t>(i) * L32;
+        uint64_t v = row[w];
+        if (w + 1 < L32) v |= static_cast<uint64_t>(row[w + 1]) << 32;
+        d = static_cast<int>((v >> r) & static_cast<uint64_t>(kDigMax));
+    }
+    out[idx] = __int2bfloat16_rn(neg[i] ? -d : d);
+}
+
+// z[u] += sum over a 32 x 32 tile of C (column-major, D x D, fp32 holding
+// integers below 2^24) of the entries with s + t = u: the tile is written
+// skewed into shared memory (entry (s, t) in row s + t, padded rows of 33:
+// both passes conflict-free), one thread sums a row (32 entries: below 2^29,
+// int32), one global 64-bit atomic per anti-diagonal of the tile.
+__global__ void __launch_bounds__(256) k_antidiag(const float *__restrict__ C, int D, unsigned long long *__restrict__ z) {
+    __shared__ int32_t sk[63 * 33];
+    const int s0 = static_cast<int>(blockIdx.x) * 32, t0 = static_cast<int>(blockIdx.y) * 32;
+    const int tx = static_cast<int>(threadIdx.x & 31), ty = static_cast<int>(threadIdx.x >> 5);
+    for (int e = threadIdx.x; e < 63 * 33; e += blockDim.x) sk[e] = 0;
+    __syncthreads();
+    const int s = s0 + tx;
+    for (int j = ty; j < 32; j += 8) {  // column t0 + j of the tile: tx + j is its anti-diagonal
+        const int t = t0 + j;
+        if (s < D && t < D) sk[(tx + j) * 33 + j] = static_cast<int32_t>(C[s + static_cast<size_t>(t) * D]);
+    }
+    __syncthreads();
+    if (threadIdx.x < 63) {
+        const int k = static_cast<int>(threadIdx.x);
+        long long v = 0;
+#pragma unroll 8
+        for (int j = 0; j < 32; ++j) v += sk[k * 33 + j];
+        if (v) atomicAdd(z + s0 + t0 + k, static_cast<unsigned long long>(v));  // two's complement: signed sum
+    }
+}
+
+// cols[w] = sum of z[u] 2^(6u - 32w) over the digit columns u whose bit 6u
+// lies in limb column w.
+__global__ void k_digits_to_cols(const long long *__restrict__ z, int nz, int W, __int128 *__restrict__ cols) {
+    const int w = static_cast<int>(blockIdx.x * blockDim.x + threadIdx.x);
+    if (w >= W) return;
+    __int128 acc = 0;
+    const int u_lo = (32 * w + kDig - 1) / kDig, u_hi = min(nz - 1, (32 * w + 31) / kDig);
+    for (int u = u_lo; u <= u_hi; ++u) acc += static_cast<__int128>(z[u]) << (kDig * u - 32 * w);
+    cols[w] = acc;
+}
+
+// One cuBLAS handle per host thread and device (a handle is not shared
+// between threads); made on first use and kept for the process.
+cublasHandle_t blas_handle() {
+    thread_local cublasHandle_t handles[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!handles[dev] && cublasCreate(&handles[dev]) != CUBLAS_STATUS_SUCCESS) handles[dev] = nullptr;
+    return handles[dev];
+}
+
 // out[w] = sum_c partial[c][w]; a block of 32 x 8 threads covers 32 columns,
 // the 8 lanes of a column take every 8th chunk and meet in shared memory.
 __global__ void __launch_bounds__(256) k_dot_reduce(const __int128 *__restrict__ partial, int chunks, int W,
@@ -258,32 +340,77 @@ extern "C" hmv_status hmv_dot(hmv_plan_t *p, const hmv_vec *x, const hmv_vec *y,
     const int n = p->n, L32 = p->L32, W = 2 * L32;
     if (!device_vec(x, n, p->b) || !device_vec(y, n, p->b) || zl < W + 2) return HMV_EINVAL;
     const int chunks = (n + kDotRows - 1) / kDotRows;
+    // digits of an entry, padded with zero digits to a multiple of 32 (16-byte
+    // aligned leading dimensions for the tensor-core GEMM kernels)
+    const int D = ((32 * L32 + kDig - 1) / kDig + 31) / 32 * 32;
+    // the dense product pays for its D x D matrix from about 2^26 limb products on
+    const bool dense = D <= kGemmMaxDigits && static_cast<double>(n) * L32 * L32 >= 67108864.0;
+    const bool same = x->limbs == y->limbs && x->neg == y->neg;
     cudaStream_t s = p->stream;
     __int128 *partial = nullptr, *cols = nullptr;
+    __nv_bfloat16 *xd = nullptr, *yd = nullptr;
+    float *cm = nullptr;
+    long long *zd = nullptr;
     uint32_t *mag = nullptr;
     uint8_t *zn = nullptr;
     int32_t *zb = nullptr, *st = nullptr;
     const int ZW = W + 2;
+    const int NZ = 2 * D + 64;  // digit columns (2D - 1) and the tiles' overhang
     // working memory from the plan (allocated by the first call, reused after)
-    Carve size;
-    size.take<__int128>(nullptr, static_cast<size_t>(chunks) * W);
-    size.take<__int128>(nullptr, W);
-    size.take<uint32_t>(nullptr, ZW);
-    size.take<uint8_t>(nullptr, 16);
-    size.take<int32_t>(nullptr, 4);
-    size.take<int32_t>(nullptr, 8);
-    cudaError_t e = grow(p->dot_buf, size.off, p->stream);
-    if (e == cudaSuccess) {
+    auto carve = [&](void *base) {
         Carve c;
-        partial = c.take<__int128>(p->dot_buf.ptr, static_cast<size_t>(chunks) * W);
-        cols = c.take<__int128>(p->dot_buf.ptr, W);
-        mag = c.take<uint32_t>(p->dot_buf.ptr, ZW);
-        zn = c.take<uint8_t>(p->dot_buf.ptr, 16);
-        zb = c.take<int32_t>(p->dot_buf.ptr, 4);
-        st = c.take<int32_t>(p->dot_buf.ptr, 8);
+        if (dense) {
+            xd = c.take<__nv_bfloat16>(base, static_cast<size_t>(n) * D);
+            yd = same ? xd : c.take<__nv_bfloat16>(base, static_cast<size_t>(n) * D);
+            cm = c.take<float>(base, static_cast<size_t>(D) * D);
+            zd = c.take<long long>(base, NZ);
+        } else {
+            partial = c.take<__int128>(base, static_cast<size_t>(chunks) * W);
+        }
+        cols = c.take<__int128>(base, W);
+        mag = c.take<uint32_t>(base, ZW);
+        zn = c.take<uint8_t>(base, 16);
+        zb = c.take<int32_t>(base, 4);
+        st = c.take<int32_t>(base, 8);
+        return c.off;
+    };
+    cudaError_t e = grow(p->dot_buf, carve(nullptr), p->stream);
+    if (e == cudaSuccess) {
+        carve(p->dot_buf.ptr);
         e = cudaMemsetAsync(st, 0, 8 * sizeof(int32_t), s);
     }
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && dense) {
+        cublasHandle_t h = blas_handle();
+        if (!h || cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) e = cudaErrorUnknown;
+        const long long nd = static_cast<long long>(n) * D;
+        if (e == cudaSuccess) {
+            k_digits7<<<static_cast<unsigned>((nd + 255) / 256), 256, 0, s>>>(x->limbs, x->neg, n, L32, D, xd);
+            if (!same)
+                k_digits7<<<static_cast<unsigned>((nd + 255) / 256), 256, 0, s>>>(y->limbs, y->neg, n, L32, D, yd);
+            e = cudaMemsetAsync(zd, 0, NZ * sizeof(long long), s);
+            p->launches_total += same ? 1 : 2;
+        }
+        const float one = 1.0f, zero = 0.0f;
+        const dim3 tiles((D + 31) / 32, (D + 31) / 32);
+        for (int c0 = 0; c0 < n && e == cudaSuccess; c0 += kGemmRows) {
+            const int kc = std::min(kGemmRows, n - c0);
+            // C (D x D, column-major) = Xc Yc^T over the chunk's rows (digit-major rows: column-major D x kc)
+            if (cublasGemmEx(h, CUBLAS_OP_N, CUBLAS_OP_T, D, D, kc, &one, xd + static_cast<size_t>(c0) * D,
+                             CUDA_R_16BF, D, yd + static_cast<size_t>(c0) * D, CUDA_R_16BF, D, &zero, cm, CUDA_R_32F,
+                             D, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS) {
+                e = cudaErrorUnknown;
+                break;
+            }
+            k_antidiag<<<tiles, 256, 0, s>>>(cm, D, reinterpret_cast<unsigned long long *>(zd));
+            p->launches_total += 1;
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) {
+            k_digits_to_cols<<<(W + 127) / 128, 128, 0, s>>>(zd, 2 * D - 1, W, cols);
+            e = launch_colsum_normalize_cols(cols, 1, W, mag, zn, zb, ZW, st, s);
+            p->launches_total += 2;
+        }
+    } else if (e == cudaSuccess) {
         const int slices = (W + kWarpCols - 1) / kWarpCols;
         const long long tasks = static_cast<long long>(slices) * chunks;
         k_dot_partial<<<static_cast<unsigned>((tasks + kBlasWarps - 1) / kBlasWarps), 32 * kBlasWarps, 0, s>>>(

@@ -28,7 +28,10 @@ def ptrs(t):
     return t[0].data_ptr(), t[1].data_ptr()
 
 
-@pytest.mark.parametrize("n,b", [(1, 32), (100, 1000), (777, 33220), (64, 2048)])
+# (777, 33220), (1500, 33220) and (5000, 4096) take the dense path (digit
+# planes on the tensor cores; the last in two 4096-row chunks, the second
+# ragged); the others the CUDA-core kernel
+@pytest.mark.parametrize("n,b", [(1, 32), (100, 1000), (777, 33220), (64, 2048), (1500, 33220), (5000, 4096)])
 def test_dot_is_exact(n, b):
     torch = pytest.importorskip("torch")
     x = uniform_vec(1000 + n, 0, n, b, 0)
@@ -38,6 +41,18 @@ def test_dot_is_exact(n, b):
         torch.cuda.synchronize()
         got = hmv.dot_device(p, ptrs(xd), ptrs(yd))
     assert got == sum(a * c for a, c in zip(x.to_ints(), y.to_ints()))
+
+
+@pytest.mark.parametrize("n,b", [(1200, 33220), (300, 1000)])
+def test_dot_of_a_vector_with_itself_is_exact(n, b):
+    """x = y (the dense path encodes the digit planes once)."""
+    torch = pytest.importorskip("torch")
+    x = uniform_vec(2000 + n, 0, n, b, 0)
+    with hmv.Plan(n, b, method=hmv.SCHOOLBOOK) as p:
+        xd = dev(x, torch)
+        torch.cuda.synchronize()
+        got = hmv.dot_device(p, ptrs(xd), ptrs(xd))
+    assert got == sum(a * a for a in x.to_ints())
 
 
 @pytest.mark.parametrize("n,b", [(50, 512), (300, 4096), (9, 65)])
