@@ -198,7 +198,7 @@ constexpr int kGemmMaxDigits = 8192;  // larger D: the CUDA-core kernel (C would
 constexpr int kDigMax = (1 << kDig) - 1;
 static_assert(static_cast<long long>(kGemmRows) * kDigMax * kDigMax < (1LL << 24), "exact fp32 chunk sums");
 
-__global__ void k_digits7(const uint32_t *__restrict__ limbs, const uint8_t *__restrict__ neg, int n, int L32, int D,
+__global__ void k_digit_planes(const uint32_t *__restrict__ limbs, const uint8_t *__restrict__ neg, int n, int L32, int D,
                           __nv_bfloat16 *__restrict__ out) {
     const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (idx >= static_cast<long long>(n) * D) return;
@@ -249,6 +249,48 @@ __global__ void k_digits_to_cols(const long long *__restrict__ z, int nz, int W,
     const int u_lo = (32 * w + kDig - 1) / kDig, u_hi = min(nz - 1, (32 * w + 31) / kDig);
     for (int u = u_lo; u <= u_hi; ++u) acc += static_cast<__int128>(z[u]) << (kDig * u - 32 * w);
     cols[w] = acc;
+}
+
+// The linear combination's large terms on the tensor cores: for scalar c (the
+// host's shifted limbs, Dc digits) and all rows x_i, the products c x_i are
+// the rows of T X^T with T the (Dc + D - 1) x D Toeplitz matrix of c's
+// digits (T[u][s] = c_(u-s)), by cuBLAS in 4096-digit chunks of the inner
+// dimension (exact fp32 sums, as the inner product's); each chunk's digit
+// columns are folded into the 128-bit limb column sums of the rows, moved up
+// by the term's limb offset.
+__global__ void k_toeplitz(const uint32_t *__restrict__ c, int nl, int neg, int Dc, int D, int Up,
+                           __nv_bfloat16 *__restrict__ T) {
+    const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= static_cast<long long>(Up) * D) return;
+    const int sidx = static_cast<int>(idx / Up), u = static_cast<int>(idx - static_cast<long long>(sidx) * Up);
+    const int v = u - sidx;  // digit of c at this entry
+    int d = 0;
+    if (v >= 0 && v < Dc) {
+        const int bit = kDig * v, w = bit >> 5, r = bit & 31;
+        if (w < nl) {
+            uint64_t x = c[w];
+            if (w + 1 < nl) x |= static_cast<uint64_t>(c[w + 1]) << 32;
+            d = static_cast<int>((x >> r) & static_cast<uint64_t>(kDigMax));
+        }
+    }
+    T[idx] = __int2bfloat16_rn(neg ? -d : d);
+}
+// cols[i][w] += sum of Cm[u][i] 2^(6u - 32 (w - off)) over the digit columns u
+// (< U) of the term's own limb column w - off.
+__global__ void k_term_cols(const float *__restrict__ Cm, int Up, int U, int n, int off, int W,
+                            __int128 *__restrict__ cols) {
+    const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= static_cast<long long>(n) * W) return;
+    const int i = static_cast<int>(idx / W), w = static_cast<int>(idx - static_cast<long long>(i) * W);
+    const int wl = w - off;
+    if (wl < 0) return;
+    const int u_lo = (32 * wl + kDig - 1) / kDig, u_hi = min(U - 1, (32 * wl + 31) / kDig);
+    if (u_lo > u_hi) return;
+    const float *col = Cm + static_cast<size_t>(i) * Up;
+    __int128 acc = 0;
+    for (int u = u_lo; u <= u_hi; ++u)
+        acc += static_cast<__int128>(static_cast<long long>(col[u])) << (kDig * u - 32 * wl);
+    cols[idx] += acc;
 }
 
 // One cuBLAS handle per host thread and device (a handle is not shared
@@ -384,9 +426,9 @@ extern "C" hmv_status hmv_dot(hmv_plan_t *p, const hmv_vec *x, const hmv_vec *y,
         if (!h || cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) e = cudaErrorUnknown;
         const long long nd = static_cast<long long>(n) * D;
         if (e == cudaSuccess) {
-            k_digits7<<<static_cast<unsigned>((nd + 255) / 256), 256, 0, s>>>(x->limbs, x->neg, n, L32, D, xd);
+            k_digit_planes<<<static_cast<unsigned>((nd + 255) / 256), 256, 0, s>>>(x->limbs, x->neg, n, L32, D, xd);
             if (!same)
-                k_digits7<<<static_cast<unsigned>((nd + 255) / 256), 256, 0, s>>>(y->limbs, y->neg, n, L32, D, yd);
+                k_digit_planes<<<static_cast<unsigned>((nd + 255) / 256), 256, 0, s>>>(y->limbs, y->neg, n, L32, D, yd);
             e = cudaMemsetAsync(zd, 0, NZ * sizeof(long long), s);
             p->launches_total += same ? 1 : 2;
         }
@@ -471,30 +513,43 @@ extern "C" hmv_status hmv_lincomb(hmv_plan_t *p, int32_t count, const hmv_scalar
     W += 1;
     const int ZW = W + 3;
     cudaStream_t s = p->stream;
+    // terms with large scalars on large problems go to the tensor cores (as
+    // the inner product's dense path), the others to the CUDA-core kernel
+    const int D = ((32 * L32 + kDig - 1) / kDig + 31) / 32 * 32;
+    bool dense[3] = {false, false, false};
+    int Upmax = 0;
+    for (int k = 0; k < count; ++k) {
+        dense[k] = D <= kGemmMaxDigits && t.nl[k] >= 64 &&
+                   static_cast<double>(n) * L32 * t.nl[k] >= 67108864.0;
+        if (dense[k]) Upmax = std::max(Upmax, ((32 * t.nl[k] + kDig - 1) / kDig + D - 1 + 31) / 32 * 32);
+    }
+    const bool any_dense = Upmax > 0;
     uint32_t *dc = nullptr, *mag = nullptr;
     __int128 *cols = nullptr;
     uint8_t *zn = nullptr;
     int32_t *zb = nullptr, *st = nullptr;
+    __nv_bfloat16 *xd = nullptr, *tm = nullptr;
+    float *cm = nullptr;
     int total = 0;
     for (int k = 0; k < count; ++k) total += t.nl[k];
     // working memory from the plan (grown when a call needs more, reused after)
-    Carve size;
-    size.take<uint32_t>(nullptr, total);
-    size.take<__int128>(nullptr, static_cast<size_t>(n) * W);
-    size.take<uint32_t>(nullptr, static_cast<size_t>(n) * ZW);
-    size.take<uint8_t>(nullptr, n);
-    size.take<int32_t>(nullptr, n);
-    size.take<int32_t>(nullptr, 8);
-    cudaError_t e = grow(p->lin_buf, size.off, p->stream);
-    if (e == cudaSuccess) {
+    auto carve = [&](void *base) {
         Carve c;
-        dc = c.take<uint32_t>(p->lin_buf.ptr, total);
-        cols = c.take<__int128>(p->lin_buf.ptr, static_cast<size_t>(n) * W);
-        mag = c.take<uint32_t>(p->lin_buf.ptr, static_cast<size_t>(n) * ZW);
-        zn = c.take<uint8_t>(p->lin_buf.ptr, n);
-        zb = c.take<int32_t>(p->lin_buf.ptr, n);
-        st = c.take<int32_t>(p->lin_buf.ptr, 8);
-    }
+        dc = c.take<uint32_t>(base, total);
+        cols = c.take<__int128>(base, static_cast<size_t>(n) * W);
+        mag = c.take<uint32_t>(base, static_cast<size_t>(n) * ZW);
+        zn = c.take<uint8_t>(base, n);
+        zb = c.take<int32_t>(base, n);
+        st = c.take<int32_t>(base, 8);
+        if (any_dense) {
+            xd = c.take<__nv_bfloat16>(base, static_cast<size_t>(n) * D);
+            tm = c.take<__nv_bfloat16>(base, static_cast<size_t>(Upmax) * D);
+            cm = c.take<float>(base, static_cast<size_t>(Upmax) * n);
+        }
+        return c.off;
+    };
+    cudaError_t e = grow(p->lin_buf, carve(nullptr), p->stream);
+    if (e == cudaSuccess) carve(p->lin_buf.ptr);
     std::vector<uint32_t> flat;
     for (int k = 0; k < count; ++k) flat.insert(flat.end(), shifted[k].begin(), shifted[k].end());
     if (e == cudaSuccess) e = cudaMemcpyAsync(dc, flat.data(), flat.size() * 4, cudaMemcpyHostToDevice, s);
@@ -505,11 +560,59 @@ extern "C" hmv_status hmv_lincomb(hmv_plan_t *p, int32_t count, const hmv_scalar
             t.c[k] = dc + o;
             o += t.nl[k];
         }
-        k_lincomb_colsum<<<dim3(n, (W / 4 + 127) / 128 + 1), 128, 0, s>>>(t, n, L32, W, cols);  // 4 columns/thread
+        // the small terms write every column sum (all zero without them) ...
+        LinTerms ts;
+        memset(&ts, 0, sizeof ts);
+        for (int k = 0; k < count; ++k) {
+            if (dense[k]) continue;
+            const int j = ts.count++;
+            ts.x[j] = t.x[k];
+            ts.xn[j] = t.xn[k];
+            ts.c[j] = t.c[k];
+            ts.nl[j] = t.nl[k];
+            ts.off[j] = t.off[k];
+            ts.sneg[j] = t.sneg[k];
+        }
+        if (ts.count > 0) {
+            k_lincomb_colsum<<<dim3(n, (W / 4 + 127) / 128 + 1), 128, 0, s>>>(ts, n, L32, W, cols);  // 4 columns/thread
+            p->launches_total++;
+            e = cudaGetLastError();
+        } else {
+            e = cudaMemsetAsync(cols, 0, static_cast<size_t>(n) * W * sizeof(__int128), s);
+        }
+        // ... and the large ones add theirs
+        cublasHandle_t h = any_dense ? blas_handle() : nullptr;
+        if (e == cudaSuccess && any_dense && (!h || cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS)) e = cudaErrorUnknown;
+        const float one = 1.0f, zero = 0.0f;
+        const long long nd = static_cast<long long>(n) * D;
+        for (int k = 0; k < count && e == cudaSuccess; ++k) {
+            if (!dense[k]) continue;
+            const int Dc = (32 * t.nl[k] + kDig - 1) / kDig, U = Dc + D - 1, Up = (U + 31) / 32 * 32;
+            k_digit_planes<<<static_cast<unsigned>((nd + 255) / 256), 256, 0, s>>>(t.x[k], t.xn[k], n, L32, D, xd);
+            const long long nt = static_cast<long long>(Up) * D;
+            k_toeplitz<<<static_cast<unsigned>((nt + 255) / 256), 256, 0, s>>>(t.c[k], t.nl[k], t.sneg[k], Dc, D, Up,
+                                                                              tm);
+            p->launches_total += 2;
+            for (int k0 = 0; k0 < D && e == cudaSuccess; k0 += kGemmRows) {
+                const int kc = std::min(kGemmRows, D - k0);
+                // Cm (Up x n, column-major) = T[:, k0:k0+kc] X[:, k0:k0+kc]^T
+                if (cublasGemmEx(h, CUBLAS_OP_N, CUBLAS_OP_N, Up, n, kc, &one, tm + static_cast<size_t>(k0) * Up,
+                                 CUDA_R_16BF, Up, xd + k0, CUDA_R_16BF, D, &zero, cm, CUDA_R_32F, Up,
+                                 CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS) {
+                    e = cudaErrorUnknown;
+                    break;
+                }
+                const long long nw = static_cast<long long>(n) * W;
+                k_term_cols<<<static_cast<unsigned>((nw + 255) / 256), 256, 0, s>>>(cm, Up, U, n, t.off[k], W, cols);
+                p->launches_total++;
+                e = cudaGetLastError();
+            }
+        }
         // value = S * 2^smin = S * 2^(e_in - 2b)
-        e = launch_colsum_round_cols(cols, n, W, L32, mag, zn, zb, ZW, st, b, static_cast<int>(smin + 2LL * b),
-                                     y->limbs, y->neg, s);
-        p->launches_total += 4;
+        if (e == cudaSuccess)
+            e = launch_colsum_round_cols(cols, n, W, L32, mag, zn, zb, ZW, st, b, static_cast<int>(smin + 2LL * b),
+                                         y->limbs, y->neg, s);
+        p->launches_total += 3;
     }
     int32_t status[8] = {0};
     if (e == cudaSuccess) e = cudaMemcpyAsync(status, st, sizeof status, cudaMemcpyDeviceToHost, s);

@@ -55,7 +55,10 @@ def test_dot_of_a_vector_with_itself_is_exact(n, b):
     assert got == sum(a * a for a in x.to_ints())
 
 
-@pytest.mark.parametrize("n,b", [(50, 512), (300, 4096), (9, 65)])
+# (1200, 33220): the b-bit scalars take the dense path (Toeplitz digit
+# matrices on the tensor cores, two 4096-digit chunks), small ones the
+# CUDA-core kernel, in the same call
+@pytest.mark.parametrize("n,b", [(50, 512), (300, 4096), (9, 65), (1200, 33220)])
 def test_lincomb_matches_oracle(n, b):
     torch = pytest.importorskip("torch")
     xs = [uniform_vec(1100 + n, t, n, b, e) for t, e in enumerate((2, -1, 0))]
