@@ -328,14 +328,18 @@ typedef struct {
 /* Exact inner product sum_i X_i Y_i of the signed mantissas of x and y (its
  * value is that integer times 2^(x.exponent + y.exponent - 2b)), written to
  * z (host, zl >= 2*ceil(b/32) + 2 limbs, little-endian magnitude) and
- * *z_neg.  HMV_EINVAL for mismatched vectors or a short z. */
+ * *z_neg.  HMV_EINVAL for mismatched vectors or a short z.  Large problems
+ * (from about 2^26 limb products, b up to about 49,000) run the products as
+ * GEMMs of 6-bit digit planes on the tensor cores (cuBLAS, every partial
+ * sum exact); the result is the same exact integer either way. */
 hmv_status hmv_dot(hmv_plan_t *plan, const hmv_vec *x, const hmv_vec *y, uint32_t *z, int32_t zl,
                    uint8_t *z_neg);
 
 /* y = sum_{k<count} c[k] * xs[k] (count 1..3), exact, then rounded to b bits
  * with the least shared exponent and round-half-even (the same rule as
  * hmv_matvec); y->exponent is written.  y may be one of the xs[k]: every
- * term is read before y is written.
+ * term is read before y is written.  Terms with large scalars on large
+ * problems run as GEMMs of digit planes on the tensor cores (as hmv_dot).
  * HMV_EUNSUPPORTED when two terms differ in scale by more than 128 ceil(b/32)
  * bits. */
 hmv_status hmv_lincomb(hmv_plan_t *plan, int32_t count, const hmv_scalar *c, const hmv_vec *xs, hmv_vec *y);
