@@ -7,11 +7,13 @@ products and the exact three-term update; the request keeps the alpha and
 beta sequence) or a plain chain v_{k+1} = A v_k.  The eigenvalue stage of a
 Lanczos run is the client's.  The server
 
-  * admits arrived requests in order while the device memory its plans need
-    (hmv_plan_bytes, computed without allocating) fits the budget; a request's
-    plan is created and its matrix loaded on a worker thread, on a CUDA stream
-    of the request's own (so the load does not queue behind the running
-    step), and it joins the first step that starts after that,
+  * admits each request at its arrival, in order, while the device memory
+    its plans need (hmv_plan_bytes, computed without allocating) fits the
+    budget: a dispatcher thread starts the admission while steps run; the
+    plan is created and its matrix loaded on a worker thread, on a CUDA
+    stream of the request's own (so the load does not queue behind the
+    running step), and the request joins the first step that starts after
+    that,
   * keeps every admitted matrix resident (one plan per request),
   * runs steps: each step advances EVERY active request by one product with
     one hmv_matvec_many call, whose leaf products share one persistent
@@ -92,6 +94,20 @@ class Server:
         self.max_active = max_active
         self.clock = clock
         self.method = method
+        self._warm_up()
+
+    def _warm_up(self):
+        # one exact inner product large enough for the tensor-core path: the
+        # library's GEMM handle and kernels are made before the first request,
+        # not inside its first product
+        torch = self.torch
+        n, b = 64, 33220
+        x = FixedVec(np.ones((n, (b + 31) // 32), dtype=np.uint32), np.zeros(n, dtype=np.uint8), b, 0)
+        with hmv.Plan(n, b, method=hmv.SCHOOLBOOK) as p:
+            xl = torch.from_numpy(x.limbs.view(np.int32)).to(self.dev)
+            xn = torch.from_numpy(x.neg).to(self.dev)
+            torch.cuda.synchronize(self.dev)
+            hmv.dot_device(p, (xl.data_ptr(), xn.data_ptr()), (xl.data_ptr(), xn.data_ptr()))
 
     def _admit(self, r: Request, now: float):
         # runs on the admission thread: the plan's load and the vectors'
@@ -138,77 +154,112 @@ class Server:
         r.stream = None
 
     def run(self, requests: list[Request]) -> dict:
+        import threading
         pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
         for r in pending:
             r.method, r.footprint = plan_choice(r.n, r.b, r.kind, self.method)
             if r.footprint > self.budget:
                 raise ValueError(f"request {r.rid} needs {r.footprint} bytes, more than the whole budget")
-        active: list[Request] = []
-        admitting: list[Request] = []
-        used = 0
-        steps, step_sizes, peak_active, peak_used = 0, [], 0, 0
+        # shared with the dispatcher thread, under cv: device bytes of the
+        # admitted plans, the number of active requests, the admissions in
+        # flight, and whether every request has been dispatched
+        cv = threading.Condition()
+        shared = {"used": 0, "peak_used": 0, "active": 0, "admitting": [], "dispatched": False, "stop": False}
         pool = ThreadPoolExecutor(max_workers=1)
         t0 = self.clock()
-        while pending or active or admitting:
-            now = self.clock() - t0
-            while pending and pending[0].arrival <= now and len(active) + len(admitting) < self.max_active:
-                r = pending[0]
-                if used + r.footprint > self.budget:
-                    break  # in order: wait for memory to free up
-                pending.pop(0)
-                used += r.footprint
-                r.admission = pool.submit(self._admit, r, now)
-                admitting.append(r)
-            waiting = []
-            for r in admitting:  # admitted requests join this step
-                if r.admission.done():
+
+        def dispatch():
+            # each request's admission starts at its arrival (in order), as
+            # soon as its plan fits the memory budget, while steps run
+            try:
+                for r in pending:
+                    with cv:
+                        while not shared["stop"]:
+                            delay = r.arrival - (self.clock() - t0)
+                            if (delay <= 0 and shared["used"] + r.footprint <= self.budget
+                                    and shared["active"] + len(shared["admitting"]) < self.max_active):
+                                break
+                            cv.wait(timeout=delay if delay > 0 else 0.05)
+                        if shared["stop"]:
+                            return
+                        shared["used"] += r.footprint
+                        shared["peak_used"] = max(shared["peak_used"], shared["used"])
+                        r.admission = pool.submit(self._admit, r, self.clock() - t0)
+                        shared["admitting"].append(r)
+                        cv.notify_all()
+            finally:
+                with cv:
+                    shared["dispatched"] = True
+                    cv.notify_all()
+
+        dispatcher = threading.Thread(target=dispatch, daemon=True)
+        dispatcher.start()
+        active: list[Request] = []
+        steps, step_sizes, peak_active = 0, [], 0
+        try:
+            while True:
+                with cv:  # admitted requests join this step (one look at each admission)
+                    joined, rest = [], []
+                    for r in shared["admitting"]:
+                        (joined if r.admission.done() else rest).append(r)
+                    shared["admitting"] = rest
+                for r in joined:
                     r.admission.result()  # an admission's error ends the run here
                     r.ready = r.arrival
                     active.append(r)
-                else:
-                    waiting.append(r)
-            admitting = waiting
-            peak_active = max(peak_active, len(active))
-            peak_used = max(peak_used, used)
-            if not active:
-                if admitting:
-                    admitting[0].admission.result()
-                elif pending:
-                    time.sleep(max(0.0, min(pending[0].arrival - (self.clock() - t0), 0.05)))
-                continue
-            xs, es, ys = [], [], []
-            for r in active:
-                if r.lanczos:
-                    vp, ev, wp = r.lz.operands()
-                else:
-                    vp, ev, wp = (r.xl.data_ptr(), r.xn.data_ptr()), r.x_exp, (r.yl.data_ptr(), r.yn.data_ptr())
-                xs.append(vp)
-                es.append(ev)
-                ys.append(wp)
-            exps = hmv.matvec_many_device([r.plan for r in active], xs, ys, es)
-            for r, e in zip(active, exps):  # the rest of each Lanczos step
-                if r.lanczos:
-                    a, bt = r.lz.finish(e)
-                    r.alphas.append(a)
-                    r.betas.append(bt)
-            t_end = self.clock() - t0
-            steps += 1
-            step_sizes.append(len(active))
-            still = []
-            for r, e in zip(active, exps):
-                r.latencies.append(t_end - r.ready)
-                r.ready = t_end
-                if not r.lanczos:
-                    r.xl, r.yl = r.yl, r.xl
-                    r.xn, r.yn = r.yn, r.xn
-                    r.x_exp = e
-                r.done += 1
-                if r.done == r.matvecs or (r.lanczos and r.betas[-1][0] == 0):
-                    self._finish(r, t_end, pool)
-                    used -= r.footprint
-                else:
-                    still.append(r)
-            active = still
+                with cv:
+                    shared["active"] = len(active)
+                    waiting = list(shared["admitting"])
+                    if not active and not waiting and shared["dispatched"]:
+                        break
+                    if not active and not waiting:
+                        cv.wait(timeout=0.05)  # until the next admission starts
+                peak_active = max(peak_active, len(active))
+                if not active:
+                    if waiting:
+                        waiting[0].admission.result()
+                    continue
+                xs, es, ys = [], [], []
+                for r in active:
+                    if r.lanczos:
+                        vp, ev, wp = r.lz.operands()
+                    else:
+                        vp, ev, wp = (r.xl.data_ptr(), r.xn.data_ptr()), r.x_exp, (r.yl.data_ptr(), r.yn.data_ptr())
+                    xs.append(vp)
+                    es.append(ev)
+                    ys.append(wp)
+                exps = hmv.matvec_many_device([r.plan for r in active], xs, ys, es)
+                for r, e in zip(active, exps):  # the rest of each Lanczos step
+                    if r.lanczos:
+                        a, bt = r.lz.finish(e)
+                        r.alphas.append(a)
+                        r.betas.append(bt)
+                t_end = self.clock() - t0
+                steps += 1
+                step_sizes.append(len(active))
+                still = []
+                for r, e in zip(active, exps):
+                    r.latencies.append(t_end - r.ready)
+                    r.ready = t_end
+                    if not r.lanczos:
+                        r.xl, r.yl = r.yl, r.xl
+                        r.xn, r.yn = r.yn, r.xn
+                        r.x_exp = e
+                    r.done += 1
+                    if r.done == r.matvecs or (r.lanczos and r.betas[-1][0] == 0):
+                        self._finish(r, t_end, pool)
+                        with cv:  # its memory counts as free for the admissions that follow its release
+                            shared["used"] -= r.footprint
+                            cv.notify_all()
+                    else:
+                        still.append(r)
+                active = still
+        finally:
+            with cv:
+                shared["stop"] = True
+                cv.notify_all()
+            dispatcher.join()
+        peak_used = shared["peak_used"]
         total = self.clock() - t0
         pool.shutdown(wait=True)
         for r in requests:
