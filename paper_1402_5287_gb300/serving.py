@@ -154,6 +154,95 @@ class Server:
         r.stream = None
 
     def run(self, requests: list[Request]) -> dict:
+        if self.method == hmv.NTT:
+            return self._run_independent(requests)
+        return self._run_steps(requests)
+
+    def _run_independent(self, requests: list[Request]) -> dict:
+        """The NTT path's server: there is no shared leaf launch to batch, so
+        every admitted request advances on its own, product after product on
+        its own stream, from a runner thread; the GPU interleaves the
+        requests' short kernels, and a request neither waits for a step
+        boundary to start nor for the other requests' products.  Admission at
+        arrival, in order, within the memory budget, as in the stepped loop."""
+        import threading
+        pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
+        for r in pending:
+            r.method, r.footprint = plan_choice(r.n, r.b, r.kind, self.method)
+            if r.footprint > self.budget:
+                raise ValueError(f"request {r.rid} needs {r.footprint} bytes, more than the whole budget")
+        cv = threading.Condition()
+        shared = {"used": 0, "peak_used": 0, "inflight": 0, "running": 0, "peak_running": 0}
+        pool = ThreadPoolExecutor(max_workers=1)  # admissions and releases, in order
+        runners = ThreadPoolExecutor(max_workers=self.max_active)
+        t0 = self.clock()
+
+        def serve(r: Request):
+            try:
+                r.admission.result()  # an admission's error ends the run
+                with cv:
+                    shared["running"] += 1
+                    shared["peak_running"] = max(shared["peak_running"], shared["running"])
+                r.ready = r.arrival
+                t_end = r.ready
+                for _ in range(r.matvecs):
+                    if r.lanczos:
+                        a, bt = r.lz.step()
+                        r.alphas.append(a)
+                        r.betas.append(bt)
+                    else:
+                        e = r.plan.matvec_device(r.xl.data_ptr(), r.xn.data_ptr(), r.x_exp, r.yl.data_ptr(),
+                                                 r.yn.data_ptr())
+                        r.xl, r.yl = r.yl, r.xl
+                        r.xn, r.yn = r.yn, r.xn
+                        r.x_exp = e
+                    t_end = self.clock() - t0
+                    r.latencies.append(t_end - r.ready)
+                    r.ready = t_end
+                    r.done += 1
+                    if r.lanczos and r.betas[-1][0] == 0:
+                        break
+                self._finish(r, t_end, pool)
+            finally:
+                with cv:
+                    shared["running"] -= 1
+                    shared["inflight"] -= 1
+                    shared["used"] -= r.footprint
+                    cv.notify_all()
+
+        futures = []
+        try:
+            for r in pending:  # dispatch at arrival, in order, within the budget
+                with cv:
+                    while True:
+                        delay = r.arrival - (self.clock() - t0)
+                        if (delay <= 0 and shared["used"] + r.footprint <= self.budget
+                                and shared["inflight"] < self.max_active):
+                            break
+                        cv.wait(timeout=delay if delay > 0 else 0.05)
+                    shared["used"] += r.footprint
+                    shared["peak_used"] = max(shared["peak_used"], shared["used"])
+                    shared["inflight"] += 1
+                r.admission = pool.submit(self._admit, r, self.clock() - t0)
+                futures.append(runners.submit(serve, r))
+            for f in futures:
+                f.result()
+        finally:
+            runners.shutdown(wait=True)
+        total = self.clock() - t0
+        pool.shutdown(wait=True)
+        for r in requests:
+            r.retired.result()
+        lat = [v for r in requests for v in r.latencies]
+        req_lat = [r.finished - r.arrival for r in requests]
+        nmv = sum(r.done for r in requests)
+        return {"matvecs": nmv, "seconds": total, "matvecs_per_s": nmv / total if total > 0 else None,
+                "p50_ms": percentile(lat, 50) * 1e3, "p99_ms": percentile(lat, 99) * 1e3,
+                "request_p50_s": percentile(req_lat, 50), "request_p99_s": percentile(req_lat, 99),
+                "steps": nmv, "mean_step_batch": 1.0, "peak_active": shared["peak_running"],
+                "peak_bytes": shared["peak_used"], "mode": "independent requests"}
+
+    def _run_steps(self, requests: list[Request]) -> dict:
         import threading
         pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
         for r in pending:
@@ -271,4 +360,4 @@ class Server:
                 "p50_ms": percentile(lat, 50) * 1e3, "p99_ms": percentile(lat, 99) * 1e3,
                 "request_p50_s": percentile(req_lat, 50), "request_p99_s": percentile(req_lat, 99),
                 "steps": steps, "mean_step_batch": float(np.mean(step_sizes)) if step_sizes else 0.0,
-                "peak_active": peak_active, "peak_bytes": peak_used}
+                "peak_active": peak_active, "peak_bytes": peak_used, "mode": "continuous batching"}
