@@ -15,13 +15,15 @@ Lanczos run is the client's.  The server
     running step), and the request joins the first step that starts after
     that,
   * keeps every admitted matrix resident (one plan per request),
-  * runs steps: each step advances EVERY active request by one product with
-    one hmv_matvec_many call, whose leaf products share one persistent
-    tensor-core launch (requests on the exact NTT path run their transforms
-    in the same call); requests that arrive during a step join at the next
-    one, finished requests leave (continuous batching) and their plans are
-    released on the worker thread, before any admission that follows, so
-    that the loop does not wait for the device memory to be freed,
+  * on the tensor-core path runs steps: each step advances EVERY active
+    request by one product with one hmv_matvec_many call, whose leaf products
+    share one persistent tensor-core launch; requests that arrive during a
+    step join at the next one, finished requests leave (continuous batching);
+    on the exact NTT path (no leaf launch to share) every request instead
+    advances on its own stream from a runner thread, the GPU interleaving the
+    requests' kernels; either way finished plans are released on the worker
+    thread, before any admission that follows, so that nothing waits for the
+    device memory to be freed,
   * records, per product, the time from when it became ready (arrival for
     the first, the previous product's completion otherwise) to completion.
 
