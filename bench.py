@@ -322,8 +322,8 @@ def run_ours(args):
         extras["vs_plain_kernel"] = plain
         extras["exact_ntt"] = measure_ntt(hmv, h, x, n, b, stream, args.steps, args.warmup)
         extras["exact_ntt"]["vs_plain_kernel"] = extras["exact_ntt"]["value"] / plain["value"]
-        extras["batched"] = measure_batched(3, 1, args.wave_gb)
-        extras["batched_exact_ntt"] = measure_batched(3, 1, args.wave_gb, "ntt")
+        extras["batched"] = measure_batched(3, 2, args.wave_gb)
+        extras["batched_exact_ntt"] = measure_batched(3, 2, args.wave_gb, "ntt")
         extras["serving"] = measure_serving(args.extra_requests, args.rate, args.matvecs_per_request,
                                             args.serve_gb, False)
         extras["serving_exact_ntt"] = measure_serving(args.extra_requests, args.rate, args.matvecs_per_request,
