@@ -275,6 +275,20 @@ def run_ours(args):
 
     traffic = leaf_traffic(st["leaf_tiles"], n, b, DIGIT_SPLIT_NAMES.get(st["digit_products"]),
                            st["leaf_tile_digits"])
+    roofline = {"bound": "tensor", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved_tflops / peak if peak else None, "traffic": traffic,
+                "kernel": "k_leaf_tc", "peak_source": peak_src,
+                "flops_per_launch": flops_per_launch, "launch_ms": leaf_ms,
+                "launches_per_matvec": launches_per_mv,
+                "issued_over_useful": issued_over_useful,
+                # the MMAs the tensor pipe actually ran (band edges included)
+                "frac_issued": achieved_tflops * issued_over_useful / peak if issued_over_useful else None,
+                "peak_sustained": peak_sust, "frac_of_sustained": achieved_tflops / peak_sust}
+    path, dtype = "karatsuba+tcgen05", "bf16"
+    if st["launches_leaf"] == 0:  # a comparison path was asked for: no tensor-core leaf ran
+        path, dtype = {"ntt": ("exact NTT, two 31-bit primes", "u32"), "fft64": ("split-FP64 FFT", "f64"),
+                       "schoolbook": ("schoolbook, 32-bit limbs", "u32")}.get(args.method, (args.method, "u32"))
+        roofline = (ntt_roofline(hmv, st, n, b, secs_max / args.steps, stream) if args.method == "ntt" else None)
 
     # end to end through the public API: host x in, host y out, copies inside the timed region
     e2e = None
@@ -335,8 +349,8 @@ def run_ours(args):
     line = {
         "metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": secs_max / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "n": n, "b": b, "kind": "hankel", "method": "karatsuba+tcgen05",
+        "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "n": n, "b": b, "kind": "hankel", "method": path,
                    "digit_split": DIGIT_SPLIT_NAMES.get(st["digit_products"], str(st["digit_products"])),
                    "digit_products": st["digit_products"],
                    "levels": st["levels"], "leaves": st["leaves"], "leaf_rows_max": st["leaf_rows_max"],
@@ -345,15 +359,7 @@ def run_ours(args):
                    "digit_format": "balanced radix-2^8 digits held exactly in bf16, fp32 windows < 2^24",
                    "l2": "working set of several GB per step (inputs larger than L2)",
                    "parallelism": f"{world} independent replica(s), one per GPU"},
-        "roofline": {"bound": "tensor", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / peak if peak else None, "traffic": traffic,
-                     "kernel": "k_leaf_tc", "peak_source": peak_src,
-                     "flops_per_launch": flops_per_launch, "launch_ms": leaf_ms,
-                     "launches_per_matvec": launches_per_mv,
-                     "issued_over_useful": issued_over_useful,
-                     # the MMAs the tensor pipe actually ran (band edges included)
-                     "frac_issued": achieved_tflops * issued_over_useful / peak if issued_over_useful else None,
-                     "peak_sustained": peak_sust, "frac_of_sustained": achieved_tflops / peak_sust},
+        "roofline": roofline,
         "stage_ms": {"prepass": st["ms_prepass"] / max(st["matvecs"], 1), "leaf": st["ms_leaf"] / max(st["matvecs"], 1),
                      "post": st["ms_post"] / max(st["matvecs"], 1), "round": st["ms_round"] / max(st["matvecs"], 1)},
         # the plain definition's work (n^2 products of D = ceil(b/8)-digit numbers, D^2 digit
@@ -655,16 +661,27 @@ def measure_ntt(hmv, h, x, n, b, stream, steps, warmup):
     plan.close()
     s = e0.elapsed_time(e1) / 1e3 / steps
     K = st["fft_log2_len"]
+    return {"value": 1.0 / s, "unit": UNIT, "ms_per_matvec": s * 1e3, "steps": steps, "warmup": max(warmup, 3),
+            "method": "exact NTT: 16-bit pieces, one cyclic convolution of 2^%d points modulo two 31-bit primes, "
+                      "Chinese remainder, carries; bit-exact" % K,
+            "roofline": ntt_roofline(hmv, st, n, b, s, stream)}
+
+
+def ntt_roofline(hmv, st, n, b, s, stream):
+    """The NTT path's roofline for a matvec of s seconds: Montgomery products
+    per matvec (each radix-2 butterfly of both transforms, the pointwise
+    product and the Chinese remainder of every kept coefficient, for both
+    primes) over the rate this GPU sustains for independent products,
+    measured now."""
+    K = st["fft_log2_len"]
     N = 1 << K
     P = (b + 15) // 16
     products = 2.0 * K * N + 2.0 * N + n * (2 * P - 1)
     peak = hmv.measure_montgomery_rate(stream.cuda_stream)
-    return {"value": 1.0 / s, "unit": UNIT, "ms_per_matvec": s * 1e3, "steps": steps, "warmup": max(warmup, 3),
-            "method": "exact NTT: 16-bit pieces, one cyclic convolution of 2^%d points modulo two 31-bit primes, "
-                      "Chinese remainder, carries; bit-exact" % K,
-            "roofline": {"bound": "alu", "achieved": products / s, "peak": peak, "unit": "Montgomery products/s",
-                         "frac": products / s / peak, "traffic": None, "products_per_matvec": products,
-                         "peak_source": "of measured: independent Montgomery products on this GPU, same run"}}
+    return {"bound": "alu", "achieved": products / s, "peak": peak, "unit": "Montgomery products/s",
+            "frac": products / s / peak, "traffic": None, "products_per_matvec": products,
+            "kernel": "k_ntt_rpass, k_ntt_rmid (the transform passes)",
+            "peak_source": "of measured: independent Montgomery products on this GPU, same run"}
 
 
 def measure_plain_kernel(hmv, h, x, n, b, stream):

@@ -85,10 +85,6 @@ __device__ __forceinline__ uint32_t table_power(const NttConst &c, int k, int m)
     return mont_mul(__ldg(c.thi[k] + (m >> kTwLoBits)), __ldg(c.tlo[k] + (m & ((1 << kTwLoBits) - 1))), c.p[k],
                     c.pinv[k]);
 }
-__device__ __forceinline__ uint32_t twiddle(const NttConst &c, int k, int m, int inverse, int half) {
-    if (!inverse || m == 0) return table_power(c, k, m);
-    return c.p[k] - table_power(c, k, half - m);  // a unit: never 0
-}
 
 // 16-bit pieces of sign-magnitude rows as residues modulo both primes, piece
 // p of row k at slot(k) S + p; slot(k) = k (matrix side) or n-1-k (vector
@@ -118,8 +114,7 @@ __global__ void k_ntt_pieces(const uint32_t *__restrict__ limbs, const uint8_t *
 }
 
 // One pass of radix-2 stages on sub-transforms of 2^r points spaced
-// st = 2^(s_lo-1) apart inside blocks of 2^s_hi points (the split-FP64 path's
-// pass structure):
+// st = 2^(s_lo-1) apart inside blocks of 2^s_hi points:
 //   forward (decimation in frequency), stages s_hi down to s_lo:
 //     (u, v) -> (u + v, (u - v) w_{2^s}^j)
 //   inverse (decimation in time), stages s_lo up to s_hi:
@@ -147,103 +142,6 @@ struct PassGeo {
     }
     __device__ int gidx(int t, int q) const { return ((blk0 + (q >> lC)) << s_hi) + low0 + (q & cmask) + (t << lst); }
 };
-
-// The radix-2 stages of one pass on the tile in shared memory (ends with a
-// __syncthreads).
-__device__ __forceinline__ void ntt_stages(uint2 *nsm, const NttConst &c, const PassGeo &g, int K, int r, int inverse) {
-    const int pts = 1 << r;
-    const int s_hi = g.s_hi, s_lo = g.s_lo, lst = g.lst, low0 = g.low0, cmask = g.cmask;
-    const int half = 1 << (K - 1);
-    const int nbf = (pts / 2) * kNttCols;
-    const int q = threadIdx.x & 15;  // the thread's column in every stage (blockDim is a multiple of 16)
-    for (int st_i = 0; st_i < r; ++st_i) {
-        const int s = inverse ? (s_lo + st_i) : (s_hi - st_i);
-        const int lh = s - s_lo;  // log2 of the span in sub-transform units
-        const int ht = 1 << lh;
-        // The thread's butterflies bf = (tid >> 4) + 16 it have u at point
-        // tlow = bf mod ht of their half block, so j = low0 + q + tlow st and
-        // the twiddle exponent m = j 2^(K-s) = mb + tlow 2^lw: constant over it
-        // when ht <= 16, else a geometric sequence in steps of 16 tlow that
-        // restarts every ht / 16 butterflies.  One table lookup per stage.
-        const int lw = K - 1 - lh;
-        const int mb = (low0 + (q & cmask)) << (K - s);
-        const int tl0 = (threadIdx.x >> 4) & (ht - 1);
-        const int per = ht > 16 ? (ht >> 4) : 1;
-        uint32_t w0[2], ws[2], w[2];
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            w0[k] = twiddle(c, k, mb + (tl0 << lw), inverse, half);
-            ws[k] = per > 1 ? twiddle(c, k, 16 << lw, inverse, half) : 0u;
-            w[k] = w0[k];
-        }
-        int it = 0;
-        for (int e = threadIdx.x; e < nbf; e += blockDim.x, ++it) {
-            const int bf = e >> 4;
-            const int tlow = bf & (ht - 1);                  // position inside the half block
-            const int t = ((bf >> lh) << (lh + 1)) + tlow;   // u's point
-            if (per > 1 && it > 0) {  // warp-uniform: it and per are the same on every lane
-                if ((it & (per - 1)) == 0) {
-                    w[0] = w0[0];
-                    w[1] = w0[1];
-                } else {
-#pragma unroll
-                    for (int k = 0; k < 2; ++k) w[k] = mont_mul(w[k], ws[k], c.p[k], c.pinv[k]);
-                }
-            }
-            const uint2 u = nsm[(t << 4) + q], v = nsm[((t + ht) << 4) + q];
-            uint32_t uo[2] = {u.x, u.y}, vo[2] = {v.x, v.y};
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const uint32_t p = c.p[k], pinv = c.pinv[k];
-                if (!inverse) {
-                    const uint32_t a = mod_add(uo[k], vo[k], p);
-                    vo[k] = mont_mul(mod_sub(uo[k], vo[k], p), w[k], p, pinv);
-                    uo[k] = a;
-                } else {
-                    const uint32_t tv = mont_mul(vo[k], w[k], p, pinv);
-                    vo[k] = mod_sub(uo[k], tv, p);
-                    uo[k] = mod_add(uo[k], tv, p);
-                }
-            }
-            nsm[(t << 4) + q] = make_uint2(uo[0], uo[1]);
-            nsm[((t + ht) << 4) + q] = make_uint2(vo[0], vo[1]);
-        }
-        __syncthreads();
-    }
-}
-
-// One pass of radix-2 stages (see ntt_stages) from global memory and back.
-__global__ void __launch_bounds__(256) k_ntt_pass(uint2 *__restrict__ d, NttConst c, int K, int s_hi, int r,
-                                                  int inverse) {
-    extern __shared__ uint2 nsm[];  // [2^r][kNttCols]
-    const PassGeo g(s_hi, r);
-    const int pts = 1 << r;
-    for (int e = threadIdx.x; e < pts * kNttCols; e += blockDim.x) nsm[e] = d[g.gidx(e >> 4, e & 15)];
-    __syncthreads();
-    ntt_stages(nsm, c, g, K, r, inverse);
-    for (int e = threadIdx.x; e < pts * kNttCols; e += blockDim.x) d[g.gidx(e >> 4, e & 15)] = nsm[e];
-}
-
-// The lowest forward stages r .. 1, the pointwise product with the matrix
-// spectrum a (Montgomery form, times 1/N) and the lowest inverse stages
-// 1 .. r in one pass: blocks of 2^r consecutive points stay in shared memory
-// (both transforms visit them in the same bit-reversed order).
-__global__ void __launch_bounds__(256) k_ntt_mid(uint2 *__restrict__ d, const uint2 *__restrict__ a, NttConst c, int K,
-                                                 int r) {
-    extern __shared__ uint2 nsm[];
-    const PassGeo g(r, r);
-    const int pts = 1 << r;
-    for (int e = threadIdx.x; e < pts * kNttCols; e += blockDim.x) nsm[e] = d[g.gidx(e >> 4, e & 15)];
-    __syncthreads();
-    ntt_stages(nsm, c, g, K, r, 0);
-    for (int e = threadIdx.x; e < pts * kNttCols; e += blockDim.x) {
-        const uint2 u = nsm[e], v = a[g.gidx(e >> 4, e & 15)];
-        nsm[e] = make_uint2(mont_mul(u.x, v.x, c.p[0], c.pinv[0]), mont_mul(u.y, v.y, c.p[1], c.pinv[1]));
-    }
-    __syncthreads();
-    ntt_stages(nsm, c, g, K, r, 1);
-    for (int e = threadIdx.x; e < pts * kNttCols; e += blockDim.x) d[g.gidx(e >> 4, e & 15)] = nsm[e];
-}
 
 // ---------------------------------------------------------------- register-blocked passes
 // The same passes with the points in registers.  A block holds 16 columns
@@ -296,12 +194,12 @@ __device__ __forceinline__ void ntt_bfly1(uint2 &u, uint2 &v, const NttConst &c)
     v = make_uint2(mod_sub(u.x, v.x, c.p[0]), mod_sub(u.y, v.y, c.p[1]));
     u = a;
 }
-// Layout B, span 2^I (I < 4): pairs (k, k + 2^I), t mod 2^I = k mod 2^I
-// (NP g is a multiple of 16), twiddle w_{2^(I+1)}^(k mod 2^I) = w_16^e.
+// Layout B, span 2^I (I < LG <= 4): pairs (k, k + 2^I), t mod 2^I = k mod 2^I
+// (NP g is a multiple of 2^I), twiddle w_{2^(I+1)}^(k mod 2^I) = w_16^e.
 template <int NP, int I, bool INV>
 __device__ __forceinline__ void ntt_b_stage(uint2 (&x)[NP], const NttConst &c) {
     constexpr int HK = 1 << I;
-    static_assert(I <= 3 && 2 * HK <= NP && NP >= 16, "spans 1..8 inside the thread");
+    static_assert(I <= 3 && 2 * HK <= NP, "spans 1..8 inside the thread (NP a multiple of 2^(I+1))");
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
         if (i & HK) continue;
@@ -478,7 +376,9 @@ __global__ void __launch_bounds__(16 << LG, NP == 32 ? 2 : 3) k_ntt_rpass(uint2 
 }
 
 // The lowest forward stages, the product with the matrix spectrum and the
-// lowest inverse stages (k_ntt_mid) with the points in registers.
+// lowest inverse stages in one pass, with the points in registers: blocks of
+// 2^r consecutive points stay on chip (both transforms visit them in the same
+// bit-reversed order).
 template <int NP, int LG>
 __global__ void __launch_bounds__(16 << LG, NP == 32 ? 2 : 3) k_ntt_rmid(uint2 *__restrict__ d,
                                                                             const uint2 *__restrict__ a, NttConst c,
@@ -512,28 +412,20 @@ constexpr size_t ntt_rsmem(int r, bool mid) {
     return (static_cast<size_t>(kTilePitch) * (1u << r) + (mid ? (1u << r) : (1u << (r - 1)))) * sizeof(uint2);
 }
 
-// dst <- src * f in the register order of k_ntt_rmid<NP, 4> for a last pass
-// of r stages: entry (bx NP + k) 256 + tid holds point NP (tid >> 4) + k of
-// column tid & 15 of that kernel's block bx.
+// dst <- src * f in the register order of k_ntt_rmid<NP, LG> for a last pass
+// of r stages (lnp = log2 NP, lt = 4 + LG the log2 of its threads): entry
+// (bx NP + k) 2^lt + tid holds point NP (tid >> 4) + k of column tid & 15 of
+// that kernel's block bx.
 __global__ void k_ntt_scale_perm(const uint2 *__restrict__ src, uint2 *__restrict__ dst, long long N, int r, int lnp,
-                                 NttConst c, uint32_t f0, uint32_t f1) {
+                                 int lt, NttConst c, uint32_t f0, uint32_t f1) {
     for (long long o = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; o < N;
          o += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const long long bx = o >> (lnp + 8);
-        const int rem = static_cast<int>(o & ((1LL << (lnp + 8)) - 1));
-        const int k = rem >> 8, tid = rem & 255;
+        const long long bx = o >> (lnp + lt);
+        const int rem = static_cast<int>(o & ((1LL << (lnp + lt)) - 1));
+        const int k = rem >> lt, tid = rem & ((1 << lt) - 1);
         const int q = tid & 15, gq = tid >> 4;
         const uint2 u = src[((bx * 16 + q) << r) + (static_cast<long long>(gq) << lnp) + k];
         dst[o] = make_uint2(mont_mul(u.x, f0, c.p[0], c.pinv[0]), mont_mul(u.y, f1, c.p[1], c.pinv[1]));
-    }
-}
-
-// a <- a * f (f = R^2 / N mod p: the spectrum in Montgomery form, times 1/N)
-__global__ void k_ntt_scale(uint2 *__restrict__ a, long long N, NttConst c, uint32_t f0, uint32_t f1) {
-    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
-         i += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const uint2 u = a[i];
-        a[i] = make_uint2(mont_mul(u.x, f0, c.p[0], c.pinv[0]), mont_mul(u.y, f1, c.p[1], c.pinv[1]));
     }
 }
 
@@ -684,38 +576,32 @@ int grid_for(long long work, int threads = 256) {
 }
 
 // Pass boundaries, from the top stage down; the last pass ends with stage 1.
-// Passes of 9 or 8 stages run with the points in registers (k_ntt_rpass,
-// k_ntt_rmid), so K is split into 9s and 8s where it can be (K = 26: 9, 9, 8)
-// and otherwise into 9s and one shorter pass at the bottom.
+// K >= 13 is cut into ceil(K / 9) passes as even as possible, the longer ones
+// first (26 = 9 + 9 + 8, 24 = 8 + 8 + 8, 23 = 8 + 8 + 7, 21 = 7 + 7 + 7,
+// 13 = 7 + 6): every pass has 6 to 9 stages and runs with the points in
+// registers.  (Splits into 9s with a short last pass ran the middle kernel
+// from shared memory, at up to five times the time per point and stage.)
 int ntt_passes(int K, int (&bounds)[8][2]) {
-    int rs[8], nr = 0;
-    int b8 = -1;
-    for (int b = 0; b <= 3 && b8 < 0; ++b)
-        if (K - 8 * b >= 0 && (K - 8 * b) % 9 == 0) b8 = b;
-    if (b8 >= 0) {
-        for (int i = 0; i < (K - 8 * b8) / 9; ++i) rs[nr++] = 9;
-        for (int i = 0; i < b8; ++i) rs[nr++] = 8;
-    } else {
-        for (int i = 0; i < K / 9; ++i) rs[nr++] = 9;
-        rs[nr++] = K % 9;
-    }
+    const int nr = (K + kNttMaxR - 1) / kNttMaxR;
     int s_hi = K;
     for (int i = 0; i < nr; ++i) {
+        const int r = K / nr + (i < K % nr ? 1 : 0);
         bounds[i][0] = s_hi;
-        bounds[i][1] = rs[i];
-        s_hi -= rs[i];
+        bounds[i][1] = r;
+        s_hi -= r;
     }
     return nr;
 }
+// The register kernels' shape for a pass of r stages: NP points a thread,
+// G = 2^LG threads a column (NP >= G: the two layouts), 16 G threads a block.
+constexpr int ntt_lg(int r) { return r >= 8 ? 4 : 3; }
+constexpr int ntt_lnp(int r) { return r - ntt_lg(r); }
 
 cudaError_t ntt_attrs() {
     static bool attr = false;
     if (attr) return cudaSuccess;
-    const int smem = static_cast<int>(kNttCols * (1u << kNttMaxR) * sizeof(uint2));
-    cudaError_t e = cudaFuncSetAttribute(k_ntt_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_ntt_rpass<32, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    // (the smaller passes stay under the default 48 KB)
+    cudaError_t e = cudaFuncSetAttribute(k_ntt_rpass<32, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(ntt_rsmem(9, false)));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_ntt_rmid<32, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -726,14 +612,16 @@ cudaError_t ntt_attrs() {
 
 cudaError_t launch_pass(hmv_plan_s *p, uint2 *data, const NttConst &c, int s_hi, int r, int inverse) {
     const unsigned blocks = static_cast<unsigned>((p->ntt_N >> r) / kNttCols);
-    const size_t smem = r >= 8 ? ntt_rsmem(r, false) : kNttCols * (size_t(1) << r) * sizeof(uint2);
-    if (r == 9)  // 32 points a thread: 16 columns x 16 threads
-        k_ntt_rpass<32, 4><<<blocks, 256, smem, p->stream>>>(data, c, p->ntt_K, s_hi, inverse);
-    else if (r == 8)  // 16 points a thread: 16 columns x 16 threads (8 threads a column with 32 points each
-                      // measured slower: 3.87 vs 3.58 ms per matvec)
-        k_ntt_rpass<16, 4><<<blocks, 256, smem, p->stream>>>(data, c, p->ntt_K, s_hi, inverse);
-    else
-        k_ntt_pass<<<blocks, 256, smem, p->stream>>>(data, c, p->ntt_K, s_hi, r, inverse);
+    const size_t smem = ntt_rsmem(r, false);
+    const int threads = 16 << ntt_lg(r);
+    switch (r) {  // points in registers: NP a thread, G threads a column (8 threads a column for the
+                  // 8-stage pass measured slower: 3.87 vs 3.58 ms per matvec); ntt_passes gives 6..9
+        case 9: k_ntt_rpass<32, 4><<<blocks, threads, smem, p->stream>>>(data, c, p->ntt_K, s_hi, inverse); break;
+        case 8: k_ntt_rpass<16, 4><<<blocks, threads, smem, p->stream>>>(data, c, p->ntt_K, s_hi, inverse); break;
+        case 7: k_ntt_rpass<16, 3><<<blocks, threads, smem, p->stream>>>(data, c, p->ntt_K, s_hi, inverse); break;
+        case 6: k_ntt_rpass<8, 3><<<blocks, threads, smem, p->stream>>>(data, c, p->ntt_K, s_hi, inverse); break;
+        default: return cudaErrorInvalidValue;
+    }
     p->launches_total++;
     return cudaGetLastError();
 }
@@ -760,13 +648,15 @@ cudaError_t run_ntt_product(hmv_plan_s *p, uint2 *data) {
     if (e == cudaSuccess) {
         const int r = bounds[np - 1][1];  // s_hi = r: blocks of 2^r consecutive points
         const unsigned blocks = static_cast<unsigned>((p->ntt_N >> r) / kNttCols);
-        const size_t smem = r >= 8 ? ntt_rsmem(r, true) : kNttCols * (size_t(1) << r) * sizeof(uint2);
-        if (r == 9)
-            k_ntt_rmid<32, 4><<<blocks, 256, smem, p->stream>>>(data, p->ntt_a, c, p->ntt_K);
-        else if (r == 8)
-            k_ntt_rmid<16, 4><<<blocks, 256, smem, p->stream>>>(data, p->ntt_a, c, p->ntt_K);
-        else
-            k_ntt_mid<<<blocks, 256, smem, p->stream>>>(data, p->ntt_a, c, p->ntt_K, r);
+        const size_t smem = ntt_rsmem(r, true);
+        const int threads = 16 << ntt_lg(r);
+        switch (r) {
+            case 9: k_ntt_rmid<32, 4><<<blocks, threads, smem, p->stream>>>(data, p->ntt_a, c, p->ntt_K); break;
+            case 8: k_ntt_rmid<16, 4><<<blocks, threads, smem, p->stream>>>(data, p->ntt_a, c, p->ntt_K); break;
+            case 7: k_ntt_rmid<16, 3><<<blocks, threads, smem, p->stream>>>(data, p->ntt_a, c, p->ntt_K); break;
+            case 6: k_ntt_rmid<8, 3><<<blocks, threads, smem, p->stream>>>(data, p->ntt_a, c, p->ntt_K); break;
+            default: return cudaErrorInvalidValue;
+        }
         p->launches_total++;
         e = cudaGetLastError();
     }
@@ -782,7 +672,7 @@ bool ntt_geometry(int n, int b, int &P, int &S, int &K) {
     P = (b + kNttPieceBits - 1) / kNttPieceBits;
     S = 2 * P - 1;
     const long long need = static_cast<long long>(2 * n - 1) * S;
-    K = kNttMaxR + 4;  // at least one block of 16 sub-transforms in the first pass
+    K = 13;  // two passes of 6 or more stages (the register kernels' shapes), 16 columns a block
     while ((1LL << K) < need) ++K;
     return K <= kNttMaxK;
 }
@@ -844,13 +734,11 @@ cudaError_t ntt_load_matrix(hmv_plan_s *p) {
     }
     int bounds[8][2];
     const int last_r = bounds[ntt_passes(p->ntt_K, bounds) - 1][1];
-    if (last_r == 9 || last_r == 8) {  // the register middle pass reads the spectrum in its own order
-        k_ntt_scale_perm<<<grid_for(p->ntt_N), 256, 0, p->stream>>>(p->ntt_a, p->ntt_x, p->ntt_N, last_r,
-                                                                    last_r == 9 ? 5 : 4, c, f[0], f[1]);
-        std::swap(p->ntt_a, p->ntt_x);  // the vector side's work array is free until the next matvec
-    } else {
-        k_ntt_scale<<<grid_for(p->ntt_N), 256, 0, p->stream>>>(p->ntt_a, p->ntt_N, c, f[0], f[1]);
-    }
+    // the middle pass reads the spectrum (in Montgomery form, times 1/N: f = R^2 / N mod p) in its own
+    // register order
+    k_ntt_scale_perm<<<grid_for(p->ntt_N), 256, 0, p->stream>>>(p->ntt_a, p->ntt_x, p->ntt_N, last_r,
+                                                                ntt_lnp(last_r), 4 + ntt_lg(last_r), c, f[0], f[1]);
+    std::swap(p->ntt_a, p->ntt_x);  // the vector side's work array is free until the next matvec
     p->launches_total++;
     return cudaGetLastError();
 }

@@ -19,18 +19,22 @@ def root(K):
 
 
 def passes(K):
-    """The library's split of stages K .. 1 into passes (9s and 8s where it can)."""
-    for b in range(4):
-        if K - 8 * b >= 0 and (K - 8 * b) % 9 == 0:
-            rs = [9] * ((K - 8 * b) // 9) + [8] * b
-            break
-    else:
-        rs = [9] * (K // 9) + [K % 9]
+    """The library's split of stages K .. 1 into ceil(K / 9) passes, as even
+    as possible, the longer ones first."""
+    nr = -(-K // 9)
     out, s_hi = [], K
-    for r in rs:
+    for i in range(nr):
+        r = K // nr + (1 if i < K % nr else 0)
         out.append((s_hi, r))
         s_hi -= r
     return out
+
+
+def shape(r):
+    """Points a thread NP and log2 of the threads a column LG for a pass of r
+    stages: 32 x 16, 16 x 16, 16 x 8, 8 x 8 for r = 9, 8, 7, 6."""
+    LG = 4 if r >= 8 else 3
+    return 1 << (r - LG), LG
 
 
 def geo(bx, s_hi, r):
@@ -106,10 +110,10 @@ def column_factors(xs, g, K, inverse, NP, LG):
 
 def run_rpass(d, K, s_hi, r, inverse, spectrum=None):
     """k_ntt_rpass (spectrum None) or k_ntt_rmid (with the pointwise product)
-    as the library launches them: 16 columns a block, 16 threads a column,
-    32 points a thread for r = 9 and 16 for r = 8; inner stages, then the
-    column factors (forward), or the factors first (inverse)."""
-    NP, LG = (32 if r == 9 else 16), 4
+    as the library launches them: 16 columns a block, G threads a column, NP
+    points a thread (shape(r)); inner stages, then the column factors
+    (forward), or the factors first (inverse)."""
+    NP, LG = shape(r)
     G = 1 << LG
     T = 16 * G
     N = len(d)
@@ -186,13 +190,14 @@ def dif_reference(a, K):
     return list(a)
 
 
-@pytest.mark.parametrize("K", [16, 17])
+@pytest.mark.parametrize("K", [13, 14, 16, 17])
 def test_register_passes_equal_radix2_transform(K):
+    """Passes 7 + 6, 7 + 7, 8 + 8 and 9 + 8: every register kernel shape."""
     rng = np.random.default_rng(K)
     N = 1 << K
     x = [int(v) for v in rng.integers(0, P1, N)]
     plan = passes(K)
-    assert all(r in (8, 9) for _, r in plan)  # the register kernels cover these sizes
+    assert all(6 <= r <= 9 for _, r in plan)  # the register kernels cover every size
     d = list(x)
     for s_hi, r in plan:
         run_rpass(d, K, s_hi, r, False)
@@ -203,10 +208,11 @@ def test_register_passes_equal_radix2_transform(K):
     assert d == [v * N % P1 for v in x]
 
 
-def test_middle_pass_is_forward_product_inverse():
+@pytest.mark.parametrize("K", [13, 16])
+def test_middle_pass_is_forward_product_inverse(K):
     """k_ntt_rmid: the last forward pass, the pointwise product and the first
-    inverse pass in one, equal to the three done apart."""
-    K = 16
+    inverse pass in one, equal to the three done apart (last pass 6 and 8
+    stages)."""
     rng = np.random.default_rng(5)
     N = 1 << K
     x = [int(v) for v in rng.integers(0, P1, N)]
@@ -225,6 +231,13 @@ def test_middle_pass_is_forward_product_inverse():
 def test_pass_split():
     assert passes(26) == [(26, 9), (17, 9), (8, 8)]
     assert passes(24) == [(24, 8), (16, 8), (8, 8)]
-    assert passes(13) == [(13, 9), (4, 4)]
+    assert passes(23) == [(23, 8), (15, 8), (7, 7)]
+    assert passes(21) == [(21, 7), (14, 7), (7, 7)]
+    assert passes(13) == [(13, 7), (6, 6)]
     for K in range(13, 27):
-        assert sum(r for _, r in passes(K)) == K and passes(K)[-1][0] == passes(K)[-1][1]
+        rs = [r for _, r in passes(K)]
+        assert sum(rs) == K and passes(K)[-1][0] == rs[-1]
+        assert all(6 <= r <= 9 for r in rs) and max(rs) - min(rs) <= 1
+        NP, LG = shape(rs[-1])
+        assert NP >= (1 << LG) and NP << LG == 1 << rs[-1]  # both layouts hold; 16 G threads cover 2^r points
+        assert (1 << (K - rs[0])) >= 16  # the first pass has 16 columns a block
