@@ -101,3 +101,36 @@ def test_ntt_benchmark_workload_sampled_and_equal_to_the_tensor_core_path():
         p.load_matrix(h)
         yt = p.matvec(x)
     assert_same(y, yt)
+
+
+def ntt_case(K):
+    """(n, b) whose Hankel product needs a transform of exactly 2^K points:
+    (2n - 1) S <= 2^K < 2 (2n - 1) S with slot stride S = 2 ceil(b/16) - 1."""
+    b = 1000 if K <= 18 else (8192 if K <= 22 else 33220)
+    S = 2 * -(-b // 16) - 1
+    return ((1 << K) // S + 1) // 2, b
+
+
+@pytest.mark.parametrize("K", range(13, 26))
+def test_ntt_every_pass_split(K):
+    """Transforms of 2^13 .. 2^25 points: every split of the stages into
+    passes of 6 to 9 (13 = 7 + 6 up to 25 = 9 + 8 + 8) and so every register
+    kernel shape, as the last (middle) pass and as a spaced one.  All rows
+    against the oracle where that is cheap, else 32 seeded rows (and the
+    largest) against it and all rows against the tensor-core path."""
+    n, b = ntt_case(K)
+    h = uniform_vec(9500 + K, 0, 2 * n - 1, b, 1)
+    x = uniform_vec(9500 + K, 1, n, b, 0)
+    with hmv.Plan(n, b, method=hmv.NTT) as p:
+        p.load_matrix(h)
+        y = p.matvec(x)
+        st = p.stats()
+    assert st["fft_log2_len"] == K
+    L32 = -(-b // 32)
+    if n * n * L32 * L32 <= 5e9:
+        assert_same(y, oracle_matvec(oracle.HANKEL, n, h, x))
+    else:
+        sampled_parity(oracle.HANKEL, n, h, x, y, 32, K)
+        with hmv.Plan(n, b) as p:
+            p.load_matrix(h)
+            assert_same(y, p.matvec(x))
