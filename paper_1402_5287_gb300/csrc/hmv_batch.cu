@@ -73,6 +73,11 @@ struct hmv_batch_s {
     hmv_plan_s *split_first = nullptr;  // status word and tile counter of the split launches
     hmv_plan_s *wave_first = nullptr;   // the same for the waves' launches (a member run in waves)
     std::vector<char> ntt;              // members on the exact NTT path (own buffers, no leaf products)
+    // parallel branches of the captured graph for the NTT members: side
+    // streams that fork from and join back to `stream` during the capture
+    std::vector<cudaStream_t> side;
+    cudaEvent_t fork_ev = nullptr;
+    std::vector<cudaEvent_t> join_ev;
 };
 
 namespace hmv {
@@ -89,6 +94,9 @@ cudaError_t balloc(hmv_batch_s *B, void **ptr, size_t bytes) {
 }
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+// Parallel branches of a batch graph for its NTT members.
+constexpr int kNttBranches = 8;
 
 size_t pair_bytes(const hmv_plan_s *p) {
     return align256(p->elems_xg * 2) + align256(p->bytes_dig) + align256(p->elems_carry * 4);
@@ -140,15 +148,45 @@ cudaError_t issue(hmv_batch_s *B) {
             kernels += 1 + std::max(p->L, 1);
         }
     }
-    // NTT members: transforms, pointwise product and extraction per right-hand side
-    for (size_t i = 0; i < B->plans.size() && e == cudaSuccess; ++i) {
-        hmv_plan_s *p = B->plans[i];
-        if (!B->ntt[i]) continue;
-        const int64_t before = p->launches_total;
-        for (int r = 0; r < p->nrhs && e == cudaSuccess; ++r)
-            e = ntt_vector_product(p, p->x_limbs_d + static_cast<size_t>(r) * p->n * p->L32,
-                                   p->x_neg_d + static_cast<size_t>(r) * p->n, r);
-        kernels += p->launches_total - before;
+    // NTT members: transforms, pointwise product and extraction per right-hand
+    // side, then the rounding, each member on one of the side streams (longest
+    // first onto the least loaded branch, by transform work): the graph gets
+    // parallel branches, so the short kernels of different members overlap
+    // on the device instead of running one after another
+    std::vector<int> nttm;
+    for (size_t i = 0; i < B->plans.size(); ++i)
+        if (B->ntt[i]) nttm.push_back(static_cast<int>(i));
+    if (!nttm.empty() && e == cudaSuccess) {
+        auto work = [&](int i) {
+            const hmv_plan_s *p = B->plans[i];
+            return static_cast<double>(p->nrhs) * static_cast<double>(p->ntt_N) * p->ntt_K;
+        };
+        std::stable_sort(nttm.begin(), nttm.end(), [&](int a, int b) { return work(a) > work(b); });
+        const int nb = static_cast<int>(std::min(B->side.size(), nttm.size()));
+        e = cudaEventRecord(B->fork_ev, B->stream);
+        for (int j = 0; j < nb && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(B->side[j], B->fork_ev, 0);
+        std::vector<double> load(nb, 0.0);
+        for (int i : nttm) {
+            if (e != cudaSuccess) break;
+            const int j = static_cast<int>(std::min_element(load.begin(), load.end()) - load.begin());
+            load[j] += work(i);
+            hmv_plan_s *p = B->plans[i];
+            p->stream = B->side[j];
+            const int64_t before = p->launches_total;
+            for (int r = 0; r < p->nrhs && e == cudaSuccess; ++r)
+                e = ntt_vector_product(p, p->x_limbs_d + static_cast<size_t>(r) * p->n * p->L32,
+                                       p->x_neg_d + static_cast<size_t>(r) * p->n, r);
+            if (e == cudaSuccess)
+                e = launch_round(p, p->n * p->nrhs, p->e_h + p->batch_x_exponent, p->y_limbs_d, p->y_neg_d);
+            kernels += p->launches_total - before + 2;
+            p->stream = B->stream;
+        }
+        // every branch joins back (also after an error: the capture must end joined)
+        for (int j = 0; j < nb; ++j) {
+            const cudaError_t je = cudaEventRecord(B->join_ev[j], B->side[j]);
+            const cudaError_t we = je == cudaSuccess ? cudaStreamWaitEvent(B->stream, B->join_ev[j], 0) : je;
+            if (e == cudaSuccess) e = we;
+        }
     }
     // split members: a round per right-hand side
     for (int r = 0; r < B->split_rounds && e == cudaSuccess; ++r) {
@@ -174,7 +212,9 @@ cudaError_t issue(hmv_batch_s *B) {
             kernels += p->launches_total - before;
         }
     }
-    for (hmv_plan_s *p : B->plans) {
+    for (size_t i = 0; i < B->plans.size(); ++i) {
+        hmv_plan_s *p = B->plans[i];
+        if (B->ntt[i]) continue;  // rounded in its branch
         if (e == cudaSuccess)
             e = launch_round(p, p->n * p->nrhs, p->e_h + p->batch_x_exponent, p->y_limbs_d, p->y_neg_d);
         kernels += 2;
@@ -210,6 +250,12 @@ void hmv_batch_free(hmv_batch_t *B) {
         hmv_free(p);
     }
     for (void *a : B->allocations) cudaFree(a);
+    for (cudaStream_t st : B->side) {
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    }
+    for (cudaEvent_t ev : B->join_ev) cudaEventDestroy(ev);
+    if (B->fork_ev) cudaEventDestroy(B->fork_ev);
     if (B->own_stream) cudaStreamDestroy(B->stream);
     delete B;
 }
@@ -277,6 +323,25 @@ hmv_status hmv_batch_create(int32_t count, const hmv_desc *descs, void *stream, 
         }
     }
     cudaError_t e = cudaSuccess;
+    int n_ntt = 0;
+    for (int i = 0; i < count; ++i) n_ntt += B->ntt[i];
+    if (n_ntt > 0) {  // the NTT members' graph branches (kNttBranches at most)
+        const int nb = std::min(n_ntt, kNttBranches);
+        e = cudaEventCreateWithFlags(&B->fork_ev, cudaEventDisableTiming);
+        for (int j = 0; j < nb && e == cudaSuccess; ++j) {
+            cudaStream_t st = nullptr;
+            cudaEvent_t ev = nullptr;
+            e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+            if (e == cudaSuccess) B->side.push_back(st);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e == cudaSuccess) B->join_ev.push_back(ev);
+        }
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            hmv_batch_free(B);
+            return HMV_ECUDA;
+        }
+    }
     size_t mA = 0, mX = 0, mP = 0;
     for (int i = 0; i < count; ++i) {
         if (B->split[i] || B->ntt[i]) continue;
