@@ -24,9 +24,10 @@
 // Montgomery form in two small tables per prime (w^m = T_hi[m >> 13] T_lo[m
 // & 8191]), data in normal form.  Radix-2 transforms, forward by decimation
 // in frequency (natural order in, bit-reversed out), inverse by decimation
-// in time (bit-reversed in, natural out), so no permutation pass; up to 9
-// stages per pass in shared memory, both primes in one pass (a uint2 per
-// point).  The matrix's spectrum is kept per plan, scaled by 1/N.
+// in time (bit-reversed in, natural out), so no permutation pass; passes of
+// 6 to 9 stages with the points in registers (one transpose through shared
+// memory a pass), both primes in one pass (a uint2 per point).  The matrix's
+// spectrum is kept per plan, scaled by 1/N.
 #include <cstring>
 #include <utility>
 #include <vector>
