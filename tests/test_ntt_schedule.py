@@ -241,3 +241,29 @@ def test_pass_split():
         NP, LG = shape(rs[-1])
         assert NP >= (1 << LG) and NP << LG == 1 << rs[-1]  # both layouts hold; 16 G threads cover 2^r points
         assert (1 << (K - rs[0])) >= 16  # the first pass has 16 columns a block
+
+
+@pytest.mark.parametrize("r", [6, 7, 8, 9])
+def test_spectrum_permutation_matches_middle_kernel_reads(r):
+    """k_ntt_scale_perm stores the matrix spectrum so that thread tid of the
+    middle kernel's block bx finds point NP (tid >> 4) + k of its column
+    tid & 15 at (bx NP + k) 16 G + tid: the store is a permutation of the N
+    points, and each of those reads lands on the point the lowest pass's
+    geometry names."""
+    NP, LG = shape(r)
+    lnp, lt = NP.bit_length() - 1, 4 + LG
+    K = r + 5  # two blocks of 16 columns
+    N = 1 << K
+    src = []
+    for o in range(N):  # the kernel's index arithmetic, entry by entry
+        bx, rem = o >> (lnp + lt), o & ((1 << (lnp + lt)) - 1)
+        k, tid = rem >> lt, rem & ((1 << lt) - 1)
+        q, gq = tid & 15, tid >> 4
+        src.append(((bx * 16 + q) << r) + (gq << lnp) + k)
+    assert sorted(src) == list(range(N))
+    for bx in range((N >> r) // 16):
+        g = geo(bx, r, r)
+        for tid in range(16 << LG):
+            q, gq = tid & 15, tid >> 4
+            for k in range(NP):
+                assert src[((bx * NP) << lt) + tid + (k << lt)] == gidx(g, NP * gq + k, q)
