@@ -230,7 +230,11 @@ hmv_status hmv_reset_stats(hmv_plan_t *plan);
  * one persistent launch over all their digit products per tile width, then
  * their interpolation.  HMV_NTT matrices (the exact NTT path; their size
  * limit as for hmv_plan) keep their own buffers too and run their
- * transforms for each right-hand side in the same graph.
+ * transforms for each right-hand side in the same graph, on up to eight
+ * parallel branches of it (the batch creates that many streams of its own
+ * when it has HMV_NTT members, forked from and joined back to `stream`, and
+ * destroys them in hmv_batch_free), so that different members' kernels
+ * overlap on the device.
  * stream: as for hmv_plan; NULL makes the batch create its own stream
  * (the legacy default stream cannot be captured).  Results are bit-identical
  * to hmv_matvec on each matrix alone.
