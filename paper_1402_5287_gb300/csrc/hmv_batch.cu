@@ -178,7 +178,7 @@ cudaError_t issue(hmv_batch_s *B) {
                                        p->x_neg_d + static_cast<size_t>(r) * p->n, r);
             if (e == cudaSuccess)
                 e = launch_round(p, p->n * p->nrhs, p->e_h + p->batch_x_exponent, p->y_limbs_d, p->y_neg_d);
-            kernels += p->launches_total - before + 2;
+            kernels += p->launches_total - before;  // the rounding's two launches included
             p->stream = B->stream;
         }
         // every branch joins back (also after an error: the capture must end joined)
