@@ -523,9 +523,23 @@ __global__ void __launch_bounds__(32 * kExWarps) k_ntt_extract(const uint2 *__re
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) k0 = min(k0, __shfl_xor_sync(0xffffffffu, k0, off));
         if (k0 == ZW) bad = true;
-        for (int w = lane; w < ZW; w += 32) {
-            if (w == k0) z[w] = ~z[w] + 1u;
-            else if (w > k0) z[w] = ~z[w];
+        // four limbs a lane per round, loaded before any is stored: with the
+        // loads and stores of z interleaved, each load waited for the one
+        // before (at n = 64 the matvec took 158.5 instead of 143 us)
+        for (int w0 = lane; w0 < ZW; w0 += 4 * 32) {
+            uint32_t v4[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int w = w0 + 32 * q;
+                v4[q] = w < ZW ? z[w] : 0u;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int w = w0 + 32 * q;
+                if (w >= ZW) break;
+                if (w == k0) z[w] = ~v4[q] + 1u;
+                else if (w > k0) z[w] = ~v4[q];
+            }
         }
         __syncwarp();
     }
